@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 state-vector simulator on the paper's random-circuit workload.
+
+Workload (one step): a 30-qubit complex128 state set to |0...0>, the seeded depth-20 random
+circuit (each layer U3 on every qubit, then CZ on (i, i+1) of the layer's parity; 890 gates),
+applied through a fusion plan whose width the library's autotuner picks, then <Z0 Z1>.
+The 16 GiB state is larger than L2, so every pass streams from HBM.
+
+value = gates/s (original gate count / device time per step; fusion shows up as a gain).
+roofline: the kernel with the largest share of device time, its algorithmic bytes per launch
+(2 x 16 B x the amplitudes it must update) over its event-timed duration, against the measured
+HBM copy bandwidth. e2e: the same metric through the public API call a user makes, wall clock,
+including planning, matrix uploads and the host read of the result.
+
+--impl reference times the FP64 CPU oracle on the same workload (bounded sample of gates per
+step). Multi-GPU (torchrun): independent replicas, one per rank, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "state-vector GB/s & gates/s at n=30 c128 vs HBM peak; adjoint-grad ms; circuits/s"
+HBM_PEAK_FALLBACK = 6800.0
+# DRAM bytes (read + write) per launch from one ncu capture, keyed by kernel; filled in only
+# for a kernel unchanged since the capture (profiles/<kernel>_<workload>.md gives the command).
+NCU_TRAFFIC = {}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=30)
+    p.add_argument("--depth", type=int, default=20)
+    p.add_argument("--seed", type=int, default=20201127)
+    p.add_argument("--fusion", type=int, default=-1, help="-1 autotune, 0 gate by gate, 1..6 width")
+    p.add_argument("--math", default="auto", choices=["auto", "fp64", "df"])
+    p.add_argument("--extras", type=int, default=1, help="also measure unfused, c64, adjoint (rank 0)")
+    p.add_argument("--cpu-sample-gates", type=int, default=9)
+    return p.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_PEAK_FALLBACK, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def zz_obs(n):
+    return W.PauliObservable(n, np.array([1.0]), np.array([0], dtype=np.uint64), np.array([3], dtype=np.uint64))
+
+
+# ---------------------------------------------------------------- CPU oracle timing
+def oracle_gates_per_s(n, circuit, n_gates):
+    """Oracle (FP64, OpenMP over B(0)) on a spread sample of the circuit's gates applied to an
+    n-qubit state; the per-gate cost does not depend on the amplitudes."""
+    import oracle
+    psi = oracle.zero_state(n)
+    idx = np.linspace(0, len(circuit.gates) - 1, n_gates).astype(int)
+    t0 = time.perf_counter()
+    for i in idx:
+        oracle.apply_gate(psi, n, circuit.gates[i])
+    dt = time.perf_counter() - t0
+    names = sorted({circuit.gates[i].name for i in idx})
+    return len(idx) / dt, oracle.threads(), dt, names
+
+
+def run_reference(args):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return
+    import oracle
+    circuit = W.u3cz_circuit(args.n, args.depth, args.seed)
+    n = args.n
+    psi = oracle.zero_state(n)
+    per_step = 3
+    rates = []
+    gi = 0
+    total_t = 0.0
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for _ in range(per_step):
+            oracle.apply_gate(psi, n, circuit.gates[gi % len(circuit.gates)])
+            gi += 1
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            rates.append(per_step / dt)
+            total_t += dt
+    v = len(rates) * per_step / total_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "gates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"random U3+CZ brickwork, n={n}, depth={args.depth}, complex128",
+                       "n": n, "depth": args.depth, "seed": args.seed},
+            "cpu_baseline": {"value": v, "unit": "gates/s", "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"{per_step} consecutive gates of the circuit per step on a 2^{n} state"},
+            "e2e": {"value": v, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    import paper_2011_13524_gb300 as qs
+
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        pg = tdist
+    qs.lib()
+    math_mode = {"fp64": qs.QS_MATH_FP64, "df": qs.QS_MATH_DF}.get(args.math)
+    if math_mode is not None:
+        qs.set_c128_math(math_mode)
+    n, dtype = args.n, qs.QS_C128
+    circuit = W.u3cz_circuit(n, args.depth, args.seed + rank)
+    G = len(circuit.gates)
+    zz = zz_obs(n)
+    stream = torch.cuda.current_stream()
+
+    t_plan0 = time.perf_counter()
+    if args.fusion < 0:
+        k, pred = qs.autotune_fusion(circuit, dtype)
+    else:
+        k, pred = args.fusion, None
+    plan = qs.FusedCircuit(circuit, k) if k > 0 else qs.FusedCircuit(circuit, 1)
+    plan_s = time.perf_counter() - t_plan0
+    if k == 0:
+        plan = None
+    st = qs.State(n, dtype)
+
+    costs = None
+    if plan is not None:
+        costs = [plan.block_cost(b, dtype) for b in range(plan.n_blocks)]
+
+    def step(timed_blocks=None):
+        st.set_basis(0)
+        if plan is None:
+            for g in circuit.gates:
+                st.apply_gate(g)
+        elif timed_blocks is not None:
+            timed_blocks.append(st.apply_plan_timed(plan))
+        else:
+            st.apply_plan(plan)
+        return st.expectation(zz)[0]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    block_times = []
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        result = step(block_times if plan is not None else None)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+        pg.barrier()
+    ms_per_step = ms / args.steps
+    value = ws * G * args.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel, from the per-block events of the timed steps
+    peak, peak_kind = measured_peaks()
+    roof = None
+    bytes_per_step = None
+    kernels_per_step = None
+    if plan is not None and block_times:
+        bt = np.mean(np.array(block_times), axis=0)
+        per_kernel = {}
+        for (kname, launches, by), t in zip(costs, bt):
+            if launches == 0:
+                continue
+            d = per_kernel.setdefault(kname, {"ms": 0.0, "bytes": 0.0, "launches": 0})
+            d["ms"] += float(t)
+            d["bytes"] += by
+            d["launches"] += launches
+        dom = max(per_kernel, key=lambda k_: per_kernel[k_]["ms"])
+        d = per_kernel[dom]
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": NCU_TRAFFIC.get(dom),
+                "bytes_per_launch": d["bytes"] / d["launches"], "ms_per_launch": d["ms"] / d["launches"],
+                "share_of_step": d["ms"] / ms_per_step,
+                "per_kernel_ms": {k_: round(v["ms"], 3) for k_, v in per_kernel.items()}}
+        bytes_per_step = sum(c[2] for c in costs)
+        kernels_per_step = sum(c[1] for c in costs)
+    launches_per_step = (kernels_per_step if kernels_per_step is not None else G) + 1 + 2
+
+    # e2e through the public API: host circuit in, host result out, planning included
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 2))
+    for _ in range(e2e_steps):
+        st.set_basis(0)
+        st.run(circuit, args.fusion)
+        st.expectation(zz)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    gate_desc = 120 * G  # sizeof(qs_gate) per gate descriptor read by the planner
+    wide = 0 if plan is None else sum(16 * (1 << len(plan.block(b)[0])) ** 2 for b in range(plan.n_blocks)
+                                       if len(plan.block(b)[0]) >= 4)
+    e2e = {"value": ws * G / e2e_s, "unit": "gates/s", "h2d_bytes_per_step": gate_desc + wide,
+           "d2h_bytes_per_step": 16, "wall_ms_per_step": 1e3 * e2e_s}
+
+    line = {"metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if qs.get_c128_math() == qs.QS_MATH_FP64 else "f32x2",
+            "data": "synthetic",
+            "config": {"workload": f"random U3+CZ brickwork, n={n}, depth={args.depth}, complex128, |0..0>, "
+                                   f"fused (autotuned width), then <Z0Z1>",
+                       "n": n, "depth": args.depth, "gates": G, "seed": args.seed, "fusion_k": k,
+                       "autotune_pred_ms": pred, "plan_blocks": None if plan is None else plan.n_blocks,
+                       "l2": "state 16 GiB > 129 MB L2 (no flush needed)", "replicas": ws},
+            "roofline": roof, "e2e": e2e, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
+            "result_z0z1": result, "plan_ms": 1e3 * plan_s}
+    if bytes_per_step is not None:
+        line["state_gbps"] = bytes_per_step / (ms_per_step / 1e3) / 1e9
+        line["state_frac_hbm"] = line["state_gbps"] / peak
+
+    if rank == 0 and ws == 1:
+        extras = {}
+        if args.extras:
+            del st
+            torch.cuda.empty_cache()
+            extras = measure_extras(args, qs, torch, circuit)
+        line["extras"] = extras
+        rate, cores, dt, names = oracle_gates_per_s(n, circuit, args.cpu_sample_gates)
+        line["cpu_baseline"] = {"value": rate, "unit": "gates/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{args.cpu_sample_gates} gates spread over the circuit ({'/'.join(names)}) "
+                                          f"applied to a 2^{n} complex128 state, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def measure_extras(args, qs, torch, circuit):
+    """Secondary numbers of the same run: unfused per-gate rate, complex64, adjoint gradient."""
+    out = {}
+    n = args.n
+    G = len(circuit.gates)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=1):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    st = qs.State(n, qs.QS_C128)
+    ms = timed(lambda: (st.set_basis(0), st.run(circuit, 0)))
+    out["c128_unfused_gates_per_s"] = G / (ms / 1e3)
+    del st
+    torch.cuda.empty_cache()
+    st = qs.State(n, qs.QS_C64)
+    k64, _ = qs.autotune_fusion(circuit, qs.QS_C64)
+    plan64 = qs.FusedCircuit(circuit, max(k64, 1))
+    ms = timed(lambda: (st.set_basis(0), st.apply_plan(plan64) if k64 else st.run(circuit, 0)), reps=2)
+    out["c64_fused_gates_per_s"] = G / (ms / 1e3)
+    out["c64_fusion_k"] = k64
+    ms = timed(lambda: (st.set_basis(0), st.run(circuit, 0)))
+    out["c64_unfused_gates_per_s"] = G / (ms / 1e3)
+    del st
+    torch.cuda.empty_cache()
+    # adjoint: n = 20 hardware-efficient ansatz, 20 layers, H = sum ZZ + sum X, complex128
+    hea = W.hea_circuit(20, 20, args.seed)
+    H = W.tfim_observable(20, 1.0)
+    qs.adjoint_grad(hea, H)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e, g = qs.adjoint_grad(hea, H)
+    out["adjoint_ms_n20_l20_c128"] = 1e3 * (time.perf_counter() - t0)
+    out["adjoint_params"] = int(hea.n_params)
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

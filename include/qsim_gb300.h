@@ -1,0 +1,241 @@
+/*
+ * qsim_gb300.h -- C ABI of the GB300 (sm_103a) state-vector simulator library
+ * (libqsim_gb300.so).
+ *
+ * The library applies quantum gates to a full 2^n-amplitude state vector held in the
+ * device memory of one GPU, evaluates Pauli observables on it, and differentiates
+ * parametric circuits, following the Schroedinger-method simulator of the Qulacs paper
+ * (Suzuki et al., Quantum 5, 559 (2021); arXiv 2011.13524).
+ *
+ * Conventions shared by every call:
+ *  - State layout (Sec. 4.2.1): amplitude psi_x of basis state |x> sits at index x of a
+ *    contiguous array of interleaved (re, im) pairs; qubit i is bit i of x ("the right-most
+ *    digit is the 0-th qubit"). QS_C128 stores two IEEE doubles per amplitude (16 bytes),
+ *    QS_C64 two IEEE floats (8 bytes).
+ *  - Gate matrix (Sec. 4.3.2, Eq. update_mat): a 2^m x 2^m complex matrix K~ in row-major
+ *    order, row = output local index z, column = input local index w, each element two
+ *    doubles (re, im); bit j of a local index corresponds to targets[j]. K need not be
+ *    unitary; no call renormalises the state.
+ *  - Every function returns a qs_status; QS_OK is 0. On any other value a message is
+ *    available from qs_last_error() (per calling thread). No C++ exception crosses this
+ *    boundary.
+ *  - Calls that only launch work are asynchronous on the state's CUDA stream. Calls that
+ *    return a host value (expectation, norm, inner product, gradients, get_vector)
+ *    synchronise that stream before returning. Errors that kernels record on the device
+ *    are reported by the next synchronising call.
+ *  - Host pointers passed in are only read during the call; the library keeps no
+ *    reference to them. Device memory passed to qs_wrap_state stays owned by the caller.
+ */
+#ifndef QSIM_GB300_H
+#define QSIM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int qs_status;
+#define QS_OK 0
+#define QS_ERR_INVALID_ARG 1 /* bad qubit index, duplicate qubit, null pointer, size out of range */
+#define QS_ERR_OOM 2         /* device allocation failed; nothing was leaked */
+#define QS_ERR_CUDA 3        /* a CUDA runtime call failed (message carries cudaGetErrorString) */
+#define QS_ERR_UNSUPPORTED 4 /* valid request the library does not implement */
+#define QS_ERR_TIMEOUT 5     /* a bounded device-side wait gave up */
+#define QS_ERR_NUMERIC 6     /* a result that must be real came out with a non-zero imaginary part */
+
+typedef int qs_dtype;
+#define QS_C64 1  /* complex64 storage, FP32 gate arithmetic with FP64-built matrices, FP64-class accumulation */
+#define QS_C128 2 /* complex128 storage */
+
+/* Arithmetic used for complex128 gate updates (qs_set_c128_math). */
+#define QS_MATH_FP64 0 /* native FP64 multiply-adds */
+#define QS_MATH_DF 1   /* double-float (two FP32 words per double, ~2^-46 relative) on the FP32 pipes */
+
+#define QS_MAX_QUBITS 34
+#define QS_MAX_TARGETS 6
+#define QS_MAX_CONTROLS 8
+
+/* Gate kinds (Sec. 4.3.2 basic gates). */
+#define QS_GATE_DENSE 0 /* mat = 2^m x 2^m gate matrix */
+#define QS_GATE_DIAG 1  /* mat = 2^m diagonal entries, psi_x <- d[r(x)] psi_x */
+#define QS_GATE_PAULI 2 /* pauli[j] in {0,1,2,3} = {I,X,Y,Z} on targets[j] */
+#define QS_GATE_NAMED 3 /* named gate of the paper's gate table, see QS_NAMED_* */
+
+/* Named gates (Sec. 4.3.3 gate table). Rotations are exp(+i theta P / 2) (the table's sign);
+ * U1/U2/U3 follow OpenQASM 2; S = diag(1,i), T = diag(1,e^{i pi/4}), sqrtX/sqrtY are the
+ * principal square roots of X/Y. Qubits: 1-qubit gates use targets[0]; CNOT and TOFFOLI are X
+ * on targets[0] with their controls in controls[]; CZ acts on targets[0..1]; SWAP on
+ * targets[0..1]; FREDKIN is SWAP on targets[0..1] with controls[0]; PAULIROT is
+ * exp(i params[0] P / 2) for the Pauli string pauli[] on targets[0..m-1]. */
+#define QS_NAMED_X 1
+#define QS_NAMED_Y 2
+#define QS_NAMED_Z 3
+#define QS_NAMED_H 4
+#define QS_NAMED_S 5
+#define QS_NAMED_SDAG 6
+#define QS_NAMED_T 7
+#define QS_NAMED_TDAG 8
+#define QS_NAMED_SQRTX 9
+#define QS_NAMED_SQRTXDAG 10
+#define QS_NAMED_SQRTY 11
+#define QS_NAMED_SQRTYDAG 12
+#define QS_NAMED_RX 13
+#define QS_NAMED_RY 14
+#define QS_NAMED_RZ 15
+#define QS_NAMED_U1 16
+#define QS_NAMED_U2 17
+#define QS_NAMED_U3 18
+#define QS_NAMED_CNOT 19
+#define QS_NAMED_CZ 20
+#define QS_NAMED_SWAP 21
+#define QS_NAMED_TOFFOLI 22
+#define QS_NAMED_FREDKIN 23
+#define QS_NAMED_PAULIROT 24
+
+/* One gate. Controls: the gate acts only on the block where qubit controls[j] holds
+ * control_values[j] (Sec. 4.3.2 controlled gates, add_control_qubit); controls and targets
+ * must be disjoint. param_index >= 0 marks a parametric rotation (RX, RY, RZ, PAULIROT) whose
+ * angle is theta[param_index] in qs_adjoint_grad and qs_batch_run; elsewhere params[0] is used. */
+typedef struct qs_gate {
+    int32_t kind;
+    int32_t named;
+    int32_t m;                                /* number of targets, 1..QS_MAX_TARGETS */
+    int32_t targets[QS_MAX_TARGETS];
+    int32_t mc;                               /* number of controls, 0..QS_MAX_CONTROLS */
+    int32_t controls[QS_MAX_CONTROLS];
+    int32_t control_values[QS_MAX_CONTROLS];
+    int32_t pauli[QS_MAX_TARGETS];
+    int32_t param_index;
+    int32_t reserved;
+    double params[3];
+    const double* mat;                        /* host pointer (DENSE, DIAG), else NULL */
+} qs_gate;
+
+/* An ordered gate array (Sec. 4.4): gates are applied first to last. */
+typedef struct qs_circuit {
+    int32_t n;                                /* qubits */
+    int32_t n_gates;
+    int32_t n_params;                         /* parameters referenced by param_index */
+    int32_t reserved;
+    const qs_gate* gates;                     /* host array of n_gates */
+} qs_circuit;
+
+/* O = sum_k coef[k] P_k (Sec. 4.5), P_k by masks: bit q of x_mask set for X or Y on qubit q,
+ * bit q of z_mask set for Z or Y on qubit q. A term with both masks 0 is coef * identity. */
+typedef struct qs_pauli_obs {
+    int32_t n_terms;
+    int32_t reserved;
+    const double* coef;                       /* host, n_terms */
+    const uint64_t* x_mask;                   /* host, n_terms */
+    const uint64_t* z_mask;                   /* host, n_terms */
+} qs_pauli_obs;
+
+typedef struct qs_state qs_state;             /* opaque */
+typedef struct qs_fused_circuit qs_fused_circuit; /* opaque */
+
+/* ---------------------------------------------------------------- library */
+/* Message of the last failing call on this thread ("" if none). Never NULL. */
+const char* qs_last_error(void);
+/* Library version string. */
+const char* qs_version(void);
+/* Arithmetic for complex128 gate updates, process-wide: QS_MATH_FP64 or QS_MATH_DF. */
+qs_status qs_set_c128_math(int mode);
+qs_status qs_get_c128_math(int* mode);
+
+/* ---------------------------------------------------------------- states (Sec. 4.2) */
+/* Allocates a 2^n state of type dt on the current device and sets it to |0...0>
+ * (Sec. 4.2.1 default initialisation). stream: a cudaStream_t (NULL = legacy default).
+ * The library owns the memory; release it with qs_destroy_state. n in [1, QS_MAX_QUBITS]. */
+qs_status qs_create_state(int n, qs_dtype dt, void* stream, qs_state** out);
+/* Wraps caller-owned device memory of 2^n amplitudes of type dt (16-byte aligned). The
+ * contents are left as they are. qs_destroy_state frees only the handle. */
+qs_status qs_wrap_state(void* dev_ptr, int n, qs_dtype dt, void* stream, qs_state** out);
+/* Frees the handle (and the memory, if the library allocated it). NULL is accepted. */
+qs_status qs_destroy_state(qs_state* s);
+/* Reports the qubit count, dtype and device pointer of a state (any output may be NULL). */
+qs_status qs_state_info(const qs_state* s, int* n, qs_dtype* dt, void** dev_ptr);
+/* Changes the stream on which later calls on this state run. */
+qs_status qs_set_stream(qs_state* s, void* stream);
+/* Computational basis state |j> (Sec. 4.2.1 set_computational_basis); j < 2^n. */
+qs_status qs_set_basis(qs_state* s, uint64_t j);
+/* Copies 2^n amplitudes of the state's dtype from src (host if is_device == 0, else device). */
+qs_status qs_load(qs_state* s, const void* src, int is_device);
+/* Copies the state into host memory of 2^n amplitudes (Sec. 4.2.2 get_vector); synchronises. */
+qs_status qs_get_vector(const qs_state* s, void* host_out);
+/* dst <- src; both states must have equal n and dtype (Sec. 4.2.1 load of another state). */
+qs_status qs_copy_state(const qs_state* src, qs_state* dst);
+/* Waits for the state's stream and reports device-side errors. */
+qs_status qs_synchronize(const qs_state* s);
+
+/* ---------------------------------------------------------------- gates (Sec. 4.3) */
+/* psi <- K psi for one gate (Eq. update_mat; controlled, diagonal, Pauli and named forms). */
+qs_status qs_apply_gate(qs_state* s, const qs_gate* g);
+/* psi <- K psi for a dense k-qubit matrix (k in 1..6), as produced by gate fusion
+ * (Sec. 5.4 merge). Equivalent to qs_apply_gate with a QS_GATE_DENSE gate. */
+qs_status qs_apply_fused(qs_state* s, int k, const int* targets, const double* mat);
+/* Applies every gate of c in order. fusion_k = 0 applies gate by gate; 1..6 first merges
+ * neighbouring gates into dense blocks of at most fusion_k qubits (Sec. 5.4, the light
+ * strategy: a gate joins the open block while the union of targets stays within the width);
+ * -1 picks the width with qs_autotune_fusion. c->n must equal the state's n. */
+qs_status qs_run_circuit(qs_state* s, const qs_circuit* c, int fusion_k);
+
+/* ---------------------------------------------------------------- fusion (Sec. 5.4) */
+/* Plans the fused circuit for width k (2..6) without applying it. */
+qs_status qs_plan_fusion(const qs_circuit* c, int k, qs_fused_circuit** out);
+/* Number of blocks of a plan and, for block b, its width and targets (ascending) and its
+ * FP64 matrix (2^w x 2^w complex, row-major) copied to host memory; any output may be NULL. */
+qs_status qs_fused_info(const qs_fused_circuit* f, int* n_blocks, int* n_source_gates);
+qs_status qs_fused_block(const qs_fused_circuit* f, int b, int* width, int* targets, double* mat);
+/* Applies a plan to a state (the plan's n must match). */
+qs_status qs_apply_fused_circuit(qs_state* s, const qs_fused_circuit* f);
+qs_status qs_destroy_fused(qs_fused_circuit* f);
+
+/* Kernel that performs block b of a plan on a state of type dt, and its algorithmic memory
+ * traffic: the bytes of state the update must read and write (Sec. 5.1 cost model,
+ * N_mem), e.g. 2 * 2^(n - controls) amplitudes for a dense block. kernel: one of QS_KERNEL_*;
+ * launches: kernels launched for the block (0 for an identity). Outputs may be NULL. */
+#define QS_KERNEL_DENSE_REG 0  /* dense gate matrix, 1..3 targets (1..4 for complex64), registers */
+#define QS_KERNEL_DENSE_SMEM 1 /* dense gate matrix, 4..6 targets, shared-memory tiles */
+#define QS_KERNEL_DIAG 2       /* diagonal gate */
+#define QS_KERNEL_PHASE 3      /* phase on the subspace of fixed bits */
+#define QS_KERNEL_PAULI 4      /* Pauli string (permutation with phases) */
+#define QS_KERNEL_SWAP 5       /* SWAP / controlled SWAP */
+#define QS_KERNEL_DENSE_DF 6   /* complex128 dense gate matrix in double-float arithmetic */
+qs_status qs_fused_block_cost(const qs_fused_circuit* f, int b, qs_dtype dt, int* kernel, int* launches,
+                              double* bytes);
+/* Applies a plan like qs_apply_fused_circuit, recording a CUDA event on the state's stream
+ * after every block; block_ms[b] receives the device time of block b. Synchronises. */
+qs_status qs_apply_fused_circuit_timed(qs_state* s, const qs_fused_circuit* f, float* block_ms);
+/* Fusion-width autotuner: plans c for every width 1..6, predicts each plan's device time from
+ * per-kernel costs measured on this GPU (timed once per process on a scratch state of
+ * min(n, 24) qubits and scaled by 2^n), and returns the fastest width in *best_k. pred_ms
+ * (optional, 7 entries): index 0 = gate by gate, 1..6 = fused widths. */
+qs_status qs_autotune_fusion(const qs_circuit* c, qs_dtype dt, int* best_k, double* pred_ms);
+
+/* ---------------------------------------------------------------- observables (Sec. 4.5) */
+/* out[0] = Re sum_k coef[k] <psi|P_k|psi>, out[1] = its imaginary part (zero up to rounding for
+ * real coefficients). Accumulates in FP64 for both dtypes; synchronises. */
+qs_status qs_expectation(const qs_state* s, const qs_pauli_obs* obs, double out[2]);
+/* out = <a|b> (Sec. 4.2.2 inner_product) as (re, im); same n and dtype; synchronises. */
+qs_status qs_inner_product(const qs_state* a, const qs_state* b, double out[2]);
+/* out = <psi|psi> (Sec. 4.2.2 get_squared_norm); synchronises. */
+qs_status qs_norm2(const qs_state* s, double* out);
+
+/* ---------------------------------------------------------------- adjoint gradient */
+/* Energy E = <psi(theta)|H|psi(theta)>, psi(theta) = U_G ... U_1 |0...0>, and dE/dtheta_p for
+ * every parameter p of c (the gates with param_index = p; a parameter shared by several gates
+ * gets the sum), by the reverse-sweep adjoint method: with lambda = H psi, each gate is
+ * un-applied from psi and lambda in turn and a rotation exp(i theta P / 2) contributes
+ * -Im <lambda|P|psi> at its position. The paper gives the parametric circuit (Sec. 4.4) but no
+ * gradient; the sign follows from its rotation convention. theta: host, c->n_params values
+ * (NULL = use each gate's params[0]). grad: host, c->n_params. Uses three device buffers of
+ * 2^n amplitudes of type dt on `stream`; synchronises. */
+qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pauli_obs* H,
+                          qs_dtype dt, void* stream, double* energy, double* grad);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSIM_GB300_H */

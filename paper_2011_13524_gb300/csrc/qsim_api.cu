@@ -1,0 +1,760 @@
+// C ABI of libqsim_gb300.so: states, gate application, fusion plans, reductions and the
+// adjoint gradient. Every entry point converts C++ errors into a qs_status and a
+// thread-local message; nothing throws across the boundary.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <memory>
+#include <new>
+#include <string>
+
+#include "qsim_internal.h"
+
+namespace qs {
+
+namespace {
+thread_local std::string g_err;
+std::atomic<int> g_c128_math{QS_MATH_FP64};
+}  // namespace
+
+void set_error(const std::string& msg) { g_err = msg; }
+void clear_error() { g_err.clear(); }
+int c128_math() { return g_c128_math.load(); }
+
+namespace {
+
+void check_state(const qs_state* s) { QS_REQUIRE(s != nullptr && s->data != nullptr, "null state"); }
+
+void* stage_of(qs_state* s) {
+    if (!s->d_stage) QS_TRY_CUDA(cudaMalloc(&s->d_stage, kStageBytes));
+    return s->d_stage;
+}
+
+void free_state_resources(qs_state* s) {
+    if (s->scratch.d_part) cudaFree(s->scratch.d_part);
+    if (s->scratch.h_out) cudaFreeHost(s->scratch.h_out);
+    if (s->d_stage) cudaFree(s->d_stage);
+    if (s->owns && s->data) cudaFree(s->data);
+    s->scratch = Scratch{};
+    s->d_stage = nullptr;
+    s->data = nullptr;
+}
+
+// adjoint of an operator: conjugate transpose (Pauli strings and SWAP are Hermitian)
+Op dagger(const Op& op) {
+    Op r = op;
+    switch (op.kind) {
+        case OpKind::Dense: {
+            const int D = 1 << int(op.targets.size());
+            for (int z = 0; z < D; z++)
+                for (int w = 0; w < D; w++) r.data[size_t(z) * D + w] = std::conj(op.data[size_t(w) * D + z]);
+            r.dmat = nullptr;
+            break;
+        }
+        case OpKind::Diag:
+            for (auto& v : r.data) v = std::conj(v);
+            break;
+        case OpKind::Phase: r.phase = std::conj(op.phase); break;
+        case OpKind::Pauli:
+        case OpKind::Swap: break;
+    }
+    return r;
+}
+
+void run_gates(qs_state* s, const qs_circuit* c, const double* theta) {
+    for (int i = 0; i < c->n_gates; i++) {
+        Op op = op_of_gate(c->gates[i], s->n, theta);
+        launch_op(op, s->data, s->n, s->dt, s->stream, stage_of(s));
+    }
+}
+
+}  // namespace
+
+// Kernel form of block b of a plan (a single gate keeps its own cheapest form).
+Op block_op(const FusionPlan& p, size_t b) {
+    const FusedBlock& fb = p.blocks[b];
+    if (fb.single_gate >= 0) return op_of_gate(p.source[fb.single_gate], p.n, nullptr);
+    Op op;
+    op.targets = fb.qubits;
+    const int D = 1 << int(fb.qubits.size());
+    if (fb.diagonal) {
+        op.kind = OpKind::Diag;
+        op.data.resize(D);
+        for (int i = 0; i < D; i++) op.data[i] = fb.mat[size_t(i) * D + i];
+    } else {
+        op.kind = OpKind::Dense;
+        op.data = fb.mat;
+    }
+    return op;
+}
+
+// Algorithmic traffic of an op on a 2^n state: amplitudes the update must read and write.
+void op_cost(const Op& op, int n, qs_dtype dt, int* kernel, int* launches, double* bytes) {
+    const double S = double(amp_bytes(dt));
+    const int mc = int(op.controls.size());
+    const double touched = std::ldexp(1.0, n - mc);
+    int k = QS_KERNEL_DENSE_REG, l = 1;
+    double by = 2.0 * S * touched;
+    switch (op.kind) {
+        case OpKind::Dense: {
+            const int m = int(op.targets.size());
+            const bool reg = m <= 3 || (m == 4 && dt == QS_C64);
+            k = reg ? QS_KERNEL_DENSE_REG : QS_KERNEL_DENSE_SMEM;
+            if (dt == QS_C128 && c128_math() == QS_MATH_DF && m <= 3) k = QS_KERNEL_DENSE_DF;
+            break;
+        }
+        case OpKind::Diag: k = QS_KERNEL_DIAG; break;
+        case OpKind::Phase:
+            k = QS_KERNEL_PHASE;
+            if (op.phase == cplx(1.0, 0.0)) { l = 0; by = 0.0; }
+            break;
+        case OpKind::Pauli:
+            k = QS_KERNEL_PAULI;
+            if (op.xmask == 0 && op.zmask == 0) { l = 0; by = 0.0; }
+            else if (op.xmask == 0) by = 1.5 * S * touched;   // read all, write the odd-parity half
+            break;
+        case OpKind::Swap: k = QS_KERNEL_SWAP; by = S * touched; break;
+    }
+    if (kernel) *kernel = k;
+    if (launches) *launches = l;
+    if (bytes) *bytes = by;
+}
+
+namespace {
+// Device copies of the wide (>= 4 target) dense matrices of a plan, in the state's element
+// type, uploaded once per application on the state's stream.
+struct WideMats {
+    void* dbuf = nullptr;
+    std::vector<const void*> ptr;
+};
+
+WideMats upload_wide(qs_state* s, const FusionPlan& p, std::vector<Op>& ops) {
+    WideMats w;
+    w.ptr.assign(ops.size(), nullptr);
+    size_t total = 0;
+    std::vector<size_t> offs(ops.size(), 0);
+    for (size_t b = 0; b < ops.size(); b++) {
+        if (ops[b].kind != OpKind::Dense || ops[b].targets.size() < 4) continue;
+        offs[b] = total;
+        total += ops[b].data.size() * amp_bytes(s->dt);
+    }
+    if (!total) return w;
+    std::vector<unsigned char> host(total);
+    for (size_t b = 0; b < ops.size(); b++) {
+        if (ops[b].kind != OpKind::Dense || ops[b].targets.size() < 4) continue;
+        unsigned char* dst = host.data() + offs[b];
+        for (size_t e = 0; e < ops[b].data.size(); e++) {
+            if (s->dt == QS_C64) {
+                float v[2] = {float(ops[b].data[e].real()), float(ops[b].data[e].imag())};
+                std::memcpy(dst + 8 * e, v, 8);
+            } else {
+                double v[2] = {ops[b].data[e].real(), ops[b].data[e].imag()};
+                std::memcpy(dst + 16 * e, v, 16);
+            }
+        }
+    }
+    QS_TRY_CUDA(cudaMallocAsync(&w.dbuf, total, s->stream));
+    QS_TRY_CUDA(cudaMemcpyAsync(w.dbuf, host.data(), total, cudaMemcpyHostToDevice, s->stream));
+    cudaStreamSynchronize(s->stream);  // the host staging vector dies on return
+    for (size_t b = 0; b < ops.size(); b++)
+        if (ops[b].kind == OpKind::Dense && ops[b].targets.size() >= 4) {
+            w.ptr[b] = static_cast<unsigned char*>(w.dbuf) + offs[b];
+            ops[b].dmat = w.ptr[b];
+        }
+    return w;
+}
+
+void apply_plan_impl(qs_state* s, const FusionPlan& p, float* block_ms) {
+    QS_REQUIRE(p.n == s->n, "plan and state have different qubit counts");
+    std::vector<Op> ops;
+    ops.reserve(p.blocks.size());
+    for (size_t b = 0; b < p.blocks.size(); b++) ops.push_back(block_op(p, b));
+    WideMats wm = upload_wide(s, p, ops);
+    std::vector<cudaEvent_t> ev;
+    try {
+        if (block_ms) {
+            ev.resize(ops.size() + 1);
+            for (auto& e : ev) QS_TRY_CUDA(cudaEventCreate(&e));
+            QS_TRY_CUDA(cudaEventRecord(ev[0], s->stream));
+        }
+        for (size_t b = 0; b < ops.size(); b++) {
+            launch_op(ops[b], s->data, s->n, s->dt, s->stream, stage_of(s));
+            if (block_ms) QS_TRY_CUDA(cudaEventRecord(ev[b + 1], s->stream));
+        }
+        if (block_ms) {
+            QS_TRY_CUDA(cudaEventSynchronize(ev.back()));
+            for (size_t b = 0; b < ops.size(); b++) QS_TRY_CUDA(cudaEventElapsedTime(&block_ms[b], ev[b], ev[b + 1]));
+        }
+    } catch (...) {
+        for (auto& e : ev) cudaEventDestroy(e);
+        if (wm.dbuf) cudaFreeAsync(wm.dbuf, s->stream);
+        throw;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (wm.dbuf) QS_TRY_CUDA(cudaFreeAsync(wm.dbuf, s->stream));
+}
+
+}  // namespace
+
+void apply_plan(qs_state* s, const FusionPlan& p) { apply_plan_impl(s, p, nullptr); }
+
+// ------------------------------------------------------------------ autotuner
+// Seconds per algorithmic byte of each kernel form, measured once per process and device
+// on a scratch state, keyed by (device, dtype, c128 arithmetic, kernel, targets).
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, double> g_cost;
+
+double measure_cost(int dev, qs_dtype dt, const Op& probe_op, int np_) {
+    qs_state* s = nullptr;
+    qs_status rc = qs_create_state(np_, dt, nullptr, &s);
+    if (rc != QS_OK) throw Error{rc, std::string("autotune: ") + qs_last_error()};
+    struct G {
+        qs_state* s;
+        ~G() { qs_destroy_state(s); }
+    } g{s};
+    Op op = probe_op;
+    std::vector<Op> one{op};
+    FusionPlan dummy;
+    dummy.n = np_;
+    WideMats wm;
+    if (op.kind == OpKind::Dense && op.targets.size() >= 4) {
+        wm = upload_wide(s, dummy, one);
+        op = one[0];
+    }
+    cudaEvent_t e0, e1;
+    QS_TRY_CUDA(cudaEventCreate(&e0));
+    QS_TRY_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int r = 0; r < 4; r++) {
+        QS_TRY_CUDA(cudaEventRecord(e0, s->stream));
+        launch_op(op, s->data, s->n, s->dt, s->stream, stage_of(s));
+        QS_TRY_CUDA(cudaEventRecord(e1, s->stream));
+        QS_TRY_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        QS_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (r > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (wm.dbuf) cudaFree(wm.dbuf);
+    (void)dev;
+    double bytes = 0;
+    op_cost(op, np_, dt, nullptr, nullptr, &bytes);
+    return bytes > 0 ? 1e-3 * best / bytes : 0.0;
+}
+
+// representative op of the same kernel form and width as `op`, on a probe state of np_ qubits
+Op probe_like(const Op& op, int np_) {
+    static const int spread[6] = {0, -1, -2, 1, -3, 2};  // low and high qubits mixed
+    auto q = [&](int j) { return spread[j] >= 0 ? spread[j] : np_ + spread[j]; };
+    Op p;
+    p.kind = op.kind;
+    switch (op.kind) {
+        case OpKind::Dense: {
+            const int m = int(op.targets.size());
+            for (int j = 0; j < m; j++) p.targets.push_back(q(j));
+            const int D = 1 << m;
+            p.data.assign(size_t(D) * D, cplx(0.0, 0.0));
+            for (int z = 0; z < D; z++)
+                for (int w = 0; w < D; w++) p.data[size_t(z) * D + w] = std::polar(1.0 / std::sqrt(double(D)), 0.37 * z * w + 0.1);
+            break;
+        }
+        case OpKind::Diag: {
+            const int m = int(op.targets.size());
+            for (int j = 0; j < m; j++) p.targets.push_back(q(j));
+            for (int i = 0; i < (1 << m); i++) p.data.push_back(std::polar(1.0, 0.3 * i + 0.2));
+            break;
+        }
+        case OpKind::Phase:
+            p.controls = {q(0), q(1)};
+            p.cvals = {1, 1};
+            p.phase = -1.0;
+            break;
+        case OpKind::Pauli: p.xmask = 1ull << q(1); break;
+        case OpKind::Swap: p.targets = {q(0), q(1)}; break;
+    }
+    return p;
+}
+
+double predicted_seconds(const Op& op, int n, qs_dtype dt) {
+    int kernel = 0, launches = 0;
+    double bytes = 0;
+    op_cost(op, n, dt, &kernel, &launches, &bytes);
+    if (!launches) return 0.0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int width = op.kind == OpKind::Dense || op.kind == OpKind::Diag ? int(op.targets.size()) : 0;
+    auto key = std::make_tuple(dev, int(dt), dt == QS_C128 ? c128_math() : 0, kernel, width);
+    double per_byte;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_cost.find(key);
+        if (it != g_cost.end()) {
+            per_byte = it->second;
+        } else {
+            const int np_ = std::max(8, std::min(n, dt == QS_C64 ? 25 : 24));
+            per_byte = measure_cost(dev, dt, probe_like(op, np_), np_);
+            g_cost[key] = per_byte;
+        }
+    }
+    return per_byte * bytes + 2e-6;  // + launch overhead
+}
+
+double predict_plan(const FusionPlan& p, qs_dtype dt) {
+    double t = 0;
+    for (size_t b = 0; b < p.blocks.size(); b++) t += predicted_seconds(block_op(p, b), p.n, dt);
+    return t;
+}
+
+double predict_unfused(const qs_circuit* c, qs_dtype dt) {
+    double t = 0;
+    for (int i = 0; i < c->n_gates; i++) t += predicted_seconds(op_of_gate(c->gates[i], c->n, nullptr), c->n, dt);
+    return t;
+}
+
+int autotune(const qs_circuit* c, qs_dtype dt, double* pred_ms) {
+    double best = predict_unfused(c, dt);
+    if (pred_ms) pred_ms[0] = 1e3 * best;
+    int best_k = 0;
+    for (int k = 1; k <= QS_MAX_TARGETS; k++) {
+        const double t = predict_plan(plan_fusion(c, k), dt);
+        if (pred_ms) pred_ms[k] = 1e3 * t;
+        if (t < best) {
+            best = t;
+            best_k = k;
+        }
+    }
+    return best_k;
+}
+}  // namespace
+
+}  // namespace qs
+
+using namespace qs;
+
+#define API_BEGIN \
+    try {         \
+        clear_error();
+#define API_END                                  \
+    }                                            \
+    catch (const Error& e) {                     \
+        set_error(e.msg);                        \
+        return e.code;                           \
+    }                                            \
+    catch (const std::bad_alloc&) {              \
+        set_error("host allocation failed");     \
+        return QS_ERR_OOM;                       \
+    }                                            \
+    catch (const std::exception& e) {            \
+        set_error(e.what());                     \
+        return QS_ERR_CUDA;                      \
+    }                                            \
+    return QS_OK;
+
+extern "C" {
+
+const char* qs_last_error(void) { return g_err.c_str(); }
+
+const char* qs_version(void) { return "qsim_gb300 0.1 (sm_103a)"; }
+
+qs_status qs_set_c128_math(int mode) {
+    API_BEGIN
+    QS_REQUIRE(mode == QS_MATH_FP64 || mode == QS_MATH_DF, "unknown complex128 arithmetic mode");
+    g_c128_math.store(mode);
+    API_END
+}
+
+qs_status qs_get_c128_math(int* mode) {
+    API_BEGIN
+    QS_REQUIRE(mode != nullptr, "null output");
+    *mode = g_c128_math.load();
+    API_END
+}
+
+qs_status qs_create_state(int n, qs_dtype dt, void* stream, qs_state** out) {
+    API_BEGIN
+    QS_REQUIRE(out != nullptr, "null output");
+    *out = nullptr;
+    QS_REQUIRE(n >= 1 && n <= QS_MAX_QUBITS, "qubit count out of range (1..34)");
+    QS_REQUIRE(dt == QS_C64 || dt == QS_C128, "unknown dtype");
+    std::unique_ptr<qs_state> s(new qs_state());
+    s->n = n;
+    s->dt = dt;
+    s->stream = static_cast<cudaStream_t>(stream);
+    s->owns = true;
+    QS_TRY_CUDA(cudaGetDevice(&s->device));
+    const size_t bytes = (size_t(1) << n) * amp_bytes(dt);
+    cudaError_t e = cudaMalloc(&s->data, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        s->data = nullptr;
+        throw Error{e == cudaErrorMemoryAllocation ? QS_ERR_OOM : QS_ERR_CUDA,
+                    std::string("state allocation failed: ") + cudaGetErrorString(e)};
+    }
+    try {
+        launch_set_basis(s->data, n, dt, 0, s->stream);
+    } catch (...) {
+        free_state_resources(s.get());
+        throw;
+    }
+    *out = s.release();
+    API_END
+}
+
+qs_status qs_wrap_state(void* dev_ptr, int n, qs_dtype dt, void* stream, qs_state** out) {
+    API_BEGIN
+    QS_REQUIRE(out != nullptr, "null output");
+    *out = nullptr;
+    QS_REQUIRE(dev_ptr != nullptr, "null device pointer");
+    QS_REQUIRE((reinterpret_cast<uintptr_t>(dev_ptr) & 15) == 0, "device pointer must be 16-byte aligned");
+    QS_REQUIRE(n >= 1 && n <= QS_MAX_QUBITS, "qubit count out of range (1..34)");
+    QS_REQUIRE(dt == QS_C64 || dt == QS_C128, "unknown dtype");
+    std::unique_ptr<qs_state> s(new qs_state());
+    s->n = n;
+    s->dt = dt;
+    s->data = dev_ptr;
+    s->owns = false;
+    s->stream = static_cast<cudaStream_t>(stream);
+    QS_TRY_CUDA(cudaGetDevice(&s->device));
+    *out = s.release();
+    API_END
+}
+
+qs_status qs_destroy_state(qs_state* s) {
+    API_BEGIN
+    if (!s) return QS_OK;
+    if (s->stream || s->data) cudaStreamSynchronize(s->stream);
+    free_state_resources(s);
+    delete s;
+    API_END
+}
+
+qs_status qs_state_info(const qs_state* s, int* n, qs_dtype* dt, void** dev_ptr) {
+    API_BEGIN
+    check_state(s);
+    if (n) *n = s->n;
+    if (dt) *dt = s->dt;
+    if (dev_ptr) *dev_ptr = s->data;
+    API_END
+}
+
+qs_status qs_set_stream(qs_state* s, void* stream) {
+    API_BEGIN
+    check_state(s);
+    s->stream = static_cast<cudaStream_t>(stream);
+    API_END
+}
+
+qs_status qs_set_basis(qs_state* s, uint64_t j) {
+    API_BEGIN
+    check_state(s);
+    QS_REQUIRE(j < (1ull << s->n), "basis index out of range");
+    launch_set_basis(s->data, s->n, s->dt, j, s->stream);
+    API_END
+}
+
+qs_status qs_load(qs_state* s, const void* src, int is_device) {
+    API_BEGIN
+    check_state(s);
+    QS_REQUIRE(src != nullptr, "null source");
+    const size_t bytes = (size_t(1) << s->n) * amp_bytes(s->dt);
+    QS_TRY_CUDA(cudaMemcpyAsync(s->data, src, bytes, is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                s->stream));
+    API_END
+}
+
+qs_status qs_get_vector(const qs_state* s, void* host_out) {
+    API_BEGIN
+    check_state(s);
+    QS_REQUIRE(host_out != nullptr, "null output");
+    const size_t bytes = (size_t(1) << s->n) * amp_bytes(s->dt);
+    QS_TRY_CUDA(cudaMemcpyAsync(host_out, s->data, bytes, cudaMemcpyDeviceToHost, s->stream));
+    QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
+    API_END
+}
+
+qs_status qs_copy_state(const qs_state* src, qs_state* dst) {
+    API_BEGIN
+    check_state(src);
+    check_state(dst);
+    QS_REQUIRE(src->n == dst->n && src->dt == dst->dt, "states differ in qubit count or dtype");
+    if (src->stream != dst->stream) QS_TRY_CUDA(cudaStreamSynchronize(src->stream));
+    const size_t bytes = (size_t(1) << src->n) * amp_bytes(src->dt);
+    QS_TRY_CUDA(cudaMemcpyAsync(dst->data, src->data, bytes, cudaMemcpyDeviceToDevice, dst->stream));
+    API_END
+}
+
+qs_status qs_synchronize(const qs_state* s) {
+    API_BEGIN
+    check_state(s);
+    QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
+    QS_TRY_CUDA(cudaGetLastError());
+    API_END
+}
+
+qs_status qs_apply_gate(qs_state* s, const qs_gate* g) {
+    API_BEGIN
+    check_state(s);
+    QS_REQUIRE(g != nullptr, "null gate");
+    Op op = op_of_gate(*g, s->n, nullptr);
+    launch_op(op, s->data, s->n, s->dt, s->stream, stage_of(s));
+    API_END
+}
+
+qs_status qs_apply_fused(qs_state* s, int k, const int* targets, const double* mat) {
+    API_BEGIN
+    check_state(s);
+    QS_REQUIRE(targets != nullptr && mat != nullptr, "null targets or matrix");
+    QS_REQUIRE(k >= 1 && k <= QS_MAX_TARGETS, "fused width must be in 1..6");
+    qs_gate g;
+    std::memset(&g, 0, sizeof(g));
+    g.kind = QS_GATE_DENSE;
+    g.m = k;
+    for (int j = 0; j < k; j++) g.targets[j] = targets[j];
+    g.mat = mat;
+    g.param_index = -1;
+    Op op = op_of_gate(g, s->n, nullptr);
+    launch_op(op, s->data, s->n, s->dt, s->stream, stage_of(s));
+    API_END
+}
+
+qs_status qs_run_circuit(qs_state* s, const qs_circuit* c, int fusion_k) {
+    API_BEGIN
+    check_state(s);
+    QS_REQUIRE(c != nullptr, "null circuit");
+    QS_REQUIRE(c->n == s->n, "circuit and state have different qubit counts");
+    QS_REQUIRE(c->n_gates >= 0 && (c->n_gates == 0 || c->gates), "null gate array");
+    QS_REQUIRE(fusion_k >= -1 && fusion_k <= QS_MAX_TARGETS, "fusion width must be -1, 0 or 1..6");
+    if (fusion_k == 0) {
+        run_gates(s, c, nullptr);
+    } else {
+        int k = fusion_k < 0 ? autotune(c, s->dt, nullptr) : fusion_k;
+        if (k == 0)
+            run_gates(s, c, nullptr);
+        else
+            apply_plan(s, plan_fusion(c, k));
+    }
+    API_END
+}
+
+qs_status qs_plan_fusion(const qs_circuit* c, int k, qs_fused_circuit** out) {
+    API_BEGIN
+    QS_REQUIRE(out != nullptr, "null output");
+    *out = nullptr;
+    std::unique_ptr<qs_fused_circuit> f(new qs_fused_circuit());
+    f->plan = plan_fusion(c, k);
+    *out = f.release();
+    API_END
+}
+
+qs_status qs_fused_info(const qs_fused_circuit* f, int* n_blocks, int* n_source_gates) {
+    API_BEGIN
+    QS_REQUIRE(f != nullptr, "null plan");
+    if (n_blocks) *n_blocks = int(f->plan.blocks.size());
+    if (n_source_gates) *n_source_gates = f->plan.n_source_gates;
+    API_END
+}
+
+qs_status qs_fused_block(const qs_fused_circuit* f, int b, int* width, int* targets, double* mat) {
+    API_BEGIN
+    QS_REQUIRE(f != nullptr, "null plan");
+    QS_REQUIRE(b >= 0 && b < int(f->plan.blocks.size()), "block index out of range");
+    const FusedBlock& fb = f->plan.blocks[b];
+    const int w = int(fb.qubits.size());
+    if (width) *width = w;
+    if (targets)
+        for (int j = 0; j < w; j++) targets[j] = fb.qubits[j];
+    if (mat) {
+        std::vector<cplx> M = fb.mat;
+        if (fb.single_gate >= 0) {
+            // a block holding one gate keeps that gate; report its matrix on the sorted qubits
+            const qs_gate& g = f->plan.source[fb.single_gate];
+            DenseOp d = dense_of_gate(g, f->plan.n, nullptr);
+            const int D = 1 << w;
+            M.assign(size_t(D) * D, 0.0);
+            for (int i = 0; i < D; i++) M[size_t(i) * D + i] = 1.0;
+            // embed: identity off the control block, the gate matrix on the target bits
+            std::vector<int> lt, lc;
+            auto local = [&](int q) { return int(std::find(fb.qubits.begin(), fb.qubits.end(), q) - fb.qubits.begin()); };
+            for (int t : d.targets) lt.push_back(local(t));
+            for (int q : d.controls) lc.push_back(local(q));
+            const int dm = 1 << int(lt.size());
+            uint64_t tmask = 0, cmask = 0, cval = 0;
+            for (size_t j = 0; j < lt.size(); j++) tmask |= 1ull << lt[j];
+            for (size_t j = 0; j < lc.size(); j++) {
+                cmask |= 1ull << lc[j];
+                if (d.cvals[j]) cval |= 1ull << lc[j];
+            }
+            std::vector<cplx> E(size_t(D) * D, 0.0);
+            for (int col = 0; col < D; col++) {
+                for (int r = 0; r < D; r++) {
+                    if ((uint64_t(r) & cmask) != cval) {
+                        if (r == col) E[size_t(r) * D + col] = 1.0;
+                        continue;
+                    }
+                    if ((uint64_t(r) & ~tmask) != (uint64_t(col) & ~tmask)) continue;
+                    int zr = 0, zc = 0;
+                    for (size_t j = 0; j < lt.size(); j++) {
+                        zr |= int((r >> lt[j]) & 1) << j;
+                        zc |= int((col >> lt[j]) & 1) << j;
+                    }
+                    E[size_t(r) * D + col] = d.mat[size_t(zr) * dm + zc];
+                }
+            }
+            M = E;
+        }
+        for (size_t e = 0; e < M.size(); e++) {
+            mat[2 * e] = M[e].real();
+            mat[2 * e + 1] = M[e].imag();
+        }
+    }
+    API_END
+}
+
+qs_status qs_apply_fused_circuit(qs_state* s, const qs_fused_circuit* f) {
+    API_BEGIN
+    check_state(s);
+    QS_REQUIRE(f != nullptr, "null plan");
+    apply_plan(s, f->plan);
+    API_END
+}
+
+qs_status qs_destroy_fused(qs_fused_circuit* f) {
+    API_BEGIN
+    delete f;
+    API_END
+}
+
+qs_status qs_fused_block_cost(const qs_fused_circuit* f, int b, qs_dtype dt, int* kernel, int* launches,
+                              double* bytes) {
+    API_BEGIN
+    QS_REQUIRE(f != nullptr, "null plan");
+    QS_REQUIRE(b >= 0 && b < int(f->plan.blocks.size()), "block index out of range");
+    QS_REQUIRE(dt == QS_C64 || dt == QS_C128, "unknown dtype");
+    op_cost(block_op(f->plan, size_t(b)), f->plan.n, dt, kernel, launches, bytes);
+    API_END
+}
+
+qs_status qs_apply_fused_circuit_timed(qs_state* s, const qs_fused_circuit* f, float* block_ms) {
+    API_BEGIN
+    check_state(s);
+    QS_REQUIRE(f != nullptr && block_ms != nullptr, "null plan or output");
+    apply_plan_impl(s, f->plan, block_ms);
+    API_END
+}
+
+qs_status qs_autotune_fusion(const qs_circuit* c, qs_dtype dt, int* best_k, double* pred_ms) {
+    API_BEGIN
+    QS_REQUIRE(c != nullptr && best_k != nullptr, "null circuit or output");
+    QS_REQUIRE(dt == QS_C64 || dt == QS_C128, "unknown dtype");
+    QS_REQUIRE(c->n >= 1 && c->n <= QS_MAX_QUBITS, "qubit count out of range");
+    *best_k = autotune(c, dt, pred_ms);
+    API_END
+}
+
+qs_status qs_expectation(const qs_state* s, const qs_pauli_obs* obs, double out[2]) {
+    API_BEGIN
+    check_state(s);
+    QS_REQUIRE(out != nullptr, "null output");
+    reduce_expectation(const_cast<qs_state*>(s), obs, out);
+    API_END
+}
+
+qs_status qs_inner_product(const qs_state* a, const qs_state* b, double out[2]) {
+    API_BEGIN
+    check_state(a);
+    check_state(b);
+    QS_REQUIRE(out != nullptr, "null output");
+    QS_REQUIRE(a->n == b->n && a->dt == b->dt, "states differ in qubit count or dtype");
+    reduce_inner(a, b, out);
+    API_END
+}
+
+qs_status qs_norm2(const qs_state* s, double* out) {
+    API_BEGIN
+    check_state(s);
+    QS_REQUIRE(out != nullptr, "null output");
+    reduce_norm2(const_cast<qs_state*>(s), out);
+    API_END
+}
+
+qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pauli_obs* H, qs_dtype dt, void* stream,
+                          double* energy, double* grad) {
+    API_BEGIN
+    QS_REQUIRE(c != nullptr && H != nullptr, "null circuit or observable");
+    QS_REQUIRE(energy != nullptr, "null energy output");
+    QS_REQUIRE(c->n_params >= 0 && (c->n_params == 0 || grad != nullptr), "null gradient output");
+    QS_REQUIRE(c->n >= 1 && c->n <= QS_MAX_QUBITS, "qubit count out of range");
+    QS_REQUIRE(c->n_gates >= 0 && (c->n_gates == 0 || c->gates), "null gate array");
+    QS_REQUIRE(dt == QS_C64 || dt == QS_C128, "unknown dtype");
+    // parametric gates: uncontrolled rotations exp(i theta P / 2)
+    for (int i = 0; i < c->n_gates; i++) {
+        const qs_gate& g = c->gates[i];
+        if (g.param_index < 0) continue;
+        QS_REQUIRE(g.param_index < c->n_params, "param_index out of range");
+        QS_REQUIRE(g.kind == QS_GATE_NAMED && (g.named == QS_NAMED_RX || g.named == QS_NAMED_RY ||
+                                               g.named == QS_NAMED_RZ || g.named == QS_NAMED_PAULIROT),
+                   "a parametric gate must be RX, RY, RZ or PAULIROT");
+        if (g.mc != 0) throw Error{QS_ERR_UNSUPPORTED, "controlled parametric rotations are not differentiated"};
+    }
+    const std::vector<PauliGroup> groups = group_observable(H, c->n);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    qs_state *psi = nullptr, *lam = nullptr;
+    qs_status rc = qs_create_state(c->n, dt, stream, &psi);
+    if (rc != QS_OK) throw Error{rc, std::string("adjoint: ") + qs_last_error()};
+    rc = qs_create_state(c->n, dt, stream, &lam);
+    if (rc != QS_OK) {
+        qs_destroy_state(psi);
+        throw Error{rc, std::string("adjoint: ") + qs_last_error()};
+    }
+    struct Guard {
+        qs_state *a, *b;
+        ~Guard() {
+            qs_destroy_state(a);
+            qs_destroy_state(b);
+        }
+    } guard{psi, lam};
+    // forward: psi = U_G ... U_1 |0>
+    run_gates(psi, c, theta);
+    // lambda = H psi ; E = Re <psi|lambda>
+    launch_apply_observable(groups, psi->data, lam->data, c->n, dt, st);
+    double e2[2];
+    reduce_inner(psi, lam, e2);
+    *energy = e2[0];
+    for (int p = 0; p < c->n_params; p++) grad[p] = 0.0;
+    // reverse sweep
+    for (int i = c->n_gates - 1; i >= 0; i--) {
+        const qs_gate& g = c->gates[i];
+        Op op = op_of_gate(g, c->n, theta);
+        if (g.param_index >= 0) {
+            uint64_t xm = 0, zm = 0;
+            auto add = [&](int id, int q) {
+                if (id == 1 || id == 2) xm |= 1ull << q;
+                if (id == 2 || id == 3) zm |= 1ull << q;
+            };
+            if (g.named == QS_NAMED_PAULIROT) {
+                for (int j = 0; j < g.m; j++) add(g.pauli[j], g.targets[j]);
+            } else {
+                add(g.named == QS_NAMED_RX ? 1 : g.named == QS_NAMED_RY ? 2 : 3, g.targets[0]);
+            }
+            double t[2];
+            reduce_pauli_transition(lam, psi, xm, zm, t);
+            // d/dtheta exp(i theta P/2) = (i/2) P U  ->  dE/dtheta = -Im <lambda|P|psi>
+            grad[g.param_index] += -t[1];
+        }
+        Op inv = dagger(op);
+        launch_op(inv, psi->data, c->n, dt, st, stage_of(psi));
+        launch_op(inv, lam->data, c->n, dt, st, stage_of(lam));
+    }
+    QS_TRY_CUDA(cudaStreamSynchronize(st));
+    API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,166 @@
+// Internal declarations shared by the translation units of libqsim_gb300.so.
+// Host-side structures, launch parameter blocks passed by value to kernels, and
+// the error helpers behind qs_last_error().
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qsim_gb300.h"
+
+namespace qs {
+
+using cplx = std::complex<double>;
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+void clear_error();
+
+struct Error {
+    qs_status code;
+    std::string msg;
+};
+
+#define QS_TRY_CUDA(expr)                                                                 \
+    do {                                                                                  \
+        cudaError_t e_ = (expr);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            throw ::qs::Error{e_ == cudaErrorMemoryAllocation ? QS_ERR_OOM : QS_ERR_CUDA, \
+                              std::string(#expr) + ": " + cudaGetErrorString(e_)};        \
+        }                                                                                 \
+    } while (0)
+
+#define QS_REQUIRE(cond, msg)                                  \
+    do {                                                       \
+        if (!(cond)) throw ::qs::Error{QS_ERR_INVALID_ARG, msg}; \
+    } while (0)
+
+// ------------------------------------------------------------------ state
+struct Scratch {
+    // Per-state reduction scratch: per-block partial sums (device) and a pinned
+    // host landing area for the final values.
+    double* d_part = nullptr;
+    size_t part_cap = 0;  // doubles
+    double* h_out = nullptr;
+    size_t out_cap = 0;   // doubles
+};
+
+}  // namespace qs
+
+struct qs_state {
+    int n = 0;
+    qs_dtype dt = QS_C128;
+    void* data = nullptr;
+    bool owns = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    qs::Scratch scratch;
+    void* d_stage = nullptr;  // kStageBytes, allocated on first wide dense gate
+};
+
+namespace qs {
+
+inline size_t amp_bytes(qs_dtype dt) { return dt == QS_C64 ? 8 : 16; }
+
+// ------------------------------------------------------------------ launch plans
+// Enumeration of the x0 of Eq. (update_mat): iteration index i -> bit string with zero
+// bits inserted at every fixed position (targets and controls), then the control bits
+// that must be 1 or'ed in.
+constexpr int kMaxFixed = QS_MAX_TARGETS + QS_MAX_CONTROLS + 2;
+struct IndexPlan {
+    uint64_t n_iter = 0;
+    uint64_t setmask = 0;
+    int32_t nfix = 0;
+    int32_t fixpos[kMaxFixed] = {};
+};
+
+IndexPlan make_index_plan(int n, const std::vector<int>& fixed, uint64_t setmask);
+
+// Gate matrix as the kernels see it: targets in the caller's order (bit j <-> targets[j]),
+// controls with their values, dense 2^m x 2^m FP64 matrix (row = output).
+struct DenseOp {
+    std::vector<int> targets;
+    std::vector<int> controls;
+    std::vector<int> cvals;
+    std::vector<cplx> mat;  // row-major 2^m x 2^m
+};
+
+// A gate decoded into the cheapest kernel that performs it.
+enum class OpKind { Dense, Diag, Phase, Pauli, Swap };
+struct Op {
+    OpKind kind = OpKind::Dense;
+    std::vector<int> targets;
+    std::vector<int> controls;
+    std::vector<int> cvals;
+    std::vector<cplx> data;   // Dense: matrix; Diag: diagonal
+    cplx phase = 1.0;         // Phase: factor on the subspace where all fixed bits match
+    uint64_t xmask = 0, zmask = 0;  // Pauli
+    const void* dmat = nullptr;     // Dense, optional: device copy of `data` in the state's element type
+};
+
+// gate descriptor -> dense operator on (targets, controls) (throws Error on bad input)
+DenseOp dense_of_gate(const qs_gate& g, int n, const double* theta_override);
+// gate descriptor -> cheapest kernel form
+Op op_of_gate(const qs_gate& g, int n, const double* theta_override);
+// validation of qubit lists
+void check_qubits(int n, const int* t, int m, const int* c, int mc);
+
+// ------------------------------------------------------------------ device launches
+// All launches are asynchronous on `st`. psi points at 2^n amplitudes of dtype dt.
+// `stage`: a device buffer of at least kStageBytes, used to hand wide dense matrices to the
+// kernels when op.dmat is not set.
+constexpr size_t kStageBytes = 64 * 64 * 16;
+void launch_op(const Op& op, void* psi, int n, qs_dtype dt, cudaStream_t st, void* stage);
+void launch_set_basis(void* psi, int n, qs_dtype dt, uint64_t j, cudaStream_t st);
+
+// Reductions: write results into the state's scratch and copy to host; synchronise.
+void reduce_norm2(qs_state* s, double* out);
+void reduce_inner(const qs_state* a, const qs_state* b, double out[2]);
+void reduce_expectation(qs_state* s, const qs_pauli_obs* obs, double out[2]);
+// <lambda| P |psi> for a Pauli string (complex), both states same n/dtype; synchronises.
+void reduce_pauli_transition(qs_state* lam, const qs_state* psi, uint64_t xmask, uint64_t zmask,
+                             double out[2]);
+
+// Observable grouped by flip mask for one pass per group.
+struct PauliGroup {
+    uint64_t xmask;
+    std::vector<double> coef;
+    std::vector<uint64_t> zmask;
+};
+std::vector<PauliGroup> group_observable(const qs_pauli_obs* obs, int n);
+
+// lambda <- O psi (sum of Pauli strings), out-of-place; asynchronous.
+void launch_apply_observable(const std::vector<PauliGroup>& groups, const void* psi, void* lam, int n,
+                             qs_dtype dt, cudaStream_t st);
+
+// complex128 arithmetic mode (QS_MATH_FP64 / QS_MATH_DF)
+int c128_math();
+
+// ------------------------------------------------------------------ fusion planner
+struct FusedBlock {
+    std::vector<int> qubits;   // ascending
+    std::vector<cplx> mat;     // 2^w x 2^w
+    int n_gates = 0;
+    bool diagonal = false;
+    int single_gate = -1;      // index of the source gate when the block holds exactly one
+};
+struct FusionPlan {
+    int n = 0;
+    int k = 0;
+    int n_source_gates = 0;
+    std::vector<FusedBlock> blocks;
+    std::vector<qs_gate> source;          // copies of single-gate blocks' gates
+    std::vector<std::vector<double>> source_mats;
+};
+FusionPlan plan_fusion(const qs_circuit* c, int k);
+void apply_plan(qs_state* s, const FusionPlan& p);
+
+}  // namespace qs
+
+struct qs_fused_circuit {
+    qs::FusionPlan plan;
+};

@@ -1,0 +1,367 @@
+// Reductions over a state vector (Sec. 4.2.2 squared norm and inner product, Sec. 4.5
+// Pauli-observable expectation and transition amplitude) and the out-of-place product
+// lambda = O psi used by the adjoint gradient.
+//
+// Sums are deterministic: every block writes its partial sums to its own slot, and one
+// block adds the slots in a fixed order. Accumulation is FP64 for both storage types;
+// complex64 amplitudes are widened to double before they are multiplied.
+//
+// Expectation: the terms of O = sum_P alpha_P P are grouped by their flip mask f (the
+// X-or-Y positions). Group f = 0 is diagonal: sum_y w(y) |psi_y|^2 with
+// w(y) = sum_P alpha_P (-1)^{popcount(y & z_P)}. A group f != 0 visits each pair
+// (y, y ^ f) once, with A = conj(psi_{y^f}) psi_y:
+//   <psi|P|psi> restricted to the pair = i^{#Y} (s(y) A + s(y^f) conj(A)).
+#include <algorithm>
+#include <map>
+
+#include "qsim_kernels.cuh"
+
+namespace qs {
+
+namespace {
+
+constexpr int kRedThreads = 256;
+constexpr int kMaxTermsPerLaunch = 48;
+
+int sms() {
+    static int s = 0;
+    if (!s) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+        if (s <= 0) s = 1;
+    }
+    return s;
+}
+
+unsigned red_grid(uint64_t work) {
+    const uint64_t want = (work + kRedThreads * 4 - 1) / (kRedThreads * 4);
+    return unsigned(std::max<uint64_t>(1, std::min<uint64_t>(want, uint64_t(sms()) * 4)));
+}
+
+__device__ __forceinline__ double2 widen(float2 v) { return make_double2(v.x, v.y); }
+__device__ __forceinline__ double2 widen(double2 v) { return v; }
+
+// Block partial of (re, im) pairs into part[2*blockIdx.x + {0,1}].
+__device__ __forceinline__ void write_partial2(double re, double im, double* part) {
+    __shared__ double sh[kRedThreads / 32];
+    const double r = block_sum<kRedThreads>(re, sh);
+    const double i = block_sum<kRedThreads>(im, sh);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = r;
+        part[2 * blockIdx.x + 1] = i;
+    }
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kRedThreads) k_norm2(const C* __restrict__ psi, uint64_t N, double* part) {
+    double acc = 0.0;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t x = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < N; x += stride) {
+        const double2 v = widen(psi[x]);
+        acc = fma(v.x, v.x, acc);
+        acc = fma(v.y, v.y, acc);
+    }
+    write_partial2(acc, 0.0, part);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kRedThreads) k_inner(const C* __restrict__ a, const C* __restrict__ b, uint64_t N,
+                                                       double* part) {
+    double re = 0.0, im = 0.0;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t x = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < N; x += stride) {
+        const double2 u = widen(a[x]), v = widen(b[x]);
+        re = fma(u.x, v.x, re);
+        re = fma(u.y, v.y, re);
+        im = fma(u.x, v.y, im);
+        im = fma(-u.y, v.x, im);
+    }
+    write_partial2(re, im, part);
+}
+
+struct TermParams {
+    uint64_t xmask;          // group flip mask
+    IndexPlan ip;            // pivot bit inserted (f != 0) or plain range (f == 0)
+    int32_t nterms;
+    double coef[kMaxTermsPerLaunch];
+    uint64_t zmask[kMaxTermsPerLaunch];
+    int32_t nY[kMaxTermsPerLaunch];
+};
+
+template <typename C>
+__global__ void __launch_bounds__(kRedThreads) k_expect_group(const C* __restrict__ psi,
+                                                              const __grid_constant__ TermParams P, double* part) {
+    double re = 0.0, im = 0.0;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P.ip.n_iter; i += stride) {
+        const uint64_t y = expand(i, P.ip);
+        if (P.xmask == 0) {
+            const double2 v = widen(psi[y]);
+            const double p = fma(v.x, v.x, v.y * v.y);
+            double w = 0.0;
+            for (int t = 0; t < P.nterms; t++) w += parity64(y & P.zmask[t]) ? -P.coef[t] : P.coef[t];
+            re = fma(w, p, re);
+        } else {
+            const uint64_t y2 = y ^ P.xmask;
+            const double2 a = widen(psi[y]), b = widen(psi[y2]);
+            const double Ar = fma(b.x, a.x, b.y * a.y);   // A = conj(b) a
+            const double Ai = fma(b.x, a.y, -b.y * a.x);
+            for (int t = 0; t < P.nterms; t++) {
+                const int s1 = parity64(y & P.zmask[t]);
+                const int s2 = parity64(y2 & P.zmask[t]);
+                // s1 A + s2 conj(A): equal signs -> 2 s Re A ; opposite -> 2 i s Im A
+                double ur, ui;
+                const double sg = s1 ? -2.0 : 2.0;
+                if (s1 == s2) { ur = sg * Ar; ui = 0.0; } else { ur = 0.0; ui = sg * Ai; }
+                double vr, vi;  // multiply by i^{nY}
+                switch (P.nY[t] & 3) {
+                    case 0: vr = ur; vi = ui; break;
+                    case 1: vr = -ui; vi = ur; break;
+                    case 2: vr = -ur; vi = -ui; break;
+                    default: vr = ui; vi = -ur; break;
+                }
+                re = fma(P.coef[t], vr, re);
+                im = fma(P.coef[t], vi, im);
+            }
+        }
+    }
+    write_partial2(re, im, part);
+}
+
+// <lam| P |psi> = sum_y conj(lam_y) i^{#Y} s(y ^ f) psi_{y ^ f}
+template <typename C>
+__global__ void __launch_bounds__(kRedThreads) k_transition(const C* __restrict__ lam, const C* __restrict__ psi,
+                                                            uint64_t N, uint64_t xmask, uint64_t zmask, int nY,
+                                                            double* part) {
+    double re = 0.0, im = 0.0;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t y = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; y < N; y += stride) {
+        const uint64_t y2 = y ^ xmask;
+        const double2 l = widen(lam[y]);
+        double2 p = widen(psi[y2]);
+        p = mul_ipow(p, nY + 2 * parity64(y2 & zmask));
+        re = fma(l.x, p.x, re);
+        re = fma(l.y, p.y, re);
+        im = fma(l.x, p.y, im);
+        im = fma(-l.y, p.x, im);
+    }
+    write_partial2(re, im, part);
+}
+
+// sum of `nslots` (re, im) partials in a fixed order -> out[0..1]
+__global__ void __launch_bounds__(kRedThreads) k_final2(const double* __restrict__ part, int nslots, double* out) {
+    __shared__ double sh[kRedThreads / 32];
+    double re = 0.0, im = 0.0;
+    for (int j = threadIdx.x; j < nslots; j += kRedThreads) {
+        re += part[2 * j];
+        im += part[2 * j + 1];
+    }
+    const double r = block_sum<kRedThreads>(re, sh);
+    const double i = block_sum<kRedThreads>(im, sh);
+    if (threadIdx.x == 0) {
+        out[0] = r;
+        out[1] = i;
+    }
+}
+
+// lambda_y = sum_groups sum_terms coef * i^{#Y} s(y ^ f) psi_{y ^ f}
+struct ObsDevTerm {
+    uint64_t xmask, zmask;
+    double coef;
+    int32_t nY, pad;
+};
+
+template <typename C>
+__global__ void __launch_bounds__(kRedThreads) k_apply_obs(const C* __restrict__ psi, C* __restrict__ lam, uint64_t N,
+                                                           const ObsDevTerm* __restrict__ terms, int nterms) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t y = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; y < N; y += stride) {
+        double re = 0.0, im = 0.0;
+        for (int t = 0; t < nterms; t++) {
+            const ObsDevTerm T = terms[t];
+            const uint64_t y2 = y ^ T.xmask;
+            double2 p = widen(psi[y2]);
+            p = mul_ipow(p, T.nY + 2 * parity64(y2 & T.zmask));
+            re = fma(T.coef, p.x, re);
+            im = fma(T.coef, p.y, im);
+        }
+        C out;
+        out.x = decltype(out.x)(re);
+        out.y = decltype(out.y)(im);
+        lam[y] = out;
+    }
+}
+
+// ---------------------------------------------------------------- host side
+void ensure_scratch(qs_state* s, size_t part_doubles) {
+    Scratch& sc = s->scratch;
+    if (sc.part_cap < part_doubles) {
+        if (sc.d_part) {
+            QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
+            cudaFree(sc.d_part);
+            sc.d_part = nullptr;
+            sc.part_cap = 0;
+        }
+        QS_TRY_CUDA(cudaMalloc(&sc.d_part, part_doubles * sizeof(double)));
+        sc.part_cap = part_doubles;
+    }
+    if (!sc.h_out) {
+        QS_TRY_CUDA(cudaMallocHost(&sc.h_out, 16 * sizeof(double)));
+        sc.out_cap = 16;
+    }
+}
+
+// final reduce of nslots partials into d_part[out_off..], copy 2 doubles to host, sync
+void finish2(qs_state* s, int nslots, double out[2]) {
+    double* d_out = s->scratch.d_part + s->scratch.part_cap - 2;
+    k_final2<<<1, kRedThreads, 0, s->stream>>>(s->scratch.d_part, nslots, d_out);
+    QS_TRY_CUDA(cudaGetLastError());
+    QS_TRY_CUDA(cudaMemcpyAsync(s->scratch.h_out, d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
+    out[0] = s->scratch.h_out[0];
+    out[1] = s->scratch.h_out[1];
+}
+
+}  // namespace
+
+std::vector<PauliGroup> group_observable(const qs_pauli_obs* obs, int n) {
+    QS_REQUIRE(obs != nullptr, "null observable");
+    QS_REQUIRE(obs->n_terms >= 0, "negative term count");
+    QS_REQUIRE(obs->n_terms == 0 || (obs->coef && obs->x_mask && obs->z_mask), "null observable arrays");
+    const uint64_t lim = n >= 64 ? ~0ull : ((1ull << n) - 1);
+    std::map<uint64_t, size_t> idx;
+    std::vector<PauliGroup> groups;
+    for (int t = 0; t < obs->n_terms; t++) {
+        QS_REQUIRE((obs->x_mask[t] & ~lim) == 0 && (obs->z_mask[t] & ~lim) == 0, "Pauli term acts on a qubit >= n");
+        auto it = idx.find(obs->x_mask[t]);
+        if (it == idx.end()) {
+            idx[obs->x_mask[t]] = groups.size();
+            groups.push_back(PauliGroup{obs->x_mask[t], {}, {}});
+            it = idx.find(obs->x_mask[t]);
+        }
+        groups[it->second].coef.push_back(obs->coef[t]);
+        groups[it->second].zmask.push_back(obs->z_mask[t]);
+    }
+    return groups;
+}
+
+void reduce_norm2(qs_state* s, double* out) {
+    const uint64_t N = 1ull << s->n;
+    const unsigned g = red_grid(N);
+    ensure_scratch(s, 2 * g + 2);
+    if (s->dt == QS_C64)
+        k_norm2<<<g, kRedThreads, 0, s->stream>>>(reinterpret_cast<const float2*>(s->data), N, s->scratch.d_part);
+    else
+        k_norm2<<<g, kRedThreads, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), N, s->scratch.d_part);
+    QS_TRY_CUDA(cudaGetLastError());
+    double r[2];
+    finish2(s, int(g), r);
+    *out = r[0];
+}
+
+void reduce_inner(const qs_state* a, const qs_state* b, double out[2]) {
+    qs_state* s = const_cast<qs_state*>(a);
+    const uint64_t N = 1ull << s->n;
+    const unsigned g = red_grid(N);
+    ensure_scratch(s, 2 * g + 2);
+    if (b->stream != s->stream) {
+        // order b's pending work before the read on a's stream
+        QS_TRY_CUDA(cudaStreamSynchronize(b->stream));
+    }
+    if (s->dt == QS_C64)
+        k_inner<<<g, kRedThreads, 0, s->stream>>>(reinterpret_cast<const float2*>(a->data),
+                                                  reinterpret_cast<const float2*>(b->data), N, s->scratch.d_part);
+    else
+        k_inner<<<g, kRedThreads, 0, s->stream>>>(reinterpret_cast<const double2*>(a->data),
+                                                  reinterpret_cast<const double2*>(b->data), N, s->scratch.d_part);
+    QS_TRY_CUDA(cudaGetLastError());
+    finish2(s, int(g), out);
+}
+
+void reduce_expectation(qs_state* s, const qs_pauli_obs* obs, double out[2]) {
+    const std::vector<PauliGroup> groups = group_observable(obs, s->n);
+    const uint64_t N = 1ull << s->n;
+    // launches: one per (group, chunk of <= kMaxTermsPerLaunch terms)
+    struct L {
+        const PauliGroup* g;
+        size_t t0, t1;
+    };
+    std::vector<L> launches;
+    for (const auto& g : groups)
+        for (size_t t0 = 0; t0 < g.coef.size(); t0 += kMaxTermsPerLaunch)
+            launches.push_back({&g, t0, std::min(g.coef.size(), t0 + kMaxTermsPerLaunch)});
+    if (launches.empty()) {
+        out[0] = out[1] = 0.0;
+        return;
+    }
+    const unsigned gmax = red_grid(N);
+    ensure_scratch(s, 2 * size_t(gmax) * launches.size() + 2);
+    int slots = 0;
+    for (const L& l : launches) {
+        TermParams P;
+        P.xmask = l.g->xmask;
+        std::vector<int> fixed;
+        if (P.xmask) fixed.push_back(__builtin_ctzll(P.xmask));
+        P.ip = make_index_plan(s->n, fixed, 0);
+        P.nterms = int(l.t1 - l.t0);
+        for (size_t t = l.t0; t < l.t1; t++) {
+            P.coef[t - l.t0] = l.g->coef[t];
+            P.zmask[t - l.t0] = l.g->zmask[t];
+            P.nY[t - l.t0] = __builtin_popcountll(l.g->xmask & l.g->zmask[t]);
+        }
+        const unsigned g = red_grid(P.ip.n_iter);
+        double* part = s->scratch.d_part + 2 * size_t(slots);
+        if (s->dt == QS_C64)
+            k_expect_group<<<g, kRedThreads, 0, s->stream>>>(reinterpret_cast<const float2*>(s->data), P, part);
+        else
+            k_expect_group<<<g, kRedThreads, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), P, part);
+        QS_TRY_CUDA(cudaGetLastError());
+        slots += int(g);
+    }
+    finish2(s, slots, out);
+}
+
+void reduce_pauli_transition(qs_state* lam, const qs_state* psi, uint64_t xmask, uint64_t zmask, double out[2]) {
+    const uint64_t N = 1ull << lam->n;
+    const unsigned g = red_grid(N);
+    ensure_scratch(lam, 2 * g + 2);
+    const int nY = __builtin_popcountll(xmask & zmask);
+    if (lam->dt == QS_C64)
+        k_transition<<<g, kRedThreads, 0, lam->stream>>>(reinterpret_cast<const float2*>(lam->data),
+                                                         reinterpret_cast<const float2*>(psi->data), N, xmask, zmask,
+                                                         nY, lam->scratch.d_part);
+    else
+        k_transition<<<g, kRedThreads, 0, lam->stream>>>(reinterpret_cast<const double2*>(lam->data),
+                                                         reinterpret_cast<const double2*>(psi->data), N, xmask, zmask,
+                                                         nY, lam->scratch.d_part);
+    QS_TRY_CUDA(cudaGetLastError());
+    finish2(lam, int(g), out);
+}
+
+void launch_apply_observable(const std::vector<PauliGroup>& groups, const void* psi, void* lam, int n, qs_dtype dt,
+                             cudaStream_t st) {
+    std::vector<ObsDevTerm> terms;
+    for (const auto& g : groups)
+        for (size_t t = 0; t < g.coef.size(); t++)
+            terms.push_back(ObsDevTerm{g.xmask, g.zmask[t], g.coef[t], __builtin_popcountll(g.xmask & g.zmask[t]), 0});
+    const uint64_t N = 1ull << n;
+    if (terms.empty()) {
+        QS_TRY_CUDA(cudaMemsetAsync(lam, 0, N * amp_bytes(dt), st));
+        return;
+    }
+    ObsDevTerm* d_terms = nullptr;
+    QS_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_terms), terms.size() * sizeof(ObsDevTerm), st));
+    QS_TRY_CUDA(cudaMemcpyAsync(d_terms, terms.data(), terms.size() * sizeof(ObsDevTerm), cudaMemcpyHostToDevice, st));
+    const unsigned g = red_grid(N);
+    if (dt == QS_C64)
+        k_apply_obs<<<g, kRedThreads, 0, st>>>(reinterpret_cast<const float2*>(psi), reinterpret_cast<float2*>(lam), N,
+                                               d_terms, int(terms.size()));
+    else
+        k_apply_obs<<<g, kRedThreads, 0, st>>>(reinterpret_cast<const double2*>(psi), reinterpret_cast<double2*>(lam),
+                                               N, d_terms, int(terms.size()));
+    QS_TRY_CUDA(cudaGetLastError());
+    QS_TRY_CUDA(cudaFreeAsync(d_terms, st));
+}
+
+}  // namespace qs

@@ -1,0 +1,92 @@
+"""CPU-only checks of the C ABI library: it builds, loads, exports every function the header
+declares, validates arguments without a GPU, and its host-side fusion planner produces block
+matrices whose product equals the unfused circuit (checked with the oracle)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+import paper_2011_13524_gb300 as qs
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "qsim_gb300.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^(?:qs_status|const char\*)\s+(qs_\w+)\(", text, re.M)))
+
+
+def test_header_declares_and_library_exports_every_function():
+    names = declared_functions()
+    assert len(names) >= 20
+    L = qs.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(names) == sorted(qs.exported_symbols())
+
+
+def test_version_and_error_message():
+    assert b"sm_103a" in qs.lib().qs_version()
+    rc = qs.lib().qs_set_c128_math(7)
+    assert rc == qs.QS_ERR_INVALID_ARG
+    assert b"mode" in qs.lib().qs_last_error()
+    qs.set_c128_math(qs.QS_MATH_FP64)
+    assert qs.get_c128_math() == qs.QS_MATH_FP64
+
+
+def test_invalid_arguments_without_gpu():
+    L = qs.lib()
+    h = ctypes.c_void_p()
+    assert L.qs_create_state(0, qs.QS_C128, None, ctypes.byref(h)) == qs.QS_ERR_INVALID_ARG
+    assert L.qs_create_state(40, qs.QS_C128, None, ctypes.byref(h)) == qs.QS_ERR_INVALID_ARG
+    assert L.qs_create_state(4, 9, None, ctypes.byref(h)) == qs.QS_ERR_INVALID_ARG
+    assert L.qs_wrap_state(None, 4, qs.QS_C128, None, ctypes.byref(h)) == qs.QS_ERR_INVALID_ARG
+    assert L.qs_wrap_state(ctypes.c_void_p(8), 4, qs.QS_C128, None, ctypes.byref(h)) == qs.QS_ERR_INVALID_ARG
+    assert L.qs_destroy_state(None) == qs.QS_OK
+    assert L.qs_apply_gate(None, None) == qs.QS_ERR_INVALID_ARG
+    # planner validation (host only)
+    bad = W.Circuit(3, [W.Gate("CNOT", (1,), controls=(1,), control_values=(1,))])
+    c, keep = qs.make_circuit(bad)
+    assert L.qs_plan_fusion(ctypes.byref(c), 3, ctypes.byref(h)) == qs.QS_ERR_INVALID_ARG
+    assert b"control" in L.qs_last_error()
+    ok = W.Circuit(3, [W.Gate("H", (0,))])
+    c, keep = qs.make_circuit(ok)
+    assert L.qs_plan_fusion(ctypes.byref(c), 7, ctypes.byref(h)) == qs.QS_ERR_INVALID_ARG
+    out_of_range = W.Circuit(3, [W.Gate("H", (3,))])
+    c, keep = qs.make_circuit(out_of_range)
+    assert L.qs_plan_fusion(ctypes.byref(c), 2, ctypes.byref(h)) == qs.QS_ERR_INVALID_ARG
+
+
+def run_plan_with_oracle(plan, n):
+    psi = oracle.zero_state(n)
+    for b in range(plan.n_blocks):
+        t, M = plan.block(b)
+        oracle.apply_matrix(psi, n, t, M)
+    return psi
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
+def test_fusion_plan_product_equals_circuit(k):
+    """Merging is exact algebra (Sec. 5.4): applying the planned blocks (with the oracle)
+    reproduces the unfused circuit."""
+    n = 8
+    for circ in [W.u3cz_circuit(n, 4, 3), W.Circuit(n, W.random_gate_suite(n, 17)),
+                 W.hea_circuit(n, 2, 5), W.rzrxrz_cnot_circuit(n, 2, 9)]:
+        ref = oracle.run_circuit(circ)
+        plan = qs.FusedCircuit(circ, k)
+        assert plan.n_source_gates == len(circ.gates)
+        widest = max(len(g.targets) + len(g.controls) for g in circ.gates)
+        assert all(w <= max(k, widest) for w in plan.widths())   # a wider gate stays alone
+        got = run_plan_with_oracle(plan, n)
+        assert np.max(np.abs(got - ref)) < 1e-12
+
+
+def test_fusion_reduces_block_count():
+    c = W.u3cz_circuit(30, 20, 1)
+    counts = {k: qs.FusedCircuit(c, k).n_blocks for k in (1, 2, 3, 4, 5, 6)}
+    assert counts[1] < len(c.gates)
+    assert counts[2] < counts[1] and counts[4] < counts[2] and counts[6] <= counts[5]

@@ -1,0 +1,295 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element.
+
+Tolerances (max-abs amplitude error): 1e-12 for complex128, 1e-5 for complex64, the bounds
+the workload states; fidelity 1 - |<ref|psi>|^2 is reported beside them. Sizes span several
+thread blocks and ragged tails (n = 1 .. 22); full-size (n = 30) runs are checked on sampled
+amplitudes that a closed form gives one by one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {1: 1e-5, 2: 1e-12}
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2011_13524_gb300 as qs
+    qs.lib()
+    return qs
+
+
+def maxabs(a, b):
+    return float(np.max(np.abs(np.asarray(a, dtype=np.complex128) - np.asarray(b, dtype=np.complex128))))
+
+
+def fidelity_gap(ref, psi):
+    ref = np.asarray(ref, dtype=np.complex128)
+    psi = np.asarray(psi, dtype=np.complex128)
+    return 1.0 - abs(np.vdot(ref, psi)) ** 2 / (np.vdot(ref, ref).real * np.vdot(psi, psi).real)
+
+
+def run_gpu(qs, circuit, dtype, fusion_k=0, psi0=None, owned=False):
+    st = qs.State(circuit.n, dtype, owned=owned)
+    if psi0 is not None:
+        st.load(psi0)
+    if fusion_k:
+        st.run(circuit, fusion_k)
+    else:
+        for g in circuit.gates:
+            st.apply_gate(g)
+    out = st.get_vector()
+    st.close()
+    return out
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 11])
+def test_every_gate_kind(qs, n, dtype):
+    for seed in range(3):
+        gates = W.random_gate_suite(n, 1000 * n + seed)
+        psi0 = W.random_state(n, seed + 7)
+        for g in gates:
+            ref = psi0.copy()
+            oracle.apply_gate(ref, n, g)
+            got = run_gpu(qs, W.Circuit(n, [g]), dtype, psi0=psi0)
+            assert maxabs(got, ref) < TOL[dtype], (g.name, g.targets, g.controls)
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+def test_dense_every_placement(qs, dtype):
+    """1- and 2-qubit dense gates on every target (ordered pair) of n = 7, non-unitary K."""
+    n = 7
+    rng = W.SplitMix64(99)
+    psi0 = W.random_state(n, 3)
+    for t in range(n):
+        g = W.Gate("DENSE", (t,), matrix=W.random_complex_matrix(2, rng) * 0.5)
+        ref = psi0.copy(); oracle.apply_gate(ref, n, g)
+        assert maxabs(run_gpu(qs, W.Circuit(n, [g]), dtype, psi0=psi0), ref) < TOL[dtype]
+    for a in range(n):
+        for b in range(n):
+            if a == b:
+                continue
+            g = W.Gate("DENSE", (a, b), matrix=W.random_complex_matrix(4, rng) * 0.3)
+            ref = psi0.copy(); oracle.apply_gate(ref, n, g)
+            assert maxabs(run_gpu(qs, W.Circuit(n, [g]), dtype, psi0=psi0), ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("m", [3, 4, 5, 6])
+@pytest.mark.parametrize("dtype", [2, 1])
+def test_wide_dense_with_controls(qs, m, dtype):
+    n = 12
+    rng = W.SplitMix64(7 + m)
+    psi0 = W.random_state(n, 11)
+    for trial in range(4):
+        qs_ = list(range(n))
+        picks = [qs_.pop(rng.randint(0, len(qs_) - 1)) for _ in range(m + 2)]
+        ctrl = tuple(picks[m:]) if trial % 2 else ()
+        cv = (1, 0) if trial % 2 else ()
+        g = W.Gate("DENSE", tuple(picks[:m]), controls=ctrl, control_values=cv,
+                   matrix=W.random_unitary(1 << m, rng))
+        ref = psi0.copy(); oracle.apply_gate(ref, n, g)
+        assert maxabs(run_gpu(qs, W.Circuit(n, [g]), dtype, psi0=psi0), ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+def test_config_n12_depth10(qs, dtype):
+    """n = 12, |0..0>, depth-10 U3 + CZ brickwork: the final state and <Z0 Z1>."""
+    c = W.u3cz_circuit(12, 10, 2021)
+    ref = oracle.run_circuit(c)
+    got = run_gpu(qs, c, dtype)
+    assert maxabs(got, ref) < TOL[dtype]
+    assert fidelity_gap(ref, got) < (1e-12 if dtype == 2 else 1e-6)
+    zz = W.PauliObservable(12, np.array([1.0]), np.array([0], dtype=np.uint64), np.array([3], dtype=np.uint64))
+    st = qs.State(12, dtype)
+    st.run(c)
+    e, ei = st.expectation(zz)
+    assert abs(e - oracle.expectation(ref, zz)[0]) < (1e-12 if dtype == 2 else 1e-5)
+    assert abs(ei) < 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("dtype", [2, 1])
+def test_fused_circuits(qs, k, dtype):
+    n = 14
+    for c in [W.u3cz_circuit(n, 6, 5), W.Circuit(n, W.random_gate_suite(n, 23)), W.rzrxrz_cnot_circuit(n, 3, 4)]:
+        ref = oracle.run_circuit(c)
+        got = run_gpu(qs, c, dtype, fusion_k=k)
+        assert maxabs(got, ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("n", [13, 17, 20, 22])
+def test_circuit_family_vs_oracle(qs, n):
+    c = W.u3cz_circuit(n, 8 if n > 20 else 20, n)
+    ref = oracle.run_circuit(c)
+    for k in (0, 2, 4):
+        got = run_gpu(qs, c, 2, fusion_k=k)
+        assert maxabs(got, ref) < 1e-12
+    got = run_gpu(qs, c, 1, fusion_k=4)
+    assert maxabs(got, ref) < 1e-5
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+def test_expectation_norm_inner(qs, dtype):
+    for n in [1, 4, 9, 15]:
+        psi = W.random_state(n, n) * 1.3
+        obs = W.random_pauli_observable(n, 9, 100 + n)
+        st = qs.State(n, dtype)
+        st.load(psi)
+        tol = 1e-12 if dtype == 2 else 2e-5
+        re, im = st.expectation(obs)
+        ore, oim = oracle.expectation(psi, obs)
+        assert abs(re - ore) < tol and abs(im - oim) < tol
+        assert abs(st.norm2() - oracle.norm2(psi, n)) < tol
+        other = qs.State(n, dtype)
+        phi = W.random_state(n, n + 50)
+        other.load(phi)
+        assert abs(st.inner(other) - oracle.inner(psi, phi, n)) < tol
+    n = 16
+    obs = W.tfim_observable(n, 1.0)
+    c = W.u3cz_circuit(n, 4, 8)
+    ref = oracle.run_circuit(c)
+    st = qs.State(n, dtype)
+    st.run(c, 2)
+    assert abs(st.expectation(obs)[0] - oracle.expectation(ref, obs)[0]) < (1e-11 if dtype == 2 else 1e-4)
+
+
+def test_identity_and_empty(qs):
+    n = 3
+    st = qs.State(n, 2)
+    ident = W.PauliObservable(n, np.array([0.25]), np.array([0], dtype=np.uint64), np.array([0], dtype=np.uint64))
+    assert abs(st.expectation(ident)[0] - 0.25) < 1e-15
+    empty = W.PauliObservable(n, np.zeros(0), np.zeros(0, dtype=np.uint64), np.zeros(0, dtype=np.uint64))
+    assert st.expectation(empty) == (0.0, 0.0)
+    st.run(W.Circuit(n, []), 0)
+    st.run(W.Circuit(n, []), 4)
+    v = st.get_vector()
+    assert v[0] == 1 and np.count_nonzero(v) == 1
+    st.set_basis(5)
+    assert st.get_vector()[5] == 1
+
+
+def test_invalid_gate_reports_error(qs):
+    st = qs.State(4, 2)
+    with pytest.raises(qs.QsError) as e:
+        st.apply_gate(W.Gate("H", (4,)))
+    assert e.value.code == qs.QS_ERR_INVALID_ARG
+    with pytest.raises(qs.QsError):
+        st.apply_gate(W.Gate("CNOT", (1,), controls=(1,), control_values=(1,)))
+    # the state is still usable afterwards
+    st.apply_gate(W.Gate("X", (0,)))
+    assert st.get_vector()[1] == 1
+
+
+def test_library_owned_state(qs):
+    c = W.u3cz_circuit(10, 5, 77)
+    ref = oracle.run_circuit(c)
+    assert maxabs(run_gpu(qs, c, 2, fusion_k=3, owned=True), ref) < 1e-12
+
+
+@pytest.mark.parametrize("dtype", [2, 1])
+def test_adjoint_gradient_vs_parameter_shift(qs, dtype):
+    n = 6
+    c = W.hea_circuit(n, 3, 12)
+    obs = W.tfim_observable(n, 1.0)
+    e, g = qs.adjoint_grad(c, obs, dtype=dtype)
+    assert abs(e - oracle.energy(c, obs)) < (1e-12 if dtype == 2 else 1e-5)
+    ps = oracle.grad_parameter_shift(c, obs, range(c.n_params))
+    assert np.max(np.abs(g - ps)) < (1e-11 if dtype == 2 else 1e-4)
+    # explicit theta
+    theta = c.parameters() + 0.1
+    e2, g2 = qs.adjoint_grad(c, obs, theta=theta, dtype=dtype)
+    cb = c.bind(theta)
+    assert abs(e2 - oracle.energy(cb, obs)) < (1e-12 if dtype == 2 else 1e-5)
+    ps2 = oracle.grad_parameter_shift(cb, obs, range(0, c.n_params, 5))
+    assert np.max(np.abs(g2[::5] - ps2)) < (1e-11 if dtype == 2 else 1e-4)
+
+
+def test_adjoint_autograd_function(qs):
+    import torch
+    n = 4
+    c = W.hea_circuit(n, 2, 3)
+    obs = W.random_pauli_observable(n, 4, 9)
+    theta = torch.tensor(c.parameters(), dtype=torch.float64, requires_grad=True)
+    E = qs.AdjointEnergy.apply(theta, c, obs)
+    E.backward()
+    ps = oracle.grad_parameter_shift(c, obs, range(c.n_params))
+    assert np.max(np.abs(theta.grad.numpy() - ps)) < 1e-11
+
+
+# ---------------------------------------------------------------- full size, sampled outputs
+def product_then_cz(n, depth, seed):
+    """depth U3 layers on every qubit, then all CZ brickwork layers: amplitude x equals
+    prod_q phi_q[x_q] * (-1)^{# CZ pairs with both bits set}, each phi_q a 1-qubit oracle run."""
+    full = W.u3cz_circuit(n, depth, seed)
+    u3 = [g for g in full.gates if g.name == "U3"]
+    cz = [g for g in full.gates if g.name == "CZ"]
+    return W.Circuit(n, u3 + cz), u3, cz
+
+
+def sampled_amplitudes(n, u3, cz, xs):
+    phis = []
+    for q in range(n):
+        phi = oracle.zero_state(1)
+        for g in u3:
+            if g.targets[0] == q:
+                oracle.apply_gate(phi, 1, W.Gate("U3", (0,), params=g.params))
+        phis.append(phi)
+    out = []
+    for x in xs:
+        a = 1.0 + 0j
+        for q in range(n):
+            a *= phis[q][(x >> q) & 1]
+        sgn = 1
+        for g in cz:
+            i, j = g.targets
+            if (x >> i) & 1 and (x >> j) & 1:
+                sgn = -sgn
+        out.append(a * sgn)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("fusion_k", [0, 4])
+def test_full_size_n30_sampled(qs, fusion_k):
+    import torch
+    n = 30
+    circ, u3, cz = product_then_cz(n, 20, 4242)
+    st = qs.State(n, 2)
+    st.run(circ, fusion_k)
+    st.synchronize()
+    rng = W.SplitMix64(5)
+    xs = [rng.next_u64() & ((1 << n) - 1) for _ in range(2000)] + [0, (1 << n) - 1]
+    ref = sampled_amplitudes(n, u3, cz, xs)
+    idx = torch.tensor(xs, dtype=torch.int64, device="cuda")
+    got = st.tensor[idx].cpu().numpy()
+    assert maxabs(got, ref) < 1e-12
+    assert abs(st.norm2() - 1.0) < 1e-11
+    st.close()
+    del st
+    torch.cuda.empty_cache()
+
+
+def test_full_size_n30_fused_equals_unfused(qs):
+    """Property at any size: the fused run equals the per-gate run, norm stays 1."""
+    import torch
+    n = 30
+    c = W.u3cz_circuit(n, 3, 99)
+    a = qs.State(n, 2)
+    a.run(c, 0)
+    b = qs.State(n, 2)
+    b.run(c, 4)
+    diff = (a.tensor - b.tensor).abs().max().item()
+    assert diff < 1e-12
+    assert abs(a.norm2() - 1.0) < 1e-11
+    a.close(); b.close()
+    del a, b
+    torch.cuda.empty_cache()
