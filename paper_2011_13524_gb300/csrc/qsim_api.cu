@@ -67,11 +67,36 @@ Op dagger(const Op& op) {
     return r;
 }
 
-void run_gates(qs_state* s, const qs_circuit* c, const double* theta) {
-    for (int i = 0; i < c->n_gates; i++) {
-        Op op = op_of_gate(c->gates[i], s->n, theta);
-        launch_op(op, s->data, s->n, s->dt, s->stream, stage_of(s));
+// A complex128 run in double-float arithmetic holds the buffer in the double-float layout
+// between one conversion pass at entry and one at exit; every entry point sees IEEE doubles.
+bool use_df(const qs_state* s) { return s->dt == QS_C128 && c128_math() == QS_MATH_DF; }
+
+struct DFScope {
+    qs_state* s;
+    bool active;
+    explicit DFScope(qs_state* st, bool on) : s(st), active(on && !st->df) {
+        if (active) {
+            launch_to_df(s->data, s->n, s->stream);
+            s->df = 1;
+        }
     }
+    ~DFScope() {
+        if (active) {
+            s->df = 0;
+            try {
+                launch_from_df(s->data, s->n, s->stream);
+            } catch (...) {
+            }
+        }
+    }
+};
+
+void run_gates(qs_state* s, const qs_circuit* c, const double* theta) {
+    std::vector<Op> ops;
+    ops.reserve(c->n_gates);
+    for (int i = 0; i < c->n_gates; i++) ops.push_back(op_of_gate(c->gates[i], s->n, theta));
+    DFScope df(s, use_df(s));
+    for (const Op& op : ops) launch_op_arith(op, s->data, s->n, arith_of(s), s->stream, stage_of(s));
 }
 
 }  // namespace
@@ -134,7 +159,7 @@ struct WideMats {
     std::vector<const void*> ptr;
 };
 
-WideMats upload_wide(qs_state* s, const FusionPlan& p, std::vector<Op>& ops) {
+WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
     WideMats w;
     w.ptr.assign(ops.size(), nullptr);
     size_t total = 0;
@@ -142,22 +167,13 @@ WideMats upload_wide(qs_state* s, const FusionPlan& p, std::vector<Op>& ops) {
     for (size_t b = 0; b < ops.size(); b++) {
         if (ops[b].kind != OpKind::Dense || ops[b].targets.size() < 4) continue;
         offs[b] = total;
-        total += ops[b].data.size() * amp_bytes(s->dt);
+        total += ops[b].data.size() * kernel_entry_bytes(ar);
     }
     if (!total) return w;
     std::vector<unsigned char> host(total);
     for (size_t b = 0; b < ops.size(); b++) {
         if (ops[b].kind != OpKind::Dense || ops[b].targets.size() < 4) continue;
-        unsigned char* dst = host.data() + offs[b];
-        for (size_t e = 0; e < ops[b].data.size(); e++) {
-            if (s->dt == QS_C64) {
-                float v[2] = {float(ops[b].data[e].real()), float(ops[b].data[e].imag())};
-                std::memcpy(dst + 8 * e, v, 8);
-            } else {
-                double v[2] = {ops[b].data[e].real(), ops[b].data[e].imag()};
-                std::memcpy(dst + 16 * e, v, 16);
-            }
-        }
+        encode_entries(ar, ops[b].data, host.data() + offs[b]);
     }
     QS_TRY_CUDA(cudaMallocAsync(&w.dbuf, total, s->stream));
     QS_TRY_CUDA(cudaMemcpyAsync(w.dbuf, host.data(), total, cudaMemcpyHostToDevice, s->stream));
@@ -175,16 +191,18 @@ void apply_plan_impl(qs_state* s, const FusionPlan& p, float* block_ms) {
     std::vector<Op> ops;
     ops.reserve(p.blocks.size());
     for (size_t b = 0; b < p.blocks.size(); b++) ops.push_back(block_op(p, b));
-    WideMats wm = upload_wide(s, p, ops);
+    const bool df_run = use_df(s);
+    WideMats wm = upload_wide(s, df_run ? Arith::DF : arith_of(s), ops);
     std::vector<cudaEvent_t> ev;
     try {
+        DFScope df(s, df_run);
         if (block_ms) {
             ev.resize(ops.size() + 1);
             for (auto& e : ev) QS_TRY_CUDA(cudaEventCreate(&e));
             QS_TRY_CUDA(cudaEventRecord(ev[0], s->stream));
         }
         for (size_t b = 0; b < ops.size(); b++) {
-            launch_op(ops[b], s->data, s->n, s->dt, s->stream, stage_of(s));
+            launch_op_arith(ops[b], s->data, s->n, arith_of(s), s->stream, stage_of(s));
             if (block_ms) QS_TRY_CUDA(cudaEventRecord(ev[b + 1], s->stream));
         }
         if (block_ms) {
@@ -221,11 +239,10 @@ double measure_cost(int dev, qs_dtype dt, const Op& probe_op, int np_) {
     } g{s};
     Op op = probe_op;
     std::vector<Op> one{op};
-    FusionPlan dummy;
-    dummy.n = np_;
+    const Arith ar = dt == QS_C64 ? Arith::F32 : (c128_math() == QS_MATH_DF ? Arith::DF : Arith::F64);
     WideMats wm;
     if (op.kind == OpKind::Dense && op.targets.size() >= 4) {
-        wm = upload_wide(s, dummy, one);
+        wm = upload_wide(s, ar, one);
         op = one[0];
     }
     cudaEvent_t e0, e1;
@@ -234,7 +251,7 @@ double measure_cost(int dev, qs_dtype dt, const Op& probe_op, int np_) {
     float best = 1e30f;
     for (int r = 0; r < 4; r++) {
         QS_TRY_CUDA(cudaEventRecord(e0, s->stream));
-        launch_op(op, s->data, s->n, s->dt, s->stream, stage_of(s));
+        launch_op_arith(op, s->data, s->n, ar, s->stream, stage_of(s));
         QS_TRY_CUDA(cudaEventRecord(e1, s->stream));
         QS_TRY_CUDA(cudaEventSynchronize(e1));
         float ms = 0;
@@ -721,10 +738,18 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
             qs_destroy_state(b);
         }
     } guard{psi, lam};
+    // both buffers stay in the double-float layout for the whole sweep when that arithmetic
+    // is selected (they are scratch states, never seen outside this call)
+    if (use_df(psi)) {
+        psi->df = 1;
+        lam->df = 1;
+        launch_set_basis_arith(psi->data, c->n, Arith::DF, 0, st);
+    }
+    const Arith ar = arith_of(psi);
     // forward: psi = U_G ... U_1 |0>
     run_gates(psi, c, theta);
     // lambda = H psi ; E = Re <psi|lambda>
-    launch_apply_observable(groups, psi->data, lam->data, c->n, dt, st);
+    launch_apply_observable(groups, psi->data, lam->data, c->n, ar, st);
     double e2[2];
     reduce_inner(psi, lam, e2);
     *energy = e2[0];
@@ -750,8 +775,8 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
             grad[g.param_index] += -t[1];
         }
         Op inv = dagger(op);
-        launch_op(inv, psi->data, c->n, dt, st, stage_of(psi));
-        launch_op(inv, lam->data, c->n, dt, st, stage_of(lam));
+        launch_op_arith(inv, psi->data, c->n, ar, st, stage_of(psi));
+        launch_op_arith(inv, lam->data, c->n, ar, st, stage_of(lam));
     }
     QS_TRY_CUDA(cudaStreamSynchronize(st));
     API_END

@@ -1,0 +1,125 @@
+// Arithmetic policies of the gate kernels.
+//
+//   NativeArith<float>  complex64 storage, FP32 multiply-adds.
+//   NativeArith<double> complex128 storage, FP64 multiply-adds.
+//   DFArith             complex128 values held as double-float pairs: each real number is
+//                       hi + lo with two FP32 words (float4 {re_hi, re_lo, im_hi, im_lo}, the
+//                       same 16 bytes as an IEEE complex128 amplitude), updated on the FP32
+//                       pipes. GB300 executes FP64 at 1/64 of the FP32 rate, so the IEEE-double
+//                       update of a dense gate is arithmetic-bound far below HBM speed; the
+//                       double-float form keeps ~2^-46 relative accuracy per update.
+//
+// Double-float products use the FMA error-free transformation (the exact error of p = a*b is
+// fma(a, b, -p)) and Knuth's TwoSum for additions, accumulated as in the compensated dot
+// product of Ogita, Rump & Oishi (SIAM J. Sci. Comput. 26, 2005): the rounded partial sum in
+// s, every rounding error and cross term in c, and one TwoSum at the end. Intrinsics with an
+// explicit rounding mode keep the compiler from contracting these steps into FMAs.
+#pragma once
+
+#include "qsim_kernels.cuh"
+
+namespace qs {
+
+template <typename R>
+struct NativeArith {
+    using C = typename CT<R>::type;
+    using K = C;
+    using Acc = C;
+    __device__ __forceinline__ static Acc zero() { return cmake<C>(0.0, 0.0); }
+    __device__ __forceinline__ static void mac(Acc& a, const K& k, const C& v) { a = cfma(k, v, a); }
+    __device__ __forceinline__ static C out(const Acc& a) { return a; }
+    __device__ __forceinline__ static C ipow(const C& v, int k) { return mul_ipow(v, k); }
+    __device__ __forceinline__ static C basis(bool one) { return cmake<C>(one ? 1.0 : 0.0, 0.0); }
+    __host__ static K host_k(double re, double im) {
+        K k;
+        k.x = R(re);
+        k.y = R(im);
+        return k;
+    }
+};
+
+// a = hi + lo with |lo| <= ulp(hi)/2 (round to nearest)
+__host__ __device__ inline void split_double(double x, float& hi, float& lo) {
+    hi = float(x);
+    lo = float(x - double(hi));
+}
+
+struct DFArith {
+    using C = float4;  // {re_hi, re_lo, im_hi, im_lo}
+    using K = float4;
+    struct Acc {
+        float rs, rc, is, ic;  // real: partial sum, compensation; imaginary likewise
+    };
+    __device__ __forceinline__ static Acc zero() { return Acc{0.f, 0.f, 0.f, 0.f}; }
+    // (s, c) += (ah + al) * (bh + bl), dropping al * bl
+    __device__ __forceinline__ static void dprod(float& s, float& c, float ah, float al, float bh, float bl) {
+        const float p = __fmul_rn(ah, bh);
+        float e = __fmaf_rn(ah, bh, -p);
+        e = __fmaf_rn(ah, bl, e);
+        e = __fmaf_rn(al, bh, e);
+        const float t = __fadd_rn(s, p);
+        const float bp = __fsub_rn(t, s);
+        const float d = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(d, e));
+    }
+    __device__ __forceinline__ static void mac(Acc& a, const K& k, const C& v) {
+        dprod(a.rs, a.rc, k.x, k.y, v.x, v.y);      // + kr vr
+        dprod(a.rs, a.rc, -k.z, -k.w, v.z, v.w);    // - ki vi
+        dprod(a.is, a.ic, k.x, k.y, v.z, v.w);      // + kr vi
+        dprod(a.is, a.ic, k.z, k.w, v.x, v.y);      // + ki vr
+    }
+    __device__ __forceinline__ static void two_sum(float a, float b, float& h, float& l) {
+        h = __fadd_rn(a, b);
+        const float bp = __fsub_rn(h, a);
+        l = __fadd_rn(__fsub_rn(a, __fsub_rn(h, bp)), __fsub_rn(b, bp));
+    }
+    __device__ __forceinline__ static C out(const Acc& a) {
+        C r;
+        two_sum(a.rs, a.rc, r.x, r.y);
+        two_sum(a.is, a.ic, r.z, r.w);
+        return r;
+    }
+    __device__ __forceinline__ static C ipow(const C& v, int k) {
+        switch (k & 3) {
+            case 0: return v;
+            case 1: return make_float4(-v.z, -v.w, v.x, v.y);
+            case 2: return make_float4(-v.x, -v.y, -v.z, -v.w);
+            default: return make_float4(v.z, v.w, -v.x, -v.y);
+        }
+    }
+    __device__ __forceinline__ static C basis(bool one) { return make_float4(one ? 1.f : 0.f, 0.f, 0.f, 0.f); }
+    __host__ static K host_k(double re, double im) {
+        K k;
+        split_double(re, k.x, k.y);
+        split_double(im, k.z, k.w);
+        return k;
+    }
+};
+
+// value of a stored element widened to FP64 (re, im)
+__device__ __forceinline__ double2 widen(float2 v) { return make_double2(v.x, v.y); }
+__device__ __forceinline__ double2 widen(double2 v) { return v; }
+__device__ __forceinline__ double2 widen(float4 v) {
+    return make_double2(double(v.x) + double(v.y), double(v.z) + double(v.w));
+}
+// FP64 (re, im) -> stored element
+template <typename C>
+__device__ __forceinline__ C narrow(double re, double im);
+template <>
+__device__ __forceinline__ float2 narrow<float2>(double re, double im) {
+    return make_float2(float(re), float(im));
+}
+template <>
+__device__ __forceinline__ double2 narrow<double2>(double re, double im) {
+    return make_double2(re, im);
+}
+template <>
+__device__ __forceinline__ float4 narrow<float4>(double re, double im) {
+    float4 r;
+    split_double(re, r.x, r.y);
+    split_double(im, r.z, r.w);
+    return r;
+}
+
+}  // namespace qs

@@ -1,6 +1,7 @@
 // Gate-update kernels (Sec. 4.3.2): dense gate matrices on 1..6 targets with controls,
-// diagonal gates, phases on a subspace, Pauli strings and SWAPs, for complex64 and
-// complex128 states. All work in place on the state vector.
+// diagonal gates, phases on a subspace, Pauli strings and SWAPs. Each kernel is written once
+// over an arithmetic policy (qsim_arith.cuh): complex64 in FP32, complex128 in FP64, and
+// complex128 held as double-float pairs on the FP32 pipes. All work in place.
 //
 // Every kernel enumerates the 2^(n - fixed) elements x0 of B(0) (Eq. update_mat) with
 // the fixed bits (targets, controls) inserted at their positions; consecutive threads
@@ -8,8 +9,9 @@
 // 2^m amplitudes of its groups form contiguous runs (coalesced for low and high targets
 // alike). Grids are a multiple of the SM count, each thread striding over the range.
 #include <algorithm>
+#include <cstring>
 
-#include "qsim_kernels.cuh"
+#include "qsim_arith.cuh"
 
 namespace qs {
 
@@ -28,37 +30,37 @@ int sm_count() {
     return sms;
 }
 
-unsigned grid_for(uint64_t work, int per_thread = 1) {
-    const uint64_t want = (work + uint64_t(kThreads) * per_thread - 1) / (uint64_t(kThreads) * per_thread);
-    const uint64_t cap = uint64_t(sm_count()) * 16;  // 16 resident-ish CTAs per SM, then stride
+unsigned grid_for(uint64_t work) {
+    const uint64_t want = (work + kThreads - 1) / kThreads;
+    const uint64_t cap = uint64_t(sm_count()) * 16;  // 16 CTAs per SM, then stride
     return unsigned(std::max<uint64_t>(1, std::min(want, cap)));
 }
 
 // ------------------------------------------------------------------ dense, registers
-template <typename R, int M>
+template <typename P, int M>
 struct DenseRegParams {
     IndexPlan ip;
     uint64_t offs[1 << M];
-    typename CT<R>::type K[(1 << M) * (1 << M)];
+    typename P::K K[(1 << M) * (1 << M)];
 };
 
-template <typename R, int M>
-__global__ void __launch_bounds__(kThreads) k_dense_reg(typename CT<R>::type* __restrict__ psi,
-                                                        const __grid_constant__ DenseRegParams<R, M> P) {
-    using C = typename CT<R>::type;
+template <typename P, int M>
+__global__ void __launch_bounds__(kThreads) k_dense_reg(typename P::C* __restrict__ psi,
+                                                        const __grid_constant__ DenseRegParams<P, M> Pm) {
+    using C = typename P::C;
     constexpr int D = 1 << M;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P.ip.n_iter; i += stride) {
-        const uint64_t x0 = expand(i, P.ip);
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < Pm.ip.n_iter; i += stride) {
+        const uint64_t x0 = expand(i, Pm.ip);
         C v[D];
 #pragma unroll
-        for (int w = 0; w < D; w++) v[w] = psi[x0 + P.offs[w]];
+        for (int w = 0; w < D; w++) v[w] = psi[x0 + Pm.offs[w]];
 #pragma unroll
         for (int z = 0; z < D; z++) {
-            C acc = cmul(P.K[z * D], v[0]);
+            typename P::Acc a = P::zero();
 #pragma unroll
-            for (int w = 1; w < D; w++) acc = cfma(P.K[z * D + w], v[w], acc);
-            psi[x0 + P.offs[z]] = acc;
+            for (int w = 0; w < D; w++) P::mac(a, Pm.K[z * D + w], v[w]);
+            psi[x0 + Pm.offs[z]] = P::out(a);
         }
     }
 }
@@ -72,93 +74,99 @@ struct DenseSmemParams {
     uint64_t offs[64];
 };
 
-template <typename R, int M>
-__global__ void __launch_bounds__(kThreads) k_dense_smem(typename CT<R>::type* __restrict__ psi,
-                                                         const typename CT<R>::type* __restrict__ Kg,
-                                                         const __grid_constant__ DenseSmemParams P) {
-    using C = typename CT<R>::type;
+template <typename P, int M>
+__global__ void __launch_bounds__(kThreads) k_dense_smem(typename P::C* __restrict__ psi,
+                                                         const typename P::K* __restrict__ Kg,
+                                                         const __grid_constant__ DenseSmemParams Pm) {
+    using C = typename P::C;
+    using K = typename P::K;
     constexpr int D = 1 << M;
     constexpr int RC = D / 8;          // row chunks of 8
     constexpr int G = kThreads / RC;   // groups per tile
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* Ks = reinterpret_cast<C*>(smem_raw);
-    C* tile = Ks + D * D;              // tile[w * G + g]
+    K* Ks = reinterpret_cast<K*>(smem_raw);
+    C* tile = reinterpret_cast<C*>(Ks + D * D);   // tile[w * G + g]
     uint64_t* xs = reinterpret_cast<uint64_t*>(tile + D * G);
     for (int e = threadIdx.x; e < D * D; e += kThreads) Ks[e] = Kg[e];
     const int g = threadIdx.x % G, rc = threadIdx.x / G;
-    const uint64_t n_tiles = (P.ip.n_iter + G - 1) / G;
+    const uint64_t n_tiles = (Pm.ip.n_iter + G - 1) / G;
     for (uint64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const uint64_t base = t * G;
         __syncthreads();  // previous tile fully consumed
         if (threadIdx.x < G) {
             const uint64_t i = base + threadIdx.x;
-            xs[threadIdx.x] = i < P.ip.n_iter ? expand(i, P.ip) : ~0ull;
+            xs[threadIdx.x] = i < Pm.ip.n_iter ? expand(i, Pm.ip) : ~0ull;
         }
         __syncthreads();
         for (int e = threadIdx.x; e < D * G; e += kThreads) {
             const int w = e / G, gg = e % G;
             const uint64_t x0 = xs[gg];
-            if (x0 != ~0ull) tile[e] = psi[x0 + P.offs[w]];
+            if (x0 != ~0ull) tile[e] = psi[x0 + Pm.offs[w]];
         }
         __syncthreads();
         const uint64_t x0 = xs[g];
         if (x0 != ~0ull) {
-            C acc[8];
+            typename P::Acc acc[8];
 #pragma unroll
-            for (int r = 0; r < 8; r++) acc[r] = cmake<C>(0.0, 0.0);
-#pragma unroll 4
+            for (int r = 0; r < 8; r++) acc[r] = P::zero();
+#pragma unroll 2
             for (int w = 0; w < D; w++) {
                 const C v = tile[w * G + g];
 #pragma unroll
-                for (int r = 0; r < 8; r++) acc[r] = cfma(Ks[(rc * 8 + r) * D + w], v, acc[r]);
+                for (int r = 0; r < 8; r++) P::mac(acc[r], Ks[(rc * 8 + r) * D + w], v);
             }
 #pragma unroll
-            for (int r = 0; r < 8; r++) psi[x0 + P.offs[rc * 8 + r]] = acc[r];
+            for (int r = 0; r < 8; r++) psi[x0 + Pm.offs[rc * 8 + r]] = P::out(acc[r]);
         }
     }
 }
 
 // ------------------------------------------------------------------ diagonal
+template <typename P>
 struct DiagParams {
     IndexPlan ip;  // controls only
     int32_t m;
     int32_t tpos[QS_MAX_TARGETS];
-    double2 d[1 << QS_MAX_TARGETS];
+    typename P::K d[1 << QS_MAX_TARGETS];
 };
 
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_diag(typename CT<R>::type* __restrict__ psi,
-                                                   const __grid_constant__ DiagParams P) {
-    using C = typename CT<R>::type;
+template <typename P>
+__global__ void __launch_bounds__(kThreads) k_diag(typename P::C* __restrict__ psi,
+                                                   const __grid_constant__ DiagParams<P> Pm) {
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P.ip.n_iter; i += stride) {
-        const uint64_t x = expand(i, P.ip);
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < Pm.ip.n_iter; i += stride) {
+        const uint64_t x = expand(i, Pm.ip);
         int r = 0;
 #pragma unroll 1
-        for (int j = 0; j < P.m; j++) r |= int((x >> P.tpos[j]) & 1) << j;
-        const double2 dd = P.d[r];
-        psi[x] = cmul(cmake<C>(dd.x, dd.y), psi[x]);
+        for (int j = 0; j < Pm.m; j++) r |= int((x >> Pm.tpos[j]) & 1) << j;
+        typename P::Acc a = P::zero();
+        P::mac(a, Pm.d[r], psi[x]);
+        psi[x] = P::out(a);
     }
 }
 
 // ------------------------------------------------------------------ phase on a subspace
 // psi_x *= phase for every x whose fixed bits match; mode 0 general, 1..3 = i^mode (exact).
+template <typename P>
 struct PhaseParams {
     IndexPlan ip;
-    double2 phase;
+    typename P::K phase;
     int32_t mode;
 };
 
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_phase(typename CT<R>::type* __restrict__ psi,
-                                                    const __grid_constant__ PhaseParams P) {
-    using C = typename CT<R>::type;
+template <typename P>
+__global__ void __launch_bounds__(kThreads) k_phase(typename P::C* __restrict__ psi,
+                                                    const __grid_constant__ PhaseParams<P> Pm) {
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    const C ph = cmake<C>(P.phase.x, P.phase.y);
-    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P.ip.n_iter; i += stride) {
-        const uint64_t x = expand(i, P.ip);
-        const C v = psi[x];
-        psi[x] = P.mode == 0 ? cmul(ph, v) : mul_ipow(v, P.mode);
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < Pm.ip.n_iter; i += stride) {
+        const uint64_t x = expand(i, Pm.ip);
+        if (Pm.mode == 0) {
+            typename P::Acc a = P::zero();
+            P::mac(a, Pm.phase, psi[x]);
+            psi[x] = P::out(a);
+        } else {
+            psi[x] = P::ipow(psi[x], Pm.mode);
+        }
     }
 }
 
@@ -171,22 +179,21 @@ struct PauliParams {
     int32_t nY;
 };
 
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_pauli(typename CT<R>::type* __restrict__ psi,
-                                                    const __grid_constant__ PauliParams P) {
-    using C = typename CT<R>::type;
+template <typename P>
+__global__ void __launch_bounds__(kThreads) k_pauli(typename P::C* __restrict__ psi,
+                                                    const __grid_constant__ PauliParams Pm) {
+    using C = typename P::C;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P.ip.n_iter; i += stride) {
-        const uint64_t y = expand(i, P.ip);
-        if (P.xmask == 0) {
-            if (parity64(y & P.zmask)) psi[y] = mul_ipow(psi[y], 2);
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < Pm.ip.n_iter; i += stride) {
+        const uint64_t y = expand(i, Pm.ip);
+        if (Pm.xmask == 0) {
+            if (parity64(y & Pm.zmask)) psi[y] = P::ipow(psi[y], 2);
             continue;
         }
-        const uint64_t y2 = y ^ P.xmask;
+        const uint64_t y2 = y ^ Pm.xmask;
         const C a = psi[y], b = psi[y2];
-        // new psi[y2] = ph s(y) a ; new psi[y] = ph s(y2) b
-        psi[y2] = mul_ipow(a, P.nY + 2 * parity64(y & P.zmask));
-        psi[y] = mul_ipow(b, P.nY + 2 * parity64(y2 & P.zmask));
+        psi[y2] = P::ipow(a, Pm.nY + 2 * parity64(y & Pm.zmask));
+        psi[y] = P::ipow(b, Pm.nY + 2 * parity64(y2 & Pm.zmask));
     }
 }
 
@@ -197,79 +204,90 @@ struct SwapParams {
     uint64_t flip;
 };
 
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_swap(typename CT<R>::type* __restrict__ psi,
-                                                   const __grid_constant__ SwapParams P) {
-    using C = typename CT<R>::type;
+template <typename P>
+__global__ void __launch_bounds__(kThreads) k_swap(typename P::C* __restrict__ psi,
+                                                   const __grid_constant__ SwapParams Pm) {
+    using C = typename P::C;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < P.ip.n_iter; i += stride) {
-        const uint64_t x = expand(i, P.ip);
-        const C a = psi[x], b = psi[x ^ P.flip];
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < Pm.ip.n_iter; i += stride) {
+        const uint64_t x = expand(i, Pm.ip);
+        const C a = psi[x], b = psi[x ^ Pm.flip];
         psi[x] = b;
-        psi[x ^ P.flip] = a;
+        psi[x ^ Pm.flip] = a;
     }
 }
 
-// ------------------------------------------------------------------ basis state
-template <typename R>
-__global__ void k_set_basis(typename CT<R>::type* __restrict__ psi, uint64_t N, uint64_t j) {
-    using C = typename CT<R>::type;
+// ------------------------------------------------------------------ basis state, layouts
+template <typename P>
+__global__ void k_set_basis(typename P::C* __restrict__ psi, uint64_t N, uint64_t j) {
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride)
-        psi[i] = cmake<C>(i == j ? 1.0 : 0.0, 0.0);
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) psi[i] = P::basis(i == j);
+}
+
+// IEEE complex128 <-> double-float, in place (same 16 bytes per amplitude)
+__global__ void k_to_df(double2* __restrict__ psi, uint64_t N) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const double2 v = psi[i];
+        float4 r;
+        split_double(v.x, r.x, r.y);
+        split_double(v.y, r.z, r.w);
+        reinterpret_cast<float4*>(psi)[i] = r;
+    }
+}
+__global__ void k_from_df(double2* __restrict__ psi, uint64_t N) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const float4 v = reinterpret_cast<const float4*>(psi)[i];
+        psi[i] = make_double2(double(v.x) + double(v.y), double(v.z) + double(v.w));
+    }
 }
 
 // ------------------------------------------------------------------ launch helpers
-template <typename R, int M>
-void launch_dense_reg(const Op& op, const IndexPlan& ip, void* psi, cudaStream_t st) {
-    using C = typename CT<R>::type;
-    DenseRegParams<R, M> P;
-    P.ip = ip;
-    constexpr int D = 1 << M;
-    for (int w = 0; w < D; w++) {
+template <int M>
+void fill_offs(const Op& op, uint64_t* offs) {
+    for (int w = 0; w < (1 << M); w++) {
         uint64_t o = 0;
         for (int j = 0; j < M; j++)
             if ((w >> j) & 1) o |= 1ull << op.targets[j];
-        P.offs[w] = o;
+        offs[w] = o;
     }
-    for (int e = 0; e < D * D; e++) {
-        C c;
-        c.x = R(op.data[e].real());
-        c.y = R(op.data[e].imag());
-        P.K[e] = c;
-    }
-    k_dense_reg<R, M><<<grid_for(ip.n_iter), kThreads, 0, st>>>(reinterpret_cast<C*>(psi), P);
 }
 
-template <typename R, int M>
+template <typename P, int M>
+void launch_dense_reg(const Op& op, const IndexPlan& ip, void* psi, cudaStream_t st) {
+    DenseRegParams<P, M> Pm;
+    Pm.ip = ip;
+    fill_offs<M>(op, Pm.offs);
+    constexpr int D = 1 << M;
+    for (int e = 0; e < D * D; e++) Pm.K[e] = P::host_k(op.data[e].real(), op.data[e].imag());
+    k_dense_reg<P, M><<<grid_for(ip.n_iter), kThreads, 0, st>>>(reinterpret_cast<typename P::C*>(psi), Pm);
+}
+
+template <typename P, int M>
 void launch_dense_smem(const Op& op, const IndexPlan& ip, void* psi, const void* dK, cudaStream_t st) {
-    using C = typename CT<R>::type;
+    using C = typename P::C;
+    using K = typename P::K;
     constexpr int D = 1 << M;
     constexpr int G = kThreads / (D / 8);
-    DenseSmemParams P;
-    P.ip = ip;
-    for (int w = 0; w < D; w++) {
-        uint64_t o = 0;
-        for (int j = 0; j < M; j++)
-            if ((w >> j) & 1) o |= 1ull << op.targets[j];
-        P.offs[w] = o;
-    }
-    const size_t smem = sizeof(C) * (D * D + D * G) + sizeof(uint64_t) * G;
+    DenseSmemParams Pm;
+    Pm.ip = ip;
+    fill_offs<M>(op, Pm.offs);
+    const size_t smem = sizeof(K) * D * D + sizeof(C) * D * G + sizeof(uint64_t) * G;
     static bool attr_set = false;
     if (!attr_set) {
-        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_smem<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_smem<P, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
         attr_set = true;
     }
     const uint64_t n_tiles = (ip.n_iter + G - 1) / G;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, uint64_t(sm_count()) * 4)));
-    k_dense_smem<R, M><<<grid, kThreads, smem, st>>>(reinterpret_cast<C*>(psi), reinterpret_cast<const C*>(dK), P);
+    k_dense_smem<P, M><<<grid, kThreads, smem, st>>>(reinterpret_cast<C*>(psi), reinterpret_cast<const K*>(dK), Pm);
 }
 
-}  // namespace
-
-template <typename R>
-static void launch_typed(const Op& op, void* psi, int n, cudaStream_t st, void* stage) {
-    using C = typename CT<R>::type;
+template <typename P>
+void launch_with(const Op& op, void* psi, int n, cudaStream_t st, void* stage) {
+    using C = typename P::C;
+    using K = typename P::K;
     std::vector<int> fixed;
     uint64_t setmask = 0;
     for (size_t j = 0; j < op.controls.size(); j++) {
@@ -281,63 +299,61 @@ static void launch_typed(const Op& op, void* psi, int n, cudaStream_t st, void* 
             const int m = int(op.targets.size());
             for (int t : op.targets) fixed.push_back(t);
             IndexPlan ip = make_index_plan(n, fixed, setmask);
-            if (m == 1) return launch_dense_reg<R, 1>(op, ip, psi, st);
-            if (m == 2) return launch_dense_reg<R, 2>(op, ip, psi, st);
-            if (m == 3) return launch_dense_reg<R, 3>(op, ip, psi, st);
-            if (m == 4 && sizeof(R) == 4) return launch_dense_reg<R, 4>(op, ip, psi, st);
+            if (m == 1) return launch_dense_reg<P, 1>(op, ip, psi, st);
+            if (m == 2) return launch_dense_reg<P, 2>(op, ip, psi, st);
+            if (m == 3) return launch_dense_reg<P, 3>(op, ip, psi, st);
+            if (m == 4 && sizeof(C) == 8) return launch_dense_reg<P, 4>(op, ip, psi, st);
             // the shared-memory kernels read the matrix from device memory: either the
-            // caller's copy (already in the state's element type) or the state's staging
+            // caller's copy (already in this policy's entry type) or the state's staging
             // buffer, refilled by a copy queued on the same stream before the launch
             const void* dK = op.dmat;
             if (!dK) {
                 QS_REQUIRE(stage != nullptr, "no staging buffer for a wide dense gate");
                 const int D = 1 << m;
-                std::vector<C> hk(size_t(D) * D);
-                for (size_t e = 0; e < hk.size(); e++) {
-                    hk[e].x = R(op.data[e].real());
-                    hk[e].y = R(op.data[e].imag());
-                }
-                QS_TRY_CUDA(cudaMemcpyAsync(stage, hk.data(), hk.size() * sizeof(C), cudaMemcpyHostToDevice, st));
+                std::vector<K> hk(size_t(D) * D);
+                for (size_t e = 0; e < hk.size(); e++) hk[e] = P::host_k(op.data[e].real(), op.data[e].imag());
+                QS_TRY_CUDA(cudaMemcpyAsync(stage, hk.data(), hk.size() * sizeof(K), cudaMemcpyHostToDevice, st));
+                QS_TRY_CUDA(cudaStreamSynchronize(st));  // hk is host memory that dies on return
                 dK = stage;
             }
-            if (m == 4) return launch_dense_smem<R, 4>(op, ip, psi, dK, st);
-            if (m == 5) return launch_dense_smem<R, 5>(op, ip, psi, dK, st);
-            if (m == 6) return launch_dense_smem<R, 6>(op, ip, psi, dK, st);
+            if (m == 4) return launch_dense_smem<P, 4>(op, ip, psi, dK, st);
+            if (m == 5) return launch_dense_smem<P, 5>(op, ip, psi, dK, st);
+            if (m == 6) return launch_dense_smem<P, 6>(op, ip, psi, dK, st);
             throw Error{QS_ERR_UNSUPPORTED, "dense gates act on at most 6 targets"};
         }
         case OpKind::Diag: {
             IndexPlan ip = make_index_plan(n, fixed, setmask);
-            DiagParams P;
-            P.ip = ip;
-            P.m = int(op.targets.size());
-            for (int j = 0; j < P.m; j++) P.tpos[j] = op.targets[j];
-            for (size_t e = 0; e < op.data.size(); e++) P.d[e] = make_double2(op.data[e].real(), op.data[e].imag());
-            k_diag<R><<<grid_for(ip.n_iter), kThreads, 0, st>>>(reinterpret_cast<C*>(psi), P);
+            DiagParams<P> Pm;
+            Pm.ip = ip;
+            Pm.m = int(op.targets.size());
+            for (int j = 0; j < Pm.m; j++) Pm.tpos[j] = op.targets[j];
+            for (size_t e = 0; e < op.data.size(); e++) Pm.d[e] = P::host_k(op.data[e].real(), op.data[e].imag());
+            k_diag<P><<<grid_for(ip.n_iter), kThreads, 0, st>>>(reinterpret_cast<C*>(psi), Pm);
             return;
         }
         case OpKind::Phase: {
             if (op.phase == cplx(1.0, 0.0)) return;
             IndexPlan ip = make_index_plan(n, fixed, setmask);
-            PhaseParams P;
-            P.ip = ip;
-            P.phase = make_double2(op.phase.real(), op.phase.imag());
-            P.mode = 0;
-            if (op.phase == cplx(0.0, 1.0)) P.mode = 1;
-            if (op.phase == cplx(-1.0, 0.0)) P.mode = 2;
-            if (op.phase == cplx(0.0, -1.0)) P.mode = 3;
-            k_phase<R><<<grid_for(ip.n_iter), kThreads, 0, st>>>(reinterpret_cast<C*>(psi), P);
+            PhaseParams<P> Pm;
+            Pm.ip = ip;
+            Pm.phase = P::host_k(op.phase.real(), op.phase.imag());
+            Pm.mode = 0;
+            if (op.phase == cplx(0.0, 1.0)) Pm.mode = 1;
+            if (op.phase == cplx(-1.0, 0.0)) Pm.mode = 2;
+            if (op.phase == cplx(0.0, -1.0)) Pm.mode = 3;
+            k_phase<P><<<grid_for(ip.n_iter), kThreads, 0, st>>>(reinterpret_cast<C*>(psi), Pm);
             return;
         }
         case OpKind::Pauli: {
             if (op.xmask == 0 && op.zmask == 0) return;
             if (op.xmask) fixed.push_back(__builtin_ctzll(op.xmask));
             IndexPlan ip = make_index_plan(n, fixed, setmask);
-            PauliParams P;
-            P.ip = ip;
-            P.xmask = op.xmask;
-            P.zmask = op.zmask;
-            P.nY = __builtin_popcountll(op.xmask & op.zmask);
-            k_pauli<R><<<grid_for(ip.n_iter), kThreads, 0, st>>>(reinterpret_cast<C*>(psi), P);
+            PauliParams Pm;
+            Pm.ip = ip;
+            Pm.xmask = op.xmask;
+            Pm.zmask = op.zmask;
+            Pm.nY = __builtin_popcountll(op.xmask & op.zmask);
+            k_pauli<P><<<grid_for(ip.n_iter), kThreads, 0, st>>>(reinterpret_cast<C*>(psi), Pm);
             return;
         }
         case OpKind::Swap: {
@@ -345,30 +361,77 @@ static void launch_typed(const Op& op, void* psi, int n, cudaStream_t st, void* 
             fixed.push_back(a);
             fixed.push_back(b);
             IndexPlan ip = make_index_plan(n, fixed, setmask | (1ull << a));
-            SwapParams P;
-            P.ip = ip;
-            P.flip = (1ull << a) | (1ull << b);
-            k_swap<R><<<grid_for(ip.n_iter), kThreads, 0, st>>>(reinterpret_cast<C*>(psi), P);
+            SwapParams Pm;
+            Pm.ip = ip;
+            Pm.flip = (1ull << a) | (1ull << b);
+            k_swap<P><<<grid_for(ip.n_iter), kThreads, 0, st>>>(reinterpret_cast<C*>(psi), Pm);
             return;
         }
     }
 }
 
+}  // namespace
+
+void launch_op_arith(const Op& op, void* psi, int n, Arith ar, cudaStream_t st, void* stage) {
+    switch (ar) {
+        case Arith::F32: launch_with<NativeArith<float>>(op, psi, n, st, stage); break;
+        case Arith::F64: launch_with<NativeArith<double>>(op, psi, n, st, stage); break;
+        case Arith::DF: launch_with<DFArith>(op, psi, n, st, stage); break;
+    }
+    QS_TRY_CUDA(cudaGetLastError());
+}
+
 void launch_op(const Op& op, void* psi, int n, qs_dtype dt, cudaStream_t st, void* stage) {
-    if (dt == QS_C64)
-        launch_typed<float>(op, psi, n, st, stage);
-    else
-        launch_typed<double>(op, psi, n, st, stage);
+    launch_op_arith(op, psi, n, dt == QS_C64 ? Arith::F32 : Arith::F64, st, stage);
+}
+
+void launch_set_basis_arith(void* psi, int n, Arith ar, uint64_t j, cudaStream_t st) {
+    const uint64_t N = 1ull << n;
+    switch (ar) {
+        case Arith::F32:
+            k_set_basis<NativeArith<float>><<<grid_for(N), kThreads, 0, st>>>(reinterpret_cast<float2*>(psi), N, j);
+            break;
+        case Arith::F64:
+            k_set_basis<NativeArith<double>><<<grid_for(N), kThreads, 0, st>>>(reinterpret_cast<double2*>(psi), N, j);
+            break;
+        case Arith::DF:
+            k_set_basis<DFArith><<<grid_for(N), kThreads, 0, st>>>(reinterpret_cast<float4*>(psi), N, j);
+            break;
+    }
     QS_TRY_CUDA(cudaGetLastError());
 }
 
 void launch_set_basis(void* psi, int n, qs_dtype dt, uint64_t j, cudaStream_t st) {
+    launch_set_basis_arith(psi, n, dt == QS_C64 ? Arith::F32 : Arith::F64, j, st);
+}
+
+void launch_to_df(void* psi, int n, cudaStream_t st) {
     const uint64_t N = 1ull << n;
-    if (dt == QS_C64)
-        k_set_basis<float><<<grid_for(N), kThreads, 0, st>>>(reinterpret_cast<float2*>(psi), N, j);
-    else
-        k_set_basis<double><<<grid_for(N), kThreads, 0, st>>>(reinterpret_cast<double2*>(psi), N, j);
+    k_to_df<<<grid_for(N), kThreads, 0, st>>>(reinterpret_cast<double2*>(psi), N);
     QS_TRY_CUDA(cudaGetLastError());
+}
+
+void launch_from_df(void* psi, int n, cudaStream_t st) {
+    const uint64_t N = 1ull << n;
+    k_from_df<<<grid_for(N), kThreads, 0, st>>>(reinterpret_cast<double2*>(psi), N);
+    QS_TRY_CUDA(cudaGetLastError());
+}
+
+// matrix entries in the form a policy's kernels read from device memory
+size_t kernel_entry_bytes(Arith ar) { return ar == Arith::F32 ? 8 : 16; }
+void encode_entries(Arith ar, const std::vector<cplx>& m, unsigned char* dst) {
+    for (size_t e = 0; e < m.size(); e++) {
+        if (ar == Arith::F32) {
+            float2 k = NativeArith<float>::host_k(m[e].real(), m[e].imag());
+            std::memcpy(dst + 8 * e, &k, 8);
+        } else if (ar == Arith::F64) {
+            double2 k = NativeArith<double>::host_k(m[e].real(), m[e].imag());
+            std::memcpy(dst + 16 * e, &k, 16);
+        } else {
+            float4 k = DFArith::host_k(m[e].real(), m[e].imag());
+            std::memcpy(dst + 16 * e, &k, 16);
+        }
+    }
 }
 
 }  // namespace qs

@@ -60,6 +60,7 @@ struct qs_state {
     int device = 0;
     qs::Scratch scratch;
     void* d_stage = nullptr;  // kStageBytes, allocated on first wide dense gate
+    int df = 0;               // 1 while a complex128 buffer holds the double-float layout
 };
 
 namespace qs {
@@ -109,13 +110,28 @@ Op op_of_gate(const qs_gate& g, int n, const double* theta_override);
 // validation of qubit lists
 void check_qubits(int n, const int* t, int m, const int* c, int mc);
 
+// Arithmetic of the gate kernels: complex64 in FP32, complex128 in FP64, or complex128 held
+// as double-float pairs (float4 {re_hi, re_lo, im_hi, im_lo}) on the FP32 pipes.
+enum class Arith { F32 = 0, F64 = 1, DF = 2 };
+inline Arith arith_of(const qs_state* s) {
+    return s->dt == QS_C64 ? Arith::F32 : (s->df ? Arith::DF : Arith::F64);
+}
+
 // ------------------------------------------------------------------ device launches
 // All launches are asynchronous on `st`. psi points at 2^n amplitudes of dtype dt.
 // `stage`: a device buffer of at least kStageBytes, used to hand wide dense matrices to the
 // kernels when op.dmat is not set.
 constexpr size_t kStageBytes = 64 * 64 * 16;
 void launch_op(const Op& op, void* psi, int n, qs_dtype dt, cudaStream_t st, void* stage);
+void launch_op_arith(const Op& op, void* psi, int n, Arith ar, cudaStream_t st, void* stage);
 void launch_set_basis(void* psi, int n, qs_dtype dt, uint64_t j, cudaStream_t st);
+void launch_set_basis_arith(void* psi, int n, Arith ar, uint64_t j, cudaStream_t st);
+// in-place layout change of a complex128 buffer: IEEE doubles <-> double-float pairs
+void launch_to_df(void* psi, int n, cudaStream_t st);
+void launch_from_df(void* psi, int n, cudaStream_t st);
+// gate-matrix entries in the layout the kernels of `ar` read from device memory
+size_t kernel_entry_bytes(Arith ar);
+void encode_entries(Arith ar, const std::vector<cplx>& m, unsigned char* dst);
 
 // Reductions: write results into the state's scratch and copy to host; synchronise.
 void reduce_norm2(qs_state* s, double* out);
@@ -135,7 +151,7 @@ std::vector<PauliGroup> group_observable(const qs_pauli_obs* obs, int n);
 
 // lambda <- O psi (sum of Pauli strings), out-of-place; asynchronous.
 void launch_apply_observable(const std::vector<PauliGroup>& groups, const void* psi, void* lam, int n,
-                             qs_dtype dt, cudaStream_t st);
+                             Arith ar, cudaStream_t st);
 
 // complex128 arithmetic mode (QS_MATH_FP64 / QS_MATH_DF)
 int c128_math();

@@ -13,8 +13,9 @@
 //   <psi|P|psi> restricted to the pair = i^{#Y} (s(y) A + s(y^f) conj(A)).
 #include <algorithm>
 #include <map>
+#include <type_traits>
 
-#include "qsim_kernels.cuh"
+#include "qsim_arith.cuh"
 
 namespace qs {
 
@@ -38,9 +39,6 @@ unsigned red_grid(uint64_t work) {
     const uint64_t want = (work + kRedThreads * 4 - 1) / (kRedThreads * 4);
     return unsigned(std::max<uint64_t>(1, std::min<uint64_t>(want, uint64_t(sms()) * 4)));
 }
-
-__device__ __forceinline__ double2 widen(float2 v) { return make_double2(v.x, v.y); }
-__device__ __forceinline__ double2 widen(double2 v) { return v; }
 
 // Block partial of (re, im) pairs into part[2*blockIdx.x + {0,1}].
 __device__ __forceinline__ void write_partial2(double re, double im, double* part) {
@@ -186,14 +184,20 @@ __global__ void __launch_bounds__(kRedThreads) k_apply_obs(const C* __restrict__
             re = fma(T.coef, p.x, re);
             im = fma(T.coef, p.y, im);
         }
-        C out;
-        out.x = decltype(out.x)(re);
-        out.y = decltype(out.y)(im);
-        lam[y] = out;
+        lam[y] = narrow<C>(re, im);
     }
 }
 
 // ---------------------------------------------------------------- host side
+// calls f(C*) with the state's buffer typed by its arithmetic layout
+template <typename F>
+void with_type(Arith ar, const void* p, F&& f) {
+    switch (ar) {
+        case Arith::F32: f(reinterpret_cast<const float2*>(p)); break;
+        case Arith::F64: f(reinterpret_cast<const double2*>(p)); break;
+        case Arith::DF: f(reinterpret_cast<const float4*>(p)); break;
+    }
+}
 void ensure_scratch(qs_state* s, size_t part_doubles) {
     Scratch& sc = s->scratch;
     if (sc.part_cap < part_doubles) {
@@ -250,10 +254,7 @@ void reduce_norm2(qs_state* s, double* out) {
     const uint64_t N = 1ull << s->n;
     const unsigned g = red_grid(N);
     ensure_scratch(s, 2 * g + 2);
-    if (s->dt == QS_C64)
-        k_norm2<<<g, kRedThreads, 0, s->stream>>>(reinterpret_cast<const float2*>(s->data), N, s->scratch.d_part);
-    else
-        k_norm2<<<g, kRedThreads, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), N, s->scratch.d_part);
+    with_type(arith_of(s), s->data, [&](auto p) { k_norm2<<<g, kRedThreads, 0, s->stream>>>(p, N, s->scratch.d_part); });
     QS_TRY_CUDA(cudaGetLastError());
     double r[2];
     finish2(s, int(g), r);
@@ -269,12 +270,11 @@ void reduce_inner(const qs_state* a, const qs_state* b, double out[2]) {
         // order b's pending work before the read on a's stream
         QS_TRY_CUDA(cudaStreamSynchronize(b->stream));
     }
-    if (s->dt == QS_C64)
-        k_inner<<<g, kRedThreads, 0, s->stream>>>(reinterpret_cast<const float2*>(a->data),
-                                                  reinterpret_cast<const float2*>(b->data), N, s->scratch.d_part);
-    else
-        k_inner<<<g, kRedThreads, 0, s->stream>>>(reinterpret_cast<const double2*>(a->data),
-                                                  reinterpret_cast<const double2*>(b->data), N, s->scratch.d_part);
+    QS_REQUIRE(arith_of(a) == arith_of(b), "states in different layouts");
+    with_type(arith_of(a), a->data, [&](auto pa) {
+        using CP = decltype(pa);
+        k_inner<<<g, kRedThreads, 0, s->stream>>>(pa, reinterpret_cast<CP>(b->data), N, s->scratch.d_part);
+    });
     QS_TRY_CUDA(cudaGetLastError());
     finish2(s, int(g), out);
 }
@@ -312,10 +312,7 @@ void reduce_expectation(qs_state* s, const qs_pauli_obs* obs, double out[2]) {
         }
         const unsigned g = red_grid(P.ip.n_iter);
         double* part = s->scratch.d_part + 2 * size_t(slots);
-        if (s->dt == QS_C64)
-            k_expect_group<<<g, kRedThreads, 0, s->stream>>>(reinterpret_cast<const float2*>(s->data), P, part);
-        else
-            k_expect_group<<<g, kRedThreads, 0, s->stream>>>(reinterpret_cast<const double2*>(s->data), P, part);
+        with_type(arith_of(s), s->data, [&](auto p) { k_expect_group<<<g, kRedThreads, 0, s->stream>>>(p, P, part); });
         QS_TRY_CUDA(cudaGetLastError());
         slots += int(g);
     }
@@ -327,19 +324,17 @@ void reduce_pauli_transition(qs_state* lam, const qs_state* psi, uint64_t xmask,
     const unsigned g = red_grid(N);
     ensure_scratch(lam, 2 * g + 2);
     const int nY = __builtin_popcountll(xmask & zmask);
-    if (lam->dt == QS_C64)
-        k_transition<<<g, kRedThreads, 0, lam->stream>>>(reinterpret_cast<const float2*>(lam->data),
-                                                         reinterpret_cast<const float2*>(psi->data), N, xmask, zmask,
-                                                         nY, lam->scratch.d_part);
-    else
-        k_transition<<<g, kRedThreads, 0, lam->stream>>>(reinterpret_cast<const double2*>(lam->data),
-                                                         reinterpret_cast<const double2*>(psi->data), N, xmask, zmask,
-                                                         nY, lam->scratch.d_part);
+    QS_REQUIRE(arith_of(lam) == arith_of(psi), "states in different layouts");
+    with_type(arith_of(lam), lam->data, [&](auto pl) {
+        using CP = decltype(pl);
+        k_transition<<<g, kRedThreads, 0, lam->stream>>>(pl, reinterpret_cast<CP>(psi->data), N, xmask, zmask, nY,
+                                                         lam->scratch.d_part);
+    });
     QS_TRY_CUDA(cudaGetLastError());
     finish2(lam, int(g), out);
 }
 
-void launch_apply_observable(const std::vector<PauliGroup>& groups, const void* psi, void* lam, int n, qs_dtype dt,
+void launch_apply_observable(const std::vector<PauliGroup>& groups, const void* psi, void* lam, int n, Arith ar,
                              cudaStream_t st) {
     std::vector<ObsDevTerm> terms;
     for (const auto& g : groups)
@@ -347,19 +342,17 @@ void launch_apply_observable(const std::vector<PauliGroup>& groups, const void* 
             terms.push_back(ObsDevTerm{g.xmask, g.zmask[t], g.coef[t], __builtin_popcountll(g.xmask & g.zmask[t]), 0});
     const uint64_t N = 1ull << n;
     if (terms.empty()) {
-        QS_TRY_CUDA(cudaMemsetAsync(lam, 0, N * amp_bytes(dt), st));
+        QS_TRY_CUDA(cudaMemsetAsync(lam, 0, N * (ar == Arith::F32 ? 8 : 16), st));
         return;
     }
     ObsDevTerm* d_terms = nullptr;
     QS_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_terms), terms.size() * sizeof(ObsDevTerm), st));
     QS_TRY_CUDA(cudaMemcpyAsync(d_terms, terms.data(), terms.size() * sizeof(ObsDevTerm), cudaMemcpyHostToDevice, st));
     const unsigned g = red_grid(N);
-    if (dt == QS_C64)
-        k_apply_obs<<<g, kRedThreads, 0, st>>>(reinterpret_cast<const float2*>(psi), reinterpret_cast<float2*>(lam), N,
-                                               d_terms, int(terms.size()));
-    else
-        k_apply_obs<<<g, kRedThreads, 0, st>>>(reinterpret_cast<const double2*>(psi), reinterpret_cast<double2*>(lam),
-                                               N, d_terms, int(terms.size()));
+    with_type(ar, psi, [&](auto pp) {
+        using C = std::remove_const_t<std::remove_pointer_t<decltype(pp)>>;
+        k_apply_obs<<<g, kRedThreads, 0, st>>>(pp, reinterpret_cast<C*>(lam), N, d_terms, int(terms.size()));
+    });
     QS_TRY_CUDA(cudaGetLastError());
     QS_TRY_CUDA(cudaFreeAsync(d_terms, st));
 }

@@ -1,0 +1,126 @@
+"""GPU parity of the complex128 double-float arithmetic (QS_MATH_DF) against the FP64 oracle.
+
+In this mode a circuit run converts the state in place to double-float pairs, applies every
+gate on the FP32 pipes and converts back; the result must still meet the complex128 bound
+(1e-12 max-abs amplitude error) and the state seen at every entry point is IEEE complex128.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2011_13524_gb300 as qs
+    qs.lib()
+    return qs
+
+
+@pytest.fixture
+def df(qs):
+    old = qs.get_c128_math()
+    qs.set_c128_math(qs.QS_MATH_DF)
+    yield qs
+    qs.set_c128_math(old)
+
+
+def maxabs(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 6, 9, 12])
+def test_df_every_gate_kind(df, n):
+    qs = df
+    for seed in range(2):
+        gates = W.random_gate_suite(n, 500 * n + seed)
+        psi0 = W.random_state(n, seed + 3)
+        for g in gates:
+            ref = psi0.copy()
+            oracle.apply_gate(ref, n, g)
+            st = qs.State(n, qs.QS_C128)
+            st.load(psi0)
+            st.run(W.Circuit(n, [g]), 0)
+            assert maxabs(st.get_vector(), ref) < 1e-12, (g.name, g.targets)
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 4, 5, 6])
+def test_df_circuits(df, k):
+    qs = df
+    for n, c in [(12, W.u3cz_circuit(12, 10, 2021)), (15, W.Circuit(15, W.random_gate_suite(15, 8))),
+                 (17, W.rzrxrz_cnot_circuit(17, 4, 2))]:
+        ref = oracle.run_circuit(c)
+        st = qs.State(n, qs.QS_C128)
+        st.run(c, k)
+        got = st.get_vector()
+        assert maxabs(got, ref) < 1e-12
+        # the buffer is IEEE complex128 again after the run
+        assert abs(st.norm2() - oracle.norm2(ref, n)) < 1e-12
+
+
+def test_df_deep_circuit_error_growth(df):
+    """890-gate depth-20 family at n = 20: error after the whole circuit within the bound."""
+    qs = df
+    c = W.u3cz_circuit(20, 20, 11)
+    ref = oracle.run_circuit(c)
+    for k in (0, 2, 3):
+        st = qs.State(20, qs.QS_C128)
+        st.run(c, k)
+        err = maxabs(st.get_vector(), ref)
+        assert err < 1e-12, (k, err)
+
+
+def test_df_non_unitary_and_small_values(df):
+    """K need not be unitary: scaled matrices and tiny amplitudes keep their relative accuracy."""
+    qs = df
+    n = 8
+    rng = W.SplitMix64(4)
+    psi0 = W.random_state(n, 2) * 1e-3
+    gates = [W.Gate("DENSE", (1, 6), matrix=W.random_complex_matrix(4, rng) * 3.0),
+             W.Gate("DENSE", (0,), matrix=W.random_complex_matrix(2, rng) * 1e-4),
+             W.Gate("DENSE", (7, 2, 4), matrix=W.random_complex_matrix(8, rng))]
+    c = W.Circuit(n, gates)
+    ref = oracle.run_circuit(c, psi0)
+    st = qs.State(n, qs.QS_C128)
+    st.load(psi0)
+    st.run(c, 0)
+    got = st.get_vector()
+    scale = np.max(np.abs(ref))
+    assert maxabs(got, ref) < 1e-13 * max(scale, 1.0) * 8
+
+
+def test_df_adjoint(df):
+    qs = df
+    c = W.hea_circuit(7, 3, 5)
+    obs = W.tfim_observable(7, 1.0)
+    e, g = qs.adjoint_grad(c, obs)
+    assert abs(e - oracle.energy(c, obs)) < 1e-12
+    ps = oracle.grad_parameter_shift(c, obs, range(c.n_params))
+    assert np.max(np.abs(g - ps)) < 1e-11
+
+
+def test_df_full_size_sampled(df):
+    import torch
+    from test_gpu_parity import product_then_cz, sampled_amplitudes
+    qs = df
+    n = 30
+    circ, u3, cz = product_then_cz(n, 20, 777)
+    st = qs.State(n, qs.QS_C128)
+    st.run(circ, 2)
+    st.synchronize()
+    rng = W.SplitMix64(6)
+    xs = [rng.next_u64() & ((1 << n) - 1) for _ in range(2000)] + [0, (1 << n) - 1]
+    ref = sampled_amplitudes(n, u3, cz, xs)
+    idx = torch.tensor(xs, dtype=torch.int64, device="cuda")
+    got = st.tensor[idx].cpu().numpy()
+    assert maxabs(got, ref) < 1e-12
+    assert abs(st.norm2() - 1.0) < 1e-11
+    st.close()
+    del st
+    torch.cuda.empty_cache()
