@@ -218,6 +218,23 @@ qs_status qs_autotune_fusion(const qs_circuit* c, qs_dtype dt, int* best_k, doub
 /* out[0] = Re sum_k coef[k] <psi|P_k|psi>, out[1] = its imaginary part (zero up to rounding for
  * real coefficients). Accumulates in FP64 for both dtypes; synchronises. */
 qs_status qs_expectation(const qs_state* s, const qs_pauli_obs* obs, double out[2]);
+/* Allocation-free expectation, for callers that cannot allocate device memory: code that runs
+ * while a stream is being captured into a CUDA graph (cudaMalloc is not allowed there), hosts
+ * whose every device byte belongs to another allocator or a fixed budget, and loops that must not
+ * touch the allocator at all. Same value as qs_expectation (within FP64 rounding of the block
+ * count), computed from caller-owned memory: dev_psi holds 2^n amplitudes of type dt in the IEEE
+ * layout (16-byte aligned), out (host) receives (re, im). The paper has no counterpart; it exists
+ * for these callers only.
+ * It calls no cudaMalloc, cudaFree or other allocating routine. Its per-block partial sums live
+ * in one fixed 512 KiB array in device memory that every GPU loading the library keeps until the
+ * process exits. The first call on a device looks up that array's address (once per device, with
+ * the device current); make that first call before any stream capture. Every call shares the
+ * array and each block overwrites its own slots, so nothing needs clearing, but calls that overlap
+ * on the GPU (other streams, other threads) race on it: serialise them. An observable that would
+ * need more than 2047 kernel launches (groups of up to 48 terms with a common X/Y pattern) is
+ * rejected with QS_ERR_INVALID_ARG before any launch. Runs on `stream`; synchronises. */
+qs_status qs_expectation_noalloc(const void* dev_psi, int n, qs_dtype dt, void* stream, const qs_pauli_obs* obs,
+                                 double out[2]);
 /* out = <a|b> (Sec. 4.2.2 inner_product) as (re, im); same n and dtype; synchronises. */
 qs_status qs_inner_product(const qs_state* a, const qs_state* b, double out[2]);
 /* out = <psi|psi> (Sec. 4.2.2 get_squared_norm); synchronises. */

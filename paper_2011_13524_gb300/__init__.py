@@ -112,6 +112,8 @@ _SIGNATURES = {
     "qs_autotune_fusion": ([ctypes.POINTER(QsCircuit), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _DP],
                            ctypes.c_int),
     "qs_expectation": ([_VOIDP, ctypes.POINTER(QsPauliObs), _DP], ctypes.c_int),
+    "qs_expectation_noalloc": ([_VOIDP, ctypes.c_int, ctypes.c_int, _VOIDP, ctypes.POINTER(QsPauliObs), _DP],
+                               ctypes.c_int),
     "qs_inner_product": ([_VOIDP, _VOIDP, _DP], ctypes.c_int),
     "qs_norm2": ([_VOIDP, _DP], ctypes.c_int),
     "qs_adjoint_grad": ([ctypes.POINTER(QsCircuit), _DP, ctypes.POINTER(QsPauliObs), ctypes.c_int, _VOIDP,

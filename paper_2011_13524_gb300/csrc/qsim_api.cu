@@ -684,6 +684,13 @@ qs_status qs_expectation(const qs_state* s, const qs_pauli_obs* obs, double out[
     API_END
 }
 
+qs_status qs_expectation_noalloc(const void* dev_psi, int n, qs_dtype dt, void* stream, const qs_pauli_obs* obs,
+                                 double out[2]) {
+    API_BEGIN
+    expectation_noalloc(dev_psi, n, dt, static_cast<cudaStream_t>(stream), obs, out);
+    API_END
+}
+
 qs_status qs_inner_product(const qs_state* a, const qs_state* b, double out[2]) {
     API_BEGIN
     check_state(a);

@@ -141,6 +141,12 @@ void reduce_expectation(qs_state* s, const qs_pauli_obs* obs, double out[2]);
 void reduce_pauli_transition(qs_state* lam, const qs_state* psi, uint64_t xmask, uint64_t zmask,
                              double out[2]);
 
+// Same value as reduce_expectation for a caller-owned device buffer (IEEE layout), with the
+// per-block partials in a fixed device array instead of allocated scratch; synchronises.
+void expectation_noalloc(const void* psi, int n, qs_dtype dt, cudaStream_t st, const qs_pauli_obs* obs,
+                         double out[2]);
+size_t noalloc_scratch_doubles();
+
 // Observable grouped by flip mask for one pass per group.
 struct PauliGroup {
     uint64_t xmask;

@@ -13,6 +13,7 @@
 //   <psi|P|psi> restricted to the pair = i^{#Y} (s(y) A + s(y^f) conj(A)).
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <type_traits>
 
 #include "qsim_arith.cuh"
@@ -355,6 +356,116 @@ void launch_apply_observable(const std::vector<PauliGroup>& groups, const void* 
     });
     QS_TRY_CUDA(cudaGetLastError());
     QS_TRY_CUDA(cudaFreeAsync(d_terms, st));
+}
+
+}  // namespace qs
+
+// ---------------------------------------------------------------- allocation-free variant
+// Scratch for qs_expectation_noalloc: the per-block partial sums live in this fixed array
+// instead of memory the library allocates. Every GPU that loads the library holds it (512 KiB)
+// until the process exits. Host code may not use the symbol as a pointer; the device address
+// is looked up once per device with cudaGetSymbolAddress.
+namespace qs {
+
+constexpr size_t kNoAllocScratchDoubles = size_t(1) << 16;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// device address of the scratch array on the current device (set up on first use there)
+double* noalloc_scratch() {
+    int dev = 0;
+    QS_TRY_CUDA(cudaGetDevice(&dev));
+    QS_REQUIRE(dev >= 0 && dev < kMaxDevices, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        QS_TRY_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    return g_noalloc_ptr[dev];
+}
+}  // namespace
+
+size_t noalloc_scratch_doubles() { return kNoAllocScratchDoubles; }
+
+void expectation_noalloc(const void* psi, int n, qs_dtype dt, cudaStream_t st, const qs_pauli_obs* obs,
+                         double out[2]) {
+    QS_REQUIRE(psi != nullptr, "null state pointer");
+    QS_REQUIRE((reinterpret_cast<uintptr_t>(psi) & 15) == 0, "state pointer must be 16-byte aligned");
+    QS_REQUIRE(n >= 1 && n <= QS_MAX_QUBITS, "qubit count out of range (1..34)");
+    QS_REQUIRE(dt == QS_C64 || dt == QS_C128, "unknown dtype");
+    QS_REQUIRE(obs != nullptr && out != nullptr, "null observable or output");
+    QS_REQUIRE(obs->n_terms >= 0, "negative term count");
+    QS_REQUIRE(obs->n_terms == 0 || (obs->coef && obs->x_mask && obs->z_mask), "null observable arrays");
+    const uint64_t lim = (1ull << n) - 1;
+    // launches: one per (distinct flip mask, chunk of kMaxTermsPerLaunch terms), counted first
+    int launches = 0;
+    for (int t = 0; t < obs->n_terms; t++) {
+        QS_REQUIRE((obs->x_mask[t] & ~lim) == 0 && (obs->z_mask[t] & ~lim) == 0, "Pauli term acts on a qubit >= n");
+        bool first = true;
+        for (int u = 0; u < t && first; u++) first = obs->x_mask[u] != obs->x_mask[t];
+        if (!first) continue;
+        int cnt = 0;
+        for (int u = t; u < obs->n_terms; u++) cnt += obs->x_mask[u] == obs->x_mask[t];
+        launches += (cnt + kMaxTermsPerLaunch - 1) / kMaxTermsPerLaunch;
+    }
+    if (launches == 0) {
+        out[0] = out[1] = 0.0;
+        return;
+    }
+    // 2 doubles per block and launch, plus the 2 final values at the end of the array
+    const size_t max_slots = (kNoAllocScratchDoubles - 2) / 2;
+    QS_REQUIRE(size_t(launches) <= max_slots / 16,
+               "observable needs more kernel launches than the allocation-free scratch holds "
+               "(at most 2047 groups of up to 48 terms with a common X/Y pattern)");
+    const unsigned cap = unsigned(max_slots / size_t(launches));
+    double* scratch = noalloc_scratch();
+    double* d_out = scratch + kNoAllocScratchDoubles - 2;
+    int slots = 0;
+    for (int t = 0; t < obs->n_terms; t++) {
+        bool first = true;
+        for (int u = 0; u < t && first; u++) first = obs->x_mask[u] != obs->x_mask[t];
+        if (!first) continue;
+        const uint64_t f = obs->x_mask[t];
+        int u = t;
+        while (u < obs->n_terms) {
+            TermParams P;
+            P.xmask = f;
+            P.ip = IndexPlan();
+            if (f) {
+                P.ip.nfix = 1;
+                P.ip.fixpos[0] = __builtin_ctzll(f);
+                P.ip.n_iter = 1ull << (n - 1);
+            } else {
+                P.ip.n_iter = 1ull << n;
+            }
+            P.nterms = 0;
+            for (; u < obs->n_terms && P.nterms < kMaxTermsPerLaunch; u++) {
+                if (obs->x_mask[u] != f) continue;
+                P.coef[P.nterms] = obs->coef[u];
+                P.zmask[P.nterms] = obs->z_mask[u];
+                P.nY[P.nterms] = __builtin_popcountll(f & obs->z_mask[u]);
+                P.nterms++;
+            }
+            if (P.nterms == 0) break;
+            const unsigned g = std::min(red_grid(P.ip.n_iter), cap);
+            double* part = scratch + 2 * size_t(slots);
+            if (dt == QS_C64)
+                k_expect_group<<<g, kRedThreads, 0, st>>>(reinterpret_cast<const float2*>(psi), P, part);
+            else
+                k_expect_group<<<g, kRedThreads, 0, st>>>(reinterpret_cast<const double2*>(psi), P, part);
+            QS_TRY_CUDA(cudaGetLastError());
+            slots += int(g);
+        }
+    }
+    k_final2<<<1, kRedThreads, 0, st>>>(scratch, slots, d_out);
+    QS_TRY_CUDA(cudaGetLastError());
+    QS_TRY_CUDA(cudaMemcpyAsync(out, d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    QS_TRY_CUDA(cudaStreamSynchronize(st));
 }
 
 }  // namespace qs
