@@ -366,6 +366,21 @@ def measure_extras(args, qs, torch, circuit):
     e, g = qs.adjoint_grad(hea, H)
     out["adjoint_ms_n20_l20_c128"] = 1e3 * (time.perf_counter() - t0)
     out["adjoint_params"] = int(hea.n_params)
+    # batch: 4096 HEA circuits, n ~ U{8..20}, 2..12 layers, 4-term Pauli observables, complex64,
+    # energies + adjoint gradients, one persistent launch replayed from a CUDA graph
+    items = W.batch_workload(4096, args.seed)
+    b = qs.Batch([i.circuit for i in items], [i.observable for i in items])
+    theta = np.concatenate([i.circuit.parameters() for i in items])
+    b.run(theta, use_graph=True)
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        b.run(theta, use_graph=True)
+    dt = (time.perf_counter() - t0) / reps
+    out["batch_circuits_per_s"] = 4096 / dt
+    out["batch_ms"] = 1e3 * dt
+    out["batch_params"] = b.total_params
+    out["batch_workspace_gib"] = b.workspace_bytes / 2**30
     return out
 
 

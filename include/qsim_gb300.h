@@ -252,6 +252,29 @@ qs_status qs_norm2(const qs_state* s, double* out);
 qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pauli_obs* H,
                           qs_dtype dt, void* stream, double* energy, double* grad);
 
+/* ---------------------------------------------------------------- batched circuits */
+/* Many independent small (circuit, observable) pairs evaluated together: energies and adjoint
+ * gradients of parametric circuits, the paper's variational usage (Sec. 3.1, Sec. 4.4) at the
+ * scale of thousands of circuits. complex64 states (QS_C64), 1..24 qubits each; gates RX, RY,
+ * RZ (parametric or fixed, uncontrolled), CZ, CNOT (one control, value 1), H, X, Y, Z.
+ * qs_batch_create validates and compiles the circuits once (per-circuit passes over 13-qubit
+ * windows, device copies, a workspace of two 2^max_n complex64 buffers per SM when max_n > 13);
+ * counts: circuits[k] and observables[k] for k < count. */
+typedef struct qs_batch qs_batch; /* opaque */
+qs_status qs_batch_create(const qs_circuit* circuits, const qs_pauli_obs* observables, int count, qs_dtype dt,
+                          qs_batch** out);
+/* Evaluates the whole batch in one persistent kernel launch on `stream`. theta: host, the
+ * parameters of every circuit concatenated in order (circuit k contributes circuits[k].n_params
+ * values; NULL only if no circuit has parameters). use_graph != 0 records the launch sequence
+ * (parameter upload, angle kernel, the persistent kernel, result download) into a CUDA graph on
+ * the first call and replays it afterwards. energies: host, count values; grads: host, the
+ * gradients concatenated like theta. Synchronises. */
+qs_status qs_batch_run(qs_batch* b, const double* theta, void* stream, int use_graph, double* energies,
+                       double* grads);
+/* Total parameters, total passes of the compiled batch and device workspace bytes (any may be NULL). */
+qs_status qs_batch_info(const qs_batch* b, int* total_params, int* total_passes, size_t* workspace_bytes);
+qs_status qs_batch_destroy(qs_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -115,6 +115,11 @@ _SIGNATURES = {
     "qs_expectation_noalloc": ([_VOIDP, ctypes.c_int, ctypes.c_int, _VOIDP, ctypes.POINTER(QsPauliObs), _DP],
                                ctypes.c_int),
     "qs_inner_product": ([_VOIDP, _VOIDP, _DP], ctypes.c_int),
+    "qs_batch_create": ([_VOIDP, _VOIDP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_VOIDP)], ctypes.c_int),
+    "qs_batch_run": ([_VOIDP, _DP, _VOIDP, ctypes.c_int, _DP, _DP], ctypes.c_int),
+    "qs_batch_info": ([_VOIDP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                       ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "qs_batch_destroy": ([_VOIDP], ctypes.c_int),
     "qs_norm2": ([_VOIDP, _DP], ctypes.c_int),
     "qs_adjoint_grad": ([ctypes.POINTER(QsCircuit), _DP, ctypes.POINTER(QsPauliObs), ctypes.c_int, _VOIDP,
                          _DP, _DP], ctypes.c_int),
@@ -399,6 +404,53 @@ def autotune_fusion(circuit, dtype: int = QS_C128):
     pred = (ctypes.c_double * 7)()
     check(lib().qs_autotune_fusion(ctypes.byref(c), int(dtype), ctypes.byref(k), pred))
     return k.value, list(pred)
+
+
+class Batch:
+    """Many (circuit, observable) pairs evaluated in one persistent launch (qs_batch_*)."""
+
+    def __init__(self, circuits, observables, dtype: int = QS_C64):
+        assert len(circuits) == len(observables) and len(circuits) > 0
+        self.count = len(circuits)
+        keep = []
+        carr = (QsCircuit * self.count)()
+        oarr = (QsPauliObs * self.count)()
+        for i, (c, o) in enumerate(zip(circuits, observables)):
+            cc, k1 = make_circuit(c)
+            oo, k2 = make_obs(o)
+            carr[i] = cc
+            oarr[i] = oo
+            keep += [k1, k2]
+        self.n_params = [int(c.n_params) for c in circuits]
+        h = ctypes.c_void_p()
+        check(lib().qs_batch_create(ctypes.cast(carr, _VOIDP), ctypes.cast(oarr, _VOIDP), self.count, int(dtype),
+                                    ctypes.byref(h)))
+        self.handle = h
+        tp, npass, ws = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_size_t(0)
+        check(lib().qs_batch_info(h, ctypes.byref(tp), ctypes.byref(npass), ctypes.byref(ws)))
+        self.total_params, self.total_passes, self.workspace_bytes = tp.value, npass.value, ws.value
+
+    def run(self, theta=None, use_graph: bool = True, stream=None):
+        """(energies, list of per-circuit gradient arrays)."""
+        e = np.zeros(self.count)
+        g = np.zeros(max(1, self.total_params))
+        th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float64)
+        assert th is None or th.size == self.total_params
+        check(lib().qs_batch_run(self.handle, None if th is None else th.ctypes.data_as(_DP), _stream_ptr(stream),
+                                 int(use_graph), e.ctypes.data_as(_DP), g.ctypes.data_as(_DP)))
+        out, off = [], 0
+        for p in self.n_params:
+            out.append(g[off:off + p].copy())
+            off += p
+        return e, out
+
+    def __del__(self):
+        try:
+            if self.handle is not None and self.handle.value:
+                lib().qs_batch_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
 
 
 def adjoint_grad(circuit, obs, theta: Optional[Sequence[float]] = None, dtype: int = QS_C128,

@@ -85,13 +85,13 @@ struct DFAcc {
 __device__ __forceinline__ void df_zero(DFAcc& a) { a.hi = 0.f; a.lo = 0.f; }
 // acc += a * b without rounding the product; the sum error goes to acc.lo
 __device__ __forceinline__ void df_add_prod(DFAcc& acc, float a, float b) {
-    const float p = a * b;
-    const float pe = fmaf(a, b, -p);
-    const float s = acc.hi + p;
-    const float bb = s - acc.hi;
-    const float e = (acc.hi - (s - bb)) + (p - bb);
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(acc.hi, p);
+    const float bb = __fsub_rn(s, acc.hi);
+    const float e = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
     acc.hi = s;
-    acc.lo += e + pe;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, pe));
 }
 __device__ __forceinline__ double df_value(const DFAcc& a) { return double(a.hi) + double(a.lo); }
 
