@@ -63,7 +63,7 @@ typedef int qs_dtype;
 #define QS_GATE_PAULI 2 /* pauli[j] in {0,1,2,3} = {I,X,Y,Z} on targets[j] */
 #define QS_GATE_NAMED 3 /* named gate of the paper's gate table, see QS_NAMED_* */
 
-/* Named gates (Sec. 4.3.3 gate table). Rotations are exp(+i theta P / 2) (the table's sign);
+/* Named gates (Sec. 4.3.4 gate table). Rotations are exp(+i theta P / 2) (the table's sign);
  * U1/U2/U3 follow OpenQASM 2; S = diag(1,i), T = diag(1,e^{i pi/4}), sqrtX/sqrtY are the
  * principal square roots of X/Y. Qubits: 1-qubit gates use targets[0]; CNOT and TOFFOLI are X
  * on targets[0] with their controls in controls[]; CZ acts on targets[0..1]; SWAP on

@@ -8,7 +8,7 @@ State convention (Sec. 4.2.1, the initialisation listing): amplitude index x has
 qubit i in bit i ("the right-most digit is the 0-th qubit"); the state is a
 complex128 numpy array of length 2**n.
 
-Gate matrices of the named gates follow the paper's gate table (Sec. 4.3.3) with
+Gate matrices of the named gates follow the paper's gate table (Sec. 4.3.4) with
 these readings where the table is terse:
   * RX, RY, RZ(theta) = exp(+i theta P / 2) (the table's sign), PAULIROT the same on a
     Pauli string;

@@ -1,6 +1,6 @@
 // Gate descriptors -> gate matrices and kernel forms (host C++).
 //
-// Named gates follow the paper's gate table (Sec. 4.3.3): Pauli matrices as printed in
+// Named gates follow the paper's gate table (Sec. 4.3.4): Pauli matrices as printed in
 // Sec. 4.3.2; rotations RX/RY/RZ = exp(+i theta P / 2), the table's sign; U1/U2/U3 from
 // OpenQASM 2, to which the table defers; S = diag(1, i), T = diag(1, e^{i pi/4}) and the
 // principal square roots of X and Y for the table's "pi/4 rotations". Each gate is then

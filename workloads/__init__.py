@@ -7,7 +7,7 @@ the CUDA path turn a ``Gate`` record into their own gate matrix.
 Random numbers: SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom
 number generators", OOPSLA 2014), uniform doubles as (x >> 11) * 2**-53.
 
-Workload shapes follow the paper's benchmark circuits (Sec. 6.4, random
+Workload shapes follow the paper's benchmark circuits (Sec. 6.6, random
 rotation layers + CZ brickwork) and the variational usage it describes (Sec. 3.1,
 Sec. 4.4 parametric circuits), with the sizes of the configured workloads:
 
