@@ -121,6 +121,26 @@ def dist():
     return ws, rank, local
 
 
+def replica_circuit(args, rank):
+    """Each rank simulates its own replica of the workload (its own seed): no data is shared."""
+    return W.u3cz_circuit(args.n, args.depth, args.seed + rank)
+
+
+def max_over_ranks(ms, pg, device):
+    """The slowest rank's time (timing only; the one collective of the multi-GPU run)."""
+    if pg is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, gates, steps, max_ms):
+    """Gates of all replicas per second of the slowest rank."""
+    return world * gates * steps / (max_ms / 1e3)
+
+
 def zz_obs(n):
     return W.PauliObservable(n, np.array([1.0]), np.array([0], dtype=np.uint64), np.array([3], dtype=np.uint64))
 
@@ -191,7 +211,7 @@ def run_ours(args):
     math_mode = {"fp64": qs.QS_MATH_FP64, "df": qs.QS_MATH_DF, "auto": qs.QS_MATH_DF}[args.math]
     qs.set_c128_math(math_mode)
     n, dtype = args.n, qs.QS_C128
-    circuit = W.u3cz_circuit(n, args.depth, args.seed + rank)
+    circuit = replica_circuit(args, rank)
     G = len(circuit.gates)
     zz = zz_obs(n)
     stream = torch.cuda.current_stream()
@@ -240,13 +260,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms, pg, "cuda")
     if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
         pg.barrier()
     ms_per_step = ms / args.steps
-    value = ws * G * args.steps / (ms / 1e3)
+    value = whole_job_rate(ws, G, args.steps, ms)
 
     # roofline of the dominant kernel, from the per-block events of the timed steps
     peak, peak_kind = measured_peaks()
@@ -381,6 +399,35 @@ def measure_extras(args, qs, torch, circuit):
     out["batch_ms"] = 1e3 * dt
     out["batch_params"] = b.total_params
     out["batch_workspace_gib"] = b.workspace_bytes / 2**30
+    del b
+    # precision: the same circuit as complex64 and complex128 (double-float) on the GPU, n = 30;
+    # max-abs amplitude difference, 1 - fidelity and the transverse-field Ising energy (h = 1)
+    a = qs.State(n, qs.QS_C128)
+    a.run(circuit, 2)
+    c = qs.State(n, qs.QS_C64)
+    c.run(circuit, 4)
+    tf = W.tfim_observable(n, 1.0)
+    e128 = a.expectation(tf)[0]
+    e64 = c.expectation(tf)[0]
+    d = (a.tensor - c.tensor.to(torch.complex128)).abs().max().item()
+    ov = torch.vdot(a.tensor, c.tensor.to(torch.complex128)).abs().item() ** 2
+    out["precision_n30"] = {"max_abs_c64_vs_c128": d, "one_minus_fidelity": 1.0 - ov / (a.norm2() * c.norm2()),
+                            "tfim_energy_c128": e128, "tfim_energy_err_c64": abs(e64 - e128),
+                            "norm2_c64": c.norm2(), "norm2_c128": a.norm2()}
+    del a, c
+    torch.cuda.empty_cache()
+    # n = 33 complex128 (128 GiB state), same circuit family at depth 20, fused k = 2
+    try:
+        c33 = W.u3cz_circuit(33, args.depth, args.seed)
+        s33 = qs.State(33, qs.QS_C128)
+        plan33 = qs.FusedCircuit(c33, 2)
+        ms33 = timed(lambda: (s33.set_basis(0), s33.apply_plan(plan33)))
+        out["c128_n33_gates_per_s"] = len(c33.gates) / (ms33 / 1e3)
+        out["c128_n33_ms"] = ms33
+        del s33
+    except Exception as e:  # not enough free device memory on this GPU
+        out["c128_n33_error"] = str(e)[:200]
+    torch.cuda.empty_cache()
     return out
 
 

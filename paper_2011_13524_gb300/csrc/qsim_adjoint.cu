@@ -1,0 +1,162 @@
+// Fused reverse step of the adjoint gradient for a single-qubit rotation
+// R_P(theta) = exp(+i theta P / 2), P in {X, Y, Z} (the paper's gate table sign).
+//
+// At gate j of the reverse sweep psi holds psi_j (the state after the gate) and lambda holds
+// lambda_j = U_{j+1}^+ ... U_G^+ H psi_G. Then dE/dtheta_j = -Im <lambda_j|P|psi_j>; afterwards
+// both buffers are multiplied by R_P(theta)^+. One pass over the qubit's amplitude pairs does
+// both: each pair contributes conj(lambda) * (P psi) to the block's partial sum, then the 2x2
+// adjoint is applied to the pair in psi and in lambda. Per-block partials land in their own
+// slots (deterministic); one final kernel reduces every gate's slots.
+#include <algorithm>
+
+#include "qsim_arith.cuh"
+
+namespace qs {
+
+namespace {
+
+constexpr int kAdjThreads = 256;
+
+// accumulators of conj(l) * p for each arithmetic policy, FP64-class in all three
+template <typename P>
+struct GradAcc;
+
+template <>
+struct GradAcc<NativeArith<double>> {
+    double re = 0.0, im = 0.0;
+    __device__ void add(double2 l, double2 p) {
+        re = fma(l.x, p.x, re);
+        re = fma(l.y, p.y, re);
+        im = fma(l.x, p.y, im);
+        im = fma(-l.y, p.x, im);
+    }
+    __device__ double imag() const { return im; }
+};
+
+template <>
+struct GradAcc<NativeArith<float>> {
+    DFAcc im;
+    __device__ GradAcc() { df_zero(im); }
+    __device__ void add(float2 l, float2 p) {
+        df_add_prod(im, l.x, p.y);
+        df_add_prod(im, -l.y, p.x);
+    }
+    __device__ double imag() const { return df_value(im); }
+};
+
+template <>
+struct GradAcc<DFArith> {
+    float s = 0.f, c = 0.f;  // imaginary part only: lx py - ly px
+    __device__ void add(float4 l, float4 p) {
+        DFArith::dprod(s, c, l.x, l.y, p.z, p.w);
+        DFArith::dprod(s, c, -l.z, -l.w, p.x, p.y);
+    }
+    __device__ double imag() const { return double(s) + double(c); }
+};
+
+template <typename P>
+struct AdjRotParams {
+    IndexPlan ip;            // pivot bit = the rotation's qubit
+    uint64_t bit;            // 1 << qubit
+    typename P::K U[4];      // R^+ as a 2x2 matrix, row-major
+    int32_t axis;            // 1 = X, 2 = Y, 3 = Z
+};
+
+template <typename P>
+__global__ void __launch_bounds__(kAdjThreads) k_adj_rot(typename P::C* __restrict__ psi, typename P::C* __restrict__ lam,
+                                                          const __grid_constant__ AdjRotParams<P> A, double* part) {
+    using C = typename P::C;
+    GradAcc<P> g;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < A.ip.n_iter; i += stride) {
+        const uint64_t i0 = expand(i, A.ip), i1 = i0 | A.bit;
+        const C a = psi[i0], b = psi[i1], la = lam[i0], lb = lam[i1];
+        // (P psi) on the pair: X -> (b, a); Y -> (-i b, i a); Z -> (a, -b)
+        if (A.axis == 1) {
+            g.add(la, b);
+            g.add(lb, a);
+        } else if (A.axis == 2) {
+            g.add(la, P::ipow(b, 3));
+            g.add(lb, P::ipow(a, 1));
+        } else {
+            g.add(la, a);
+            g.add(lb, P::ipow(b, 2));
+        }
+        typename P::Acc r0 = P::zero(), r1 = P::zero(), s0 = P::zero(), s1 = P::zero();
+        P::mac(r0, A.U[0], a); P::mac(r0, A.U[1], b);
+        P::mac(r1, A.U[2], a); P::mac(r1, A.U[3], b);
+        P::mac(s0, A.U[0], la); P::mac(s0, A.U[1], lb);
+        P::mac(s1, A.U[2], la); P::mac(s1, A.U[3], lb);
+        psi[i0] = P::out(r0);
+        psi[i1] = P::out(r1);
+        lam[i0] = P::out(s0);
+        lam[i1] = P::out(s1);
+    }
+    __shared__ double sh[kAdjThreads / 32];
+    const double v = block_sum<kAdjThreads>(g.imag(), sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+// out[s] = sum of part[s * nb .. s * nb + nb) in a fixed order, one block per slot
+__global__ void __launch_bounds__(kAdjThreads) k_slot_sums(const double* __restrict__ part, int nb, double* out) {
+    __shared__ double sh[kAdjThreads / 32];
+    double v = 0.0;
+    for (int j = threadIdx.x; j < nb; j += kAdjThreads) v += part[size_t(blockIdx.x) * nb + j];
+    const double r = block_sum<kAdjThreads>(v, sh);
+    if (threadIdx.x == 0) out[blockIdx.x] = r;
+}
+
+int sm_count_adj() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+template <typename P>
+void launch_rot(void* psi, void* lam, int n, int qubit, int axis, double theta, double* part, unsigned grid,
+                cudaStream_t st) {
+    AdjRotParams<P> A;
+    A.ip = make_index_plan(n, {qubit}, 0);
+    A.bit = 1ull << qubit;
+    A.axis = axis;
+    // R^+ = cos(theta/2) I - i sin(theta/2) P
+    const double c = std::cos(theta / 2), s = std::sin(theta / 2);
+    cplx U[4];
+    if (axis == 1) { U[0] = c; U[1] = cplx(0, -s); U[2] = cplx(0, -s); U[3] = c; }
+    else if (axis == 2) { U[0] = c; U[1] = -s; U[2] = s; U[3] = c; }
+    else { U[0] = cplx(c, -s); U[1] = 0.0; U[2] = 0.0; U[3] = cplx(c, s); }
+    for (int e = 0; e < 4; e++) A.U[e] = P::host_k(U[e].real(), U[e].imag());
+    k_adj_rot<P><<<grid, kAdjThreads, 0, st>>>(reinterpret_cast<typename P::C*>(psi),
+                                               reinterpret_cast<typename P::C*>(lam), A, part);
+}
+
+}  // namespace
+
+unsigned adj_grid(int n) {
+    const uint64_t pairs = 1ull << (n - 1);
+    const uint64_t want = (pairs + kAdjThreads - 1) / kAdjThreads;
+    return unsigned(std::max<uint64_t>(1, std::min<uint64_t>(want, uint64_t(sm_count_adj()) * 8)));
+}
+
+void launch_adjoint_rotation(void* psi, void* lam, int n, Arith ar, int qubit, int axis, double theta, double* part,
+                             unsigned grid, cudaStream_t st) {
+    switch (ar) {
+        case Arith::F32: launch_rot<NativeArith<float>>(psi, lam, n, qubit, axis, theta, part, grid, st); break;
+        case Arith::F64: launch_rot<NativeArith<double>>(psi, lam, n, qubit, axis, theta, part, grid, st); break;
+        case Arith::DF: launch_rot<DFArith>(psi, lam, n, qubit, axis, theta, part, grid, st); break;
+    }
+    QS_TRY_CUDA(cudaGetLastError());
+}
+
+void launch_slot_sums(const double* part, int nslots, unsigned nb, double* out, cudaStream_t st) {
+    if (nslots <= 0) return;
+    k_slot_sums<<<nslots, kAdjThreads, 0, st>>>(part, int(nb), out);
+    QS_TRY_CUDA(cudaGetLastError());
+}
+
+}  // namespace qs

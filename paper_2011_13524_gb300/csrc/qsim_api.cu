@@ -761,30 +761,59 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
     reduce_inner(psi, lam, e2);
     *energy = e2[0];
     for (int p = 0; p < c->n_params; p++) grad[p] = 0.0;
-    // reverse sweep
-    for (int i = c->n_gates - 1; i >= 0; i--) {
-        const qs_gate& g = c->gates[i];
-        Op op = op_of_gate(g, c->n, theta);
-        if (g.param_index >= 0) {
-            uint64_t xm = 0, zm = 0;
-            auto add = [&](int id, int q) {
-                if (id == 1 || id == 2) xm |= 1ull << q;
-                if (id == 2 || id == 3) zm |= 1ull << q;
-            };
-            if (g.named == QS_NAMED_PAULIROT) {
-                for (int j = 0; j < g.m; j++) add(g.pauli[j], g.targets[j]);
-            } else {
-                add(g.named == QS_NAMED_RX ? 1 : g.named == QS_NAMED_RY ? 2 : 3, g.targets[0]);
+    // single-qubit rotations use the fused reverse step (gradient partials + un-apply in one
+    // pass, no host synchronisation); their partial sums are reduced once after the sweep
+    auto fused_rot = [&](const qs_gate& g) {
+        return g.param_index >= 0 && g.mc == 0 &&
+               (g.named == QS_NAMED_RX || g.named == QS_NAMED_RY || g.named == QS_NAMED_RZ);
+    };
+    int nslots = 0;
+    for (int i = 0; i < c->n_gates; i++) nslots += fused_rot(c->gates[i]) ? 1 : 0;
+    const unsigned nb = adj_grid(c->n);
+    double* d_part = nullptr;
+    if (nslots) QS_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_part), sizeof(double) * (size_t(nslots) * nb + nslots), st));
+    std::vector<int> slot_param;
+    try {
+        for (int i = c->n_gates - 1; i >= 0; i--) {
+            const qs_gate& g = c->gates[i];
+            if (fused_rot(g)) {
+                const int axis = g.named == QS_NAMED_RX ? 1 : g.named == QS_NAMED_RY ? 2 : 3;
+                const double th = theta ? theta[g.param_index] : g.params[0];
+                launch_adjoint_rotation(psi->data, lam->data, c->n, ar, g.targets[0], axis, th,
+                                        d_part + size_t(slot_param.size()) * nb, nb, st);
+                slot_param.push_back(g.param_index);
+                continue;
             }
-            double t[2];
-            reduce_pauli_transition(lam, psi, xm, zm, t);
-            // d/dtheta exp(i theta P/2) = (i/2) P U  ->  dE/dtheta = -Im <lambda|P|psi>
-            grad[g.param_index] += -t[1];
+            Op op = op_of_gate(g, c->n, theta);
+            if (g.param_index >= 0) {
+                uint64_t xm = 0, zm = 0;
+                for (int j = 0; j < g.m; j++) {
+                    const int id = g.pauli[j], q = g.targets[j];
+                    if (id == 1 || id == 2) xm |= 1ull << q;
+                    if (id == 2 || id == 3) zm |= 1ull << q;
+                }
+                double t[2];
+                reduce_pauli_transition(lam, psi, xm, zm, t);
+                // d/dtheta exp(i theta P/2) = (i/2) P U  ->  dE/dtheta = -Im <lambda|P|psi>
+                grad[g.param_index] += -t[1];
+            }
+            Op inv = dagger(op);
+            launch_op_arith(inv, psi->data, c->n, ar, st, stage_of(psi));
+            launch_op_arith(inv, lam->data, c->n, ar, st, stage_of(lam));
         }
-        Op inv = dagger(op);
-        launch_op_arith(inv, psi->data, c->n, ar, st, stage_of(psi));
-        launch_op_arith(inv, lam->data, c->n, ar, st, stage_of(lam));
+        if (nslots) {
+            double* d_sums = d_part + size_t(nslots) * nb;
+            launch_slot_sums(d_part, nslots, nb, d_sums, st);
+            std::vector<double> sums(nslots);
+            QS_TRY_CUDA(cudaMemcpyAsync(sums.data(), d_sums, sizeof(double) * nslots, cudaMemcpyDeviceToHost, st));
+            QS_TRY_CUDA(cudaStreamSynchronize(st));
+            for (int sidx = 0; sidx < nslots; sidx++) grad[slot_param[sidx]] += -sums[sidx];
+        }
+    } catch (...) {
+        if (d_part) cudaFreeAsync(d_part, st);
+        throw;
     }
+    if (d_part) QS_TRY_CUDA(cudaFreeAsync(d_part, st));
     QS_TRY_CUDA(cudaStreamSynchronize(st));
     API_END
 }

@@ -29,27 +29,41 @@ namespace qs {
 
 namespace {
 
-constexpr int kBT = 1024;        // threads per CTA
-constexpr int kLocal = 13;       // qubits per shared-memory chunk
-constexpr int kChunk = 1 << kLocal;
+constexpr int kBT = 512;               // threads per CTA: 16 warps
+constexpr int kWarps = kBT / 32;
+constexpr int kLocal = 13;             // qubits per chunk
+constexpr int kChunk = 1 << kLocal;    // 16 warps x 32 lanes x 16 registers
+constexpr int kRegBits = 4;
+constexpr int kRegs = 1 << kRegBits;
+constexpr int kMaxStageParams = 32;
+constexpr int kClasses = 5;            // groups of 16, 8, 4, 2, 1 warps
 constexpr int kMaxBatchQubits = 24;
 
 enum BKind : uint8_t { BK_RX = 0, BK_RY = 1, BK_RZ = 2, BK_CZ = 3, BK_CNOT = 4, BK_H = 5, BK_X = 6, BK_Y = 7, BK_Z = 8 };
 
+// one gate in the local coordinates of its pass
 struct BGate {
     uint8_t kind;
-    uint8_t a;      // local bit of the target (CNOT: target)
-    uint8_t b;      // local bit of the second qubit (CZ) or control (CNOT)
-    uint8_t pad;
-    int32_t slot;   // angle slot in the item's angle array (rotations), -1 otherwise
+    uint8_t a;      // local bit of the target
+    uint8_t b;      // local bit of the second qubit (CZ) or of the control (CNOT)
+    uint8_t ja;     // register bit holding the target (non-diagonal gates)
+    int32_t slot;   // angle slot (rotations), -1 otherwise
     int32_t grad;   // gradient index (parametric rotations), -1 otherwise
 };
 
+// gates whose non-diagonal actions stay inside the register sub-cube spanned by act[]
+struct BStage {
+    int32_t g0, g1;
+    int32_t nact;
+    int32_t nparam;
+    uint8_t act[4];
+};
+
 struct BPass {
-    int32_t g0, g1;               // gate range
+    int32_t s0, s1;               // stage range
     uint32_t tab_lo[128];         // local index bits 0..6 -> address bits
     uint32_t tab_hi[64];          // local index bits 7..12 -> address bits
-    uint32_t nonlocal;            // qubits outside the window (address bits fixed per chunk)
+    uint32_t nonlocal;            // qubits outside the window (fixed per chunk)
     int32_t nlocal;
 };
 
@@ -69,132 +83,39 @@ struct BItem {
 
 struct BatchDev {
     const BItem* items;
-    const int32_t* order;
+    const int32_t* order;         // items grouped by class, longest first within a class
     const BPass* passes;
+    const BStage* stages;
     const BGate* gates;
     const BTerm* terms;
     const float2* cs;             // (cos, sin) of theta/2 per angle slot
-    float2* ws;                   // per-CTA workspace: psi and lambda, 2^maxn each
-    uint64_t ws_stride;           // amplitudes per buffer
+    float2* ws;                   // per-CTA workspace: psi and lambda, 2^maxn each (chunked circuits)
+    uint64_t ws_stride;
     double* energy;
     double* grad;
-    int32_t count;
-    int32_t want_grad;
-    unsigned int* counter;
+    unsigned int* counters;       // one work counter per class
+    int32_t cls_begin[kClasses + 1];
 };
 
-__device__ __forceinline__ uint32_t insert0(uint32_t i, int b) {
-    const uint32_t lo = i & ((1u << b) - 1u);
-    return ((i ^ lo) << 1) | lo;
-}
-
-__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-
-// apply gate g (or its adjoint) to a chunk of `size` amplitudes in shared memory
-__device__ void apply_local(float2* s, int size, const BGate& g, float2 cs, bool adjoint) {
-    const float c = cs.x, sn = adjoint ? -cs.y : cs.y;
-    switch (g.kind) {
-        case BK_RX: case BK_RY: case BK_RZ: case BK_H: case BK_X: case BK_Y: {
-            const int half = size >> 1;
-            for (int i = threadIdx.x; i < half; i += kBT) {
-                const uint32_t i0 = insert0(i, g.a), i1 = i0 | (1u << g.a);
-                const float2 u = s[i0], v = s[i1];
-                float2 r0, r1;
-                if (g.kind == BK_RX) {         // [[c, i s], [i s, c]]
-                    r0 = make_float2(c * u.x - sn * v.y, c * u.y + sn * v.x);
-                    r1 = make_float2(c * v.x - sn * u.y, c * v.y + sn * u.x);
-                } else if (g.kind == BK_RY) {  // [[c, s], [-s, c]]
-                    r0 = make_float2(c * u.x + sn * v.x, c * u.y + sn * v.y);
-                    r1 = make_float2(c * v.x - sn * u.x, c * v.y - sn * u.y);
-                } else if (g.kind == BK_RZ) {  // diag(c + i s, c - i s)
-                    r0 = cmulf(make_float2(c, sn), u);
-                    r1 = cmulf(make_float2(c, -sn), v);
-                } else if (g.kind == BK_H) {
-                    const float h = 0.70710678118654752f;
-                    r0 = make_float2(h * (u.x + v.x), h * (u.y + v.y));
-                    r1 = make_float2(h * (u.x - v.x), h * (u.y - v.y));
-                } else if (g.kind == BK_X) {
-                    r0 = v; r1 = u;
-                } else {                       // Y = [[0, -i], [i, 0]]
-                    r0 = make_float2(v.y, -v.x);
-                    r1 = make_float2(-u.y, u.x);
-                }
-                s[i0] = r0;
-                s[i1] = r1;
-            }
-            break;
-        }
-        case BK_Z: {
-            for (int i = threadIdx.x; i < (size >> 1); i += kBT) {
-                const uint32_t x = insert0(i, g.a) | (1u << g.a);
-                s[x] = make_float2(-s[x].x, -s[x].y);
-            }
-            break;
-        }
-        case BK_CZ: {
-            const int lo = min(g.a, g.b), hi = max(g.a, g.b);
-            for (int i = threadIdx.x; i < (size >> 2); i += kBT) {
-                const uint32_t x = insert0(insert0(i, lo), hi) | (1u << g.a) | (1u << g.b);
-                s[x] = make_float2(-s[x].x, -s[x].y);
-            }
-            break;
-        }
-        case BK_CNOT: {  // control b, target a
-            const int lo = min(g.a, g.b), hi = max(g.a, g.b);
-            for (int i = threadIdx.x; i < (size >> 2); i += kBT) {
-                const uint32_t x = insert0(insert0(i, lo), hi) | (1u << g.b);
-                const uint32_t y = x | (1u << g.a);
-                const float2 u = s[x];
-                s[x] = s[y];
-                s[y] = u;
-            }
-            break;
-        }
+// group barrier: the CTA, a named barrier over the group's warps, or the warp
+__device__ __forceinline__ void gbar(int G, int w0) {
+    if (G == kWarps) {
+        __syncthreads();
+    } else if (G == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + w0), "r"(G * 32) : "memory");
     }
 }
 
-// this thread's share of <lam|P|psi> for the rotation axis of g on local bit a (exact products,
-// double-float sums)
-__device__ void grad_local(const float2* sp, const float2* sl, int size, const BGate& g, DFAcc& re, DFAcc& im) {
-    const int half = size >> 1;
-    for (int i = threadIdx.x; i < half; i += kBT) {
-        const uint32_t i0 = insert0(i, g.a), i1 = i0 | (1u << g.a);
-        const float2 a = sp[i0], b = sp[i1], la = sl[i0], lb = sl[i1];
-        // P psi on the pair: X -> (b, a); Y -> (-i b, i a); Z -> (a, -b)
-        float2 p0, p1;
-        if (g.kind == BK_RX) { p0 = b; p1 = a; }
-        else if (g.kind == BK_RY) { p0 = make_float2(b.y, -b.x); p1 = make_float2(-a.y, a.x); }
-        else { p0 = a; p1 = make_float2(-b.x, -b.y); }
-        // conj(l) * p = (lx px + ly py) + i (lx py - ly px)
-        df_add_prod(re, la.x, p0.x); df_add_prod(re, la.y, p0.y);
-        df_add_prod(im, la.x, p0.y); df_add_prod(im, -la.y, p0.x);
-        df_add_prod(re, lb.x, p1.x); df_add_prod(re, lb.y, p1.y);
-        df_add_prod(im, lb.x, p1.y); df_add_prod(im, -lb.y, p1.x);
-    }
-}
+// shared-memory position of local index l: the low four bits are XOR-folded with the higher
+// ones so that lanes spread over the banks whichever bits are in registers
+__device__ __forceinline__ uint32_t swz(uint32_t l) { return l ^ ((l >> 4) & 15u) ^ ((l >> 8) & 15u); }
 
-__device__ double block_sum_d(double v, double* red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x < 32) {
-        r = red[threadIdx.x];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
-    }
-    return r;  // thread 0
-}
-
-__device__ __forceinline__ uint32_t chunk_addr(const BPass& P, uint32_t base, int l) {
+__device__ __forceinline__ uint32_t chunk_addr(const BPass& P, uint32_t base, uint32_t l) {
     return base | P.tab_lo[l & 127] | P.tab_hi[l >> 7];
 }
 
-// address base of chunk c: deposit c into the non-local bits
 __device__ __forceinline__ uint32_t chunk_base(uint32_t nonlocal, uint32_t c) {
     uint32_t r = 0, m = nonlocal;
     while (m) {
@@ -206,115 +127,423 @@ __device__ __forceinline__ uint32_t chunk_base(uint32_t nonlocal, uint32_t c) {
     return r;
 }
 
+// chunk transfers between global memory and the shared-memory slice (chunked circuits run on
+// the whole CTA: 512 threads x 16 amplitudes); every load is issued before the first store
+__device__ __noinline__ void chunk_load(const BPass& P, uint32_t base, const float2* __restrict__ g, float2* s,
+                                           int tg) {
+    float2 t[kRegs];
+#pragma unroll
+    for (int j = 0; j < kRegs; j++) t[j] = g[chunk_addr(P, base, uint32_t(tg + j * kBT))];
+#pragma unroll
+    for (int j = 0; j < kRegs; j++) s[uint32_t(tg + j * kBT) ^ ((uint32_t(tg + j * kBT) >> 4) & 15u) ^
+                                      ((uint32_t(tg + j * kBT) >> 8) & 15u)] = t[j];
+}
+__device__ __noinline__ void chunk_store(const BPass& P, uint32_t base, float2* __restrict__ g, const float2* s,
+                                            int tg) {
+    float2 t[kRegs];
+#pragma unroll
+    for (int j = 0; j < kRegs; j++) {
+        const uint32_t l = uint32_t(tg + j * kBT);
+        t[j] = s[l ^ ((l >> 4) & 15u) ^ ((l >> 8) & 15u)];
+    }
+#pragma unroll
+    for (int j = 0; j < kRegs; j++) g[chunk_addr(P, base, uint32_t(tg + j * kBT))] = t[j];
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// 2x2 complex matrix of a non-diagonal single-qubit gate (or of its adjoint)
+struct M2 {
+    float2 m00, m01, m10, m11;
+};
+__device__ __forceinline__ M2 gate_m2(uint8_t kind, float c, float sn) {
+    M2 m;
+    switch (kind) {
+        case BK_RX:  // [[c, i s], [i s, c]]
+            m.m00 = make_float2(c, 0.f); m.m01 = make_float2(0.f, sn);
+            m.m10 = make_float2(0.f, sn); m.m11 = make_float2(c, 0.f);
+            break;
+        case BK_RY:  // [[c, s], [-s, c]]
+            m.m00 = make_float2(c, 0.f); m.m01 = make_float2(sn, 0.f);
+            m.m10 = make_float2(-sn, 0.f); m.m11 = make_float2(c, 0.f);
+            break;
+        case BK_H: {
+            const float h = 0.70710678118654752f;
+            m.m00 = make_float2(h, 0.f); m.m01 = make_float2(h, 0.f);
+            m.m10 = make_float2(h, 0.f); m.m11 = make_float2(-h, 0.f);
+            break;
+        }
+        case BK_X:
+            m.m00 = make_float2(0.f, 0.f); m.m01 = make_float2(1.f, 0.f);
+            m.m10 = make_float2(1.f, 0.f); m.m11 = make_float2(0.f, 0.f);
+            break;
+        default:  // Y = [[0, -i], [i, 0]]
+            m.m00 = make_float2(0.f, 0.f); m.m01 = make_float2(0.f, -1.f);
+            m.m10 = make_float2(0.f, 1.f); m.m11 = make_float2(0.f, 0.f);
+            break;
+    }
+    return m;
+}
+
+__device__ __forceinline__ float2 cfma2(float2 a, float2 b, float2 acc) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+    return acc;
+}
+
+// 2x2 update of the register pairs (r, r | 2^J)
+template <int J>
+__device__ __forceinline__ void pairs_1q(float2 (&v)[kRegs], int R, const M2& m) {
+#pragma unroll
+    for (int r = 0; r < kRegs; r++) {
+        if ((r >> J) & 1) continue;
+        if (r >= R) continue;
+        const int r1 = r | (1 << J);
+        const float2 u = v[r], w = v[r1];
+        v[r] = cfma2(m.m01, w, cfma2(m.m00, u, make_float2(0.f, 0.f)));
+        v[r1] = cfma2(m.m11, w, cfma2(m.m10, u, make_float2(0.f, 0.f)));
+    }
+}
+
+// local index of register r of this thread: the thread's base (its bits outside the register
+// sub-cube) plus the active bits selected by r
+struct LocalMap {
+    uint32_t base;
+    uint32_t am[kRegBits];
+    __device__ __forceinline__ uint32_t at(int r) const {
+        uint32_t o = base;
+#pragma unroll
+        for (int j = 0; j < kRegBits; j++)
+            if ((r >> j) & 1) o |= am[j];
+        return o;
+    }
+};
+
+template <int J>
+__device__ __forceinline__ void pairs_cnot(float2 (&v)[kRegs], const LocalMap& li, int R, int cb) {
+#pragma unroll
+    for (int r = 0; r < kRegs; r++) {
+        if ((r >> J) & 1) continue;
+        if (r >= R) continue;
+        const int r1 = r | (1 << J);
+        if ((li.at(r) >> cb) & 1) {
+            const float2 u = v[r];
+            v[r] = v[r1];
+            v[r1] = u;
+        }
+    }
+}
+
+// apply g (or its adjoint) to the registers
+__device__ __forceinline__ void apply_reg(float2 (&v)[kRegs], const LocalMap& li, int R, const BGate& g,
+                                          float2 cs, bool adjoint) {
+    const float c = cs.x, sn = adjoint ? -cs.y : cs.y;
+    switch (g.kind) {
+        case BK_RZ: {  // diag(c + i s, c - i s)
+#pragma unroll
+            for (int r = 0; r < kRegs; r++)
+                if (r < R) v[r] = cmulf(make_float2(c, ((li.at(r) >> g.a) & 1) ? -sn : sn), v[r]);
+            break;
+        }
+        case BK_Z: {
+#pragma unroll
+            for (int r = 0; r < kRegs; r++)
+                if (r < R && ((li.at(r) >> g.a) & 1)) v[r] = make_float2(-v[r].x, -v[r].y);
+            break;
+        }
+        case BK_CZ: {
+#pragma unroll
+            for (int r = 0; r < kRegs; r++)
+                if (r < R && ((li.at(r) >> g.a) & 1) && ((li.at(r) >> g.b) & 1)) v[r] = make_float2(-v[r].x, -v[r].y);
+            break;
+        }
+        case BK_CNOT:
+            switch (g.ja) {
+                case 0: pairs_cnot<0>(v, li, R, g.b); break;
+                case 1: pairs_cnot<1>(v, li, R, g.b); break;
+                case 2: pairs_cnot<2>(v, li, R, g.b); break;
+                default: pairs_cnot<3>(v, li, R, g.b); break;
+            }
+            break;
+        default: {
+            const M2 m = gate_m2(g.kind, c, sn);
+            switch (g.ja) {
+                case 0: pairs_1q<0>(v, R, m); break;
+                case 1: pairs_1q<1>(v, R, m); break;
+                case 2: pairs_1q<2>(v, R, m); break;
+                default: pairs_1q<3>(v, R, m); break;
+            }
+            break;
+        }
+    }
+}
+
+// Im sum conj(lam) (P psi) over this thread's registers, P the axis of rotation g
+template <int J>
+__device__ __forceinline__ void grad_pairs(const float2 (&p)[kRegs], const float2 (&l)[kRegs], int R, uint8_t kind,
+                                           DFAcc& im) {
+#pragma unroll
+    for (int r = 0; r < kRegs; r++) {
+        if ((r >> J) & 1) continue;
+        if (r >= R) continue;
+        const int r1 = r | (1 << J);
+        const float2 a = p[r], b = p[r1], la = l[r], lb = l[r1];
+        float2 p0, p1;  // X -> (b, a); Y -> (-i b, i a)
+        if (kind == BK_RX) { p0 = b; p1 = a; }
+        else { p0 = make_float2(b.y, -b.x); p1 = make_float2(-a.y, a.x); }
+        df_add_prod(im, la.x, p0.y);
+        df_add_prod(im, -la.y, p0.x);
+        df_add_prod(im, lb.x, p1.y);
+        df_add_prod(im, -lb.y, p1.x);
+    }
+}
+
+__device__ __forceinline__ double grad_reg(const float2 (&p)[kRegs], const float2 (&l)[kRegs], const LocalMap& li,
+                                           int R, const BGate& g) {
+    DFAcc im;
+    df_zero(im);
+    if (g.kind == BK_RZ) {  // Z: (a, -b) by the target bit
+#pragma unroll
+        for (int r = 0; r < kRegs; r++) {
+            if (r >= R) continue;
+            const float sg = ((li.at(r) >> g.a) & 1) ? -1.f : 1.f;
+            df_add_prod(im, l[r].x, sg * p[r].y);
+            df_add_prod(im, -l[r].y, sg * p[r].x);
+        }
+    } else {
+        switch (g.ja) {
+            case 0: grad_pairs<0>(p, l, R, g.kind, im); break;
+            case 1: grad_pairs<1>(p, l, R, g.kind, im); break;
+            case 2: grad_pairs<2>(p, l, R, g.kind, im); break;
+            default: grad_pairs<3>(p, l, R, g.kind, im); break;
+        }
+    }
+    return df_value(im);
+}
+
+// local-index map of thread tg in stage S of a window of nl local bits
+__device__ __forceinline__ LocalMap stage_map(const BStage& S, int nl, int tg) {
+    LocalMap m;
+    uint32_t actmask = 0;
+#pragma unroll
+    for (int j = 0; j < kRegBits; j++) {
+        m.am[j] = j < S.nact ? (1u << S.act[j]) : 0u;
+        actmask |= m.am[j];
+    }
+    uint32_t base = 0, t = uint32_t(tg);
+    for (int b = 0; b < nl; b++) {
+        if ((actmask >> b) & 1) continue;
+        if (t & 1u) base |= 1u << b;
+        t >>= 1;
+    }
+    m.base = base;
+    return m;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __global__ void __launch_bounds__(kBT, 1) k_batch(const BatchDev B) {
     extern __shared__ __align__(16) unsigned char smem[];
-    float2* sp = reinterpret_cast<float2*>(smem);
-    float2* sl = sp + kChunk;
-    __shared__ double red[32];
-    __shared__ int s_item;
+    float2* smem_p = reinterpret_cast<float2*>(smem);
+    float2* smem_l = smem_p + kChunk;
+    __shared__ double red[2][kMaxStageParams][kWarps];  // gradient partials per stage parity
+    __shared__ double redE[kWarps];
+    __shared__ int s_claim[kWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2* gpsi = B.ws + uint64_t(blockIdx.x) * 2 * B.ws_stride;
     float2* glam = gpsi + B.ws_stride;
-    while (true) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_item = int(atomicAdd(B.counter, 1u));
-        __syncthreads();
-        const int w = s_item;
-        if (w >= B.count) break;
-        const BItem it = B.items[B.order[w]];
-        const bool resident = it.n <= kLocal;
-        const int size = resident ? (1 << it.n) : kChunk;
-        const uint32_t N = 1u << it.n;
-        for (int j = threadIdx.x; j < it.ngrad; j += kBT) B.grad[it.grad0 + j] = 0.0;
-        // ---------------- forward sweep
-        for (int p = it.p0; p < it.p1; p++) {
-            const BPass& P = B.passes[p];
-            const uint32_t nch = resident ? 1u : (N >> kLocal);
-            for (uint32_t c = 0; c < nch; c++) {
-                const uint32_t base = resident ? 0u : chunk_base(P.nonlocal, c);
-                if (p == it.p0) {
-                    for (int l = threadIdx.x; l < size; l += kBT)
-                        sp[l] = make_float2((base == 0 && l == 0) ? 1.f : 0.f, 0.f);
-                } else if (!resident) {
-                    for (int l = threadIdx.x; l < size; l += kBT) sp[l] = gpsi[chunk_addr(P, base, l)];
+    int parity = 0;
+    for (int cls = 0; cls < kClasses; cls++) {
+        const int G = kWarps >> cls;
+        const int w0 = (warp / G) * G;
+        const int tg = threadIdx.x - w0 * 32;
+        const int nthr = G * 32;
+        float2* sp = smem_p + w0 * 32 * kRegs;
+        float2* sl = smem_l + w0 * 32 * kRegs;
+        const int count = B.cls_begin[cls + 1] - B.cls_begin[cls];
+        while (true) {
+            if (tg == 0) s_claim[w0] = int(atomicAdd(&B.counters[cls], 1u));
+            gbar(G, w0);
+            const int k = s_claim[w0];
+            gbar(G, w0);
+            if (k >= count) break;
+            const int item = B.order[B.cls_begin[cls] + k];
+            const BItem it = B.items[item];
+            const int nl = it.n < kLocal ? it.n : kLocal;
+            const bool resident = it.n <= kLocal;
+            const uint32_t size = 1u << nl;
+            const uint32_t N = 1u << it.n;
+            const int R = 1 << (nl < kRegBits ? nl : kRegBits);
+            const int T = int(size) / R;  // threads holding registers
+            const float2* cs = B.cs + it.angle0;
+            for (int j = tg; j < it.ngrad; j += nthr) B.grad[it.grad0 + j] = 0.0;
+            // ---------------- forward sweep
+            for (int p = it.p0; p < it.p1; p++) {
+                const BPass& P = B.passes[p];
+                const uint32_t nch = resident ? 1u : (N >> kLocal);
+                for (uint32_t c = 0; c < nch; c++) {
+                    const uint32_t base = resident ? 0u : chunk_base(P.nonlocal, c);
+                    if (p == it.p0) {
+                        for (uint32_t l = tg; l < size; l += nthr)
+                            sp[swz(l)] = make_float2((base == 0 && l == 0) ? 1.f : 0.f, 0.f);
+                    } else if (!resident) {
+                        chunk_load(P, base, gpsi, sp, tg);
+                    }
+                    gbar(G, w0);
+                    for (int s = P.s0; s < P.s1; s++) {
+                        const BStage S = B.stages[s];
+                        if (tg < T) {
+                            const LocalMap li = stage_map(S, nl, tg);
+                            float2 v[kRegs];
+#pragma unroll
+                            for (int r = 0; r < kRegs; r++)
+                                if (r < R) v[r] = sp[swz(li.at(r))];
+                            for (int gi = S.g0; gi < S.g1; gi++) {
+                                const BGate g = B.gates[gi];
+                                apply_reg(v, li, R, g, g.slot >= 0 ? cs[g.slot] : make_float2(1.f, 0.f), false);
+                            }
+#pragma unroll
+                            for (int r = 0; r < kRegs; r++)
+                                if (r < R) sp[swz(li.at(r))] = v[r];
+                        }
+                        gbar(G, w0);
+                    }
+                    if (!resident) {
+                        chunk_store(P, base, gpsi, sp, tg);
+                        gbar(G, w0);
+                    }
                 }
-                __syncthreads();
-                for (int gi = P.g0; gi < P.g1; gi++) {
-                    const BGate g = B.gates[gi];
-                    const float2 cs = g.slot >= 0 ? B.cs[it.angle0 + g.slot] : make_float2(1.f, 0.f);
-                    apply_local(sp, size, g, cs, false);
-                    __syncthreads();
-                }
-                if (!resident)
-                    for (int l = threadIdx.x; l < size; l += kBT) gpsi[chunk_addr(B.passes[p], base, l)] = sp[l];
-                __syncthreads();
             }
-        }
-        // ---------------- lambda = H psi, E = Re <psi|lambda>
-        {
-            DFAcc e;
-            df_zero(e);
-            const float2* src = resident ? sp : gpsi;
-            float2* dst = resident ? sl : glam;
-            for (uint32_t y = threadIdx.x; y < N; y += kBT) {
-                double re = 0.0, im = 0.0;
-                for (int t = it.t0; t < it.t1; t++) {
-                    const BTerm T = B.terms[t];
-                    const uint32_t y2 = y ^ T.xmask;
-                    float2 v = src[y2];
-                    v = mul_ipow(v, T.nY + 2 * (__popc(y2 & T.zmask) & 1));
-                    re = fma(T.coef, double(v.x), re);
-                    im = fma(T.coef, double(v.y), im);
+            // ---------------- lambda = H psi and E = Re <psi|lambda>
+            {
+                DFAcc e;
+                df_zero(e);
+                constexpr int U = 2;
+                for (uint32_t y0 = tg; y0 < N; y0 += U * nthr) {
+                    float2 src[U][4];
+                    float2 ps[U];
+                    const int nt = it.t1 - it.t0;
+#pragma unroll
+                    for (int k = 0; k < U; k++) {
+                        const uint32_t y = y0 + k * nthr;
+                        if (y >= N) continue;
+                        ps[k] = resident ? sp[swz(y)] : gpsi[y];
+#pragma unroll
+                        for (int t = 0; t < 4; t++)
+                            if (t < nt) {
+                                const uint32_t y2 = y ^ B.terms[it.t0 + t].xmask;
+                                src[k][t] = resident ? sp[swz(y2)] : gpsi[y2];
+                            }
+                    }
+#pragma unroll
+                    for (int k = 0; k < U; k++) {
+                        const uint32_t y = y0 + k * nthr;
+                        if (y >= N) continue;
+                        double re = 0.0, im = 0.0;
+                        for (int t = it.t0; t < it.t1; t++) {
+                            const BTerm Tm = B.terms[t];
+                            const uint32_t y2 = y ^ Tm.xmask;
+                            float2 v = (t - it.t0 < 4) ? src[k][min(t - it.t0, 3)] : (resident ? sp[swz(y2)] : gpsi[y2]);
+                            v = mul_ipow(v, Tm.nY + 2 * (__popc(y2 & Tm.zmask) & 1));
+                            re = fma(Tm.coef, double(v.x), re);
+                            im = fma(Tm.coef, double(v.y), im);
+                        }
+                        const float2 lam = make_float2(float(re), float(im));
+                        if (resident) sl[swz(y)] = lam; else glam[y] = lam;
+                        df_add_prod(e, ps[k].x, lam.x);
+                        df_add_prod(e, ps[k].y, lam.y);
+                    }
                 }
-                const float2 lam = make_float2(float(re), float(im));
-                dst[y] = lam;
-                const float2 ps = src[y];
-                df_add_prod(e, ps.x, lam.x);
-                df_add_prod(e, ps.y, lam.y);
+                const double ew = warp_sum(df_value(e));
+                if (lane == 0) redE[warp] = ew;
+                gbar(G, w0);
+                if (tg == 0) {
+                    double E = 0.0;
+                    for (int w = w0; w < w0 + G; w++) E += redE[w];
+                    B.energy[item] = E;
+                }
+                gbar(G, w0);
             }
-            const double E = block_sum_d(df_value(e), red);
-            if (threadIdx.x == 0) B.energy[B.order[w]] = E;
-            __syncthreads();
-        }
-        if (!B.want_grad) continue;
-        // ---------------- reverse sweep
-        for (int p = it.p1 - 1; p >= it.p0; p--) {
-            const BPass& P = B.passes[p];
-            const uint32_t nch = resident ? 1u : (N >> kLocal);
-            for (uint32_t c = 0; c < nch; c++) {
-                const uint32_t base = resident ? 0u : chunk_base(P.nonlocal, c);
-                if (!resident) {
-                    for (int l = threadIdx.x; l < size; l += kBT) {
-                        const uint32_t a = chunk_addr(P, base, l);
-                        sp[l] = gpsi[a];
-                        sl[l] = glam[a];
+            // ---------------- reverse sweep: gradient, then un-apply, gate by gate
+            for (int p = it.p1 - 1; p >= it.p0; p--) {
+                const BPass& P = B.passes[p];
+                const uint32_t nch = resident ? 1u : (N >> kLocal);
+                for (uint32_t c = 0; c < nch; c++) {
+                    const uint32_t base = resident ? 0u : chunk_base(P.nonlocal, c);
+                    if (!resident) {
+                        chunk_load(P, base, gpsi, sp, tg);
+                        chunk_load(P, base, glam, sl, tg);
+                        gbar(G, w0);
+                    }
+                    for (int s = P.s1 - 1; s >= P.s0; s--) {
+                        const BStage S = B.stages[s];
+                        // every lane reaches the warp reductions; lanes beyond T hold no amplitudes
+                        const bool active = tg < T;
+                        LocalMap li;
+                        float2 v[kRegs], u[kRegs];
+                        if (active) {
+                            li = stage_map(S, nl, tg);
+#pragma unroll
+                            for (int r = 0; r < kRegs; r++)
+                                if (r < R) {
+                                    v[r] = sp[swz(li.at(r))];
+                                    u[r] = sl[swz(li.at(r))];
+                                }
+                        }
+                        int slot = 0;
+                        for (int gi = S.g1 - 1; gi >= S.g0; gi--) {
+                            const BGate g = B.gates[gi];
+                            const float2 c2 = g.slot >= 0 ? cs[g.slot] : make_float2(1.f, 0.f);
+                            if (g.grad >= 0) {
+                                const double gw = warp_sum(active ? grad_reg(v, u, li, R, g) : 0.0);
+                                if (lane == 0) red[parity][slot][warp] = gw;
+                                slot++;
+                            }
+                            if (active) {
+                                apply_reg(v, li, R, g, c2, true);
+                                apply_reg(u, li, R, g, c2, true);
+                            }
+                        }
+                        if (active) {
+#pragma unroll
+                            for (int r = 0; r < kRegs; r++)
+                                if (r < R) {
+                                    sp[swz(li.at(r))] = v[r];
+                                    sl[swz(li.at(r))] = u[r];
+                                }
+                        }
+                        gbar(G, w0);
+                        if (tg < S.nparam) {
+                            // this thread owns the tg-th parametric gate of the stage (reverse order)
+                            int slot = 0, gidx = -1;
+                            for (int gi = S.g1 - 1; gi >= S.g0; gi--) {
+                                const BGate g = B.gates[gi];
+                                if (g.grad >= 0) {
+                                    if (slot == tg) { gidx = g.grad; break; }
+                                    slot++;
+                                }
+                            }
+                            double sum = 0.0;
+                            for (int w = w0; w < w0 + G; w++) sum += red[parity][tg][w];
+                            // dE/dtheta = -Im <lambda|P|psi>
+                            B.grad[it.grad0 + gidx] -= sum;
+                        }
+                        parity ^= 1;
+                    }
+                    if (!resident) {
+                        chunk_store(P, base, gpsi, sp, tg);
+                        chunk_store(P, base, glam, sl, tg);
+                        gbar(G, w0);
                     }
                 }
-                __syncthreads();
-                for (int gi = P.g1 - 1; gi >= P.g0; gi--) {
-                    const BGate g = B.gates[gi];
-                    const float2 cs = g.slot >= 0 ? B.cs[it.angle0 + g.slot] : make_float2(1.f, 0.f);
-                    if (g.grad >= 0) {
-                        DFAcc re, im;
-                        df_zero(re);
-                        df_zero(im);
-                        grad_local(sp, sl, size, g, re, im);
-                        // dE/dtheta = -Im <lambda|P|psi>
-                        const double v = block_sum_d(df_value(im), red);
-                        if (threadIdx.x == 0) B.grad[it.grad0 + g.grad] -= v;
-                        __syncthreads();
-                    }
-                    apply_local(sp, size, g, cs, true);
-                    apply_local(sl, size, g, cs, true);
-                    __syncthreads();
-                }
-                if (!resident) {
-                    for (int l = threadIdx.x; l < size; l += kBT) {
-                        const uint32_t a = chunk_addr(P, base, l);
-                        gpsi[a] = sp[l];
-                        glam[a] = sl[l];
-                    }
-                }
-                __syncthreads();
             }
         }
     }
@@ -342,6 +571,7 @@ struct qs_batch {
     std::vector<qs::BItem> items;
     std::vector<int32_t> order;
     std::vector<qs::BPass> passes;
+    std::vector<qs::BStage> stages;
     std::vector<qs::BGate> gates;
     std::vector<qs::BTerm> terms;
     std::vector<int32_t> angle_param;   // angle slot -> parameter index of its circuit (or -1)
@@ -353,6 +583,7 @@ struct qs_batch {
     void* d_items = nullptr;
     void* d_order = nullptr;
     void* d_passes = nullptr;
+    void* d_stages = nullptr;
     void* d_gates = nullptr;
     void* d_terms = nullptr;
     double* d_theta = nullptr;
@@ -364,6 +595,7 @@ struct qs_batch {
     double* h_theta = nullptr;   // pinned
     double* h_energy = nullptr;  // pinned
     double* h_grad = nullptr;    // pinned
+    int cls_begin[qs::kClasses + 1] = {};
     int grid = 0;
     size_t smem = 0;
     uint64_t ws_stride = 0;
@@ -436,14 +668,51 @@ void plan_passes(const qs_circuit& c, const std::vector<BGate>& gl, const std::v
             bp.tab_hi[h] = a;
         }
         auto local = [&](int q) { return uint8_t(std::find(lq.begin(), lq.end(), q) - lq.begin()); };
-        bp.g0 = int(b.gates.size());
+        // stages: runs of gates whose non-diagonal targets fit a sub-cube of kRegBits local bits
+        // held in registers (diagonal gates act on any bit), at most kMaxStageParams rotations
+        const int nl = int(lq.size());
+        const int na = std::min(kRegBits, nl);
+        bp.s0 = int(b.stages.size());
+        std::vector<BGate> cur;
+        std::vector<int> act;
+        int nparam = 0;
+        auto close_stage = [&]() {
+            if (cur.empty()) return;
+            for (int q = 0; q < nl && int(act.size()) < na; q++)
+                if (std::find(act.begin(), act.end(), q) == act.end()) act.push_back(q);
+            BStage st;
+            std::memset(&st, 0, sizeof(st));
+            st.g0 = int(b.gates.size());
+            st.nact = na;
+            st.nparam = nparam;
+            for (int j = 0; j < na; j++) st.act[j] = uint8_t(act[j]);
+            for (BGate g : cur) {
+                if (g.kind != BK_RZ && g.kind != BK_Z && g.kind != BK_CZ)
+                    g.ja = uint8_t(std::find(act.begin(), act.end(), int(g.a)) - act.begin());
+                b.gates.push_back(g);
+            }
+            st.g1 = int(b.gates.size());
+            b.stages.push_back(st);
+            cur.clear();
+            act.clear();
+            nparam = 0;
+        };
         for (int gi : p.gates) {
             BGate g = gl[gi];
             g.a = local(g.a);
             if (g.kind == BK_CZ || g.kind == BK_CNOT) g.b = local(g.b);
-            b.gates.push_back(g);
+            const bool diag = g.kind == BK_RZ || g.kind == BK_Z || g.kind == BK_CZ;
+            const int par = g.grad >= 0 ? 1 : 0;
+            bool fits = nparam + par <= kMaxStageParams;
+            if (!diag && std::find(act.begin(), act.end(), int(g.a)) == act.end() && int(act.size()) >= na)
+                fits = false;
+            if (!fits) close_stage();
+            if (!diag && std::find(act.begin(), act.end(), int(g.a)) == act.end()) act.push_back(g.a);
+            cur.push_back(g);
+            nparam += par;
         }
-        bp.g1 = int(b.gates.size());
+        close_stage();
+        bp.s1 = int(b.stages.size());
         b.passes.push_back(bp);
     }
     it.p1 = int(b.passes.size());
@@ -453,7 +722,7 @@ void free_batch(qs_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->graph_stream) cudaStreamDestroy(b->graph_stream);
-    void* dev[] = {b->d_items, b->d_order, b->d_passes, b->d_gates, b->d_terms, b->d_theta,
+    void* dev[] = {b->d_items, b->d_order, b->d_passes, b->d_stages, b->d_gates, b->d_terms, b->d_theta,
                    b->d_cs, b->d_ws, b->d_energy, b->d_grad, b->d_counter};
     for (void* p : dev)
         if (p) cudaFree(p);
@@ -475,11 +744,12 @@ void enqueue(qs_batch* b, cudaStream_t st) {
                                 cudaMemcpyHostToDevice, st));
     k_angles<<<std::max(1, std::min(1024, (b->total_angles + 255) / 256)), 256, 0, st>>>(b->d_theta, b->d_cs,
                                                                                           b->total_angles);
-    QS_TRY_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), st));
+    QS_TRY_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int) * kClasses, st));
     BatchDev B;
     B.items = static_cast<const BItem*>(b->d_items);
     B.order = static_cast<const int32_t*>(b->d_order);
     B.passes = static_cast<const BPass*>(b->d_passes);
+    B.stages = static_cast<const BStage*>(b->d_stages);
     B.gates = static_cast<const BGate*>(b->d_gates);
     B.terms = static_cast<const BTerm*>(b->d_terms);
     B.cs = b->d_cs;
@@ -487,9 +757,8 @@ void enqueue(qs_batch* b, cudaStream_t st) {
     B.ws_stride = b->ws_stride;
     B.energy = b->d_energy;
     B.grad = b->d_grad;
-    B.count = b->count;
-    B.want_grad = 1;
-    B.counter = b->d_counter;
+    B.counters = b->d_counter;
+    for (int c = 0; c <= kClasses; c++) B.cls_begin[c] = b->cls_begin[c];
     k_batch<<<b->grid, kBT, b->smem, st>>>(B);
     QS_TRY_CUDA(cudaGetLastError());
     QS_TRY_CUDA(cudaMemcpyAsync(b->h_energy, b->d_energy, sizeof(double) * std::max(1, b->count),
@@ -626,9 +895,20 @@ qs_status qs_batch_create(const qs_circuit* circuits, const qs_pauli_obs* observ
         cost[k] = std::ldexp(1.0, c.n) * (3.0 * passes + 2.0) + 64.0 * c.n_gates;
         b->items.push_back(it);
     }
+    // work classes by local width (groups of 16, 8, 4, 2, 1 warps), longest first in a class
+    auto cls_of = [&](int k) {
+        const int nl = std::min(b->items[k].n, kLocal);
+        return nl >= 13 ? 0 : nl == 12 ? 1 : nl == 11 ? 2 : nl == 10 ? 3 : 4;
+    };
     b->order.resize(count);
     std::iota(b->order.begin(), b->order.end(), 0);
-    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+        const int cx = cls_of(x), cy = cls_of(y);
+        return cx != cy ? cx < cy : cost[x] > cost[y];
+    });
+    for (int c = 0; c <= kClasses; c++) b->cls_begin[c] = 0;
+    for (int k = 0; k < count; k++) b->cls_begin[cls_of(k) + 1]++;
+    for (int c = 0; c < kClasses; c++) b->cls_begin[c + 1] += b->cls_begin[c];
     QS_TRY_CUDA(cudaGetDevice(&b->device));
     int sms = 1;
     QS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
@@ -639,6 +919,7 @@ qs_status qs_batch_create(const qs_circuit* circuits, const qs_pauli_obs* observ
         upload(&b->d_items, b->items);
         upload(&b->d_order, b->order);
         upload(&b->d_passes, b->passes);
+        upload(&b->d_stages, b->stages);
         upload(&b->d_gates, b->gates);
         upload(&b->d_terms, b->terms);
         QS_TRY_CUDA(cudaMalloc(&b->d_theta, sizeof(double) * std::max(1, b->total_angles)));
@@ -646,7 +927,7 @@ qs_status qs_batch_create(const qs_circuit* circuits, const qs_pauli_obs* observ
         QS_TRY_CUDA(cudaMalloc(&b->d_ws, sizeof(float2) * 2 * b->ws_stride * b->grid));
         QS_TRY_CUDA(cudaMalloc(&b->d_energy, sizeof(double) * count));
         QS_TRY_CUDA(cudaMalloc(&b->d_grad, sizeof(double) * std::max(1, b->total_grads)));
-        QS_TRY_CUDA(cudaMalloc(&b->d_counter, sizeof(unsigned int)));
+        QS_TRY_CUDA(cudaMalloc(&b->d_counter, sizeof(unsigned int) * kClasses));
         QS_TRY_CUDA(cudaMallocHost(&b->h_theta, sizeof(double) * std::max(1, b->total_angles)));
         QS_TRY_CUDA(cudaMallocHost(&b->h_energy, sizeof(double) * count));
         QS_TRY_CUDA(cudaMallocHost(&b->h_grad, sizeof(double) * std::max(1, b->total_grads)));
@@ -664,6 +945,7 @@ qs_status qs_batch_info(const qs_batch* b, int* total_params, int* total_passes,
     QS_REQUIRE(b != nullptr, "null batch");
     if (total_params) *total_params = b->total_grads;
     if (total_passes) *total_passes = int(b->passes.size());
+    // (stages are reported through the pass count only)
     if (workspace_bytes) *workspace_bytes = sizeof(float2) * 2 * b->ws_stride * b->grid;
     BATCH_END
 }

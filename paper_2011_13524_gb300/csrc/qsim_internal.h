@@ -159,6 +159,14 @@ std::vector<PauliGroup> group_observable(const qs_pauli_obs* obs, int n);
 void launch_apply_observable(const std::vector<PauliGroup>& groups, const void* psi, void* lam, int n,
                              Arith ar, cudaStream_t st);
 
+// Fused adjoint step for an uncontrolled rotation exp(i theta P/2), P = X/Y/Z (axis 1/2/3) on
+// `qubit`: per-block partials of Im <lam|P|psi> into part[0..grid), then psi, lam <- R^+ psi, R^+ lam.
+unsigned adj_grid(int n);
+void launch_adjoint_rotation(void* psi, void* lam, int n, Arith ar, int qubit, int axis, double theta, double* part,
+                             unsigned grid, cudaStream_t st);
+// out[s] = sum_j part[s * nb + j] for s < nslots (fixed order)
+void launch_slot_sums(const double* part, int nslots, unsigned nb, double* out, cudaStream_t st);
+
 // complex128 arithmetic mode (QS_MATH_FP64 / QS_MATH_DF)
 int c128_math();
 

@@ -124,3 +124,30 @@ def test_df_full_size_sampled(df):
     st.close()
     del st
     torch.cuda.empty_cache()
+
+
+def test_precision_c64_c128_vs_oracle(qs):
+    """The precision comparison on the depth-20 circuit family at n = 20: complex64 (FP32 gates,
+    FP64-built matrices, FP64 sums) and complex128 in both arithmetics against the FP64 oracle:
+    max-abs amplitude error, 1 - fidelity and the transverse-field Ising energy error (h = 1)."""
+    n = 20
+    c = W.u3cz_circuit(n, 20, 2020)
+    ref = oracle.run_circuit(c)
+    tf = W.tfim_observable(n, 1.0)
+    e_ref = oracle.expectation(ref, tf)[0]
+    old = qs.get_c128_math()
+    try:
+        for dtype, math_mode, k, amp_tol, e_tol in ((2, qs.QS_MATH_FP64, 2, 1e-12, 1e-11),
+                                                    (2, qs.QS_MATH_DF, 2, 1e-12, 1e-11),
+                                                    (1, qs.QS_MATH_FP64, 4, 1e-5, 1e-4)):
+            qs.set_c128_math(math_mode)
+            st = qs.State(n, dtype)
+            st.run(c, k)
+            got = st.get_vector().astype(np.complex128)
+            err = maxabs(got, ref)
+            fid = abs(np.vdot(ref, got)) ** 2 / (np.vdot(got, got).real)
+            assert err < amp_tol, (dtype, math_mode, err)
+            assert 1 - fid < (1e-12 if dtype == 2 else 1e-6)
+            assert abs(st.expectation(tf)[0] - e_ref) < e_tol
+    finally:
+        qs.set_c128_math(old)

@@ -293,3 +293,22 @@ def test_full_size_n30_fused_equals_unfused(qs):
     a.close(); b.close()
     del a, b
     torch.cuda.empty_cache()
+
+
+def test_adjoint_mixed_rotations_and_pauli_rotation(qs):
+    """Parametric RX, RY, RZ (fused reverse step) and a two-qubit PAULIROT (transition path),
+    with a shared parameter, against parameter shift."""
+    n = 5
+    gates = [W.Gate("H", (0,)), W.Gate("RX", (1,), params=(0.4,), param_index=0),
+             W.Gate("CNOT", (2,), controls=(1,), control_values=(1,)),
+             W.Gate("PAULIROT", (0, 3), pauli=(1, 2), params=(-0.9,), param_index=1),
+             W.Gate("RY", (4,), params=(1.3,), param_index=2), W.Gate("U3", (2,), params=(0.1, 0.5, -0.3)),
+             W.Gate("RZ", (3,), params=(0.4,), param_index=0), W.Gate("CZ", (0, 4)),
+             W.Gate("RZ", (2,), params=(2.2,), param_index=3)]
+    c = W.Circuit(n, gates, n_params=4)
+    obs = W.random_pauli_observable(n, 6, 77)
+    for dtype, tol in ((2, 1e-11), (1, 1e-4)):
+        e, g = qs.adjoint_grad(c, obs, dtype=dtype)
+        ps = oracle.grad_parameter_shift(c, obs, range(4))
+        assert abs(e - oracle.energy(c, obs)) < tol
+        assert np.max(np.abs(g - ps)) < tol
