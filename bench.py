@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--math", default="auto", choices=["auto", "fp64", "df"])
     p.add_argument("--extras", type=int, default=1, help="also measure unfused, c64, adjoint (rank 0)")
     p.add_argument("--cpu-sample-gates", type=int, default=9)
+    p.add_argument("--only", default="", choices=["", "batch"],
+                   help="profiling aid: time only the batched workload and print its numbers")
+    p.add_argument("--batch-count", type=int, default=4096)
     return p.parse_args()
 
 
@@ -386,7 +389,7 @@ def measure_extras(args, qs, torch, circuit):
     out["adjoint_params"] = int(hea.n_params)
     # batch: 4096 HEA circuits, n ~ U{8..20}, 2..12 layers, 4-term Pauli observables, complex64,
     # energies + adjoint gradients, one persistent launch replayed from a CUDA graph
-    items = W.batch_workload(4096, args.seed)
+    items = W.batch_workload(args.batch_count, args.seed)
     b = qs.Batch([i.circuit for i in items], [i.observable for i in items])
     theta = np.concatenate([i.circuit.parameters() for i in items])
     b.run(theta, use_graph=True)
@@ -395,7 +398,7 @@ def measure_extras(args, qs, torch, circuit):
     for _ in range(reps):
         b.run(theta, use_graph=True)
     dt = (time.perf_counter() - t0) / reps
-    out["batch_circuits_per_s"] = 4096 / dt
+    out["batch_circuits_per_s"] = args.batch_count / dt
     out["batch_ms"] = 1e3 * dt
     out["batch_params"] = b.total_params
     out["batch_workspace_gib"] = b.workspace_bytes / 2**30
@@ -431,8 +434,27 @@ def measure_extras(args, qs, torch, circuit):
     return out
 
 
+def run_batch_only(args):
+    import torch
+    import paper_2011_13524_gb300 as qs
+    items = W.batch_workload(args.batch_count, args.seed)
+    b = qs.Batch([i.circuit for i in items], [i.observable for i in items])
+    theta = np.concatenate([i.circuit.parameters() for i in items])
+    for _ in range(args.warmup):
+        b.run(theta, use_graph=True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b.run(theta, use_graph=True)
+    dt = (time.perf_counter() - t0) / args.steps
+    print(json.dumps({"batch_circuits": args.batch_count, "batch_ms": 1e3 * dt,
+                      "batch_circuits_per_s": args.batch_count / dt, "passes": b.total_passes}), flush=True)
+
+
 def main():
     args = parse()
+    if args.only == "batch":
+        run_batch_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

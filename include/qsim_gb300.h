@@ -255,7 +255,7 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
 /* ---------------------------------------------------------------- batched circuits */
 /* Many independent small (circuit, observable) pairs evaluated together: energies and adjoint
  * gradients of parametric circuits, the paper's variational usage (Sec. 3.1, Sec. 4.4) at the
- * scale of thousands of circuits. complex64 states (QS_C64), 1..24 qubits each; gates RX, RY,
+ * scale of thousands of circuits. complex64 states (QS_C64), 4..24 qubits each; gates RX, RY,
  * RZ (parametric or fixed, uncontrolled), CZ, CNOT (one control, value 1), H, X, Y, Z.
  * qs_batch_create validates and compiles the circuits once (per-circuit passes over 13-qubit
  * windows, device copies, a workspace of two 2^max_n complex64 buffers per SM when max_n > 13);

@@ -2,7 +2,8 @@
 // replayed from a CUDA graph: for every (circuit, observable) pair the energy
 // E = <psi|H|psi> and the adjoint gradient dE/dtheta (reverse sweep of Sec. 4.4 parametric
 // circuits, rotation convention exp(+i theta P / 2) of the paper's gate table), complex64
-// storage with compensated FP32 products summed in FP64.
+// storage; gradient partials are FP32 within a warp (at most 32 x 32 products) and FP64 across
+// warps and chunks; the energy is a compensated (double-float) sum.
 //
 // Layout of the work:
 //  * One CTA of 1024 threads per SM claims circuits through an atomic counter, longest first
@@ -42,14 +43,17 @@ constexpr int kMaxBatchQubits = 24;
 enum BKind : uint8_t { BK_RX = 0, BK_RY = 1, BK_RZ = 2, BK_CZ = 3, BK_CNOT = 4, BK_H = 5, BK_X = 6, BK_Y = 7, BK_Z = 8 };
 
 // one gate in the local coordinates of its pass
-struct BGate {
+struct __align__(16) BGate {
     uint8_t kind;
     uint8_t a;      // local bit of the target
     uint8_t b;      // local bit of the second qubit (CZ) or of the control (CNOT)
-    uint8_t ja;     // register bit holding the target (non-diagonal gates)
-    int32_t slot;   // angle slot (rotations), -1 otherwise
+    uint8_t ja;     // register bit holding the target, or kNoReg when it is not a register bit
+    uint8_t jb;     // register bit holding the second qubit / control, or kNoReg
+    uint8_t pad[3];
     int32_t grad;   // gradient index (parametric rotations), -1 otherwise
+    float c, s;     // cos, sin of theta/2 (rotations; written before every run), else 1, 0
 };
+constexpr uint8_t kNoReg = 0xff;
 
 // gates whose non-diagonal actions stay inside the register sub-cube spanned by act[]
 struct BStage {
@@ -81,19 +85,38 @@ struct BItem {
     int32_t grad0, ngrad;         // gradient outputs
 };
 
+enum LevelKind : int32_t { LV_FWD = 0, LV_LAMBDA = 1, LV_REV = 2, LV_FINAL = 3 };
+struct LevelEntry {
+    int32_t item;
+    int32_t pass;                 // pass index (forward / reverse levels)
+    int32_t unit0;                // first unit of this entry within the level
+    int32_t kind;
+};
+constexpr long long kBarrierSpinLimit = 1ll << 25;  // x 256 ns sleeps: ~10 s
+
 struct BatchDev {
     const BItem* items;
-    const int32_t* order;         // items grouped by class, longest first within a class
+    const int32_t* order;         // resident items grouped by class, longest first within a class
     const BPass* passes;
     const BStage* stages;
     const BGate* gates;
     const BTerm* terms;
-    const float2* cs;             // (cos, sin) of theta/2 per angle slot
-    float2* ws;                   // per-CTA workspace: psi and lambda, 2^maxn each (chunked circuits)
-    uint64_t ws_stride;
+    float2* ws;                   // psi and lambda of every circuit wider than the window
+    const uint64_t* ws_off;       // item -> offset of its psi buffer (lambda follows)
     double* energy;
     double* grad;
-    unsigned int* counters;       // one work counter per class
+    double* part_e;               // per wide item: energy partial per chunk
+    const int64_t* part_e_off;
+    double* part_g;               // per wide item: gradient partial per (parameter, chunk)
+    const int64_t* part_g_off;
+    const LevelEntry* lev_entries;
+    const int32_t* lev_off;       // nlevels + 1
+    const int32_t* lev_units;     // units per level
+    int32_t nlevels;
+    unsigned int* counters;       // kClasses resident counters, then one per level
+    unsigned int* bar_count;
+    unsigned int* bar_gen;
+    int* err;
     int32_t cls_begin[kClasses + 1];
 };
 
@@ -150,6 +173,11 @@ __device__ __noinline__ void chunk_store(const BPass& P, uint32_t base, float2* 
     for (int j = 0; j < kRegs; j++) g[chunk_addr(P, base, uint32_t(tg + j * kBT))] = t[j];
 }
 
+// |0...0> restricted to a chunk: amplitude 1 at local index 0 of the chunk with base 0
+__device__ __forceinline__ void sp_init(float2* s, uint32_t l, uint32_t base) {
+    s[l ^ ((l >> 4) & 15u) ^ ((l >> 8) & 15u)] = make_float2((base == 0 && l == 0) ? 1.f : 0.f, 0.f);
+}
+
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -195,18 +223,58 @@ __device__ __forceinline__ float2 cfma2(float2 a, float2 b, float2 acc) {
     return acc;
 }
 
-// 2x2 update of the register pairs (r, r | 2^J)
+// 2x2 update of the register pairs (r, r | 2^J) by a general complex matrix (H, X, Y)
 template <int J>
 __device__ __forceinline__ void pairs_1q(float2 (&v)[kRegs], int R, const M2& m) {
 #pragma unroll
     for (int r = 0; r < kRegs; r++) {
         if ((r >> J) & 1) continue;
-        if (r >= R) continue;
         const int r1 = r | (1 << J);
         const float2 u = v[r], w = v[r1];
         v[r] = cfma2(m.m01, w, cfma2(m.m00, u, make_float2(0.f, 0.f)));
         v[r1] = cfma2(m.m11, w, cfma2(m.m10, u, make_float2(0.f, 0.f)));
     }
+}
+
+// RY = [[c, s], [-s, c]] (real): 8 FMA per pair
+template <int J>
+__device__ __forceinline__ void pairs_ry(float2 (&v)[kRegs], int R, float c, float sn) {
+#pragma unroll
+    for (int r = 0; r < kRegs; r++) {
+        if ((r >> J) & 1) continue;
+        const int r1 = r | (1 << J);
+        const float2 u = v[r], w = v[r1];
+        v[r] = make_float2(fmaf(c, u.x, sn * w.x), fmaf(c, u.y, sn * w.y));
+        v[r1] = make_float2(fmaf(c, w.x, -sn * u.x), fmaf(c, w.y, -sn * u.y));
+    }
+}
+
+// RX = [[c, i s], [i s, c]]: 8 FMA per pair
+template <int J>
+__device__ __forceinline__ void pairs_rx(float2 (&v)[kRegs], int R, float c, float sn) {
+#pragma unroll
+    for (int r = 0; r < kRegs; r++) {
+        if ((r >> J) & 1) continue;
+        const int r1 = r | (1 << J);
+        const float2 u = v[r], w = v[r1];
+        v[r] = make_float2(fmaf(c, u.x, -sn * w.y), fmaf(c, u.y, sn * w.x));
+        v[r1] = make_float2(fmaf(c, w.x, -sn * u.y), fmaf(c, w.y, sn * u.x));
+    }
+}
+
+template <int J>
+__device__ __forceinline__ void pairs_kind(float2 (&v)[kRegs], int R, uint8_t kind, float c, float sn) {
+    if (kind == BK_RY) pairs_ry<J>(v, R, c, sn);
+    else if (kind == BK_RX) pairs_rx<J>(v, R, c, sn);
+    else pairs_1q<J>(v, R, gate_m2(kind, c, sn));
+}
+
+// which of the 16 registers have local bit `bit` set: a fixed pattern when the bit is one of the
+// register bits (position j), else all or none according to the thread's base
+__device__ __forceinline__ uint32_t reg_mask(uint8_t j, uint32_t base, uint8_t bit) {
+    const uint32_t pat[kRegBits] = {0xAAAAu, 0xCCCCu, 0xF0F0u, 0xFF00u};
+    if (j != kNoReg) return pat[j & 3];
+    return ((base >> bit) & 1u) ? 0xFFFFu : 0u;
 }
 
 // local index of register r of this thread: the thread's base (its bits outside the register
@@ -224,13 +292,12 @@ struct LocalMap {
 };
 
 template <int J>
-__device__ __forceinline__ void pairs_cnot(float2 (&v)[kRegs], const LocalMap& li, int R, int cb) {
+__device__ __forceinline__ void pairs_cnot(float2 (&v)[kRegs], uint32_t cmask) {
 #pragma unroll
     for (int r = 0; r < kRegs; r++) {
         if ((r >> J) & 1) continue;
-        if (r >= R) continue;
         const int r1 = r | (1 << J);
-        if ((li.at(r) >> cb) & 1) {
+        if ((cmask >> r) & 1u) {
             const float2 u = v[r];
             v[r] = v[r1];
             v[r1] = u;
@@ -244,75 +311,77 @@ __device__ __forceinline__ void apply_reg(float2 (&v)[kRegs], const LocalMap& li
     const float c = cs.x, sn = adjoint ? -cs.y : cs.y;
     switch (g.kind) {
         case BK_RZ: {  // diag(c + i s, c - i s)
+            const uint32_t m = reg_mask(g.ja, li.base, g.a);
 #pragma unroll
-            for (int r = 0; r < kRegs; r++)
-                if (r < R) v[r] = cmulf(make_float2(c, ((li.at(r) >> g.a) & 1) ? -sn : sn), v[r]);
+            for (int r = 0; r < kRegs; r++) v[r] = cmulf(make_float2(c, ((m >> r) & 1u) ? -sn : sn), v[r]);
             break;
         }
         case BK_Z: {
+            const uint32_t m = reg_mask(g.ja, li.base, g.a);
 #pragma unroll
             for (int r = 0; r < kRegs; r++)
-                if (r < R && ((li.at(r) >> g.a) & 1)) v[r] = make_float2(-v[r].x, -v[r].y);
+                if ((m >> r) & 1u) v[r] = make_float2(-v[r].x, -v[r].y);
             break;
         }
         case BK_CZ: {
+            const uint32_t m = reg_mask(g.ja, li.base, g.a) & reg_mask(g.jb, li.base, g.b);
 #pragma unroll
             for (int r = 0; r < kRegs; r++)
-                if (r < R && ((li.at(r) >> g.a) & 1) && ((li.at(r) >> g.b) & 1)) v[r] = make_float2(-v[r].x, -v[r].y);
+                if ((m >> r) & 1u) v[r] = make_float2(-v[r].x, -v[r].y);
             break;
         }
-        case BK_CNOT:
+        case BK_CNOT: {
+            const uint32_t m = reg_mask(g.jb, li.base, g.b);
             switch (g.ja) {
-                case 0: pairs_cnot<0>(v, li, R, g.b); break;
-                case 1: pairs_cnot<1>(v, li, R, g.b); break;
-                case 2: pairs_cnot<2>(v, li, R, g.b); break;
-                default: pairs_cnot<3>(v, li, R, g.b); break;
-            }
-            break;
-        default: {
-            const M2 m = gate_m2(g.kind, c, sn);
-            switch (g.ja) {
-                case 0: pairs_1q<0>(v, R, m); break;
-                case 1: pairs_1q<1>(v, R, m); break;
-                case 2: pairs_1q<2>(v, R, m); break;
-                default: pairs_1q<3>(v, R, m); break;
+                case 0: pairs_cnot<0>(v, m); break;
+                case 1: pairs_cnot<1>(v, m); break;
+                case 2: pairs_cnot<2>(v, m); break;
+                default: pairs_cnot<3>(v, m); break;
             }
             break;
         }
+        default:
+            switch (g.ja) {
+                case 0: pairs_kind<0>(v, R, g.kind, c, sn); break;
+                case 1: pairs_kind<1>(v, R, g.kind, c, sn); break;
+                case 2: pairs_kind<2>(v, R, g.kind, c, sn); break;
+                default: pairs_kind<3>(v, R, g.kind, c, sn); break;
+            }
+            break;
     }
 }
 
-// Im sum conj(lam) (P psi) over this thread's registers, P the axis of rotation g
+// Im sum conj(lam) (P psi) over this thread's registers, P the axis of rotation g. The thread's
+// partial (at most 32 products of complex64 data) is an FP32 FMA chain; the sums across threads,
+// warps and chunks are FP64.
 template <int J>
 __device__ __forceinline__ void grad_pairs(const float2 (&p)[kRegs], const float2 (&l)[kRegs], int R, uint8_t kind,
-                                           DFAcc& im) {
+                                           float& im) {
 #pragma unroll
     for (int r = 0; r < kRegs; r++) {
         if ((r >> J) & 1) continue;
-        if (r >= R) continue;
         const int r1 = r | (1 << J);
         const float2 a = p[r], b = p[r1], la = l[r], lb = l[r1];
         float2 p0, p1;  // X -> (b, a); Y -> (-i b, i a)
         if (kind == BK_RX) { p0 = b; p1 = a; }
         else { p0 = make_float2(b.y, -b.x); p1 = make_float2(-a.y, a.x); }
-        df_add_prod(im, la.x, p0.y);
-        df_add_prod(im, -la.y, p0.x);
-        df_add_prod(im, lb.x, p1.y);
-        df_add_prod(im, -lb.y, p1.x);
+        im = fmaf(la.x, p0.y, im);
+        im = fmaf(-la.y, p0.x, im);
+        im = fmaf(lb.x, p1.y, im);
+        im = fmaf(-lb.y, p1.x, im);
     }
 }
 
-__device__ __forceinline__ double grad_reg(const float2 (&p)[kRegs], const float2 (&l)[kRegs], const LocalMap& li,
-                                           int R, const BGate& g) {
-    DFAcc im;
-    df_zero(im);
+__device__ __forceinline__ float grad_reg(const float2 (&p)[kRegs], const float2 (&l)[kRegs], const LocalMap& li,
+                                          int R, const BGate& g) {
+    float im = 0.f;
     if (g.kind == BK_RZ) {  // Z: (a, -b) by the target bit
+        const uint32_t m = reg_mask(g.ja, li.base, g.a);
 #pragma unroll
         for (int r = 0; r < kRegs; r++) {
-            if (r >= R) continue;
-            const float sg = ((li.at(r) >> g.a) & 1) ? -1.f : 1.f;
-            df_add_prod(im, l[r].x, sg * p[r].y);
-            df_add_prod(im, -l[r].y, sg * p[r].x);
+            const float sg = ((m >> r) & 1u) ? -1.f : 1.f;
+            im = fmaf(sg * l[r].x, p[r].y, im);
+            im = fmaf(-sg * l[r].y, p[r].x, im);
         }
     } else {
         switch (g.ja) {
@@ -322,7 +391,7 @@ __device__ __forceinline__ double grad_reg(const float2 (&p)[kRegs], const float
             default: grad_pairs<3>(p, l, R, g.kind, im); break;
         }
     }
-    return df_value(im);
+    return im;
 }
 
 // local-index map of thread tg in stage S of a window of nl local bits
@@ -344,10 +413,160 @@ __device__ __forceinline__ LocalMap stage_map(const BStage& S, int nl, int tg) {
     return m;
 }
 
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     return v;
+}
+
+// ---------------------------------------------------------------- stage bodies
+// forward: registers <- slice, gates, slice <- registers
+__device__ __forceinline__ void stage_forward(const BatchDev& B, const BStage& S, int nl, int tg, int T, float2* sp) {
+    if (tg >= T) return;
+    const LocalMap li = stage_map(S, nl, tg);
+    float2 v[kRegs];
+#pragma unroll
+    for (int r = 0; r < kRegs; r++) v[r] = sp[swz(li.at(r))];
+    BGate g = B.gates[S.g0];
+    for (int gi = S.g0; gi < S.g1; gi++) {
+        const BGate gn = gi + 1 < S.g1 ? B.gates[gi + 1] : g;  // prefetch
+        apply_reg(v, li, kRegs, g, make_float2(g.c, g.s), false);
+        g = gn;
+    }
+#pragma unroll
+    for (int r = 0; r < kRegs; r++) sp[swz(li.at(r))] = v[r];
+}
+
+// reverse: gradient partials of the stage's rotations into red[slot][warp], un-apply from psi
+// and lambda. Every lane reaches the warp reductions; lanes beyond T hold no amplitudes.
+__device__ __forceinline__ void stage_reverse(const BatchDev& B, const BStage& S, int nl, int tg, int T, float2* sp,
+                                              float2* sl, double (*red)[kWarps], int warp, int lane) {
+    const bool active = tg < T;
+    LocalMap li;
+    float2 v[kRegs], u[kRegs];
+    if (active) {
+        li = stage_map(S, nl, tg);
+#pragma unroll
+        for (int r = 0; r < kRegs; r++) {
+            v[r] = sp[swz(li.at(r))];
+            u[r] = sl[swz(li.at(r))];
+        }
+    }
+    int slot = 0;
+    BGate g = B.gates[S.g1 - 1];
+    for (int gi = S.g1 - 1; gi >= S.g0; gi--) {
+        const BGate gn = gi > S.g0 ? B.gates[gi - 1] : g;  // prefetch
+        const float2 c2 = make_float2(g.c, g.s);
+        if (g.grad >= 0) {
+            // lane partials (<= 32 FP32 products) summed in FP32 across the warp, then FP64
+            const float gw = warp_sum_f(active ? grad_reg(v, u, li, kRegs, g) : 0.f);
+            if (lane == 0) red[slot][warp] = double(gw);
+            slot++;
+        }
+        if (active) {
+            apply_reg(v, li, kRegs, g, c2, true);
+            apply_reg(u, li, kRegs, g, c2, true);
+        }
+        g = gn;
+    }
+    if (active) {
+#pragma unroll
+        for (int r = 0; r < kRegs; r++) {
+            sp[swz(li.at(r))] = v[r];
+            sl[swz(li.at(r))] = u[r];
+        }
+    }
+}
+
+// after the stage barrier: thread tg < S.nparam owns the tg-th rotation of the stage (reverse
+// order); returns its gradient index and the sum of the warps' partials (fixed order)
+__device__ __forceinline__ int stage_param(const BatchDev& B, const BStage& S, int tg, const double (*red)[kWarps],
+                                           int w0, int G, double* sum) {
+    if (tg >= S.nparam) return -1;
+    int slot = 0, gidx = -1;
+    for (int gi = S.g1 - 1; gi >= S.g0; gi--) {
+        const int gr = B.gates[gi].grad;
+        if (gr >= 0) {
+            if (slot == tg) { gidx = gr; break; }
+            slot++;
+        }
+    }
+    double v = 0.0;
+    for (int w = w0; w < w0 + G; w++) v += red[tg][w];
+    *sum = v;
+    return gidx;
+}
+
+// lambda_y = sum_t coef i^{#Y} s(y ^ f) psi_{y ^ f} for y in [y0, y1) (stride nthr), and this
+// thread's share of Re <psi|lambda>; src/dst are shared slices (resident) or global buffers
+template <bool RES>
+__device__ __forceinline__ double lambda_range(const BatchDev& B, const BItem& it, const float2* src, float2* dst,
+                                               uint32_t y0, uint32_t y1, int tg, int nthr) {
+    DFAcc e;
+    df_zero(e);
+    const int nt = it.t1 - it.t0;
+    for (uint32_t y = y0 + tg; y < y1; y += nthr) {
+        float2 s4[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++)
+            if (t < nt) {
+                const uint32_t y2 = y ^ B.terms[it.t0 + t].xmask;
+                s4[t] = RES ? src[swz(y2)] : src[y2];
+            }
+        const float2 ps = RES ? src[swz(y)] : src[y];
+        float re = 0.f, im = 0.f;  // lambda is stored as complex64
+        for (int t = 0; t < nt; t++) {
+            const BTerm Tm = B.terms[it.t0 + t];
+            const uint32_t y2 = y ^ Tm.xmask;
+            float2 v = t < 4 ? s4[min(t, 3)] : (RES ? src[swz(y2)] : src[y2]);
+            v = mul_ipow(v, Tm.nY + 2 * (__popc(y2 & Tm.zmask) & 1));
+            re = fmaf(float(Tm.coef), v.x, re);
+            im = fmaf(float(Tm.coef), v.y, im);
+        }
+        const float2 lam = make_float2(re, im);
+        if (RES) dst[swz(y)] = lam; else dst[y] = lam;
+        df_add_prod(e, ps.x, lam.x);
+        df_add_prod(e, ps.y, lam.y);
+    }
+    return df_value(e);
+}
+
+// grid-wide barrier with a bounded wait (all CTAs are co-resident: cooperative launch). On
+// timeout it sets the error flag and returns false; every caller then leaves the kernel.
+__device__ bool grid_barrier(unsigned int* count, unsigned int* gen, int* err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vgen = gen;
+        const unsigned int g = *vgen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            *count = 0;
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == g) {
+                if (++spins > kBarrierSpinLimit || *(volatile int*)err) {
+                    atomicExch(err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(256);
+            }
+        }
+        __threadfence();
+        s_ok = ok && !*(volatile int*)err;
+    }
+    __syncthreads();
+    return s_ok != 0;
 }
 
 __global__ void __launch_bounds__(kBT, 1) k_batch(const BatchDev B) {
@@ -358,9 +577,95 @@ __global__ void __launch_bounds__(kBT, 1) k_batch(const BatchDev B) {
     __shared__ double redE[kWarps];
     __shared__ int s_claim[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2* gpsi = B.ws + uint64_t(blockIdx.x) * 2 * B.ws_stride;
-    float2* glam = gpsi + B.ws_stride;
     int parity = 0;
+
+    // ================= circuits wider than the window: level-synchronous over the grid
+    for (int lv = 0; lv < B.nlevels; lv++) {
+        const int total = B.lev_units[lv];
+        while (true) {
+            if (threadIdx.x == 0) s_claim[0] = int(atomicAdd(&B.counters[kClasses + lv], 1u));
+            __syncthreads();
+            const int u = s_claim[0];
+            __syncthreads();
+            if (u >= total) break;
+            // entry of this unit: last entry with unit0 <= u
+            int lo = B.lev_off[lv], hi = B.lev_off[lv + 1] - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (B.lev_entries[mid].unit0 <= u) lo = mid; else hi = mid - 1;
+            }
+            const LevelEntry E = B.lev_entries[lo];
+            const int item = E.item;
+            const BItem it = B.items[item];
+            const uint32_t c = uint32_t(u - E.unit0);
+            const uint32_t nch = 1u << (it.n - kLocal);
+            float2* gpsi = B.ws + B.ws_off[item];
+            float2* glam = gpsi + (uint64_t(1) << it.n);
+            const int tg = threadIdx.x;
+            if (E.kind == LV_FWD) {
+                const BPass& P = B.passes[E.pass];
+                const uint32_t base = chunk_base(P.nonlocal, c);
+                if (E.pass == it.p0) {
+                    for (uint32_t l = tg; l < kChunk; l += kBT) sp_init(smem_p, l, base);
+                } else {
+                    chunk_load(P, base, gpsi, smem_p, tg);
+                }
+                __syncthreads();
+                for (int s = P.s0; s < P.s1; s++) {
+                    stage_forward(B, B.stages[s], kLocal, tg, kBT, smem_p);
+                    __syncthreads();
+                }
+                chunk_store(P, base, gpsi, smem_p, tg);
+                __syncthreads();
+            } else if (E.kind == LV_LAMBDA) {
+                const uint32_t y0 = c << kLocal;
+                const double ew = warp_sum(lambda_range<false>(B, it, gpsi, glam, y0, y0 + kChunk, tg, kBT));
+                if (lane == 0) redE[warp] = ew;
+                __syncthreads();
+                if (tg == 0) {
+                    double e = 0.0;
+                    for (int w = 0; w < kWarps; w++) e += redE[w];
+                    B.part_e[B.part_e_off[item] + c] = e;
+                }
+                __syncthreads();
+            } else if (E.kind == LV_REV) {
+                const BPass& P = B.passes[E.pass];
+                const uint32_t base = chunk_base(P.nonlocal, c);
+                chunk_load(P, base, gpsi, smem_p, tg);
+                chunk_load(P, base, glam, smem_l, tg);
+                __syncthreads();
+                double* pg = B.part_g + B.part_g_off[item];
+                for (int s = P.s1 - 1; s >= P.s0; s--) {
+                    const BStage S = B.stages[s];
+                    stage_reverse(B, S, kLocal, tg, kBT, smem_p, smem_l, red[parity], warp, lane);
+                    __syncthreads();
+                    double sum;
+                    const int gidx = stage_param(B, S, tg, red[parity], 0, kWarps, &sum);
+                    if (gidx >= 0) pg[size_t(gidx) * nch + c] -= sum;  // dE/dtheta = -Im <lambda|P|psi>
+                    parity ^= 1;
+                }
+                chunk_store(P, base, gpsi, smem_p, tg);
+                chunk_store(P, base, glam, smem_l, tg);
+                __syncthreads();
+            } else {  // LV_FINAL: energy and gradients of the item, sums in chunk order
+                if (tg == 0) {
+                    double e = 0.0;
+                    for (uint32_t k = 0; k < nch; k++) e += B.part_e[B.part_e_off[item] + k];
+                    B.energy[item] = e;
+                }
+                const double* pg = B.part_g + B.part_g_off[item];
+                for (int j = tg; j < it.ngrad; j += kBT) {
+                    double gsum = 0.0;
+                    for (uint32_t k = 0; k < nch; k++) gsum += pg[size_t(j) * nch + k];
+                    B.grad[it.grad0 + j] = gsum;
+                }
+                __syncthreads();
+            }
+        }
+        if (!grid_barrier(B.bar_count, B.bar_gen, B.err)) return;
+    }
+
+    // ================= circuits within the window: whole circuit per warp group, in shared memory
     for (int cls = 0; cls < kClasses; cls++) {
         const int G = kWarps >> cls;
         const int w0 = (warp / G) * G;
@@ -377,92 +682,19 @@ __global__ void __launch_bounds__(kBT, 1) k_batch(const BatchDev B) {
             if (k >= count) break;
             const int item = B.order[B.cls_begin[cls] + k];
             const BItem it = B.items[item];
-            const int nl = it.n < kLocal ? it.n : kLocal;
-            const bool resident = it.n <= kLocal;
+            const int nl = it.n;
             const uint32_t size = 1u << nl;
-            const uint32_t N = 1u << it.n;
-            const int R = 1 << (nl < kRegBits ? nl : kRegBits);
-            const int T = int(size) / R;  // threads holding registers
-            const float2* cs = B.cs + it.angle0;
+            const int T = int(size) / kRegs;
             for (int j = tg; j < it.ngrad; j += nthr) B.grad[it.grad0 + j] = 0.0;
-            // ---------------- forward sweep
-            for (int p = it.p0; p < it.p1; p++) {
-                const BPass& P = B.passes[p];
-                const uint32_t nch = resident ? 1u : (N >> kLocal);
-                for (uint32_t c = 0; c < nch; c++) {
-                    const uint32_t base = resident ? 0u : chunk_base(P.nonlocal, c);
-                    if (p == it.p0) {
-                        for (uint32_t l = tg; l < size; l += nthr)
-                            sp[swz(l)] = make_float2((base == 0 && l == 0) ? 1.f : 0.f, 0.f);
-                    } else if (!resident) {
-                        chunk_load(P, base, gpsi, sp, tg);
-                    }
-                    gbar(G, w0);
-                    for (int s = P.s0; s < P.s1; s++) {
-                        const BStage S = B.stages[s];
-                        if (tg < T) {
-                            const LocalMap li = stage_map(S, nl, tg);
-                            float2 v[kRegs];
-#pragma unroll
-                            for (int r = 0; r < kRegs; r++)
-                                if (r < R) v[r] = sp[swz(li.at(r))];
-                            for (int gi = S.g0; gi < S.g1; gi++) {
-                                const BGate g = B.gates[gi];
-                                apply_reg(v, li, R, g, g.slot >= 0 ? cs[g.slot] : make_float2(1.f, 0.f), false);
-                            }
-#pragma unroll
-                            for (int r = 0; r < kRegs; r++)
-                                if (r < R) sp[swz(li.at(r))] = v[r];
-                        }
-                        gbar(G, w0);
-                    }
-                    if (!resident) {
-                        chunk_store(P, base, gpsi, sp, tg);
-                        gbar(G, w0);
-                    }
-                }
+            for (uint32_t l = tg; l < size; l += nthr) sp_init(sp, l, 0u);
+            gbar(G, w0);
+            const BPass& P = B.passes[it.p0];  // one pass holds the whole circuit
+            for (int s = P.s0; s < P.s1; s++) {
+                stage_forward(B, B.stages[s], nl, tg, T, sp);
+                gbar(G, w0);
             }
-            // ---------------- lambda = H psi and E = Re <psi|lambda>
             {
-                DFAcc e;
-                df_zero(e);
-                constexpr int U = 2;
-                for (uint32_t y0 = tg; y0 < N; y0 += U * nthr) {
-                    float2 src[U][4];
-                    float2 ps[U];
-                    const int nt = it.t1 - it.t0;
-#pragma unroll
-                    for (int k = 0; k < U; k++) {
-                        const uint32_t y = y0 + k * nthr;
-                        if (y >= N) continue;
-                        ps[k] = resident ? sp[swz(y)] : gpsi[y];
-#pragma unroll
-                        for (int t = 0; t < 4; t++)
-                            if (t < nt) {
-                                const uint32_t y2 = y ^ B.terms[it.t0 + t].xmask;
-                                src[k][t] = resident ? sp[swz(y2)] : gpsi[y2];
-                            }
-                    }
-#pragma unroll
-                    for (int k = 0; k < U; k++) {
-                        const uint32_t y = y0 + k * nthr;
-                        if (y >= N) continue;
-                        double re = 0.0, im = 0.0;
-                        for (int t = it.t0; t < it.t1; t++) {
-                            const BTerm Tm = B.terms[t];
-                            const uint32_t y2 = y ^ Tm.xmask;
-                            float2 v = (t - it.t0 < 4) ? src[k][min(t - it.t0, 3)] : (resident ? sp[swz(y2)] : gpsi[y2]);
-                            v = mul_ipow(v, Tm.nY + 2 * (__popc(y2 & Tm.zmask) & 1));
-                            re = fma(Tm.coef, double(v.x), re);
-                            im = fma(Tm.coef, double(v.y), im);
-                        }
-                        const float2 lam = make_float2(float(re), float(im));
-                        if (resident) sl[swz(y)] = lam; else glam[y] = lam;
-                        df_add_prod(e, ps[k].x, lam.x);
-                        df_add_prod(e, ps[k].y, lam.y);
-                    }
-                }
-                const double ew = warp_sum(df_value(e));
+                const double ew = warp_sum(lambda_range<true>(B, it, sp, sl, 0u, size, tg, nthr));
                 if (lane == 0) redE[warp] = ew;
                 gbar(G, w0);
                 if (tg == 0) {
@@ -472,89 +704,29 @@ __global__ void __launch_bounds__(kBT, 1) k_batch(const BatchDev B) {
                 }
                 gbar(G, w0);
             }
-            // ---------------- reverse sweep: gradient, then un-apply, gate by gate
-            for (int p = it.p1 - 1; p >= it.p0; p--) {
-                const BPass& P = B.passes[p];
-                const uint32_t nch = resident ? 1u : (N >> kLocal);
-                for (uint32_t c = 0; c < nch; c++) {
-                    const uint32_t base = resident ? 0u : chunk_base(P.nonlocal, c);
-                    if (!resident) {
-                        chunk_load(P, base, gpsi, sp, tg);
-                        chunk_load(P, base, glam, sl, tg);
-                        gbar(G, w0);
-                    }
-                    for (int s = P.s1 - 1; s >= P.s0; s--) {
-                        const BStage S = B.stages[s];
-                        // every lane reaches the warp reductions; lanes beyond T hold no amplitudes
-                        const bool active = tg < T;
-                        LocalMap li;
-                        float2 v[kRegs], u[kRegs];
-                        if (active) {
-                            li = stage_map(S, nl, tg);
-#pragma unroll
-                            for (int r = 0; r < kRegs; r++)
-                                if (r < R) {
-                                    v[r] = sp[swz(li.at(r))];
-                                    u[r] = sl[swz(li.at(r))];
-                                }
-                        }
-                        int slot = 0;
-                        for (int gi = S.g1 - 1; gi >= S.g0; gi--) {
-                            const BGate g = B.gates[gi];
-                            const float2 c2 = g.slot >= 0 ? cs[g.slot] : make_float2(1.f, 0.f);
-                            if (g.grad >= 0) {
-                                const double gw = warp_sum(active ? grad_reg(v, u, li, R, g) : 0.0);
-                                if (lane == 0) red[parity][slot][warp] = gw;
-                                slot++;
-                            }
-                            if (active) {
-                                apply_reg(v, li, R, g, c2, true);
-                                apply_reg(u, li, R, g, c2, true);
-                            }
-                        }
-                        if (active) {
-#pragma unroll
-                            for (int r = 0; r < kRegs; r++)
-                                if (r < R) {
-                                    sp[swz(li.at(r))] = v[r];
-                                    sl[swz(li.at(r))] = u[r];
-                                }
-                        }
-                        gbar(G, w0);
-                        if (tg < S.nparam) {
-                            // this thread owns the tg-th parametric gate of the stage (reverse order)
-                            int slot = 0, gidx = -1;
-                            for (int gi = S.g1 - 1; gi >= S.g0; gi--) {
-                                const BGate g = B.gates[gi];
-                                if (g.grad >= 0) {
-                                    if (slot == tg) { gidx = g.grad; break; }
-                                    slot++;
-                                }
-                            }
-                            double sum = 0.0;
-                            for (int w = w0; w < w0 + G; w++) sum += red[parity][tg][w];
-                            // dE/dtheta = -Im <lambda|P|psi>
-                            B.grad[it.grad0 + gidx] -= sum;
-                        }
-                        parity ^= 1;
-                    }
-                    if (!resident) {
-                        chunk_store(P, base, gpsi, sp, tg);
-                        chunk_store(P, base, glam, sl, tg);
-                        gbar(G, w0);
-                    }
-                }
+            for (int s = P.s1 - 1; s >= P.s0; s--) {
+                const BStage S = B.stages[s];
+                stage_reverse(B, S, nl, tg, T, sp, sl, red[parity], warp, lane);
+                gbar(G, w0);
+                double sum;
+                const int gidx = stage_param(B, S, tg, red[parity], w0, G, &sum);
+                if (gidx >= 0) B.grad[it.grad0 + gidx] -= sum;
+                parity ^= 1;
             }
         }
     }
 }
 
-// (cos, sin) of theta/2 for every angle slot
-__global__ void k_angles(const double* __restrict__ theta, float2* __restrict__ cs, int m) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+// (cos, sin) of theta/2 into every rotation's gate record
+__global__ void k_angles(const double* __restrict__ theta, const int32_t* __restrict__ gate_slot,
+                         BGate* __restrict__ gates, int ng) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += gridDim.x * blockDim.x) {
+        const int sl = gate_slot[i];
+        if (sl < 0) continue;
         double s, c;
-        sincos(0.5 * theta[i], &s, &c);
-        cs[i] = make_float2(float(c), float(s));
+        sincos(0.5 * theta[sl], &s, &c);
+        gates[i].c = float(c);
+        gates[i].s = float(s);
     }
 }
 
@@ -573,22 +745,41 @@ struct qs_batch {
     std::vector<qs::BPass> passes;
     std::vector<qs::BStage> stages;
     std::vector<qs::BGate> gates;
+    std::vector<int32_t> gate_slot;     // emitted gate -> absolute angle slot (or -1)
     std::vector<qs::BTerm> terms;
     std::vector<int32_t> angle_param;   // angle slot -> parameter index of its circuit (or -1)
     std::vector<double> angle_fixed;    // angle slot -> fixed angle (when not parametric)
     std::vector<int32_t> angle_item;    // angle slot -> item
     std::vector<int32_t> param0;        // item -> first parameter in the caller's theta array
     std::vector<int32_t> grad_of_item;  // item -> grad0
+    // circuits wider than the window: buffers and levels
+    std::vector<uint64_t> ws_off;       // item -> psi offset (amplitudes)
+    std::vector<int64_t> part_e_off, part_g_off;
+    std::vector<qs::LevelEntry> lev_entries;
+    std::vector<int32_t> lev_off, lev_units;
+    uint64_t ws_amps = 0;
+    int64_t part_e_total = 0, part_g_total = 0;
     // device buffers
     void* d_items = nullptr;
     void* d_order = nullptr;
     void* d_passes = nullptr;
     void* d_stages = nullptr;
     void* d_gates = nullptr;
+    void* d_gate_slot = nullptr;
     void* d_terms = nullptr;
     double* d_theta = nullptr;
-    float2* d_cs = nullptr;
     float2* d_ws = nullptr;
+    void* d_ws_off = nullptr;
+    double* d_part_e = nullptr;
+    void* d_part_e_off = nullptr;
+    double* d_part_g = nullptr;
+    void* d_part_g_off = nullptr;
+    void* d_lev_entries = nullptr;
+    void* d_lev_off = nullptr;
+    void* d_lev_units = nullptr;
+    unsigned int* d_bar = nullptr;    // count, generation
+    int* d_err = nullptr;
+    int* h_err = nullptr;             // pinned
     double* d_energy = nullptr;
     double* d_grad = nullptr;
     unsigned int* d_counter = nullptr;
@@ -598,7 +789,6 @@ struct qs_batch {
     int cls_begin[qs::kClasses + 1] = {};
     int grid = 0;
     size_t smem = 0;
-    uint64_t ws_stride = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t graph_stream = nullptr;
@@ -610,6 +800,7 @@ namespace {
 
 // split one circuit into passes over windows of <= kLocal qubits
 void plan_passes(const qs_circuit& c, const std::vector<BGate>& gl, const std::vector<uint32_t>& gmask,
+                 const std::vector<int32_t>& gslot,
                  qs_batch& b, BItem& it) {
     const int n = c.n;
     const int win = std::min(n, kLocal);
@@ -674,6 +865,7 @@ void plan_passes(const qs_circuit& c, const std::vector<BGate>& gl, const std::v
         const int na = std::min(kRegBits, nl);
         bp.s0 = int(b.stages.size());
         std::vector<BGate> cur;
+        std::vector<int32_t> cur_slot;
         std::vector<int> act;
         int nparam = 0;
         auto close_stage = [&]() {
@@ -686,14 +878,21 @@ void plan_passes(const qs_circuit& c, const std::vector<BGate>& gl, const std::v
             st.nact = na;
             st.nparam = nparam;
             for (int j = 0; j < na; j++) st.act[j] = uint8_t(act[j]);
-            for (BGate g : cur) {
-                if (g.kind != BK_RZ && g.kind != BK_Z && g.kind != BK_CZ)
-                    g.ja = uint8_t(std::find(act.begin(), act.end(), int(g.a)) - act.begin());
+            auto regpos = [&](int bit) {
+                const auto f = std::find(act.begin(), act.end(), bit);
+                return f == act.end() ? kNoReg : uint8_t(f - act.begin());
+            };
+            for (size_t q = 0; q < cur.size(); q++) {
+                BGate g = cur[q];
+                g.ja = regpos(g.a);
+                g.jb = (g.kind == BK_CZ || g.kind == BK_CNOT) ? regpos(g.b) : kNoReg;
                 b.gates.push_back(g);
+                b.gate_slot.push_back(cur_slot[q]);
             }
             st.g1 = int(b.gates.size());
             b.stages.push_back(st);
             cur.clear();
+            cur_slot.clear();
             act.clear();
             nparam = 0;
         };
@@ -709,6 +908,7 @@ void plan_passes(const qs_circuit& c, const std::vector<BGate>& gl, const std::v
             if (!fits) close_stage();
             if (!diag && std::find(act.begin(), act.end(), int(g.a)) == act.end()) act.push_back(g.a);
             cur.push_back(g);
+            cur_slot.push_back(gslot[gi]);
             nparam += par;
         }
         close_stage();
@@ -722,13 +922,16 @@ void free_batch(qs_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->graph_stream) cudaStreamDestroy(b->graph_stream);
-    void* dev[] = {b->d_items, b->d_order, b->d_passes, b->d_stages, b->d_gates, b->d_terms, b->d_theta,
-                   b->d_cs, b->d_ws, b->d_energy, b->d_grad, b->d_counter};
+    void* dev[] = {b->d_items, b->d_order, b->d_passes, b->d_stages, b->d_gates, b->d_gate_slot, b->d_terms,
+                   b->d_theta, b->d_ws, b->d_ws_off, b->d_part_e, b->d_part_e_off, b->d_part_g, b->d_part_g_off,
+                   b->d_lev_entries, b->d_lev_off, b->d_lev_units, b->d_bar, b->d_err, b->d_energy, b->d_grad,
+                   b->d_counter};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (b->h_theta) cudaFreeHost(b->h_theta);
     if (b->h_energy) cudaFreeHost(b->h_energy);
     if (b->h_grad) cudaFreeHost(b->h_grad);
+    if (b->h_err) cudaFreeHost(b->h_err);
 }
 
 template <typename T>
@@ -742,9 +945,14 @@ void upload(void** d, const std::vector<T>& h) {
 void enqueue(qs_batch* b, cudaStream_t st) {
     QS_TRY_CUDA(cudaMemcpyAsync(b->d_theta, b->h_theta, sizeof(double) * std::max(1, b->total_angles),
                                 cudaMemcpyHostToDevice, st));
-    k_angles<<<std::max(1, std::min(1024, (b->total_angles + 255) / 256)), 256, 0, st>>>(b->d_theta, b->d_cs,
-                                                                                          b->total_angles);
-    QS_TRY_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int) * kClasses, st));
+    const int ng = int(b->gates.size());
+    k_angles<<<std::max(1, std::min(1024, (ng + 255) / 256)), 256, 0, st>>>(
+        b->d_theta, static_cast<const int32_t*>(b->d_gate_slot), static_cast<BGate*>(b->d_gates), ng);
+    const int nlev = int(b->lev_units.size());
+    QS_TRY_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int) * (kClasses + nlev), st));
+    QS_TRY_CUDA(cudaMemsetAsync(b->d_bar, 0, sizeof(unsigned int) * 2, st));
+    QS_TRY_CUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), st));
+    if (b->part_g_total) QS_TRY_CUDA(cudaMemsetAsync(b->d_part_g, 0, sizeof(double) * b->part_g_total, st));
     BatchDev B;
     B.items = static_cast<const BItem*>(b->d_items);
     B.order = static_cast<const int32_t*>(b->d_order);
@@ -752,15 +960,37 @@ void enqueue(qs_batch* b, cudaStream_t st) {
     B.stages = static_cast<const BStage*>(b->d_stages);
     B.gates = static_cast<const BGate*>(b->d_gates);
     B.terms = static_cast<const BTerm*>(b->d_terms);
-    B.cs = b->d_cs;
     B.ws = b->d_ws;
-    B.ws_stride = b->ws_stride;
+    B.ws_off = static_cast<const uint64_t*>(b->d_ws_off);
     B.energy = b->d_energy;
     B.grad = b->d_grad;
+    B.part_e = b->d_part_e;
+    B.part_e_off = static_cast<const int64_t*>(b->d_part_e_off);
+    B.part_g = b->d_part_g;
+    B.part_g_off = static_cast<const int64_t*>(b->d_part_g_off);
+    B.lev_entries = static_cast<const LevelEntry*>(b->d_lev_entries);
+    B.lev_off = static_cast<const int32_t*>(b->d_lev_off);
+    B.lev_units = static_cast<const int32_t*>(b->d_lev_units);
+    B.nlevels = nlev;
     B.counters = b->d_counter;
+    B.bar_count = b->d_bar;
+    B.bar_gen = b->d_bar + 1;
+    B.err = b->d_err;
     for (int c = 0; c <= kClasses; c++) B.cls_begin[c] = b->cls_begin[c];
-    k_batch<<<b->grid, kBT, b->smem, st>>>(B);
-    QS_TRY_CUDA(cudaGetLastError());
+    // cooperative launch: every CTA is resident at once, so the grid barrier cannot wait on a
+    // CTA that never runs
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b->grid);
+    cfg.blockDim = dim3(kBT);
+    cfg.dynamicSmemBytes = b->smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    QS_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_batch, B));
+    QS_TRY_CUDA(cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     QS_TRY_CUDA(cudaMemcpyAsync(b->h_energy, b->d_energy, sizeof(double) * std::max(1, b->count),
                                 cudaMemcpyDeviceToHost, st));
     QS_TRY_CUDA(cudaMemcpyAsync(b->h_grad, b->d_grad, sizeof(double) * std::max(1, b->total_grads),
@@ -808,7 +1038,7 @@ qs_status qs_batch_create(const qs_circuit* circuits, const qs_pauli_obs* observ
     for (int k = 0; k < count; k++) {
         const qs_circuit& c = circuits[k];
         const qs_pauli_obs& o = observables[k];
-        QS_REQUIRE(c.n >= 1 && c.n <= kMaxBatchQubits, "batched circuits have 1..24 qubits");
+        QS_REQUIRE(c.n >= 4 && c.n <= kMaxBatchQubits, "batched circuits have 4..24 qubits");
         QS_REQUIRE(c.n_gates >= 0 && (c.n_gates == 0 || c.gates), "null gate array");
         QS_REQUIRE(c.n_params >= 0, "negative parameter count");
         b->max_n = std::max(b->max_n, c.n);
@@ -821,14 +1051,17 @@ qs_status qs_batch_create(const qs_circuit* circuits, const qs_pauli_obs* observ
         b->param0.push_back(param_base);
         std::vector<BGate> gl;
         std::vector<uint32_t> gm;
+        std::vector<int32_t> gs;  // absolute angle slot of each gate (-1: none)
         int slots = 0;
         for (int i = 0; i < c.n_gates; i++) {
             const qs_gate& g = c.gates[i];
             check_qubits(c.n, g.targets, g.m, g.controls, g.mc);
             BGate bg;
             std::memset(&bg, 0, sizeof(bg));
-            bg.slot = -1;
             bg.grad = -1;
+            bg.c = 1.f;
+            bg.s = 0.f;
+            int32_t aslot = -1;
             bg.a = uint8_t(g.targets[0]);
             uint32_t m = 1u << g.targets[0];
             QS_REQUIRE(g.kind == QS_GATE_NAMED, "batched circuits take named gates only");
@@ -838,7 +1071,7 @@ qs_status qs_batch_create(const qs_circuit* circuits, const qs_pauli_obs* observ
                 case QS_NAMED_RZ:
                     QS_REQUIRE(g.mc == 0 && g.m == 1, "batched rotations act on one qubit, uncontrolled");
                     bg.kind = g.named == QS_NAMED_RX ? BK_RX : g.named == QS_NAMED_RY ? BK_RY : BK_RZ;
-                    bg.slot = slots++;
+                    aslot = b->total_angles + slots++;
                     b->angle_item.push_back(k);
                     if (g.param_index >= 0) {
                         QS_REQUIRE(g.param_index < c.n_params, "param_index out of range");
@@ -871,8 +1104,9 @@ qs_status qs_batch_create(const qs_circuit* circuits, const qs_pauli_obs* observ
             if (g.named != QS_NAMED_CNOT) QS_REQUIRE(g.mc == 0, "only CNOT may carry a control in a batch");
             gl.push_back(bg);
             gm.push_back(m);
+            gs.push_back(aslot);
         }
-        plan_passes(c, gl, gm, *b, it);
+        plan_passes(c, gl, gm, gs, *b, it);
         // observable terms
         QS_REQUIRE(o.n_terms >= 0 && (o.n_terms == 0 || (o.coef && o.x_mask && o.z_mask)), "bad observable");
         it.t0 = int(b->terms.size());
@@ -895,10 +1129,12 @@ qs_status qs_batch_create(const qs_circuit* circuits, const qs_pauli_obs* observ
         cost[k] = std::ldexp(1.0, c.n) * (3.0 * passes + 2.0) + 64.0 * c.n_gates;
         b->items.push_back(it);
     }
-    // work classes by local width (groups of 16, 8, 4, 2, 1 warps), longest first in a class
+    // circuits within the window: work classes by width (groups of 16, 8, 4, 2, 1 warps),
+    // longest first in a class; wider circuits (class kClasses) go through the levels instead
     auto cls_of = [&](int k) {
-        const int nl = std::min(b->items[k].n, kLocal);
-        return nl >= 13 ? 0 : nl == 12 ? 1 : nl == 11 ? 2 : nl == 10 ? 3 : 4;
+        const int n = b->items[k].n;
+        if (n > kLocal) return kClasses;
+        return n == 13 ? 0 : n == 12 ? 1 : n == 11 ? 2 : n == 10 ? 3 : 4;
     };
     b->order.resize(count);
     std::iota(b->order.begin(), b->order.end(), 0);
@@ -907,27 +1143,103 @@ qs_status qs_batch_create(const qs_circuit* circuits, const qs_pauli_obs* observ
         return cx != cy ? cx < cy : cost[x] > cost[y];
     });
     for (int c = 0; c <= kClasses; c++) b->cls_begin[c] = 0;
-    for (int k = 0; k < count; k++) b->cls_begin[cls_of(k) + 1]++;
+    for (int k = 0; k < count; k++)
+        if (cls_of(k) < kClasses) b->cls_begin[cls_of(k) + 1]++;
     for (int c = 0; c < kClasses; c++) b->cls_begin[c + 1] += b->cls_begin[c];
     QS_TRY_CUDA(cudaGetDevice(&b->device));
     int sms = 1;
     QS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
-    b->grid = std::max(1, std::min(sms, count));
     b->smem = 2 * sizeof(float2) * kChunk;
-    b->ws_stride = b->max_n > kLocal ? (uint64_t(1) << b->max_n) : 1;
+    QS_TRY_CUDA(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem)));
+    int per_sm = 0;
+    QS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kBT, b->smem));
+    if (per_sm < 1) throw Error{QS_ERR_UNSUPPORTED, "batch kernel does not fit on an SM"};
+    b->grid = sms * per_sm;  // all co-resident (cooperative launch)
+    // circuits wider than the window get their own psi / lambda buffers and partial-sum slots,
+    // and their passes become levels shared by the whole grid
+    b->ws_off.assign(count, 0);
+    b->part_e_off.assign(count, 0);
+    b->part_g_off.assign(count, 0);
+    int maxp = 0;
+    std::vector<int> wide;
+    for (int k = 0; k < count; k++) {
+        const BItem& it = b->items[k];
+        if (it.n <= kLocal) continue;
+        wide.push_back(k);
+        const int64_t nch = int64_t(1) << (it.n - kLocal);
+        b->ws_off[k] = b->ws_amps;
+        b->ws_amps += 2 * (uint64_t(1) << it.n);
+        b->part_e_off[k] = b->part_e_total;
+        b->part_e_total += nch;
+        b->part_g_off[k] = b->part_g_total;
+        b->part_g_total += nch * it.ngrad;
+        maxp = std::max(maxp, it.p1 - it.p0);
+    }
+    // longest circuits first inside every level
+    std::stable_sort(wide.begin(), wide.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    auto add_level = [&](int kind, int r) {
+        int units = 0;
+        b->lev_off.push_back(int(b->lev_entries.size()));
+        for (int k : wide) {
+            const BItem& it = b->items[k];
+            const int np_ = it.p1 - it.p0;
+            const int nch = 1 << (it.n - kLocal);
+            LevelEntry e;
+            e.item = k;
+            e.kind = kind;
+            e.unit0 = units;
+            if (kind == LV_FWD) {
+                if (r >= np_) continue;
+                e.pass = it.p0 + r;
+                units += nch;
+            } else if (kind == LV_REV) {
+                if (r >= np_) continue;
+                e.pass = it.p1 - 1 - r;
+                units += nch;
+            } else if (kind == LV_LAMBDA) {
+                e.pass = -1;
+                units += nch;
+            } else {
+                e.pass = -1;
+                units += 1;
+            }
+            b->lev_entries.push_back(e);
+        }
+        b->lev_units.push_back(units);
+    };
+    if (!wide.empty()) {
+        for (int r = 0; r < maxp; r++) add_level(LV_FWD, r);
+        add_level(LV_LAMBDA, 0);
+        for (int r = 0; r < maxp; r++) add_level(LV_REV, r);
+        add_level(LV_FINAL, 0);
+        b->lev_off.push_back(int(b->lev_entries.size()));
+    } else {
+        b->lev_off.push_back(0);
+    }
     try {
         upload(&b->d_items, b->items);
         upload(&b->d_order, b->order);
         upload(&b->d_passes, b->passes);
         upload(&b->d_stages, b->stages);
         upload(&b->d_gates, b->gates);
+        upload(&b->d_gate_slot, b->gate_slot);
         upload(&b->d_terms, b->terms);
         QS_TRY_CUDA(cudaMalloc(&b->d_theta, sizeof(double) * std::max(1, b->total_angles)));
-        QS_TRY_CUDA(cudaMalloc(&b->d_cs, sizeof(float2) * std::max(1, b->total_angles)));
-        QS_TRY_CUDA(cudaMalloc(&b->d_ws, sizeof(float2) * 2 * b->ws_stride * b->grid));
+        QS_TRY_CUDA(cudaMalloc(&b->d_ws, sizeof(float2) * std::max<uint64_t>(1, b->ws_amps)));
+        upload(&b->d_ws_off, b->ws_off);
+        upload(&b->d_part_e_off, b->part_e_off);
+        upload(&b->d_part_g_off, b->part_g_off);
+        QS_TRY_CUDA(cudaMalloc(&b->d_part_e, sizeof(double) * std::max<int64_t>(1, b->part_e_total)));
+        QS_TRY_CUDA(cudaMalloc(&b->d_part_g, sizeof(double) * std::max<int64_t>(1, b->part_g_total)));
+        upload(&b->d_lev_entries, b->lev_entries);
+        upload(&b->d_lev_off, b->lev_off);
+        upload(&b->d_lev_units, b->lev_units);
+        QS_TRY_CUDA(cudaMalloc(&b->d_bar, sizeof(unsigned int) * 2));
+        QS_TRY_CUDA(cudaMalloc(&b->d_err, sizeof(int)));
+        QS_TRY_CUDA(cudaMallocHost(&b->h_err, sizeof(int)));
         QS_TRY_CUDA(cudaMalloc(&b->d_energy, sizeof(double) * count));
         QS_TRY_CUDA(cudaMalloc(&b->d_grad, sizeof(double) * std::max(1, b->total_grads)));
-        QS_TRY_CUDA(cudaMalloc(&b->d_counter, sizeof(unsigned int) * kClasses));
+        QS_TRY_CUDA(cudaMalloc(&b->d_counter, sizeof(unsigned int) * (kClasses + b->lev_units.size())));
         QS_TRY_CUDA(cudaMallocHost(&b->h_theta, sizeof(double) * std::max(1, b->total_angles)));
         QS_TRY_CUDA(cudaMallocHost(&b->h_energy, sizeof(double) * count));
         QS_TRY_CUDA(cudaMallocHost(&b->h_grad, sizeof(double) * std::max(1, b->total_grads)));
@@ -946,7 +1258,8 @@ qs_status qs_batch_info(const qs_batch* b, int* total_params, int* total_passes,
     if (total_params) *total_params = b->total_grads;
     if (total_passes) *total_passes = int(b->passes.size());
     // (stages are reported through the pass count only)
-    if (workspace_bytes) *workspace_bytes = sizeof(float2) * 2 * b->ws_stride * b->grid;
+    if (workspace_bytes)
+        *workspace_bytes = sizeof(float2) * b->ws_amps + sizeof(double) * size_t(b->part_e_total + b->part_g_total);
     BATCH_END
 }
 
@@ -982,6 +1295,7 @@ qs_status qs_batch_run(qs_batch* b, const double* theta, void* stream, int use_g
         enqueue(b, st);
     }
     QS_TRY_CUDA(cudaStreamSynchronize(st));
+    if (*b->h_err) throw Error{QS_ERR_TIMEOUT, "batch kernel: a grid barrier wait ran out (work abandoned)"};
     std::memcpy(energies, b->h_energy, sizeof(double) * b->count);
     if (b->total_grads) std::memcpy(grads, b->h_grad, sizeof(double) * b->total_grads);
     BATCH_END

@@ -34,7 +34,7 @@ def check_items(items, energies, grads, theta_of, e_tol=2e-5, g_tol=5e-5, sample
 
 
 def test_batch_resident_small(qs):
-    items = W.batch_workload(24, 7, n_lo=2, n_hi=11, l_lo=1, l_hi=4)
+    items = W.batch_workload(24, 7, n_lo=4, n_hi=11, l_lo=1, l_hi=4)
     b = qs.Batch([i.circuit for i in items], [i.observable for i in items])
     theta = np.concatenate([i.circuit.parameters() for i in items])
     e, g = b.run(theta, use_graph=False)
@@ -53,7 +53,7 @@ def test_batch_chunked_large(qs):
 
 
 def test_batch_graph_replay_new_theta(qs):
-    items = W.batch_workload(40, 3, n_lo=3, n_hi=15, l_lo=1, l_hi=5)
+    items = W.batch_workload(40, 3, n_lo=4, n_hi=15, l_lo=1, l_hi=5)
     b = qs.Batch([i.circuit for i in items], [i.observable for i in items])
     rng = W.SplitMix64(1)
     offs = np.cumsum([0] + [i.circuit.n_params for i in items])
@@ -82,7 +82,11 @@ def test_batch_other_gates_and_fixed_angles(qs):
 
 
 def test_batch_rejects_unsupported(qs):
-    c = W.Circuit(3, [W.Gate("U3", (0,), params=(0.1, 0.2, 0.3))])
+    c = W.Circuit(5, [W.Gate("U3", (0,), params=(0.1, 0.2, 0.3))])
     with pytest.raises(qs.QsError) as e:
-        qs.Batch([c], [W.tfim_observable(3)])
+        qs.Batch([c], [W.tfim_observable(5)])
     assert e.value.code == qs.QS_ERR_UNSUPPORTED
+    small = W.Circuit(3, [W.Gate("H", (0,))])
+    with pytest.raises(qs.QsError) as e:
+        qs.Batch([small], [W.tfim_observable(3)])
+    assert e.value.code == qs.QS_ERR_INVALID_ARG
