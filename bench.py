@@ -38,7 +38,8 @@ METRIC = "state-vector GB/s & gates/s at n=30 c128 vs HBM peak; adjoint-grad ms;
 HBM_PEAK_FALLBACK = 6800.0
 # DRAM bytes (read + write) per launch from one ncu capture, keyed by kernel; filled in only
 # for a kernel unchanged since the capture (profiles/<kernel>_<workload>.md gives the command).
-NCU_TRAFFIC = {}
+# dense_df: 4.2344 GB per launch at n = 27 (dense_df_2q_n27.md), scaled by 2^(30-27) to n = 30.
+NCU_TRAFFIC = {("dense_df", 30): 4.2344e9 * 8}
 
 
 def parse():
@@ -289,7 +290,7 @@ def run_ours(args):
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": NCU_TRAFFIC.get(dom),
+                "traffic": NCU_TRAFFIC.get((dom, n)),
                 "bytes_per_launch": d["bytes"] / d["launches"], "ms_per_launch": d["ms"] / d["launches"],
                 "share_of_step": d["ms"] / ms_per_step,
                 "per_kernel_ms": {k_: round(v["ms"], 3) for k_, v in per_kernel.items()}}
