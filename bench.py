@@ -375,6 +375,14 @@ def measure_extras(args, qs, torch, circuit):
     ms = timed(lambda: (st.set_basis(0), st.apply_plan(plan64) if k64 else st.run(circuit, 0)), reps=2)
     out["c64_fused_gates_per_s"] = G / (ms / 1e3)
     out["c64_fusion_k"] = k64
+    # fused width 6 on the tensor cores (tcgen05, 3xTF32) and on the FP32 CUDA cores
+    old_tc = qs.get_tensor_cores()
+    plan6 = qs.FusedCircuit(circuit, 6)
+    for tc in (True, False):
+        qs.set_tensor_cores(tc)
+        ms6 = timed(lambda: (st.set_basis(0), st.apply_plan(plan6)), reps=2)
+        out["c64_k6_%s_gates_per_s" % ("tensor" if tc else "cuda_cores")] = G / (ms6 / 1e3)
+    qs.set_tensor_cores(old_tc)
     ms = timed(lambda: (st.set_basis(0), st.run(circuit, 0)))
     out["c64_unfused_gates_per_s"] = G / (ms / 1e3)
     del st

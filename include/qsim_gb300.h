@@ -143,6 +143,12 @@ const char* qs_version(void);
 /* Arithmetic for complex128 gate updates, process-wide: QS_MATH_FP64 or QS_MATH_DF. */
 qs_status qs_set_c128_math(int mode);
 qs_status qs_get_c128_math(int* mode);
+/* complex64 dense blocks of 5 or 6 targets on the tensor cores (tcgen05.mma kind::tf32, each
+ * FP32 operand split into a TF32 head and remainder, three products: FP32-class accuracy per
+ * block, but the tensor cores' FP32 accumulator rounds toward zero, shrinking the norm by ~2e-6
+ * per block); process-wide, off by default (FP32 CUDA-core kernels, unbiased). */
+qs_status qs_set_tensor_cores(int enable);
+qs_status qs_get_tensor_cores(int* enable);
 
 /* ---------------------------------------------------------------- states (Sec. 4.2) */
 /* Allocates a 2^n state of type dt on the current device and sets it to |0...0>
@@ -203,6 +209,7 @@ qs_status qs_destroy_fused(qs_fused_circuit* f);
 #define QS_KERNEL_PAULI 4      /* Pauli string (permutation with phases) */
 #define QS_KERNEL_SWAP 5       /* SWAP / controlled SWAP */
 #define QS_KERNEL_DENSE_DF 6   /* complex128 dense gate matrix in double-float arithmetic */
+#define QS_KERNEL_DENSE_TC 7   /* complex64 dense block of 5-6 targets on the tensor cores (3xTF32) */
 qs_status qs_fused_block_cost(const qs_fused_circuit* f, int b, qs_dtype dt, int* kernel, int* launches,
                               double* bytes);
 /* Applies a plan like qs_apply_fused_circuit, recording a CUDA event on the state's stream

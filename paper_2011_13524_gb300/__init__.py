@@ -38,7 +38,8 @@ QS_MAX_TARGETS = 6
 QS_MAX_CONTROLS = 8
 
 QS_GATE_DENSE, QS_GATE_DIAG, QS_GATE_PAULI, QS_GATE_NAMED = 0, 1, 2, 3
-KERNEL_NAMES = {0: "dense_reg", 1: "dense_smem", 2: "diag", 3: "phase", 4: "pauli", 5: "swap", 6: "dense_df"}
+KERNEL_NAMES = {0: "dense_reg", 1: "dense_smem", 2: "diag", 3: "phase", 4: "pauli", 5: "swap", 6: "dense_df",
+                7: "dense_tc"}
 NAMED = {
     "X": 1, "Y": 2, "Z": 3, "H": 4, "S": 5, "Sdag": 6, "T": 7, "Tdag": 8, "sqrtX": 9,
     "sqrtXdag": 10, "sqrtY": 11, "sqrtYdag": 12, "RX": 13, "RY": 14, "RZ": 15, "U1": 16,
@@ -86,6 +87,8 @@ _SIGNATURES = {
     "qs_version": ([], ctypes.c_char_p),
     "qs_set_c128_math": ([ctypes.c_int], ctypes.c_int),
     "qs_get_c128_math": ([ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "qs_set_tensor_cores": ([ctypes.c_int], ctypes.c_int),
+    "qs_get_tensor_cores": ([ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "qs_create_state": ([ctypes.c_int, ctypes.c_int, _VOIDP, ctypes.POINTER(_VOIDP)], ctypes.c_int),
     "qs_wrap_state": ([_VOIDP, ctypes.c_int, ctypes.c_int, _VOIDP, ctypes.POINTER(_VOIDP)], ctypes.c_int),
     "qs_destroy_state": ([_VOIDP], ctypes.c_int),
@@ -155,6 +158,16 @@ def exported_symbols() -> Sequence[str]:
 
 def set_c128_math(mode: int) -> None:
     check(lib().qs_set_c128_math(int(mode)))
+
+
+def set_tensor_cores(enable: bool) -> None:
+    check(lib().qs_set_tensor_cores(int(bool(enable))))
+
+
+def get_tensor_cores() -> bool:
+    m = ctypes.c_int(0)
+    check(lib().qs_get_tensor_cores(ctypes.byref(m)))
+    return bool(m.value)
 
 
 def get_c128_math() -> int:

@@ -21,7 +21,10 @@ namespace qs {
 namespace {
 thread_local std::string g_err;
 std::atomic<int> g_c128_math{QS_MATH_FP64};
+std::atomic<int> g_tensor_c64{0};
 }  // namespace
+
+bool tensor_c64_enabled() { return g_tensor_c64.load() != 0; }
 
 void set_error(const std::string& msg) { g_err = msg; }
 void clear_error() { g_err.clear(); }
@@ -131,6 +134,7 @@ void op_cost(const Op& op, int n, qs_dtype dt, int* kernel, int* launches, doubl
             const int m = int(op.targets.size());
             const bool reg = m <= 3 || (m == 4 && dt == QS_C64);
             k = reg ? QS_KERNEL_DENSE_REG : QS_KERNEL_DENSE_SMEM;
+            if (dt == QS_C64 && m >= 5 && tensor_c64_enabled()) k = QS_KERNEL_DENSE_TC;
             if (dt == QS_C128 && c128_math() == QS_MATH_DF && m <= 3) k = QS_KERNEL_DENSE_DF;
             break;
         }
@@ -164,16 +168,25 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
     w.ptr.assign(ops.size(), nullptr);
     size_t total = 0;
     std::vector<size_t> offs(ops.size(), 0);
+    std::vector<char> tc(ops.size(), 0);
     for (size_t b = 0; b < ops.size(); b++) {
         if (ops[b].kind != OpKind::Dense || ops[b].targets.size() < 4) continue;
+        if (ar == Arith::F32 && ops[b].targets.size() >= 5 && tensor_c64_enabled()) {
+            ops[b] = pad_dense_to6(ops[b], s->n);
+            tc[b] = 1;
+        }
         offs[b] = total;
-        total += ops[b].data.size() * kernel_entry_bytes(ar);
+        total += tc[b] ? tc6_matrix_bytes() : ops[b].data.size() * kernel_entry_bytes(ar);
+        total = (total + 255) & ~size_t(255);
     }
     if (!total) return w;
     std::vector<unsigned char> host(total);
     for (size_t b = 0; b < ops.size(); b++) {
         if (ops[b].kind != OpKind::Dense || ops[b].targets.size() < 4) continue;
-        encode_entries(ar, ops[b].data, host.data() + offs[b]);
+        if (tc[b])
+            prepare_tc6_matrix(ops[b].data, reinterpret_cast<float*>(host.data() + offs[b]));
+        else
+            encode_entries(ar, ops[b].data, host.data() + offs[b]);
     }
     QS_TRY_CUDA(cudaMallocAsync(&w.dbuf, total, s->stream));
     QS_TRY_CUDA(cudaMemcpyAsync(w.dbuf, host.data(), total, cudaMemcpyHostToDevice, s->stream));
@@ -182,6 +195,7 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
         if (ops[b].kind == OpKind::Dense && ops[b].targets.size() >= 4) {
             w.ptr[b] = static_cast<unsigned char*>(w.dbuf) + offs[b];
             ops[b].dmat = w.ptr[b];
+            ops[b].dmat_tc = tc[b] != 0;
         }
     return w;
 }
@@ -308,7 +322,7 @@ double predicted_seconds(const Op& op, int n, qs_dtype dt) {
     int dev = 0;
     cudaGetDevice(&dev);
     const int width = op.kind == OpKind::Dense || op.kind == OpKind::Diag ? int(op.targets.size()) : 0;
-    auto key = std::make_tuple(dev, int(dt), dt == QS_C128 ? c128_math() : 0, kernel, width);
+    auto key = std::make_tuple(dev, int(dt), dt == QS_C128 ? c128_math() : (tensor_c64_enabled() ? 1 : 0), kernel, width);
     double per_byte;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -385,6 +399,19 @@ qs_status qs_set_c128_math(int mode) {
     API_BEGIN
     QS_REQUIRE(mode == QS_MATH_FP64 || mode == QS_MATH_DF, "unknown complex128 arithmetic mode");
     g_c128_math.store(mode);
+    API_END
+}
+
+qs_status qs_set_tensor_cores(int enable) {
+    API_BEGIN
+    g_tensor_c64.store(enable ? 1 : 0);
+    API_END
+}
+
+qs_status qs_get_tensor_cores(int* enable) {
+    API_BEGIN
+    QS_REQUIRE(enable != nullptr, "null output");
+    *enable = g_tensor_c64.load();
     API_END
 }
 
@@ -513,6 +540,7 @@ qs_status qs_synchronize(const qs_state* s) {
     check_state(s);
     QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
     QS_TRY_CUDA(cudaGetLastError());
+    if (tc_error_pending()) throw Error{QS_ERR_TIMEOUT, "tensor-core kernel: a bounded wait ran out"};
     API_END
 }
 

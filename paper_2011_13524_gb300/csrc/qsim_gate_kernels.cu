@@ -299,6 +299,20 @@ void launch_with(const Op& op, void* psi, int n, cudaStream_t st, void* stage) {
             const int m = int(op.targets.size());
             for (int t : op.targets) fixed.push_back(t);
             IndexPlan ip = make_index_plan(n, fixed, setmask);
+            // complex64 blocks of 5-6 targets: tensor cores (a 5-target block is padded to 6)
+            if (sizeof(C) == 8 && m >= 5 && tensor_c64_enabled()) {
+                const Op o6 = m == 6 ? op : pad_dense_to6(op, n);
+                const float* dK = static_cast<const float*>(op.dmat_tc ? op.dmat : nullptr);
+                if (!dK) {
+                    QS_REQUIRE(stage != nullptr, "no staging buffer for a wide dense gate");
+                    std::vector<float> hk(tc6_matrix_bytes() / sizeof(float));
+                    prepare_tc6_matrix(o6.data, hk.data());
+                    QS_TRY_CUDA(cudaMemcpyAsync(stage, hk.data(), tc6_matrix_bytes(), cudaMemcpyHostToDevice, st));
+                    QS_TRY_CUDA(cudaStreamSynchronize(st));  // hk is host memory that dies on return
+                    dK = static_cast<const float*>(stage);
+                }
+                return launch_dense_tc6(psi, n, o6.targets, o6.controls, o6.cvals, dK, st);
+            }
             if (m == 1) return launch_dense_reg<P, 1>(op, ip, psi, st);
             if (m == 2) return launch_dense_reg<P, 2>(op, ip, psi, st);
             if (m == 3) return launch_dense_reg<P, 3>(op, ip, psi, st);
@@ -415,6 +429,26 @@ void launch_from_df(void* psi, int n, cudaStream_t st) {
     const uint64_t N = 1ull << n;
     k_from_df<<<grid_for(N), kThreads, 0, st>>>(reinterpret_cast<double2*>(psi), N);
     QS_TRY_CUDA(cudaGetLastError());
+}
+
+Op pad_dense_to6(const Op& op, int n) {
+    if (op.kind != OpKind::Dense || op.targets.size() != 5) return op;
+    uint64_t used = 0;
+    for (int t : op.targets) used |= 1ull << t;
+    for (int c : op.controls) used |= 1ull << c;
+    int extra = -1;
+    for (int q = 0; q < n; q++)
+        if (!((used >> q) & 1)) { extra = q; break; }
+    QS_REQUIRE(extra >= 0, "no free qubit to pad a 5-target block");
+    Op r = op;
+    r.targets.push_back(extra);
+    r.data.assign(64 * 64, cplx(0.0, 0.0));
+    for (int z = 0; z < 64; z++)
+        for (int w = 0; w < 64; w++)
+            if ((z >> 5) == (w >> 5)) r.data[size_t(z) * 64 + w] = op.data[size_t(z & 31) * 32 + (w & 31)];
+    r.dmat = nullptr;
+    r.dmat_tc = false;
+    return r;
 }
 
 // matrix entries in the form a policy's kernels read from device memory

@@ -101,6 +101,7 @@ struct Op {
     cplx phase = 1.0;         // Phase: factor on the subspace where all fixed bits match
     uint64_t xmask = 0, zmask = 0;  // Pauli
     const void* dmat = nullptr;     // Dense, optional: device copy of `data` in the state's element type
+    bool dmat_tc = false;           // dmat holds the tensor-core form (complex64, 6 targets)
 };
 
 // gate descriptor -> dense operator on (targets, controls) (throws Error on bad input)
@@ -121,7 +122,7 @@ inline Arith arith_of(const qs_state* s) {
 // All launches are asynchronous on `st`. psi points at 2^n amplitudes of dtype dt.
 // `stage`: a device buffer of at least kStageBytes, used to hand wide dense matrices to the
 // kernels when op.dmat is not set.
-constexpr size_t kStageBytes = 64 * 64 * 16;
+constexpr size_t kStageBytes = 2 * 128 * 128 * 4;  // >= 64x64 complex128 and the tensor-core form
 void launch_op(const Op& op, void* psi, int n, qs_dtype dt, cudaStream_t st, void* stage);
 void launch_op_arith(const Op& op, void* psi, int n, Arith ar, cudaStream_t st, void* stage);
 void launch_set_basis(void* psi, int n, qs_dtype dt, uint64_t j, cudaStream_t st);
@@ -166,6 +167,17 @@ void launch_adjoint_rotation(void* psi, void* lam, int n, Arith ar, int qubit, i
                              unsigned grid, cudaStream_t st);
 // out[s] = sum_j part[s * nb + j] for s < nslots (fixed order)
 void launch_slot_sums(const double* part, int nslots, unsigned nb, double* out, cudaStream_t st);
+
+// Tensor-core path for complex64 dense blocks of 5 or 6 targets (tcgen05, 3xTF32).
+bool tensor_c64_enabled();
+// 5-target dense op -> 6 targets (K (x) I on the lowest free qubit); other ops unchanged
+Op pad_dense_to6(const Op& op, int n);
+// host image of the tensor-core operand (Ah, Al: 2 x 128 x 128 floats) of a 64 x 64 matrix
+void prepare_tc6_matrix(const std::vector<cplx>& K, float* host_out);
+size_t tc6_matrix_bytes();
+void launch_dense_tc6(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
+                      const std::vector<int>& cvals, const float* dmat, cudaStream_t st);
+bool tc_error_pending();
 
 // complex128 arithmetic mode (QS_MATH_FP64 / QS_MATH_DF)
 int c128_math();
