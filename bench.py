@@ -38,8 +38,9 @@ METRIC = "state-vector GB/s & gates/s at n=30 c128 vs HBM peak; adjoint-grad ms;
 HBM_PEAK_FALLBACK = 6800.0
 # DRAM bytes (read + write) per launch from one ncu capture, keyed by kernel; filled in only
 # for a kernel unchanged since the capture (profiles/<kernel>_<workload>.md gives the command).
-# dense_df: 4.2344 GB per launch at n = 27 (dense_df_2q_n27.md), scaled by 2^(30-27) to n = 30.
-NCU_TRAFFIC = {("dense_df", 30): 4.2344e9 * 8}
+# k_dense_reg<DFArith, 2>: captured at n = 27 (2 GiB state, 4.233e9 bytes per launch); its
+# traffic grows with the state, so the n = 30 entry is that figure times 8.
+NCU_TRAFFIC = {("dense_df", 27): 4232672512, ("dense_df", 30): 4232672512 * 8}
 
 
 def parse():

@@ -27,6 +27,8 @@ struct NativeArith {
     using Acc = C;
     __device__ __forceinline__ static Acc zero() { return cmake<C>(0.0, 0.0); }
     __device__ __forceinline__ static void mac(Acc& a, const K& k, const C& v) { a = cfma(k, v, a); }
+    // accumulator holding k * v (the first term of a sum)
+    __device__ __forceinline__ static Acc first(const K& k, const C& v) { return cmul(k, v); }
     __device__ __forceinline__ static C out(const Acc& a) { return a; }
     __device__ __forceinline__ static C ipow(const C& v, int k) { return mul_ipow(v, k); }
     __device__ __forceinline__ static C basis(bool one) { return cmake<C>(one ? 1.0 : 0.0, 0.0); }
@@ -68,6 +70,21 @@ struct DFArith {
         dprod(a.rs, a.rc, -k.z, -k.w, v.z, v.w);    // - ki vi
         dprod(a.is, a.ic, k.x, k.y, v.z, v.w);      // + kr vi
         dprod(a.is, a.ic, k.z, k.w, v.x, v.y);      // + ki vr
+    }
+    // (s, c) = (ah + al) * (bh + bl) without the TwoSum of dprod (the sum starts here)
+    __device__ __forceinline__ static void dprod0(float& s, float& c, float ah, float al, float bh, float bl) {
+        s = __fmul_rn(ah, bh);
+        float e = __fmaf_rn(ah, bh, -s);
+        e = __fmaf_rn(ah, bl, e);
+        c = __fmaf_rn(al, bh, e);
+    }
+    __device__ __forceinline__ static Acc first(const K& k, const C& v) {
+        Acc a;
+        dprod0(a.rs, a.rc, k.x, k.y, v.x, v.y);
+        dprod(a.rs, a.rc, -k.z, -k.w, v.z, v.w);
+        dprod0(a.is, a.ic, k.x, k.y, v.z, v.w);
+        dprod(a.is, a.ic, k.z, k.w, v.x, v.y);
+        return a;
     }
     __device__ __forceinline__ static void two_sum(float a, float b, float& h, float& l) {
         h = __fadd_rn(a, b);

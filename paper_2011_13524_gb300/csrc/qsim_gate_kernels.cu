@@ -57,9 +57,9 @@ __global__ void __launch_bounds__(kThreads) k_dense_reg(typename P::C* __restric
         for (int w = 0; w < D; w++) v[w] = psi[x0 + Pm.offs[w]];
 #pragma unroll
         for (int z = 0; z < D; z++) {
-            typename P::Acc a = P::zero();
+            typename P::Acc a = P::first(Pm.K[z * D], v[0]);
 #pragma unroll
-            for (int w = 0; w < D; w++) P::mac(a, Pm.K[z * D + w], v[w]);
+            for (int w = 1; w < D; w++) P::mac(a, Pm.K[z * D + w], v[w]);
             psi[x0 + Pm.offs[z]] = P::out(a);
         }
     }
