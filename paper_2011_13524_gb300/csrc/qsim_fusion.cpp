@@ -3,14 +3,24 @@
 // the state instead of one pass per gate; merging multiplies the arithmetic by
 // 2^(|M1 u M2| - |M1|) and halves the memory traffic.
 //
-// Planner (the light strategy with a width budget k): every qubit belongs to at most one
-// open block. A gate whose qubits (targets and controls) meet a set S of open blocks joins
-// them when the union of their qubits has at most k elements; the blocks of S are pairwise
-// disjoint and therefore commute, so merging them and appending the gate is exact. When the
-// union is too wide, the blocks of S are emitted and the gate opens a new block. Open
-// blocks that do not touch the gate commute with it and stay open. Merged matrices follow
-// merge(g1, g2) = g2 * g1 (g1 applied first), built in FP64 by applying each gate to the
-// columns of the block matrix.
+// Two partitions of the gate list into blocks of at most k qubits are formed and the one with
+// fewer blocks is kept (ties: the first).
+//
+// 1. Open-block greedy (the light strategy with a width budget k): every qubit belongs to at
+//    most one open block. A gate whose qubits (targets and controls) meet a set S of open
+//    blocks joins them when the union of their qubits has at most k elements; the blocks of S
+//    are pairwise disjoint and therefore commute, so merging them and appending the gate is
+//    exact. When the union is too wide, the blocks of S are emitted and the gate opens a new
+//    block. Open blocks that do not touch the gate commute with it and stay open.
+// 2. Frontier growth: a block starts from the earliest gate not yet emitted and takes every
+//    later gate whose qubits lie inside the block's qubit set Q and whose earlier gates on
+//    those qubits are all emitted or already in the block. While |Q| < k the block widens by
+//    the ready gate whose new qubit set lets the most gates join. A block built this way is
+//    closed under "comes earlier on a shared qubit", so emitting it before the gates that remain
+//    only moves it past gates on other qubits, with which it commutes: the product is exact.
+//
+// Merged matrices follow merge(g1, g2) = g2 * g1 (g1 applied first), built in FP64 by
+// applying each gate, in circuit order, to the columns of the block matrix.
 #include <algorithm>
 #include <cstring>
 
@@ -106,24 +116,22 @@ void emit(const OpenBlock& b, const qs_circuit* c, FusionPlan& plan) {
     plan.blocks.push_back(std::move(fb));
 }
 
-}  // namespace
-
-FusionPlan plan_fusion(const qs_circuit* c, int k) {
-    QS_REQUIRE(c != nullptr, "null circuit");
-    QS_REQUIRE(c->n >= 1 && c->n <= QS_MAX_QUBITS, "qubit count out of range");
-    QS_REQUIRE(c->n_gates >= 0 && (c->n_gates == 0 || c->gates != nullptr), "null gate array");
-    QS_REQUIRE(k >= 1 && k <= QS_MAX_TARGETS, "fusion width must be in 1..6");
-    FusionPlan plan;
-    plan.n = c->n;
-    plan.k = k;
-    plan.n_source_gates = c->n_gates;
+// Partition 1: open-block greedy. Returns the blocks in emission order.
+std::vector<OpenBlock> partition_greedy(const qs_circuit* c, const std::vector<uint64_t>& masks, int k) {
+    std::vector<OpenBlock> out;
     std::vector<OpenBlock> open;          // slots; empty mask = free
     std::vector<int> owner(c->n, -1);     // qubit -> slot
     int counter = 0;
+    auto free_slot = [&]() {
+        for (size_t s = 0; s < open.size(); s++)
+            if (open[s].mask == 0) return int(s);
+        open.emplace_back();
+        return int(open.size()) - 1;
+    };
     auto close_slots = [&](std::vector<int> slots) {
         std::sort(slots.begin(), slots.end(), [&](int a, int b) { return open[a].order < open[b].order; });
         for (int s : slots) {
-            emit(open[s], c, plan);
+            out.push_back(open[s]);
             for (int q = 0; q < c->n; q++)
                 if (owner[q] == s) owner[q] = -1;
             open[s].mask = 0;
@@ -131,10 +139,7 @@ FusionPlan plan_fusion(const qs_circuit* c, int k) {
         }
     };
     for (int i = 0; i < c->n_gates; i++) {
-        const qs_gate& g = c->gates[i];
-        QS_REQUIRE(g.m >= 1 && g.m <= QS_MAX_TARGETS, "target count out of range (1..6)");
-        check_qubits(c->n, g.targets, g.m, g.controls, g.mc);
-        const uint64_t gm = gate_mask(g);
+        const uint64_t gm = masks[i];
         std::vector<int> touched;
         uint64_t uni = gm;
         for (int q = 0; q < c->n; q++)
@@ -143,7 +148,6 @@ FusionPlan plan_fusion(const qs_circuit* c, int k) {
                 touched.push_back(owner[q]);
                 uni |= open[owner[q]].mask;
             }
-        int slot;
         if (__builtin_popcountll(uni) <= k) {
             // merge the touched blocks (disjoint, commuting) and append the gate
             OpenBlock nb;
@@ -156,14 +160,9 @@ FusionPlan plan_fusion(const qs_circuit* c, int k) {
                 open[s].gates.clear();
             }
             nb.gates.push_back(i);
-            slot = touched.empty() ? -1 : touched[0];
-            if (slot < 0) {
-                for (size_t s = 0; s < open.size(); s++)
-                    if (open[s].mask == 0) { slot = int(s); break; }
-                if (slot < 0) { open.emplace_back(); slot = int(open.size()) - 1; }
-            }
+            const int slot = touched.empty() ? free_slot() : touched[0];
             for (int q = 0; q < c->n; q++)
-                if (((uni >> q) & 1)) owner[q] = slot;
+                if ((uni >> q) & 1) owner[q] = slot;
             open[slot] = std::move(nb);
         } else {
             close_slots(touched);
@@ -171,10 +170,7 @@ FusionPlan plan_fusion(const qs_circuit* c, int k) {
             nb.mask = gm;
             nb.order = counter++;
             nb.gates.push_back(i);
-            slot = -1;
-            for (size_t s = 0; s < open.size(); s++)
-                if (open[s].mask == 0) { slot = int(s); break; }
-            if (slot < 0) { open.emplace_back(); slot = int(open.size()) - 1; }
+            const int slot = free_slot();
             open[slot] = std::move(nb);
             for (int q = 0; q < c->n; q++)
                 if ((gm >> q) & 1) owner[q] = slot;
@@ -184,6 +180,125 @@ FusionPlan plan_fusion(const qs_circuit* c, int k) {
     for (size_t s = 0; s < open.size(); s++)
         if (open[s].mask) rest.push_back(int(s));
     close_slots(rest);
+    return out;
+}
+
+// Partition 2: frontier growth. `rem` lists the gates not yet emitted, in circuit order; a
+// scan over it keeps `blocked`, the qubits of every passed gate that is outside the block: a
+// later gate on such a qubit has an earlier gate that is neither emitted nor in the block.
+// Membership: gate g is in the block when in[g] == blk, or, during a trial widening, when
+// trial[g] == tid.
+struct Frontier {
+    const std::vector<uint64_t>& masks;
+    const std::vector<int>& rem;
+    uint64_t all;
+    std::vector<int>& in;
+    std::vector<int>& trial;
+    int blk = 0;
+    int tid = 0;
+    bool member(int g, bool use_trial) const { return in[g] == blk || (use_trial && trial[g] == tid); }
+    // Adds to the block (or to the trial) every gate that can join with qubit set q.
+    int close_over(uint64_t q, bool use_trial) {
+        uint64_t blocked = 0;
+        int added = 0;
+        for (int g : rem) {
+            if (member(g, use_trial)) continue;
+            const uint64_t m = masks[g];
+            if (!(m & blocked) && (m & ~q) == 0) {
+                if (use_trial) trial[g] = tid;
+                else in[g] = blk;
+                added++;
+            } else {
+                blocked |= m;
+                if ((blocked & q) == q) break;
+            }
+        }
+        return added;
+    }
+    // Distinct qubit sets q | m of the ready gates that widen q without exceeding k qubits.
+    std::vector<uint64_t> widening(uint64_t q, int k) const {
+        std::vector<uint64_t> cand;
+        uint64_t blocked = 0;
+        for (int g : rem) {
+            if (member(g, false)) continue;
+            const uint64_t m = masks[g];
+            if (!(m & blocked) && (m & ~q) && __builtin_popcountll(q | m) <= k &&
+                std::find(cand.begin(), cand.end(), q | m) == cand.end())
+                cand.push_back(q | m);
+            blocked |= m;
+            if (blocked == all) break;
+        }
+        return cand;
+    }
+};
+
+std::vector<OpenBlock> partition_frontier(const qs_circuit* c, const std::vector<uint64_t>& masks, int k) {
+    std::vector<OpenBlock> out;
+    std::vector<int> rem(c->n_gates);
+    for (int i = 0; i < c->n_gates; i++) rem[i] = i;
+    std::vector<int> in(c->n_gates, -1), trial(c->n_gates, -1);
+    const uint64_t all = c->n >= 64 ? ~0ull : ((1ull << c->n) - 1);
+    Frontier f{masks, rem, all, in, trial};
+    while (!rem.empty()) {
+        uint64_t q = masks[rem[0]];
+        in[rem[0]] = f.blk;
+        f.close_over(q, false);
+        while (__builtin_popcountll(q) < k) {
+            const std::vector<uint64_t> cand = f.widening(q, k);
+            if (cand.empty()) break;
+            int best = -1;
+            uint64_t best_q = 0;
+            for (uint64_t u : cand) {
+                f.tid++;
+                const int got = f.close_over(u, true);
+                // more gates first, then the narrower set
+                if (got > best || (got == best && __builtin_popcountll(u) < __builtin_popcountll(best_q))) {
+                    best = got;
+                    best_q = u;
+                }
+            }
+            q = best_q;
+            f.close_over(q, false);
+        }
+        OpenBlock b;
+        std::vector<int> keep;
+        for (int g : rem) {
+            if (in[g] == f.blk) {
+                b.gates.push_back(g);
+                b.mask |= masks[g];
+            } else {
+                keep.push_back(g);
+            }
+        }
+        out.push_back(std::move(b));
+        rem.swap(keep);
+        f.blk++;
+    }
+    return out;
+}
+
+}  // namespace
+
+FusionPlan plan_fusion(const qs_circuit* c, int k) {
+    QS_REQUIRE(c != nullptr, "null circuit");
+    QS_REQUIRE(c->n >= 1 && c->n <= QS_MAX_QUBITS, "qubit count out of range");
+    QS_REQUIRE(c->n_gates >= 0 && (c->n_gates == 0 || c->gates != nullptr), "null gate array");
+    QS_REQUIRE(k >= 1 && k <= QS_MAX_TARGETS, "fusion width must be in 1..6");
+    std::vector<uint64_t> masks(c->n_gates);
+    for (int i = 0; i < c->n_gates; i++) {
+        const qs_gate& g = c->gates[i];
+        QS_REQUIRE(g.m >= 1 && g.m <= QS_MAX_TARGETS, "target count out of range (1..6)");
+        check_qubits(c->n, g.targets, g.m, g.controls, g.mc);
+        masks[i] = gate_mask(g);
+    }
+    FusionPlan plan;
+    plan.n = c->n;
+    plan.k = k;
+    plan.n_source_gates = c->n_gates;
+    std::vector<OpenBlock> a = partition_greedy(c, masks, k);
+    std::vector<OpenBlock> b = partition_frontier(c, masks, k);
+    const std::vector<OpenBlock>& best = b.size() < a.size() ? b : a;
+    for (const OpenBlock& blk : best) emit(blk, c, plan);
     // keep copies of the gates that stay unfused (their matrices are rebuilt at launch)
     for (auto& b : plan.blocks) {
         if (b.single_gate < 0) continue;

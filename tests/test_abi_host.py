@@ -90,3 +90,19 @@ def test_fusion_reduces_block_count():
     counts = {k: qs.FusedCircuit(c, k).n_blocks for k in (1, 2, 3, 4, 5, 6)}
     assert counts[1] < len(c.gates)
     assert counts[2] < counts[1] and counts[4] < counts[2] and counts[6] <= counts[5]
+    # frontier growth reorders gates on disjoint qubits: on the brickwork a 4-qubit block
+    # covers two layers of a 4-qubit window (~11 gates), a 6-qubit block a light-cone triangle
+    assert counts[4] <= 80 and counts[6] <= 42, counts
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5, 6])
+def test_fusion_reordered_blocks_exact(k):
+    """Blocks taken out of circuit order (frontier growth) still give the circuit's product:
+    deeper circuits and mixed controlled / multi-target gates at n = 10."""
+    n = 10
+    for circ in [W.u3cz_circuit(n, 10, 21), W.Circuit(n, W.random_gate_suite(n, 23) * 2),
+                 W.hea_circuit(n, 4, 6), W.rzrxrz_cnot_circuit(n, 5, 7)]:
+        ref = oracle.run_circuit(circ)
+        plan = qs.FusedCircuit(circ, k)
+        got = run_plan_with_oracle(plan, n)
+        assert np.max(np.abs(got - ref)) < 1e-12
