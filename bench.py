@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--seed", type=int, default=20201127)
     p.add_argument("--fusion", type=int, default=-1, help="-1 autotune, 0 gate by gate, 1..6 width")
     p.add_argument("--math", default="auto", choices=["auto", "fp64", "df"])
+    p.add_argument("--tensor", type=int, default=-1,
+                   help="tensor-core path mask (1 complex64, 2 complex128 double-float); -1 = library default")
     p.add_argument("--extras", type=int, default=1, help="also measure unfused, c64, adjoint (rank 0)")
     p.add_argument("--cpu-sample-gates", type=int, default=9)
     p.add_argument("--only", default="", choices=["", "batch"],
@@ -215,6 +217,8 @@ def run_ours(args):
     # complex128 gate arithmetic: double-float on the FP32 pipes unless FP64 is asked for
     math_mode = {"fp64": qs.QS_MATH_FP64, "df": qs.QS_MATH_DF, "auto": qs.QS_MATH_DF}[args.math]
     qs.set_c128_math(math_mode)
+    if args.tensor >= 0:
+        qs.set_tensor_cores(args.tensor)
     n, dtype = args.n, qs.QS_C128
     circuit = replica_circuit(args, rank)
     G = len(circuit.gates)

@@ -143,12 +143,21 @@ const char* qs_version(void);
 /* Arithmetic for complex128 gate updates, process-wide: QS_MATH_FP64 or QS_MATH_DF. */
 qs_status qs_set_c128_math(int mode);
 qs_status qs_get_c128_math(int* mode);
-/* complex64 dense blocks of 5 or 6 targets on the tensor cores (tcgen05.mma kind::tf32, each
- * FP32 operand split into a TF32 head and remainder, three products: FP32-class accuracy per
- * block, but the tensor cores' FP32 accumulator rounds toward zero, shrinking the norm by ~2e-6
- * per block); process-wide, off by default (FP32 CUDA-core kernels, unbiased). */
-qs_status qs_set_tensor_cores(int enable);
-qs_status qs_get_tensor_cores(int* enable);
+/* Tensor-core paths for fused dense blocks (Sec. 5.4 blocks applied by Eq. update_mat),
+ * process-wide, as a bit mask:
+ * QS_TENSOR_C64: complex64 blocks of 5 or 6 targets (tcgen05.mma kind::tf32, each FP32 operand
+ *   split into a TF32 head and remainder, three products: FP32-class accuracy per block, but the
+ *   tensor cores' FP32 accumulator rounds toward zero, shrinking the norm by ~2e-6 per block).
+ * QS_TENSOR_C128: complex128 blocks of 4 targets in double-float runs (QS_MATH_DF): the matrix
+ *   and every 16-amplitude group are scaled by powers of two and cut into six 8-bit bf16 slices
+ *   (the splitting of Ozaki, Ogita, Oishi and Rump); the 21 slice products of weight >= 2^-48
+ *   are summed exactly in FP32 by tcgen05.mma kind::f16 and combined exactly in double-float:
+ *   about 2^-45 relative error per block, the accuracy of the double-float CUDA-core kernels.
+ * Unknown bits -> QS_ERR_INVALID_ARG. Default: none. */
+#define QS_TENSOR_C64 1
+#define QS_TENSOR_C128 2
+qs_status qs_set_tensor_cores(int mask);
+qs_status qs_get_tensor_cores(int* mask);
 
 /* ---------------------------------------------------------------- states (Sec. 4.2) */
 /* Allocates a 2^n state of type dt on the current device and sets it to |0...0>
@@ -210,6 +219,7 @@ qs_status qs_destroy_fused(qs_fused_circuit* f);
 #define QS_KERNEL_SWAP 5       /* SWAP / controlled SWAP */
 #define QS_KERNEL_DENSE_DF 6   /* complex128 dense gate matrix in double-float arithmetic */
 #define QS_KERNEL_DENSE_TC 7   /* complex64 dense block of 5-6 targets on the tensor cores (3xTF32) */
+#define QS_KERNEL_DENSE_OZ 8   /* double-float complex128 block of 4 targets on the tensor cores (bf16 slices) */
 qs_status qs_fused_block_cost(const qs_fused_circuit* f, int b, qs_dtype dt, int* kernel, int* launches,
                               double* bytes);
 /* Applies a plan like qs_apply_fused_circuit, recording a CUDA event on the state's stream

@@ -21,10 +21,11 @@ namespace qs {
 namespace {
 thread_local std::string g_err;
 std::atomic<int> g_c128_math{QS_MATH_FP64};
-std::atomic<int> g_tensor_c64{0};
+std::atomic<int> g_tensor{0};  // QS_TENSOR_* bits
 }  // namespace
 
-bool tensor_c64_enabled() { return g_tensor_c64.load() != 0; }
+bool tensor_c64_enabled() { return (g_tensor.load() & QS_TENSOR_C64) != 0; }
+bool tensor_c128_enabled() { return (g_tensor.load() & QS_TENSOR_C128) != 0; }
 
 void set_error(const std::string& msg) { g_err = msg; }
 void clear_error() { g_err.clear(); }
@@ -136,6 +137,7 @@ void op_cost(const Op& op, int n, qs_dtype dt, int* kernel, int* launches, doubl
             k = reg ? QS_KERNEL_DENSE_REG : QS_KERNEL_DENSE_SMEM;
             if (dt == QS_C64 && m >= 5 && tensor_c64_enabled()) k = QS_KERNEL_DENSE_TC;
             if (dt == QS_C128 && c128_math() == QS_MATH_DF && m <= 3) k = QS_KERNEL_DENSE_DF;
+            if (dt == QS_C128 && c128_math() == QS_MATH_DF && m == 4 && tensor_c128_enabled()) k = QS_KERNEL_DENSE_OZ;
             break;
         }
         case OpKind::Diag: k = QS_KERNEL_DIAG; break;
@@ -168,15 +170,19 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
     w.ptr.assign(ops.size(), nullptr);
     size_t total = 0;
     std::vector<size_t> offs(ops.size(), 0);
-    std::vector<char> tc(ops.size(), 0);
+    std::vector<char> tc(ops.size(), 0), oz(ops.size(), 0);
     for (size_t b = 0; b < ops.size(); b++) {
         if (ops[b].kind != OpKind::Dense || ops[b].targets.size() < 4) continue;
         if (ar == Arith::F32 && ops[b].targets.size() >= 5 && tensor_c64_enabled()) {
             ops[b] = pad_dense_to6(ops[b], s->n);
             tc[b] = 1;
         }
+        if (ar == Arith::DF && ops[b].targets.size() == 4 && tensor_c128_enabled()) {
+            ops[b] = sort_targets(ops[b]);
+            oz[b] = 1;
+        }
         offs[b] = total;
-        total += tc[b] ? tc6_matrix_bytes() : ops[b].data.size() * kernel_entry_bytes(ar);
+        total += tc[b] ? tc6_matrix_bytes() : oz[b] ? oz4_matrix_bytes() : ops[b].data.size() * kernel_entry_bytes(ar);
         total = (total + 255) & ~size_t(255);
     }
     if (!total) return w;
@@ -185,6 +191,8 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
         if (ops[b].kind != OpKind::Dense || ops[b].targets.size() < 4) continue;
         if (tc[b])
             prepare_tc6_matrix(ops[b].data, reinterpret_cast<float*>(host.data() + offs[b]));
+        else if (oz[b])
+            prepare_oz4_matrix(ops[b].data, host.data() + offs[b]);
         else
             encode_entries(ar, ops[b].data, host.data() + offs[b]);
     }
@@ -196,6 +204,7 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
             w.ptr[b] = static_cast<unsigned char*>(w.dbuf) + offs[b];
             ops[b].dmat = w.ptr[b];
             ops[b].dmat_tc = tc[b] != 0;
+            ops[b].dmat_oz = oz[b] != 0;
         }
     return w;
 }
@@ -323,6 +332,7 @@ double predicted_seconds(const Op& op, int n, qs_dtype dt) {
     cudaGetDevice(&dev);
     const int width = op.kind == OpKind::Dense || op.kind == OpKind::Diag ? int(op.targets.size()) : 0;
     auto key = std::make_tuple(dev, int(dt), dt == QS_C128 ? c128_math() : (tensor_c64_enabled() ? 1 : 0), kernel, width);
+    // (the kernel id already tells the tensor-core forms apart)
     double per_byte;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -402,16 +412,17 @@ qs_status qs_set_c128_math(int mode) {
     API_END
 }
 
-qs_status qs_set_tensor_cores(int enable) {
+qs_status qs_set_tensor_cores(int mask) {
     API_BEGIN
-    g_tensor_c64.store(enable ? 1 : 0);
+    QS_REQUIRE((mask & ~(QS_TENSOR_C64 | QS_TENSOR_C128)) == 0, "unknown tensor-core path bits");
+    g_tensor.store(mask);
     API_END
 }
 
-qs_status qs_get_tensor_cores(int* enable) {
+qs_status qs_get_tensor_cores(int* mask) {
     API_BEGIN
-    QS_REQUIRE(enable != nullptr, "null output");
-    *enable = g_tensor_c64.load();
+    QS_REQUIRE(mask != nullptr, "null output");
+    *mask = g_tensor.load();
     API_END
 }
 
@@ -541,6 +552,7 @@ qs_status qs_synchronize(const qs_state* s) {
     QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
     QS_TRY_CUDA(cudaGetLastError());
     if (tc_error_pending()) throw Error{QS_ERR_TIMEOUT, "tensor-core kernel: a bounded wait ran out"};
+    if (oz_error_pending()) throw Error{QS_ERR_TIMEOUT, "tensor-core double-float kernel: a bounded wait ran out"};
     API_END
 }
 

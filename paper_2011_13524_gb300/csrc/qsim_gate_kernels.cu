@@ -9,6 +9,7 @@
 // 2^m amplitudes of its groups form contiguous runs (coalesced for low and high targets
 // alike). Grids are a multiple of the SM count, each thread striding over the range.
 #include <algorithm>
+#include <type_traits>
 #include <cstring>
 
 #include "qsim_arith.cuh"
@@ -313,6 +314,20 @@ void launch_with(const Op& op, void* psi, int n, cudaStream_t st, void* stage) {
                 }
                 return launch_dense_tc6(psi, n, o6.targets, o6.controls, o6.cvals, dK, st);
             }
+            // double-float blocks of 4 targets: tensor cores (targets ascending)
+            if (std::is_same<P, DFArith>::value && m == 4 && tensor_c128_enabled()) {
+                const Op os = op.dmat_oz ? op : sort_targets(op);
+                const void* dK = op.dmat_oz ? op.dmat : nullptr;
+                if (!dK) {
+                    QS_REQUIRE(stage != nullptr, "no staging buffer for a wide dense gate");
+                    std::vector<unsigned char> hk(oz4_matrix_bytes());
+                    prepare_oz4_matrix(os.data, hk.data());
+                    QS_TRY_CUDA(cudaMemcpyAsync(stage, hk.data(), hk.size(), cudaMemcpyHostToDevice, st));
+                    QS_TRY_CUDA(cudaStreamSynchronize(st));  // hk is host memory that dies on return
+                    dK = stage;
+                }
+                return launch_dense_oz4(psi, n, os.targets, os.controls, os.cvals, dK, st);
+            }
             if (m == 1) return launch_dense_reg<P, 1>(op, ip, psi, st);
             if (m == 2) return launch_dense_reg<P, 2>(op, ip, psi, st);
             if (m == 3) return launch_dense_reg<P, 3>(op, ip, psi, st);
@@ -448,6 +463,30 @@ Op pad_dense_to6(const Op& op, int n) {
             if ((z >> 5) == (w >> 5)) r.data[size_t(z) * 64 + w] = op.data[size_t(z & 31) * 32 + (w & 31)];
     r.dmat = nullptr;
     r.dmat_tc = false;
+    return r;
+}
+
+Op sort_targets(const Op& op) {
+    const int m = int(op.targets.size());
+    std::vector<int> perm(m);
+    for (int j = 0; j < m; j++) perm[j] = j;
+    std::sort(perm.begin(), perm.end(), [&](int a, int b) { return op.targets[a] < op.targets[b]; });
+    Op r = op;
+    for (int j = 0; j < m; j++) r.targets[j] = op.targets[perm[j]];
+    if (op.kind == OpKind::Dense) {
+        const int D = 1 << m;
+        auto old_index = [&](int x) {  // bit j of the new local index is bit perm[j] of the old one
+            int o = 0;
+            for (int j = 0; j < m; j++)
+                if ((x >> j) & 1) o |= 1 << perm[j];
+            return o;
+        };
+        for (int z = 0; z < D; z++)
+            for (int w = 0; w < D; w++) r.data[size_t(z) * D + w] = op.data[size_t(old_index(z)) * D + old_index(w)];
+    }
+    r.dmat = nullptr;
+    r.dmat_tc = false;
+    r.dmat_oz = false;
     return r;
 }
 

@@ -102,6 +102,7 @@ struct Op {
     uint64_t xmask = 0, zmask = 0;  // Pauli
     const void* dmat = nullptr;     // Dense, optional: device copy of `data` in the state's element type
     bool dmat_tc = false;           // dmat holds the tensor-core form (complex64, 6 targets)
+    bool dmat_oz = false;           // dmat holds the sliced tensor-core form (double-float, 4 targets)
 };
 
 // gate descriptor -> dense operator on (targets, controls) (throws Error on bad input)
@@ -178,6 +179,18 @@ size_t tc6_matrix_bytes();
 void launch_dense_tc6(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
                       const std::vector<int>& cvals, const float* dmat, cudaStream_t st);
 bool tc_error_pending();
+
+// Tensor-core path for double-float complex128 dense blocks of 4 targets (tcgen05, bf16
+// slices with exact FP32 accumulation).
+bool tensor_c128_enabled();
+// the same op with its targets ascending (matrix local bits permuted to match)
+Op sort_targets(const Op& op);
+// host image of the sliced operand of a 16 x 16 matrix (stacked bf16 slices, row scales)
+size_t oz4_matrix_bytes();
+void prepare_oz4_matrix(const std::vector<cplx>& K, unsigned char* host_out);
+void launch_dense_oz4(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
+                      const std::vector<int>& cvals, const void* dmat, cudaStream_t st);
+bool oz_error_pending();
 
 // complex128 arithmetic mode (QS_MATH_FP64 / QS_MATH_DF)
 int c128_math();

@@ -1,0 +1,142 @@
+"""GPU parity of the tensor-core path for 4-target dense blocks of double-float complex128 runs
+(QS_MATH_DF with QS_TENSOR_C128: bf16 slices, exact FP32 sums on tcgen05) against the FP64
+oracle, at the complex128 bound (1e-12 max-abs amplitude error)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2011_13524_gb300 as qs
+    qs.lib()
+    return qs
+
+
+@pytest.fixture
+def oz(qs):
+    old_m, old_t = qs.get_c128_math(), qs.get_tensor_cores()
+    qs.set_c128_math(qs.QS_MATH_DF)
+    qs.set_tensor_cores(qs.QS_TENSOR_C128)
+    yield qs
+    qs.set_c128_math(old_m)
+    qs.set_tensor_cores(old_t)
+
+
+def maxabs(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))))
+
+
+def run_one(qs, n, gate, psi0):
+    st = qs.State(n, qs.QS_C128)
+    st.load(psi0)
+    st.run(W.Circuit(n, [gate]), 0)
+    return st.get_vector()
+
+
+@pytest.mark.parametrize("n", [4, 5, 8, 11, 12, 13, 15])
+def test_oz_single_gate_placements(oz, n):
+    """One 4-target dense gate (random, non-unitary) on low, high, mixed and unsorted targets;
+    n = 4 is a single group, n = 11 exactly one 128-group tile, n = 12, 13, 15 several tiles."""
+    qs = oz
+    rng = W.SplitMix64(100 + n)
+    psi0 = W.random_state(n, n)
+    placements = [(0, 1, 2, 3), (n - 1, n - 2, n - 3, n - 4), (0, 2, n - 1, 1), (3, 0, n - 2, 1)]
+    for t in placements:
+        if len(set(t)) < 4:
+            continue
+        K = W.random_complex_matrix(16, rng)
+        g = W.Gate("DENSE", t, matrix=K)
+        ref = psi0.copy()
+        oracle.apply_gate(ref, n, g)
+        got = run_one(qs, n, g, psi0)
+        assert maxabs(got, ref) < 1e-12 * max(1.0, float(np.max(np.abs(ref)))), t
+
+
+@pytest.mark.parametrize("n", [6, 9, 14])
+def test_oz_controlled_gate(oz, n):
+    qs = oz
+    rng = W.SplitMix64(7 + n)
+    psi0 = W.random_state(n, 3 * n)
+    for t, c, cv in [((1, 2, 3, 4), (0,), (1,)), ((0, n - 1, 2, 3), (1,), (0,))]:
+        g = W.Gate("DENSE", t, controls=c, control_values=cv, matrix=W.random_unitary(16, rng))
+        ref = psi0.copy()
+        oracle.apply_gate(ref, n, g)
+        assert maxabs(run_one(qs, n, g, psi0), ref) < 1e-12
+
+
+def test_oz_scaled_and_zero_groups(oz):
+    """Groups of very different magnitude, all-zero groups (basis-like states) and a
+    non-unitary matrix with large entries: errors stay relative to each group's scale."""
+    qs = oz
+    n = 12
+    rng = W.SplitMix64(5)
+    psi0 = W.random_state(n, 9)
+    psi0[: 1 << 8] *= 1e-6          # groups with tiny amplitudes
+    psi0[1 << 10: 1 << 11] = 0.0     # whole zero groups for targets above bit 3
+    K = W.random_complex_matrix(16, rng) * 7.5
+    g = W.Gate("DENSE", (4, 5, 6, 7), matrix=K)
+    ref = psi0.copy()
+    oracle.apply_gate(ref, n, g)
+    got = run_one(qs, n, g, psi0)
+    err = np.abs(got - ref)
+    assert float(np.max(err)) < 1e-12 * 8
+    small = slice(0, 1 << 8)
+    # in tiny groups the error scales down with the group (relative to 1e-6 amplitudes)
+    assert float(np.max(err[small])) < 1e-17
+
+
+@pytest.mark.parametrize("n", [12, 16, 20])
+def test_oz_fused_circuits(oz, n):
+    qs = oz
+    c = W.u3cz_circuit(n, 20 if n < 20 else 10, 40 + n)
+    ref = oracle.run_circuit(c)
+    st = qs.State(n, qs.QS_C128)
+    st.run(c, 4)
+    got = st.get_vector()
+    assert maxabs(got, ref) < 1e-12
+    assert abs(st.norm2() - 1.0) < 1e-12
+
+
+def test_oz_matches_cuda_core_path(oz):
+    """Same plan through the tensor-core kernel and the double-float CUDA-core kernel."""
+    qs = oz
+    n = 18
+    c = W.Circuit(n, W.random_gate_suite(n, 12))
+    plan = qs.FusedCircuit(c, 4)
+    a = qs.State(n, qs.QS_C128)
+    a.apply_plan(plan)
+    qs.set_tensor_cores(0)
+    b = qs.State(n, qs.QS_C128)
+    b.apply_plan(plan)
+    qs.set_tensor_cores(qs.QS_TENSOR_C128)
+    assert maxabs(a.get_vector(), b.get_vector()) < 1e-12
+
+
+def test_oz_full_size_sampled(oz):
+    import torch
+    from test_gpu_parity import product_then_cz, sampled_amplitudes
+    qs = oz
+    n = 30
+    circ, u3, cz = product_then_cz(n, 20, 778)
+    st = qs.State(n, qs.QS_C128)
+    plan = qs.FusedCircuit(circ, 4)
+    st.apply_plan(plan)
+    st.synchronize()
+    rng = W.SplitMix64(8)
+    xs = [rng.next_u64() & ((1 << n) - 1) for _ in range(2000)] + [0, (1 << n) - 1]
+    ref = sampled_amplitudes(n, u3, cz, xs)
+    idx = torch.tensor(xs, dtype=torch.int64, device="cuda")
+    got = st.tensor[idx].cpu().numpy()
+    assert maxabs(got, ref) < 1e-12
+    assert abs(st.norm2() - 1.0) < 1e-11
+    st.close()
+    del st
+    torch.cuda.empty_cache()
