@@ -23,11 +23,12 @@
 // its products: columns (s + t) * 32 of the accumulator block receive A_s B_t, so a single
 // MMA with N = 32 * min(6, 7 - s) feeds diagonals s..min(s + 5, 6).
 //
-// Pipeline (one CTA per SM, 512 threads, two buffers of everything): while the tensor cores
-// run tile j, the threads load tile j + 1 (cp.async into shared memory), finish tile j - 1
-// (TMEM -> double-float -> shared staging -> coalesced stores), then slice tile j + 1. Every
-// mbarrier wait is bounded; on expiry the kernel records an error, waits (bounded) for its
-// MMAs and frees TMEM.
+// Pipeline: two CTAs per SM (256 threads, ~95 KB of shared memory and 256 TMEM columns
+// each), so that one CTA's tensor-core and memory phases overlap the other's CUDA-core work.
+// Within a CTA: slice tile j, start its MMAs, start the cp.async loads of tile j + 1, then
+// read the accumulators (TMEM -> double-float -> shared staging) and store tile j coalesced.
+// Every mbarrier wait is bounded; on expiry the kernel records an error, waits (bounded) for
+// its MMAs and frees TMEM.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -44,8 +45,9 @@ constexpr int kOzR = 2 * kOzD;          // reals per group (K and N of one produ
 constexpr int kOzTG = 128;              // groups per tile (M)
 constexpr int kOzNS = 6;                // slices per operand
 constexpr int kOzND = 7;                // accumulated diagonals d = s + t <= 6
-constexpr int kOzThreads = 512;
-constexpr int kOzAmpsPerThread = kOzD / (kOzThreads / kOzTG);  // 4
+constexpr int kOzThreads = 256;                                // two CTAs per SM
+constexpr int kOzAmpsPerThread = kOzD / (kOzThreads / kOzTG);  // 8
+constexpr int kOzElemsPerThread = kOzTG * kOzD / kOzThreads;   // 8 loads / stores per tile
 constexpr uint32_t kOzSbo = (kOzR / 8) * 128;                  // 8-row group stride (K-major)
 constexpr uint32_t kOzLbo = 128;
 constexpr size_t kOzSlice = size_t(kOzTG) * kOzR * 2;          // one state slice, bf16
@@ -53,20 +55,21 @@ constexpr size_t kOzABuf = kOzNS * kOzSlice;                   // 48 KB
 constexpr size_t kOzRaw = size_t(kOzTG) * kOzD * 16;           // 32 KB of double-float amplitudes
 constexpr size_t kOzMat = size_t(kOzNS) * kOzR * kOzR * 2;     // 12 KB
 constexpr int kOzAccCols = kOzND * kOzR;                       // 224 columns per accumulator set
-constexpr int kOzTmemCols = 512;                               // two sets, rounded to a power of 2
+constexpr int kOzTmemCols = 256;                               // one set, rounded to a power of 2
 constexpr long long kOzSpinLimit = 1ll << 22;
 
 static_assert(kOzABuf >= kOzRaw, "output staging reuses a slice buffer");
+static_assert(kOzAccCols <= kOzTmemCols, "accumulators fit the TMEM allocation");
 
-// shared-memory plan (bytes)
-constexpr size_t kOffRaw = 0;                           // 2 x 32 KB
-constexpr size_t kOffA = kOffRaw + 2 * kOzRaw;          // 2 x 48 KB
-constexpr size_t kOffMat = kOffA + 2 * kOzABuf;         // 12 KB
+// shared-memory plan (bytes), ~95 KB: two CTAs per SM
+constexpr size_t kOffRaw = 0;                           // 32 KB
+constexpr size_t kOffA = kOffRaw + kOzRaw;              // 48 KB (slices, then output staging)
+constexpr size_t kOffMat = kOffA + kOzABuf;             // 12 KB
 constexpr size_t kOffMu = kOffMat + kOzMat;             // 32 floats
-constexpr size_t kOffNu = kOffMu + kOzR * 4;            // 2 x 128 floats
-constexpr size_t kOffNuPart = kOffNu + 2 * kOzTG * 4;   // 4 x 128 floats
-constexpr size_t kOffX0 = kOffNuPart + 4 * kOzTG * 4;   // 3 x 128 uint64
-constexpr size_t kOzSmem = kOffX0 + 3 * kOzTG * 8;
+constexpr size_t kOffNu = kOffMu + kOzR * 4;            // 128 floats
+constexpr size_t kOffNuPart = kOffNu + kOzTG * 4;       // 2 x 128 floats
+constexpr size_t kOffX0 = kOffNuPart + 2 * kOzTG * 4;   // 2 x 128 uint64
+constexpr size_t kOzSmem = kOffX0 + 2 * kOzTG * 8;
 
 struct OzParams {
     IndexPlan ip;            // 4 targets (and controls) inserted
@@ -164,16 +167,16 @@ __device__ __forceinline__ float pow2_ceil(float m) {
     return __uint_as_float(e << 23);
 }
 
-__global__ void __launch_bounds__(kOzThreads, 1) k_dense_oz4(float4* __restrict__ psi, const unsigned char* __restrict__ dmat,
+__global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict__ psi, const unsigned char* __restrict__ dmat,
                                                              const __grid_constant__ OzParams P, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int g = tid & (kOzTG - 1), q = tid >> 7;  // group and amplitude quarter of this thread
-    auto raw = [&](uint64_t b) { return reinterpret_cast<float4*>(smem + kOffRaw + (b & 1) * kOzRaw); };
-    auto abuf = [&](uint64_t b) { return smem + kOffA + (b & 1) * kOzABuf; };
+    const int g = tid & (kOzTG - 1), h = tid >> 7;  // group and amplitude half of this thread
+    float4* raw = reinterpret_cast<float4*>(smem + kOffRaw);
+    unsigned char* abuf = smem + kOffA;
     const float* mu = reinterpret_cast<const float*>(smem + kOffMu);
     float* nu = reinterpret_cast<float*>(smem + kOffNu);
     float* nu_part = reinterpret_cast<float*>(smem + kOffNuPart);
@@ -183,8 +186,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_dense_oz4(float4* __restrict_
     for (int i = tid; i < int((kOzMat + kOzR * 4) / 16); i += kOzThreads)
         reinterpret_cast<uint4*>(smem + kOffMat)[i] = reinterpret_cast<const uint4*>(dmat)[i];
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
         s_fail = 0;
     }
     if (warp == 0) {
@@ -198,74 +200,80 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_dense_oz4(float4* __restrict_
     const uint32_t tmem = tmem_base;
     const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
     const uint64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-    const uint32_t lowmask = (1u << P.low) - 1u;
 
-    // element e of a tile -> (group, amplitude), consecutive e at consecutive addresses where
-    // the low targets allow it
-    auto elem = [&](uint32_t e, uint32_t& gg, uint32_t& w) {
-        const uint32_t wl = e & lowmask, rest = e >> P.low;
-        gg = rest & (kOzTG - 1);
-        w = ((rest >> 7) << P.low) | wl;
-    };
+    // this thread's loads / stores of a tile: element e -> (group, amplitude) with consecutive e
+    // at consecutive addresses where the low targets allow it; fixed for every tile
+    uint32_t el_g[kOzElemsPerThread], el_slot[kOzElemsPerThread];
+    uint64_t el_off[kOzElemsPerThread];
+    {
+        const uint32_t lowmask = (1u << P.low) - 1u;
+#pragma unroll
+        for (int i = 0; i < kOzElemsPerThread; i++) {
+            const uint32_t e = uint32_t(tid + i * kOzThreads);
+            const uint32_t wl = e & lowmask, rest = e >> P.low;
+            const uint32_t gg = rest & (kOzTG - 1), w = ((rest >> 7) << P.low) | wl;
+            el_g[i] = gg;
+            el_slot[i] = raw_slot(gg, w);
+            el_off[i] = P.offs[w];
+        }
+    }
     auto fill_x0 = [&](uint64_t j) {
         const uint64_t tile = blockIdx.x + j * gridDim.x;
         if (tid < kOzTG) {
             const uint64_t gi = tile * kOzTG + tid;
-            x0s[(j % 3) * kOzTG + tid] = gi < P.n_groups ? expand(gi, P.ip) : ~0ull;
+            x0s[(j & 1) * kOzTG + tid] = gi < P.n_groups ? expand(gi, P.ip) : ~0ull;
         }
     };
-    auto load = [&](uint64_t j) {  // cp.async of tile j into raw(j) (x0 list ready)
-        const uint64_t* x = x0s + (j % 3) * kOzTG;
-        const uint32_t base = smem_u32(raw(j));
+    auto load = [&](uint64_t j) {  // cp.async of tile j into raw (x0 list ready)
+        const uint64_t* x = x0s + (j & 1) * kOzTG;
+        const uint32_t base = smem_u32(raw);
 #pragma unroll
-        for (int i = 0; i < kOzTG * kOzD / kOzThreads; i++) {
-            uint32_t gg, w;
-            elem(uint32_t(tid + i * kOzThreads), gg, w);
-            const uint64_t x0 = x[gg];
+        for (int i = 0; i < kOzElemsPerThread; i++) {
+            const uint64_t x0 = x[el_g[i]];
             const bool ok = x0 != ~0ull;
-            cp_async16(base + raw_slot(gg, w) * 16, ok ? psi + x0 + P.offs[w] : psi, ok);
+            cp_async16(base + el_slot[i] * 16, ok ? psi + x0 + el_off[i] : psi, ok);
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    auto slice = [&](uint64_t j) {  // raw(j) -> state slices abuf(j), scales nu[j & 1]
-        const float4* rw = raw(j);
-        float4 v[kOzAmpsPerThread];
+    auto slice = [&]() {  // raw -> state slices in abuf, scales nu
         float m = 0.f;
 #pragma unroll
         for (int i = 0; i < kOzAmpsPerThread; i++) {
-            v[i] = rw[raw_slot(g, q * kOzAmpsPerThread + i)];
-            m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].z)));
+            const float4 v = raw[raw_slot(g, h * kOzAmpsPerThread + i)];
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.z)));
         }
-        nu_part[q * kOzTG + g] = m;
+        nu_part[h * kOzTG + g] = m;
         __syncthreads();
-        m = fmaxf(fmaxf(nu_part[g], nu_part[kOzTG + g]), fmaxf(nu_part[2 * kOzTG + g], nu_part[3 * kOzTG + g]));
+        m = fmaxf(nu_part[g], nu_part[kOzTG + g]);
         const float nv = pow2_ceil(m);
-        if (q == 0) nu[(j & 1) * kOzTG + g] = nv;
+        if (h == 0) nu[g] = nv;
         const float inv = __uint_as_float((254u - (__float_as_uint(nv) >> 23)) << 23);
-        uint32_t pk[kOzNS][kOzAmpsPerThread];
+        // two passes of 4 amplitudes = K columns 16h + 8c .. 16h + 8c + 7: one 16-byte chunk per slice
 #pragma unroll
-        for (int i = 0; i < kOzAmpsPerThread; i++) {
-            float ar[kOzNS], ai[kOzNS];
-            slice6(v[i].x, v[i].y, inv, ar);
-            slice6(v[i].z, v[i].w, inv, ai);
+        for (int c = 0; c < 2; c++) {
+            uint32_t pk[kOzNS][4];
 #pragma unroll
-            for (int s = 0; s < kOzNS; s++) pk[s][i] = pack_bf16(ar[s], ai[s]);
+            for (int i = 0; i < 4; i++) {
+                const float4 v = raw[raw_slot(g, h * kOzAmpsPerThread + 4 * c + i)];
+                float ar[kOzNS], ai[kOzNS];
+                slice6(v.x, v.y, inv, ar);
+                slice6(v.z, v.w, inv, ai);
+#pragma unroll
+                for (int s = 0; s < kOzNS; s++) pk[s][i] = pack_bf16(ar[s], ai[s]);
+            }
+            const uint32_t off = kmaj(uint32_t(g), uint32_t(16 * h + 8 * c));
+#pragma unroll
+            for (int s = 0; s < kOzNS; s++)
+                *reinterpret_cast<uint4*>(abuf + s * kOzSlice + off) = make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
         }
-        // this thread's 4 amplitudes are K = 8q .. 8q+7 of row g: one 16-byte chunk per slice
-        unsigned char* ab = abuf(j);
-        const uint32_t off = kmaj(uint32_t(g), uint32_t(8 * q));
-#pragma unroll
-        for (int s = 0; s < kOzNS; s++)
-            *reinterpret_cast<uint4*>(ab + s * kOzSlice + off) = make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     };
-    auto issue = [&](uint64_t j) {  // MMAs of tile j into accumulator set j & 1
+    auto issue = [&]() {  // MMAs of the tile into the accumulator set
         if (tid != 0) return;
-        const uint32_t d0 = tmem + uint32_t((j & 1) * kOzAccCols);
-        const uint32_t a0 = smem_u32(abuf(j)), m0 = smem_u32(smem + kOffMat);
+        const uint32_t a0 = smem_u32(abuf), m0 = smem_u32(smem + kOffMat);
         // state slice s times matrix slices t = t0 .. t0 + nt - 1 into diagonals s + t
         auto prod = [&](int s, int t0, int nt, int ks, uint32_t acc) {
-            mma_bf16(d0 + uint32_t((s + t0) * kOzR), sdesc(a0 + uint32_t(s * kOzSlice) + uint32_t(ks * 256)),
+            mma_bf16(tmem + uint32_t((s + t0) * kOzR), sdesc(a0 + uint32_t(s * kOzSlice) + uint32_t(ks * 256)),
                      sdesc(m0 + uint32_t(t0 * kOzR / 8) * kOzSbo + uint32_t(ks * 256)), idesc(uint32_t(nt * kOzR)), acc);
         };
 #pragma unroll
@@ -282,51 +290,51 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_dense_oz4(float4* __restrict_
 #pragma unroll
             for (int s = 2; s < kOzNS; s++) prod(s, 0, kOzND - s < kOzNS ? kOzND - s : kOzNS, ks, 1u);
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(&mbar[j & 1])));
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar)));
     };
-    auto epilogue = [&](uint64_t j) {  // accumulator set j & 1 -> staging abuf(j)
-        const int b = int(j & 1);
+    auto epilogue = [&]() {  // accumulators -> double-float outputs in the staging area (abuf)
         const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
-        uint32_t r[kOzND][8];
+        const float nv = nu[g];
+        float4* stg = reinterpret_cast<float4*>(abuf);
 #pragma unroll
-        for (int d = 0; d < kOzND; d++) {
-            const uint32_t taddr = tmem + lane_base + uint32_t(b * kOzAccCols + d * kOzR + 8 * q);
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                         : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3]), "=r"(r[d][4]), "=r"(r[d][5]),
-                           "=r"(r[d][6]), "=r"(r[d][7])
-                         : "r"(taddr));
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const float nv = nu[b * kOzTG + g];
-        float4* stg = reinterpret_cast<float4*>(abuf(b));
+        for (int c = 0; c < 2; c++) {
+            const int col0 = 16 * h + 8 * c;  // 8 output reals = 4 amplitudes
+            uint32_t r[kOzND][8];
 #pragma unroll
-        for (int i = 0; i < kOzAmpsPerThread; i++) {
-            float o[4];
-#pragma unroll
-            for (int c = 0; c < 2; c++) {
-                const int col = 2 * i + c;
-                float s = __uint_as_float(r[kOzND - 1][col]), lo = 0.f, t;
-#pragma unroll
-                for (int d = kOzND - 2; d >= 0; d--) {
-                    fast_two_sum(__uint_as_float(r[d][col]), s, s, t);
-                    lo = __fadd_rn(lo, t);
-                }
-                const float sc = __fmul_rn(mu[8 * q + col], nv);
-                fast_two_sum(__fmul_rn(s, sc), __fmul_rn(lo, sc), o[2 * c], o[2 * c + 1]);
+            for (int d = 0; d < kOzND; d++) {
+                const uint32_t taddr = tmem + lane_base + uint32_t(d * kOzR + col0);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3]), "=r"(r[d][4]),
+                               "=r"(r[d][5]), "=r"(r[d][6]), "=r"(r[d][7])
+                             : "r"(taddr));
             }
-            stg[raw_slot(g, q * kOzAmpsPerThread + i)] = make_float4(o[0], o[1], o[2], o[3]);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                float o[4];
+#pragma unroll
+                for (int cc = 0; cc < 2; cc++) {
+                    const int col = 2 * i + cc;
+                    float sm = __uint_as_float(r[kOzND - 1][col]), lo = 0.f, t;
+#pragma unroll
+                    for (int d = kOzND - 2; d >= 0; d--) {
+                        fast_two_sum(__uint_as_float(r[d][col]), sm, sm, t);
+                        lo = __fadd_rn(lo, t);
+                    }
+                    const float sc = __fmul_rn(mu[col0 + col], nv);
+                    fast_two_sum(__fmul_rn(sm, sc), __fmul_rn(lo, sc), o[2 * cc], o[2 * cc + 1]);
+                }
+                stg[raw_slot(g, (col0 >> 1) + i)] = make_float4(o[0], o[1], o[2], o[3]);
+            }
         }
     };
-    auto store = [&](uint64_t j) {  // staging abuf(j) -> the state, coalesced
-        const uint64_t* x = x0s + (j % 3) * kOzTG;
-        const float4* stg = reinterpret_cast<const float4*>(abuf(j));
+    auto store = [&](uint64_t j) {  // staging -> the state, coalesced
+        const uint64_t* x = x0s + (j & 1) * kOzTG;
+        const float4* stg = reinterpret_cast<const float4*>(abuf);
 #pragma unroll
-        for (int i = 0; i < kOzTG * kOzD / kOzThreads; i++) {
-            uint32_t gg, w;
-            elem(uint32_t(tid + i * kOzThreads), gg, w);
-            const uint64_t x0 = x[gg];
-            if (x0 != ~0ull) psi[x0 + P.offs[w]] = stg[raw_slot(gg, w)];
+        for (int i = 0; i < kOzElemsPerThread; i++) {
+            const uint64_t x0 = x[el_g[i]];
+            if (x0 != ~0ull) psi[x0 + el_off[i]] = stg[el_slot[i]];
         }
     };
 
@@ -335,40 +343,33 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_dense_oz4(float4* __restrict_
         __syncthreads();
         load(0);
     }
-    for (uint64_t j = 0; j <= my_tiles && my_tiles > 0; j++) {
-        if (j < my_tiles) {
-            asm volatile("cp.async.wait_all;" ::: "memory");
+    for (uint64_t j = 0; j < my_tiles; j++) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();  // raw holds tile j; the staging area of tile j - 1 has been stored
+        slice();
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        issue();
+        if (j + 1 < my_tiles) {  // raw is free: fetch the next tile while the tensor cores work
+            fill_x0(j + 1);
             __syncthreads();
-            slice(j);
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            issue(j);
-            if (j + 1 < my_tiles) {
-                fill_x0(j + 1);
-                __syncthreads();
-                load(j + 1);
-            }
+            load(j + 1);
         }
-        if (j >= 1) {
-            const uint64_t p = j - 1;
-            if (tid == 0 && !mbar_wait(smem_u32(&mbar[p & 1]), uint32_t((p >> 1) & 1))) s_fail = 1;
-            __syncthreads();
-            if (s_fail) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            epilogue(p);
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-            store(p);
-            __syncthreads();
-        }
+        if (tid == 0 && !mbar_wait(smem_u32(&mbar), uint32_t(j & 1))) s_fail = 1;
+        __syncthreads();
+        if (s_fail) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        epilogue();
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        store(j);
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     if (s_fail && tid == 0) {
         atomicExch(err, 1);
-        // let every committed MMA finish before TMEM is released (bounded)
-        mbar_wait(smem_u32(&mbar[0]), 0);
-        mbar_wait(smem_u32(&mbar[1]), 0);
+        mbar_wait(smem_u32(&mbar), 0);  // bounded: let the MMAs in flight finish before TMEM is freed
+        mbar_wait(smem_u32(&mbar), 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -459,7 +460,7 @@ void launch_dense_oz4(void* psi, int n, const std::vector<int>& targets, const s
     P.low = low;
     P.n_groups = P.ip.n_iter;
     const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
-    const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, uint64_t(g_oz_sms))));
+    const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, 2 * uint64_t(g_oz_sms))));
     k_dense_oz4<<<grid, kOzThreads, kOzSmem, st>>>(reinterpret_cast<float4*>(psi),
                                                    static_cast<const unsigned char*>(dmat), P, g_oz_err);
     QS_TRY_CUDA(cudaGetLastError());
