@@ -38,9 +38,11 @@ METRIC = "state-vector GB/s & gates/s at n=30 c128 vs HBM peak; adjoint-grad ms;
 HBM_PEAK_FALLBACK = 6800.0
 # DRAM bytes (read + write) per launch from one ncu capture, keyed by kernel; filled in only
 # for a kernel unchanged since the capture (profiles/<kernel>_<workload>.md gives the command).
-# k_dense_reg<DFArith, 2>: captured at n = 27 (2 GiB state, 4.233e9 bytes per launch); its
-# traffic grows with the state, so the n = 30 entry is that figure times 8.
-NCU_TRAFFIC = {("dense_df", 27): 4232672512, ("dense_df", 30): 4232672512 * 8}
+# k_dense_reg<DFArith, 2>: captured at n = 27 (2 GiB state, 4.233e9 bytes per launch);
+# k_dense_oz4: captured at n = 24 (256 MiB state, 4.760e8 bytes per launch). Traffic grows with
+# the state, so the n = 30 entries are those figures times 8 and 64.
+NCU_TRAFFIC = {("dense_df", 27): 4232672512, ("dense_df", 30): 4232672512 * 8,
+               ("dense_oz", 24): 476010496, ("dense_oz", 30): 476010496 * 64}
 
 
 def parse():
@@ -372,6 +374,19 @@ def measure_extras(args, qs, torch, circuit):
     st = qs.State(n, qs.QS_C128)
     ms = timed(lambda: (st.set_basis(0), st.run(circuit, 0)))
     out["c128_unfused_gates_per_s"] = G / (ms / 1e3)
+    # the same circuit fused on the CUDA cores (double-float, tensor cores off) and with plain
+    # FP64 arithmetic, each at its own autotuned width
+    old_tc, old_math = qs.get_tensor_cores(), qs.get_c128_math()
+    for label, tc, math_mode in (("c128_df_cuda_cores", 0, qs.QS_MATH_DF), ("c128_fp64", 0, qs.QS_MATH_FP64)):
+        qs.set_tensor_cores(tc)
+        qs.set_c128_math(math_mode)
+        kk, _ = qs.autotune_fusion(circuit, qs.QS_C128)
+        pl = qs.FusedCircuit(circuit, max(kk, 1))
+        ms = timed(lambda: (st.set_basis(0), st.apply_plan(pl)))
+        out[label + "_gates_per_s"] = G / (ms / 1e3)
+        out[label + "_fusion_k"] = kk
+    qs.set_tensor_cores(old_tc)
+    qs.set_c128_math(old_math)
     del st
     torch.cuda.empty_cache()
     st = qs.State(n, qs.QS_C64)
@@ -433,11 +448,13 @@ def measure_extras(args, qs, torch, circuit):
                             "norm2_c64": c.norm2(), "norm2_c128": a.norm2()}
     del a, c
     torch.cuda.empty_cache()
-    # n = 33 complex128 (128 GiB state), same circuit family at depth 20, fused k = 2
+    # n = 33 complex128 (128 GiB state), same circuit family at depth 20, autotuned width
     try:
         c33 = W.u3cz_circuit(33, args.depth, args.seed)
         s33 = qs.State(33, qs.QS_C128)
-        plan33 = qs.FusedCircuit(c33, 2)
+        k33, _ = qs.autotune_fusion(c33, qs.QS_C128)
+        plan33 = qs.FusedCircuit(c33, max(k33, 1))
+        out["c128_n33_fusion_k"] = k33
         ms33 = timed(lambda: (s33.set_basis(0), s33.apply_plan(plan33)))
         out["c128_n33_gates_per_s"] = len(c33.gates) / (ms33 / 1e3)
         out["c128_n33_ms"] = ms33

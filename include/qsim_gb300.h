@@ -153,7 +153,8 @@ qs_status qs_get_c128_math(int* mode);
  *   (the splitting of Ozaki, Ogita, Oishi and Rump); the 21 slice products of weight >= 2^-48
  *   are summed exactly in FP32 by tcgen05.mma kind::f16 and combined exactly in double-float:
  *   about 2^-45 relative error per block, the accuracy of the double-float CUDA-core kernels.
- * Unknown bits -> QS_ERR_INVALID_ARG. Default: none. */
+ * Unknown bits -> QS_ERR_INVALID_ARG. Default: QS_TENSOR_C128 (its blocks meet the complex128
+ * bound; the complex64 path stays opt-in because of its norm drift). */
 #define QS_TENSOR_C64 1
 #define QS_TENSOR_C128 2
 qs_status qs_set_tensor_cores(int mask);

@@ -21,7 +21,7 @@ namespace qs {
 namespace {
 thread_local std::string g_err;
 std::atomic<int> g_c128_math{QS_MATH_FP64};
-std::atomic<int> g_tensor{0};  // QS_TENSOR_* bits
+std::atomic<int> g_tensor{QS_TENSOR_C128};  // QS_TENSOR_* bits
 }  // namespace
 
 bool tensor_c64_enabled() { return (g_tensor.load() & QS_TENSOR_C64) != 0; }

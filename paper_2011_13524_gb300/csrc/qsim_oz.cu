@@ -76,6 +76,7 @@ struct OzParams {
     uint64_t offs[kOzD];     // s(w), targets ascending
     uint64_t n_groups;
     int low;                 // targets 0..low-1 are qubits 0..low-1 (coalescing)
+    int swz;                 // swizzle shift of the staging slots: max(0, 3 - low)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -84,8 +85,12 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return static_cast
 __device__ __forceinline__ uint32_t kmaj(uint32_t r, uint32_t k) {
     return (r >> 3) * kOzSbo + (k >> 3) * kOzLbo + (r & 7) * 16 + (k & 7) * 2;
 }
-// raw / staging slot of (group g, amplitude w): w-major, XOR-swizzled in 16-byte units
-__device__ __forceinline__ uint32_t raw_slot(uint32_t g, uint32_t w) { return w * kOzTG + (g ^ (w & 7)); }
+// raw / staging slot of (group g, amplitude w): w-major, XOR-swizzled in 16-byte units so that
+// eight consecutive lanes hit eight bank groups both when they share w (consecutive g) and when
+// they run over the 2^low low amplitudes of 8 / 2^low groups (the coalesced load order)
+__device__ __forceinline__ uint32_t raw_slot(uint32_t g, uint32_t w, int swz) {
+    return w * kOzTG + (g ^ ((w << swz) & 7));
+}
 
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     uint64_t d = uint64_t((saddr >> 4) & 0x3FFF);
@@ -175,6 +180,7 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int g = tid & (kOzTG - 1), h = tid >> 7;  // group and amplitude half of this thread
+    const int swz = P.swz;
     float4* raw = reinterpret_cast<float4*>(smem + kOffRaw);
     unsigned char* abuf = smem + kOffA;
     const float* mu = reinterpret_cast<const float*>(smem + kOffMu);
@@ -213,7 +219,7 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
             const uint32_t wl = e & lowmask, rest = e >> P.low;
             const uint32_t gg = rest & (kOzTG - 1), w = ((rest >> 7) << P.low) | wl;
             el_g[i] = gg;
-            el_slot[i] = raw_slot(gg, w);
+            el_slot[i] = raw_slot(gg, w, swz);
             el_off[i] = P.offs[w];
         }
     }
@@ -235,11 +241,12 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    auto slice = [&]() {  // raw -> state slices in abuf, scales nu
+    auto slice = [&](uint64_t j) {  // raw -> state slices in abuf, scales nu; x0 list of tile j + 1
+        if (j + 1 < my_tiles) fill_x0(j + 1);
         float m = 0.f;
 #pragma unroll
         for (int i = 0; i < kOzAmpsPerThread; i++) {
-            const float4 v = raw[raw_slot(g, h * kOzAmpsPerThread + i)];
+            const float4 v = raw[raw_slot(g, h * kOzAmpsPerThread + i, swz)];
             m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.z)));
         }
         nu_part[h * kOzTG + g] = m;
@@ -254,7 +261,7 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
             uint32_t pk[kOzNS][4];
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-                const float4 v = raw[raw_slot(g, h * kOzAmpsPerThread + 4 * c + i)];
+                const float4 v = raw[raw_slot(g, h * kOzAmpsPerThread + 4 * c + i, swz)];
                 float ar[kOzNS], ai[kOzNS];
                 slice6(v.x, v.y, inv, ar);
                 slice6(v.z, v.w, inv, ai);
@@ -324,7 +331,7 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
                     const float sc = __fmul_rn(mu[col0 + col], nv);
                     fast_two_sum(__fmul_rn(sm, sc), __fmul_rn(lo, sc), o[2 * cc], o[2 * cc + 1]);
                 }
-                stg[raw_slot(g, (col0 >> 1) + i)] = make_float4(o[0], o[1], o[2], o[3]);
+                stg[raw_slot(g, (col0 >> 1) + i, swz)] = make_float4(o[0], o[1], o[2], o[3]);
             }
         }
     };
@@ -346,16 +353,12 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
     for (uint64_t j = 0; j < my_tiles; j++) {
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();  // raw holds tile j; the staging area of tile j - 1 has been stored
-        slice();
+        slice(j);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         issue();
-        if (j + 1 < my_tiles) {  // raw is free: fetch the next tile while the tensor cores work
-            fill_x0(j + 1);
-            __syncthreads();
-            load(j + 1);
-        }
+        if (j + 1 < my_tiles) load(j + 1);  // raw is free: fetch the next tile while the tensor cores work
         if (tid == 0 && !mbar_wait(smem_u32(&mbar), uint32_t(j & 1))) s_fail = 1;
         __syncthreads();
         if (s_fail) break;
@@ -458,6 +461,7 @@ void launch_dense_oz4(void* psi, int n, const std::vector<int>& targets, const s
     int low = 0;
     while (low < kOzQ && targets[low] == low) low++;
     P.low = low;
+    P.swz = low >= 3 ? 0 : 3 - low;
     P.n_groups = P.ip.n_iter;
     const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, 2 * uint64_t(g_oz_sms))));
