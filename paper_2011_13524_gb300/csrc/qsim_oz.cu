@@ -23,12 +23,14 @@
 // its products: columns (s + t) * 32 of the accumulator block receive A_s B_t, so a single
 // MMA with N = 32 * min(6, 7 - s) feeds diagonals s..min(s + 5, 6).
 //
-// Pipeline: two CTAs per SM (256 threads, ~95 KB of shared memory and 256 TMEM columns
-// each), so that one CTA's tensor-core and memory phases overlap the other's CUDA-core work.
-// Within a CTA: slice tile j, start its MMAs, start the cp.async loads of tile j + 1, then
-// read the accumulators (TMEM -> double-float -> shared staging) and store tile j coalesced.
-// Every mbarrier wait is bounded; on expiry the kernel records an error, waits (bounded) for
-// its MMAs and frees TMEM.
+// Pipeline: two CTAs per SM (256 threads, ~110 KB of shared memory and 256 TMEM columns each).
+// A thread owns half of one group (8 amplitudes): it loads them straight into registers,
+// slices them, and later writes that half's outputs straight back, so no staging copies are
+// needed (for low targets the loads and stores are strided; the rest of each 32-byte sector is
+// touched by the same thread and served by L2). Per tile j: the loads of tile j + 1 are issued,
+// tile j is sliced into the second slice buffer while the MMAs of tile j - 1 run, tile j - 1's
+// accumulators are folded and stored, and the MMAs of tile j start. Every mbarrier wait is
+// bounded; on expiry the kernel records an error, waits (bounded) for its MMAs and frees TMEM.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -47,36 +49,28 @@ constexpr int kOzNS = 6;                // slices per operand
 constexpr int kOzND = 7;                // accumulated diagonals d = s + t <= 6
 constexpr int kOzThreads = 256;                                // two CTAs per SM
 constexpr int kOzAmpsPerThread = kOzD / (kOzThreads / kOzTG);  // 8
-constexpr int kOzElemsPerThread = kOzTG * kOzD / kOzThreads;   // 8 loads / stores per tile
 constexpr uint32_t kOzSbo = (kOzR / 8) * 128;                  // 8-row group stride (K-major)
 constexpr uint32_t kOzLbo = 128;
 constexpr size_t kOzSlice = size_t(kOzTG) * kOzR * 2;          // one state slice, bf16
 constexpr size_t kOzABuf = kOzNS * kOzSlice;                   // 48 KB
-constexpr size_t kOzRaw = size_t(kOzTG) * kOzD * 16;           // 32 KB of double-float amplitudes
 constexpr size_t kOzMat = size_t(kOzNS) * kOzR * kOzR * 2;     // 12 KB
 constexpr int kOzAccCols = kOzND * kOzR;                       // 224 columns per accumulator set
 constexpr int kOzTmemCols = 256;                               // one set, rounded to a power of 2
 constexpr long long kOzSpinLimit = 1ll << 22;
 
-static_assert(kOzABuf >= kOzRaw, "output staging reuses a slice buffer");
 static_assert(kOzAccCols <= kOzTmemCols, "accumulators fit the TMEM allocation");
 
-// shared-memory plan (bytes), ~95 KB: two CTAs per SM
-constexpr size_t kOffRaw = 0;                           // 32 KB
-constexpr size_t kOffA = kOffRaw + kOzRaw;              // 48 KB (slices, then output staging)
-constexpr size_t kOffMat = kOffA + kOzABuf;             // 12 KB
+// shared-memory plan (bytes), ~110 KB: two CTAs per SM
+constexpr size_t kOffA = 0;                             // 2 x 48 KB state slices
+constexpr size_t kOffMat = kOffA + 2 * kOzABuf;         // 12 KB
 constexpr size_t kOffMu = kOffMat + kOzMat;             // 32 floats
-constexpr size_t kOffNu = kOffMu + kOzR * 4;            // 128 floats
-constexpr size_t kOffNuPart = kOffNu + kOzTG * 4;       // 2 x 128 floats
-constexpr size_t kOffX0 = kOffNuPart + 2 * kOzTG * 4;   // 2 x 128 uint64
-constexpr size_t kOzSmem = kOffX0 + 2 * kOzTG * 8;
+constexpr size_t kOffNuPart = kOffMu + kOzR * 4;        // 2 x 128 floats
+constexpr size_t kOzSmem = kOffNuPart + 2 * kOzTG * 4;
 
 struct OzParams {
     IndexPlan ip;            // 4 targets (and controls) inserted
     uint64_t offs[kOzD];     // s(w), targets ascending
     uint64_t n_groups;
-    int low;                 // targets 0..low-1 are qubits 0..low-1 (coalescing)
-    int swz;                 // swizzle shift of the staging slots: max(0, 3 - low)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -85,13 +79,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return static_cast
 __device__ __forceinline__ uint32_t kmaj(uint32_t r, uint32_t k) {
     return (r >> 3) * kOzSbo + (k >> 3) * kOzLbo + (r & 7) * 16 + (k & 7) * 2;
 }
-// raw / staging slot of (group g, amplitude w): w-major, XOR-swizzled in 16-byte units so that
-// eight consecutive lanes hit eight bank groups both when they share w (consecutive g) and when
-// they run over the 2^low low amplitudes of 8 / 2^low groups (the coalesced load order)
-__device__ __forceinline__ uint32_t raw_slot(uint32_t g, uint32_t w, int swz) {
-    return w * kOzTG + (g ^ ((w << swz) & 7));
-}
-
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     uint64_t d = uint64_t((saddr >> 4) & 0x3FFF);
     d |= uint64_t((kOzLbo >> 4) & 0x3FFF) << 16;
@@ -122,10 +109,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
         if (done) return true;
     }
     return false;
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
 }
 
 // value rounded to a multiple of 2^-8(s+1) (|x| <= 2^(14-8s)); the magic constant is
@@ -179,14 +162,11 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int g = tid & (kOzTG - 1), h = tid >> 7;  // group and amplitude half of this thread
-    const int swz = P.swz;
-    float4* raw = reinterpret_cast<float4*>(smem + kOffRaw);
-    unsigned char* abuf = smem + kOffA;
+    // thread (g, h): group g of the tile (= TMEM lane), amplitudes 8h .. 8h + 7
+    const int g = tid & (kOzTG - 1), h = tid >> 7;
     const float* mu = reinterpret_cast<const float*>(smem + kOffMu);
-    float* nu = reinterpret_cast<float*>(smem + kOffNu);
     float* nu_part = reinterpret_cast<float*>(smem + kOffNuPart);
-    uint64_t* x0s = reinterpret_cast<uint64_t*>(smem + kOffX0);
+    auto abuf = [&](uint64_t j) { return smem + kOffA + (j & 1) * kOzABuf; };
 
     // matrix slices (stacked, already in the K-major layout) and row scales, once per CTA
     for (int i = tid; i < int((kOzMat + kOzR * 4) / 16); i += kOzThreads)
@@ -206,81 +186,55 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
     const uint32_t tmem = tmem_base;
     const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
     const uint64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    uint64_t off[kOzAmpsPerThread];  // s(w) of this thread's amplitudes
+#pragma unroll
+    for (int i = 0; i < kOzAmpsPerThread; i++) off[i] = P.offs[h * kOzAmpsPerThread + i];
 
-    // this thread's loads / stores of a tile: element e -> (group, amplitude) with consecutive e
-    // at consecutive addresses where the low targets allow it; fixed for every tile
-    uint32_t el_g[kOzElemsPerThread], el_slot[kOzElemsPerThread];
-    uint64_t el_off[kOzElemsPerThread];
-    {
-        const uint32_t lowmask = (1u << P.low) - 1u;
-#pragma unroll
-        for (int i = 0; i < kOzElemsPerThread; i++) {
-            const uint32_t e = uint32_t(tid + i * kOzThreads);
-            const uint32_t wl = e & lowmask, rest = e >> P.low;
-            const uint32_t gg = rest & (kOzTG - 1), w = ((rest >> 7) << P.low) | wl;
-            el_g[i] = gg;
-            el_slot[i] = raw_slot(gg, w, swz);
-            el_off[i] = P.offs[w];
-        }
-    }
-    auto fill_x0 = [&](uint64_t j) {
-        const uint64_t tile = blockIdx.x + j * gridDim.x;
-        if (tid < kOzTG) {
-            const uint64_t gi = tile * kOzTG + tid;
-            x0s[(j & 1) * kOzTG + tid] = gi < P.n_groups ? expand(gi, P.ip) : ~0ull;
-        }
+    auto group_x0 = [&](uint64_t j) {  // this thread's group in tile j (~0 past the end)
+        const uint64_t gi = (blockIdx.x + j * gridDim.x) * kOzTG + uint64_t(g);
+        return gi < P.n_groups ? expand(gi, P.ip) : ~0ull;
     };
-    auto load = [&](uint64_t j) {  // cp.async of tile j into raw (x0 list ready)
-        const uint64_t* x = x0s + (j & 1) * kOzTG;
-        const uint32_t base = smem_u32(raw);
+    auto load = [&](uint64_t x0, float4 (&v)[kOzAmpsPerThread]) {
 #pragma unroll
-        for (int i = 0; i < kOzElemsPerThread; i++) {
-            const uint64_t x0 = x[el_g[i]];
-            const bool ok = x0 != ~0ull;
-            cp_async16(base + el_slot[i] * 16, ok ? psi + x0 + el_off[i] : psi, ok);
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
+        for (int i = 0; i < kOzAmpsPerThread; i++)
+            v[i] = x0 != ~0ull ? psi[x0 + off[i]] : make_float4(0.f, 0.f, 0.f, 0.f);
     };
-    auto slice = [&](uint64_t j) {  // raw -> state slices in abuf, scales nu; x0 list of tile j + 1
-        if (j + 1 < my_tiles) fill_x0(j + 1);
+    // slices of this thread's amplitudes into abuf(j); returns the group scale nu
+    auto slice = [&](uint64_t j, const float4 (&v)[kOzAmpsPerThread]) {
         float m = 0.f;
 #pragma unroll
-        for (int i = 0; i < kOzAmpsPerThread; i++) {
-            const float4 v = raw[raw_slot(g, h * kOzAmpsPerThread + i, swz)];
-            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.z)));
-        }
+        for (int i = 0; i < kOzAmpsPerThread; i++) m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].z)));
         nu_part[h * kOzTG + g] = m;
         __syncthreads();
         m = fmaxf(nu_part[g], nu_part[kOzTG + g]);
         const float nv = pow2_ceil(m);
-        if (h == 0) nu[g] = nv;
         const float inv = __uint_as_float((254u - (__float_as_uint(nv) >> 23)) << 23);
-        // two passes of 4 amplitudes = K columns 16h + 8c .. 16h + 8c + 7: one 16-byte chunk per slice
+        unsigned char* ab = abuf(j);
 #pragma unroll
-        for (int c = 0; c < 2; c++) {
+        for (int c = 0; c < 2; c++) {  // 4 amplitudes = K columns 16h + 8c .. +7: one 16-byte chunk per slice
             uint32_t pk[kOzNS][4];
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-                const float4 v = raw[raw_slot(g, h * kOzAmpsPerThread + 4 * c + i, swz)];
                 float ar[kOzNS], ai[kOzNS];
-                slice6(v.x, v.y, inv, ar);
-                slice6(v.z, v.w, inv, ai);
+                slice6(v[4 * c + i].x, v[4 * c + i].y, inv, ar);
+                slice6(v[4 * c + i].z, v[4 * c + i].w, inv, ai);
 #pragma unroll
-                for (int s = 0; s < kOzNS; s++) pk[s][i] = pack_bf16(ar[s], ai[s]);
+                for (int s2 = 0; s2 < kOzNS; s2++) pk[s2][i] = pack_bf16(ar[s2], ai[s2]);
             }
-            const uint32_t off = kmaj(uint32_t(g), uint32_t(16 * h + 8 * c));
+            const uint32_t o = kmaj(uint32_t(g), uint32_t(16 * h + 8 * c));
 #pragma unroll
-            for (int s = 0; s < kOzNS; s++)
-                *reinterpret_cast<uint4*>(abuf + s * kOzSlice + off) = make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
+            for (int s2 = 0; s2 < kOzNS; s2++)
+                *reinterpret_cast<uint4*>(ab + s2 * kOzSlice + o) = make_uint4(pk[s2][0], pk[s2][1], pk[s2][2], pk[s2][3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        return nv;
     };
-    auto issue = [&]() {  // MMAs of the tile into the accumulator set
+    auto issue = [&](uint64_t j) {  // MMAs of tile j into the accumulator set
         if (tid != 0) return;
-        const uint32_t a0 = smem_u32(abuf), m0 = smem_u32(smem + kOffMat);
-        // state slice s times matrix slices t = t0 .. t0 + nt - 1 into diagonals s + t
-        auto prod = [&](int s, int t0, int nt, int ks, uint32_t acc) {
-            mma_bf16(tmem + uint32_t((s + t0) * kOzR), sdesc(a0 + uint32_t(s * kOzSlice) + uint32_t(ks * 256)),
+        const uint32_t a0 = smem_u32(abuf(j)), m0 = smem_u32(smem + kOffMat);
+        // state slice s times matrix slices t0 .. t0 + nt - 1 into diagonals s + t
+        auto prod = [&](int s2, int t0, int nt, int ks, uint32_t acc) {
+            mma_bf16(tmem + uint32_t((s2 + t0) * kOzR), sdesc(a0 + uint32_t(s2 * kOzSlice) + uint32_t(ks * 256)),
                      sdesc(m0 + uint32_t(t0 * kOzR / 8) * kOzSbo + uint32_t(ks * 256)), idesc(uint32_t(nt * kOzR)), acc);
         };
 #pragma unroll
@@ -295,29 +249,27 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
                 prod(1, 0, kOzNS, ks, 1u);
             }
 #pragma unroll
-            for (int s = 2; s < kOzNS; s++) prod(s, 0, kOzND - s < kOzNS ? kOzND - s : kOzNS, ks, 1u);
+            for (int s2 = 2; s2 < kOzNS; s2++) prod(s2, 0, kOzND - s2 < kOzNS ? kOzND - s2 : kOzNS, ks, 1u);
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar)));
     };
-    auto epilogue = [&]() {  // accumulators -> double-float outputs in the staging area (abuf)
+    // accumulators -> double-float outputs, stored straight to the state
+    auto epilogue = [&](uint64_t x0, float nv) {
         const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
-        const float nv = nu[g];
-        float4* stg = reinterpret_cast<float4*>(abuf);
 #pragma unroll
-        for (int c = 0; c < 2; c++) {
-            const int col0 = 16 * h + 8 * c;  // 8 output reals = 4 amplitudes
-            uint32_t r[kOzND][8];
+        for (int c = 0; c < 4; c++) {
+            const int col0 = 16 * h + 4 * c;  // 4 output reals = 2 amplitudes
+            uint32_t r[kOzND][4];
 #pragma unroll
             for (int d = 0; d < kOzND; d++) {
                 const uint32_t taddr = tmem + lane_base + uint32_t(d * kOzR + col0);
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                             : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3]), "=r"(r[d][4]),
-                               "=r"(r[d][5]), "=r"(r[d][6]), "=r"(r[d][7])
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                             : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3])
                              : "r"(taddr));
             }
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int i = 0; i < 4; i++) {
+            for (int i = 0; i < 2; i++) {
                 float o[4];
 #pragma unroll
                 for (int cc = 0; cc < 2; cc++) {
@@ -331,44 +283,45 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
                     const float sc = __fmul_rn(mu[col0 + col], nv);
                     fast_two_sum(__fmul_rn(sm, sc), __fmul_rn(lo, sc), o[2 * cc], o[2 * cc + 1]);
                 }
-                stg[raw_slot(g, (col0 >> 1) + i, swz)] = make_float4(o[0], o[1], o[2], o[3]);
+                if (x0 != ~0ull) psi[x0 + off[2 * c + i]] = make_float4(o[0], o[1], o[2], o[3]);
             }
         }
     };
-    auto store = [&](uint64_t j) {  // staging -> the state, coalesced
-        const uint64_t* x = x0s + (j & 1) * kOzTG;
-        const float4* stg = reinterpret_cast<const float4*>(abuf);
-#pragma unroll
-        for (int i = 0; i < kOzElemsPerThread; i++) {
-            const uint64_t x0 = x[el_g[i]];
-            if (x0 != ~0ull) psi[x0 + el_off[i]] = stg[el_slot[i]];
-        }
-    };
 
+    // software pipeline: loads of tile j + 1 and the slices of tile j overlap the MMAs of tile
+    // j - 1; then tile j - 1 is finished and the MMAs of tile j start
+    float4 vcur[kOzAmpsPerThread], vnext[kOzAmpsPerThread];
+    uint64_t x0_cur = 0, x0_prev = 0;
+    float nv_prev = 1.f;
     if (my_tiles > 0) {
-        fill_x0(0);
-        __syncthreads();
-        load(0);
+        x0_cur = group_x0(0);
+        load(x0_cur, vcur);
     }
-    for (uint64_t j = 0; j < my_tiles; j++) {
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncthreads();  // raw holds tile j; the staging area of tile j - 1 has been stored
-        slice(j);
+    for (uint64_t j = 0; j <= my_tiles && my_tiles > 0; j++) {
+        uint64_t x0_next = 0;
+        if (j + 1 < my_tiles) {
+            x0_next = group_x0(j + 1);
+            load(x0_next, vnext);
+        }
+        float nv_cur = 1.f;
+        if (j < my_tiles) nv_cur = slice(j, vcur);  // abuf(j) was read by the MMAs of tile j - 2
+        if (j >= 1) {
+            if (tid == 0 && !mbar_wait(smem_u32(&mbar), uint32_t((j - 1) & 1))) s_fail = 1;
+            __syncthreads();
+            if (s_fail) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            epilogue(x0_prev, nv_prev);
+        }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        __syncthreads();  // slices of tile j written; accumulators of tile j - 1 read
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        issue();
-        if (j + 1 < my_tiles) load(j + 1);  // raw is free: fetch the next tile while the tensor cores work
-        if (tid == 0 && !mbar_wait(smem_u32(&mbar), uint32_t(j & 1))) s_fail = 1;
-        __syncthreads();
-        if (s_fail) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        epilogue();
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        store(j);
+        if (j < my_tiles) issue(j);
+        x0_prev = x0_cur;
+        nv_prev = nv_cur;
+        x0_cur = x0_next;
+#pragma unroll
+        for (int i = 0; i < kOzAmpsPerThread; i++) vcur[i] = vnext[i];
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
     if (s_fail && tid == 0) {
         atomicExch(err, 1);
         mbar_wait(smem_u32(&mbar), 0);  // bounded: let the MMAs in flight finish before TMEM is freed
@@ -458,10 +411,6 @@ void launch_dense_oz4(void* psi, int n, const std::vector<int>& targets, const s
             if ((w >> j) & 1) o |= 1ull << targets[j];
         P.offs[w] = o;
     }
-    int low = 0;
-    while (low < kOzQ && targets[low] == low) low++;
-    P.low = low;
-    P.swz = low >= 3 ? 0 : 3 - low;
     P.n_groups = P.ip.n_iter;
     const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, 2 * uint64_t(g_oz_sms))));
