@@ -12,9 +12,10 @@
 // 2^-8(s+t+2), every sum of the products with the same s + t = d is an integer number of those
 // units below 2^24, and the tensor cores add them without rounding (checked on the hardware
 // for sums up to 2^23.3 units). The 26 products with s + t <= 6 go to seven FP32 accumulators
-// D_0..D_6, one per d; they are combined exactly from the smallest (each D_d is a multiple of
-// the unit in the last place of the partial sum below it, so Fast2Sum is error-free) into a
-// double-float value and scaled back by mu_n nu. What is dropped (slice remainders below
+// D_0..D_6, one per d; D_6 + D_5 + D_4 is summed in FP32 (its rounding lies below 2^-50 of the
+// output scale), then D_3..D_0 are added exactly (each D_d is a multiple of the unit in the
+// last place of the partial sum below it, so Fast2Sum is error-free) into a double-float value,
+// scaled back by mu_n nu. What is dropped (slice remainders below
 // 2^-48 and the products with s + t >= 7) bounds the error at about 2^-45 of max|v| max|K~|
 // per output, the accuracy of the double-float CUDA-core kernels.
 //
@@ -59,6 +60,7 @@ constexpr int kOzTmemCols = 256;                               // one set, round
 constexpr long long kOzSpinLimit = 1ll << 22;
 
 static_assert(kOzAccCols <= kOzTmemCols, "accumulators fit the TMEM allocation");
+static_assert(kOzND == 7, "the epilogue folds seven diagonals");
 
 // shared-memory plan (bytes), ~110 KB: two CTAs per SM
 constexpr size_t kOffA = 0;                             // 2 x 48 KB state slices
@@ -255,18 +257,15 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
     };
     // accumulators -> double-float outputs, stored straight to the state
     auto epilogue = [&](uint64_t x0, float nv) {
-        const uint32_t lane_base = uint32_t((warp & 3) * 32) << 16;
+        const uint32_t lane_base = tmem + (uint32_t((warp & 3) * 32) << 16) + uint32_t(16 * h);
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
-            const int col0 = 16 * h + 4 * c;  // 4 output reals = 2 amplitudes
+        for (int c = 0; c < 4; c++) {  // 4 output reals = 2 amplitudes per step
             uint32_t r[kOzND][4];
 #pragma unroll
-            for (int d = 0; d < kOzND; d++) {
-                const uint32_t taddr = tmem + lane_base + uint32_t(d * kOzR + col0);
+            for (int d = 0; d < kOzND; d++)
                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
                              : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3])
-                             : "r"(taddr));
-            }
+                             : "r"(lane_base + uint32_t(d * kOzR + 4 * c)));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int i = 0; i < 2; i++) {
@@ -274,13 +273,17 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
 #pragma unroll
                 for (int cc = 0; cc < 2; cc++) {
                     const int col = 2 * i + cc;
-                    float sm = __uint_as_float(r[kOzND - 1][col]), lo = 0.f, t;
+                    // D_6 + D_5 + D_4 in FP32 (rounding far below 2^-48 of the output), then
+                    // D_3..D_0 added exactly with Fast2Sum, the errors collected in lo
+                    float sm = __fadd_rn(__fadd_rn(__uint_as_float(r[6][col]), __uint_as_float(r[5][col])),
+                                         __uint_as_float(r[4][col]));
+                    float lo = 0.f, t;
 #pragma unroll
-                    for (int d = kOzND - 2; d >= 0; d--) {
+                    for (int d = 3; d >= 0; d--) {
                         fast_two_sum(__uint_as_float(r[d][col]), sm, sm, t);
                         lo = __fadd_rn(lo, t);
                     }
-                    const float sc = __fmul_rn(mu[col0 + col], nv);
+                    const float sc = __fmul_rn(mu[16 * h + 4 * c + col], nv);
                     fast_two_sum(__fmul_rn(sm, sc), __fmul_rn(lo, sc), o[2 * cc], o[2 * cc + 1]);
                 }
                 if (x0 != ~0ull) psi[x0 + off[2 * c + i]] = make_float4(o[0], o[1], o[2], o[3]);
