@@ -192,9 +192,11 @@ qs_status qs_apply_gate(qs_state* s, const qs_gate* g);
  * (Sec. 5.4 merge). Equivalent to qs_apply_gate with a QS_GATE_DENSE gate. */
 qs_status qs_apply_fused(qs_state* s, int k, const int* targets, const double* mat);
 /* Applies every gate of c in order. fusion_k = 0 applies gate by gate; 1..6 first merges
- * neighbouring gates into dense blocks of at most fusion_k qubits (Sec. 5.4, the light
- * strategy: a gate joins the open block while the union of targets stays within the width);
- * -1 picks the width with qs_autotune_fusion. c->n must equal the state's n. */
+ * gates into dense blocks of at most fusion_k qubits (Sec. 5.4 merge; the planner keeps the
+ * partition with fewer blocks of two: an open-block greedy one, where a gate joins the open
+ * block while the union of qubits stays within the width, and a frontier-growth one, which
+ * may move a block past gates on other qubits, with which it commutes); -1 picks the width
+ * with qs_autotune_fusion. c->n must equal the state's n. */
 qs_status qs_run_circuit(qs_state* s, const qs_circuit* c, int fusion_k);
 
 /* ---------------------------------------------------------------- fusion (Sec. 5.4) */

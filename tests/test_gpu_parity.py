@@ -312,3 +312,47 @@ def test_adjoint_mixed_rotations_and_pauli_rotation(qs):
         ps = oracle.grad_parameter_shift(c, obs, range(4))
         assert abs(e - oracle.energy(c, obs)) < tol
         assert np.max(np.abs(g - ps)) < tol
+
+
+@pytest.mark.parametrize("n", [24, 26])
+def test_circuit_family_vs_oracle_large(qs, n):
+    """The depth-20 U3+CZ family at n = 24 and 26 against the FP64 oracle (the largest sizes the
+    oracle cross-check covers), complex128 at the autotuned width with the library's default
+    arithmetic (double-float, tensor-core blocks) and on the double-float CUDA cores, whole
+    vectors compared."""
+    c = W.u3cz_circuit(n, 20, 300 + n)
+    ref = oracle.run_circuit(c)
+    old_m, old_t = qs.get_c128_math(), qs.get_tensor_cores()
+    try:
+        qs.set_c128_math(qs.QS_MATH_DF)
+        for tmask in (qs.QS_TENSOR_C128, 0):
+            qs.set_tensor_cores(tmask)
+            st = qs.State(n, qs.QS_C128)
+            st.run(c, -1)
+            got = st.get_vector()
+            st.close()
+            assert maxabs(got, ref) < 1e-12, tmask
+            assert fidelity_gap(ref, got) < 1e-12
+    finally:
+        qs.set_c128_math(old_m)
+        qs.set_tensor_cores(old_t)
+
+
+def test_precision_n24_vs_oracle(qs):
+    """The precision configuration against the FP64 oracle at n = 24: complex64 (FP32 gates,
+    FP64-built fused matrices, FP64 norm and expectation sums) and complex128 on the GPU;
+    max-abs amplitude error, 1 - fidelity and the transverse-field Ising energy error (h = 1)."""
+    n = 24
+    c = W.u3cz_circuit(n, 20, 2424)
+    ref = oracle.run_circuit(c)
+    tf = W.tfim_observable(n, 1.0)
+    e_ref = oracle.expectation(ref, tf)[0]
+    for dtype, amp_tol, fid_tol, e_tol in ((2, 1e-12, 1e-12, 1e-11), (1, 1e-5, 1e-6, 1e-5)):
+        st = qs.State(n, dtype)
+        st.run(c, -1)
+        got = st.get_vector().astype(np.complex128)
+        assert maxabs(got, ref) < amp_tol, dtype
+        assert fidelity_gap(ref, got) < fid_tol, dtype
+        assert abs(st.expectation(tf)[0] - e_ref) < e_tol, dtype
+        assert abs(st.norm2() - 1.0) < (1e-12 if dtype == 2 else 1e-5)
+        st.close()
