@@ -235,12 +235,25 @@ def make_gate(g) -> Tuple[QsGate, _Keep]:
 
 
 def make_circuit(circuit) -> Tuple[QsCircuit, _Keep]:
-    keep = _Keep()
-    arr = (QsGate * max(1, len(circuit.gates)))()
-    for i, g in enumerate(circuit.gates):
-        fill_gate(arr[i], g, keep)
-    keep.refs.append(arr)
-    c = QsCircuit(int(circuit.n), len(circuit.gates), int(getattr(circuit, "n_params", 0)), 0,
+    """Marshals a circuit into a qs_circuit. The gate array of a circuit without matrix gates is
+    kept on the circuit object and reused while its gate list holds the same (immutable) gates,
+    so a loop over parameter vectors does not rebuild it."""
+    gates = circuit.gates
+    cache = getattr(circuit, "_qs_marshal", None)
+    if cache is not None and cache[0] == len(gates) and all(a is b for a, b in zip(cache[1], gates)):
+        arr, keep = cache[2], cache[3]
+    else:
+        keep = _Keep()
+        arr = (QsGate * max(1, len(gates)))()
+        for i, g in enumerate(gates):
+            fill_gate(arr[i], g, keep)
+        keep.refs.append(arr)
+        if all(g.name not in ("DENSE", "DIAG") for g in gates):
+            try:
+                circuit._qs_marshal = (len(gates), list(gates), arr, keep)
+            except AttributeError:  # a circuit type that takes no new attributes
+                pass
+    c = QsCircuit(int(circuit.n), len(gates), int(getattr(circuit, "n_params", 0)), 0,
                   ctypes.cast(arr, ctypes.POINTER(QsGate)))
     return c, keep
 

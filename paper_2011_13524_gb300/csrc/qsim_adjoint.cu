@@ -106,6 +106,125 @@ __global__ void __launch_bounds__(kAdjThreads) k_slot_sums(const double* __restr
     if (threadIdx.x == 0) out[blockIdx.x] = r;
 }
 
+// ---- reverse step for a run of diagonal gates
+// Diagonal gates commute with each other and with every diagonal Pauli string P (a Z string),
+// so for a parametric gate exp(i theta P / 2) inside a run of diagonal gates,
+// <lambda_j|P|psi_j> = <lambda|P|psi> with psi, lambda taken after the whole run: one pass
+// computes every such gradient of the run and then multiplies both buffers by the run's inverse
+// (the product of the conjugated diagonals). Each factor of that product is either a table over
+// up to 6 qubits (applied where a condition on other bits holds) or a sign (-1)^popc(x & zmask).
+template <typename P>
+struct DiagGrad;  // FP64-class accumulator of sum_x sign(x) Im(conj(lam_x) psi_x)
+template <>
+struct DiagGrad<NativeArith<double>> {
+    double v = 0.0;
+    __device__ static void term(double2 l, double2 p, double& w) { w = fma(l.x, p.y, -l.y * p.x); }
+    __device__ void add(double w, bool neg) { v += neg ? -w : w; }
+    __device__ double value() const { return v; }
+};
+struct DiagGradPair {
+    float s = 0.f, c = 0.f;
+    __device__ void addp(float ws, float wc, bool neg) {
+        if (neg) { ws = -ws; wc = -wc; }
+        float h, e;
+        DFArith::two_sum(s, ws, h, e);
+        s = h;
+        c = __fadd_rn(c, __fadd_rn(e, wc));
+    }
+    __device__ double value() const { return double(s) + double(c); }
+};
+template <>
+struct DiagGrad<DFArith> : DiagGradPair {
+    struct W { float s, c; };
+    __device__ static void term(float4 l, float4 p, W& w) {
+        DFArith::dprod0(w.s, w.c, l.x, l.y, p.z, p.w);
+        DFArith::dprod(w.s, w.c, -l.z, -l.w, p.x, p.y);
+    }
+    __device__ void add(const W& w, bool neg) { addp(w.s, w.c, neg); }
+};
+template <>
+struct DiagGrad<NativeArith<float>> : DiagGradPair {
+    struct W { float s, c; };
+    __device__ static void term(float2 l, float2 p, W& w) {
+        DFArith::dprod0(w.s, w.c, l.x, 0.f, p.y, 0.f);
+        DFArith::dprod(w.s, w.c, -l.y, 0.f, p.x, 0.f);
+    }
+    __device__ void add(const W& w, bool neg) { addp(w.s, w.c, neg); }
+};
+template <typename P>
+struct DiagTermType { using type = typename DiagGrad<P>::W; };
+template <>
+struct DiagTermType<NativeArith<double>> { using type = double; };
+
+__device__ __forceinline__ float4 kmul(float4 a, float4 b) { return DFArith::out(DFArith::first(a, b)); }
+__device__ __forceinline__ float2 kmul(float2 a, float2 b) { return cmul(a, b); }
+__device__ __forceinline__ double2 kmul(double2 a, double2 b) { return cmul(a, b); }
+template <typename K>
+__device__ __forceinline__ K kone();
+template <>
+__device__ __forceinline__ float4 kone<float4>() { return make_float4(1.f, 0.f, 0.f, 0.f); }
+template <>
+__device__ __forceinline__ float2 kone<float2>() { return make_float2(1.f, 0.f); }
+template <>
+__device__ __forceinline__ double2 kone<double2>() { return make_double2(1.0, 0.0); }
+
+template <typename P>
+__global__ void __launch_bounds__(kAdjThreads) k_adj_diag(typename P::C* __restrict__ psi, typename P::C* __restrict__ lam,
+                                                           const typename P::K* __restrict__ tab,
+                                                           const __grid_constant__ AdjDiagParams A, double* part) {
+    using C = typename P::C;
+    using K = typename P::K;
+    extern __shared__ __align__(16) unsigned char adj_smem[];
+    K* stab = reinterpret_cast<K*>(adj_smem);
+    for (int i = threadIdx.x; i < A.ntab; i += kAdjThreads) stab[i] = tab[i];
+    __syncthreads();
+    DiagGrad<P> acc[kAdjDiagMaxG];
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t x = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < A.n_amp; x += stride) {
+        C p = psi[x], l = lam[x];
+        if (A.ng) {
+            typename DiagTermType<P>::type w;
+            DiagGrad<P>::term(l, p, w);
+#pragma unroll
+            for (int g = 0; g < kAdjDiagMaxG; g++)
+                if (g < A.ng) acc[g].add(w, parity64(x & A.gz[g]) != 0);
+        }
+        K f = kone<K>();
+        int sign = 0;
+#pragma unroll 1
+        for (int k = 0; k < A.nf; k++) {
+            const AdjDiagFactor& F = A.f[k];
+            if ((x & F.cond_mask) != F.cond_val) continue;
+            sign ^= parity64(x & F.zmask);
+            if (F.sign_only) {
+                sign ^= 1;
+            } else if (F.tab_off >= 0) {
+                int li = 0;
+                for (int j = 0; j < F.nq; j++) li |= int((x >> F.q[j]) & 1) << j;
+                f = kmul(f, stab[F.tab_off + li]);
+            }
+        }
+        p = P::out(P::first(f, p));
+        l = P::out(P::first(f, l));
+        if (sign) {
+            p = P::ipow(p, 2);
+            l = P::ipow(l, 2);
+        }
+        psi[x] = p;
+        lam[x] = l;
+    }
+    __shared__ double sh[kAdjThreads / 32];
+#pragma unroll 1
+    for (int g = 0; g < A.ng; g++) {
+        double v = 0.0;
+#pragma unroll
+        for (int h = 0; h < kAdjDiagMaxG; h++)
+            if (h == g) v = acc[h].value();
+        const double r = block_sum<kAdjThreads>(v, sh);
+        if (threadIdx.x == 0) part[size_t(g) * gridDim.x + blockIdx.x] = r;
+    }
+}
+
 int sm_count_adj() {
     static int sms = 0;
     if (!sms) {
@@ -149,6 +268,26 @@ void launch_adjoint_rotation(void* psi, void* lam, int n, Arith ar, int qubit, i
         case Arith::F32: launch_rot<NativeArith<float>>(psi, lam, n, qubit, axis, theta, part, grid, st); break;
         case Arith::F64: launch_rot<NativeArith<double>>(psi, lam, n, qubit, axis, theta, part, grid, st); break;
         case Arith::DF: launch_rot<DFArith>(psi, lam, n, qubit, axis, theta, part, grid, st); break;
+    }
+    QS_TRY_CUDA(cudaGetLastError());
+}
+
+void launch_adjoint_diag(void* psi, void* lam, int n, Arith ar, const void* tab, const AdjDiagParams& A, double* part,
+                         unsigned grid, cudaStream_t st) {
+    const size_t smem = size_t(A.ntab) * kernel_entry_bytes(ar);
+    switch (ar) {
+        case Arith::F32:
+            k_adj_diag<NativeArith<float>><<<grid, kAdjThreads, smem, st>>>(
+                static_cast<float2*>(psi), static_cast<float2*>(lam), static_cast<const float2*>(tab), A, part);
+            break;
+        case Arith::F64:
+            k_adj_diag<NativeArith<double>><<<grid, kAdjThreads, smem, st>>>(
+                static_cast<double2*>(psi), static_cast<double2*>(lam), static_cast<const double2*>(tab), A, part);
+            break;
+        case Arith::DF:
+            k_adj_diag<DFArith><<<grid, kAdjThreads, smem, st>>>(
+                static_cast<float4*>(psi), static_cast<float4*>(lam), static_cast<const float4*>(tab), A, part);
+            break;
     }
     QS_TRY_CUDA(cudaGetLastError());
 }

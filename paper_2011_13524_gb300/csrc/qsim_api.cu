@@ -793,35 +793,180 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
         launch_set_basis_arith(psi->data, c->n, Arith::DF, 0, st);
     }
     const Arith ar = arith_of(psi);
-    // forward: psi = U_G ... U_1 |0>
-    run_gates(psi, c, theta);
+    // forward: psi = U_G ... U_1 |0>, fused (the partition of a circuit structure is cached, so
+    // repeated calls with new angles only rebuild the block matrices)
+    const int kf = (ar == Arith::DF && tensor_c128_enabled()) || ar == Arith::F32 ? 4 : 2;
+    apply_plan(psi, plan_fusion(c, kf, theta));
     // lambda = H psi ; E = Re <psi|lambda>
     launch_apply_observable(groups, psi->data, lam->data, c->n, ar, st);
     double e2[2];
     reduce_inner(psi, lam, e2);
     *energy = e2[0];
     for (int p = 0; p < c->n_params; p++) grad[p] = 0.0;
-    // single-qubit rotations use the fused reverse step (gradient partials + un-apply in one
-    // pass, no host synchronisation); their partial sums are reduced once after the sweep
+
+    // The reverse sweep as steps: single-qubit X/Y rotations use the fused reverse step
+    // (gradient partials + un-apply in one pass); maximal runs of diagonal gates (CZ, phases,
+    // RZ and Z-string rotations, diagonal gates) take one pass for the whole run; other gates
+    // are un-applied on both buffers, and a parametric Pauli rotation with X or Y factors gets
+    // its gradient from a transition amplitude first. Partial sums of the device-side
+    // gradients land in per-block slots, reduced once after the sweep.
     auto fused_rot = [&](const qs_gate& g) {
-        return g.param_index >= 0 && g.mc == 0 &&
-               (g.named == QS_NAMED_RX || g.named == QS_NAMED_RY || g.named == QS_NAMED_RZ);
+        return g.param_index >= 0 && g.mc == 0 && (g.named == QS_NAMED_RX || g.named == QS_NAMED_RY);
     };
+    struct Step {
+        int kind = 0;               // 0 rotation, 1 diagonal run, 2 other gate
+        int gate = -1;              // kinds 0 and 2
+        int slot0 = 0;              // first gradient slot
+        AdjDiagParams A;            // kind 1
+        size_t tab_byte = 0;        // kind 1: offset of its tables in the upload
+        std::vector<int> params;    // kind 1: parameter index of each gradient term
+    };
+    std::vector<Step> steps;
+    std::vector<cplx> tabs;         // every run's tables, in order
     int nslots = 0;
-    for (int i = 0; i < c->n_gates; i++) nslots += fused_rot(c->gates[i]) ? 1 : 0;
-    const unsigned nb = adj_grid(c->n);
-    double* d_part = nullptr;
-    if (nslots) QS_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_part), sizeof(double) * (size_t(nslots) * nb + nslots), st));
-    std::vector<int> slot_param;
-    try {
+    {
+        std::vector<int> run;       // gate indices, reverse order
+        auto flush = [&]() {
+            if (run.empty()) return;
+            Step stp;
+            stp.kind = 1;
+            stp.slot0 = nslots;
+            stp.A.n_amp = 1ull << c->n;
+            stp.tab_byte = tabs.size();
+            // single-qubit uncontrolled diagonals multiply into per-qubit pairs, then into tables
+            // over up to 4 qubits; every other diagonal keeps a factor of its own
+            std::map<int, std::pair<cplx, cplx>> one;
+            int ntab = 0;
+            auto add_factor = [&](const AdjDiagFactor& f, const std::vector<cplx>& t) {
+                QS_REQUIRE(stp.A.nf < kAdjDiagMaxF, "diagonal run too long");
+                AdjDiagFactor g = f;
+                if (!t.empty()) {
+                    g.tab_off = ntab;
+                    for (const cplx& v : t) tabs.push_back(v);
+                    ntab += int(t.size());
+                }
+                stp.A.f[stp.A.nf++] = g;
+            };
+            for (int gi : run) {
+                const qs_gate& g = c->gates[gi];
+                Op op = dagger(op_of_gate(g, c->n, theta));
+                if (g.param_index >= 0) {
+                    uint64_t zm = 0;
+                    for (int j = 0; j < g.m; j++)
+                        if (g.kind == QS_GATE_NAMED && g.named == QS_NAMED_RZ) zm |= 1ull << g.targets[j];
+                        else if (g.pauli[j] == 3) zm |= 1ull << g.targets[j];
+                    stp.A.gz[stp.A.ng++] = zm;
+                    stp.params.push_back(g.param_index);
+                }
+                uint64_t cm = 0, cv = 0;
+                for (size_t j = 0; j < op.controls.size(); j++) {
+                    cm |= 1ull << op.controls[j];
+                    if (op.cvals[j]) cv |= 1ull << op.controls[j];
+                }
+                AdjDiagFactor f;
+                f.cond_mask = cm;
+                f.cond_val = cv;
+                if (op.kind == OpKind::Pauli) {
+                    f.zmask = op.zmask;
+                    add_factor(f, {});
+                } else if (op.kind == OpKind::Phase) {
+                    if (op.phase == cplx(-1.0, 0.0)) {
+                        f.sign_only = 1;
+                        add_factor(f, {});
+                    } else if (op.phase != cplx(1.0, 0.0)) {
+                        add_factor(f, {op.phase});
+                    }
+                } else if (op.targets.size() == 1 && cm == 0) {
+                    auto it = one.find(op.targets[0]);
+                    if (it == one.end()) one[op.targets[0]] = {op.data[0], op.data[1]};
+                    else it->second = {it->second.first * op.data[0], it->second.second * op.data[1]};
+                } else {
+                    f.nq = int(op.targets.size());
+                    for (int j = 0; j < f.nq; j++) f.q[j] = op.targets[j];
+                    add_factor(f, op.data);
+                }
+            }
+            std::vector<std::pair<int, std::pair<cplx, cplx>>> ones(one.begin(), one.end());
+            for (size_t i0 = 0; i0 < ones.size(); i0 += 4) {
+                AdjDiagFactor f;
+                f.nq = int(std::min<size_t>(4, ones.size() - i0));
+                std::vector<cplx> t(size_t(1) << f.nq, cplx(1.0, 0.0));
+                for (int j = 0; j < f.nq; j++) {
+                    f.q[j] = ones[i0 + j].first;
+                    for (size_t li = 0; li < t.size(); li++)
+                        t[li] *= ((li >> j) & 1) ? ones[i0 + j].second.second : ones[i0 + j].second.first;
+                }
+                add_factor(f, t);
+            }
+            stp.A.ntab = ntab;
+            QS_REQUIRE(ntab <= kAdjDiagMaxTab, "diagonal run tables too large");
+            nslots += stp.A.ng;
+            steps.push_back(std::move(stp));
+            run.clear();
+        };
         for (int i = c->n_gates - 1; i >= 0; i--) {
             const qs_gate& g = c->gates[i];
+            const Op op = op_of_gate(g, c->n, theta);
+            const bool diag = op.kind == OpKind::Diag || op.kind == OpKind::Phase ||
+                              (op.kind == OpKind::Pauli && op.xmask == 0);
+            const bool diag_param = g.param_index < 0 || (op.kind != OpKind::Dense && g.mc == 0);
+            if (diag && diag_param) {
+                // bound the run by the kernel's factor, gradient and table limits (worst case)
+                const int tab_need = op.kind == OpKind::Diag ? (1 << op.targets.size()) : 1;
+                int nf = 0, ng = 0, nt = 0;
+                for (int gi : run) {
+                    const Op o2 = op_of_gate(c->gates[gi], c->n, theta);
+                    nf++;
+                    nt += o2.kind == OpKind::Diag ? (1 << o2.targets.size()) : 1;
+                    ng += c->gates[gi].param_index >= 0;
+                }
+                if (nf + 1 > kAdjDiagMaxF || ng + (g.param_index >= 0) > kAdjDiagMaxG || nt + tab_need > kAdjDiagMaxTab)
+                    flush();
+                run.push_back(i);
+                continue;
+            }
+            flush();
+            Step stp;
+            stp.gate = i;
             if (fused_rot(g)) {
-                const int axis = g.named == QS_NAMED_RX ? 1 : g.named == QS_NAMED_RY ? 2 : 3;
+                stp.kind = 0;
+                stp.slot0 = nslots++;
+            } else {
+                stp.kind = 2;
+            }
+            steps.push_back(stp);
+        }
+        flush();
+    }
+    const unsigned nb = adj_grid(c->n);
+    double* d_part = nullptr;
+    void* d_tab = nullptr;
+    const size_t eb = kernel_entry_bytes(ar);
+    if (nslots) QS_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_part), sizeof(double) * (size_t(nslots) * nb + nslots), st));
+    std::vector<int> slot_param(nslots, -1);
+    try {
+        if (!tabs.empty()) {
+            std::vector<unsigned char> host(tabs.size() * eb);
+            encode_entries(ar, tabs, host.data());
+            QS_TRY_CUDA(cudaMallocAsync(&d_tab, host.size(), st));
+            QS_TRY_CUDA(cudaMemcpyAsync(d_tab, host.data(), host.size(), cudaMemcpyHostToDevice, st));
+            QS_TRY_CUDA(cudaStreamSynchronize(st));  // the host copy dies on return
+        }
+        for (const Step& stp : steps) {
+            if (stp.kind == 1) {
+                launch_adjoint_diag(psi->data, lam->data, c->n, ar,
+                                    static_cast<const unsigned char*>(d_tab) + stp.tab_byte * eb, stp.A,
+                                    d_part ? d_part + size_t(stp.slot0) * nb : nullptr, nb, st);
+                for (size_t g = 0; g < stp.params.size(); g++) slot_param[stp.slot0 + g] = stp.params[g];
+                continue;
+            }
+            const qs_gate& g = c->gates[stp.gate];
+            if (stp.kind == 0) {
+                const int axis = g.named == QS_NAMED_RX ? 1 : 2;
                 const double th = theta ? theta[g.param_index] : g.params[0];
                 launch_adjoint_rotation(psi->data, lam->data, c->n, ar, g.targets[0], axis, th,
-                                        d_part + size_t(slot_param.size()) * nb, nb, st);
-                slot_param.push_back(g.param_index);
+                                        d_part + size_t(stp.slot0) * nb, nb, st);
+                slot_param[stp.slot0] = g.param_index;
                 continue;
             }
             Op op = op_of_gate(g, c->n, theta);
@@ -851,8 +996,10 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
         }
     } catch (...) {
         if (d_part) cudaFreeAsync(d_part, st);
+        if (d_tab) cudaFreeAsync(d_tab, st);
         throw;
     }
+    if (d_tab) QS_TRY_CUDA(cudaFreeAsync(d_tab, st));
     if (d_part) QS_TRY_CUDA(cudaFreeAsync(d_part, st));
     QS_TRY_CUDA(cudaStreamSynchronize(st));
     API_END

@@ -23,6 +23,8 @@
 // applying each gate, in circuit order, to the columns of the block matrix.
 #include <algorithm>
 #include <cstring>
+#include <list>
+#include <mutex>
 
 #include "qsim_internal.h"
 
@@ -87,7 +89,7 @@ bool dense_is_diagonal(const DenseOp& d) {
     return true;
 }
 
-void emit(const OpenBlock& b, const qs_circuit* c, FusionPlan& plan) {
+void emit(const OpenBlock& b, const qs_circuit* c, const double* theta, FusionPlan& plan) {
     FusedBlock fb;
     for (int q = 0; q < 64; q++)
         if ((b.mask >> q) & 1) fb.qubits.push_back(q);
@@ -104,7 +106,7 @@ void emit(const OpenBlock& b, const qs_circuit* c, FusionPlan& plan) {
     bool diag = true;
     for (int gi : b.gates) {
         const qs_gate& g = c->gates[gi];
-        DenseOp d = dense_of_gate(g, c->n, nullptr);
+        DenseOp d = dense_of_gate(g, c->n, theta);
         diag = diag && dense_is_diagonal(d);
         std::vector<int> lt, lc;
         auto local = [&](int q) { return int(std::find(fb.qubits.begin(), fb.qubits.end(), q) - fb.qubits.begin()); };
@@ -279,7 +281,40 @@ std::vector<OpenBlock> partition_frontier(const qs_circuit* c, const std::vector
 
 }  // namespace
 
-FusionPlan plan_fusion(const qs_circuit* c, int k) {
+// The partition depends only on the qubit sets of the gates and on k, not on angles or matrix
+// entries: a circuit run again with new parameters (an optimisation loop, the adjoint's forward
+// pass) reuses it. A few recent partitions are kept.
+namespace {
+struct PartitionKey {
+    int n = 0, k = 0;
+    std::vector<uint64_t> masks;
+    bool operator==(const PartitionKey& o) const { return n == o.n && k == o.k && masks == o.masks; }
+};
+std::mutex g_part_mu;
+std::list<std::pair<PartitionKey, std::vector<OpenBlock>>> g_part_cache;
+constexpr size_t kPartCacheSize = 16;
+
+std::vector<OpenBlock> partition(const qs_circuit* c, const std::vector<uint64_t>& masks, int k) {
+    PartitionKey key{c->n, k, masks};
+    {
+        std::lock_guard<std::mutex> lk(g_part_mu);
+        for (auto it = g_part_cache.begin(); it != g_part_cache.end(); ++it)
+            if (it->first == key) {
+                g_part_cache.splice(g_part_cache.begin(), g_part_cache, it);
+                return it->second;
+            }
+    }
+    std::vector<OpenBlock> a = partition_greedy(c, masks, k);
+    std::vector<OpenBlock> b = partition_frontier(c, masks, k);
+    std::vector<OpenBlock> best = b.size() < a.size() ? std::move(b) : std::move(a);
+    std::lock_guard<std::mutex> lk(g_part_mu);
+    g_part_cache.emplace_front(std::move(key), best);
+    if (g_part_cache.size() > kPartCacheSize) g_part_cache.pop_back();
+    return best;
+}
+}  // namespace
+
+FusionPlan plan_fusion(const qs_circuit* c, int k, const double* theta) {
     QS_REQUIRE(c != nullptr, "null circuit");
     QS_REQUIRE(c->n >= 1 && c->n <= QS_MAX_QUBITS, "qubit count out of range");
     QS_REQUIRE(c->n_gates >= 0 && (c->n_gates == 0 || c->gates != nullptr), "null gate array");
@@ -295,14 +330,12 @@ FusionPlan plan_fusion(const qs_circuit* c, int k) {
     plan.n = c->n;
     plan.k = k;
     plan.n_source_gates = c->n_gates;
-    std::vector<OpenBlock> a = partition_greedy(c, masks, k);
-    std::vector<OpenBlock> b = partition_frontier(c, masks, k);
-    const std::vector<OpenBlock>& best = b.size() < a.size() ? b : a;
-    for (const OpenBlock& blk : best) emit(blk, c, plan);
+    for (const OpenBlock& blk : partition(c, masks, k)) emit(blk, c, theta, plan);
     // keep copies of the gates that stay unfused (their matrices are rebuilt at launch)
     for (auto& b : plan.blocks) {
         if (b.single_gate < 0) continue;
         qs_gate g = c->gates[b.single_gate];
+        if (theta && g.param_index >= 0) g.params[0] = theta[g.param_index];  // the angle this plan was made for
         std::vector<double> mat;
         if (g.kind == QS_GATE_DENSE || g.kind == QS_GATE_DIAG) {
             const size_t D = size_t(1) << g.m;

@@ -166,6 +166,28 @@ void launch_apply_observable(const std::vector<PauliGroup>& groups, const void* 
 unsigned adj_grid(int n);
 void launch_adjoint_rotation(void* psi, void* lam, int n, Arith ar, int qubit, int axis, double theta, double* part,
                              unsigned grid, cudaStream_t st);
+// Reverse step for a run of diagonal gates on psi and lam (both multiplied by the run's inverse),
+// with the gradient partials of the run's diagonal rotations exp(i theta P / 2) (P a Z string
+// gz[g]) computed before: part[g * grid + block] = block's sum of (-1)^popc(x & gz[g]) Im(conj(lam_x) psi_x).
+constexpr int kAdjDiagMaxF = 24;
+constexpr int kAdjDiagMaxG = 24;
+constexpr int kAdjDiagMaxTab = 1024;
+struct AdjDiagFactor {
+    uint64_t cond_mask = 0, cond_val = 0;  // applies where (x & cond_mask) == cond_val
+    uint64_t zmask = 0;                    // sign (-1)^popc(x & zmask)
+    int32_t sign_only = 0;                 // the factor is -1 (no table)
+    int32_t tab_off = -1;                  // table of 2^nq entries (or none)
+    int32_t nq = 0;
+    int32_t q[6] = {0, 0, 0, 0, 0, 0};     // table index bit j = bit q[j] of x
+};
+struct AdjDiagParams {
+    uint64_t n_amp = 0;
+    int32_t nf = 0, ng = 0, ntab = 0, pad = 0;
+    AdjDiagFactor f[kAdjDiagMaxF];
+    uint64_t gz[kAdjDiagMaxG];
+};
+void launch_adjoint_diag(void* psi, void* lam, int n, Arith ar, const void* tab, const AdjDiagParams& A, double* part,
+                         unsigned grid, cudaStream_t st);
 // out[s] = sum_j part[s * nb + j] for s < nslots (fixed order)
 void launch_slot_sums(const double* part, int nslots, unsigned nb, double* out, cudaStream_t st);
 
@@ -211,7 +233,8 @@ struct FusionPlan {
     std::vector<qs_gate> source;          // copies of single-gate blocks' gates
     std::vector<std::vector<double>> source_mats;
 };
-FusionPlan plan_fusion(const qs_circuit* c, int k);
+// theta (optional): parameter vector overriding the angles of parametric gates
+FusionPlan plan_fusion(const qs_circuit* c, int k, const double* theta = nullptr);
 void apply_plan(qs_state* s, const FusionPlan& p);
 
 }  // namespace qs

@@ -314,6 +314,60 @@ def test_adjoint_mixed_rotations_and_pauli_rotation(qs):
         assert np.max(np.abs(g - ps)) < tol
 
 
+def test_adjoint_diagonal_runs(qs):
+    """Runs of diagonal gates in the reverse sweep (one pass per run): CZ ladders, a controlled
+    phase, S and T, a 2-qubit DIAG gate with a control, RZ twice on one qubit inside a run, a
+    parametric Z-string PAULIROT and a Z-string PAULI gate, between dense layers; complex128 and
+    complex64 against parameter shift, and the energy against the oracle."""
+    n = 7
+    rng = W.SplitMix64(91)
+    gates = [W.Gate("H", (q,)) for q in range(n)]
+    gates += [W.Gate("RZ", (q,), params=(0.3 + 0.1 * q,), param_index=q) for q in range(n)]
+    gates += [W.Gate("CZ", (q, q + 1)) for q in range(n - 1)]
+    gates += [W.Gate("RZ", (2,), params=(-0.7,), param_index=7), W.Gate("S", (4,)), W.Gate("T", (1,)),
+              W.Gate("U1", (5,), params=(0.9,), controls=(0,), control_values=(1,)),
+              W.Gate("DIAG", (3, 6), controls=(2,), control_values=(0,),
+                     matrix=np.exp(1j * np.array([0.1, -0.4, 0.8, 1.9]))),
+              W.Gate("PAULIROT", (1, 4, 6), pauli=(3, 3, 3), params=(0.55,), param_index=8),
+              W.Gate("PAULI", (0, 5), pauli=(3, 3)),
+              W.Gate("RZ", (2,), params=(0.25,), param_index=9)]
+    gates += [W.Gate("RY", (q,), params=(0.2 * q - 0.5,), param_index=10 + q) for q in range(n)]
+    gates += [W.Gate("CZ", (q, q + 2)) for q in range(n - 2)]
+    gates += [W.Gate("RZ", (q,), params=(1.1 - 0.3 * q,), param_index=10 + n + q) for q in range(n)]
+    gates += [W.Gate("RX", (q,), params=(0.5,), param_index=2) for q in (0, 3)]  # shares RZ(2)'s angle
+    c = W.Circuit(n, gates, n_params=10 + 2 * n)
+    obs = W.random_pauli_observable(n, 8, 5150)
+    # parameter 2 enters three gates: the two-point shift rule is exact only for one occurrence,
+    # so that component is checked against central differences
+    single = [p for p in range(c.n_params) if p != 2]
+    ps = oracle.grad_parameter_shift(c, obs, single)
+    fd2 = oracle.grad_finite_difference(c, obs, [2], h=1e-5)[0]
+    e_ref = oracle.energy(c, obs)
+    old = qs.get_c128_math()
+    try:
+        for dtype, math_mode, tol, fd_tol in ((2, qs.QS_MATH_DF, 1e-11, 1e-8), (2, qs.QS_MATH_FP64, 1e-11, 1e-8),
+                                              (1, qs.QS_MATH_FP64, 1e-4, 1e-4)):
+            qs.set_c128_math(math_mode)
+            e, g = qs.adjoint_grad(c, obs, dtype=dtype)
+            assert abs(e - e_ref) < tol, (dtype, math_mode)
+            assert np.max(np.abs(g[single] - ps)) < tol, (dtype, math_mode, np.max(np.abs(g[single] - ps)))
+            assert abs(g[2] - fd2) < fd_tol, (dtype, math_mode, g[2], fd2)
+    finally:
+        qs.set_c128_math(old)
+
+
+def test_adjoint_hea_n12_vs_parameter_shift(qs):
+    """The hardware-efficient ansatz of the differentiation configuration at n = 12 (RY and RZ
+    layers, CZ ladders): the RZ layer and the ladder form one diagonal run per layer."""
+    c = W.hea_circuit(12, 6, 4)
+    obs = W.tfim_observable(12, 1.0)
+    e, g = qs.adjoint_grad(c, obs)
+    assert abs(e - oracle.energy(c, obs)) < 1e-12
+    idx = list(range(0, c.n_params, 7))
+    ps = oracle.grad_parameter_shift(c, obs, idx)
+    assert np.max(np.abs(g[idx] - ps)) < 1e-11
+
+
 @pytest.mark.parametrize("n", [24, 26])
 def test_circuit_family_vs_oracle_large(qs, n):
     """The depth-20 U3+CZ family at n = 24 and 26 against the FP64 oracle (the largest sizes the
