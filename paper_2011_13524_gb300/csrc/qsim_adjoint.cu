@@ -113,48 +113,45 @@ __global__ void __launch_bounds__(kAdjThreads) k_slot_sums(const double* __restr
 // computes every such gradient of the run and then multiplies both buffers by the run's inverse
 // (the product of the conjugated diagonals). Each factor of that product is either a table over
 // up to 6 qubits (applied where a condition on other bits holds) or a sign (-1)^popc(x & zmask).
+// FP64-class running sums: double for the FP64 policy, an FP32 (sum, compensation) pair
+// (Knuth TwoSum) for the FP32 and double-float policies
 template <typename P>
-struct DiagGrad;  // FP64-class accumulator of sum_x sign(x) Im(conj(lam_x) psi_x)
-template <>
-struct DiagGrad<NativeArith<double>> {
-    double v = 0.0;
-    __device__ static void term(double2 l, double2 p, double& w) { w = fma(l.x, p.y, -l.y * p.x); }
-    __device__ void add(double w, bool neg) { v += neg ? -w : w; }
-    __device__ double value() const { return v; }
-};
-struct DiagGradPair {
+struct RedSum {
     float s = 0.f, c = 0.f;
-    __device__ void addp(float ws, float wc, bool neg) {
+    __device__ void add(float ws, float wc, bool neg) {
         if (neg) { ws = -ws; wc = -wc; }
         float h, e;
         DFArith::two_sum(s, ws, h, e);
         s = h;
         c = __fadd_rn(c, __fadd_rn(e, wc));
     }
+    __device__ void add(const RedSum& o, bool neg) { add(o.s, o.c, neg); }
     __device__ double value() const { return double(s) + double(c); }
 };
 template <>
-struct DiagGrad<DFArith> : DiagGradPair {
-    struct W { float s, c; };
-    __device__ static void term(float4 l, float4 p, W& w) {
-        DFArith::dprod0(w.s, w.c, l.x, l.y, p.z, p.w);
-        DFArith::dprod(w.s, w.c, -l.z, -l.w, p.x, p.y);
-    }
-    __device__ void add(const W& w, bool neg) { addp(w.s, w.c, neg); }
+struct RedSum<NativeArith<double>> {
+    double v = 0.0;
+    __device__ void add(const RedSum& o, bool neg) { v += neg ? -o.v : o.v; }
+    __device__ double value() const { return v; }
 };
-template <>
-struct DiagGrad<NativeArith<float>> : DiagGradPair {
-    struct W { float s, c; };
-    __device__ static void term(float2 l, float2 p, W& w) {
-        DFArith::dprod0(w.s, w.c, l.x, 0.f, p.y, 0.f);
-        DFArith::dprod(w.s, w.c, -l.y, 0.f, p.x, 0.f);
-    }
-    __device__ void add(const W& w, bool neg) { addp(w.s, w.c, neg); }
-};
-template <typename P>
-struct DiagTermType { using type = typename DiagGrad<P>::W; };
-template <>
-struct DiagTermType<NativeArith<double>> { using type = double; };
+// Im(conj(l) p) of one amplitude as a RedSum
+__device__ __forceinline__ RedSum<DFArith> im_conj_prod(float4 l, float4 p, RedSum<DFArith>) {
+    RedSum<DFArith> w;
+    DFArith::dprod0(w.s, w.c, l.x, l.y, p.z, p.w);
+    DFArith::dprod(w.s, w.c, -l.z, -l.w, p.x, p.y);
+    return w;
+}
+__device__ __forceinline__ RedSum<NativeArith<float>> im_conj_prod(float2 l, float2 p, RedSum<NativeArith<float>>) {
+    RedSum<NativeArith<float>> w;
+    DFArith::dprod0(w.s, w.c, l.x, 0.f, p.y, 0.f);
+    DFArith::dprod(w.s, w.c, -l.y, 0.f, p.x, 0.f);
+    return w;
+}
+__device__ __forceinline__ RedSum<NativeArith<double>> im_conj_prod(double2 l, double2 p, RedSum<NativeArith<double>>) {
+    RedSum<NativeArith<double>> w;
+    w.v = fma(l.x, p.y, -l.y * p.x);
+    return w;
+}
 
 __device__ __forceinline__ float4 kmul(float4 a, float4 b) { return DFArith::out(DFArith::first(a, b)); }
 __device__ __forceinline__ float2 kmul(float2 a, float2 b) { return cmul(a, b); }
@@ -168,72 +165,94 @@ __device__ __forceinline__ float2 kone<float2>() { return make_float2(1.f, 0.f);
 template <>
 __device__ __forceinline__ double2 kone<double2>() { return make_double2(1.0, 0.0); }
 
+constexpr int kDiagKA = 4;  // amplitudes per thread between two gradient flushes
+
+// Thread t of T = grid x 256 threads takes the amplitudes x = j T + t. Between flushes it keeps
+// one running sum of Im(conj(lam_x) psi_x) per j (kDiagKA of them); at a flush the warp's sums go
+// through shared memory and lane g adds every one of them with the sign (-1)^popc(x & gz[g]) of
+// its own gradient term, so the per-amplitude cost does not grow with the number of gradients.
 template <typename P>
 __global__ void __launch_bounds__(kAdjThreads) k_adj_diag(typename P::C* __restrict__ psi, typename P::C* __restrict__ lam,
                                                            const typename P::K* __restrict__ tab,
                                                            const __grid_constant__ AdjDiagParams A, double* part) {
     using C = typename P::C;
     using K = typename P::K;
+    using R = RedSum<P>;
     extern __shared__ __align__(16) unsigned char adj_smem[];
     K* stab = reinterpret_cast<K*>(adj_smem);
+    R* red = reinterpret_cast<R*>(adj_smem + ((size_t(A.ntab) * sizeof(K) + 15) & ~size_t(15)));  // [warp][lane][j]
+    R* wred = red + (kAdjThreads / 32) * 32 * kDiagKA;                                             // [warp][g]
     for (int i = threadIdx.x; i < A.ntab; i += kAdjThreads) stab[i] = tab[i];
     __syncthreads();
-    DiagGrad<P> acc[kAdjDiagMaxG];
-    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t x = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < A.n_amp; x += stride) {
-        C p = psi[x], l = lam[x];
-        if (A.ng) {
-            typename DiagTermType<P>::type w;
-            DiagGrad<P>::term(l, p, w);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t T = uint64_t(gridDim.x) * kAdjThreads;
+    const uint64_t t = uint64_t(blockIdx.x) * kAdjThreads + threadIdx.x;
+    const uint64_t J = (A.n_amp + T - 1) / T;
+    const uint64_t gz = lane < A.ng ? A.gz[lane] : 0;
+    R gsum;  // lane g: this warp's sum for gradient term g
+    R* myred = red + (size_t(warp) * 32) * kDiagKA;
+    for (uint64_t j0 = 0; j0 < J; j0 += kDiagKA) {
+        R acc[kDiagKA];
 #pragma unroll
-            for (int g = 0; g < kAdjDiagMaxG; g++)
-                if (g < A.ng) acc[g].add(w, parity64(x & A.gz[g]) != 0);
-        }
-        K f = kone<K>();
-        int sign = 0;
+        for (int j = 0; j < kDiagKA; j++) {
+            const uint64_t x = (j0 + j) * T + t;
+            if (j0 + j >= J || x >= A.n_amp) continue;
+            C p = psi[x], l = lam[x];
+            if (A.ng) acc[j] = im_conj_prod(l, p, R());
+            K f = kone<K>();
+            int sign = 0;
 #pragma unroll 1
-        for (int k = 0; k < A.nf; k++) {
-            const AdjDiagFactor& F = A.f[k];
-            if ((x & F.cond_mask) != F.cond_val) continue;
-            sign ^= parity64(x & F.zmask);
-            if (F.sign_only) {
-                sign ^= 1;
-            } else if (F.tab_off >= 0) {
-                int li = 0;
-                for (int j = 0; j < F.nq; j++) li |= int((x >> F.q[j]) & 1) << j;
-                f = kmul(f, stab[F.tab_off + li]);
+            for (int k = 0; k < A.nf; k++) {
+                const AdjDiagFactor& F = A.f[k];
+                if ((x & F.cond_mask) != F.cond_val) continue;
+                sign ^= parity64(x & F.zmask);
+                if (F.sign_only) {
+                    sign ^= 1;
+                } else if (F.tab_off >= 0) {
+                    int li = 0;
+                    for (int b = 0; b < F.nq; b++) li |= int((x >> F.q[b]) & 1) << b;
+                    f = kmul(f, stab[F.tab_off + li]);
+                }
             }
+            p = P::out(P::first(f, p));
+            l = P::out(P::first(f, l));
+            if (sign) {
+                p = P::ipow(p, 2);
+                l = P::ipow(l, 2);
+            }
+            psi[x] = p;
+            lam[x] = l;
         }
-        p = P::out(P::first(f, p));
-        l = P::out(P::first(f, l));
-        if (sign) {
-            p = P::ipow(p, 2);
-            l = P::ipow(l, 2);
-        }
-        psi[x] = p;
-        lam[x] = l;
-    }
-    __shared__ double sh[kAdjThreads / 32];
-#pragma unroll 1
-    for (int g = 0; g < A.ng; g++) {
-        double v = 0.0;
+        if (A.ng) {
 #pragma unroll
-        for (int h = 0; h < kAdjDiagMaxG; h++)
-            if (h == g) v = acc[h].value();
-        const double r = block_sum<kAdjThreads>(v, sh);
-        if (threadIdx.x == 0) part[size_t(g) * gridDim.x + blockIdx.x] = r;
+            for (int j = 0; j < kDiagKA; j++) myred[lane * kDiagKA + j] = acc[j];
+            __syncwarp();
+            if (lane < A.ng) {
+                const uint64_t t0 = t - uint64_t(lane);
+                for (int src = 0; src < 32; src++)
+#pragma unroll
+                    for (int j = 0; j < kDiagKA; j++) {
+                        const uint64_t x = (j0 + j) * T + t0 + uint64_t(src);
+                        gsum.add(myred[src * kDiagKA + j], parity64(x & gz) != 0);
+                    }
+            }
+            __syncwarp();
+        }
+    }
+    if (A.ng) {
+        if (lane < A.ng) wred[warp * 32 + lane] = gsum;
+        __syncthreads();
+        if (threadIdx.x < A.ng) {
+            R total;
+            for (int w = 0; w < kAdjThreads / 32; w++) total.add(wred[w * 32 + threadIdx.x], false);
+            part[size_t(threadIdx.x) * gridDim.x + blockIdx.x] = total.value();
+        }
     }
 }
 
-int sm_count_adj() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    return sms;
+size_t adj_diag_smem(int ntab, Arith ar) {
+    const size_t rs = ar == Arith::F64 ? sizeof(double) : 2 * sizeof(float);
+    return ((size_t(ntab) * kernel_entry_bytes(ar) + 15) & ~size_t(15)) + rs * (kAdjThreads / 32) * 32 * (kDiagKA + 1);
 }
 
 template <typename P>
@@ -258,8 +277,10 @@ void launch_rot(void* psi, void* lam, int n, int qubit, int axis, double theta, 
 
 unsigned adj_grid(int n) {
     const uint64_t pairs = 1ull << (n - 1);
-    const uint64_t want = (pairs + kAdjThreads - 1) / kAdjThreads;
-    return unsigned(std::max<uint64_t>(1, std::min<uint64_t>(want, uint64_t(sm_count_adj()) * 8)));
+    // a power of two (the diagonal-run kernel's amplitude partition relies on it)
+    uint64_t want = 1;
+    while (want * 2 * kAdjThreads <= pairs && want < 1024) want *= 2;
+    return unsigned(want);
 }
 
 void launch_adjoint_rotation(void* psi, void* lam, int n, Arith ar, int qubit, int axis, double theta, double* part,
@@ -274,7 +295,7 @@ void launch_adjoint_rotation(void* psi, void* lam, int n, Arith ar, int qubit, i
 
 void launch_adjoint_diag(void* psi, void* lam, int n, Arith ar, const void* tab, const AdjDiagParams& A, double* part,
                          unsigned grid, cudaStream_t st) {
-    const size_t smem = size_t(A.ntab) * kernel_entry_bytes(ar);
+    const size_t smem = adj_diag_smem(A.ntab, ar);
     switch (ar) {
         case Arith::F32:
             k_adj_diag<NativeArith<float>><<<grid, kAdjThreads, smem, st>>>(

@@ -826,7 +826,9 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
     int nslots = 0;
     {
         std::vector<int> run;       // gate indices, reverse order
+        int run_f = 0, run_g = 0, run_t = 0;  // its factor, gradient and table-entry bounds
         auto flush = [&]() {
+            run_f = run_g = run_t = 0;
             if (run.empty()) return;
             Step stp;
             stp.kind = 1;
@@ -913,16 +915,13 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
             if (diag && diag_param) {
                 // bound the run by the kernel's factor, gradient and table limits (worst case)
                 const int tab_need = op.kind == OpKind::Diag ? (1 << op.targets.size()) : 1;
-                int nf = 0, ng = 0, nt = 0;
-                for (int gi : run) {
-                    const Op o2 = op_of_gate(c->gates[gi], c->n, theta);
-                    nf++;
-                    nt += o2.kind == OpKind::Diag ? (1 << o2.targets.size()) : 1;
-                    ng += c->gates[gi].param_index >= 0;
-                }
-                if (nf + 1 > kAdjDiagMaxF || ng + (g.param_index >= 0) > kAdjDiagMaxG || nt + tab_need > kAdjDiagMaxTab)
+                if (run_f + 1 > kAdjDiagMaxF || run_g + (g.param_index >= 0) > kAdjDiagMaxG ||
+                    run_t + tab_need > kAdjDiagMaxTab)
                     flush();
                 run.push_back(i);
+                run_f += 1;
+                run_g += g.param_index >= 0;
+                run_t += tab_need;
                 continue;
             }
             flush();

@@ -169,7 +169,7 @@ void launch_adjoint_rotation(void* psi, void* lam, int n, Arith ar, int qubit, i
 // Reverse step for a run of diagonal gates on psi and lam (both multiplied by the run's inverse),
 // with the gradient partials of the run's diagonal rotations exp(i theta P / 2) (P a Z string
 // gz[g]) computed before: part[g * grid + block] = block's sum of (-1)^popc(x & gz[g]) Im(conj(lam_x) psi_x).
-constexpr int kAdjDiagMaxF = 24;
+constexpr int kAdjDiagMaxF = 48;
 constexpr int kAdjDiagMaxG = 24;
 constexpr int kAdjDiagMaxTab = 1024;
 struct AdjDiagFactor {

@@ -361,6 +361,8 @@ void prepare_oz4_matrix(const std::vector<cplx>& K, unsigned char* host_out) {
     QS_REQUIRE(K.size() == size_t(kOzD) * kOzD, "tensor-core double-float path takes 4-target matrices");
     std::memset(host_out, 0, oz4_matrix_bytes());
     float* mu = reinterpret_cast<float*>(host_out + kOzMat);
+    double magic[kOzNS];
+    for (int t = 0; t < kOzNS; t++) magic[t] = 1.5 * std::ldexp(1.0, 52 - 8 * (t + 1));
     for (int n = 0; n < kOzR; n++) {
         double m = 0.0;
         for (int k = 0; k < kOzR; k++) m = std::max(m, std::fabs(real_form(K, n, k)));
@@ -374,8 +376,9 @@ void prepare_oz4_matrix(const std::vector<cplx>& K, unsigned char* host_out) {
         for (int k = 0; k < kOzR; k++) {
             double r = real_form(K, n, k) / scale;  // exact (power of two), |r| <= 1
             for (int t = 0; t < kOzNS; t++) {
-                const double u = std::ldexp(1.0, -8 * (t + 1));
-                const double a = std::nearbyint(r / u) * u;
+                // r rounded to a multiple of u = 2^-8(t+1): (r + c) - c with c = 1.5 * 2^52 * u
+                // (|r| is far below 2^51 u, so the sum stays in c's binade; exact in FP64)
+                const double a = (r + magic[t]) - magic[t];
                 r -= a;
                 const int row = t * kOzR + n;
                 const size_t off = size_t(row >> 3) * kOzSbo + size_t(k >> 3) * kOzLbo + size_t(row & 7) * 16 +
