@@ -97,6 +97,74 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rot(typename P::C* __restri
     if (threadIdx.x == 0) part[blockIdx.x] = v;
 }
 
+// Two consecutive reverse steps for rotations on distinct qubits a (later in the circuit) and b:
+// each group of four amplitudes (bits a, b) gets the gradient partial of a, the un-apply of
+// R_a, then the gradient partial of b and the un-apply of R_b, all in registers. Partials of a
+// go to part[0 .. grid), those of b to part[grid .. 2 grid).
+template <typename P>
+struct AdjRot2Params {
+    IndexPlan ip;            // bits a and b inserted
+    uint64_t bit[2];         // 1 << a, 1 << b
+    typename P::K U[2][4];   // R_a^+, R_b^+
+    int32_t axis[2];
+};
+
+template <typename P>
+__device__ __forceinline__ void rot_step(typename P::C& a, typename P::C& b, typename P::C& la, typename P::C& lb,
+                                         int axis, const typename P::K* U, GradAcc<P>& g) {
+    if (axis == 1) {
+        g.add(la, b);
+        g.add(lb, a);
+    } else if (axis == 2) {
+        g.add(la, P::ipow(b, 3));
+        g.add(lb, P::ipow(a, 1));
+    } else {
+        g.add(la, a);
+        g.add(lb, P::ipow(b, 2));
+    }
+    typename P::Acc r0 = P::first(U[0], a), r1 = P::first(U[2], a), s0 = P::first(U[0], la), s1 = P::first(U[2], la);
+    P::mac(r0, U[1], b);
+    P::mac(r1, U[3], b);
+    P::mac(s0, U[1], lb);
+    P::mac(s1, U[3], lb);
+    a = P::out(r0);
+    b = P::out(r1);
+    la = P::out(s0);
+    lb = P::out(s1);
+}
+
+template <typename P>
+__global__ void __launch_bounds__(kAdjThreads) k_adj_rot2(typename P::C* __restrict__ psi, typename P::C* __restrict__ lam,
+                                                           const __grid_constant__ AdjRot2Params<P> A, double* part) {
+    using C = typename P::C;
+    GradAcc<P> ga, gb;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < A.ip.n_iter; i += stride) {
+        const uint64_t i0 = expand(i, A.ip);
+        const uint64_t ix[4] = {i0, i0 | A.bit[0], i0 | A.bit[1], i0 | A.bit[0] | A.bit[1]};
+        C v[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            v[e] = psi[ix[e]];
+            l[e] = lam[ix[e]];
+        }
+        rot_step<P>(v[0], v[1], l[0], l[1], A.axis[0], A.U[0], ga);  // pairs along a
+        rot_step<P>(v[2], v[3], l[2], l[3], A.axis[0], A.U[0], ga);
+        rot_step<P>(v[0], v[2], l[0], l[2], A.axis[1], A.U[1], gb);  // pairs along b
+        rot_step<P>(v[1], v[3], l[1], l[3], A.axis[1], A.U[1], gb);
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            psi[ix[e]] = v[e];
+            lam[ix[e]] = l[e];
+        }
+    }
+    __shared__ double sh[kAdjThreads / 32];
+    const double va = block_sum<kAdjThreads>(ga.imag(), sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = va;
+    const double vb = block_sum<kAdjThreads>(gb.imag(), sh);
+    if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = vb;
+}
+
 // out[s] = sum of part[s * nb .. s * nb + nb) in a fixed order, one block per slot
 __global__ void __launch_bounds__(kAdjThreads) k_slot_sums(const double* __restrict__ part, int nb, double* out) {
     __shared__ double sh[kAdjThreads / 32];
@@ -255,6 +323,30 @@ size_t adj_diag_smem(int ntab, Arith ar) {
     return ((size_t(ntab) * kernel_entry_bytes(ar) + 15) & ~size_t(15)) + rs * (kAdjThreads / 32) * 32 * (kDiagKA + 1);
 }
 
+// R_P(theta)^+ = cos(theta/2) I - i sin(theta/2) P as a row-major 2x2 matrix
+void rot_dagger(int axis, double theta, cplx (&U)[4]) {
+    const double c = std::cos(theta / 2), s = std::sin(theta / 2);
+    if (axis == 1) { U[0] = c; U[1] = cplx(0, -s); U[2] = cplx(0, -s); U[3] = c; }
+    else if (axis == 2) { U[0] = c; U[1] = -s; U[2] = s; U[3] = c; }
+    else { U[0] = cplx(c, -s); U[1] = 0.0; U[2] = 0.0; U[3] = cplx(c, s); }
+}
+
+template <typename P>
+void launch_rot2(void* psi, void* lam, int n, const int (&qubit)[2], const int (&axis)[2], const double (&theta)[2],
+                 double* part, unsigned grid, cudaStream_t st) {
+    AdjRot2Params<P> A;
+    A.ip = make_index_plan(n, {qubit[0], qubit[1]}, 0);
+    for (int r = 0; r < 2; r++) {
+        A.bit[r] = 1ull << qubit[r];
+        A.axis[r] = axis[r];
+        cplx U[4];
+        rot_dagger(axis[r], theta[r], U);
+        for (int e = 0; e < 4; e++) A.U[r][e] = P::host_k(U[e].real(), U[e].imag());
+    }
+    k_adj_rot2<P><<<grid, kAdjThreads, 0, st>>>(reinterpret_cast<typename P::C*>(psi),
+                                                reinterpret_cast<typename P::C*>(lam), A, part);
+}
+
 template <typename P>
 void launch_rot(void* psi, void* lam, int n, int qubit, int axis, double theta, double* part, unsigned grid,
                 cudaStream_t st) {
@@ -289,6 +381,16 @@ void launch_adjoint_rotation(void* psi, void* lam, int n, Arith ar, int qubit, i
         case Arith::F32: launch_rot<NativeArith<float>>(psi, lam, n, qubit, axis, theta, part, grid, st); break;
         case Arith::F64: launch_rot<NativeArith<double>>(psi, lam, n, qubit, axis, theta, part, grid, st); break;
         case Arith::DF: launch_rot<DFArith>(psi, lam, n, qubit, axis, theta, part, grid, st); break;
+    }
+    QS_TRY_CUDA(cudaGetLastError());
+}
+
+void launch_adjoint_rotation2(void* psi, void* lam, int n, Arith ar, const int (&qubit)[2], const int (&axis)[2],
+                              const double (&theta)[2], double* part, unsigned grid, cudaStream_t st) {
+    switch (ar) {
+        case Arith::F32: launch_rot2<NativeArith<float>>(psi, lam, n, qubit, axis, theta, part, grid, st); break;
+        case Arith::F64: launch_rot2<NativeArith<double>>(psi, lam, n, qubit, axis, theta, part, grid, st); break;
+        case Arith::DF: launch_rot2<DFArith>(psi, lam, n, qubit, axis, theta, part, grid, st); break;
     }
     QS_TRY_CUDA(cudaGetLastError());
 }

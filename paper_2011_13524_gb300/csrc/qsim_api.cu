@@ -814,8 +814,9 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
         return g.param_index >= 0 && g.mc == 0 && (g.named == QS_NAMED_RX || g.named == QS_NAMED_RY);
     };
     struct Step {
-        int kind = 0;               // 0 rotation, 1 diagonal run, 2 other gate
-        int gate = -1;              // kinds 0 and 2
+        int kind = 0;               // 0 rotation, 1 diagonal run, 2 other gate, 3 two rotations
+        int gate = -1;              // kinds 0, 2 and 3
+        int gate2 = -1;             // kind 3: the second rotation (slot slot0 + 1)
         int slot0 = 0;              // first gradient slot
         AdjDiagParams A;            // kind 1
         size_t tab_byte = 0;        // kind 1: offset of its tables in the upload
@@ -937,6 +938,23 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
         }
         flush();
     }
+    // two consecutive rotation steps on distinct qubits share one pass (their slots are adjacent)
+    {
+        std::vector<Step> merged;
+        for (size_t i = 0; i < steps.size(); i++) {
+            if (i + 1 < steps.size() && steps[i].kind == 0 && steps[i + 1].kind == 0 &&
+                c->gates[steps[i].gate].targets[0] != c->gates[steps[i + 1].gate].targets[0] && c->n >= 2) {
+                Step m = steps[i];
+                m.kind = 3;
+                m.gate2 = steps[i + 1].gate;
+                merged.push_back(m);
+                i++;
+                continue;
+            }
+            merged.push_back(steps[i]);
+        }
+        steps.swap(merged);
+    }
     const unsigned nb = adj_grid(c->n);
     double* d_part = nullptr;
     void* d_tab = nullptr;
@@ -960,6 +978,16 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
                 continue;
             }
             const qs_gate& g = c->gates[stp.gate];
+            if (stp.kind == 3) {
+                const qs_gate& g2 = c->gates[stp.gate2];
+                const int q[2] = {g.targets[0], g2.targets[0]};
+                const int ax[2] = {g.named == QS_NAMED_RX ? 1 : 2, g2.named == QS_NAMED_RX ? 1 : 2};
+                const double th[2] = {theta ? theta[g.param_index] : g.params[0], theta ? theta[g2.param_index] : g2.params[0]};
+                launch_adjoint_rotation2(psi->data, lam->data, c->n, ar, q, ax, th, d_part + size_t(stp.slot0) * nb, nb, st);
+                slot_param[stp.slot0] = g.param_index;
+                slot_param[stp.slot0 + 1] = g2.param_index;
+                continue;
+            }
             if (stp.kind == 0) {
                 const int axis = g.named == QS_NAMED_RX ? 1 : 2;
                 const double th = theta ? theta[g.param_index] : g.params[0];

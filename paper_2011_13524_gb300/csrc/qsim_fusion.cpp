@@ -23,8 +23,10 @@
 // applying each gate, in circuit order, to the columns of the block matrix.
 #include <algorithm>
 #include <cstring>
+#include <exception>
 #include <list>
 #include <mutex>
+#include <thread>
 
 #include "qsim_internal.h"
 
@@ -89,15 +91,14 @@ bool dense_is_diagonal(const DenseOp& d) {
     return true;
 }
 
-void emit(const OpenBlock& b, const qs_circuit* c, const double* theta, FusionPlan& plan) {
+FusedBlock emit(const OpenBlock& b, const qs_circuit* c, const double* theta) {
     FusedBlock fb;
     for (int q = 0; q < 64; q++)
         if ((b.mask >> q) & 1) fb.qubits.push_back(q);
     fb.n_gates = int(b.gates.size());
     if (b.gates.size() == 1) {
         fb.single_gate = b.gates[0];
-        plan.blocks.push_back(std::move(fb));
-        return;
+        return fb;
     }
     const int w = int(fb.qubits.size());
     const int D = 1 << w;
@@ -115,7 +116,7 @@ void emit(const OpenBlock& b, const qs_circuit* c, const double* theta, FusionPl
         apply_to_columns(fb.mat, w, d, lt, lc);
     }
     fb.diagonal = diag;
-    plan.blocks.push_back(std::move(fb));
+    return fb;
 }
 
 // Partition 1: open-block greedy. Returns the blocks in emission order.
@@ -330,7 +331,30 @@ FusionPlan plan_fusion(const qs_circuit* c, int k, const double* theta) {
     plan.n = c->n;
     plan.k = k;
     plan.n_source_gates = c->n_gates;
-    for (const OpenBlock& blk : partition(c, masks, k)) emit(blk, c, theta, plan);
+    // block matrices: independent of each other, built by several host threads for long plans
+    const std::vector<OpenBlock> parts = partition(c, masks, k);
+    plan.blocks.resize(parts.size());
+    size_t work = 0;
+    for (const OpenBlock& blk : parts) work += blk.gates.size() << (2 * __builtin_popcountll(blk.mask));
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const unsigned nth = work < (1u << 16) ? 1u : std::min<unsigned>(std::min(hw, 8u), unsigned(parts.size()));
+    if (nth <= 1) {
+        for (size_t i = 0; i < parts.size(); i++) plan.blocks[i] = emit(parts[i], c, theta);
+    } else {
+        std::vector<std::thread> pool;
+        std::vector<std::exception_ptr> errs(nth);
+        for (unsigned w = 0; w < nth; w++)
+            pool.emplace_back([&, w]() {
+                try {
+                    for (size_t i = w; i < parts.size(); i += nth) plan.blocks[i] = emit(parts[i], c, theta);
+                } catch (...) {
+                    errs[w] = std::current_exception();
+                }
+            });
+        for (auto& th : pool) th.join();
+        for (auto& e : errs)
+            if (e) std::rethrow_exception(e);
+    }
     // keep copies of the gates that stay unfused (their matrices are rebuilt at launch)
     for (auto& b : plan.blocks) {
         if (b.single_gate < 0) continue;

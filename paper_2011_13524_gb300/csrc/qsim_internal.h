@@ -166,6 +166,10 @@ void launch_apply_observable(const std::vector<PauliGroup>& groups, const void* 
 unsigned adj_grid(int n);
 void launch_adjoint_rotation(void* psi, void* lam, int n, Arith ar, int qubit, int axis, double theta, double* part,
                              unsigned grid, cudaStream_t st);
+// Two consecutive rotation steps on distinct qubits (qubit[0] first), one pass: partials of the
+// first into part[0 .. grid), of the second into part[grid .. 2 grid).
+void launch_adjoint_rotation2(void* psi, void* lam, int n, Arith ar, const int (&qubit)[2], const int (&axis)[2],
+                              const double (&theta)[2], double* part, unsigned grid, cudaStream_t st);
 // Reverse step for a run of diagonal gates on psi and lam (both multiplied by the run's inverse),
 // with the gradient partials of the run's diagonal rotations exp(i theta P / 2) (P a Z string
 // gz[g]) computed before: part[g * grid + block] = block's sum of (-1)^popc(x & gz[g]) Im(conj(lam_x) psi_x).
