@@ -448,6 +448,32 @@ def measure_extras(args, qs, torch, circuit):
                             "norm2_c64": c.norm2(), "norm2_c128": a.norm2()}
     del a, c
     torch.cuda.empty_cache()
+    # the comparison circuit of Sec. 7 (RZ RX RZ layers, CNOT ring, 10 repetitions), n = 30,
+    # complex128 at the autotuned width
+    cc = W.rzrxrz_cnot_circuit(n, 10, args.seed)
+    kc, _ = qs.autotune_fusion(cc, qs.QS_C128)
+    plc = qs.FusedCircuit(cc, max(kc, 1))
+    stc = qs.State(n, qs.QS_C128)
+    ms = timed(lambda: (stc.set_basis(0), stc.apply_plan(plc)))
+    out["comparison_circuit_gates"] = len(cc.gates)
+    out["comparison_circuit_fusion_k"] = kc
+    out["comparison_circuit_blocks"] = plc.n_blocks
+    out["comparison_circuit_gates_per_s"] = len(cc.gates) / (ms / 1e3)
+    del stc
+    torch.cuda.empty_cache()
+    # Pauli rotation of an n-qubit X/Y/Z string (one pass over amplitude pairs), and one Trotter
+    # slice of the transverse-field Ising chain (2n - 1 Pauli rotations), complex128 double-float
+    stp = qs.State(n, qs.QS_C128)
+    xm = sum(1 << q for q in range(n) if q % 3 != 2)
+    zm = sum(1 << q for q in range(n) if q % 3 != 0)
+    ms = timed(lambda: stp.apply_pauli_rotation(xm, zm, 0.3), reps=3)
+    out["pauli_rotation_call_n30_ms"] = ms  # one public call: includes the double-float layout passes
+    tf = W.tfim_observable(n, 1.0)
+    ms = timed(lambda: stp.apply_observable_rotation(tf, 0.1, 1))
+    out["tfim_trotter_slice_n30_ms"] = ms
+    out["pauli_rotation_in_trotter_n30_gbps"] = tf.n_terms * 2 * 16 * 2.0 ** n / (ms / 1e3) / 1e9
+    del stp
+    torch.cuda.empty_cache()
     # n = 33 complex128 (128 GiB state), same circuit family at depth 20, autotuned width
     try:
         c33 = W.u3cz_circuit(33, args.depth, args.seed)

@@ -199,6 +199,17 @@ qs_status qs_apply_fused(qs_state* s, int k, const int* targets, const double* m
  * with qs_autotune_fusion. c->n must equal the state's n. */
 qs_status qs_run_circuit(qs_state* s, const qs_circuit* c, int fusion_k);
 
+/* Pauli rotation gate (Sec. 4.3.2): psi <- exp(i angle P / 2) psi = cos(angle/2) psi +
+ * i sin(angle/2) P psi, the half-angle convention of the RX/RY/RZ table, for a Pauli string P of
+ * any length given by masks as in qs_pauli_obs (bit q of x_mask: X or Y on qubit q; of z_mask:
+ * Z or Y). One O(2^n) pass whatever the length. Masks naming a qubit >= n -> QS_ERR_INVALID_ARG. */
+qs_status qs_apply_pauli_rotation(qs_state* s, uint64_t x_mask, uint64_t z_mask, double angle);
+/* Time evolution under an observable by the first-order Trotter decomposition (Sec. 4.5,
+ * observable rotation): psi <- [prod_k exp(i (angle / n_slices) alpha_k P_k)]^n_slices psi, terms
+ * in the observable's order, each factor a Pauli rotation with angle 2 angle alpha_k / n_slices
+ * (an identity term is a global phase). Exact for commuting terms. n_slices >= 1. */
+qs_status qs_apply_observable_rotation(qs_state* s, const qs_pauli_obs* H, double angle, int n_slices);
+
 /* ---------------------------------------------------------------- fusion (Sec. 5.4) */
 /* Plans the fused circuit for width k (2..6) without applying it. */
 qs_status qs_plan_fusion(const qs_circuit* c, int k, qs_fused_circuit** out);
@@ -223,6 +234,7 @@ qs_status qs_destroy_fused(qs_fused_circuit* f);
 #define QS_KERNEL_DENSE_DF 6   /* complex128 dense gate matrix in double-float arithmetic */
 #define QS_KERNEL_DENSE_TC 7   /* complex64 dense block of 5-6 targets on the tensor cores (3xTF32) */
 #define QS_KERNEL_DENSE_OZ 8   /* double-float complex128 block of 4 targets on the tensor cores (bf16 slices) */
+#define QS_KERNEL_PAULI_ROT 9  /* Pauli rotation exp(i phi P / 2), one pass over amplitude pairs */
 qs_status qs_fused_block_cost(const qs_fused_circuit* f, int b, qs_dtype dt, int* kernel, int* launches,
                               double* bytes);
 /* Applies a plan like qs_apply_fused_circuit, recording a CUDA event on the state's stream

@@ -198,6 +198,22 @@ def apply_pauli(psi: np.ndarray, n: int, xmask: int, zmask: int) -> np.ndarray:
     return out
 
 
+def apply_pauli_rotation(psi: np.ndarray, n: int, xmask: int, zmask: int, angle: float) -> np.ndarray:
+    """exp(i angle P / 2) psi = cos(angle/2) psi + i sin(angle/2) P psi (Sec. 4.3.2 Pauli rotation,
+    the half-angle convention of the rotation gates), P given by masks."""
+    return math.cos(angle / 2) * psi + 1j * math.sin(angle / 2) * apply_pauli(psi, n, xmask, zmask)
+
+
+def observable_rotation(psi: np.ndarray, n: int, obs, angle: float, n_slices: int) -> np.ndarray:
+    """First-order Trotter product [prod_k exp(i (angle / r) coef_k P_k)]^r psi, terms in order
+    (Sec. 4.5 observable rotation)."""
+    out = np.array(psi, dtype=np.complex128, copy=True)
+    for _ in range(n_slices):
+        for c, xm, zm in zip(obs.coef, obs.x_mask, obs.z_mask):
+            out = apply_pauli_rotation(out, n, int(xm), int(zm), 2.0 * angle * float(c) / n_slices)
+    return out
+
+
 # ---------------------------------------------------------------- reductions
 def expectation(psi: np.ndarray, obs) -> Tuple[float, float]:
     """(Re, Im) of sum_k coef_k <psi|P_k|psi>."""

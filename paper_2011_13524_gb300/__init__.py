@@ -39,7 +39,7 @@ QS_MAX_CONTROLS = 8
 
 QS_GATE_DENSE, QS_GATE_DIAG, QS_GATE_PAULI, QS_GATE_NAMED = 0, 1, 2, 3
 KERNEL_NAMES = {0: "dense_reg", 1: "dense_smem", 2: "diag", 3: "phase", 4: "pauli", 5: "swap", 6: "dense_df",
-                7: "dense_tc", 8: "dense_oz"}
+                7: "dense_tc", 8: "dense_oz", 9: "pauli_rot"}
 NAMED = {
     "X": 1, "Y": 2, "Z": 3, "H": 4, "S": 5, "Sdag": 6, "T": 7, "Tdag": 8, "sqrtX": 9,
     "sqrtXdag": 10, "sqrtY": 11, "sqrtYdag": 12, "RX": 13, "RY": 14, "RZ": 15, "U1": 16,
@@ -101,6 +101,8 @@ _SIGNATURES = {
     "qs_copy_state": ([_VOIDP, _VOIDP], ctypes.c_int),
     "qs_synchronize": ([_VOIDP], ctypes.c_int),
     "qs_apply_gate": ([_VOIDP, ctypes.POINTER(QsGate)], ctypes.c_int),
+    "qs_apply_pauli_rotation": ([_VOIDP, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double], ctypes.c_int),
+    "qs_apply_observable_rotation": ([_VOIDP, ctypes.POINTER(QsPauliObs), ctypes.c_double, ctypes.c_int], ctypes.c_int),
     "qs_apply_fused": ([_VOIDP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _DP], ctypes.c_int),
     "qs_run_circuit": ([_VOIDP, ctypes.POINTER(QsCircuit), ctypes.c_int], ctypes.c_int),
     "qs_plan_fusion": ([ctypes.POINTER(QsCircuit), ctypes.c_int, ctypes.POINTER(_VOIDP)], ctypes.c_int),
@@ -367,6 +369,15 @@ class State:
         return np.array(out[: plan.n_blocks], dtype=np.float64)
 
     # -- reductions
+    def apply_pauli_rotation(self, x_mask: int, z_mask: int, angle: float) -> None:
+        """psi <- exp(i angle P / 2) psi for the Pauli string given by the masks (any length)."""
+        check(lib().qs_apply_pauli_rotation(self.handle, int(x_mask), int(z_mask), float(angle)))
+
+    def apply_observable_rotation(self, obs, angle: float, n_slices: int = 1) -> None:
+        """First-order Trotter evolution exp(i angle H) of the observable H in n_slices steps."""
+        o, keep = make_obs(obs)
+        check(lib().qs_apply_observable_rotation(self.handle, ctypes.byref(o), float(angle), int(n_slices)))
+
     def expectation(self, obs) -> Tuple[float, float]:
         o, keep = make_obs(obs)
         out = (ctypes.c_double * 2)()

@@ -65,6 +65,7 @@ Op dagger(const Op& op) {
             for (auto& v : r.data) v = std::conj(v);
             break;
         case OpKind::Phase: r.phase = std::conj(op.phase); break;
+        case OpKind::PauliRot: r.angle = -op.angle; break;
         case OpKind::Pauli:
         case OpKind::Swap: break;
     }
@@ -151,6 +152,7 @@ void op_cost(const Op& op, int n, qs_dtype dt, int* kernel, int* launches, doubl
             else if (op.xmask == 0) by = 1.5 * S * touched;   // read all, write the odd-parity half
             break;
         case OpKind::Swap: k = QS_KERNEL_SWAP; by = S * touched; break;
+        case OpKind::PauliRot: k = QS_KERNEL_PAULI_ROT; break;
     }
     if (kernel) *kernel = k;
     if (launches) *launches = l;
@@ -319,6 +321,11 @@ Op probe_like(const Op& op, int np_) {
             break;
         case OpKind::Pauli: p.xmask = 1ull << q(1); break;
         case OpKind::Swap: p.targets = {q(0), q(1)}; break;
+        case OpKind::PauliRot:
+            p.xmask = (1ull << q(1)) | (1ull << q(0));
+            p.zmask = 1ull << q(0);
+            p.angle = 0.7;
+            break;
     }
     return p;
 }
@@ -746,6 +753,43 @@ qs_status qs_norm2(const qs_state* s, double* out) {
     check_state(s);
     QS_REQUIRE(out != nullptr, "null output");
     reduce_norm2(const_cast<qs_state*>(s), out);
+    API_END
+}
+
+qs_status qs_apply_pauli_rotation(qs_state* s, uint64_t x_mask, uint64_t z_mask, double angle) {
+    API_BEGIN
+    QS_REQUIRE(s != nullptr, "null state");
+    const uint64_t all = s->n >= 64 ? ~0ull : ((1ull << s->n) - 1);
+    QS_REQUIRE(((x_mask | z_mask) & ~all) == 0, "Pauli mask names a qubit outside the state");
+    Op op;
+    op.kind = OpKind::PauliRot;
+    op.xmask = x_mask;
+    op.zmask = z_mask;
+    op.angle = angle;
+    DFScope df(s, use_df(s));
+    launch_op_arith(op, s->data, s->n, arith_of(s), s->stream, stage_of(s));
+    API_END
+}
+
+qs_status qs_apply_observable_rotation(qs_state* s, const qs_pauli_obs* H, double angle, int n_slices) {
+    API_BEGIN
+    QS_REQUIRE(s != nullptr && H != nullptr, "null state or observable");
+    QS_REQUIRE(n_slices >= 1, "n_slices must be positive");
+    QS_REQUIRE(H->n_terms >= 0 && (H->n_terms == 0 || (H->coef && H->x_mask && H->z_mask)), "null observable arrays");
+    const uint64_t all = s->n >= 64 ? ~0ull : ((1ull << s->n) - 1);
+    std::vector<Op> ops;
+    for (int k = 0; k < H->n_terms; k++) {
+        QS_REQUIRE(((H->x_mask[k] | H->z_mask[k]) & ~all) == 0, "Pauli mask names a qubit outside the state");
+        Op op;
+        op.kind = OpKind::PauliRot;
+        op.xmask = H->x_mask[k];
+        op.zmask = H->z_mask[k];
+        op.angle = 2.0 * angle * H->coef[k] / n_slices;  // exp(i (angle / r) alpha_k P_k)
+        ops.push_back(op);
+    }
+    DFScope df(s, use_df(s));
+    for (int r = 0; r < n_slices; r++)
+        for (const Op& op : ops) launch_op_arith(op, s->data, s->n, arith_of(s), s->stream, stage_of(s));
     API_END
 }
 

@@ -198,6 +198,39 @@ __global__ void __launch_bounds__(kThreads) k_pauli(typename P::C* __restrict__ 
     }
 }
 
+// ------------------------------------------------------------------ Pauli rotation
+// exp(i phi P / 2) = cos(phi/2) I + i sin(phi/2) P for a Pauli string P of any length (Sec.
+// 4.3.2, Pauli rotation gate), P|y> = i^nY (-1)^popc(y & zmask) |y ^ xmask>. With X or Y factors
+// the update pairs y (pivot bit 0) with y ^ xmask; a Z string (or the identity) is diagonal.
+template <typename P>
+struct PauliRotParams {
+    IndexPlan ip;
+    uint64_t xmask, zmask;
+    typename P::K c;      // cos(phi/2)
+    typename P::K kp, km;  // +- i^(1 + nY) sin(phi/2); diagonal case: cos +- i sin
+};
+
+template <typename P>
+__global__ void __launch_bounds__(kThreads) k_pauli_rot(typename P::C* __restrict__ psi,
+                                                        const __grid_constant__ PauliRotParams<P> Pm) {
+    using C = typename P::C;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < Pm.ip.n_iter; i += stride) {
+        const uint64_t y = expand(i, Pm.ip);
+        if (Pm.xmask == 0) {
+            psi[y] = P::out(P::first(parity64(y & Pm.zmask) ? Pm.km : Pm.kp, psi[y]));
+            continue;
+        }
+        const uint64_t y2 = y ^ Pm.xmask;
+        const C a = psi[y], b = psi[y2];
+        typename P::Acc ra = P::first(Pm.c, a), rb = P::first(Pm.c, b);
+        P::mac(ra, parity64(y2 & Pm.zmask) ? Pm.km : Pm.kp, b);
+        P::mac(rb, parity64(y & Pm.zmask) ? Pm.km : Pm.kp, a);
+        psi[y] = P::out(ra);
+        psi[y2] = P::out(rb);
+    }
+}
+
 // ------------------------------------------------------------------ SWAP
 // fixed bits: a = 1, b = 0 (+ controls); swap psi[x] <-> psi[x ^ (a | b)].
 struct SwapParams {
@@ -383,6 +416,28 @@ void launch_with(const Op& op, void* psi, int n, cudaStream_t st, void* stage) {
             Pm.zmask = op.zmask;
             Pm.nY = __builtin_popcountll(op.xmask & op.zmask);
             k_pauli<P><<<grid_for(ip.n_iter), kThreads, 0, st>>>(reinterpret_cast<C*>(psi), Pm);
+            return;
+        }
+        case OpKind::PauliRot: {
+            if (op.xmask) fixed.push_back(__builtin_ctzll(op.xmask));
+            IndexPlan ip = make_index_plan(n, fixed, setmask);
+            PauliRotParams<P> Pm;
+            Pm.ip = ip;
+            Pm.xmask = op.xmask;
+            Pm.zmask = op.zmask;
+            const double c = std::cos(op.angle / 2), sn = std::sin(op.angle / 2);
+            Pm.c = P::host_k(c, 0.0);
+            if (op.xmask) {
+                // i^(1 + nY) sin
+                const int e = (1 + __builtin_popcountll(op.xmask & op.zmask)) & 3;
+                const double re = e == 0 ? sn : e == 2 ? -sn : 0.0, im = e == 1 ? sn : e == 3 ? -sn : 0.0;
+                Pm.kp = P::host_k(re, im);
+                Pm.km = P::host_k(-re, -im);
+            } else {
+                Pm.kp = P::host_k(c, sn);
+                Pm.km = P::host_k(c, -sn);
+            }
+            k_pauli_rot<P><<<grid_for(ip.n_iter), kThreads, 0, st>>>(reinterpret_cast<C*>(psi), Pm);
             return;
         }
         case OpKind::Swap: {

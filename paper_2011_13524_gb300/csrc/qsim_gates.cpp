@@ -235,6 +235,24 @@ Op op_of_gate(const qs_gate& g, int n, const double* theta) {
         op.kind = OpKind::Swap;
         return op;
     }
+    if (named && g.named == QS_NAMED_PAULIROT) {
+        // a string with an X or Y factor: one pass over amplitude pairs whatever its length
+        // (Z strings stay diagonal gates below)
+        uint64_t xm = 0, zm = 0;
+        for (int j = 0; j < g.m; j++) {
+            const int id = g.pauli[j], q = d.targets[j];
+            if (id == 1 || id == 2) xm |= 1ull << q;
+            if (id == 2 || id == 3) zm |= 1ull << q;
+        }
+        if (xm) {
+            op.kind = OpKind::PauliRot;
+            op.targets.clear();
+            op.xmask = xm;
+            op.zmask = zm;
+            op.angle = angle(g, theta);
+            return op;
+        }
+    }
     if (is_diagonal(d.mat, D)) {
         std::vector<cplx> diag(D);
         for (int i = 0; i < D; i++) diag[i] = d.mat[size_t(i) * D + i];

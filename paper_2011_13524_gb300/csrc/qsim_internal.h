@@ -91,7 +91,7 @@ struct DenseOp {
 };
 
 // A gate decoded into the cheapest kernel that performs it.
-enum class OpKind { Dense, Diag, Phase, Pauli, Swap };
+enum class OpKind { Dense, Diag, Phase, Pauli, Swap, PauliRot };
 struct Op {
     OpKind kind = OpKind::Dense;
     std::vector<int> targets;
@@ -99,7 +99,8 @@ struct Op {
     std::vector<int> cvals;
     std::vector<cplx> data;   // Dense: matrix; Diag: diagonal
     cplx phase = 1.0;         // Phase: factor on the subspace where all fixed bits match
-    uint64_t xmask = 0, zmask = 0;  // Pauli
+    uint64_t xmask = 0, zmask = 0;  // Pauli, PauliRot
+    double angle = 0.0;             // PauliRot: exp(i angle P / 2)
     const void* dmat = nullptr;     // Dense, optional: device copy of `data` in the state's element type
     bool dmat_tc = false;           // dmat holds the tensor-core form (complex64, 6 targets)
     bool dmat_oz = false;           // dmat holds the sliced tensor-core form (double-float, 4 targets)

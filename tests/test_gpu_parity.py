@@ -368,6 +368,22 @@ def test_adjoint_hea_n12_vs_parameter_shift(qs):
     assert np.max(np.abs(g[idx] - ps)) < 1e-11
 
 
+@pytest.mark.parametrize("n", [12, 20])
+def test_comparison_circuit_vs_oracle(qs, n):
+    """The comparison circuit of Sec. 7 (RZ RX RZ rotation layers, CNOT ring with target i and
+    control (i + 1) mod n, 10 repetitions and a final layer): complex128 at the autotuned width
+    and complex64 against the oracle."""
+    c = W.rzrxrz_cnot_circuit(n, 10, 700 + n)
+    ref = oracle.run_circuit(c)
+    for dtype in (2, 1):
+        st = qs.State(n, dtype)
+        st.run(c, -1)
+        got = st.get_vector()
+        st.close()
+        assert maxabs(got, ref) < TOL[dtype], dtype
+        assert fidelity_gap(ref, got) < (1e-12 if dtype == 2 else 1e-6)
+
+
 @pytest.mark.parametrize("n", [24, 26])
 def test_circuit_family_vs_oracle_large(qs, n):
     """The depth-20 U3+CZ family at n = 24 and 26 against the FP64 oracle (the largest sizes the

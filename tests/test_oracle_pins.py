@@ -442,3 +442,62 @@ def test_parameter_shift_matches_brute_force_derivative():
         grads[g.param_index] = 2 * np.vdot(U @ psi0, O @ (dU @ psi0)).real
     ps = oracle.grad_parameter_shift(c, obs, range(c.n_params))
     assert np.max(np.abs(ps - grads)) < 1e-12
+
+
+# ---------------------------------------------------------------- Pauli and observable rotations
+def random_masks(n, rng):
+    xm = zm = 0
+    while xm == 0 and zm == 0:
+        for q in range(n):
+            pid = int(rng.next_u64() % 4)
+            if pid in (1, 2):
+                xm |= 1 << q
+            if pid in (2, 3):
+                zm |= 1 << q
+    return xm, zm
+
+
+@pytest.mark.parametrize("n", [1, 3, 5])
+def test_pauli_rotation_is_matrix_exponential(n):
+    """exp(i angle P / 2) by the oracle's pass equals scipy's expm of the Kronecker-built Pauli
+    string (Y strings, identity factors, every length)."""
+    rng = W.SplitMix64(40 + n)
+    for _ in range(6):
+        xm, zm = random_masks(n, rng)
+        angle = 4 * math.pi * rng.uniform() - 2 * math.pi
+        v = rand_vec(n, rng)
+        got = oracle.apply_pauli_rotation(v.copy(), n, xm, zm, angle)
+        ref = scipy.linalg.expm(1j * angle / 2 * pauli_full(n, xm, zm)) @ v
+        assert np.max(np.abs(got - ref)) < 1e-13
+    # the identity string is the global phase exp(i angle / 2)
+    v = rand_vec(n, rng)
+    assert np.max(np.abs(oracle.apply_pauli_rotation(v.copy(), n, 0, 0, 0.8) - np.exp(0.4j) * v)) < 1e-15
+
+
+def test_observable_rotation_commuting_terms_exact():
+    """For commuting terms (Z strings and an identity term) every Trotter slicing equals
+    expm(i angle H)."""
+    n = 4
+    obs = W.PauliObservable(n, np.array([0.7, -1.1, 0.4, 0.25]), np.zeros(4, dtype=np.uint64),
+                            np.array([0b0011, 0b0110, 0b1001, 0], dtype=np.uint64))
+    H = sum(c * pauli_full(n, int(x), int(z)) for c, x, z in zip(obs.coef, obs.x_mask, obs.z_mask))
+    rng = W.SplitMix64(3)
+    v = rand_vec(n, rng)
+    ref = scipy.linalg.expm(1j * 0.9 * H) @ v
+    for r in (1, 3, 10):
+        assert np.max(np.abs(oracle.observable_rotation(v, n, obs, 0.9, r) - ref)) < 1e-13
+
+
+def test_observable_rotation_trotter_error_falls_as_one_over_slices():
+    """Non-commuting terms (transverse-field Ising chain): the first-order product approaches
+    expm(i angle H) with an error falling like 1 / n_slices."""
+    n = 4
+    obs = W.tfim_observable(n, 1.0)
+    H = sum(c * pauli_full(n, int(x), int(z)) for c, x, z in zip(obs.coef, obs.x_mask, obs.z_mask))
+    rng = W.SplitMix64(4)
+    v = rand_vec(n, rng)
+    ref = scipy.linalg.expm(1j * 0.5 * H) @ v
+    err = {r: np.max(np.abs(oracle.observable_rotation(v, n, obs, 0.5, r) - ref)) for r in (1, 4, 16, 64)}
+    assert err[1] > 1e-3
+    for r in (4, 16, 64):
+        assert 0.15 < err[r] * r / err[1] < 2.0, err
