@@ -474,6 +474,20 @@ def measure_extras(args, qs, torch, circuit):
     out["pauli_rotation_in_trotter_n30_gbps"] = tf.n_terms * 2 * 16 * 2.0 ** n / (ms / 1e3) / 1e9
     del stp
     torch.cuda.empty_cache()
+    # analysis calls at n = 30 complex128: transition amplitude of the TFIM observable between two
+    # states, and 100000 Z-basis samples (uniforms from the seeded generator)
+    sa, sb = qs.State(n, qs.QS_C128), qs.State(n, qs.QS_C128)
+    for q in range(n):
+        sb.apply_gate(W.Gate("H", (q,)))
+    ms = timed(lambda: sa.transition_amplitude(tf, sb))
+    out["transition_amplitude_tfim_n30_ms"] = ms
+    rng = W.SplitMix64(args.seed)
+    uni = np.array([rng.uniform() for _ in range(100000)])
+    t0 = time.perf_counter()
+    sb.sample(uni)
+    out["sample_1e5_n30_ms"] = 1e3 * (time.perf_counter() - t0)
+    del sa, sb
+    torch.cuda.empty_cache()
     # n = 33 complex128 (128 GiB state), same circuit family at depth 20, autotuned width
     try:
         c33 = W.u3cz_circuit(33, args.depth, args.seed)

@@ -269,6 +269,18 @@ qs_status qs_expectation_noalloc(const void* dev_psi, int n, qs_dtype dt, void* 
                                  double out[2]);
 /* out = <a|b> (Sec. 4.2.2 inner_product) as (re, im); same n and dtype; synchronises. */
 qs_status qs_inner_product(const qs_state* a, const qs_state* b, double out[2]);
+/* Transition amplitude of an observable (Sec. 4.5): out = <bra|H|ket> = sum_k coef_k
+ * <bra|P_k|ket> as (re, im), FP64 sums. Both states must have the same n and dtype. */
+qs_status qs_transition_amplitude(const qs_state* bra, const qs_pauli_obs* H, const qs_state* ket, double out[2]);
+/* Marginal probability (Sec. 4.2.2): measured_value[q] for every qubit q is 0, 1 or 2
+ * (2 = any value); out = sum of |psi_x|^2 over the x that match (not divided by the norm).
+ * Other values -> QS_ERR_INVALID_ARG. */
+qs_status qs_marginal_probability(const qs_state* s, const int32_t* measured_value, double* out);
+/* Z-basis sampling (Sec. 4.2.2): out[k] = the first basis index x whose cumulative probability
+ * sum_{y <= x} |psi_y|^2 exceeds uniforms[k] * ||psi||^2, for caller-drawn uniforms[k] in [0, 1)
+ * (host arrays of count entries). The cumulative distribution is built per call from chunk
+ * masses (2^n / 4096 doubles of device scratch). A zero state -> QS_ERR_NUMERIC. */
+qs_status qs_sample(const qs_state* s, int count, const double* uniforms, uint64_t* out);
 /* out = <psi|psi> (Sec. 4.2.2 get_squared_norm); synchronises. */
 qs_status qs_norm2(const qs_state* s, double* out);
 

@@ -232,6 +232,32 @@ def inner(a: np.ndarray, b: np.ndarray, n: int) -> complex:
     return complex(out[0], out[1])
 
 
+def transition_amplitude(bra: np.ndarray, ket: np.ndarray, n: int, obs) -> complex:
+    """<bra|H|ket> = sum_k coef_k <bra|P_k|ket> (Sec. 4.5), each term by applying P_k to ket."""
+    total = 0j
+    for c, xm, zm in zip(obs.coef, obs.x_mask, obs.z_mask):
+        total += float(c) * inner(bra, apply_pauli(np.ascontiguousarray(ket, dtype=np.complex128), n, int(xm), int(zm)), n)
+    return total
+
+
+def marginal_probability(psi: np.ndarray, n: int, measured) -> float:
+    """Sum of |psi_x|^2 over the x whose bit q equals measured[q] wherever measured[q] is 0 or 1
+    (2 = any value), Sec. 4.2.2."""
+    x = np.arange(1 << n, dtype=np.uint64)
+    keep = np.ones(1 << n, dtype=bool)
+    for q, v in enumerate(measured):
+        if v in (0, 1):
+            keep &= ((x >> np.uint64(q)) & np.uint64(1)) == np.uint64(v)
+    return float(np.sum(np.abs(np.asarray(psi)[keep]) ** 2))
+
+
+def sample(psi: np.ndarray, uniforms) -> np.ndarray:
+    """For each u in [0, 1): the first index whose cumulative probability exceeds u times the
+    total (Sec. 4.2.2 sampling, with the random numbers given)."""
+    cdf = np.cumsum(np.abs(np.asarray(psi)) ** 2)
+    return np.searchsorted(cdf, np.asarray(uniforms, dtype=np.float64) * cdf[-1], side="right").astype(np.uint64)
+
+
 def norm2(psi: np.ndarray, n: int) -> float:
     return lib().oracle_norm2(_ptr(psi), n)
 

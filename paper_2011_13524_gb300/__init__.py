@@ -102,6 +102,9 @@ _SIGNATURES = {
     "qs_synchronize": ([_VOIDP], ctypes.c_int),
     "qs_apply_gate": ([_VOIDP, ctypes.POINTER(QsGate)], ctypes.c_int),
     "qs_apply_pauli_rotation": ([_VOIDP, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double], ctypes.c_int),
+    "qs_transition_amplitude": ([_VOIDP, ctypes.POINTER(QsPauliObs), _VOIDP, _DP], ctypes.c_int),
+    "qs_marginal_probability": ([_VOIDP, ctypes.POINTER(ctypes.c_int32), _DP], ctypes.c_int),
+    "qs_sample": ([_VOIDP, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     "qs_apply_observable_rotation": ([_VOIDP, ctypes.POINTER(QsPauliObs), ctypes.c_double, ctypes.c_int], ctypes.c_int),
     "qs_apply_fused": ([_VOIDP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _DP], ctypes.c_int),
     "qs_run_circuit": ([_VOIDP, ctypes.POINTER(QsCircuit), ctypes.c_int], ctypes.c_int),
@@ -377,6 +380,32 @@ class State:
         """First-order Trotter evolution exp(i angle H) of the observable H in n_slices steps."""
         o, keep = make_obs(obs)
         check(lib().qs_apply_observable_rotation(self.handle, ctypes.byref(o), float(angle), int(n_slices)))
+
+    def transition_amplitude(self, obs, ket: "State") -> complex:
+        """<self|H|ket> for the observable H."""
+        o, keep = make_obs(obs)
+        out = (ctypes.c_double * 2)()
+        check(lib().qs_transition_amplitude(self.handle, ctypes.byref(o), ket.handle, out))
+        return complex(out[0], out[1])
+
+    def marginal_probability(self, measured_value: Sequence[int]) -> float:
+        """Probability of the measured values (0, 1, or 2 for any) of qubits 0 .. n-1."""
+        mv = np.ascontiguousarray(measured_value, dtype=np.int32)
+        if mv.size != self.n:
+            raise QsError(QS_ERR_INVALID_ARG, "one measured value per qubit")
+        out = ctypes.c_double(0)
+        check(lib().qs_marginal_probability(self.handle, mv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                            ctypes.byref(out)))
+        return out.value
+
+    def sample(self, uniforms) -> np.ndarray:
+        """Z-basis samples: for each uniform u in [0, 1), the first index whose cumulative
+        probability exceeds u times the squared norm."""
+        u = np.ascontiguousarray(uniforms, dtype=np.float64)
+        out = np.zeros(max(1, u.size), dtype=np.uint64)
+        check(lib().qs_sample(self.handle, int(u.size), u.ctypes.data_as(_DP),
+                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        return out[: u.size]
 
     def expectation(self, obs) -> Tuple[float, float]:
         o, keep = make_obs(obs)

@@ -748,6 +748,33 @@ qs_status qs_inner_product(const qs_state* a, const qs_state* b, double out[2]) 
     API_END
 }
 
+qs_status qs_transition_amplitude(const qs_state* bra, const qs_pauli_obs* H, const qs_state* ket, double out[2]) {
+    API_BEGIN
+    check_state(bra);
+    check_state(ket);
+    QS_REQUIRE(out != nullptr, "null output");
+    QS_REQUIRE(bra->n == ket->n && bra->dt == ket->dt, "states differ in qubit count or dtype");
+    reduce_transition(bra, H, ket, out);
+    API_END
+}
+
+qs_status qs_marginal_probability(const qs_state* s, const int32_t* measured_value, double* out) {
+    API_BEGIN
+    check_state(s);
+    QS_REQUIRE(measured_value != nullptr && out != nullptr, "null argument");
+    reduce_marginal(s, measured_value, out);
+    API_END
+}
+
+qs_status qs_sample(const qs_state* s, int count, const double* uniforms, uint64_t* out) {
+    API_BEGIN
+    check_state(s);
+    QS_REQUIRE(count >= 0, "negative sample count");
+    QS_REQUIRE(count == 0 || (uniforms != nullptr && out != nullptr), "null argument");
+    sample_state(s, count, uniforms, out);
+    API_END
+}
+
 qs_status qs_norm2(const qs_state* s, double* out) {
     API_BEGIN
     check_state(s);

@@ -141,6 +141,12 @@ void reduce_norm2(qs_state* s, double* out);
 void reduce_inner(const qs_state* a, const qs_state* b, double out[2]);
 void reduce_expectation(qs_state* s, const qs_pauli_obs* obs, double out[2]);
 // <lambda| P |psi> for a Pauli string (complex), both states same n/dtype; synchronises.
+// <bra|H|ket>, (re, im)
+void reduce_transition(const qs_state* bra, const qs_pauli_obs* obs, const qs_state* ket, double out[2]);
+// probability of the measured values (measured[q] = 0, 1, or 2 for any) of every qubit
+void reduce_marginal(const qs_state* s, const int32_t* measured, double* out);
+// out[k] = first x whose cumulative probability exceeds uniforms[k] times the total
+void sample_state(const qs_state* s, int count, const double* uniforms, uint64_t* out);
 void reduce_pauli_transition(qs_state* lam, const qs_state* psi, uint64_t xmask, uint64_t zmask,
                              double out[2]);
 

@@ -12,6 +12,7 @@
 // (y, y ^ f) once, with A = conj(psi_{y^f}) psi_y:
 //   <psi|P|psi> restricted to the pair = i^{#Y} (s(y) A + s(y^f) conj(A)).
 #include <algorithm>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <type_traits>
@@ -146,6 +147,121 @@ __global__ void __launch_bounds__(kRedThreads) k_transition(const C* __restrict_
         im = fma(-l.y, p.x, im);
     }
     write_partial2(re, im, part);
+}
+
+// <bra| sum_t coef_t P_t |ket> over the terms of one flip group: sum_y conj(bra_y) coef_t i^nY_t
+// (-1)^popc(x & z_t) ket_x with x = y ^ xmask (P_t |x> lands on |y>)
+template <typename C>
+__global__ void __launch_bounds__(kRedThreads) k_transition_group(const C* __restrict__ bra, const C* __restrict__ ket,
+                                                                  uint64_t N, const __grid_constant__ TermParams P,
+                                                                  double* part) {
+    double re = 0.0, im = 0.0;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t y = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; y < N; y += stride) {
+        const uint64_t x = y ^ P.xmask;
+        const double2 b = widen(bra[y]), k = widen(ket[x]);
+        const double vr = fma(b.x, k.x, b.y * k.y), vi = fma(b.x, k.y, -b.y * k.x);  // conj(b) k
+        for (int t = 0; t < P.nterms; t++) {
+            const double w = parity64(x & P.zmask[t]) ? -P.coef[t] : P.coef[t];
+            const double ur = w * vr, ui = w * vi;
+            switch (P.nY[t] & 3) {
+                case 0: re += ur; im += ui; break;
+                case 1: re -= ui; im += ur; break;
+                case 2: re -= ur; im -= ui; break;
+                default: re += ui; im -= ur; break;
+            }
+        }
+    }
+    write_partial2(re, im, part);
+}
+
+// sum of |psi_x|^2 over the x whose measured bits are fixed: i runs over the free qubits, its
+// bits deposited at their positions, the measured ones set from `set`
+struct FreeBits {
+    uint64_t set;
+    int32_t nfree;
+    int8_t pos[64];
+};
+template <typename C>
+__global__ void __launch_bounds__(kRedThreads) k_norm2_sub(const C* __restrict__ psi, const __grid_constant__ FreeBits F,
+                                                           double* part) {
+    double acc = 0.0;
+    const uint64_t n_iter = 1ull << F.nfree;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n_iter; i += stride) {
+        uint64_t x = F.set;
+        for (int j = 0; j < F.nfree; j++) x |= ((i >> j) & 1ull) << F.pos[j];
+        const double2 v = widen(psi[x]);
+        acc = fma(v.x, v.x, acc);
+        acc = fma(v.y, v.y, acc);
+    }
+    write_partial2(acc, 0.0, part);
+}
+
+// sampling, step 1: probability mass of each chunk of 2^chunk_log amplitudes (one block each)
+template <typename C>
+__global__ void __launch_bounds__(kRedThreads) k_chunk_mass(const C* __restrict__ psi, uint64_t N, int chunk_log,
+                                                            double* mass) {
+    const uint64_t base = uint64_t(blockIdx.x) << chunk_log;
+    const uint64_t end = N < base + (1ull << chunk_log) ? N : base + (1ull << chunk_log);
+    double acc = 0.0;
+    for (uint64_t x = base + threadIdx.x; x < end; x += blockDim.x) {
+        const double2 v = widen(psi[x]);
+        acc = fma(v.x, v.x, acc);
+        acc = fma(v.y, v.y, acc);
+    }
+    __shared__ double sh[kRedThreads / 32];
+    const double r = block_sum<kRedThreads>(acc, sh);
+    if (threadIdx.x == 0) mass[blockIdx.x] = r;
+}
+
+// sampling, step 2: one warp per sample finds, inside its chunk, the first x whose running mass
+// (lanes own consecutive stretches, summed in order) exceeds the residual target
+template <typename C>
+__global__ void __launch_bounds__(kRedThreads) k_sample_find(const C* __restrict__ psi, uint64_t N, int chunk_log,
+                                                             const uint64_t* __restrict__ chunk,
+                                                             const double* __restrict__ resid, int count,
+                                                             uint64_t* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int s = int((uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+    if (s >= count) return;
+    const uint64_t base = chunk[s] << chunk_log;
+    const uint64_t len = N - base < (1ull << chunk_log) ? N - base : (1ull << chunk_log);
+    const uint64_t per = (len + 31) / 32;
+    const uint64_t lo = len < uint64_t(lane) * per ? len : uint64_t(lane) * per;
+    const uint64_t hi = len < lo + per ? len : lo + per;
+    auto mass = [&](uint64_t x) {
+        const double2 v = widen(psi[base + x]);
+        return fma(v.x, v.x, v.y * v.y);
+    };
+    double own = 0.0;
+    for (uint64_t x = lo; x < hi; x++) own += mass(x);
+    double incl = own;  // inclusive scan over lanes, in lane order
+    for (int d = 1; d < 32; d <<= 1) {
+        const double v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+    }
+    const double r = resid[s];
+    const unsigned over = __ballot_sync(0xffffffffu, incl > r);
+    const unsigned nonzero = __ballot_sync(0xffffffffu, own > 0.0);
+    // the lane whose stretch crosses r; past the end (rounding) the last lane with mass
+    const int L = over ? __ffs(over) - 1 : (nonzero ? 31 - __clz(nonzero) : 31);
+    if (lane == L) {
+        double acc = incl - own;
+        uint64_t pick = hi > lo ? hi - 1 : lo, last = pick;
+        bool found = false;
+        for (uint64_t x = lo; x < hi; x++) {
+            const double m = mass(x);
+            if (m > 0.0) last = x;
+            acc += m;
+            if (acc > r) {
+                pick = x;
+                found = true;
+                break;
+            }
+        }
+        out[s] = base + (found ? pick : last);
+    }
 }
 
 // sum of `nslots` (re, im) partials in a fixed order -> out[0..1]
@@ -333,6 +449,126 @@ void reduce_pauli_transition(qs_state* lam, const qs_state* psi, uint64_t xmask,
     });
     QS_TRY_CUDA(cudaGetLastError());
     finish2(lam, int(g), out);
+}
+
+void reduce_transition(const qs_state* bra, const qs_pauli_obs* obs, const qs_state* ket, double out[2]) {
+    qs_state* s = const_cast<qs_state*>(bra);
+    const std::vector<PauliGroup> groups = group_observable(obs, s->n);
+    const uint64_t N = 1ull << s->n;
+    QS_REQUIRE(arith_of(bra) == arith_of(ket), "states in different layouts");
+    if (ket->stream != s->stream) QS_TRY_CUDA(cudaStreamSynchronize(ket->stream));
+    std::vector<std::pair<const PauliGroup*, std::pair<size_t, size_t>>> launches;
+    for (const auto& g : groups)
+        for (size_t t0 = 0; t0 < g.coef.size(); t0 += kMaxTermsPerLaunch)
+            launches.push_back({&g, {t0, std::min(g.coef.size(), t0 + kMaxTermsPerLaunch)}});
+    if (launches.empty()) {
+        out[0] = out[1] = 0.0;
+        return;
+    }
+    const unsigned gr = red_grid(N);
+    ensure_scratch(s, 2 * size_t(gr) * launches.size() + 2);
+    int slots = 0;
+    for (const auto& l : launches) {
+        TermParams P;
+        P.xmask = l.first->xmask;
+        P.ip = make_index_plan(s->n, {}, 0);
+        P.nterms = int(l.second.second - l.second.first);
+        for (size_t t = l.second.first; t < l.second.second; t++) {
+            P.coef[t - l.second.first] = l.first->coef[t];
+            P.zmask[t - l.second.first] = l.first->zmask[t];
+            P.nY[t - l.second.first] = __builtin_popcountll(l.first->xmask & l.first->zmask[t]);
+        }
+        double* part = s->scratch.d_part + 2 * size_t(slots);
+        with_type(arith_of(s), s->data, [&](auto pb) {
+            using CP = decltype(pb);
+            k_transition_group<<<gr, kRedThreads, 0, s->stream>>>(pb, reinterpret_cast<CP>(ket->data), N, P, part);
+        });
+        QS_TRY_CUDA(cudaGetLastError());
+        slots += int(gr);
+    }
+    finish2(s, slots, out);
+}
+
+void reduce_marginal(const qs_state* st, const int32_t* measured, double* out) {
+    qs_state* s = const_cast<qs_state*>(st);
+    FreeBits F;
+    F.set = 0;
+    F.nfree = 0;
+    for (int q = 0; q < s->n; q++) {
+        QS_REQUIRE(measured[q] >= 0 && measured[q] <= 2, "measured values must be 0, 1 or 2 (any)");
+        if (measured[q] == 2) F.pos[F.nfree++] = int8_t(q);
+        else if (measured[q] == 1) F.set |= 1ull << q;
+    }
+    const uint64_t work = 1ull << F.nfree;
+    const unsigned g = red_grid(work);
+    ensure_scratch(s, 2 * g + 2);
+    with_type(arith_of(s), s->data, [&](auto p) { k_norm2_sub<<<g, kRedThreads, 0, s->stream>>>(p, F, s->scratch.d_part); });
+    QS_TRY_CUDA(cudaGetLastError());
+    double r[2];
+    finish2(s, int(g), r);
+    *out = r[0];
+}
+
+void sample_state(const qs_state* st, int count, const double* uniforms, uint64_t* out) {
+    qs_state* s = const_cast<qs_state*>(st);
+    if (count == 0) return;
+    for (int k = 0; k < count; k++) QS_REQUIRE(uniforms[k] >= 0.0 && uniforms[k] < 1.0, "uniforms must lie in [0, 1)");
+    const uint64_t N = 1ull << s->n;
+    const int chunk_log = std::min(s->n, 12);
+    const uint64_t B = N >> chunk_log;
+    double* d_mass = nullptr;
+    uint64_t* d_chunk = nullptr;
+    double* d_resid = nullptr;
+    uint64_t* d_out = nullptr;
+    auto cleanup = [&]() {
+        if (d_mass) cudaFreeAsync(d_mass, s->stream);
+        if (d_chunk) cudaFreeAsync(d_chunk, s->stream);
+        if (d_resid) cudaFreeAsync(d_resid, s->stream);
+        if (d_out) cudaFreeAsync(d_out, s->stream);
+    };
+    try {
+        QS_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_mass), B * sizeof(double), s->stream));
+        with_type(arith_of(s), s->data, [&](auto p) {
+            k_chunk_mass<<<unsigned(B), kRedThreads, 0, s->stream>>>(p, N, chunk_log, d_mass);
+        });
+        QS_TRY_CUDA(cudaGetLastError());
+        // cumulative distribution over chunks, in order, on the host
+        std::vector<double> mass(B), cum(B + 1, 0.0);
+        QS_TRY_CUDA(cudaMemcpyAsync(mass.data(), d_mass, B * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
+        for (uint64_t b = 0; b < B; b++) cum[b + 1] = cum[b] + mass[b];
+        const double total = cum[B];
+        if (!(total > 0.0)) throw Error{QS_ERR_NUMERIC, "sampling a zero state"};
+        std::vector<uint64_t> chunk(count);
+        std::vector<double> resid(count);
+        for (int k = 0; k < count; k++) {
+            const double target = uniforms[k] * total;
+            // first chunk whose cumulative mass exceeds the target
+            uint64_t c = uint64_t(std::upper_bound(cum.begin() + 1, cum.end(), target) - (cum.begin() + 1));
+            if (c >= B) {  // rounding at the top: the last chunk with mass
+                c = B - 1;
+                while (c > 0 && !(mass[c] > 0.0)) c--;
+            }
+            chunk[k] = c;
+            resid[k] = target - cum[c];
+        }
+        QS_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_chunk), count * sizeof(uint64_t), s->stream));
+        QS_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_resid), count * sizeof(double), s->stream));
+        QS_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_out), count * sizeof(uint64_t), s->stream));
+        QS_TRY_CUDA(cudaMemcpyAsync(d_chunk, chunk.data(), count * sizeof(uint64_t), cudaMemcpyHostToDevice, s->stream));
+        QS_TRY_CUDA(cudaMemcpyAsync(d_resid, resid.data(), count * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+        const unsigned blocks = unsigned((uint64_t(count) * 32 + kRedThreads - 1) / kRedThreads);
+        with_type(arith_of(s), s->data, [&](auto p) {
+            k_sample_find<<<blocks, kRedThreads, 0, s->stream>>>(p, N, chunk_log, d_chunk, d_resid, count, d_out);
+        });
+        QS_TRY_CUDA(cudaGetLastError());
+        QS_TRY_CUDA(cudaMemcpyAsync(out, d_out, count * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream));
+        QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
+    } catch (...) {
+        cleanup();
+        throw;
+    }
+    cleanup();
 }
 
 void launch_apply_observable(const std::vector<PauliGroup>& groups, const void* psi, void* lam, int n, Arith ar,

@@ -501,3 +501,56 @@ def test_observable_rotation_trotter_error_falls_as_one_over_slices():
     assert err[1] > 1e-3
     for r in (4, 16, 64):
         assert 0.15 < err[r] * r / err[1] < 2.0, err
+
+
+# ---------------------------------------------------------------- analysis functions
+def test_transition_amplitude_pins():
+    """<bra|H|ket>: equals <psi|H|psi> (the oracle's expectation routine) when bra = ket, and
+    vdot(bra, H ket) with H built from Kronecker products."""
+    n = 4
+    rng = W.SplitMix64(81)
+    obs = W.random_pauli_observable(n, 6, 82)
+    psi = rand_vec(n, rng)
+    t = oracle.transition_amplitude(psi, psi, n, obs)
+    e = oracle.expectation(psi, obs)
+    assert abs(t - complex(e[0], e[1])) < 1e-13
+    bra, ket = rand_vec(n, rng), rand_vec(n, rng)
+    H = sum(float(c) * pauli_full(n, int(x), int(z)) for c, x, z in zip(obs.coef, obs.x_mask, obs.z_mask))
+    assert abs(oracle.transition_amplitude(bra, ket, n, obs) - np.vdot(bra, H @ ket)) < 1e-13
+
+
+def test_marginal_probability_pins():
+    """Against slicing the state as an n-axis tensor (axis n-1-q is qubit q), the all-wildcard
+    case is the squared norm, and a qubit's two outcomes add up to its wildcard."""
+    n = 5
+    rng = W.SplitMix64(83)
+    psi = rand_vec(n, rng) * 1.3
+    T = np.abs(psi.reshape((2,) * n)) ** 2
+    for _ in range(10):
+        mv = [int(rng.next_u64() % 3) for _ in range(n)]
+        idx = tuple(slice(None) if mv[n - 1 - a] == 2 else mv[n - 1 - a] for a in range(n))
+        assert abs(oracle.marginal_probability(psi, n, mv) - float(np.sum(T[idx]))) < 1e-13
+        q = int(rng.next_u64() % n)
+        m0, m1, m2 = list(mv), list(mv), list(mv)
+        m0[q], m1[q], m2[q] = 0, 1, 2
+        assert abs(oracle.marginal_probability(psi, n, m0) + oracle.marginal_probability(psi, n, m1) -
+                   oracle.marginal_probability(psi, n, m2)) < 1e-13
+    assert abs(oracle.marginal_probability(psi, n, [2] * n) - np.vdot(psi, psi).real) < 1e-13
+
+
+def test_sampling_pins():
+    """Inverse-CDF sampling: exact outcomes for a 1-qubit state with probabilities (1/4, 3/4) and
+    for a basis state; outcome frequencies of many uniforms within 5 sigma of |psi_x|^2."""
+    psi = np.array([0.5, math.sqrt(0.75)], dtype=np.complex128)
+    assert list(oracle.sample(psi, [0.0, 0.1, 0.2499, 0.2501, 0.9])) == [0, 0, 0, 1, 1]
+    e5 = np.zeros(8, dtype=np.complex128)
+    e5[5] = 1j
+    assert set(oracle.sample(e5, [0.0, 0.3, 0.99]).tolist()) == {5}
+    n = 3
+    rng = W.SplitMix64(84)
+    v = rand_vec(n, rng)
+    p = np.abs(v) ** 2 / np.vdot(v, v).real
+    m = 20000
+    u = np.array([rng.uniform() for _ in range(m)])
+    counts = np.bincount(oracle.sample(v, u).astype(np.int64), minlength=8)
+    assert np.all(np.abs(counts - m * p) < 5 * np.sqrt(m * p * (1 - p)) + 1)
