@@ -83,6 +83,82 @@ uint64_t gate_mask(const qs_gate& g) {
     return m;
 }
 
+// Qubits of a gate on which it commutes with Z, X or Y (block-diagonal in that single-qubit
+// basis). Two gates whose shared qubits all carry a common such basis commute: both are then
+// block-diagonal in the joint eigenbasis of the shared qubits and act on disjoint qubits
+// otherwise. Controls commute with Z; named gates take their table's structure; a dense
+// matrix is tested entry by entry.
+struct GateTags {
+    uint64_t zc = 0, xc = 0, yc = 0;
+};
+
+GateTags gate_tags(const qs_gate& g, int n) {
+    GateTags t;
+    for (int j = 0; j < g.mc; j++) t.zc |= 1ull << g.controls[j];
+    uint64_t tm = 0;
+    for (int j = 0; j < g.m; j++) tm |= 1ull << g.targets[j];
+    auto pauli_tag = [&](int id, int q) {
+        const uint64_t b = 1ull << q;
+        if (id == 0) { t.zc |= b; t.xc |= b; t.yc |= b; }
+        else if (id == 1) t.xc |= b;
+        else if (id == 2) t.yc |= b;
+        else t.zc |= b;
+    };
+    if (g.kind == QS_GATE_DIAG) {
+        t.zc |= tm;
+        return t;
+    }
+    if (g.kind == QS_GATE_PAULI) {
+        for (int j = 0; j < g.m; j++) pauli_tag(g.pauli[j], g.targets[j]);
+        return t;
+    }
+    if (g.kind == QS_GATE_NAMED) {
+        switch (g.named) {
+            case QS_NAMED_Z: case QS_NAMED_S: case QS_NAMED_SDAG: case QS_NAMED_T: case QS_NAMED_TDAG:
+            case QS_NAMED_RZ: case QS_NAMED_U1: case QS_NAMED_CZ:
+                t.zc |= tm;
+                return t;
+            case QS_NAMED_X: case QS_NAMED_SQRTX: case QS_NAMED_SQRTXDAG: case QS_NAMED_RX:
+            case QS_NAMED_CNOT: case QS_NAMED_TOFFOLI:
+                t.xc |= tm;
+                return t;
+            case QS_NAMED_Y: case QS_NAMED_SQRTY: case QS_NAMED_SQRTYDAG: case QS_NAMED_RY:
+                t.yc |= tm;
+                return t;
+            case QS_NAMED_PAULIROT:
+                for (int j = 0; j < g.m; j++) pauli_tag(g.pauli[j], g.targets[j]);
+                return t;
+            default:
+                return t;  // H, U2, U3, SWAP, FREDKIN: no common basis claimed
+        }
+    }
+    // dense matrix: test each target bit
+    const DenseOp d = dense_of_gate(g, n, nullptr);
+    const int m = int(d.targets.size()), D = 1 << m;
+    double scale = 0.0;
+    for (const cplx& v : d.mat) scale = std::max(scale, std::abs(v));
+    const double tol = 1e-14 * std::max(scale, 1.0);
+    for (int j = 0; j < m; j++) {
+        const int b = 1 << j;
+        bool z = true, x = true, y = true;
+        for (int r = 0; r < D && (z || x || y); r++)
+            for (int c = 0; c < D; c++) {
+                const cplx v = d.mat[size_t(r) * D + c];
+                if (((r ^ c) & b) && std::abs(v) > tol) z = false;
+                // X K X = K: K[r][c] = K[r^b][c^b]; Y K Y = K: the same up to the sign (-1)^(bit r + bit c)
+                const cplx w = d.mat[size_t(r ^ b) * D + (c ^ b)];
+                if (std::abs(v - w) > tol) x = false;
+                const double sg = (((r & b) != 0) != ((c & b) != 0)) ? -1.0 : 1.0;
+                if (std::abs(v - sg * w) > tol) y = false;
+            }
+        const uint64_t q = 1ull << d.targets[j];
+        if (z) t.zc |= q;
+        if (x) t.xc |= q;
+        if (y) t.yc |= q;
+    }
+    return t;
+}
+
 bool dense_is_diagonal(const DenseOp& d) {
     const int D = 1 << int(d.targets.size());
     for (int z = 0; z < D; z++)
@@ -186,34 +262,51 @@ std::vector<OpenBlock> partition_greedy(const qs_circuit* c, const std::vector<u
     return out;
 }
 
-// Partition 2: frontier growth. `rem` lists the gates not yet emitted, in circuit order; a
-// scan over it keeps `blocked`, the qubits of every passed gate that is outside the block: a
-// later gate on such a qubit has an earlier gate that is neither emitted nor in the block.
-// Membership: gate g is in the block when in[g] == blk, or, during a trial widening, when
-// trial[g] == tid.
+// Partition 2: frontier growth. `rem` lists the gates not yet emitted, in circuit order. A scan
+// over it keeps, for the gates it passes that stay outside the block, the qubits they touch
+// (`blocked`) and, per qubit, whether all of them commute with Z, X or Y there (bz, bx, by). A
+// later gate may join the block when on each of its blocked qubits it shares one of those bases:
+// it then commutes with every gate it moves ahead of. Membership: gate g is in the block when
+// in[g] == blk, or, during a trial widening, when trial[g] == tid.
 struct Frontier {
     const std::vector<uint64_t>& masks;
+    const std::vector<GateTags>& tags;
     const std::vector<int>& rem;
     uint64_t all;
     std::vector<int>& in;
     std::vector<int>& trial;
     int blk = 0;
     int tid = 0;
+    struct Scan {
+        uint64_t blocked = 0, bz = ~0ull, bx = ~0ull, by = ~0ull;
+        bool ready(uint64_t m, const GateTags& t) const {
+            const uint64_t ok = (t.zc & bz) | (t.xc & bx) | (t.yc & by);
+            return (m & blocked & ~ok) == 0;
+        }
+        void pass(uint64_t m, const GateTags& t) {
+            blocked |= m;
+            bz &= ~(m & ~t.zc);
+            bx &= ~(m & ~t.xc);
+            by &= ~(m & ~t.yc);
+        }
+        // no gate on these qubits can be ready any more
+        bool closed(uint64_t q) const { return (blocked & q) == q && ((bz | bx | by) & q) == 0; }
+    };
     bool member(int g, bool use_trial) const { return in[g] == blk || (use_trial && trial[g] == tid); }
     // Adds to the block (or to the trial) every gate that can join with qubit set q.
     int close_over(uint64_t q, bool use_trial) {
-        uint64_t blocked = 0;
+        Scan sc;
         int added = 0;
         for (int g : rem) {
             if (member(g, use_trial)) continue;
             const uint64_t m = masks[g];
-            if (!(m & blocked) && (m & ~q) == 0) {
+            if ((m & ~q) == 0 && sc.ready(m, tags[g])) {
                 if (use_trial) trial[g] = tid;
                 else in[g] = blk;
                 added++;
             } else {
-                blocked |= m;
-                if ((blocked & q) == q) break;
+                sc.pass(m, tags[g]);
+                if (sc.closed(q)) break;
             }
         }
         return added;
@@ -221,27 +314,28 @@ struct Frontier {
     // Distinct qubit sets q | m of the ready gates that widen q without exceeding k qubits.
     std::vector<uint64_t> widening(uint64_t q, int k) const {
         std::vector<uint64_t> cand;
-        uint64_t blocked = 0;
+        Scan sc;
         for (int g : rem) {
             if (member(g, false)) continue;
             const uint64_t m = masks[g];
-            if (!(m & blocked) && (m & ~q) && __builtin_popcountll(q | m) <= k &&
+            if ((m & ~q) && __builtin_popcountll(q | m) <= k && sc.ready(m, tags[g]) &&
                 std::find(cand.begin(), cand.end(), q | m) == cand.end())
                 cand.push_back(q | m);
-            blocked |= m;
-            if (blocked == all) break;
+            sc.pass(m, tags[g]);
+            if (sc.closed(all)) break;
         }
         return cand;
     }
 };
 
-std::vector<OpenBlock> partition_frontier(const qs_circuit* c, const std::vector<uint64_t>& masks, int k) {
+std::vector<OpenBlock> partition_frontier(const qs_circuit* c, const std::vector<uint64_t>& masks,
+                                          const std::vector<GateTags>& tags, int k) {
     std::vector<OpenBlock> out;
     std::vector<int> rem(c->n_gates);
     for (int i = 0; i < c->n_gates; i++) rem[i] = i;
     std::vector<int> in(c->n_gates, -1), trial(c->n_gates, -1);
     const uint64_t all = c->n >= 64 ? ~0ull : ((1ull << c->n) - 1);
-    Frontier f{masks, rem, all, in, trial};
+    Frontier f{masks, tags, rem, all, in, trial};
     while (!rem.empty()) {
         uint64_t q = masks[rem[0]];
         in[rem[0]] = f.blk;
@@ -288,15 +382,21 @@ std::vector<OpenBlock> partition_frontier(const qs_circuit* c, const std::vector
 namespace {
 struct PartitionKey {
     int n = 0, k = 0;
-    std::vector<uint64_t> masks;
+    std::vector<uint64_t> masks;  // per gate: qubits, then the Z, X, Y commuting-basis masks
     bool operator==(const PartitionKey& o) const { return n == o.n && k == o.k && masks == o.masks; }
 };
 std::mutex g_part_mu;
 std::list<std::pair<PartitionKey, std::vector<OpenBlock>>> g_part_cache;
 constexpr size_t kPartCacheSize = 16;
 
-std::vector<OpenBlock> partition(const qs_circuit* c, const std::vector<uint64_t>& masks, int k) {
+std::vector<OpenBlock> partition(const qs_circuit* c, const std::vector<uint64_t>& masks,
+                                 const std::vector<GateTags>& tags, int k) {
     PartitionKey key{c->n, k, masks};
+    for (const GateTags& t : tags) {
+        key.masks.push_back(t.zc);
+        key.masks.push_back(t.xc);
+        key.masks.push_back(t.yc);
+    }
     {
         std::lock_guard<std::mutex> lk(g_part_mu);
         for (auto it = g_part_cache.begin(); it != g_part_cache.end(); ++it)
@@ -306,7 +406,7 @@ std::vector<OpenBlock> partition(const qs_circuit* c, const std::vector<uint64_t
             }
     }
     std::vector<OpenBlock> a = partition_greedy(c, masks, k);
-    std::vector<OpenBlock> b = partition_frontier(c, masks, k);
+    std::vector<OpenBlock> b = partition_frontier(c, masks, tags, k);
     std::vector<OpenBlock> best = b.size() < a.size() ? std::move(b) : std::move(a);
     std::lock_guard<std::mutex> lk(g_part_mu);
     g_part_cache.emplace_front(std::move(key), best);
@@ -321,18 +421,20 @@ FusionPlan plan_fusion(const qs_circuit* c, int k, const double* theta) {
     QS_REQUIRE(c->n_gates >= 0 && (c->n_gates == 0 || c->gates != nullptr), "null gate array");
     QS_REQUIRE(k >= 1 && k <= QS_MAX_TARGETS, "fusion width must be in 1..6");
     std::vector<uint64_t> masks(c->n_gates);
+    std::vector<GateTags> tags(c->n_gates);
     for (int i = 0; i < c->n_gates; i++) {
         const qs_gate& g = c->gates[i];
         QS_REQUIRE(g.m >= 1 && g.m <= QS_MAX_TARGETS, "target count out of range (1..6)");
         check_qubits(c->n, g.targets, g.m, g.controls, g.mc);
         masks[i] = gate_mask(g);
+        tags[i] = gate_tags(g, c->n);
     }
     FusionPlan plan;
     plan.n = c->n;
     plan.k = k;
     plan.n_source_gates = c->n_gates;
     // block matrices: independent of each other, built by several host threads for long plans
-    const std::vector<OpenBlock> parts = partition(c, masks, k);
+    const std::vector<OpenBlock> parts = partition(c, masks, tags, k);
     plan.blocks.resize(parts.size());
     size_t work = 0;
     for (const OpenBlock& blk : parts) work += blk.gates.size() << (2 * __builtin_popcountll(blk.mask));

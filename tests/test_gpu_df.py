@@ -151,3 +151,33 @@ def test_precision_c64_c128_vs_oracle(qs):
             assert abs(st.expectation(tf)[0] - e_ref) < e_tol
     finally:
         qs.set_c128_math(old)
+
+
+def test_df_layout_round_trip_wide_range(df):
+    """The in-place layout change and back (an empty circuit run) keeps every amplitude between
+    1e-28 and 1e30 to 2^-47 relative (both conversion branches, signs), zeros exactly, and values
+    below the FP32 exponent range (1e-300 .. 1e-40) to 1e-37 absolute."""
+    qs = df
+    n = 12
+    rng = W.SplitMix64(12)
+    N = 1 << n
+    mags = np.array([10.0 ** (-28 + 58 * rng.uniform()) for _ in range(N)])
+    tiny = np.array([10.0 ** (-300 + 260 * rng.uniform()) for _ in range(N)])
+    signs = np.array([1 if rng.next_u64() & 1 else -1 for _ in range(2 * N)]).reshape(2, -1)
+    psi0 = signs[0] * mags + 1j * signs[1] * mags[::-1]
+    psi0[::97] = 0.0
+    psi0[5::7] = signs[0][5::7] * tiny[5::7] + 1j * tiny[::-1][5::7]
+    st = qs.State(n, qs.QS_C128)
+    st.load(psi0)
+    st.run(W.Circuit(n, []), 0)
+    got = st.get_vector()
+    small = np.zeros(N, dtype=bool)
+    small[5::7] = True
+    small[::97] = False
+    zero = np.zeros(N, dtype=bool)
+    zero[::97] = True
+    normal = ~(small | zero)
+    assert np.all(got[zero] == 0)
+    rel = np.abs(got[normal] - psi0[normal]) / np.abs(psi0[normal])
+    assert float(np.max(rel)) < 2.0 ** -47
+    assert float(np.max(np.abs(got[small] - psi0[small]))) < 1e-37
