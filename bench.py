@@ -488,6 +488,18 @@ def measure_extras(args, qs, torch, circuit):
     out["sample_1e5_n30_ms"] = 1e3 * (time.perf_counter() - t0)
     del sa, sb
     torch.cuda.empty_cache()
+    # a commuting (IQP-like) circuit: H layers around 20 diagonal layers, n = 30 complex128
+    ci = W.iqp_circuit(n, 20, args.seed)
+    ki, _ = qs.autotune_fusion(ci, qs.QS_C128)
+    pli = qs.FusedCircuit(ci, max(ki, 1))
+    sti = qs.State(n, qs.QS_C128)
+    ms = timed(lambda: (sti.set_basis(0), sti.apply_plan(pli)))
+    out["iqp_circuit_gates"] = len(ci.gates)
+    out["iqp_circuit_fusion_k"] = ki
+    out["iqp_circuit_blocks"] = pli.n_blocks
+    out["iqp_circuit_gates_per_s"] = len(ci.gates) / (ms / 1e3)
+    del sti
+    torch.cuda.empty_cache()
     # n = 33 complex128 (128 GiB state), same circuit family at depth 20, autotuned width
     try:
         c33 = W.u3cz_circuit(33, args.depth, args.seed)

@@ -184,9 +184,16 @@ def test_fusion_commutation_respects_non_commuting_gates():
 
 def test_fusion_commutation_shrinks_commuting_circuits():
     """The ansatz's RZ layers commute with the CZ ladders: far fewer blocks than the
-    disjoint-qubit rule alone gives (k = 4: 94 for n = 20, 20 layers)."""
+    disjoint-qubit rule alone gives (k = 4: 94 for n = 20, 20 layers). In an IQP-like circuit
+    everything between the two Hadamard layers commutes: one block per neighbouring pair."""
     c = W.hea_circuit(20, 20, 1)
     assert qs.FusedCircuit(c, 4).n_blocks <= 64
+    assert qs.FusedCircuit(W.iqp_circuit(30, 20, 1), 2).n_blocks <= 29
+    n = 9
+    iqp = W.iqp_circuit(n, 8, 5)
+    ref = oracle.run_circuit(iqp)
+    for k in (2, 4, 6):
+        assert np.max(np.abs(run_plan_with_oracle(qs.FusedCircuit(iqp, k), n) - ref)) < 1e-12
 
 
 @pytest.mark.parametrize("k", [2, 3, 4, 5, 6])

@@ -384,6 +384,18 @@ def test_comparison_circuit_vs_oracle(qs, n):
         assert fidelity_gap(ref, got) < (1e-12 if dtype == 2 else 1e-6)
 
 
+def test_commuting_circuits_vs_oracle(qs):
+    """Circuits whose fusion plans move blocks across commuting gates (an IQP-like circuit and
+    the hardware-efficient ansatz), autotuned width, complex128 and complex64, against the oracle."""
+    for c in (W.iqp_circuit(16, 12, 3), W.hea_circuit(16, 8, 4).bind(W.hea_circuit(16, 8, 4).parameters())):
+        ref = oracle.run_circuit(c)
+        for dtype in (2, 1):
+            st = qs.State(c.n, dtype)
+            st.run(c, -1)
+            assert maxabs(st.get_vector(), ref) < TOL[dtype], dtype
+            st.close()
+
+
 @pytest.mark.parametrize("n", [24, 26])
 def test_circuit_family_vs_oracle_large(qs, n):
     """The depth-20 U3+CZ family at n = 24 and 26 against the FP64 oracle (the largest sizes the

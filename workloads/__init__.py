@@ -175,6 +175,21 @@ def rzrxrz_cnot_circuit(n: int, reps: int, seed: int) -> Circuit:
     return Circuit(n, gates)
 
 
+def iqp_circuit(n: int, layers: int, seed: int) -> Circuit:
+    """Commuting (IQP-like) circuit: H on every qubit, then `layers` diagonal layers (RZ with a
+    seeded angle in [0, 2 pi) on every qubit, CZ(i, i+1) for i of the layer's parity), then H on
+    every qubit. Every gate between the two H layers is diagonal."""
+    rng = SplitMix64(seed)
+    gates: List[Gate] = [Gate("H", (q,)) for q in range(n)]
+    for layer in range(layers):
+        for q in range(n):
+            gates.append(Gate("RZ", (q,), params=(2.0 * math.pi * rng.uniform(),)))
+        for i in range(layer % 2, n - 1, 2):
+            gates.append(Gate("CZ", (i, i + 1)))
+    gates += [Gate("H", (q,)) for q in range(n)]
+    return Circuit(n, gates)
+
+
 def hea_circuit(n: int, layers: int, seed: int, lo: float = -math.pi, hi: float = math.pi) -> Circuit:
     """Hardware-efficient ansatz: per layer RY(theta) on all qubits, RZ(theta) on all qubits,
     CZ ladder (i, i+1) for i = 0..n-2. Every rotation is its own parameter."""
