@@ -446,6 +446,18 @@ def measure_extras(args, qs, torch, circuit):
     out["precision_n30"] = {"max_abs_c64_vs_c128": d, "one_minus_fidelity": 1.0 - ov / (a.norm2() * c.norm2()),
                             "tfim_energy_c128": e128, "tfim_energy_err_c64": abs(e64 - e128),
                             "norm2_c64": c.norm2(), "norm2_c128": a.norm2()}
+    # Pauli expectation of that Ising chain (2n - 1 terms, n + 1 flip-mask groups): tiled reads,
+    # each evaluating every group whose flip mask lies in its tile, double-float arithmetic
+    masks, single = qs.expectation_plan(n, tf)
+    reads = len(masks) + single
+    groups = len(set(int(x) for x in tf.x_mask))
+    for label, stt, S in (("c128", a, 16), ("c64", c, 8)):
+        ms = timed(lambda: stt.expectation(tf), reps=3)
+        out["tfim_expectation_n30_%s_ms" % label] = ms
+        out["tfim_expectation_n30_%s_read_gbps" % label] = reads * S * 2.0 ** n / (ms / 1e3) / 1e9
+        out["tfim_expectation_n30_%s_group_gbps" % label] = groups * S * 2.0 ** n / (ms / 1e3) / 1e9
+    out["tfim_expectation_n30_reads"] = reads
+    out["tfim_expectation_n30_groups"] = groups
     del a, c
     torch.cuda.empty_cache()
     # the comparison circuit of Sec. 7 (RZ RX RZ layers, CNOT ring, 10 repetitions), n = 30,

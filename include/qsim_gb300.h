@@ -247,9 +247,18 @@ qs_status qs_apply_fused_circuit_timed(qs_state* s, const qs_fused_circuit* f, f
 qs_status qs_autotune_fusion(const qs_circuit* c, qs_dtype dt, int* best_k, double* pred_ms);
 
 /* ---------------------------------------------------------------- observables (Sec. 4.5) */
-/* out[0] = Re sum_k coef[k] <psi|P_k|psi>, out[1] = its imaginary part (zero up to rounding for
- * real coefficients). Accumulates in FP64 for both dtypes; synchronises. */
+/* out[0] = sum_k coef[k] <psi|P_k|psi>, out[1] = 0 (the terms are Hermitian and the coefficients
+ * real, so the sum is formed as a real number). Terms with the same X-or-Y mask form a group; one
+ * read of the state evaluates every group whose mask lies in a tile of 12 qubits (qubits 0..2
+ * plus up to 9 others), in double-float arithmetic with FP64-class accuracy for complex128 and
+ * exact products for complex64; groups with more than 9 X/Y positions above qubit 2 take one
+ * read each. Synchronises. */
 qs_status qs_expectation(const qs_state* s, const qs_pauli_obs* obs, double out[2]);
+/* Host only (no GPU needed): how qs_expectation reads an n-qubit state for obs. *n_passes = the
+ * tiled reads; tile_masks (optional, cap entries) receives each read's tile qubits as a bit mask;
+ * *n_single (optional) = the reads of single groups that fit no tile. */
+qs_status qs_expectation_plan(int n, const qs_pauli_obs* obs, int* n_passes, uint64_t* tile_masks, int cap,
+                              int* n_single);
 /* Allocation-free expectation, for callers that cannot allocate device memory: code that runs
  * while a stream is being captured into a CUDA graph (cudaMalloc is not allowed there), hosts
  * whose every device byte belongs to another allocator or a fixed budget, and loops that must not
@@ -262,9 +271,9 @@ qs_status qs_expectation(const qs_state* s, const qs_pauli_obs* obs, double out[
  * process exits. The first call on a device looks up that array's address (once per device, with
  * the device current); make that first call before any stream capture. Every call shares the
  * array and each block overwrites its own slots, so nothing needs clearing, but calls that overlap
- * on the GPU (other streams, other threads) race on it: serialise them. An observable that would
- * need more than 2047 kernel launches (groups of up to 48 terms with a common X/Y pattern) is
- * rejected with QS_ERR_INVALID_ARG before any launch. Runs on `stream`; synchronises. */
+ * on the GPU (other streams, other threads) race on it: serialise them. The launches share the
+ * array's 32767 block partials (grids shrink to fit); an observable that needs more launches than
+ * that is rejected with QS_ERR_INVALID_ARG before any launch. Runs on `stream`; synchronises. */
 qs_status qs_expectation_noalloc(const void* dev_psi, int n, qs_dtype dt, void* stream, const qs_pauli_obs* obs,
                                  double out[2]);
 /* out = <a|b> (Sec. 4.2.2 inner_product) as (re, im); same n and dtype; synchronises. */

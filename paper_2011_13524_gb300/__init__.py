@@ -120,6 +120,9 @@ _SIGNATURES = {
     "qs_autotune_fusion": ([ctypes.POINTER(QsCircuit), ctypes.c_int, ctypes.POINTER(ctypes.c_int), _DP],
                            ctypes.c_int),
     "qs_expectation": ([_VOIDP, ctypes.POINTER(QsPauliObs), _DP], ctypes.c_int),
+    "qs_expectation_plan": ([ctypes.c_int, ctypes.POINTER(QsPauliObs), ctypes.POINTER(ctypes.c_int),
+                             ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+                            ctypes.c_int),
     "qs_expectation_noalloc": ([_VOIDP, ctypes.c_int, ctypes.c_int, _VOIDP, ctypes.POINTER(QsPauliObs), _DP],
                                ctypes.c_int),
     "qs_inner_product": ([_VOIDP, _VOIDP, _DP], ctypes.c_int),
@@ -272,6 +275,17 @@ def make_obs(obs) -> Tuple[QsPauliObs, _Keep]:
     o = QsPauliObs(len(coef), 0, coef.ctypes.data_as(_DP), xm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
                    zm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
     return o, keep
+
+
+def expectation_plan(n: int, obs):
+    """How qs_expectation reads an n-qubit state for obs (host only): (tile qubit masks of the
+    tiled reads, number of single-group reads)."""
+    o, keep = make_obs(obs)
+    npass, nsingle = ctypes.c_int(0), ctypes.c_int(0)
+    masks = (ctypes.c_uint64 * 64)()
+    check(lib().qs_expectation_plan(int(n), ctypes.byref(o), ctypes.byref(npass), masks, 64, ctypes.byref(nsingle)))
+    del keep
+    return [int(masks[i]) for i in range(min(npass.value, 64))], nsingle.value
 
 
 def _stream_ptr(stream) -> Optional[int]:

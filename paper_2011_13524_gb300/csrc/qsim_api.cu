@@ -731,6 +731,20 @@ qs_status qs_expectation(const qs_state* s, const qs_pauli_obs* obs, double out[
     API_END
 }
 
+qs_status qs_expectation_plan(int n, const qs_pauli_obs* obs, int* n_passes, uint64_t* tile_masks, int cap,
+                              int* n_single) {
+    API_BEGIN
+    QS_REQUIRE(n >= 1 && n <= QS_MAX_QUBITS, "qubit count out of range (1..34)");
+    QS_REQUIRE(n_passes != nullptr, "null output");
+    QS_REQUIRE(cap >= 0 && (cap == 0 || tile_masks != nullptr), "null tile mask array");
+    const std::vector<PauliGroup> groups = group_observable(obs, n);
+    const ExpectPlan plan = plan_expectation(groups, n);
+    *n_passes = int(plan.passes.size());
+    for (size_t p = 0; p < plan.tmask.size() && p < size_t(cap); p++) tile_masks[p] = plan.tmask[p];
+    if (n_single) *n_single = int(plan.heavy.size());
+    API_END
+}
+
 qs_status qs_expectation_noalloc(const void* dev_psi, int n, qs_dtype dt, void* stream, const qs_pauli_obs* obs,
                                  double out[2]) {
     API_BEGIN

@@ -139,4 +139,47 @@ __device__ __forceinline__ float4 narrow<float4>(double re, double im) {
     return r;
 }
 
+// double -> (hi, lo) floats with hi = RN(x) and lo = RN(x - hi), as split_double, but on the
+// integer pipes (GB300 runs FP64 and its conversions at 1/64 of the FP32 rate): hi takes the top
+// 24 significant bits rounded to nearest-even, lo the exact remainder rescaled (an integer below
+// 2^29 converted with rounding to nearest, times powers of two: an exact scaling into FP32's
+// normal range, then one rounding to the final, possibly subnormal, value, which equals RN of the
+// remainder). Zero is split directly. Magnitudes below 2^-126 (under FP32's normal range) become
+// a signed zero: the absolute change is below 1.2e-38. At or above 2^125 (huge, non-finite) it
+// falls back to the FP64 instructions.
+__device__ __forceinline__ void split_double_int(double x, float& hi, float& lo) {
+    const uint64_t b = uint64_t(__double_as_longlong(x));
+    const uint32_t e = uint32_t(b >> 52) & 0x7FFu;
+    const uint32_t sign = uint32_t(b >> 63) << 31;
+    if (e < 897u) {  // +-0 and |x| < 2^-126
+        hi = __uint_as_float(sign);
+        lo = 0.f;
+        return;
+    }
+    if (e > 1148u) {
+        split_double(x, hi, lo);
+        return;
+    }
+    const uint64_t m = b & ((1ull << 52) - 1);
+    const uint32_t hm = uint32_t(m >> 29);
+    const uint32_t rem = uint32_t(m & ((1ull << 29) - 1));
+    const uint32_t up = (rem > (1u << 28) || (rem == (1u << 28) && (hm & 1u))) ? 1u : 0u;
+    hi = __uint_as_float(sign | (((e - 1023u + 127u) << 23) + hm + up));
+    const int32_t li = int32_t(rem) - int32_t(up << 29);
+    const uint32_t off = e < 960u ? 64u : 0u;                         // keep the first scale normal
+    const float scale = __uint_as_float((e + off - 1075u + 127u) << 23);  // 2^(e + off - 1075)
+    const float unscale = __uint_as_float((127u - off) << 23);            // 2^-off
+    const float l = __fmul_rn(__fmul_rn(__int2float_rn(li), scale), unscale);
+    lo = sign ? -l : l;
+}
+// float -> double exactly, on the integer pipes for zero and normal floats
+__device__ __forceinline__ double widen_float_int(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    if ((u << 1) == 0u) return __longlong_as_double(static_cast<long long>(uint64_t(u >> 31) << 63));
+    if (e == 0u || e == 255u) return double(f);
+    const uint64_t b = (uint64_t(u >> 31) << 63) | (uint64_t(e - 127u + 1023u) << 52) | (uint64_t(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double(static_cast<long long>(b));
+}
+
 }  // namespace qs

@@ -258,45 +258,8 @@ __global__ void k_set_basis(typename P::C* __restrict__ psi, uint64_t N, uint64_
     for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) psi[i] = P::basis(i == j);
 }
 
-// IEEE complex128 <-> double-float, in place (same 16 bytes per amplitude)
-// double -> (hi, lo) floats with hi = RN(x) and lo = RN(x - hi), as split_double, but on the
-// integer pipes (GB300 runs FP64 and its conversions at 1/64 of the FP32 rate): hi takes the top
-// 24 significant bits rounded to nearest-even, lo the exact remainder rescaled (an integer below
-// 2^29 converted with rounding to nearest, times a power of two, which equals RN of the
-// remainder). Zero is split directly; outside 2^-63 <= |x| < 2^125 (tiny, huge, non-finite) it
-// falls back to the FP64 instructions.
-__device__ __forceinline__ void split_double_int(double x, float& hi, float& lo) {
-    const uint64_t b = uint64_t(__double_as_longlong(x));
-    const uint32_t e = uint32_t(b >> 52) & 0x7FFu;
-    if ((b << 1) == 0) {  // +-0
-        hi = __uint_as_float(uint32_t(b >> 32));
-        lo = 0.f;
-        return;
-    }
-    if (e < 960u || e > 1148u) {
-        split_double(x, hi, lo);
-        return;
-    }
-    const uint32_t sign = uint32_t(b >> 63) << 31;
-    const uint64_t m = b & ((1ull << 52) - 1);
-    const uint32_t hm = uint32_t(m >> 29);
-    const uint32_t rem = uint32_t(m & ((1ull << 29) - 1));
-    const uint32_t up = (rem > (1u << 28) || (rem == (1u << 28) && (hm & 1u))) ? 1u : 0u;
-    hi = __uint_as_float(sign | (((e - 1023u + 127u) << 23) + hm + up));
-    const int32_t li = int32_t(rem) - int32_t(up << 29);
-    const float scale = __uint_as_float((e - 1075u + 127u) << 23);  // 2^(e - 1075), normal
-    const float l = __fmul_rn(__int2float_rn(li), scale);
-    lo = sign ? -l : l;
-}
-// float -> double exactly, on the integer pipes for normal floats
-__device__ __forceinline__ double widen_float_int(float f) {
-    const uint32_t u = __float_as_uint(f);
-    const uint32_t e = (u >> 23) & 0xFFu;
-    if (e == 0u || e == 255u) return double(f);
-    const uint64_t b = (uint64_t(u >> 31) << 63) | (uint64_t(e - 127u + 1023u) << 52) | (uint64_t(u & 0x7FFFFFu) << 29);
-    return __longlong_as_double(static_cast<long long>(b));
-}
-
+// IEEE complex128 <-> double-float, in place (same 16 bytes per amplitude), with the
+// integer-pipe splits of qsim_arith.cuh
 // In-place layout changes, four amplitudes per thread and step so that four loads are in flight
 // before the first store (the stores alias the loaded buffer, so the compiler keeps the order).
 constexpr int kConvUnroll = 4;

@@ -164,6 +164,66 @@ struct PauliGroup {
 };
 std::vector<PauliGroup> group_observable(const qs_pauli_obs* obs, int n);
 
+// Tiled expectation passes: a pass reads the state once as tiles of 2^12 amplitude slots (the
+// amplitudes whose qubits outside a set T agree; T holds qubits 0..2 and 9 others, or all qubits
+// of a smaller state, whose missing tile bits are virtual and read as zero amplitudes) and
+// evaluates every flip-mask group whose flip mask lies in T. Groups whose flip mask has more than
+// 9 bits above qubit 2 run one launch each.
+constexpr int kTileBits = 12;
+constexpr int kTileAmps = 1 << kTileBits;
+constexpr int kTileThreads = 256;
+constexpr int kTileLowBits = 3;
+constexpr int kTileMaxGroups = 24;
+constexpr int kTileMaxSlots = 128;
+constexpr int kTileMaxTerms = 128;
+constexpr int kTileGroupTerms = 64;
+constexpr int kHeavyChunkTerms = 48;
+// Group kinds: the diagonal group (16 amplitudes per thread) and flip groups (8 pair
+// representatives per thread) that need Re A, Im A or both.
+enum TileKind : uint8_t { kTileDiag = 0, kTileRe = 1, kTileIm = 2, kTileReIm = 3 };
+struct TileGroup {
+    uint32_t f = 0;          // tile-local flip mask (0: the diagonal group)
+    uint32_t excl = 0;       // the 4 tile-local bits that are not thread bits, ascending, one per byte
+    uint32_t imask[4] = {};  // tile-local bit of item bit i (the pivot is not an item bit)
+    uint16_t slot0 = 0;      // first slot of the group
+    uint8_t kind = 0;        // TileKind
+    uint8_t wht = 0;         // some slot has a nonzero item mask: full Walsh-Hadamard transform
+    uint8_t bstart[17] = {}; // slots of bucket k (component * 8 + item mask): [bstart[k], bstart[k + 1])
+};
+struct TileSlot {
+    uint16_t term0 = 0, nterm = 0;
+    uint16_t zthr = 0;       // Z bits over the thread bits, in thread-index order
+    uint8_t bucket = 0, pad = 0;
+};
+struct TileTerm {
+    uint64_t zR = 0;         // Z bits outside the tile
+    double alpha = 0.0;      // coefficient with the pair factor folded in
+};
+struct TileParams {
+    uint64_t rest_mask = 0;  // qubits outside the tile
+    uint64_t n_tiles = 0;
+    uint64_t dep_hi[kTileAmps / kTileThreads] = {};  // global offset of tile-local index 256 k
+    int32_t b = 0, ngroups = 0, nslots = 0, nterms = 0;  // b: real tile bits (<= 12)
+    uint8_t tpos[kTileBits] = {};  // tile-local bit i < b = qubit tpos[i]
+    TileGroup g[kTileMaxGroups];
+    TileSlot s[kTileMaxSlots];
+    TileTerm t[kTileMaxTerms];
+};
+struct HeavyChunk {
+    const PauliGroup* g;
+    size_t t0, t1;
+};
+struct ExpectPlan {
+    std::vector<TileParams> passes;
+    std::vector<uint64_t> tmask;     // qubits of each pass's tile
+    std::vector<HeavyChunk> heavy;   // terms [t0, t1) of groups that fit no tile
+};
+ExpectPlan plan_expectation(const std::vector<PauliGroup>& groups, int n);
+unsigned expect_pass_grid(const TileParams& P, Arith ar);
+// part[2 j], part[2 j + 1] = block j's partial (real, 0) for j < grid
+void launch_expect_pass(const TileParams& P, const void* psi, Arith ar, double* part, unsigned grid,
+                        cudaStream_t st);
+
 // lambda <- O psi (sum of Pauli strings), out-of-place; asynchronous.
 void launch_apply_observable(const std::vector<PauliGroup>& groups, const void* psi, void* lam, int n,
                              Arith ar, cudaStream_t st);

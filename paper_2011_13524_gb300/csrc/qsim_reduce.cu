@@ -25,6 +25,7 @@ namespace {
 
 constexpr int kRedThreads = 256;
 constexpr int kMaxTermsPerLaunch = 48;
+static_assert(kHeavyChunkTerms <= kMaxTermsPerLaunch, "heavy chunks must fit one launch");
 
 int sms() {
     static int s = 0;
@@ -396,44 +397,68 @@ void reduce_inner(const qs_state* a, const qs_state* b, double out[2]) {
     finish2(s, int(g), out);
 }
 
+// Launches of one expectation: the tile passes, then one launch per heavy chunk. With a cap on
+// the block partials the grids shrink proportionally (the kernels loop over their work).
+struct ExpectLaunches {
+    std::vector<unsigned> pass_grid, heavy_grid;
+    size_t slots = 0;
+};
+ExpectLaunches expectation_launches(const ExpectPlan& plan, int n, Arith ar, size_t cap) {
+    ExpectLaunches L;
+    for (const TileParams& P : plan.passes) L.pass_grid.push_back(expect_pass_grid(P, ar));
+    for (const HeavyChunk& h : plan.heavy) L.heavy_grid.push_back(red_grid((1ull << n) >> (h.g->xmask ? 1 : 0)));
+    size_t tot = 0;
+    for (unsigned g : L.pass_grid) tot += g;
+    for (unsigned g : L.heavy_grid) tot += g;
+    if (tot > cap) {
+        const size_t nl = L.pass_grid.size() + L.heavy_grid.size();
+        QS_REQUIRE(nl <= cap, "observable needs more kernel launches than the partial-sum scratch holds");
+        const size_t per = cap / nl;
+        for (unsigned& g : L.pass_grid) g = unsigned(std::min<size_t>(g, per));
+        for (unsigned& g : L.heavy_grid) g = unsigned(std::min<size_t>(g, per));
+    }
+    for (unsigned g : L.pass_grid) L.slots += g;
+    for (unsigned g : L.heavy_grid) L.slots += g;
+    return L;
+}
+
+void launch_expectation(const ExpectPlan& plan, const ExpectLaunches& L, const void* psi, int n, Arith ar,
+                        cudaStream_t st, double* part) {
+    size_t slots = 0;
+    for (size_t p = 0; p < plan.passes.size(); p++) {
+        launch_expect_pass(plan.passes[p], psi, ar, part + 2 * slots, L.pass_grid[p], st);
+        slots += L.pass_grid[p];
+    }
+    for (size_t h = 0; h < plan.heavy.size(); h++) {
+        const HeavyChunk& c = plan.heavy[h];
+        TermParams P;
+        P.xmask = c.g->xmask;
+        std::vector<int> fixed;
+        if (P.xmask) fixed.push_back(__builtin_ctzll(P.xmask));
+        P.ip = make_index_plan(n, fixed, 0);
+        P.nterms = int(c.t1 - c.t0);
+        for (size_t t = c.t0; t < c.t1; t++) {
+            P.coef[t - c.t0] = c.g->coef[t];
+            P.zmask[t - c.t0] = c.g->zmask[t];
+            P.nY[t - c.t0] = __builtin_popcountll(c.g->xmask & c.g->zmask[t]);
+        }
+        with_type(ar, psi, [&](auto p) { k_expect_group<<<L.heavy_grid[h], kRedThreads, 0, st>>>(p, P, part + 2 * slots); });
+        QS_TRY_CUDA(cudaGetLastError());
+        slots += L.heavy_grid[h];
+    }
+}
+
 void reduce_expectation(qs_state* s, const qs_pauli_obs* obs, double out[2]) {
     const std::vector<PauliGroup> groups = group_observable(obs, s->n);
-    const uint64_t N = 1ull << s->n;
-    // launches: one per (group, chunk of <= kMaxTermsPerLaunch terms)
-    struct L {
-        const PauliGroup* g;
-        size_t t0, t1;
-    };
-    std::vector<L> launches;
-    for (const auto& g : groups)
-        for (size_t t0 = 0; t0 < g.coef.size(); t0 += kMaxTermsPerLaunch)
-            launches.push_back({&g, t0, std::min(g.coef.size(), t0 + kMaxTermsPerLaunch)});
-    if (launches.empty()) {
+    if (groups.empty()) {
         out[0] = out[1] = 0.0;
         return;
     }
-    const unsigned gmax = red_grid(N);
-    ensure_scratch(s, 2 * size_t(gmax) * launches.size() + 2);
-    int slots = 0;
-    for (const L& l : launches) {
-        TermParams P;
-        P.xmask = l.g->xmask;
-        std::vector<int> fixed;
-        if (P.xmask) fixed.push_back(__builtin_ctzll(P.xmask));
-        P.ip = make_index_plan(s->n, fixed, 0);
-        P.nterms = int(l.t1 - l.t0);
-        for (size_t t = l.t0; t < l.t1; t++) {
-            P.coef[t - l.t0] = l.g->coef[t];
-            P.zmask[t - l.t0] = l.g->zmask[t];
-            P.nY[t - l.t0] = __builtin_popcountll(l.g->xmask & l.g->zmask[t]);
-        }
-        const unsigned g = red_grid(P.ip.n_iter);
-        double* part = s->scratch.d_part + 2 * size_t(slots);
-        with_type(arith_of(s), s->data, [&](auto p) { k_expect_group<<<g, kRedThreads, 0, s->stream>>>(p, P, part); });
-        QS_TRY_CUDA(cudaGetLastError());
-        slots += int(g);
-    }
-    finish2(s, slots, out);
+    const ExpectPlan plan = plan_expectation(groups, s->n);
+    const ExpectLaunches L = expectation_launches(plan, s->n, arith_of(s), size_t(1) << 40);
+    ensure_scratch(s, 2 * L.slots + 2);
+    launch_expectation(plan, L, s->data, s->n, arith_of(s), s->stream, s->scratch.d_part);
+    finish2(s, int(L.slots), out);
 }
 
 void reduce_pauli_transition(qs_state* lam, const qs_state* psi, uint64_t xmask, uint64_t zmask, double out[2]) {
@@ -637,67 +662,19 @@ void expectation_noalloc(const void* psi, int n, qs_dtype dt, cudaStream_t st, c
     QS_REQUIRE(obs != nullptr && out != nullptr, "null observable or output");
     QS_REQUIRE(obs->n_terms >= 0, "negative term count");
     QS_REQUIRE(obs->n_terms == 0 || (obs->coef && obs->x_mask && obs->z_mask), "null observable arrays");
-    const uint64_t lim = (1ull << n) - 1;
-    // launches: one per (distinct flip mask, chunk of kMaxTermsPerLaunch terms), counted first
-    int launches = 0;
-    for (int t = 0; t < obs->n_terms; t++) {
-        QS_REQUIRE((obs->x_mask[t] & ~lim) == 0 && (obs->z_mask[t] & ~lim) == 0, "Pauli term acts on a qubit >= n");
-        bool first = true;
-        for (int u = 0; u < t && first; u++) first = obs->x_mask[u] != obs->x_mask[t];
-        if (!first) continue;
-        int cnt = 0;
-        for (int u = t; u < obs->n_terms; u++) cnt += obs->x_mask[u] == obs->x_mask[t];
-        launches += (cnt + kMaxTermsPerLaunch - 1) / kMaxTermsPerLaunch;
-    }
-    if (launches == 0) {
+    const std::vector<PauliGroup> groups = group_observable(obs, n);
+    if (groups.empty()) {
         out[0] = out[1] = 0.0;
         return;
     }
-    // 2 doubles per block and launch, plus the 2 final values at the end of the array
-    const size_t max_slots = (kNoAllocScratchDoubles - 2) / 2;
-    QS_REQUIRE(size_t(launches) <= max_slots / 16,
-               "observable needs more kernel launches than the allocation-free scratch holds "
-               "(at most 2047 groups of up to 48 terms with a common X/Y pattern)");
-    const unsigned cap = unsigned(max_slots / size_t(launches));
+    const Arith ar = dt == QS_C64 ? Arith::F32 : Arith::F64;
+    const ExpectPlan plan = plan_expectation(groups, n);
+    // 2 doubles per block partial, plus the 2 final values at the end of the array
+    const ExpectLaunches L = expectation_launches(plan, n, ar, (kNoAllocScratchDoubles - 2) / 2);
     double* scratch = noalloc_scratch();
     double* d_out = scratch + kNoAllocScratchDoubles - 2;
-    int slots = 0;
-    for (int t = 0; t < obs->n_terms; t++) {
-        bool first = true;
-        for (int u = 0; u < t && first; u++) first = obs->x_mask[u] != obs->x_mask[t];
-        if (!first) continue;
-        const uint64_t f = obs->x_mask[t];
-        int u = t;
-        while (u < obs->n_terms) {
-            TermParams P;
-            P.xmask = f;
-            P.ip = IndexPlan();
-            if (f) {
-                P.ip.nfix = 1;
-                P.ip.fixpos[0] = __builtin_ctzll(f);
-                P.ip.n_iter = 1ull << (n - 1);
-            } else {
-                P.ip.n_iter = 1ull << n;
-            }
-            P.nterms = 0;
-            for (; u < obs->n_terms && P.nterms < kMaxTermsPerLaunch; u++) {
-                if (obs->x_mask[u] != f) continue;
-                P.coef[P.nterms] = obs->coef[u];
-                P.zmask[P.nterms] = obs->z_mask[u];
-                P.nY[P.nterms] = __builtin_popcountll(f & obs->z_mask[u]);
-                P.nterms++;
-            }
-            if (P.nterms == 0) break;
-            const unsigned g = std::min(red_grid(P.ip.n_iter), cap);
-            double* part = scratch + 2 * size_t(slots);
-            if (dt == QS_C64)
-                k_expect_group<<<g, kRedThreads, 0, st>>>(reinterpret_cast<const float2*>(psi), P, part);
-            else
-                k_expect_group<<<g, kRedThreads, 0, st>>>(reinterpret_cast<const double2*>(psi), P, part);
-            QS_TRY_CUDA(cudaGetLastError());
-            slots += int(g);
-        }
-    }
+    launch_expectation(plan, L, psi, n, ar, st, scratch);
+    const int slots = int(L.slots);
     k_final2<<<1, kRedThreads, 0, st>>>(scratch, slots, d_out);
     QS_TRY_CUDA(cudaGetLastError());
     QS_TRY_CUDA(cudaMemcpyAsync(out, d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -207,3 +207,44 @@ def test_fusion_reordered_blocks_exact(k):
         plan = qs.FusedCircuit(circ, k)
         got = run_plan_with_oracle(plan, n)
         assert np.max(np.abs(got - ref)) < 1e-12
+
+
+def test_expectation_plan_packs_flip_groups_into_tiles():
+    """The host plan of qs_expectation: each tiled read holds qubits 0..2 plus 9 others, every
+    flip mask lies inside the tile of some read, and a 30-qubit transverse-field Ising chain
+    (31 flip-mask groups) needs 3 reads instead of 31."""
+    n = 30
+    obs = W.tfim_observable(n, 1.0)
+    masks, single = qs.expectation_plan(n, obs)
+    assert len(masks) == 3 and single == 0
+    for m in masks:
+        assert m & 7 == 7 and bin(m).count("1") == 12 and m < (1 << n)
+    for f in set(int(x) for x in obs.x_mask):
+        assert any(f & ~m == 0 for m in masks), f
+    # small states: the tile is the whole state; a read takes at most 24 flip-mask groups
+    r = W.random_pauli_observable(9, 30, 1)
+    groups = len(set(int(x) for x in r.x_mask))
+    masks, single = qs.expectation_plan(9, r)
+    assert masks == [(1 << 9) - 1] * ((groups + 23) // 24) and single == 0
+    # a diagonal observable: one read whatever its size
+    z = W.PauliObservable(24, np.ones(40), np.zeros(40, dtype=np.uint64),
+                          np.arange(1, 41, dtype=np.uint64) * 12345)
+    masks, single = qs.expectation_plan(24, z)
+    assert len(masks) == 1 and single == 0
+    # a flip mask with 10 X positions above qubit 2 fits no tile: a single-group read
+    wide = sum(1 << q for q in range(3, 13))
+    w = W.PauliObservable(20, np.array([1.0, 0.5]), np.array([wide, 1], dtype=np.uint64),
+                          np.array([0, 0], dtype=np.uint64))
+    masks, single = qs.expectation_plan(20, w)
+    assert single == 1 and len(masks) == 1 and masks[0] & 1
+    # Heisenberg chain (XX, YY share a flip mask; ZZ diagonal) on 24 qubits: 3 reads
+    terms = []
+    for i in range(23):
+        m = (1 << i) | (1 << (i + 1))
+        terms += [(1.0, m, 0), (1.0, m, m), (1.0, 0, m)]
+    h = W.PauliObservable(24, np.array([t[0] for t in terms]), np.array([t[1] for t in terms], dtype=np.uint64),
+                          np.array([t[2] for t in terms], dtype=np.uint64))
+    masks, single = qs.expectation_plan(24, h)
+    assert single == 0 and len(masks) <= 3
+    with pytest.raises(qs.QsError):
+        qs.expectation_plan(35, obs)

@@ -53,11 +53,23 @@ def test_noalloc_matches_allocating_entry_point(qs, dtype):
         st.close()
 
 
+def wide_masks(n, count):
+    """The first `count` flip masks with 10 or more X positions above qubit 2: none fits a tile,
+    so each takes a launch of its own."""
+    out = []
+    f = 0
+    while len(out) < count:
+        f += 1
+        if bin(f >> 3).count("1") >= 10:
+            out.append(f)
+    return np.array(out, dtype=np.uint64)
+
+
 def test_noalloc_rejects_oversized_observable(qs):
-    n = 13
+    n = 20
     st = qs.State(n, 2)
-    m = 2100                      # distinct X/Y patterns -> one launch each, beyond the 2047 limit
-    obs = W.PauliObservable(n, np.ones(m), np.arange(1, m + 1, dtype=np.uint64), np.zeros(m, dtype=np.uint64))
+    m = 33000                     # single-group launches beyond the 32767 block partials
+    obs = W.PauliObservable(n, np.ones(m), wide_masks(n, m), np.zeros(m, dtype=np.uint64))
     rc, _ = noalloc(qs, st, obs)
     assert rc == qs.QS_ERR_INVALID_ARG
     assert b"launches" in qs.lib().qs_last_error()
