@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <tuple>
 
 #include "qsim_arith.cuh"
 
@@ -385,6 +386,168 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_expect_tiled(const C* __res
     }
 }
 
+// ---------------------------------------------------------------- transition amplitude
+// <bra| sum_t alpha_t P_t |ket> with P_t |x> = i^{nY} (-1)^{popc(x & z)} |x ^ f>: per flip group,
+// sum_y conj(bra_y) ket_{y^f} alpha (-i)^{nY} (-1)^{popc(y & z)} over every y (no pairing), on
+// tiles of 2^11 slots of both states. Each thread takes 8 items of a group (3 item bits); the
+// slot's rotation (-i)^{nY} picks the component and sign of Q = Q_re + i Q_im for each output.
+__device__ __forceinline__ uint32_t thread_slot3(uint32_t tid, uint32_t ex) {
+    uint32_t tb = tid;
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+        const uint32_t p = (ex >> (8 * e)) & 0xFFu;
+        const uint32_t lo = tb & ((1u << p) - 1u);
+        tb = ((tb ^ lo) << 1) | lo;
+    }
+    return tb;
+}
+
+template <int B0, int B1>
+__device__ __forceinline__ void trans_slot_sums(const TileGroup& G, const TileSlot* S, const float2* gam, uint32_t tid,
+                                                const float* qr, const float* qrl, const float* qi,
+                                                const float* qil, float& rh, float& rl, float& ih, float& il) {
+#pragma unroll
+    for (int bk = B0; bk < B1; bk++) {
+        const int s1 = G.slot0 + G.bstart[bk + 1];
+        for (int s = G.slot0 + G.bstart[bk]; s < s1; s++) {
+            const float2 g = gam[s];
+            const TileSlot sl = S[s];
+            const uint32_t flip = uint32_t(__popc(tid & sl.zthr) & 1) << 31;
+            const uint32_t rot = sl.pad;
+            const bool odd = rot & 1u;
+            const uint32_t fr = flip ^ (uint32_t(rot >= 2u) << 31);
+            const uint32_t fi = flip ^ (uint32_t(rot == 1u || rot == 2u) << 31);
+            acc_prod(rh, rl, flip_sign(g.x, fr), flip_sign(g.y, fr), odd ? qi[bk] : qr[bk], odd ? qil[bk] : qrl[bk]);
+            acc_prod(ih, il, flip_sign(g.x, fi), flip_sign(g.y, fi), odd ? qr[bk] : qi[bk], odd ? qrl[bk] : qil[bk]);
+        }
+    }
+}
+
+template <typename E, bool kLo>
+__device__ __forceinline__ void trans_group(const TileGroup& G, const TileSlot* S, const E* tbra, const E* tket,
+                                            const float2* gam, uint32_t tid, float& rh, float& rl, float& ih,
+                                            float& il) {
+    const uint32_t tb = thread_slot3(tid, G.excl);
+    const uint32_t f = G.f;
+    uint32_t o[8];
+    o[0] = tb;
+#pragma unroll
+    for (int k = 1; k < 8; k++) o[k] = o[k ^ (1 << top_bit(k))] | G.imask[top_bit(k)];
+    float qr[8], qrl[8], qi[8], qil[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const DFc b = dfc(tbra[o[k]]), c = dfc(tket[o[k] ^ f]);
+        // conj(b) c = (b.re c.re + b.im c.im) + i (b.re c.im - b.im c.re)
+        df_dot2<kLo>(b.rh, b.rl, c.rh, c.rl, b.ih, b.il, c.ih, c.il, qr[k], qrl[k]);
+        df_dot2<kLo>(b.rh, b.rl, c.ih, c.il, -b.ih, -b.il, c.rh, c.rl, qi[k], qil[k]);
+    }
+    const bool full = G.wht != 0;
+    grid_transform<8>(qr, qrl, full);
+    grid_transform<8>(qi, qil, full);
+    if (full)
+        trans_slot_sums<0, 8>(G, S, gam, tid, qr, qrl, qi, qil, rh, rl, ih, il);
+    else
+        trans_slot_sums<0, 1>(G, S, gam, tid, qr, qrl, qi, qil, rh, rl, ih, il);
+}
+
+constexpr size_t trans_smem_bytes(size_t elem) {
+    return 2 * elem * (size_t(1) << kTransBits) + sizeof(float2) * kTileMaxSlots + sizeof(TileSlot) * kTileMaxSlots +
+           sizeof(TileTerm) * kTileMaxTerms;
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kTileThreads, 2) k_transition_tiled(const C* __restrict__ bra,
+                                                                       const C* __restrict__ ket,
+                                                                       const __grid_constant__ TileParams P,
+                                                                       double* __restrict__ part) {
+    using E = typename TileElem<C>::T;
+    constexpr int kA = 1 << kTransBits;
+    extern __shared__ __align__(16) unsigned char tsm[];
+    E* tbra = reinterpret_cast<E*>(tsm);
+    E* tket = tbra + kA;
+    float2* gam = reinterpret_cast<float2*>(tket + kA);
+    TileSlot* slots = reinterpret_cast<TileSlot*>(gam + kTileMaxSlots);
+    TileTerm* terms = reinterpret_cast<TileTerm*>(slots + kTileMaxSlots);
+    const uint32_t tid = threadIdx.x;
+    for (int i = tid; i < P.nslots; i += kTileThreads) slots[i] = P.s[i];
+    for (int i = tid; i < P.nterms; i += kTileThreads) terms[i] = P.t[i];
+    const int namps = 1 << P.b;
+    for (int j = namps + int(tid); j < kA; j += kTileThreads) {
+        tbra[j] = E{};
+        tket[j] = E{};
+    }
+    uint64_t dthr = 0;
+    for (int i = 0; i < 8 && i < P.b; i++)
+        if ((tid >> i) & 1) dthr |= 1ull << P.tpos[i];
+    uint64_t rbase = deposit64(blockIdx.x, P.rest_mask);
+    const uint64_t step = deposit64(gridDim.x, P.rest_mask);
+    double accr = 0.0, acci = 0.0;
+    __syncthreads();
+    for (uint64_t r = blockIdx.x; r < P.n_tiles; r += gridDim.x) {
+        __syncthreads();  // the previous tile's readers are done
+#pragma unroll
+        for (int hf = 0; hf < 2; hf++) {
+            constexpr int kH = kA / kTileThreads / 2;
+            C v[kH], w[kH];
+#pragma unroll
+            for (int k = 0; k < kH; k++) {
+                const int j = int(tid) + kTileThreads * (hf * kH + k);
+                if (j < namps) {
+                    const uint64_t a = rbase | dthr | P.dep_hi[hf * kH + k];
+                    v[k] = bra[a];
+                    w[k] = ket[a];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kH; k++) {
+                const int j = int(tid) + kTileThreads * (hf * kH + k);
+                if (j < namps) {
+                    tbra[j] = to_tile(v[k]);
+                    tket[j] = to_tile(w[k]);
+                }
+            }
+        }
+        if (int(tid) < P.nslots) {
+            const TileSlot sl = slots[tid];
+            double gsum = 0.0;
+            for (int t = sl.term0; t < sl.term0 + sl.nterm; t++) {
+                const TileTerm T = terms[t];
+                gsum += (__popcll(rbase & T.zR) & 1) ? -T.alpha : T.alpha;
+            }
+            float h, l;
+            split_double_int(gsum, h, l);
+            gam[tid] = make_float2(h, l);
+        }
+        __syncthreads();
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+        for (int g = 0; g < P.ngroups; g++)
+            trans_group<E, TileElem<C>::kLo>(P.g[g], slots, tbra, tket, gam, tid, rh, rl, ih, il);
+        accr += widen_float_int(rh) + widen_float_int(rl);
+        acci += widen_float_int(ih) + widen_float_int(il);
+        rbase = ((rbase | ~P.rest_mask) + step) & P.rest_mask;
+    }
+    __shared__ double sh[kTileThreads / 32];
+    const double tr = block_sum<kTileThreads>(accr, sh);
+    const double ti = block_sum<kTileThreads>(acci, sh);
+    if (tid == 0) {
+        part[2 * blockIdx.x] = tr;
+        part[2 * blockIdx.x + 1] = ti;
+    }
+}
+
+template <typename C>
+int trans_blocks_per_sm() {
+    static int b = 0;
+    if (!b) {
+        const size_t bytes = trans_smem_bytes(sizeof(typename TileElem<C>::T));
+        cudaFuncSetAttribute(k_transition_tiled<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transition_tiled<C>, kTileThreads, bytes);
+        b = nb > 0 ? nb : 1;
+    }
+    return b;
+}
+
 template <typename C>
 int tile_blocks_per_sm() {
     static int b = 0;
@@ -492,22 +655,27 @@ void build_group(const Chunk& ch, const int* tpos, int b, uint64_t T, TileParams
 
 }  // namespace
 
-ExpectPlan plan_expectation(const std::vector<PauliGroup>& groups, int n) {
-    ExpectPlan plan;
-    const int b = std::min(n, kTileBits);
+namespace {
+
+// Packs the flip-mask groups into tiles of tbits qubits (qubits 0..2 plus tbits - 3 others, or
+// the whole state) with the fewest new tile qubits per group; a group whose flip mask has more
+// than tbits - 3 bits above qubit 2 goes to plan.heavy. build(chunk, tpos, b, T, P) adds a group.
+template <class Build>
+void pack_tiles(const std::vector<PauliGroup>& groups, int n, int tbits, ExpectPlan& plan, Build build) {
+    const int b = std::min(n, tbits);
     const uint64_t full = n >= 64 ? ~0ull : ((1ull << n) - 1);
-    const uint64_t low = n <= kTileBits ? full : ((1ull << kTileLowBits) - 1);
+    const uint64_t low = n <= tbits ? full : ((1ull << kTileLowBits) - 1);
     const int hbudget = b - __builtin_popcountll(low);
     std::vector<const PauliGroup*> order;
     for (const auto& g : groups) order.push_back(&g);
     std::stable_sort(order.begin(), order.end(),
                      [](const PauliGroup* a, const PauliGroup* c) { return a->xmask < c->xmask; });
-    struct Build {
+    struct Pass {
         uint64_t T;
         std::vector<Chunk> ch;
         int terms;
     };
-    std::vector<Build> passes;
+    std::vector<Pass> passes;
     for (const PauliGroup* g : order) {
         const uint64_t h = g->xmask & ~low;
         if (__builtin_popcountll(h) > hbudget) {
@@ -520,7 +688,7 @@ ExpectPlan plan_expectation(const std::vector<PauliGroup>& groups, int n) {
             const int nt = int(t1 - t0);
             int best = -1, best_growth = 1 << 30;
             for (size_t p = 0; p < passes.size(); p++) {
-                const Build& B = passes[p];
+                const Pass& B = passes[p];
                 if (B.ch.size() >= size_t(kTileMaxGroups) || B.terms + nt > kTileMaxTerms) continue;
                 const uint64_t U = B.T | h;
                 if (__builtin_popcountll(U & ~low) > hbudget) continue;
@@ -531,7 +699,7 @@ ExpectPlan plan_expectation(const std::vector<PauliGroup>& groups, int n) {
                 }
             }
             if (best < 0) {
-                passes.push_back(Build{low | h, {}, 0});
+                passes.push_back(Pass{low | h, {}, 0});
                 best = int(passes.size()) - 1;
             }
             passes[size_t(best)].T |= h;
@@ -539,7 +707,7 @@ ExpectPlan plan_expectation(const std::vector<PauliGroup>& groups, int n) {
             passes[size_t(best)].terms += nt;
         }
     }
-    for (Build& B : passes) {
+    for (Pass& B : passes) {
         // pad T with the lowest unused qubits up to b bits
         for (int q = 0; q < n && __builtin_popcountll(B.T) < b; q++) B.T |= 1ull << q;
         TileParams P{};
@@ -551,18 +719,88 @@ ExpectPlan plan_expectation(const std::vector<PauliGroup>& groups, int n) {
         for (int i = 0; i < b; i++) P.tpos[i] = uint8_t(tpos[i]);
         P.rest_mask = full & ~B.T;
         P.n_tiles = 1ull << (n - b);
-        for (int k = 0; k < kTileAmps / kTileThreads; k++) {
+        for (int k = 0; k < (1 << (tbits - 8)); k++) {
             uint64_t o = 0;
             for (int i = 8; i < b; i++)
                 if (((k << 8) >> i) & 1) o |= 1ull << tpos[i];
             P.dep_hi[k] = o;
         }
-        for (const Chunk& c : B.ch) build_group(c, tpos, b, B.T, P);
-        // groups that use only the plain sum of Re A first, so that the kernel takes them in pairs
-        std::stable_partition(P.g, P.g + P.ngroups, [](const TileGroup& G) { return G.kind == kTileRe && !G.wht; });
+        for (const Chunk& c : B.ch) build(c, tpos, b, B.T, P);
         plan.passes.push_back(P);
         plan.tmask.push_back(B.T);
     }
+}
+
+// transition group: 3 item bits (no pivot: every tile slot y is a term), slots keyed by
+// (item mask, thread mask, nY mod 4)
+void build_trans_group(const Chunk& ch, const int* tpos, int b, uint64_t T, TileParams& P) {
+    QS_REQUIRE(P.ngroups < kTileMaxGroups, "tile pass group overflow");
+    TileGroup& G = P.g[P.ngroups++];
+    G = TileGroup();
+    const uint64_t f = ch.g->xmask;
+    G.f = compress_bits(f, tpos, b);
+    std::vector<std::pair<int, int>> cand;  // (score, -bit)
+    for (int q = 0; q < kTransBits; q++) {
+        int score = 0;
+        if (q < b)
+            for (size_t t = ch.t0; t < ch.t1; t++) score += int((ch.g->zmask[t] >> tpos[q]) & 1);
+        cand.push_back({score, -q});
+    }
+    std::sort(cand.begin(), cand.end());
+    int items[3];
+    for (int i = 0; i < 3; i++) items[i] = -cand[size_t(i)].second;
+    std::sort(items, items + 3);
+    int thr[kTransBits];
+    int nthr = 0;
+    for (int q = 0; q < kTransBits; q++)
+        if (q != items[0] && q != items[1] && q != items[2]) thr[nthr++] = q;
+    QS_REQUIRE(nthr == 8, "tile bit split");
+    for (int e = 0; e < 3; e++) G.excl |= uint32_t(items[e]) << (8 * e);
+    for (int i = 0; i < 3; i++) G.imask[i] = 1u << items[i];
+    std::map<std::tuple<int, uint32_t, int>, std::vector<TileTerm>> keyed;
+    for (size_t t = ch.t0; t < ch.t1; t++) {
+        const uint64_t z = ch.g->zmask[t];
+        const uint32_t zl = compress_bits(z & T, tpos, b);
+        const int m = int(compress_bits(zl, items, 3));
+        const uint32_t zthr = compress_bits(zl, thr, nthr);
+        if (m) G.wht = 1;
+        keyed[std::make_tuple(m, zthr, __builtin_popcountll(f & z) & 3)].push_back(TileTerm{z & ~T, ch.g->coef[t]});
+    }
+    G.kind = kTileReIm;
+    G.slot0 = uint16_t(P.nslots);
+    int cnt[16] = {};
+    for (const auto& kv : keyed) {
+        QS_REQUIRE(P.nslots < kTileMaxSlots, "tile pass slot overflow");
+        TileSlot& S = P.s[P.nslots++];
+        S.term0 = uint16_t(P.nterms);
+        S.nterm = uint16_t(kv.second.size());
+        S.zthr = uint16_t(std::get<1>(kv.first));
+        S.bucket = uint8_t(std::get<0>(kv.first));
+        S.pad = uint8_t(std::get<2>(kv.first));  // (-i)^{nY} rotation
+        for (const TileTerm& tt : kv.second) {
+            QS_REQUIRE(P.nterms < kTileMaxTerms, "tile pass term overflow");
+            P.t[P.nterms++] = tt;
+        }
+        cnt[std::get<0>(kv.first)]++;
+    }
+    G.bstart[0] = 0;
+    for (int k = 0; k < 16; k++) G.bstart[k + 1] = uint8_t(G.bstart[k] + cnt[k]);
+}
+
+}  // namespace
+
+ExpectPlan plan_expectation(const std::vector<PauliGroup>& groups, int n) {
+    ExpectPlan plan;
+    pack_tiles(groups, n, kTileBits, plan, build_group);
+    // groups that use only the plain sum of Re A first, so that the kernel takes them in pairs
+    for (TileParams& P : plan.passes)
+        std::stable_partition(P.g, P.g + P.ngroups, [](const TileGroup& G) { return G.kind == kTileRe && !G.wht; });
+    return plan;
+}
+
+ExpectPlan plan_transition(const std::vector<PauliGroup>& groups, int n) {
+    ExpectPlan plan;
+    pack_tiles(groups, n, kTransBits, plan, build_trans_group);
     return plan;
 }
 
@@ -591,6 +829,39 @@ void launch_expect_pass(const TileParams& P, const void* psi, Arith ar, double* 
             tile_blocks_per_sm<float4>();
             k_expect_tiled<float4><<<grid, kTileThreads, tile_smem_bytes(sizeof(float4)), st>>>(
                 static_cast<const float4*>(psi), P, part);
+            break;
+    }
+    QS_TRY_CUDA(cudaGetLastError());
+}
+
+unsigned trans_pass_grid(const TileParams& P, Arith ar) {
+    int bps = 1;
+    switch (ar) {
+        case Arith::F32: bps = trans_blocks_per_sm<float2>(); break;
+        case Arith::F64: bps = trans_blocks_per_sm<double2>(); break;
+        default: bps = trans_blocks_per_sm<float4>(); break;
+    }
+    const uint64_t want = uint64_t(bps) * uint64_t(sm_count());
+    return unsigned(std::max<uint64_t>(1, std::min<uint64_t>(P.n_tiles, want)));
+}
+
+void launch_transition_pass(const TileParams& P, const void* bra, const void* ket, Arith ar, double* part,
+                            unsigned grid, cudaStream_t st) {
+    switch (ar) {
+        case Arith::F32:
+            trans_blocks_per_sm<float2>();
+            k_transition_tiled<float2><<<grid, kTileThreads, trans_smem_bytes(sizeof(float2)), st>>>(
+                static_cast<const float2*>(bra), static_cast<const float2*>(ket), P, part);
+            break;
+        case Arith::F64:
+            trans_blocks_per_sm<double2>();
+            k_transition_tiled<double2><<<grid, kTileThreads, trans_smem_bytes(sizeof(float4)), st>>>(
+                static_cast<const double2*>(bra), static_cast<const double2*>(ket), P, part);
+            break;
+        default:
+            trans_blocks_per_sm<float4>();
+            k_transition_tiled<float4><<<grid, kTileThreads, trans_smem_bytes(sizeof(float4)), st>>>(
+                static_cast<const float4*>(bra), static_cast<const float4*>(ket), P, part);
             break;
     }
     QS_TRY_CUDA(cudaGetLastError());

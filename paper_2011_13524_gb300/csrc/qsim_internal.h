@@ -170,6 +170,7 @@ std::vector<PauliGroup> group_observable(const qs_pauli_obs* obs, int n);
 // evaluates every flip-mask group whose flip mask lies in T. Groups whose flip mask has more than
 // 9 bits above qubit 2 run one launch each.
 constexpr int kTileBits = 12;
+constexpr int kTransBits = 11;  // tiles of the two-state transition passes
 constexpr int kTileAmps = 1 << kTileBits;
 constexpr int kTileThreads = 256;
 constexpr int kTileLowBits = 3;
@@ -193,7 +194,8 @@ struct TileGroup {
 struct TileSlot {
     uint16_t term0 = 0, nterm = 0;
     uint16_t zthr = 0;       // Z bits over the thread bits, in thread-index order
-    uint8_t bucket = 0, pad = 0;
+    uint8_t bucket = 0;
+    uint8_t pad = 0;         // transition slots: nY mod 4, the rotation (-i)^{nY}
 };
 struct TileTerm {
     uint64_t zR = 0;         // Z bits outside the tile
@@ -220,6 +222,12 @@ struct ExpectPlan {
 };
 ExpectPlan plan_expectation(const std::vector<PauliGroup>& groups, int n);
 unsigned expect_pass_grid(const TileParams& P, Arith ar);
+// Transition amplitude <bra|O|ket>: tiles of 2^11 slots of both states (qubits 0..2 plus 8
+// others); flip groups with more than 8 bits above qubit 2 go to heavy.
+ExpectPlan plan_transition(const std::vector<PauliGroup>& groups, int n);
+unsigned trans_pass_grid(const TileParams& P, Arith ar);
+void launch_transition_pass(const TileParams& P, const void* bra, const void* ket, Arith ar, double* part,
+                            unsigned grid, cudaStream_t st);
 // part[2 j], part[2 j + 1] = block j's partial (real, 0) for j < grid
 void launch_expect_pass(const TileParams& P, const void* psi, Arith ar, double* part, unsigned grid,
                         cudaStream_t st);

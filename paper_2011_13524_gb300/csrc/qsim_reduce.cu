@@ -482,36 +482,47 @@ void reduce_transition(const qs_state* bra, const qs_pauli_obs* obs, const qs_st
     const uint64_t N = 1ull << s->n;
     QS_REQUIRE(arith_of(bra) == arith_of(ket), "states in different layouts");
     if (ket->stream != s->stream) QS_TRY_CUDA(cudaStreamSynchronize(ket->stream));
-    std::vector<std::pair<const PauliGroup*, std::pair<size_t, size_t>>> launches;
-    for (const auto& g : groups)
-        for (size_t t0 = 0; t0 < g.coef.size(); t0 += kMaxTermsPerLaunch)
-            launches.push_back({&g, {t0, std::min(g.coef.size(), t0 + kMaxTermsPerLaunch)}});
-    if (launches.empty()) {
+    if (groups.empty()) {
         out[0] = out[1] = 0.0;
         return;
     }
+    const Arith ar = arith_of(s);
+    const ExpectPlan plan = plan_transition(groups, s->n);
+    std::vector<unsigned> grids;
+    size_t slots_needed = 0;
+    for (const TileParams& P : plan.passes) {
+        grids.push_back(trans_pass_grid(P, ar));
+        slots_needed += grids.back();
+    }
     const unsigned gr = red_grid(N);
-    ensure_scratch(s, 2 * size_t(gr) * launches.size() + 2);
-    int slots = 0;
-    for (const auto& l : launches) {
+    slots_needed += size_t(gr) * plan.heavy.size();
+    ensure_scratch(s, 2 * slots_needed + 2);
+    size_t slots = 0;
+    for (size_t p = 0; p < plan.passes.size(); p++) {
+        launch_transition_pass(plan.passes[p], bra->data, ket->data, ar, s->scratch.d_part + 2 * slots, grids[p],
+                               s->stream);
+        slots += grids[p];
+    }
+    // flip groups wider than a tile: one pass each
+    for (const HeavyChunk& c : plan.heavy) {
         TermParams P;
-        P.xmask = l.first->xmask;
+        P.xmask = c.g->xmask;
         P.ip = make_index_plan(s->n, {}, 0);
-        P.nterms = int(l.second.second - l.second.first);
-        for (size_t t = l.second.first; t < l.second.second; t++) {
-            P.coef[t - l.second.first] = l.first->coef[t];
-            P.zmask[t - l.second.first] = l.first->zmask[t];
-            P.nY[t - l.second.first] = __builtin_popcountll(l.first->xmask & l.first->zmask[t]);
+        P.nterms = int(c.t1 - c.t0);
+        for (size_t t = c.t0; t < c.t1; t++) {
+            P.coef[t - c.t0] = c.g->coef[t];
+            P.zmask[t - c.t0] = c.g->zmask[t];
+            P.nY[t - c.t0] = __builtin_popcountll(c.g->xmask & c.g->zmask[t]);
         }
-        double* part = s->scratch.d_part + 2 * size_t(slots);
-        with_type(arith_of(s), s->data, [&](auto pb) {
+        double* part = s->scratch.d_part + 2 * slots;
+        with_type(ar, s->data, [&](auto pb) {
             using CP = decltype(pb);
             k_transition_group<<<gr, kRedThreads, 0, s->stream>>>(pb, reinterpret_cast<CP>(ket->data), N, P, part);
         });
         QS_TRY_CUDA(cudaGetLastError());
-        slots += int(gr);
+        slots += gr;
     }
-    finish2(s, slots, out);
+    finish2(s, int(slots), out);
 }
 
 void reduce_marginal(const qs_state* st, const int32_t* measured, double* out) {

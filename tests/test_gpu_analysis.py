@@ -116,3 +116,72 @@ def test_sampling_full_size(qs):
     st.close()
     del st
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n", [2, 11, 12, 15, 17])
+@pytest.mark.parametrize("dtype", [2, 1])
+def test_transition_amplitude_tiled_kinds(qs, n, dtype):
+    """Every observable kind of the tiled passes (Ising, Heisenberg with Y pairs, one flip group
+    with many Z patterns, random strings, some too wide for a tile) against the oracle on the
+    states the GPU holds."""
+    from test_gpu_expect import observables
+    bra0, ket0 = W.random_state(n, 40 + n), W.random_state(n, 80 + n) * 0.8
+    bra, ket = qs.State(n, dtype), qs.State(n, dtype)
+    bra.load(bra0)
+    ket.load(ket0)
+    vb, vk = bra.get_vector().astype(np.complex128), ket.get_vector().astype(np.complex128)
+    nb, nk = float(np.linalg.norm(vb)), float(np.linalg.norm(vk))
+    for name, obs in observables(n, 2000 + n).items():
+        ref = oracle.transition_amplitude(vb, vk, n, obs)
+        got = bra.transition_amplitude(obs, ket)
+        scale = float(np.sum(np.abs(obs.coef))) * nb * nk
+        assert abs(got - ref) <= 1e-13 * max(1.0, scale), (name, got, ref)
+    bra.close()
+    ket.close()
+
+
+def single_qubit_state(theta, phi):
+    return np.array([math.cos(theta / 2), complex(math.cos(phi), math.sin(phi)) * math.sin(theta / 2)])
+
+
+PAULI = {(0, 0): np.eye(2), (1, 0): np.array([[0, 1], [1, 0]]), (1, 1): np.array([[0, -1j], [1j, 0]]),
+         (0, 1): np.diag([1.0, -1.0])}
+
+
+def test_transition_amplitude_full_size(qs):
+    """n = 30 complex128: two product states from U3 gates, an observable with nearest-neighbour
+    ZZ, XX and YY, single X, Y and Z and a wide Y string; <bra|P|ket> factorises over qubits."""
+    import torch
+    n = 30
+    rng = W.SplitMix64(404)
+    ang = [[(math.pi * rng.uniform(), 2 * math.pi * rng.uniform()) for _ in range(n)] for _ in range(2)]
+    states = []
+    for a in ang:
+        st = qs.State(n, 2)
+        st.run(W.Circuit(n, [W.Gate("U3", (q,), params=(a[q][0], a[q][1], 0.0)) for q in range(n)]), 0)
+        states.append(st)
+    terms = []
+    for i in range(n - 1):
+        m = (1 << i) | (1 << (i + 1))
+        terms += [(rng.uniform_range(-1, 1), 0, m), (rng.uniform_range(-1, 1), m, 0), (rng.uniform_range(-1, 1), m, m)]
+    for q in range(n):
+        terms += [(rng.uniform_range(-1, 1), 1 << q, 0), (rng.uniform_range(-1, 1), 1 << q, 1 << q),
+                  (rng.uniform_range(-1, 1), 0, 1 << q)]
+    wide = sum(1 << q for q in range(3, 30, 2))
+    terms.append((0.9, wide, wide))
+    obs = W.PauliObservable(n, np.array([t[0] for t in terms]), np.array([t[1] for t in terms], dtype=np.uint64),
+                            np.array([t[2] for t in terms], dtype=np.uint64))
+    b1 = [single_qubit_state(*ang[0][q]) for q in range(n)]
+    k1 = [single_qubit_state(*ang[1][q]) for q in range(n)]
+    ref = 0j
+    for c, xm, zm in zip(obs.coef, obs.x_mask, obs.z_mask):
+        v = complex(c)
+        for q in range(n):
+            v *= np.vdot(b1[q], PAULI[((int(xm) >> q) & 1, (int(zm) >> q) & 1)] @ k1[q])
+        ref += v
+    got = states[0].transition_amplitude(obs, states[1])
+    assert abs(got - ref) < 1e-11, (got, ref)
+    for st in states:
+        st.close()
+    del states
+    torch.cuda.empty_cache()
