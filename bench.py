@@ -489,8 +489,8 @@ def measure_extras(args, qs, torch, circuit):
     # analysis calls at n = 30 complex128: transition amplitude of the TFIM observable between two
     # states, and 100000 Z-basis samples (uniforms from the seeded generator)
     sa, sb = qs.State(n, qs.QS_C128), qs.State(n, qs.QS_C128)
-    for q in range(n):
-        sb.apply_gate(W.Gate("H", (q,)))
+    sa.run(W.u3cz_circuit(n, 4, args.seed + 1), 4)
+    sb.run(W.u3cz_circuit(n, 4, args.seed + 2), 4)
     ms = timed(lambda: sa.transition_amplitude(tf, sb))
     out["transition_amplitude_tfim_n30_ms"] = ms
     rng = W.SplitMix64(args.seed)
