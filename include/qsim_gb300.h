@@ -148,11 +148,12 @@ qs_status qs_get_c128_math(int* mode);
  * QS_TENSOR_C64: complex64 blocks of 5 or 6 targets (tcgen05.mma kind::tf32, each FP32 operand
  *   split into a TF32 head and remainder, three products: FP32-class accuracy per block, but the
  *   tensor cores' FP32 accumulator rounds toward zero, shrinking the norm by ~2e-6 per block).
- * QS_TENSOR_C128: complex128 blocks of 4 targets in double-float runs (QS_MATH_DF): the matrix
- *   and every 16-amplitude group are scaled by powers of two and cut into six 8-bit bf16 slices
- *   (the splitting of Ozaki, Ogita, Oishi and Rump); the 21 slice products of weight >= 2^-48
- *   are summed exactly in FP32 by tcgen05.mma kind::f16 and combined exactly in double-float:
- *   about 2^-45 relative error per block, the accuracy of the double-float CUDA-core kernels.
+ * QS_TENSOR_C128: complex128 blocks of 4 or 5 targets in double-float runs (QS_MATH_DF): the
+ *   matrix and every 16- or 32-amplitude group are scaled by powers of two and cut into six
+ *   8-bit bf16 slices (the splitting of Ozaki, Ogita, Oishi and Rump); the 26 slice products of
+ *   state slice s and matrix slice t with s + t <= 6 are summed exactly in FP32 by
+ *   tcgen05.mma kind::f16 and combined exactly in double-float: about 2^-45 relative error per
+ *   block, the accuracy of the double-float CUDA-core kernels.
  * Unknown bits -> QS_ERR_INVALID_ARG. Default: QS_TENSOR_C128 (its blocks meet the complex128
  * bound; the complex64 path stays opt-in because of its norm drift). */
 #define QS_TENSOR_C64 1
@@ -233,7 +234,7 @@ qs_status qs_destroy_fused(qs_fused_circuit* f);
 #define QS_KERNEL_SWAP 5       /* SWAP / controlled SWAP */
 #define QS_KERNEL_DENSE_DF 6   /* complex128 dense gate matrix in double-float arithmetic */
 #define QS_KERNEL_DENSE_TC 7   /* complex64 dense block of 5-6 targets on the tensor cores (3xTF32) */
-#define QS_KERNEL_DENSE_OZ 8   /* double-float complex128 block of 4 targets on the tensor cores (bf16 slices) */
+#define QS_KERNEL_DENSE_OZ 8   /* double-float complex128 block of 4 or 5 targets on the tensor cores (bf16 slices) */
 #define QS_KERNEL_PAULI_ROT 9  /* Pauli rotation exp(i phi P / 2), one pass over amplitude pairs */
 qs_status qs_fused_block_cost(const qs_fused_circuit* f, int b, qs_dtype dt, int* kernel, int* launches,
                               double* bytes);

@@ -138,7 +138,8 @@ void op_cost(const Op& op, int n, qs_dtype dt, int* kernel, int* launches, doubl
             k = reg ? QS_KERNEL_DENSE_REG : QS_KERNEL_DENSE_SMEM;
             if (dt == QS_C64 && m >= 5 && tensor_c64_enabled()) k = QS_KERNEL_DENSE_TC;
             if (dt == QS_C128 && c128_math() == QS_MATH_DF && m <= 3) k = QS_KERNEL_DENSE_DF;
-            if (dt == QS_C128 && c128_math() == QS_MATH_DF && m == 4 && tensor_c128_enabled()) k = QS_KERNEL_DENSE_OZ;
+            if (dt == QS_C128 && c128_math() == QS_MATH_DF && (m == 4 || m == 5) && tensor_c128_enabled())
+                k = QS_KERNEL_DENSE_OZ;
             break;
         }
         case OpKind::Diag: k = QS_KERNEL_DIAG; break;
@@ -179,12 +180,15 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
             ops[b] = pad_dense_to6(ops[b], s->n);
             tc[b] = 1;
         }
-        if (ar == Arith::DF && ops[b].targets.size() == 4 && tensor_c128_enabled()) {
+        if (ar == Arith::DF && (ops[b].targets.size() == 4 || ops[b].targets.size() == 5) && tensor_c128_enabled()) {
             ops[b] = sort_targets(ops[b]);
-            oz[b] = 1;
+            oz[b] = char(ops[b].targets.size());
         }
         offs[b] = total;
-        total += tc[b] ? tc6_matrix_bytes() : oz[b] ? oz4_matrix_bytes() : ops[b].data.size() * kernel_entry_bytes(ar);
+        total += tc[b]         ? tc6_matrix_bytes()
+                 : oz[b] == 4 ? oz4_matrix_bytes()
+                 : oz[b] == 5 ? oz5_matrix_bytes()
+                              : ops[b].data.size() * kernel_entry_bytes(ar);
         total = (total + 255) & ~size_t(255);
     }
     if (!total) return w;
@@ -193,8 +197,10 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
         if (ops[b].kind != OpKind::Dense || ops[b].targets.size() < 4) continue;
         if (tc[b])
             prepare_tc6_matrix(ops[b].data, reinterpret_cast<float*>(host.data() + offs[b]));
-        else if (oz[b])
+        else if (oz[b] == 4)
             prepare_oz4_matrix(ops[b].data, host.data() + offs[b]);
+        else if (oz[b] == 5)
+            prepare_oz5_matrix(ops[b].data, host.data() + offs[b]);
         else
             encode_entries(ar, ops[b].data, host.data() + offs[b]);
     }

@@ -380,6 +380,20 @@ void launch_with(const Op& op, void* psi, int n, cudaStream_t st, void* stage) {
                 }
                 return launch_dense_oz4(psi, n, os.targets, os.controls, os.cvals, dK, st);
             }
+            // double-float blocks of 5 targets: tensor cores, outputs in two halves
+            if (std::is_same<P, DFArith>::value && m == 5 && tensor_c128_enabled()) {
+                const Op os = op.dmat_oz ? op : sort_targets(op);
+                const void* dK = op.dmat_oz ? op.dmat : nullptr;
+                if (!dK) {
+                    QS_REQUIRE(stage != nullptr && oz5_matrix_bytes() <= kStageBytes, "no staging buffer for a wide dense gate");
+                    std::vector<unsigned char> hk(oz5_matrix_bytes());
+                    prepare_oz5_matrix(os.data, hk.data());
+                    QS_TRY_CUDA(cudaMemcpyAsync(stage, hk.data(), hk.size(), cudaMemcpyHostToDevice, st));
+                    QS_TRY_CUDA(cudaStreamSynchronize(st));  // hk is host memory that dies on return
+                    dK = stage;
+                }
+                return launch_dense_oz5(psi, n, os.targets, os.controls, os.cvals, dK, st);
+            }
             if (m == 1) return launch_dense_reg<P, 1>(op, ip, psi, st);
             if (m == 2) return launch_dense_reg<P, 2>(op, ip, psi, st);
             if (m == 3) return launch_dense_reg<P, 3>(op, ip, psi, st);

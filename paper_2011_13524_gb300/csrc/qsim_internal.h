@@ -291,6 +291,11 @@ size_t oz4_matrix_bytes();
 void prepare_oz4_matrix(const std::vector<cplx>& K, unsigned char* host_out);
 void launch_dense_oz4(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
                       const std::vector<int>& cvals, const void* dmat, cudaStream_t st);
+// 5-target blocks: the same method with the outputs in two halves (two stacked half matrices)
+size_t oz5_matrix_bytes();
+void prepare_oz5_matrix(const std::vector<cplx>& K, unsigned char* host_out);
+void launch_dense_oz5(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
+                      const std::vector<int>& cvals, const void* dmat, cudaStream_t st);
 bool oz_error_pending();
 
 // complex128 arithmetic mode (QS_MATH_FP64 / QS_MATH_DF)

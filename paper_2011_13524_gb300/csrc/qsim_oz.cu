@@ -335,6 +335,246 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kOzTmemCols));
 }
 
+// ---------------------------------------------------------------- 5-target blocks
+// The same method for 32 x 32 complex blocks: A is the 64 x 64 real form, K = 64 (four K-steps),
+// 128 groups of 32 amplitudes per tile. The accumulators of all 64 output reals (7 x 64 TMEM
+// columns) would leave no room for a second set, so the outputs are split into two halves of
+// 32 reals (amplitudes 0..15 and 16..31), each with its own stacked matrix slices (192 x 64),
+// seven diagonals of 32 columns (TMEM columns 0..223 and 256..479) and its own commit barrier:
+// half 0 is folded while the MMAs of half 1 still run. One CTA per SM (512 threads: four per
+// group, each owning four amplitudes of either half; 146 KB of shared memory with one state
+// slice buffer of 96 KB; all 512 TMEM columns).
+constexpr int kOz5Q = 5;
+constexpr int kOz5D = 1 << kOz5Q;                               // 32 amplitudes per group
+constexpr int kOz5R = 2 * kOz5D;                                // 64 reals per group
+constexpr int kOz5Threads = 512;
+constexpr int kOz5TPG = kOz5Threads / kOzTG;                    // 4 threads per group
+constexpr int kOz5Amps = kOz5D / kOz5TPG;                       // 8 amplitudes per thread
+constexpr uint32_t kOz5Sbo = (kOz5R / 8) * 128;                 // 1024
+constexpr size_t kOz5Slice = size_t(kOzTG) * kOz5R * 2;         // 16 KB
+constexpr size_t kOz5ABuf = kOzNS * kOz5Slice;                  // 96 KB
+constexpr int kOz5HalfRows = kOzNS * kOz5D;                     // 192 rows per half stack
+constexpr size_t kOz5Half = size_t(kOz5HalfRows) * kOz5R * 2;   // 24 KB
+constexpr size_t kOz5Mat = 2 * kOz5Half;                        // 48 KB
+constexpr int kOz5TmemCols = 512;
+constexpr uint32_t kOz5HalfCol = 256;
+constexpr size_t kOff5A = 0;
+constexpr size_t kOff5Mat = kOff5A + kOz5ABuf;
+constexpr size_t kOff5Mu = kOff5Mat + kOz5Mat;
+constexpr size_t kOff5NuPart = kOff5Mu + kOz5R * 4;
+constexpr size_t kOz5Smem = kOff5NuPart + size_t(kOz5TPG) * kOzTG * 4;
+static_assert(kOzND * kOz5D <= int(kOz5HalfCol), "a half's accumulators fit its TMEM columns");
+
+struct Oz5Params {
+    IndexPlan ip;            // 5 targets (and controls) inserted
+    uint64_t offs[kOz5D];    // s(w), targets ascending
+    uint64_t n_groups;
+};
+
+__device__ __forceinline__ uint32_t kmaj5(uint32_t r, uint32_t k) {
+    return (r >> 3) * kOz5Sbo + (k >> 3) * kOzLbo + (r & 7) * 16 + (k & 7) * 2;
+}
+__device__ __forceinline__ uint64_t sdesc5(uint32_t saddr) {
+    uint64_t d = uint64_t((saddr >> 4) & 0x3FFF);
+    d |= uint64_t((kOzLbo >> 4) & 0x3FFF) << 16;
+    d |= uint64_t((kOz5Sbo >> 4) & 0x3FFF) << 32;
+    d |= uint64_t(1) << 46;
+    return d;
+}
+
+__global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict__ psi,
+                                                               const unsigned char* __restrict__ dmat,
+                                                               const __grid_constant__ Oz5Params P, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // thread (g, q): group g of the tile (= TMEM lane); amplitudes 4q..4q+3 (half 0) and
+    // 16+4q..16+4q+3 (half 1), held as v[0..3] and v[4..7]
+    const int g = tid & (kOzTG - 1), q = tid >> 7;
+    const float* mu = reinterpret_cast<const float*>(smem + kOff5Mu);
+    float* nu_part = reinterpret_cast<float*>(smem + kOff5NuPart);
+    unsigned char* ab = smem + kOff5A;
+
+    for (int i = tid; i < int((kOz5Mat + kOz5R * 4) / 16); i += kOz5Threads)
+        reinterpret_cast<uint4*>(smem + kOff5Mat)[i] = reinterpret_cast<const uint4*>(dmat)[i];
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        s_fail = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(kOz5TmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
+    const uint64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    uint64_t off[kOz5Amps];
+#pragma unroll
+    for (int i = 0; i < kOz5Amps; i++) off[i] = P.offs[(i >> 2) * (kOz5D / 2) + 4 * q + (i & 3)];
+
+    auto group_x0 = [&](uint64_t j) {
+        const uint64_t gi = (blockIdx.x + j * gridDim.x) * kOzTG + uint64_t(g);
+        return gi < P.n_groups ? expand(gi, P.ip) : ~0ull;
+    };
+    auto load = [&](uint64_t x0, float4 (&v)[kOz5Amps]) {
+#pragma unroll
+        for (int i = 0; i < kOz5Amps; i++)
+            v[i] = x0 != ~0ull ? psi[x0 + off[i]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    auto slice = [&](const float4 (&v)[kOz5Amps]) {
+        float m = 0.f;
+#pragma unroll
+        for (int i = 0; i < kOz5Amps; i++) m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].z)));
+        nu_part[q * kOzTG + g] = m;
+        __syncthreads();
+        m = nu_part[g];
+#pragma unroll
+        for (int t = 1; t < kOz5TPG; t++) m = fmaxf(m, nu_part[t * kOzTG + g]);
+        const float nv = pow2_ceil(m);
+        const float inv = __uint_as_float((254u - (__float_as_uint(nv) >> 23)) << 23);
+#pragma unroll
+        for (int c = 0; c < 2; c++) {  // 4 amplitudes = K columns 32c + 8q .. +7: one 16-byte chunk per slice
+            uint32_t pk[kOzNS][4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                float ar[kOzNS], ai[kOzNS];
+                slice6(v[4 * c + i].x, v[4 * c + i].y, inv, ar);
+                slice6(v[4 * c + i].z, v[4 * c + i].w, inv, ai);
+#pragma unroll
+                for (int s2 = 0; s2 < kOzNS; s2++) pk[s2][i] = pack_bf16(ar[s2], ai[s2]);
+            }
+            const uint32_t o = kmaj5(uint32_t(g), uint32_t(32 * c + 8 * q));
+#pragma unroll
+            for (int s2 = 0; s2 < kOzNS; s2++)
+                *reinterpret_cast<uint4*>(ab + s2 * kOz5Slice + o) = make_uint4(pk[s2][0], pk[s2][1], pk[s2][2], pk[s2][3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        return nv;
+    };
+    auto issue = [&]() {  // MMAs of the tile in the slice buffer: half 0, commit, half 1, commit
+        if (tid != 0) return;
+        const uint32_t a0 = smem_u32(ab), m0 = smem_u32(smem + kOff5Mat);
+#pragma unroll
+        for (int hv = 0; hv < 2; hv++) {
+            auto prod = [&](int s2, int t0, int nt, int ks, uint32_t acc) {
+                mma_bf16(tmem + kOz5HalfCol * uint32_t(hv) + uint32_t((s2 + t0) * kOz5D),
+                         sdesc5(a0 + uint32_t(s2 * kOz5Slice) + uint32_t(ks * 256)),
+                         sdesc5(m0 + uint32_t(hv * kOz5Half) + uint32_t(t0 * kOz5D / 8) * kOz5Sbo + uint32_t(ks * 256)),
+                         idesc(uint32_t(nt * kOz5D)), acc);
+            };
+#pragma unroll
+            for (int ks = 0; ks < kOz5R / 16; ks++) {
+                if (ks == 0) {
+                    prod(1, 0, kOzNS, 0, 0u);
+                    prod(0, 0, 1, 0, 0u);
+                    prod(0, 1, kOzNS - 1, 0, 1u);
+                } else {
+                    prod(0, 0, kOzNS, ks, 1u);
+                    prod(1, 0, kOzNS, ks, 1u);
+                }
+#pragma unroll
+                for (int s2 = 2; s2 < kOzNS; s2++) prod(s2, 0, kOzND - s2 < kOzNS ? kOzND - s2 : kOzNS, ks, 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&mbar[hv])));
+        }
+    };
+    // half hv's accumulators -> double-float outputs of this thread's 4 amplitudes of that half
+    auto epilogue = [&](int hv, uint64_t x0, float nv) {
+        const uint32_t lane_base = tmem + (uint32_t((warp & 3) * 32) << 16) + kOz5HalfCol * uint32_t(hv) + uint32_t(8 * q);
+#pragma unroll
+        for (int c = 0; c < 2; c++) {  // 4 output reals = 2 amplitudes per step
+            uint32_t r[kOzND][4];
+#pragma unroll
+            for (int d = 0; d < kOzND; d++)
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                             : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3])
+                             : "r"(lane_base + uint32_t(d * kOz5D + 4 * c)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                float o[4];
+#pragma unroll
+                for (int cc = 0; cc < 2; cc++) {
+                    const int col = 2 * i + cc;
+                    float sm = __fadd_rn(__fadd_rn(__uint_as_float(r[6][col]), __uint_as_float(r[5][col])),
+                                         __uint_as_float(r[4][col]));
+                    float lo = 0.f, t;
+#pragma unroll
+                    for (int d = 3; d >= 0; d--) {
+                        fast_two_sum(__uint_as_float(r[d][col]), sm, sm, t);
+                        lo = __fadd_rn(lo, t);
+                    }
+                    const float sc = __fmul_rn(mu[kOz5D * hv + 8 * q + 4 * c + col], nv);
+                    fast_two_sum(__fmul_rn(sm, sc), __fmul_rn(lo, sc), o[2 * cc], o[2 * cc + 1]);
+                }
+                if (x0 != ~0ull) psi[x0 + off[4 * hv + 2 * c + i]] = make_float4(o[0], o[1], o[2], o[3]);
+            }
+        }
+    };
+
+    // per tile j: loads of tile j + 1; fold half 0 of tile j - 1 (its half 1 MMAs may still
+    // run), then half 1; slice tile j into the (now free) buffer; start the MMAs of tile j
+    float4 vcur[kOz5Amps], vnext[kOz5Amps];
+    uint64_t x0_cur = 0, x0_prev = 0;
+    float nv_prev = 1.f;
+    if (my_tiles > 0) {
+        x0_cur = group_x0(0);
+        load(x0_cur, vcur);
+    }
+    for (uint64_t j = 0; j <= my_tiles && my_tiles > 0; j++) {
+        uint64_t x0_next = 0;
+        if (j + 1 < my_tiles) {
+            x0_next = group_x0(j + 1);
+            load(x0_next, vnext);
+        }
+        if (j >= 1) {
+            bool failed = false;
+#pragma unroll
+            for (int hv = 0; hv < 2; hv++) {
+                if (tid == 0 && !mbar_wait(smem_u32(&mbar[hv]), uint32_t((j - 1) & 1))) s_fail = 1;
+                __syncthreads();
+                if (s_fail) {
+                    failed = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                epilogue(hv, x0_prev, nv_prev);
+            }
+            if (failed) break;
+        }
+        float nv_cur = 1.f;
+        if (j < my_tiles) nv_cur = slice(vcur);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // slices of tile j written; accumulators of tile j - 1 read
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (j < my_tiles) issue();
+        x0_prev = x0_cur;
+        nv_prev = nv_cur;
+        x0_cur = x0_next;
+#pragma unroll
+        for (int i = 0; i < kOz5Amps; i++) vcur[i] = vnext[i];
+    }
+    if (s_fail && tid == 0) {
+        atomicExch(err, 1);
+        // bounded: let the MMAs in flight finish before TMEM is freed
+        mbar_wait(smem_u32(&mbar[0]), 0);
+        mbar_wait(smem_u32(&mbar[0]), 1);
+        mbar_wait(smem_u32(&mbar[1]), 0);
+        mbar_wait(smem_u32(&mbar[1]), 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kOz5TmemCols));
+}
+
 int g_oz_sms = 0;
 int* g_oz_err = nullptr;
 
@@ -422,6 +662,87 @@ void launch_dense_oz4(void* psi, int n, const std::vector<int>& targets, const s
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, 2 * uint64_t(g_oz_sms))));
     k_dense_oz4<<<grid, kOzThreads, kOzSmem, st>>>(reinterpret_cast<float4*>(psi),
                                                    static_cast<const unsigned char*>(dmat), P, g_oz_err);
+    QS_TRY_CUDA(cudaGetLastError());
+}
+
+size_t oz5_matrix_bytes() { return kOz5Mat + kOz5R * 4; }
+
+// Two stacked half matrices (output reals 0..31 and 32..63), each [B_0; ...; B_5] of the scaled
+// real form's rows in that half (192 x 64 bf16, K-major core-matrix layout), then the 64 row
+// scales.
+void prepare_oz5_matrix(const std::vector<cplx>& K, unsigned char* host_out) {
+    QS_REQUIRE(K.size() == size_t(kOz5D) * kOz5D, "5-target tensor-core path takes 32 x 32 matrices");
+    std::memset(host_out, 0, oz5_matrix_bytes());
+    float* mu = reinterpret_cast<float*>(host_out + kOz5Mat);
+    double magic[kOzNS];
+    for (int t = 0; t < kOzNS; t++) magic[t] = 1.5 * std::ldexp(1.0, 52 - 8 * (t + 1));
+    auto rf = [&](int n, int k) {
+        const cplx e = K[size_t(n >> 1) * kOz5D + size_t(k >> 1)];
+        if ((n & 1) == 0) return (k & 1) == 0 ? e.real() : -e.imag();
+        return (k & 1) == 0 ? e.imag() : e.real();
+    };
+    for (int n = 0; n < kOz5R; n++) {
+        double m = 0.0;
+        for (int k = 0; k < kOz5R; k++) m = std::max(m, std::fabs(rf(n, k)));
+        double scale = 1.0;
+        if (m > 0.0) {
+            int e = 0;
+            const double f = std::frexp(m, &e);
+            scale = f == 0.5 ? m : std::ldexp(1.0, e);
+        }
+        mu[n] = float(scale);
+        const int hv = n / kOz5D, nl = n % kOz5D;
+        for (int k = 0; k < kOz5R; k++) {
+            double r = rf(n, k) / scale;
+            for (int t = 0; t < kOzNS; t++) {
+                const double a = (r + magic[t]) - magic[t];
+                r -= a;
+                const int row = t * kOz5D + nl;
+                const size_t off = size_t(hv) * kOz5Half + size_t(row >> 3) * kOz5Sbo + size_t(k >> 3) * kOzLbo +
+                                   size_t(row & 7) * 16 + size_t(k & 7) * 2;
+                const uint16_t bits = bf16_bits_exact(a);
+                std::memcpy(host_out + off, &bits, 2);
+            }
+        }
+    }
+}
+
+void launch_dense_oz5(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
+                      const std::vector<int>& cvals, const void* dmat, cudaStream_t st) {
+    QS_REQUIRE(targets.size() == size_t(kOz5Q), "5-target tensor-core path takes 5 targets");
+    QS_REQUIRE(std::is_sorted(targets.begin(), targets.end()), "targets must be ascending");
+    static bool attr = false;
+    if (!g_oz_sms) {
+        int dev = 0;
+        QS_TRY_CUDA(cudaGetDevice(&dev));
+        QS_TRY_CUDA(cudaDeviceGetAttribute(&g_oz_sms, cudaDevAttrMultiProcessorCount, dev));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
+        QS_TRY_CUDA(cudaMalloc(&g_oz_err, sizeof(int)));
+        QS_TRY_CUDA(cudaMemset(g_oz_err, 0, sizeof(int)));
+    }
+    if (!attr) {
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz5, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOz5Smem)));
+        attr = true;
+    }
+    std::vector<int> fixed(targets);
+    uint64_t setmask = 0;
+    for (size_t i = 0; i < controls.size(); i++) {
+        fixed.push_back(controls[i]);
+        if (cvals[i]) setmask |= 1ull << controls[i];
+    }
+    Oz5Params P;
+    P.ip = make_index_plan(n, fixed, setmask);
+    P.n_groups = P.ip.n_iter;
+    for (int w = 0; w < kOz5D; w++) {
+        uint64_t o = 0;
+        for (int j = 0; j < kOz5Q; j++)
+            if ((w >> j) & 1) o |= 1ull << targets[j];
+        P.offs[w] = o;
+    }
+    const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
+    const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, uint64_t(g_oz_sms))));
+    k_dense_oz5<<<grid, kOz5Threads, kOz5Smem, st>>>(reinterpret_cast<float4*>(psi),
+                                                     static_cast<const unsigned char*>(dmat), P, g_oz_err);
     QS_TRY_CUDA(cudaGetLastError());
 }
 

@@ -140,3 +140,93 @@ def test_oz_full_size_sampled(oz):
     st.close()
     del st
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n", [5, 6, 11, 12, 13, 16])
+def test_oz5_single_gate_placements(oz, n):
+    """One 5-target dense gate (random, non-unitary) on low, high, mixed and unsorted targets:
+    n = 5 is a single group, n = 12 exactly one 128-group tile, 13 and 16 several tiles; both
+    output halves and all four threads of a group are exercised."""
+    qs = oz
+    rng = W.SplitMix64(200 + n)
+    psi0 = W.random_state(n, 3 * n + 1)
+    placements = [(0, 1, 2, 3, 4), tuple(range(n - 1, n - 6, -1)), (0, 2, n - 1, 1, n - 2), (4, 0, n - 3, 1, 2)]
+    for t in placements:
+        if len(set(t)) < 5 or max(t) >= n:
+            continue
+        K = W.random_complex_matrix(32, rng)
+        g = W.Gate("DENSE", t, matrix=K)
+        ref = psi0.copy()
+        oracle.apply_gate(ref, n, g)
+        got = run_one(qs, n, g, psi0)
+        assert maxabs(got, ref) < 1e-12 * max(1.0, float(np.max(np.abs(ref)))), t
+
+
+def test_oz5_controlled_and_scaled(oz):
+    """A controlled 5-target unitary, and a large non-unitary matrix on a state with tiny and
+    zero groups (errors relative to each group's scale)."""
+    qs = oz
+    n = 13
+    rng = W.SplitMix64(77)
+    psi0 = W.random_state(n, 12)
+    g = W.Gate("DENSE", (1, 2, 3, 5, 9), controls=(0,), control_values=(1,), matrix=W.random_unitary(32, rng))
+    ref = psi0.copy()
+    oracle.apply_gate(ref, n, g)
+    assert maxabs(run_one(qs, n, g, psi0), ref) < 1e-12
+    psi1 = psi0.copy()
+    psi1[: 1 << 9] *= 1e-6
+    psi1[1 << 11: 1 << 12] = 0.0
+    K = W.random_complex_matrix(32, rng) * 6.0
+    g = W.Gate("DENSE", (4, 5, 6, 7, 8), matrix=K)   # every group below 2^9 is entirely tiny
+    ref = psi1.copy()
+    oracle.apply_gate(ref, n, g)
+    got = run_one(qs, n, g, psi1)
+    err = np.abs(got - ref)
+    assert float(np.max(err)) < 1e-12 * 8
+    assert float(np.max(err[: 1 << 9])) < 1e-17
+
+
+@pytest.mark.parametrize("n", [12, 16, 20])
+def test_oz5_fused_circuits(oz, n):
+    qs = oz
+    c = W.u3cz_circuit(n, 20 if n < 20 else 10, 60 + n)
+    ref = oracle.run_circuit(c)
+    st = qs.State(n, qs.QS_C128)
+    st.run(c, 5)
+    assert maxabs(st.get_vector(), ref) < 1e-12
+    assert abs(st.norm2() - 1.0) < 1e-12
+
+
+def test_oz5_matches_cuda_core_path(oz):
+    qs = oz
+    n = 17
+    c = W.Circuit(n, W.random_gate_suite(n, 31))
+    plan = qs.FusedCircuit(c, 5)
+    a = qs.State(n, qs.QS_C128)
+    a.apply_plan(plan)
+    qs.set_tensor_cores(0)
+    b = qs.State(n, qs.QS_C128)
+    b.apply_plan(plan)
+    qs.set_tensor_cores(qs.QS_TENSOR_C128)
+    assert maxabs(a.get_vector(), b.get_vector()) < 1e-12
+
+
+def test_oz5_full_size_sampled(oz):
+    import torch
+    from test_gpu_parity import product_then_cz, sampled_amplitudes
+    qs = oz
+    n = 30
+    circ, u3, cz = product_then_cz(n, 20, 779)
+    st = qs.State(n, qs.QS_C128)
+    st.apply_plan(qs.FusedCircuit(circ, 5))
+    st.synchronize()
+    rng = W.SplitMix64(9)
+    xs = [rng.next_u64() & ((1 << n) - 1) for _ in range(2000)] + [0, (1 << n) - 1]
+    ref = sampled_amplitudes(n, u3, cz, xs)
+    idx = torch.tensor(xs, dtype=torch.int64, device="cuda")
+    got = st.tensor[idx].cpu().numpy()
+    assert maxabs(got, ref) < 1e-12
+    assert abs(st.norm2() - 1.0) < 1e-11
+    st.close()
+    del st
+    torch.cuda.empty_cache()
