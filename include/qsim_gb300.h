@@ -234,8 +234,9 @@ qs_status qs_destroy_fused(qs_fused_circuit* f);
 #define QS_KERNEL_SWAP 5       /* SWAP / controlled SWAP */
 #define QS_KERNEL_DENSE_DF 6   /* complex128 dense gate matrix in double-float arithmetic */
 #define QS_KERNEL_DENSE_TC 7   /* complex64 dense block of 5-6 targets on the tensor cores (3xTF32) */
-#define QS_KERNEL_DENSE_OZ 8   /* double-float complex128 block of 4 or 5 targets on the tensor cores (bf16 slices) */
+#define QS_KERNEL_DENSE_OZ 8   /* double-float complex128 block of 4 targets on the tensor cores (bf16 slices) */
 #define QS_KERNEL_PAULI_ROT 9  /* Pauli rotation exp(i phi P / 2), one pass over amplitude pairs */
+#define QS_KERNEL_DENSE_OZ5 10 /* double-float complex128 block of 5 targets on the tensor cores (bf16 slices) */
 qs_status qs_fused_block_cost(const qs_fused_circuit* f, int b, qs_dtype dt, int* kernel, int* launches,
                               double* bytes);
 /* Applies a plan like qs_apply_fused_circuit, recording a CUDA event on the state's stream

@@ -139,7 +139,7 @@ void op_cost(const Op& op, int n, qs_dtype dt, int* kernel, int* launches, doubl
             if (dt == QS_C64 && m >= 5 && tensor_c64_enabled()) k = QS_KERNEL_DENSE_TC;
             if (dt == QS_C128 && c128_math() == QS_MATH_DF && m <= 3) k = QS_KERNEL_DENSE_DF;
             if (dt == QS_C128 && c128_math() == QS_MATH_DF && (m == 4 || m == 5) && tensor_c128_enabled())
-                k = QS_KERNEL_DENSE_OZ;
+                k = m == 4 ? QS_KERNEL_DENSE_OZ : QS_KERNEL_DENSE_OZ5;
             break;
         }
         case OpKind::Diag: k = QS_KERNEL_DIAG; break;
