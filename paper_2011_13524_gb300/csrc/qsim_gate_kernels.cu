@@ -290,8 +290,7 @@ __global__ void k_from_df(double2* __restrict__ psi, uint64_t N) {
 #pragma unroll
         for (int u = 0; u < kConvUnroll; u++) {
             if (i0 + u * stride >= N) continue;
-            psi[i0 + u * stride] = make_double2(widen_float_int(v[u].x) + widen_float_int(v[u].y),
-                                                widen_float_int(v[u].z) + widen_float_int(v[u].w));
+            psi[i0 + u * stride] = make_double2(join_df_int(v[u].x, v[u].y), join_df_int(v[u].z, v[u].w));
         }
     }
 }

@@ -181,3 +181,28 @@ def test_df_layout_round_trip_wide_range(df):
     rel = np.abs(got[normal] - psi0[normal]) / np.abs(psi0[normal])
     assert float(np.max(rel)) < 2.0 ** -47
     assert float(np.max(np.abs(got[small] - psi0[small]))) < 1e-37
+
+
+def test_df_layout_round_trip_bit_exact(df):
+    """In place to double-float and back: every amplitude in FP32's normal range comes back as
+    exactly RN(hi + lo) with hi = RN_float(x), lo = RN_float(x - hi) (numpy's float32 rounding and
+    FP64 sum), whichever path (integer pipes or the FP64 add) the join takes."""
+    qs = df
+    n = 13
+    rng = np.random.default_rng(1313)
+    N = 1 << n
+    mags = 10.0 ** rng.uniform(-25, 25, 2 * N)
+    vals = rng.choice([-1.0, 1.0], 2 * N) * mags
+    vals[::37] *= (1 - 2.0 ** -30)   # significands with long runs of ones
+    vals[5::41] = np.ldexp(1.0, rng.integers(-60, 60, len(vals[5::41])))  # powers of two
+    psi0 = vals[0::2] + 1j * vals[1::2]
+    st = qs.State(n, qs.QS_C128)
+    st.load(psi0)
+    st.run(W.Circuit(n, []), 0)
+    got = st.get_vector()
+    re = np.ascontiguousarray(psi0).view(np.float64)
+    hi = re.astype(np.float32)
+    lo = (re - hi.astype(np.float64)).astype(np.float32)
+    want = hi.astype(np.float64) + lo.astype(np.float64)
+    assert np.array_equal(np.ascontiguousarray(got).view(np.float64).view(np.uint64), want.view(np.uint64))
+    st.close()
