@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--fusion", type=int, default=-1, help="-1 autotune, 0 gate by gate, 1..6 width")
     p.add_argument("--math", default="auto", choices=["auto", "fp64", "df"])
     p.add_argument("--tensor", type=int, default=-1,
-                   help="tensor-core path mask (1 complex64, 2 complex128 double-float); -1 = library default")
+                   help="tensor-core path mask (1 complex64 TF32, 2 complex128 double-float, 4 complex64 bf16 slices); -1 = library default")
     p.add_argument("--extras", type=int, default=1, help="also measure unfused, c64, adjoint (rank 0)")
     p.add_argument("--cpu-sample-gates", type=int, default=9)
     p.add_argument("--only", default="", choices=["", "batch"],

@@ -21,11 +21,12 @@ namespace qs {
 namespace {
 thread_local std::string g_err;
 std::atomic<int> g_c128_math{QS_MATH_FP64};
-std::atomic<int> g_tensor{QS_TENSOR_C128};  // QS_TENSOR_* bits
+std::atomic<int> g_tensor{QS_TENSOR_C128 | QS_TENSOR_C64X};  // QS_TENSOR_* bits
 }  // namespace
 
 bool tensor_c64_enabled() { return (g_tensor.load() & QS_TENSOR_C64) != 0; }
 bool tensor_c128_enabled() { return (g_tensor.load() & QS_TENSOR_C128) != 0; }
+bool tensor_c64x_enabled() { return (g_tensor.load() & QS_TENSOR_C64X) != 0; }
 
 void set_error(const std::string& msg) { g_err = msg; }
 void clear_error() { g_err.clear(); }
@@ -137,6 +138,7 @@ void op_cost(const Op& op, int n, qs_dtype dt, int* kernel, int* launches, doubl
             const bool reg = m <= 3 || (m == 4 && dt == QS_C64);
             k = reg ? QS_KERNEL_DENSE_REG : QS_KERNEL_DENSE_SMEM;
             if (dt == QS_C64 && m >= 5 && tensor_c64_enabled()) k = QS_KERNEL_DENSE_TC;
+            if (dt == QS_C64 && m == 5 && tensor_c64x_enabled()) k = QS_KERNEL_DENSE_BZ5;
             if (dt == QS_C128 && c128_math() == QS_MATH_DF && m <= 3) k = QS_KERNEL_DENSE_DF;
             if (dt == QS_C128 && c128_math() == QS_MATH_DF && (m == 4 || m == 5) && tensor_c128_enabled())
                 k = m == 4 ? QS_KERNEL_DENSE_OZ : QS_KERNEL_DENSE_OZ5;
@@ -176,7 +178,10 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
     std::vector<char> tc(ops.size(), 0), oz(ops.size(), 0);
     for (size_t b = 0; b < ops.size(); b++) {
         if (ops[b].kind != OpKind::Dense || ops[b].targets.size() < 4) continue;
-        if (ar == Arith::F32 && ops[b].targets.size() >= 5 && tensor_c64_enabled()) {
+        if (ar == Arith::F32 && ops[b].targets.size() == 5 && tensor_c64x_enabled()) {
+            ops[b] = sort_targets(ops[b]);
+            oz[b] = 6;  // the complex64 5-target form
+        } else if (ar == Arith::F32 && ops[b].targets.size() >= 5 && tensor_c64_enabled()) {
             ops[b] = pad_dense_to6(ops[b], s->n);
             tc[b] = 1;
         }
@@ -188,6 +193,7 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
         total += tc[b]         ? tc6_matrix_bytes()
                  : oz[b] == 4 ? oz4_matrix_bytes()
                  : oz[b] == 5 ? oz5_matrix_bytes()
+                 : oz[b] == 6 ? bz5_matrix_bytes()
                               : ops[b].data.size() * kernel_entry_bytes(ar);
         total = (total + 255) & ~size_t(255);
     }
@@ -201,6 +207,8 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
             prepare_oz4_matrix(ops[b].data, host.data() + offs[b]);
         else if (oz[b] == 5)
             prepare_oz5_matrix(ops[b].data, host.data() + offs[b]);
+        else if (oz[b] == 6)
+            prepare_bz5_matrix(ops[b].data, host.data() + offs[b]);
         else
             encode_entries(ar, ops[b].data, host.data() + offs[b]);
     }
@@ -344,7 +352,8 @@ double predicted_seconds(const Op& op, int n, qs_dtype dt) {
     int dev = 0;
     cudaGetDevice(&dev);
     const int width = op.kind == OpKind::Dense || op.kind == OpKind::Diag ? int(op.targets.size()) : 0;
-    auto key = std::make_tuple(dev, int(dt), dt == QS_C128 ? c128_math() : (tensor_c64_enabled() ? 1 : 0), kernel, width);
+    auto key = std::make_tuple(dev, int(dt), dt == QS_C128 ? c128_math() : g_tensor.load() & (QS_TENSOR_C64 | QS_TENSOR_C64X),
+                               kernel, width);
     // (the kernel id already tells the tensor-core forms apart)
     double per_byte;
     {
@@ -427,7 +436,7 @@ qs_status qs_set_c128_math(int mode) {
 
 qs_status qs_set_tensor_cores(int mask) {
     API_BEGIN
-    QS_REQUIRE((mask & ~(QS_TENSOR_C64 | QS_TENSOR_C128)) == 0, "unknown tensor-core path bits");
+    QS_REQUIRE((mask & ~(QS_TENSOR_C64 | QS_TENSOR_C128 | QS_TENSOR_C64X)) == 0, "unknown tensor-core path bits");
     g_tensor.store(mask);
     API_END
 }

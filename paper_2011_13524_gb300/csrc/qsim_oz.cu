@@ -575,6 +575,187 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kOz5TmemCols));
 }
 
+// ---------------------------------------------------------------- complex64, 5-target blocks
+// The same splitting for complex64 states (float2): the group vector (scaled by its power of two
+// nu) and the matrix rows (scaled by mu_n) are cut into three 8-bit slices on the grids 2^-8,
+// 2^-16, 2^-24, which hold every bit of an FP32 value down to 2^-24 of the group's scale; the six
+// products with s + t <= 2 are summed exactly in FP32 by the tensor cores into three diagonals
+// (3 x 64 TMEM columns), and the epilogue adds them in FP32 from the smallest (one rounding to
+// nearest, no bias) and scales by mu_n nu. Error about 2^-24 of max|v| max|K~| per output, the
+// accuracy of the FP32 CUDA-core kernels. Tile: 128 groups of 32 amplitudes; 256 threads
+// (thread (g, h) owns amplitudes 16h .. 16h + 15 of group g), one slice buffer (48 KB), two CTAs
+// per SM so that one CTA's MMAs overlap the other's slicing and folding.
+constexpr int kBzNS = 3;                                        // slices per operand
+constexpr int kBzND = 3;                                        // diagonals s + t <= 2
+constexpr int kBzThreads = 256;
+constexpr int kBzAmps = kOz5D / (kBzThreads / kOzTG);           // 16 amplitudes per thread
+constexpr size_t kBzSlice = size_t(kOzTG) * kOz5R * 2;          // 16 KB
+constexpr size_t kBzABuf = kBzNS * kBzSlice;                    // 48 KB
+constexpr size_t kBzMat = size_t(kBzNS) * kOz5R * kOz5R * 2;    // 24 KB: [B_0; B_1; B_2] 192 x 64
+constexpr int kBzTmemCols = 256;
+constexpr size_t kOffBzA = 0;
+constexpr size_t kOffBzMat = kOffBzA + kBzABuf;
+constexpr size_t kOffBzMu = kOffBzMat + kBzMat;
+constexpr size_t kOffBzNuPart = kOffBzMu + kOz5R * 4;
+constexpr size_t kBzSmem = kOffBzNuPart + 2 * kOzTG * 4;
+static_assert(kBzND * kOz5R <= kBzTmemCols, "accumulators fit the TMEM allocation");
+
+// the three slices of x * inv (|x * inv| <= 1): multiples of 2^-8, 2^-16, 2^-24
+__device__ __forceinline__ void slice3(float x, float inv, float (&a)[kBzNS]) {
+    x = __fmul_rn(x, inv);
+    a[0] = grid_round<0>(x);
+    const float r = __fsub_rn(x, a[0]);
+    a[1] = grid_round<1>(r);
+    a[2] = grid_round<2>(__fsub_rn(r, a[1]));
+}
+
+__global__ void __launch_bounds__(kBzThreads, 2) k_dense_bz5(float2* __restrict__ psi, const unsigned char* __restrict__ dmat,
+                                                             const __grid_constant__ Oz5Params P, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int g = tid & (kOzTG - 1), h = tid >> 7;
+    const float* mu = reinterpret_cast<const float*>(smem + kOffBzMu);
+    float* nu_part = reinterpret_cast<float*>(smem + kOffBzNuPart);
+    unsigned char* ab = smem + kOffBzA;
+
+    for (int i = tid; i < int((kBzMat + kOz5R * 4) / 16); i += kBzThreads)
+        reinterpret_cast<uint4*>(smem + kOffBzMat)[i] = reinterpret_cast<const uint4*>(dmat)[i];
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        s_fail = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(kBzTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
+    const uint64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+
+    auto group_x0 = [&](uint64_t j) {
+        const uint64_t gi = (blockIdx.x + j * gridDim.x) * kOzTG + uint64_t(g);
+        return gi < P.n_groups ? expand(gi, P.ip) : ~0ull;
+    };
+    auto load = [&](uint64_t x0, float2 (&v)[kBzAmps]) {
+#pragma unroll
+        for (int i = 0; i < kBzAmps; i++)
+            v[i] = x0 != ~0ull ? psi[x0 + P.offs[kBzAmps * h + i]] : make_float2(0.f, 0.f);
+    };
+    auto slice = [&](const float2 (&v)[kBzAmps]) {
+        float m = 0.f;
+#pragma unroll
+        for (int i = 0; i < kBzAmps; i++) m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
+        nu_part[h * kOzTG + g] = m;
+        __syncthreads();
+        m = fmaxf(nu_part[g], nu_part[kOzTG + g]);
+        const float nv = pow2_ceil(m);
+        const float inv = __uint_as_float((254u - (__float_as_uint(nv) >> 23)) << 23);
+#pragma unroll
+        for (int c = 0; c < kBzAmps / 4; c++) {  // 4 amplitudes = K columns 32h + 8c .. +7
+            uint32_t pk[kBzNS][4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                float ar[kBzNS], ai[kBzNS];
+                slice3(v[4 * c + i].x, inv, ar);
+                slice3(v[4 * c + i].y, inv, ai);
+#pragma unroll
+                for (int s2 = 0; s2 < kBzNS; s2++) pk[s2][i] = pack_bf16(ar[s2], ai[s2]);
+            }
+            const uint32_t o = kmaj5(uint32_t(g), uint32_t(32 * h + 8 * c));
+#pragma unroll
+            for (int s2 = 0; s2 < kBzNS; s2++)
+                *reinterpret_cast<uint4*>(ab + s2 * kBzSlice + o) = make_uint4(pk[s2][0], pk[s2][1], pk[s2][2], pk[s2][3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        return nv;
+    };
+    auto issue = [&]() {  // state slice s times matrix slices 0 .. 2 - s into diagonals s .. 2
+        if (tid != 0) return;
+        const uint32_t a0 = smem_u32(ab), m0 = smem_u32(smem + kOffBzMat);
+#pragma unroll
+        for (int ks = 0; ks < kOz5R / 16; ks++)
+#pragma unroll
+            for (int s2 = 0; s2 < kBzNS; s2++)
+                mma_bf16(tmem + uint32_t(s2 * kOz5R), sdesc5(a0 + uint32_t(s2 * kBzSlice) + uint32_t(ks * 256)),
+                         sdesc5(m0 + uint32_t(ks * 256)), idesc(uint32_t((kBzND - s2) * kOz5R)),
+                         (ks == 0 && s2 == 0) ? 0u : 1u);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar)));
+    };
+    auto epilogue = [&](uint64_t x0, float nv) {
+        const uint32_t lane_base = tmem + (uint32_t((warp & 3) * 32) << 16) + uint32_t(32 * h);
+#pragma unroll
+        for (int c = 0; c < kBzAmps / 2; c++) {  // 4 output reals = 2 amplitudes per step
+            uint32_t r[kBzND][4];
+#pragma unroll
+            for (int d = 0; d < kBzND; d++)
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                             : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3])
+                             : "r"(lane_base + uint32_t(d * kOz5R + 4 * c)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                float o[2];
+#pragma unroll
+                for (int cc = 0; cc < 2; cc++) {
+                    const int col = 2 * i + cc;
+                    const float sm = __fadd_rn(__fadd_rn(__uint_as_float(r[2][col]), __uint_as_float(r[1][col])),
+                                               __uint_as_float(r[0][col]));
+                    o[cc] = __fmul_rn(sm, __fmul_rn(mu[32 * h + 4 * c + col], nv));
+                }
+                if (x0 != ~0ull) psi[x0 + P.offs[kBzAmps * h + 2 * c + i]] = make_float2(o[0], o[1]);
+            }
+        }
+    };
+
+    float2 vcur[kBzAmps], vnext[kBzAmps];
+    uint64_t x0_cur = 0, x0_prev = 0;
+    float nv_prev = 1.f;
+    if (my_tiles > 0) {
+        x0_cur = group_x0(0);
+        load(x0_cur, vcur);
+    }
+    for (uint64_t j = 0; j <= my_tiles && my_tiles > 0; j++) {
+        uint64_t x0_next = 0;
+        if (j + 1 < my_tiles) {
+            x0_next = group_x0(j + 1);
+            load(x0_next, vnext);
+        }
+        if (j >= 1) {
+            if (tid == 0 && !mbar_wait(smem_u32(&mbar), uint32_t((j - 1) & 1))) s_fail = 1;
+            __syncthreads();
+            if (s_fail) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            epilogue(x0_prev, nv_prev);
+        }
+        float nv_cur = 1.f;
+        if (j < my_tiles) nv_cur = slice(vcur);  // the buffer was read by the MMAs of tile j - 1 (done)
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // slices of tile j written; accumulators of tile j - 1 read
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (j < my_tiles) issue();
+        x0_prev = x0_cur;
+        nv_prev = nv_cur;
+        x0_cur = x0_next;
+#pragma unroll
+        for (int i = 0; i < kBzAmps; i++) vcur[i] = vnext[i];
+    }
+    if (s_fail && tid == 0) {
+        atomicExch(err, 1);
+        mbar_wait(smem_u32(&mbar), 0);  // bounded: let the MMAs in flight finish before TMEM is freed
+        mbar_wait(smem_u32(&mbar), 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBzTmemCols));
+}
+
 int g_oz_sms = 0;
 int* g_oz_err = nullptr;
 
@@ -743,6 +924,85 @@ void launch_dense_oz5(void* psi, int n, const std::vector<int>& targets, const s
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, uint64_t(g_oz_sms))));
     k_dense_oz5<<<grid, kOz5Threads, kOz5Smem, st>>>(reinterpret_cast<float4*>(psi),
                                                      static_cast<const unsigned char*>(dmat), P, g_oz_err);
+    QS_TRY_CUDA(cudaGetLastError());
+}
+
+size_t bz5_matrix_bytes() { return kBzMat + kOz5R * 4; }
+
+// [B_0; B_1; B_2] (192 x 64 bf16, K-major core-matrix layout) of the row-scaled real form, then
+// the 64 row scales.
+void prepare_bz5_matrix(const std::vector<cplx>& K, unsigned char* host_out) {
+    QS_REQUIRE(K.size() == size_t(kOz5D) * kOz5D, "5-target tensor-core path takes 32 x 32 matrices");
+    std::memset(host_out, 0, bz5_matrix_bytes());
+    float* mu = reinterpret_cast<float*>(host_out + kBzMat);
+    double magic[kBzNS];
+    for (int t = 0; t < kBzNS; t++) magic[t] = 1.5 * std::ldexp(1.0, 52 - 8 * (t + 1));
+    auto rf = [&](int n, int k) {
+        const cplx e = K[size_t(n >> 1) * kOz5D + size_t(k >> 1)];
+        if ((n & 1) == 0) return (k & 1) == 0 ? e.real() : -e.imag();
+        return (k & 1) == 0 ? e.imag() : e.real();
+    };
+    for (int n = 0; n < kOz5R; n++) {
+        double m = 0.0;
+        for (int k = 0; k < kOz5R; k++) m = std::max(m, std::fabs(rf(n, k)));
+        double scale = 1.0;
+        if (m > 0.0) {
+            int e = 0;
+            const double f = std::frexp(m, &e);
+            scale = f == 0.5 ? m : std::ldexp(1.0, e);
+        }
+        mu[n] = float(scale);
+        for (int k = 0; k < kOz5R; k++) {
+            double r = rf(n, k) / scale;
+            for (int t = 0; t < kBzNS; t++) {
+                const double a = (r + magic[t]) - magic[t];
+                r -= a;
+                const int row = t * kOz5R + n;
+                const size_t off = size_t(row >> 3) * kOz5Sbo + size_t(k >> 3) * kOzLbo + size_t(row & 7) * 16 +
+                                   size_t(k & 7) * 2;
+                const uint16_t bits = bf16_bits_exact(a);
+                std::memcpy(host_out + off, &bits, 2);
+            }
+        }
+    }
+}
+
+void launch_dense_bz5(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
+                      const std::vector<int>& cvals, const void* dmat, cudaStream_t st) {
+    QS_REQUIRE(targets.size() == size_t(kOz5Q), "5-target tensor-core path takes 5 targets");
+    QS_REQUIRE(std::is_sorted(targets.begin(), targets.end()), "targets must be ascending");
+    static bool attr = false;
+    if (!g_oz_sms) {
+        int dev = 0;
+        QS_TRY_CUDA(cudaGetDevice(&dev));
+        QS_TRY_CUDA(cudaDeviceGetAttribute(&g_oz_sms, cudaDevAttrMultiProcessorCount, dev));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
+        QS_TRY_CUDA(cudaMalloc(&g_oz_err, sizeof(int)));
+        QS_TRY_CUDA(cudaMemset(g_oz_err, 0, sizeof(int)));
+    }
+    if (!attr) {
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_bz5, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBzSmem)));
+        attr = true;
+    }
+    std::vector<int> fixed(targets);
+    uint64_t setmask = 0;
+    for (size_t i = 0; i < controls.size(); i++) {
+        fixed.push_back(controls[i]);
+        if (cvals[i]) setmask |= 1ull << controls[i];
+    }
+    Oz5Params P;
+    P.ip = make_index_plan(n, fixed, setmask);
+    P.n_groups = P.ip.n_iter;
+    for (int w = 0; w < kOz5D; w++) {
+        uint64_t o = 0;
+        for (int j = 0; j < kOz5Q; j++)
+            if ((w >> j) & 1) o |= 1ull << targets[j];
+        P.offs[w] = o;
+    }
+    const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
+    const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, 2 * uint64_t(g_oz_sms))));
+    k_dense_bz5<<<grid, kBzThreads, kBzSmem, st>>>(reinterpret_cast<float2*>(psi),
+                                                   static_cast<const unsigned char*>(dmat), P, g_oz_err);
     QS_TRY_CUDA(cudaGetLastError());
 }
 

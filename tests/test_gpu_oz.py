@@ -113,10 +113,11 @@ def test_oz_matches_cuda_core_path(oz):
     plan = qs.FusedCircuit(c, 4)
     a = qs.State(n, qs.QS_C128)
     a.apply_plan(plan)
+    mask = qs.get_tensor_cores()
     qs.set_tensor_cores(0)
     b = qs.State(n, qs.QS_C128)
     b.apply_plan(plan)
-    qs.set_tensor_cores(qs.QS_TENSOR_C128)
+    qs.set_tensor_cores(mask)
     assert maxabs(a.get_vector(), b.get_vector()) < 1e-12
 
 
@@ -204,10 +205,11 @@ def test_oz5_matches_cuda_core_path(oz):
     plan = qs.FusedCircuit(c, 5)
     a = qs.State(n, qs.QS_C128)
     a.apply_plan(plan)
+    mask = qs.get_tensor_cores()
     qs.set_tensor_cores(0)
     b = qs.State(n, qs.QS_C128)
     b.apply_plan(plan)
-    qs.set_tensor_cores(qs.QS_TENSOR_C128)
+    qs.set_tensor_cores(mask)
     assert maxabs(a.get_vector(), b.get_vector()) < 1e-12
 
 
