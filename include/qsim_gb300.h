@@ -154,11 +154,11 @@ qs_status qs_get_c128_math(int* mode);
  *   state slice s and matrix slice t with s + t <= 6 are summed exactly in FP32 by
  *   tcgen05.mma kind::f16 and combined exactly in double-float: about 2^-45 relative error per
  *   block, the accuracy of the double-float CUDA-core kernels.
- * QS_TENSOR_C64X: complex64 blocks of 5 targets: the matrix and every 32-amplitude group cut
- *   into three 8-bit bf16 slices; the 6 products with s + t <= 2 summed exactly in FP32 by
- *   tcgen05.mma kind::f16, added in FP32 with one rounding to nearest: about 2^-24 relative
- *   error per block and no drift, the accuracy of the FP32 CUDA-core kernels. Takes precedence
- *   over QS_TENSOR_C64 for 5-target blocks.
+ * QS_TENSOR_C64X: complex64 blocks of 5 or 6 targets: the matrix and every 32- or 64-amplitude
+ *   group cut into three 8-bit bf16 slices; the 6 products with s + t <= 2 summed exactly in
+ *   FP32 by tcgen05.mma kind::f16, added in FP32 with one rounding to nearest: about 2^-24
+ *   relative error per block and no drift, the accuracy of the FP32 CUDA-core kernels. Takes
+ *   precedence over QS_TENSOR_C64.
  * Unknown bits -> QS_ERR_INVALID_ARG. Default: QS_TENSOR_C128 | QS_TENSOR_C64X (their blocks
  * meet the complex128 and complex64 bounds; the TF32 path stays opt-in because of its norm
  * drift). */
@@ -244,7 +244,7 @@ qs_status qs_destroy_fused(qs_fused_circuit* f);
 #define QS_KERNEL_DENSE_OZ 8   /* double-float complex128 block of 4 targets on the tensor cores (bf16 slices) */
 #define QS_KERNEL_PAULI_ROT 9  /* Pauli rotation exp(i phi P / 2), one pass over amplitude pairs */
 #define QS_KERNEL_DENSE_OZ5 10 /* double-float complex128 block of 5 targets on the tensor cores (bf16 slices) */
-#define QS_KERNEL_DENSE_BZ5 11 /* complex64 block of 5 targets on the tensor cores (bf16 slices) */
+#define QS_KERNEL_DENSE_BZ 11  /* complex64 block of 5 or 6 targets on the tensor cores (bf16 slices) */
 qs_status qs_fused_block_cost(const qs_fused_circuit* f, int b, qs_dtype dt, int* kernel, int* launches,
                               double* bytes);
 /* Applies a plan like qs_apply_fused_circuit, recording a CUDA event on the state's stream

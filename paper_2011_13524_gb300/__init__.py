@@ -39,7 +39,7 @@ QS_MAX_CONTROLS = 8
 
 QS_GATE_DENSE, QS_GATE_DIAG, QS_GATE_PAULI, QS_GATE_NAMED = 0, 1, 2, 3
 KERNEL_NAMES = {0: "dense_reg", 1: "dense_smem", 2: "diag", 3: "phase", 4: "pauli", 5: "swap", 6: "dense_df",
-                7: "dense_tc", 8: "dense_oz", 9: "pauli_rot", 10: "dense_oz5", 11: "dense_bz5"}
+                7: "dense_tc", 8: "dense_oz", 9: "pauli_rot", 10: "dense_oz5", 11: "dense_bz"}
 NAMED = {
     "X": 1, "Y": 2, "Z": 3, "H": 4, "S": 5, "Sdag": 6, "T": 7, "Tdag": 8, "sqrtX": 9,
     "sqrtXdag": 10, "sqrtY": 11, "sqrtYdag": 12, "RX": 13, "RY": 14, "RZ": 15, "U1": 16,

@@ -138,7 +138,7 @@ void op_cost(const Op& op, int n, qs_dtype dt, int* kernel, int* launches, doubl
             const bool reg = m <= 3 || (m == 4 && dt == QS_C64);
             k = reg ? QS_KERNEL_DENSE_REG : QS_KERNEL_DENSE_SMEM;
             if (dt == QS_C64 && m >= 5 && tensor_c64_enabled()) k = QS_KERNEL_DENSE_TC;
-            if (dt == QS_C64 && m == 5 && tensor_c64x_enabled()) k = QS_KERNEL_DENSE_BZ5;
+            if (dt == QS_C64 && (m == 5 || m == 6) && tensor_c64x_enabled()) k = QS_KERNEL_DENSE_BZ;
             if (dt == QS_C128 && c128_math() == QS_MATH_DF && m <= 3) k = QS_KERNEL_DENSE_DF;
             if (dt == QS_C128 && c128_math() == QS_MATH_DF && (m == 4 || m == 5) && tensor_c128_enabled())
                 k = m == 4 ? QS_KERNEL_DENSE_OZ : QS_KERNEL_DENSE_OZ5;
@@ -178,9 +178,9 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
     std::vector<char> tc(ops.size(), 0), oz(ops.size(), 0);
     for (size_t b = 0; b < ops.size(); b++) {
         if (ops[b].kind != OpKind::Dense || ops[b].targets.size() < 4) continue;
-        if (ar == Arith::F32 && ops[b].targets.size() == 5 && tensor_c64x_enabled()) {
+        if (ar == Arith::F32 && (ops[b].targets.size() == 5 || ops[b].targets.size() == 6) && tensor_c64x_enabled()) {
             ops[b] = sort_targets(ops[b]);
-            oz[b] = 6;  // the complex64 5-target form
+            oz[b] = char(10 + ops[b].targets.size());  // the complex64 form, 15 or 16
         } else if (ar == Arith::F32 && ops[b].targets.size() >= 5 && tensor_c64_enabled()) {
             ops[b] = pad_dense_to6(ops[b], s->n);
             tc[b] = 1;
@@ -193,7 +193,7 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
         total += tc[b]         ? tc6_matrix_bytes()
                  : oz[b] == 4 ? oz4_matrix_bytes()
                  : oz[b] == 5 ? oz5_matrix_bytes()
-                 : oz[b] == 6 ? bz5_matrix_bytes()
+                 : oz[b] >= 15 ? bz_matrix_bytes(oz[b] - 10)
                               : ops[b].data.size() * kernel_entry_bytes(ar);
         total = (total + 255) & ~size_t(255);
     }
@@ -207,8 +207,8 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
             prepare_oz4_matrix(ops[b].data, host.data() + offs[b]);
         else if (oz[b] == 5)
             prepare_oz5_matrix(ops[b].data, host.data() + offs[b]);
-        else if (oz[b] == 6)
-            prepare_bz5_matrix(ops[b].data, host.data() + offs[b]);
+        else if (oz[b] >= 15)
+            prepare_bz_matrix(oz[b] - 10, ops[b].data, host.data() + offs[b]);
         else
             encode_entries(ar, ops[b].data, host.data() + offs[b]);
     }

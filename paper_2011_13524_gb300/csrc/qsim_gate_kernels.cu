@@ -351,19 +351,19 @@ void launch_with(const Op& op, void* psi, int n, cudaStream_t st, void* stage) {
             const int m = int(op.targets.size());
             for (int t : op.targets) fixed.push_back(t);
             IndexPlan ip = make_index_plan(n, fixed, setmask);
-            // complex64 blocks of 5 targets: tensor cores, bf16 slices with exact sums
-            if (sizeof(C) == 8 && m == 5 && tensor_c64x_enabled()) {
+            // complex64 blocks of 5 or 6 targets: tensor cores, bf16 slices with exact sums
+            if (sizeof(C) == 8 && (m == 5 || m == 6) && tensor_c64x_enabled()) {
                 const Op os = op.dmat_oz ? op : sort_targets(op);
                 const void* dK = op.dmat_oz ? op.dmat : nullptr;
                 if (!dK) {
-                    QS_REQUIRE(stage != nullptr && bz5_matrix_bytes() <= kStageBytes, "no staging buffer for a wide dense gate");
-                    std::vector<unsigned char> hk(bz5_matrix_bytes());
-                    prepare_bz5_matrix(os.data, hk.data());
+                    QS_REQUIRE(stage != nullptr && bz_matrix_bytes(m) <= kStageBytes, "no staging buffer for a wide dense gate");
+                    std::vector<unsigned char> hk(bz_matrix_bytes(m));
+                    prepare_bz_matrix(m, os.data, hk.data());
                     QS_TRY_CUDA(cudaMemcpyAsync(stage, hk.data(), hk.size(), cudaMemcpyHostToDevice, st));
                     QS_TRY_CUDA(cudaStreamSynchronize(st));  // hk is host memory that dies on return
                     dK = stage;
                 }
-                return launch_dense_bz5(psi, n, os.targets, os.controls, os.cvals, dK, st);
+                return launch_dense_bz(psi, n, os.targets, os.controls, os.cvals, dK, st);
             }
             // complex64 blocks of 5-6 targets: tensor cores (a 5-target block is padded to 6)
             if (sizeof(C) == 8 && m >= 5 && tensor_c64_enabled()) {

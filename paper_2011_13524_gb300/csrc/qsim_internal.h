@@ -296,12 +296,13 @@ size_t oz5_matrix_bytes();
 void prepare_oz5_matrix(const std::vector<cplx>& K, unsigned char* host_out);
 void launch_dense_oz5(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
                       const std::vector<int>& cvals, const void* dmat, cudaStream_t st);
-// complex64 5-target blocks: three bf16 slices per operand, exact FP32 sums, one FP32 rounding
+// complex64 5- and 6-target blocks: three bf16 slices per operand, exact FP32 sums, one FP32
+// rounding per output
 bool tensor_c64x_enabled();
-size_t bz5_matrix_bytes();
-void prepare_bz5_matrix(const std::vector<cplx>& K, unsigned char* host_out);
-void launch_dense_bz5(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
-                      const std::vector<int>& cvals, const void* dmat, cudaStream_t st);
+size_t bz_matrix_bytes(int q);
+void prepare_bz_matrix(int q, const std::vector<cplx>& K, unsigned char* host_out);
+void launch_dense_bz(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
+                     const std::vector<int>& cvals, const void* dmat, cudaStream_t st);
 bool oz_error_pending();
 
 // complex128 arithmetic mode (QS_MATH_FP64 / QS_MATH_DF)

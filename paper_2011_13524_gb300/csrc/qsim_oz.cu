@@ -575,30 +575,47 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kOz5TmemCols));
 }
 
-// ---------------------------------------------------------------- complex64, 5-target blocks
+// ---------------------------------------------------------------- complex64, 5- and 6-target blocks
 // The same splitting for complex64 states (float2): the group vector (scaled by its power of two
 // nu) and the matrix rows (scaled by mu_n) are cut into three 8-bit slices on the grids 2^-8,
 // 2^-16, 2^-24, which hold every bit of an FP32 value down to 2^-24 of the group's scale; the six
-// products with s + t <= 2 are summed exactly in FP32 by the tensor cores into three diagonals
-// (3 x 64 TMEM columns), and the epilogue adds them in FP32 from the smallest (one rounding to
-// nearest, no bias) and scales by mu_n nu. Error about 2^-24 of max|v| max|K~| per output, the
-// accuracy of the FP32 CUDA-core kernels. Tile: 128 groups of 32 amplitudes; 256 threads
-// (thread (g, h) owns amplitudes 16h .. 16h + 15 of group g), one slice buffer (48 KB), two CTAs
-// per SM so that one CTA's MMAs overlap the other's slicing and folding.
-constexpr int kBzNS = 3;                                        // slices per operand
-constexpr int kBzND = 3;                                        // diagonals s + t <= 2
-constexpr int kBzThreads = 256;
-constexpr int kBzAmps = kOz5D / (kBzThreads / kOzTG);           // 16 amplitudes per thread
-constexpr size_t kBzSlice = size_t(kOzTG) * kOz5R * 2;          // 16 KB
-constexpr size_t kBzABuf = kBzNS * kBzSlice;                    // 48 KB
-constexpr size_t kBzMat = size_t(kBzNS) * kOz5R * kOz5R * 2;    // 24 KB: [B_0; B_1; B_2] 192 x 64
-constexpr int kBzTmemCols = 256;
-constexpr size_t kOffBzA = 0;
-constexpr size_t kOffBzMat = kOffBzA + kBzABuf;
-constexpr size_t kOffBzMu = kOffBzMat + kBzMat;
-constexpr size_t kOffBzNuPart = kOffBzMu + kOz5R * 4;
-constexpr size_t kBzSmem = kOffBzNuPart + 2 * kOzTG * 4;
-static_assert(kBzND * kOz5R <= kBzTmemCols, "accumulators fit the TMEM allocation");
+// products with s + t <= 2 are summed exactly in FP32 by the tensor cores into three diagonals,
+// and the epilogue adds them in FP32 from the smallest (one rounding to nearest, no bias) and
+// scales by mu_n nu. Error about 2^-24 of max|v| max|K~| per output, the accuracy of the FP32
+// CUDA-core kernels. Tile: 128 groups; each thread owns 16 amplitudes of a group; one slice
+// buffer. Q = 5: R = 64 reals, 256 threads, two CTAs per SM (75 KB, 256 TMEM columns each) so
+// that one CTA's MMAs overlap the other's slicing and folding. Q = 6: R = 128, 512 threads, one
+// CTA per SM (194 KB, 384 of 512 TMEM columns); the first slice's products (N = 384) take two
+// MMAs, as N is at most 256.
+constexpr int kBzNS = 3;   // slices per operand
+constexpr int kBzND = 3;   // diagonals s + t <= 2
+template <int Q>
+struct Bz {
+    static constexpr int D = 1 << Q;                                   // amplitudes per group
+    static constexpr int R = 2 * D;                                    // reals per group
+    static constexpr int Threads = Q == 5 ? 256 : 512;
+    static constexpr int Tpg = Threads / kOzTG;                        // threads per group
+    static constexpr int Amps = D / Tpg;                               // 16
+    static constexpr uint32_t Sbo = (R / 8) * 128;
+    static constexpr size_t Slice = size_t(kOzTG) * R * 2;
+    static constexpr size_t ABuf = kBzNS * Slice;
+    static constexpr size_t Mat = size_t(kBzNS) * R * R * 2;          // [B_0; B_1; B_2]
+    static constexpr int TmemCols = Q == 5 ? 256 : 512;
+    static constexpr size_t OffA = 0;
+    static constexpr size_t OffMat = OffA + ABuf;
+    static constexpr size_t OffMu = OffMat + Mat;
+    static constexpr size_t OffNu = OffMu + R * 4;
+    static constexpr size_t Smem = OffNu + size_t(Tpg) * kOzTG * 4;
+    static constexpr int MinBlocks = Q == 5 ? 2 : 1;
+    static_assert(kBzND * R <= TmemCols, "accumulators fit the TMEM allocation");
+    static_assert(Amps == 16, "sixteen amplitudes per thread");
+};
+template <int Q>
+struct BzParams {
+    IndexPlan ip;
+    uint64_t offs[1 << Q];
+    uint64_t n_groups;
+};
 
 // the three slices of x * inv (|x * inv| <= 1): multiples of 2^-8, 2^-16, 2^-24
 __device__ __forceinline__ void slice3(float x, float inv, float (&a)[kBzNS]) {
@@ -609,27 +626,40 @@ __device__ __forceinline__ void slice3(float x, float inv, float (&a)[kBzNS]) {
     a[2] = grid_round<2>(__fsub_rn(r, a[1]));
 }
 
-__global__ void __launch_bounds__(kBzThreads, 2) k_dense_bz5(float2* __restrict__ psi, const unsigned char* __restrict__ dmat,
-                                                             const __grid_constant__ Oz5Params P, int* err) {
+template <int Q>
+__device__ __forceinline__ uint64_t bz_desc(uint32_t saddr) {
+    uint64_t d = uint64_t((saddr >> 4) & 0x3FFF);
+    d |= uint64_t((kOzLbo >> 4) & 0x3FFF) << 16;
+    d |= uint64_t((Bz<Q>::Sbo >> 4) & 0x3FFF) << 32;
+    d |= uint64_t(1) << 46;
+    return d;
+}
+
+template <int Q>
+__global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(float2* __restrict__ psi,
+                                                                               const unsigned char* __restrict__ dmat,
+                                                                               const __grid_constant__ BzParams<Q> P,
+                                                                               int* err) {
+    using B = Bz<Q>;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int g = tid & (kOzTG - 1), h = tid >> 7;
-    const float* mu = reinterpret_cast<const float*>(smem + kOffBzMu);
-    float* nu_part = reinterpret_cast<float*>(smem + kOffBzNuPart);
-    unsigned char* ab = smem + kOffBzA;
+    const int g = tid & (kOzTG - 1), h = tid >> 7;  // thread (g, h): amplitudes 16h .. 16h + 15 of group g
+    const float* mu = reinterpret_cast<const float*>(smem + B::OffMu);
+    float* nu_part = reinterpret_cast<float*>(smem + B::OffNu);
+    unsigned char* ab = smem + B::OffA;
 
-    for (int i = tid; i < int((kBzMat + kOz5R * 4) / 16); i += kBzThreads)
-        reinterpret_cast<uint4*>(smem + kOffBzMat)[i] = reinterpret_cast<const uint4*>(dmat)[i];
+    for (int i = tid; i < int((B::Mat + B::R * 4) / 16); i += B::Threads)
+        reinterpret_cast<uint4*>(smem + B::OffMat)[i] = reinterpret_cast<const uint4*>(dmat)[i];
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
         s_fail = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(kBzTmemCols));
+                     "r"(B::TmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -643,22 +673,24 @@ __global__ void __launch_bounds__(kBzThreads, 2) k_dense_bz5(float2* __restrict_
         const uint64_t gi = (blockIdx.x + j * gridDim.x) * kOzTG + uint64_t(g);
         return gi < P.n_groups ? expand(gi, P.ip) : ~0ull;
     };
-    auto load = [&](uint64_t x0, float2 (&v)[kBzAmps]) {
+    auto load = [&](uint64_t x0, float2 (&v)[B::Amps]) {
 #pragma unroll
-        for (int i = 0; i < kBzAmps; i++)
-            v[i] = x0 != ~0ull ? psi[x0 + P.offs[kBzAmps * h + i]] : make_float2(0.f, 0.f);
+        for (int i = 0; i < B::Amps; i++)
+            v[i] = x0 != ~0ull ? psi[x0 + P.offs[B::Amps * h + i]] : make_float2(0.f, 0.f);
     };
-    auto slice = [&](const float2 (&v)[kBzAmps]) {
+    auto slice = [&](const float2 (&v)[B::Amps]) {
         float m = 0.f;
 #pragma unroll
-        for (int i = 0; i < kBzAmps; i++) m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
+        for (int i = 0; i < B::Amps; i++) m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
         nu_part[h * kOzTG + g] = m;
         __syncthreads();
-        m = fmaxf(nu_part[g], nu_part[kOzTG + g]);
+        m = nu_part[g];
+#pragma unroll
+        for (int t = 1; t < B::Tpg; t++) m = fmaxf(m, nu_part[t * kOzTG + g]);
         const float nv = pow2_ceil(m);
         const float inv = __uint_as_float((254u - (__float_as_uint(nv) >> 23)) << 23);
 #pragma unroll
-        for (int c = 0; c < kBzAmps / 4; c++) {  // 4 amplitudes = K columns 32h + 8c .. +7
+        for (int c = 0; c < B::Amps / 4; c++) {  // 4 amplitudes = K columns 32h + 8c .. +7
             uint32_t pk[kBzNS][4];
 #pragma unroll
             for (int i = 0; i < 4; i++) {
@@ -668,36 +700,46 @@ __global__ void __launch_bounds__(kBzThreads, 2) k_dense_bz5(float2* __restrict_
 #pragma unroll
                 for (int s2 = 0; s2 < kBzNS; s2++) pk[s2][i] = pack_bf16(ar[s2], ai[s2]);
             }
-            const uint32_t o = kmaj5(uint32_t(g), uint32_t(32 * h + 8 * c));
+            const uint32_t r = uint32_t(g), k = uint32_t(32 * h + 8 * c);
+            const uint32_t o = (r >> 3) * B::Sbo + (k >> 3) * kOzLbo + (r & 7) * 16;
 #pragma unroll
             for (int s2 = 0; s2 < kBzNS; s2++)
-                *reinterpret_cast<uint4*>(ab + s2 * kBzSlice + o) = make_uint4(pk[s2][0], pk[s2][1], pk[s2][2], pk[s2][3]);
+                *reinterpret_cast<uint4*>(ab + s2 * B::Slice + o) = make_uint4(pk[s2][0], pk[s2][1], pk[s2][2], pk[s2][3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         return nv;
     };
     auto issue = [&]() {  // state slice s times matrix slices 0 .. 2 - s into diagonals s .. 2
         if (tid != 0) return;
-        const uint32_t a0 = smem_u32(ab), m0 = smem_u32(smem + kOffBzMat);
+        const uint32_t a0 = smem_u32(ab), m0 = smem_u32(smem + B::OffMat);
+        auto prod = [&](int s2, int t0, int nt, int ks, uint32_t acc) {
+            mma_bf16(tmem + uint32_t((s2 + t0) * B::R), bz_desc<Q>(a0 + uint32_t(s2 * B::Slice) + uint32_t(ks * 256)),
+                     bz_desc<Q>(m0 + uint32_t(t0 * B::R / 8) * B::Sbo + uint32_t(ks * 256)), idesc(uint32_t(nt * B::R)), acc);
+        };
 #pragma unroll
-        for (int ks = 0; ks < kOz5R / 16; ks++)
-#pragma unroll
-            for (int s2 = 0; s2 < kBzNS; s2++)
-                mma_bf16(tmem + uint32_t(s2 * kOz5R), sdesc5(a0 + uint32_t(s2 * kBzSlice) + uint32_t(ks * 256)),
-                         sdesc5(m0 + uint32_t(ks * 256)), idesc(uint32_t((kBzND - s2) * kOz5R)),
-                         (ks == 0 && s2 == 0) ? 0u : 1u);
+        for (int ks = 0; ks < B::R / 16; ks++) {
+            const uint32_t first = ks == 0 ? 0u : 1u;
+            if (3 * B::R <= 256) {
+                prod(0, 0, 3, ks, first);
+            } else {  // N = 3 R above 256: slices 0-1, then slice 2
+                prod(0, 0, 2, ks, first);
+                prod(0, 2, 1, ks, first);
+            }
+            prod(1, 0, 2, ks, 1u);
+            prod(2, 0, 1, ks, 1u);
+        }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar)));
     };
     auto epilogue = [&](uint64_t x0, float nv) {
         const uint32_t lane_base = tmem + (uint32_t((warp & 3) * 32) << 16) + uint32_t(32 * h);
 #pragma unroll
-        for (int c = 0; c < kBzAmps / 2; c++) {  // 4 output reals = 2 amplitudes per step
+        for (int c = 0; c < B::Amps / 2; c++) {  // 4 output reals = 2 amplitudes per step
             uint32_t r[kBzND][4];
 #pragma unroll
             for (int d = 0; d < kBzND; d++)
                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
                              : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3])
-                             : "r"(lane_base + uint32_t(d * kOz5R + 4 * c)));
+                             : "r"(lane_base + uint32_t(d * B::R + 4 * c)));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int i = 0; i < 2; i++) {
@@ -709,12 +751,12 @@ __global__ void __launch_bounds__(kBzThreads, 2) k_dense_bz5(float2* __restrict_
                                                __uint_as_float(r[0][col]));
                     o[cc] = __fmul_rn(sm, __fmul_rn(mu[32 * h + 4 * c + col], nv));
                 }
-                if (x0 != ~0ull) psi[x0 + P.offs[kBzAmps * h + 2 * c + i]] = make_float2(o[0], o[1]);
+                if (x0 != ~0ull) psi[x0 + P.offs[B::Amps * h + 2 * c + i]] = make_float2(o[0], o[1]);
             }
         }
     };
 
-    float2 vcur[kBzAmps], vnext[kBzAmps];
+    float2 vcur[B::Amps], vnext[B::Amps];
     uint64_t x0_cur = 0, x0_prev = 0;
     float nv_prev = 1.f;
     if (my_tiles > 0) {
@@ -744,7 +786,7 @@ __global__ void __launch_bounds__(kBzThreads, 2) k_dense_bz5(float2* __restrict_
         nv_prev = nv_cur;
         x0_cur = x0_next;
 #pragma unroll
-        for (int i = 0; i < kBzAmps; i++) vcur[i] = vnext[i];
+        for (int i = 0; i < B::Amps; i++) vcur[i] = vnext[i];
     }
     if (s_fail && tid == 0) {
         atomicExch(err, 1);
@@ -753,7 +795,7 @@ __global__ void __launch_bounds__(kBzThreads, 2) k_dense_bz5(float2* __restrict_
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBzTmemCols));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(B::TmemCols));
 }
 
 int g_oz_sms = 0;
@@ -927,24 +969,27 @@ void launch_dense_oz5(void* psi, int n, const std::vector<int>& targets, const s
     QS_TRY_CUDA(cudaGetLastError());
 }
 
-size_t bz5_matrix_bytes() { return kBzMat + kOz5R * 4; }
+size_t bz_matrix_bytes(int q) { return q == 5 ? Bz<5>::Mat + Bz<5>::R * 4 : Bz<6>::Mat + Bz<6>::R * 4; }
 
-// [B_0; B_1; B_2] (192 x 64 bf16, K-major core-matrix layout) of the row-scaled real form, then
-// the 64 row scales.
-void prepare_bz5_matrix(const std::vector<cplx>& K, unsigned char* host_out) {
-    QS_REQUIRE(K.size() == size_t(kOz5D) * kOz5D, "5-target tensor-core path takes 32 x 32 matrices");
-    std::memset(host_out, 0, bz5_matrix_bytes());
-    float* mu = reinterpret_cast<float*>(host_out + kBzMat);
+// [B_0; B_1; B_2] (3 R x R bf16, K-major core-matrix layout) of the row-scaled real form of a
+// 2^q x 2^q matrix, then the R row scales.
+void prepare_bz_matrix(int q, const std::vector<cplx>& K, unsigned char* host_out) {
+    QS_REQUIRE(q == 5 || q == 6, "complex64 tensor-core path takes 5 or 6 targets");
+    const int D = 1 << q, R = 2 * D;
+    const size_t sbo = size_t(R / 8) * 128;
+    QS_REQUIRE(K.size() == size_t(D) * D, "matrix size does not match the target count");
+    std::memset(host_out, 0, bz_matrix_bytes(q));
+    float* mu = reinterpret_cast<float*>(host_out + size_t(kBzNS) * R * R * 2);
     double magic[kBzNS];
     for (int t = 0; t < kBzNS; t++) magic[t] = 1.5 * std::ldexp(1.0, 52 - 8 * (t + 1));
     auto rf = [&](int n, int k) {
-        const cplx e = K[size_t(n >> 1) * kOz5D + size_t(k >> 1)];
+        const cplx e = K[size_t(n >> 1) * D + size_t(k >> 1)];
         if ((n & 1) == 0) return (k & 1) == 0 ? e.real() : -e.imag();
         return (k & 1) == 0 ? e.imag() : e.real();
     };
-    for (int n = 0; n < kOz5R; n++) {
+    for (int n = 0; n < R; n++) {
         double m = 0.0;
-        for (int k = 0; k < kOz5R; k++) m = std::max(m, std::fabs(rf(n, k)));
+        for (int k = 0; k < R; k++) m = std::max(m, std::fabs(rf(n, k)));
         double scale = 1.0;
         if (m > 0.0) {
             int e = 0;
@@ -952,13 +997,13 @@ void prepare_bz5_matrix(const std::vector<cplx>& K, unsigned char* host_out) {
             scale = f == 0.5 ? m : std::ldexp(1.0, e);
         }
         mu[n] = float(scale);
-        for (int k = 0; k < kOz5R; k++) {
+        for (int k = 0; k < R; k++) {
             double r = rf(n, k) / scale;
             for (int t = 0; t < kBzNS; t++) {
                 const double a = (r + magic[t]) - magic[t];
                 r -= a;
-                const int row = t * kOz5R + n;
-                const size_t off = size_t(row >> 3) * kOz5Sbo + size_t(k >> 3) * kOzLbo + size_t(row & 7) * 16 +
+                const int row = t * R + n;
+                const size_t off = size_t(row >> 3) * sbo + size_t(k >> 3) * kOzLbo + size_t(row & 7) * 16 +
                                    size_t(k & 7) * 2;
                 const uint16_t bits = bf16_bits_exact(a);
                 std::memcpy(host_out + off, &bits, 2);
@@ -967,10 +1012,10 @@ void prepare_bz5_matrix(const std::vector<cplx>& K, unsigned char* host_out) {
     }
 }
 
-void launch_dense_bz5(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
-                      const std::vector<int>& cvals, const void* dmat, cudaStream_t st) {
-    QS_REQUIRE(targets.size() == size_t(kOz5Q), "5-target tensor-core path takes 5 targets");
-    QS_REQUIRE(std::is_sorted(targets.begin(), targets.end()), "targets must be ascending");
+template <int Q>
+void launch_bz_t(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
+                 const std::vector<int>& cvals, const void* dmat, cudaStream_t st) {
+    using B = Bz<Q>;
     static bool attr = false;
     if (!g_oz_sms) {
         int dev = 0;
@@ -981,7 +1026,7 @@ void launch_dense_bz5(void* psi, int n, const std::vector<int>& targets, const s
         QS_TRY_CUDA(cudaMemset(g_oz_err, 0, sizeof(int)));
     }
     if (!attr) {
-        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_bz5, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBzSmem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_bz<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(B::Smem)));
         attr = true;
     }
     std::vector<int> fixed(targets);
@@ -990,20 +1035,31 @@ void launch_dense_bz5(void* psi, int n, const std::vector<int>& targets, const s
         fixed.push_back(controls[i]);
         if (cvals[i]) setmask |= 1ull << controls[i];
     }
-    Oz5Params P;
+    BzParams<Q> P;
     P.ip = make_index_plan(n, fixed, setmask);
     P.n_groups = P.ip.n_iter;
-    for (int w = 0; w < kOz5D; w++) {
+    for (int w = 0; w < B::D; w++) {
         uint64_t o = 0;
-        for (int j = 0; j < kOz5Q; j++)
+        for (int j = 0; j < Q; j++)
             if ((w >> j) & 1) o |= 1ull << targets[j];
         P.offs[w] = o;
     }
     const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
-    const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, 2 * uint64_t(g_oz_sms))));
-    k_dense_bz5<<<grid, kBzThreads, kBzSmem, st>>>(reinterpret_cast<float2*>(psi),
-                                                   static_cast<const unsigned char*>(dmat), P, g_oz_err);
+    const unsigned grid =
+        unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, uint64_t(B::MinBlocks) * uint64_t(g_oz_sms))));
+    k_dense_bz<Q><<<grid, B::Threads, B::Smem, st>>>(reinterpret_cast<float2*>(psi),
+                                                     static_cast<const unsigned char*>(dmat), P, g_oz_err);
     QS_TRY_CUDA(cudaGetLastError());
+}
+
+void launch_dense_bz(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
+                     const std::vector<int>& cvals, const void* dmat, cudaStream_t st) {
+    QS_REQUIRE(targets.size() == 5 || targets.size() == 6, "complex64 tensor-core path takes 5 or 6 targets");
+    QS_REQUIRE(std::is_sorted(targets.begin(), targets.end()), "targets must be ascending");
+    if (targets.size() == 5)
+        launch_bz_t<5>(psi, n, targets, controls, cvals, dmat, st);
+    else
+        launch_bz_t<6>(psi, n, targets, controls, cvals, dmat, st);
 }
 
 // device-side error recorded by the kernel (a bounded wait ran out); cleared on read

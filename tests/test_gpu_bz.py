@@ -1,7 +1,7 @@
-"""Tensor-core path for complex64 dense blocks of 5 targets with bf16 slices and exact FP32 sums
-(QS_TENSOR_C64X, on by default) against the FP64 oracle and the FP32 CUDA-core kernels: target
-placements (low, high, mixed, unsorted), controls, ragged tiles, fused circuits at width 5, and a
-full-size run whose norm shows no drift (one rounding to nearest per output)."""
+"""Tensor-core path for complex64 dense blocks of 5 and 6 targets with bf16 slices and exact FP32
+sums (QS_TENSOR_C64X, on by default) against the FP64 oracle and the FP32 CUDA-core kernels:
+target placements (low, high, mixed, unsorted), controls, ragged tiles, fused circuits at widths
+5 and 6, and full-size runs whose norm shows no drift (one rounding to nearest per output)."""
 import numpy as np
 import pytest
 
@@ -99,6 +99,69 @@ def test_bz5_full_size_no_drift(qs):
         assert (a.tensor - b.tensor).abs().max().item() < 5e-6
         assert abs(a.norm2() - 1.0) < 1e-5
         assert abs(b.norm2() - 1.0) < 1e-5
+    finally:
+        qs.set_tensor_cores(old)
+    del a, b
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n", [6, 7, 12, 13, 17])
+def test_bz6_single_gate_placements(qs, n):
+    rng = W.SplitMix64(600 + n)
+    psi0 = W.random_state(n, 7 * n)
+    for t in [(0, 1, 2, 3, 4, 5), tuple(range(n - 1, n - 7, -1)), (7, 0, n - 1, 3, n - 2, 5), (5, 4, 3, 2, 1, 0)]:
+        if len(set(t)) < 6 or max(t) >= n:
+            continue
+        g = W.Gate("DENSE", t, matrix=W.random_unitary(64, rng))
+        ref = psi0.copy()
+        oracle.apply_gate(ref, n, g)
+        got = run(qs, n, [g], psi0, qs.QS_TENSOR_C64X)
+        cuda_cores = run(qs, n, [g], psi0, 0)
+        assert np.max(np.abs(got - ref)) < 1e-6, t
+        assert np.max(np.abs(got - cuda_cores)) < 1e-6, t
+
+
+def test_bz6_controlled(qs):
+    n = 11
+    rng = W.SplitMix64(92)
+    psi0 = W.random_state(n, 6)
+    g = W.Gate("DENSE", (1, 2, 4, 6, 8, 9), controls=(0, 10), control_values=(1, 0), matrix=W.random_unitary(64, rng))
+    ref = psi0.copy()
+    oracle.apply_gate(ref, n, g)
+    assert np.max(np.abs(run(qs, n, [g], psi0, qs.QS_TENSOR_C64X) - ref)) < 1e-6
+
+
+@pytest.mark.parametrize("n", [12, 18])
+def test_bz6_fused_circuits(qs, n):
+    c = W.u3cz_circuit(n, 16, 90 + n)
+    ref = oracle.run_circuit(c)
+    old = qs.get_tensor_cores()
+    try:
+        qs.set_tensor_cores(qs.QS_TENSOR_C64X)
+        st = qs.State(n, qs.QS_C64)
+        st.run(c, 6)
+        st.synchronize()
+        assert np.max(np.abs(st.get_vector() - ref)) < 1e-5
+    finally:
+        qs.set_tensor_cores(old)
+
+
+def test_bz6_full_size_no_drift(qs):
+    import torch
+    n = 28
+    c = W.u3cz_circuit(n, 20, 44)
+    old = qs.get_tensor_cores()
+    try:
+        qs.set_tensor_cores(qs.QS_TENSOR_C64X)
+        a = qs.State(n, qs.QS_C64)
+        a.run(c, 6)
+        qs.set_tensor_cores(0)
+        b = qs.State(n, qs.QS_C64)
+        b.run(c, 6)
+        a.synchronize()
+        b.synchronize()
+        assert (a.tensor - b.tensor).abs().max().item() < 5e-6
+        assert abs(a.norm2() - 1.0) < 1e-5
     finally:
         qs.set_tensor_cores(old)
     del a, b
