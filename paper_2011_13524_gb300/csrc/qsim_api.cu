@@ -266,7 +266,7 @@ void apply_plan(qs_state* s, const FusionPlan& p) { apply_plan_impl(s, p, nullpt
 // on a scratch state, keyed by (device, dtype, c128 arithmetic, kernel, targets).
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int>, double> g_cost;
+std::map<std::tuple<int, int, int, int, int, bool>, double> g_cost;
 
 double measure_cost(int dev, qs_dtype dt, const Op& probe_op, int np_) {
     qs_state* s = nullptr;
@@ -306,10 +306,21 @@ double measure_cost(int dev, qs_dtype dt, const Op& probe_op, int np_) {
     return bytes > 0 ? 1e-3 * best / bytes : 0.0;
 }
 
-// representative op of the same kernel form and width as `op`, on a probe state of np_ qubits
+// whether an op's targets include qubit 0 or 1: such blocks read and write their amplitudes in
+// short contiguous runs per thread, which costs the wide kernels more than other placements
+bool touches_low(const Op& op) {
+    if (op.kind != OpKind::Dense && op.kind != OpKind::Diag) return false;
+    for (int t : op.targets)
+        if (t <= 1) return true;
+    return false;
+}
+
+// representative op of the same kernel form and width as `op`, on a probe state of np_ qubits:
+// low and high qubits mixed when `op` touches qubit 0 or 1, consecutive middle qubits otherwise
 Op probe_like(const Op& op, int np_) {
-    static const int spread[6] = {0, -1, -2, 1, -3, 2};  // low and high qubits mixed
-    auto q = [&](int j) { return spread[j] >= 0 ? spread[j] : np_ + spread[j]; };
+    static const int spread[6] = {0, -1, -2, 1, -3, 2};
+    const bool low = touches_low(op);
+    auto q = [&](int j) { return low ? (spread[j] >= 0 ? spread[j] : np_ + spread[j]) : np_ / 2 - 3 + j; };
     Op p;
     p.kind = op.kind;
     switch (op.kind) {
@@ -353,7 +364,7 @@ double predicted_seconds(const Op& op, int n, qs_dtype dt) {
     cudaGetDevice(&dev);
     const int width = op.kind == OpKind::Dense || op.kind == OpKind::Diag ? int(op.targets.size()) : 0;
     auto key = std::make_tuple(dev, int(dt), dt == QS_C128 ? c128_math() : g_tensor.load() & (QS_TENSOR_C64 | QS_TENSOR_C64X),
-                               kernel, width);
+                               kernel, width, touches_low(op));
     // (the kernel id already tells the tensor-core forms apart)
     double per_byte;
     {
