@@ -157,6 +157,20 @@ __device__ __forceinline__ float pow2_ceil(float m) {
     return __uint_as_float(e << 23);
 }
 
+// two adjacent amplitudes (32 bytes, 32-byte aligned) in one 256-bit access: used when the
+// block's lowest target is qubit 0, where each thread's amplitudes come in such pairs
+__device__ __forceinline__ void ld_pair(const float4* p, float4& a, float4& b) {
+    asm("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+__device__ __forceinline__ void st_pair(float4* p, const float4& a, const float4& b) {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(a.x), "f"(a.y), "f"(a.z), "f"(a.w),
+                 "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+                 : "memory");
+}
+
+template <bool kPairs>
 __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict__ psi, const unsigned char* __restrict__ dmat,
                                                              const __grid_constant__ OzParams P, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -197,9 +211,21 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
         return gi < P.n_groups ? expand(gi, P.ip) : ~0ull;
     };
     auto load = [&](uint64_t x0, float4 (&v)[kOzAmpsPerThread]) {
+        if (kPairs) {
 #pragma unroll
-        for (int i = 0; i < kOzAmpsPerThread; i++)
-            v[i] = x0 != ~0ull ? psi[x0 + off[i]] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = 0; i < kOzAmpsPerThread; i += 2) {
+                if (x0 != ~0ull) {
+                    ld_pair(psi + x0 + off[i], v[i], v[i + 1]);
+                } else {
+                    v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    v[i + 1] = v[i];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kOzAmpsPerThread; i++)
+                v[i] = x0 != ~0ull ? psi[x0 + off[i]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     };
     // slices of this thread's amplitudes into abuf(j); returns the group scale nu
     auto slice = [&](uint64_t j, const float4 (&v)[kOzAmpsPerThread]) {
@@ -267,9 +293,9 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
                              : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3])
                              : "r"(lane_base + uint32_t(d * kOzR + 4 * c)));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float o[2][4];
 #pragma unroll
             for (int i = 0; i < 2; i++) {
-                float o[4];
 #pragma unroll
                 for (int cc = 0; cc < 2; cc++) {
                     const int col = 2 * i + cc;
@@ -284,9 +310,18 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
                         lo = __fadd_rn(lo, t);
                     }
                     const float sc = __fmul_rn(mu[16 * h + 4 * c + col], nv);
-                    fast_two_sum(__fmul_rn(sm, sc), __fmul_rn(lo, sc), o[2 * cc], o[2 * cc + 1]);
+                    fast_two_sum(__fmul_rn(sm, sc), __fmul_rn(lo, sc), o[i][2 * cc], o[i][2 * cc + 1]);
                 }
-                if (x0 != ~0ull) psi[x0 + off[2 * c + i]] = make_float4(o[0], o[1], o[2], o[3]);
+            }
+            if (x0 != ~0ull) {
+                const float4 a = make_float4(o[0][0], o[0][1], o[0][2], o[0][3]);
+                const float4 b = make_float4(o[1][0], o[1][1], o[1][2], o[1][3]);
+                if (kPairs) {
+                    st_pair(psi + x0 + off[2 * c], a, b);
+                } else {
+                    psi[x0 + off[2 * c]] = a;
+                    psi[x0 + off[2 * c + 1]] = b;
+                }
             }
         }
     };
@@ -382,6 +417,7 @@ __device__ __forceinline__ uint64_t sdesc5(uint32_t saddr) {
     return d;
 }
 
+template <bool kPairs>
 __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict__ psi,
                                                                const unsigned char* __restrict__ dmat,
                                                                const __grid_constant__ Oz5Params P, int* err) {
@@ -424,9 +460,21 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
         return gi < P.n_groups ? expand(gi, P.ip) : ~0ull;
     };
     auto load = [&](uint64_t x0, float4 (&v)[kOz5Amps]) {
+        if (kPairs) {
 #pragma unroll
-        for (int i = 0; i < kOz5Amps; i++)
-            v[i] = x0 != ~0ull ? psi[x0 + off[i]] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = 0; i < kOz5Amps; i += 2) {
+                if (x0 != ~0ull) {
+                    ld_pair(psi + x0 + off[i], v[i], v[i + 1]);
+                } else {
+                    v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    v[i + 1] = v[i];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kOz5Amps; i++)
+                v[i] = x0 != ~0ull ? psi[x0 + off[i]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     };
     auto slice = [&](const float4 (&v)[kOz5Amps]) {
         float m = 0.f;
@@ -498,9 +546,9 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
                              : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3])
                              : "r"(lane_base + uint32_t(d * kOz5D + 4 * c)));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float o[2][4];
 #pragma unroll
             for (int i = 0; i < 2; i++) {
-                float o[4];
 #pragma unroll
                 for (int cc = 0; cc < 2; cc++) {
                     const int col = 2 * i + cc;
@@ -513,9 +561,18 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
                         lo = __fadd_rn(lo, t);
                     }
                     const float sc = __fmul_rn(mu[kOz5D * hv + 8 * q + 4 * c + col], nv);
-                    fast_two_sum(__fmul_rn(sm, sc), __fmul_rn(lo, sc), o[2 * cc], o[2 * cc + 1]);
+                    fast_two_sum(__fmul_rn(sm, sc), __fmul_rn(lo, sc), o[i][2 * cc], o[i][2 * cc + 1]);
                 }
-                if (x0 != ~0ull) psi[x0 + off[4 * hv + 2 * c + i]] = make_float4(o[0], o[1], o[2], o[3]);
+            }
+            if (x0 != ~0ull) {
+                const float4 a = make_float4(o[0][0], o[0][1], o[0][2], o[0][3]);
+                const float4 b = make_float4(o[1][0], o[1][1], o[1][2], o[1][3]);
+                if (kPairs) {
+                    st_pair(psi + x0 + off[4 * hv + 2 * c], a, b);
+                } else {
+                    psi[x0 + off[4 * hv + 2 * c]] = a;
+                    psi[x0 + off[4 * hv + 2 * c + 1]] = b;
+                }
             }
         }
     };
@@ -635,7 +692,7 @@ __device__ __forceinline__ uint64_t bz_desc(uint32_t saddr) {
     return d;
 }
 
-template <int Q>
+template <int Q, bool kPairs>
 __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(float2* __restrict__ psi,
                                                                                const unsigned char* __restrict__ dmat,
                                                                                const __grid_constant__ BzParams<Q> P,
@@ -674,9 +731,19 @@ __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(f
         return gi < P.n_groups ? expand(gi, P.ip) : ~0ull;
     };
     auto load = [&](uint64_t x0, float2 (&v)[B::Amps]) {
+        if (kPairs) {  // lowest target qubit 0: adjacent 16-byte-aligned pairs, one 128-bit load each
 #pragma unroll
-        for (int i = 0; i < B::Amps; i++)
-            v[i] = x0 != ~0ull ? psi[x0 + P.offs[B::Amps * h + i]] : make_float2(0.f, 0.f);
+            for (int i = 0; i < B::Amps; i += 2) {
+                const float4 w = x0 != ~0ull ? *reinterpret_cast<const float4*>(psi + x0 + P.offs[B::Amps * h + i])
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+                v[i] = make_float2(w.x, w.y);
+                v[i + 1] = make_float2(w.z, w.w);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < B::Amps; i++)
+                v[i] = x0 != ~0ull ? psi[x0 + P.offs[B::Amps * h + i]] : make_float2(0.f, 0.f);
+        }
     };
     auto slice = [&](const float2 (&v)[B::Amps]) {
         float m = 0.f;
@@ -741,17 +808,20 @@ __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(f
                              : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3])
                              : "r"(lane_base + uint32_t(d * B::R + 4 * c)));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float o[4];
 #pragma unroll
-            for (int i = 0; i < 2; i++) {
-                float o[2];
-#pragma unroll
-                for (int cc = 0; cc < 2; cc++) {
-                    const int col = 2 * i + cc;
-                    const float sm = __fadd_rn(__fadd_rn(__uint_as_float(r[2][col]), __uint_as_float(r[1][col])),
-                                               __uint_as_float(r[0][col]));
-                    o[cc] = __fmul_rn(sm, __fmul_rn(mu[32 * h + 4 * c + col], nv));
+            for (int col = 0; col < 4; col++) {
+                const float sm = __fadd_rn(__fadd_rn(__uint_as_float(r[2][col]), __uint_as_float(r[1][col])),
+                                           __uint_as_float(r[0][col]));
+                o[col] = __fmul_rn(sm, __fmul_rn(mu[32 * h + 4 * c + col], nv));
+            }
+            if (x0 != ~0ull) {
+                if (kPairs) {
+                    *reinterpret_cast<float4*>(psi + x0 + P.offs[B::Amps * h + 2 * c]) = make_float4(o[0], o[1], o[2], o[3]);
+                } else {
+                    psi[x0 + P.offs[B::Amps * h + 2 * c]] = make_float2(o[0], o[1]);
+                    psi[x0 + P.offs[B::Amps * h + 2 * c + 1]] = make_float2(o[2], o[3]);
                 }
-                if (x0 != ~0ull) psi[x0 + P.offs[B::Amps * h + 2 * c + i]] = make_float2(o[0], o[1]);
             }
         }
     };
@@ -862,7 +932,8 @@ void launch_dense_oz4(void* psi, int n, const std::vector<int>& targets, const s
         int dev = 0;
         QS_TRY_CUDA(cudaGetDevice(&dev));
         QS_TRY_CUDA(cudaDeviceGetAttribute(&g_oz_sms, cudaDevAttrMultiProcessorCount, dev));
-        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
         QS_TRY_CUDA(cudaMalloc(&g_oz_err, sizeof(int)));
         QS_TRY_CUDA(cudaMemset(g_oz_err, 0, sizeof(int)));
     }
@@ -883,8 +954,14 @@ void launch_dense_oz4(void* psi, int n, const std::vector<int>& targets, const s
     P.n_groups = P.ip.n_iter;
     const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, 2 * uint64_t(g_oz_sms))));
-    k_dense_oz4<<<grid, kOzThreads, kOzSmem, st>>>(reinterpret_cast<float4*>(psi),
-                                                   static_cast<const unsigned char*>(dmat), P, g_oz_err);
+    // lowest target qubit 0 (and a 32-byte-aligned state): each thread's amplitudes come in
+    // adjacent 32-byte-aligned pairs
+    if (targets[0] == 0 && (reinterpret_cast<uintptr_t>(psi) & 31) == 0)
+        k_dense_oz4<true><<<grid, kOzThreads, kOzSmem, st>>>(reinterpret_cast<float4*>(psi),
+                                                             static_cast<const unsigned char*>(dmat), P, g_oz_err);
+    else
+        k_dense_oz4<false><<<grid, kOzThreads, kOzSmem, st>>>(reinterpret_cast<float4*>(psi),
+                                                              static_cast<const unsigned char*>(dmat), P, g_oz_err);
     QS_TRY_CUDA(cudaGetLastError());
 }
 
@@ -939,12 +1016,14 @@ void launch_dense_oz5(void* psi, int n, const std::vector<int>& targets, const s
         int dev = 0;
         QS_TRY_CUDA(cudaGetDevice(&dev));
         QS_TRY_CUDA(cudaDeviceGetAttribute(&g_oz_sms, cudaDevAttrMultiProcessorCount, dev));
-        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
         QS_TRY_CUDA(cudaMalloc(&g_oz_err, sizeof(int)));
         QS_TRY_CUDA(cudaMemset(g_oz_err, 0, sizeof(int)));
     }
     if (!attr) {
-        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz5, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOz5Smem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz5<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOz5Smem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz5<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOz5Smem)));
         attr = true;
     }
     std::vector<int> fixed(targets);
@@ -964,8 +1043,12 @@ void launch_dense_oz5(void* psi, int n, const std::vector<int>& targets, const s
     }
     const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, uint64_t(g_oz_sms))));
-    k_dense_oz5<<<grid, kOz5Threads, kOz5Smem, st>>>(reinterpret_cast<float4*>(psi),
-                                                     static_cast<const unsigned char*>(dmat), P, g_oz_err);
+    if (targets[0] == 0 && (reinterpret_cast<uintptr_t>(psi) & 31) == 0)
+        k_dense_oz5<true><<<grid, kOz5Threads, kOz5Smem, st>>>(reinterpret_cast<float4*>(psi),
+                                                               static_cast<const unsigned char*>(dmat), P, g_oz_err);
+    else
+        k_dense_oz5<false><<<grid, kOz5Threads, kOz5Smem, st>>>(reinterpret_cast<float4*>(psi),
+                                                                static_cast<const unsigned char*>(dmat), P, g_oz_err);
     QS_TRY_CUDA(cudaGetLastError());
 }
 
@@ -1021,12 +1104,14 @@ void launch_bz_t(void* psi, int n, const std::vector<int>& targets, const std::v
         int dev = 0;
         QS_TRY_CUDA(cudaGetDevice(&dev));
         QS_TRY_CUDA(cudaDeviceGetAttribute(&g_oz_sms, cudaDevAttrMultiProcessorCount, dev));
-        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
         QS_TRY_CUDA(cudaMalloc(&g_oz_err, sizeof(int)));
         QS_TRY_CUDA(cudaMemset(g_oz_err, 0, sizeof(int)));
     }
     if (!attr) {
-        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_bz<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(B::Smem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_bz<Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(B::Smem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_bz<Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(B::Smem)));
         attr = true;
     }
     std::vector<int> fixed(targets);
@@ -1047,8 +1132,12 @@ void launch_bz_t(void* psi, int n, const std::vector<int>& targets, const std::v
     const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
     const unsigned grid =
         unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, uint64_t(B::MinBlocks) * uint64_t(g_oz_sms))));
-    k_dense_bz<Q><<<grid, B::Threads, B::Smem, st>>>(reinterpret_cast<float2*>(psi),
-                                                     static_cast<const unsigned char*>(dmat), P, g_oz_err);
+    if (targets[0] == 0 && (reinterpret_cast<uintptr_t>(psi) & 15) == 0)
+        k_dense_bz<Q, true><<<grid, B::Threads, B::Smem, st>>>(reinterpret_cast<float2*>(psi),
+                                                               static_cast<const unsigned char*>(dmat), P, g_oz_err);
+    else
+        k_dense_bz<Q, false><<<grid, B::Threads, B::Smem, st>>>(reinterpret_cast<float2*>(psi),
+                                                                static_cast<const unsigned char*>(dmat), P, g_oz_err);
     QS_TRY_CUDA(cudaGetLastError());
 }
 

@@ -232,3 +232,41 @@ def test_oz5_full_size_sampled(oz):
     st.close()
     del st
     torch.cuda.empty_cache()
+
+
+def test_oz_paired_access_alignment(oz):
+    """Blocks whose lowest target is qubit 0 move amplitude pairs with 256-bit accesses when the
+    state is 32-byte aligned; a state wrapped 16 bytes into a buffer takes the single-amplitude
+    path. Both give the oracle's result (4- and 5-target blocks, complex128 double-float; and
+    complex64 5-target blocks, whose pairs need only the 16 bytes every state has)."""
+    import torch
+    qs = oz
+    n = 13
+    rng = W.SplitMix64(57)
+    psi0 = W.random_state(n, 13)
+    gates = [W.Gate("DENSE", (0, 1, 2, 3), matrix=W.random_unitary(16, rng)),
+             W.Gate("DENSE", (0, 4, 5, 9, 12), matrix=W.random_unitary(32, rng)),
+             W.Gate("DENSE", (0, 1, 2, 3, 4), controls=(7,), control_values=(1,), matrix=W.random_unitary(32, rng))]
+    ref = psi0.copy()
+    for g in gates:
+        oracle.apply_gate(ref, n, g)
+    for offset in (0, 1):  # amplitudes: 0 -> 32-byte aligned, 1 -> 16 bytes off
+        buf = torch.zeros((1 << n) + 2, dtype=torch.complex128, device="cuda")
+        view = buf[offset:offset + (1 << n)]
+        st = qs.State(n, qs.QS_C128, tensor=view)
+        st.load(psi0)
+        st.run(W.Circuit(n, gates), 0)
+        assert maxabs(st.get_vector(), ref) < 1e-12, offset
+        assert buf[:offset].abs().max().item() == 0 if offset else True
+        assert buf[offset + (1 << n):].abs().max().item() == 0
+    c64_gates = gates[1:]
+    ref64 = psi0.copy()
+    for g in c64_gates:
+        oracle.apply_gate(ref64, n, g)
+    qs.set_tensor_cores(qs.QS_TENSOR_C128 | qs.QS_TENSOR_C64X)
+    for offset in (0, 2):  # complex64 states are 16-byte aligned (a wrapped pointer must be)
+        buf = torch.zeros((1 << n) + 2, dtype=torch.complex64, device="cuda")
+        st = qs.State(n, qs.QS_C64, tensor=buf[offset:offset + (1 << n)])
+        st.load(psi0)
+        st.run(W.Circuit(n, c64_gates), 0)
+        assert maxabs(st.get_vector(), ref64) < 1e-5, offset
