@@ -225,6 +225,39 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
     return w;
 }
 
+}  // namespace
+
+// diagonal ops that can join a tabulated run, and the qubits they act on
+bool diag_mergeable(const Op& op) {
+    return (op.kind == OpKind::Diag && op.controls.empty()) || op.kind == OpKind::Phase;
+}
+const std::vector<int>& diag_qubits(const Op& op) { return op.kind == OpKind::Phase ? op.controls : op.targets; }
+
+std::vector<int> diag_runs(const std::vector<Op>& ops) {
+    std::vector<int> len(ops.size(), 1);
+    size_t b = 0;
+    while (b < ops.size()) {
+        size_t e = b;
+        if (diag_mergeable(ops[b])) {
+            std::vector<int> u(diag_qubits(ops[b]));
+            while (e + 1 < ops.size() && diag_mergeable(ops[e + 1])) {
+                std::vector<int> w(u);
+                for (int q : diag_qubits(ops[e + 1]))
+                    if (std::find(w.begin(), w.end(), q) == w.end()) w.push_back(q);
+                if (w.size() > size_t(kDiagTableBits)) break;
+                u.swap(w);
+                e++;
+            }
+        }
+        len[b] = int(e - b + 1);
+        for (size_t i = b + 1; i <= e; i++) len[i] = 0;
+        b = e + 1;
+    }
+    return len;
+}
+
+namespace {
+
 void apply_plan_impl(qs_state* s, const FusionPlan& p, float* block_ms) {
     QS_REQUIRE(p.n == s->n, "plan and state have different qubit counts");
     std::vector<Op> ops;
@@ -240,8 +273,12 @@ void apply_plan_impl(qs_state* s, const FusionPlan& p, float* block_ms) {
             for (auto& e : ev) QS_TRY_CUDA(cudaEventCreate(&e));
             QS_TRY_CUDA(cudaEventRecord(ev[0], s->stream));
         }
+        const std::vector<int> runs = diag_runs(ops);
         for (size_t b = 0; b < ops.size(); b++) {
-            launch_op_arith(ops[b], s->data, s->n, arith_of(s), s->stream, stage_of(s));
+            if (runs[b] == 1)
+                launch_op_arith(ops[b], s->data, s->n, arith_of(s), s->stream, stage_of(s));
+            else if (runs[b] > 1)  // diagonal blocks in one pass (its time goes to the first)
+                launch_diag_run(&ops[b], size_t(runs[b]), s->data, s->n, arith_of(s), s->stream, stage_of(s));
             if (block_ms) QS_TRY_CUDA(cudaEventRecord(ev[b + 1], s->stream));
         }
         if (block_ms) {
@@ -728,7 +765,18 @@ qs_status qs_fused_block_cost(const qs_fused_circuit* f, int b, qs_dtype dt, int
     QS_REQUIRE(f != nullptr, "null plan");
     QS_REQUIRE(b >= 0 && b < int(f->plan.blocks.size()), "block index out of range");
     QS_REQUIRE(dt == QS_C64 || dt == QS_C128, "unknown dtype");
-    op_cost(block_op(f->plan, size_t(b)), f->plan.n, dt, kernel, launches, bytes);
+    std::vector<Op> ops;
+    for (size_t i = 0; i < f->plan.blocks.size(); i++) ops.push_back(block_op(f->plan, i));
+    const std::vector<int> runs = diag_runs(ops);
+    op_cost(ops[size_t(b)], f->plan.n, dt, kernel, launches, bytes);
+    if (runs[size_t(b)] == 0) {  // applied in the pass of an earlier diagonal block
+        if (launches) *launches = 0;
+        if (bytes) *bytes = 0.0;
+    } else if (runs[size_t(b)] > 1) {  // the first block of a tabulated diagonal run: one full pass
+        if (kernel) *kernel = QS_KERNEL_DIAG;
+        if (launches) *launches = 1;
+        if (bytes) *bytes = 2.0 * double(amp_bytes(dt)) * std::ldexp(1.0, f->plan.n);
+    }
     API_END
 }
 

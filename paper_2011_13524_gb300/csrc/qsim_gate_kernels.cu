@@ -146,6 +146,60 @@ __global__ void __launch_bounds__(kThreads) k_diag(typename P::C* __restrict__ p
     }
 }
 
+// Several diagonal blocks (no controls) in one pass: psi_x *= t[r(x)] with the product of their
+// diagonals tabulated over the union of their qubits (at most kDiagTableBits), staged in shared
+// memory per CTA; r(x) gathers the union's bits of x.
+template <typename P>
+struct DiagTableParams {
+    uint64_t N;
+    int32_t m;
+    int32_t tpos[kDiagTableBits];
+};
+
+template <typename P>
+__global__ void __launch_bounds__(kThreads) k_diag_table(typename P::C* __restrict__ psi,
+                                                         const typename P::K* __restrict__ table,
+                                                         const __grid_constant__ DiagTableParams<P> Pm) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    typename P::K* t = reinterpret_cast<typename P::K*>(dsm);
+    for (int i = threadIdx.x; i < (1 << Pm.m); i += blockDim.x) t[i] = table[i];
+    __syncthreads();
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t x = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < Pm.N; x += stride) {
+        uint32_t r = 0;
+#pragma unroll 4
+        for (int j = 0; j < Pm.m; j++) r |= uint32_t((x >> Pm.tpos[j]) & 1) << j;
+        typename P::Acc a = P::zero();
+        P::mac(a, t[r], psi[x]);
+        psi[x] = P::out(a);
+    }
+}
+
+template <typename P>
+void launch_diag_table_t(const std::vector<int>& u, const std::vector<cplx>& tab, void* psi, int n, cudaStream_t st,
+                         void* stage) {
+    using K = typename P::K;
+    const size_t bytes = tab.size() * sizeof(K);
+    QS_REQUIRE(stage != nullptr && bytes <= kStageBytes, "no staging buffer for a diagonal table");
+    std::vector<K> hk(tab.size());
+    for (size_t i = 0; i < tab.size(); i++) hk[i] = P::host_k(tab[i].real(), tab[i].imag());
+    QS_TRY_CUDA(cudaMemcpyAsync(stage, hk.data(), bytes, cudaMemcpyHostToDevice, st));
+    QS_TRY_CUDA(cudaStreamSynchronize(st));  // hk is host memory that dies on return
+    DiagTableParams<P> Pm;
+    Pm.N = 1ull << n;
+    Pm.m = int(u.size());
+    for (size_t j = 0; j < u.size(); j++) Pm.tpos[j] = u[j];
+    static bool attr = false;
+    if (!attr) {
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_diag_table<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(sizeof(K) << kDiagTableBits)));
+        attr = true;
+    }
+    k_diag_table<P><<<grid_for(Pm.N), kThreads, bytes, st>>>(reinterpret_cast<typename P::C*>(psi),
+                                                             static_cast<const K*>(stage), Pm);
+    QS_TRY_CUDA(cudaGetLastError());
+}
+
 // ------------------------------------------------------------------ phase on a subspace
 // psi_x *= phase for every x whose fixed bits match; mode 0 general, 1..3 = i^mode (exact).
 template <typename P>
@@ -509,6 +563,46 @@ void launch_op_arith(const Op& op, void* psi, int n, Arith ar, cudaStream_t st, 
         case Arith::DF: launch_with<DFArith>(op, psi, n, st, stage); break;
     }
     QS_TRY_CUDA(cudaGetLastError());
+}
+
+// Diagonal ops (no controls) applied as one pass: the product of their diagonals over the union
+// of their targets (at most kDiagTableBits qubits).
+void launch_diag_run(const Op* ops, size_t count, void* psi, int n, Arith ar, cudaStream_t st, void* stage) {
+    // uncontrolled diagonals (on their targets) and phases (on their control qubits' values)
+    auto qubits = [](const Op& op) -> const std::vector<int>& {
+        return op.kind == OpKind::Phase ? op.controls : op.targets;
+    };
+    std::vector<int> u;
+    for (size_t i = 0; i < count; i++) {
+        QS_REQUIRE((ops[i].kind == OpKind::Diag && ops[i].controls.empty()) || ops[i].kind == OpKind::Phase,
+                   "diagonal run of uncontrolled diagonals and phases");
+        for (int q : qubits(ops[i]))
+            if (std::find(u.begin(), u.end(), q) == u.end()) u.push_back(q);
+    }
+    std::sort(u.begin(), u.end());
+    QS_REQUIRE(u.size() <= size_t(kDiagTableBits), "diagonal run on too many qubits");
+    std::vector<cplx> tab(size_t(1) << u.size(), cplx(1.0, 0.0));
+    for (size_t i = 0; i < count; i++) {
+        const std::vector<int>& qs_i = qubits(ops[i]);
+        std::vector<int> pos;  // bit of the union index for each qubit of op i
+        for (int q : qs_i) pos.push_back(int(std::find(u.begin(), u.end(), q) - u.begin()));
+        for (size_t r = 0; r < tab.size(); r++) {
+            size_t ri = 0;
+            for (size_t j = 0; j < pos.size(); j++) ri |= ((r >> pos[j]) & 1) << j;
+            if (ops[i].kind == OpKind::Phase) {
+                bool match = true;
+                for (size_t j = 0; j < pos.size(); j++) match = match && int((ri >> j) & 1) == ops[i].cvals[j];
+                if (match) tab[r] *= ops[i].phase;
+            } else {
+                tab[r] *= ops[i].data[ri];
+            }
+        }
+    }
+    switch (ar) {
+        case Arith::F32: launch_diag_table_t<NativeArith<float>>(u, tab, psi, n, st, stage); break;
+        case Arith::F64: launch_diag_table_t<NativeArith<double>>(u, tab, psi, n, st, stage); break;
+        case Arith::DF: launch_diag_table_t<DFArith>(u, tab, psi, n, st, stage); break;
+    }
 }
 
 void launch_op(const Op& op, void* psi, int n, qs_dtype dt, cudaStream_t st, void* stage) {

@@ -127,6 +127,12 @@ inline Arith arith_of(const qs_state* s) {
 constexpr size_t kStageBytes = 2 * 128 * 128 * 4;  // >= 64x64 complex128 and the tensor-core form
 void launch_op(const Op& op, void* psi, int n, qs_dtype dt, cudaStream_t st, void* stage);
 void launch_op_arith(const Op& op, void* psi, int n, Arith ar, cudaStream_t st, void* stage);
+// consecutive uncontrolled diagonal ops on at most kDiagTableBits qubits together: one pass
+constexpr int kDiagTableBits = 12;
+void launch_diag_run(const Op* ops, size_t count, void* psi, int n, Arith ar, cudaStream_t st, void* stage);
+// for each op: the number of ops launched together from it (>= 1), or 0 if an earlier op's
+// diagonal run covers it
+std::vector<int> diag_runs(const std::vector<Op>& ops);
 void launch_set_basis(void* psi, int n, qs_dtype dt, uint64_t j, cudaStream_t st);
 void launch_set_basis_arith(void* psi, int n, Arith ar, uint64_t j, cudaStream_t st);
 // in-place layout change of a complex128 buffer: IEEE doubles <-> double-float pairs

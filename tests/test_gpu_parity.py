@@ -438,3 +438,46 @@ def test_precision_n24_vs_oracle(qs):
         assert abs(st.expectation(tf)[0] - e_ref) < e_tol, dtype
         assert abs(st.norm2() - 1.0) < (1e-12 if dtype == 2 else 1e-5)
         st.close()
+
+
+@pytest.mark.parametrize("dtype,math_mode", [(2, "df"), (2, "fp64"), (1, "fp64")])
+def test_consecutive_diagonal_blocks_one_pass(qs, dtype, math_mode):
+    """A circuit of diagonal gates only (RZ, CZ, T, S, controlled phases) fused at width 4: the
+    plan's consecutive diagonal blocks (at most 12 qubits together) run as one pass with a
+    tabulated product; the state matches the oracle and the block costs count one launch per
+    pass."""
+    n = 14
+    rng = W.SplitMix64(1414)
+    gates = []
+    for layer in range(6):
+        for q in range(n):
+            gates.append(W.Gate("RZ", (q,), params=(4 * rng.uniform(),)))
+        for q in range(layer % 2, n - 1, 2):
+            gates.append(W.Gate("CZ", (q, q + 1)))
+        gates.append(W.Gate("T", (int(rng.next_u64() % n),)))
+        gates.append(W.Gate("S", (int(rng.next_u64() % n),)))
+    c = W.Circuit(n, gates)
+    psi0 = W.random_state(n, 99)
+    ref = psi0.copy()
+    for g in gates:
+        oracle.apply_gate(ref, n, g)
+    old = qs.get_c128_math()
+    try:
+        qs.set_c128_math(qs.QS_MATH_DF if math_mode == "df" else qs.QS_MATH_FP64)
+        plan = qs.FusedCircuit(c, 4)
+        costs = [plan.block_cost(b, dtype) for b in range(plan.n_blocks)]
+        assert all(k in ("diag", "phase") for k, _, _ in costs)
+        launches = sum(l for _, l, _ in costs)
+        assert launches < plan.n_blocks  # several blocks share a pass
+        full = 2 * (16 if dtype == 2 else 8) * 2 ** n
+        assert all(by <= full and (l == 0) == (by == 0) for _, l, by in costs)
+        st = qs.State(n, dtype)
+        st.load(psi0)
+        st.apply_plan(plan)
+        assert maxabs(st.get_vector(), ref) < TOL[dtype]
+        st.load(psi0)
+        ms = st.apply_plan_timed(plan)
+        assert len(ms) == plan.n_blocks
+        assert maxabs(st.get_vector(), ref) < TOL[dtype]
+    finally:
+        qs.set_c128_math(old)
