@@ -277,6 +277,7 @@ struct Frontier {
     std::vector<int>& trial;
     int blk = 0;
     int tid = 0;
+    long long visits = 0;  // gates visited by close_over and widening so far: a deterministic work count
     struct Scan {
         uint64_t blocked = 0, bz = ~0ull, bx = ~0ull, by = ~0ull;
         bool ready(uint64_t m, const GateTags& t) const {
@@ -298,6 +299,7 @@ struct Frontier {
         Scan sc;
         int added = 0;
         for (int g : rem) {
+            visits++;
             if (member(g, use_trial)) continue;
             const uint64_t m = masks[g];
             if ((m & ~q) == 0 && sc.ready(m, tags[g])) {
@@ -312,10 +314,11 @@ struct Frontier {
         return added;
     }
     // Distinct qubit sets q | m of the ready gates that widen q without exceeding k qubits.
-    std::vector<uint64_t> widening(uint64_t q, int k) const {
+    std::vector<uint64_t> widening(uint64_t q, int k) {
         std::vector<uint64_t> cand;
         Scan sc;
         for (int g : rem) {
+            visits++;
             if (member(g, false)) continue;
             const uint64_t m = masks[g];
             if ((m & ~q) && __builtin_popcountll(q | m) <= k && sc.ready(m, tags[g]) &&
@@ -328,8 +331,33 @@ struct Frontier {
     }
 };
 
+// The most gates that `levels` more widenings of q can add, the trial gates of the last
+// close_over (tid) counted in the block meanwhile.
+int lookahead(Frontier& f, const std::vector<int>& rem, uint64_t q, int k, int levels) {
+    const int t1 = f.tid;
+    std::vector<int> added;
+    for (int g : rem)
+        if (f.trial[g] == t1 && f.in[g] != f.blk) {
+            f.in[g] = f.blk;
+            added.push_back(g);
+        }
+    int more = 0;
+    for (uint64_t u2 : f.widening(q, k)) {
+        f.tid++;
+        int got = f.close_over(u2, true);
+        if (levels > 1 && __builtin_popcountll(u2) < k) got += lookahead(f, rem, u2, k, levels - 1);
+        more = std::max(more, got);
+    }
+    for (int g : added) f.in[g] = -1;
+    return more;
+}
+
+// depth: 1 picks each widening by the gates it absorbs; d > 1 by the best total after d - 1
+// more widenings (each trial runs on top of the previous one's membership).
+// A search that would visit more than max_visits gates is abandoned (empty result).
 std::vector<OpenBlock> partition_frontier(const qs_circuit* c, const std::vector<uint64_t>& masks,
-                                          const std::vector<GateTags>& tags, int k) {
+                                          const std::vector<GateTags>& tags, int k, int depth = 1,
+                                          long long max_visits = -1) {
     std::vector<OpenBlock> out;
     std::vector<int> rem(c->n_gates);
     for (int i = 0; i < c->n_gates; i++) rem[i] = i;
@@ -337,6 +365,7 @@ std::vector<OpenBlock> partition_frontier(const qs_circuit* c, const std::vector
     const uint64_t all = c->n >= 64 ? ~0ull : ((1ull << c->n) - 1);
     Frontier f{masks, tags, rem, all, in, trial};
     while (!rem.empty()) {
+        if (max_visits >= 0 && f.visits > max_visits) return {};
         uint64_t q = masks[rem[0]];
         in[rem[0]] = f.blk;
         f.close_over(q, false);
@@ -347,7 +376,8 @@ std::vector<OpenBlock> partition_frontier(const qs_circuit* c, const std::vector
             uint64_t best_q = 0;
             for (uint64_t u : cand) {
                 f.tid++;
-                const int got = f.close_over(u, true);
+                int got = f.close_over(u, true);
+                if (depth > 1 && __builtin_popcountll(u) < k) got += lookahead(f, rem, u, k, depth - 1);
                 // more gates first, then the narrower set
                 if (got > best || (got == best && __builtin_popcountll(u) < __builtin_popcountll(best_q))) {
                     best = got;
@@ -408,6 +438,11 @@ std::vector<OpenBlock> partition(const qs_circuit* c, const std::vector<uint64_t
     std::vector<OpenBlock> a = partition_greedy(c, masks, k);
     std::vector<OpenBlock> b = partition_frontier(c, masks, tags, k);
     std::vector<OpenBlock> best = b.size() < a.size() ? std::move(b) : std::move(a);
+    // wider lookahead: depth 2 always, depth 3 within a budget of visited gates (about 0.1 s)
+    for (int depth = 2; depth <= 3; depth++) {
+        std::vector<OpenBlock> d = partition_frontier(c, masks, tags, k, depth, depth == 2 ? -1 : 15000000);
+        if (!d.empty() && d.size() < best.size()) best = std::move(d);
+    }
     std::lock_guard<std::mutex> lk(g_part_mu);
     g_part_cache.emplace_front(std::move(key), best);
     if (g_part_cache.size() > kPartCacheSize) g_part_cache.pop_back();
