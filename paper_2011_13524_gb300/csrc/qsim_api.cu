@@ -954,7 +954,11 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
     const Arith ar = arith_of(psi);
     // forward: psi = U_G ... U_1 |0>, fused (the partition of a circuit structure is cached, so
     // repeated calls with new angles only rebuild the block matrices)
-    const int kf = (ar == Arith::DF && tensor_c128_enabled()) || ar == Arith::F32 ? 4 : 2;
+    // (tensor-core widths: 5 for double-float, 6 for complex64; the CUDA-core kernels' own)
+    const int kf = ar == Arith::DF && tensor_c128_enabled()     ? 5
+                   : ar == Arith::F32 && tensor_c64x_enabled() ? 6
+                   : ar == Arith::F32                           ? 4
+                                                                : 2;
     apply_plan(psi, plan_fusion(c, kf, theta));
     // lambda = H psi ; E = Re <psi|lambda>
     launch_apply_observable(groups, psi->data, lam->data, c->n, ar, st);

@@ -306,6 +306,31 @@ __global__ void __launch_bounds__(kRedThreads) k_apply_obs(const C* __restrict__
     }
 }
 
+// double-float states: the same sum in double-float arithmetic on the FP32 pipes (exact
+// products with the split coefficient, compensated sums)
+struct ObsDevTermDF {
+    uint64_t xmask, zmask;
+    float ch, cl;  // coefficient = ch + cl
+    int32_t nY, pad;
+};
+
+__global__ void __launch_bounds__(kRedThreads) k_apply_obs_df(const float4* __restrict__ psi, float4* __restrict__ lam,
+                                                              uint64_t N, const ObsDevTermDF* __restrict__ terms,
+                                                              int nterms) {
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t y = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; y < N; y += stride) {
+        DFArith::Acc a = DFArith::zero();
+        for (int t = 0; t < nterms; t++) {
+            const ObsDevTermDF T = terms[t];
+            const uint64_t y2 = y ^ T.xmask;
+            const float4 v = DFArith::ipow(psi[y2], T.nY + 2 * parity64(y2 & T.zmask));
+            DFArith::dprod(a.rs, a.rc, T.ch, T.cl, v.x, v.y);
+            DFArith::dprod(a.is, a.ic, T.ch, T.cl, v.z, v.w);
+        }
+        lam[y] = DFArith::out(a);
+    }
+}
+
 // ---------------------------------------------------------------- host side
 // calls f(C*) with the state's buffer typed by its arithmetic layout
 template <typename F>
@@ -622,10 +647,26 @@ void launch_apply_observable(const std::vector<PauliGroup>& groups, const void* 
     QS_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_terms), terms.size() * sizeof(ObsDevTerm), st));
     QS_TRY_CUDA(cudaMemcpyAsync(d_terms, terms.data(), terms.size() * sizeof(ObsDevTerm), cudaMemcpyHostToDevice, st));
     const unsigned g = red_grid(N);
-    with_type(ar, psi, [&](auto pp) {
-        using C = std::remove_const_t<std::remove_pointer_t<decltype(pp)>>;
-        k_apply_obs<<<g, kRedThreads, 0, st>>>(pp, reinterpret_cast<C*>(lam), N, d_terms, int(terms.size()));
-    });
+    if (ar == Arith::DF) {
+        std::vector<ObsDevTermDF> tdf(terms.size());
+        for (size_t t = 0; t < terms.size(); t++) {
+            tdf[t].xmask = terms[t].xmask;
+            tdf[t].zmask = terms[t].zmask;
+            split_double(terms[t].coef, tdf[t].ch, tdf[t].cl);
+            tdf[t].nY = terms[t].nY;
+            tdf[t].pad = 0;
+        }
+        static_assert(sizeof(ObsDevTermDF) <= sizeof(ObsDevTerm), "the term buffer holds either form");
+        QS_TRY_CUDA(cudaMemcpyAsync(d_terms, tdf.data(), tdf.size() * sizeof(ObsDevTermDF), cudaMemcpyHostToDevice, st));
+        QS_TRY_CUDA(cudaStreamSynchronize(st));  // tdf is host memory that dies on return
+        k_apply_obs_df<<<g, kRedThreads, 0, st>>>(static_cast<const float4*>(psi), static_cast<float4*>(lam), N,
+                                                  reinterpret_cast<const ObsDevTermDF*>(d_terms), int(terms.size()));
+    } else {
+        with_type(ar, psi, [&](auto pp) {
+            using C = std::remove_const_t<std::remove_pointer_t<decltype(pp)>>;
+            k_apply_obs<<<g, kRedThreads, 0, st>>>(pp, reinterpret_cast<C*>(lam), N, d_terms, int(terms.size()));
+        });
+    }
     QS_TRY_CUDA(cudaGetLastError());
     QS_TRY_CUDA(cudaFreeAsync(d_terms, st));
 }
