@@ -158,9 +158,11 @@ __device__ __forceinline__ float pow2_ceil(float m) {
 }
 
 // two adjacent amplitudes (32 bytes, 32-byte aligned) in one 256-bit access: used when the
-// block's lowest target is qubit 0, where each thread's amplitudes come in such pairs
+// block's lowest target is qubit 0, where each thread's amplitudes come in such pairs. Loads of
+// the state bypass L1 (.cg): every amplitude is read once, and for low targets a warp's access
+// spans 32 lines whose other sectors other warps read later, which in L1 only evicts lines early.
 __device__ __forceinline__ void ld_pair(const float4* p, float4& a, float4& b) {
-    asm("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+    asm("ld.global.cg.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
         : "l"(p));
 }
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
         } else {
 #pragma unroll
             for (int i = 0; i < kOzAmpsPerThread; i++)
-                v[i] = x0 != ~0ull ? psi[x0 + off[i]] : make_float4(0.f, 0.f, 0.f, 0.f);
+                v[i] = x0 != ~0ull ? __ldcg(psi + x0 + off[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     };
     // slices of this thread's amplitudes into abuf(j); returns the group scale nu
@@ -473,7 +475,7 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
         } else {
 #pragma unroll
             for (int i = 0; i < kOz5Amps; i++)
-                v[i] = x0 != ~0ull ? psi[x0 + off[i]] : make_float4(0.f, 0.f, 0.f, 0.f);
+                v[i] = x0 != ~0ull ? __ldcg(psi + x0 + off[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     };
     auto slice = [&](const float4 (&v)[kOz5Amps]) {
