@@ -248,3 +248,39 @@ def test_expectation_plan_packs_flip_groups_into_tiles():
     assert single == 0 and len(masks) <= 3
     with pytest.raises(qs.QsError):
         qs.expectation_plan(35, obs)
+
+
+def test_diagonal_runs_share_one_pass_in_block_costs():
+    """Consecutive uncontrolled diagonal and phase blocks of a plan run as one pass: the block
+    costs (host only) report one launch and one full pass for the first block of each run, none
+    for the others, and never join more than 12 qubits in a run."""
+    n = 16
+    gates = []
+    for layer in range(4):
+        for q in range(n):
+            gates.append(W.Gate("RZ", (q,), params=(0.1 * (q + layer),)))
+        for q in range(layer % 2, n - 1, 2):
+            gates.append(W.Gate("CZ", (q, q + 1)))
+    plan = qs.FusedCircuit(W.Circuit(n, gates), 4)
+    costs = [plan.block_cost(b, qs.QS_C128) for b in range(plan.n_blocks)]
+    full = 2 * 16 * 2 ** n
+    launches = [l for _, l, _ in costs]
+    assert sum(launches) < plan.n_blocks
+    # a run starts at each block with a launch; its blocks up to the next launch share it
+    runs, cur = [], None
+    for b, (kind, l, by) in enumerate(costs):
+        assert kind in ("diag", "phase")
+        if l:
+            cur = [b]
+            runs.append(cur)
+            assert 0 < by <= full
+        else:
+            assert by == 0 and cur is not None
+            cur.append(b)
+    for r in runs:
+        qubits = set()
+        for b in r:
+            qubits |= set(plan.block(b)[0])
+        assert len(qubits) <= 12
+        if len(r) > 1:
+            assert costs[r[0]][2] == full
