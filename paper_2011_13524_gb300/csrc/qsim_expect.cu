@@ -10,13 +10,16 @@
 //
 // A tile is the 2^b amplitudes whose bits outside a set T of b <= 12 qubits (always holding
 // qubits 0..2, so that a tile is read in runs of 8 contiguous amplitudes) equal a fixed rest
-// index r. Every group with f inside T is evaluated from the tile in shared memory, so one read
-// of the state serves all of them: a transverse-field Ising chain of 30 qubits (31 groups) takes
-// 3 passes. Within a group a thread owns 2^nitem items (amplitudes, or pair representatives)
-// that differ in the group's item bits; the signs that vary over the items are handled by a
-// Walsh-Hadamard transform of the thread's item values, the signs over the thread's own bits and
-// over the rest index by per-term factors. Terms that share (component, item mask, thread mask)
-// share one slot, whose coefficient sum over the rest-index signs is formed once per tile.
+// index r; it occupies 2^12 slots in shared memory, the slots of a smaller state's missing
+// (virtual) tile bits holding zeros. Every group with f inside T is evaluated from the tile, so
+// one read of the state serves all of them: a transverse-field Ising chain of 30 qubits (31
+// groups) takes 3 reads. Within a group each of the 256 threads owns 16 amplitudes (diagonal
+// group) or 8 pair representatives that differ in the group's item bits; the signs that vary
+// over the items are handled by a Walsh-Hadamard transform of the thread's item values, the signs
+// over the thread's own bits and over the rest index by per-term factors. Terms that share
+// (component, item mask, thread mask) share one slot, whose coefficient sum over the rest-index
+// signs is formed once per tile. The transition amplitude (second half of this file) uses the
+// same packing on tiles of 2^11 slots of two states.
 //
 // Item values and their transforms are exact sums on a power-of-two grid: each value
 // h + l (double-float) is split into H = RN(h + c) - c with c = 1.5 * 2^e above the thread's
