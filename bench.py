@@ -39,11 +39,11 @@ HBM_PEAK_FALLBACK = 6800.0
 # DRAM bytes (read + write) per launch from one ncu capture, keyed by kernel; filled in only
 # for a kernel unchanged since the capture (profiles/<kernel>_<workload>.md gives the command).
 # k_dense_reg<DFArith, 2>: captured at n = 27 (2 GiB state, 4.233e9 bytes per launch);
-# k_dense_oz4 and k_dense_oz5: captured at n = 24 (256 MiB state, 4.759e8 and 4.745e8 bytes per
+# k_dense_oz4 and k_dense_oz5: captured at n = 24 (256 MiB state, 4.750e8 and 4.756e8 bytes per
 # launch). Traffic grows with the state, so the n = 30 entries are those figures times 8 and 64.
 NCU_TRAFFIC = {("dense_df", 27): 4232672512, ("dense_df", 30): 4232672512 * 8,
-               ("dense_oz", 24): 475897344, ("dense_oz", 30): 475897344 * 64,
-               ("dense_oz5", 24): 474511104, ("dense_oz5", 30): 474511104 * 64}
+               ("dense_oz", 24): 475004672, ("dense_oz", 30): 475004672 * 64,
+               ("dense_oz5", 24): 475586560, ("dense_oz5", 30): 475586560 * 64}
 
 
 def parse():
