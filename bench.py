@@ -304,7 +304,12 @@ def run_ours(args):
                 "per_kernel_ms": {k_: round(v["ms"], 3) for k_, v in per_kernel.items()}}
         bytes_per_step = sum(c[2] for c in costs)
         kernels_per_step = sum(c[1] for c in costs)
-    conversions = 2 if math_mode == qs.QS_MATH_DF else 0   # in-place layout change at entry and exit
+    # separate in-place layout changes of a double-float run (entry and exit, unless folded into
+    # the plan's first and last passes; per gate when gates are applied one by one)
+    if plan is not None:
+        conversions = plan.layout_passes(dtype)
+    else:
+        conversions = 2 * G if math_mode == qs.QS_MATH_DF else 0
     launches_per_step = (kernels_per_step if kernels_per_step is not None else G) + 1 + 2 + conversions
 
     # e2e through the public API: host circuit in, host result out, planning included

@@ -247,6 +247,14 @@ qs_status qs_destroy_fused(qs_fused_circuit* f);
 #define QS_KERNEL_DENSE_BZ 11  /* complex64 block of 5 or 6 targets on the tensor cores (bf16 slices) */
 qs_status qs_fused_block_cost(const qs_fused_circuit* f, int b, qs_dtype dt, int* kernel, int* launches,
                               double* bytes);
+/* Separate layout-change passes (0, 1 or 2) that applying the plan to a complex128 state adds
+ * under the current settings: a double-float run (QS_MATH_DF) holds the state as hi/lo float
+ * pairs between a change at entry and one at exit, each a full read and write of the state,
+ * unless the first block is an uncontrolled 4- or 5-target tensor-core block (it reads the
+ * IEEE doubles itself) or the last pass is a run of diagonal blocks (it writes IEEE doubles);
+ * 0 for complex64 and FP64 runs. Block b's kernel in qs_fused_block_cost includes what it
+ * folds in. */
+qs_status qs_fused_layout_passes(const qs_fused_circuit* f, qs_dtype dt, int* passes);
 /* Applies a plan like qs_apply_fused_circuit, recording a CUDA event on the state's stream
  * after every block; block_ms[b] receives the device time of block b. Synchronises. */
 qs_status qs_apply_fused_circuit_timed(qs_state* s, const qs_fused_circuit* f, float* block_ms);

@@ -114,6 +114,7 @@ _SIGNATURES = {
                        ctypes.c_int),
     "qs_apply_fused_circuit": ([_VOIDP, _VOIDP], ctypes.c_int),
     "qs_destroy_fused": ([_VOIDP], ctypes.c_int),
+    "qs_fused_layout_passes": ([_VOIDP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "qs_fused_block_cost": ([_VOIDP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_int), _DP], ctypes.c_int),
     "qs_apply_fused_circuit_timed": ([_VOIDP, _VOIDP, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
@@ -466,6 +467,12 @@ class FusedCircuit:
         check(lib().qs_fused_block_cost(self.handle, b, int(dtype), ctypes.byref(k), ctypes.byref(l),
                                         ctypes.byref(by)))
         return KERNEL_NAMES[k.value], l.value, by.value
+
+    def layout_passes(self, dtype: int) -> int:
+        """Separate layout-change passes a run of this plan adds (double-float complex128)."""
+        p = ctypes.c_int(0)
+        check(lib().qs_fused_layout_passes(self.handle, int(dtype), ctypes.byref(p)))
+        return p.value
 
     def widths(self):
         out = []

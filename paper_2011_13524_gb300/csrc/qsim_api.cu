@@ -77,14 +77,25 @@ Op dagger(const Op& op) {
 // between one conversion pass at entry and one at exit; every entry point sees IEEE doubles.
 bool use_df(const qs_state* s) { return s->dt == QS_C128 && c128_math() == QS_MATH_DF; }
 
+// With `deferred`, the entry conversion is left to the first launch (launch_op_arith with
+// ieee_in), and entered() marks the buffer as converted once that launch is queued; left()
+// marks a last launch that wrote IEEE doubles itself.
 struct DFScope {
     qs_state* s;
     bool active;
-    explicit DFScope(qs_state* st, bool on) : s(st), active(on && !st->df) {
+    explicit DFScope(qs_state* st, bool on, bool deferred = false) : s(st), active(on && !st->df && !deferred) {
         if (active) {
             launch_to_df(s->data, s->n, s->stream);
             s->df = 1;
         }
+    }
+    void entered() {
+        active = true;
+        s->df = 1;
+    }
+    void left() {
+        active = false;
+        s->df = 0;
     }
     ~DFScope() {
         if (active) {
@@ -258,6 +269,23 @@ std::vector<int> diag_runs(const std::vector<Op>& ops) {
 
 namespace {
 
+// A double-float run folds the layout changes into its first and last passes where those read
+// every amplitude once: a tensor-core block first (it splits the IEEE doubles as it loads them),
+// a tabulated diagonal run last (it writes RN(hi + lo)).
+struct LayoutFold {
+    bool in = false, out = false;
+    size_t last = 0;  // the last op that launches
+};
+LayoutFold layout_fold(const std::vector<Op>& ops, const std::vector<int>& runs) {
+    LayoutFold f;
+    if (ops.empty()) return f;
+    for (size_t b = 0; b < ops.size(); b++)
+        if (runs[b] > 0) f.last = b;
+    f.in = runs[0] == 1 && takes_ieee_in(ops[0]);
+    f.out = runs[f.last] > 1;
+    return f;
+}
+
 void apply_plan_impl(qs_state* s, const FusionPlan& p, float* block_ms) {
     QS_REQUIRE(p.n == s->n, "plan and state have different qubit counts");
     std::vector<Op> ops;
@@ -267,18 +295,26 @@ void apply_plan_impl(qs_state* s, const FusionPlan& p, float* block_ms) {
     WideMats wm = upload_wide(s, df_run ? Arith::DF : arith_of(s), ops);
     std::vector<cudaEvent_t> ev;
     try {
-        DFScope df(s, df_run);
+        const std::vector<int> runs = diag_runs(ops);
+        const LayoutFold fold = df_run && !s->df ? layout_fold(ops, runs) : LayoutFold{};
+        const bool in_fused = fold.in, out_fused = fold.out;
+        const size_t last = fold.last;
+        const Arith ar = df_run ? Arith::DF : arith_of(s);
+        DFScope df(s, df_run, in_fused);
         if (block_ms) {
             ev.resize(ops.size() + 1);
             for (auto& e : ev) QS_TRY_CUDA(cudaEventCreate(&e));
             QS_TRY_CUDA(cudaEventRecord(ev[0], s->stream));
         }
-        const std::vector<int> runs = diag_runs(ops);
         for (size_t b = 0; b < ops.size(); b++) {
-            if (runs[b] == 1)
-                launch_op_arith(ops[b], s->data, s->n, arith_of(s), s->stream, stage_of(s));
-            else if (runs[b] > 1)  // diagonal blocks in one pass (its time goes to the first)
-                launch_diag_run(&ops[b], size_t(runs[b]), s->data, s->n, arith_of(s), s->stream, stage_of(s));
+            if (runs[b] == 1) {
+                launch_op_arith(ops[b], s->data, s->n, ar, s->stream, stage_of(s), in_fused && b == 0);
+                if (in_fused && b == 0) df.entered();
+            } else if (runs[b] > 1) {  // diagonal blocks in one pass (its time goes to the first)
+                const bool to_ieee = out_fused && b == last;
+                launch_diag_run(&ops[b], size_t(runs[b]), s->data, s->n, ar, s->stream, stage_of(s), to_ieee);
+                if (to_ieee) df.left();
+            }
             if (block_ms) QS_TRY_CUDA(cudaEventRecord(ev[b + 1], s->stream));
         }
         if (block_ms) {
@@ -776,6 +812,20 @@ qs_status qs_fused_block_cost(const qs_fused_circuit* f, int b, qs_dtype dt, int
         if (kernel) *kernel = QS_KERNEL_DIAG;
         if (launches) *launches = 1;
         if (bytes) *bytes = 2.0 * double(amp_bytes(dt)) * std::ldexp(1.0, f->plan.n);
+    }
+    API_END
+}
+
+qs_status qs_fused_layout_passes(const qs_fused_circuit* f, qs_dtype dt, int* passes) {
+    API_BEGIN
+    QS_REQUIRE(f != nullptr && passes != nullptr, "null plan or output");
+    QS_REQUIRE(dt == QS_C64 || dt == QS_C128, "unknown dtype");
+    *passes = 0;
+    if (dt == QS_C128 && c128_math() == QS_MATH_DF) {
+        std::vector<Op> ops;
+        for (size_t i = 0; i < f->plan.blocks.size(); i++) ops.push_back(block_op(f->plan, i));
+        const LayoutFold fold = layout_fold(ops, diag_runs(ops));
+        *passes = 2 - int(fold.in) - int(fold.out);
     }
     API_END
 }

@@ -182,29 +182,40 @@ __device__ __forceinline__ double widen_float_int(float f) {
     return __longlong_as_double(static_cast<long long>(b));
 }
 
-// RN(hi + lo) as a double for a double-float pair, on the integer pipes when the exact sum fits
-// the 53-bit significand: both normal and lo's exponent 24..29 below hi's (every pair with
-// |lo| <= ulp(hi) has it at least 24 below), so lo's significand, shifted into hi's, stays an
-// integer and the sum or difference is exact (a difference that drops below 2^52 is shifted back
-// by one bit, still exact). Otherwise (lo smaller, zero hi, subnormal, non-finite) the FP64 add.
+// RN(hi + lo) as a double for a double-float pair, on the integer pipes when both are normal and
+// lo's exponent is 24..55 below hi's (every pair with |lo| <= ulp(hi)/2 has it at least 24 below):
+// hi's significand is placed at bits 62..39 of a 64-bit word and lo's shifted in beside it, with
+// the bits shifted out folded into bit 0 (a sticky bit, enough to round correctly with 10 bits
+// below the result's last place); the sum or difference (a difference below 2^62 moves up one
+// bit) is then rounded to 53 bits, to nearest with ties to even. Otherwise (zero hi, subnormal,
+// non-finite, lo far smaller) the FP64 add.
 __device__ __forceinline__ double join_df_int(float hi, float lo) {
     const uint32_t uh = __float_as_uint(hi), ul = __float_as_uint(lo);
     if ((ul << 1) == 0u) return widen_float_int(hi);
     const uint32_t eh = (uh >> 23) & 0xFFu, el = (ul >> 23) & 0xFFu;
-    if (eh == 0u || eh == 255u || el == 0u || (eh - el) - 24u > 5u) return widen_float_int(hi) + widen_float_int(lo);
-    uint64_t mh = uint64_t((uh & 0x7FFFFFu) | 0x800000u) << 29;
-    const uint64_t ml = (uint64_t((ul & 0x7FFFFFu) | 0x800000u) << 29) >> (eh - el);
-    uint64_t e = uint64_t(eh - 127u + 1023u);
+    const uint32_t d = eh - el;
+    if (eh == 0u || eh == 255u || el == 0u || d - 24u > 31u) return widen_float_int(hi) + widen_float_int(lo);
+    uint64_t mh = uint64_t((uh & 0x7FFFFFu) | 0x800000u) << 39;
+    const uint64_t lf = uint64_t((ul & 0x7FFFFFu) | 0x800000u) << 39;
+    const uint64_t ml = (lf >> d) | uint64_t((lf << (64u - d)) != 0u);
+    uint64_t e = uint64_t(eh) + 896u;  // biased double exponent of hi
     if ((uh ^ ul) >> 31) {
         mh -= ml;
-        if (mh < (1ull << 52)) {
+        if (mh < (1ull << 62)) {
             mh <<= 1;
             e -= 1;
         }
     } else {
         mh += ml;
     }
-    return __longlong_as_double(static_cast<long long>((uint64_t(uh >> 31) << 63) | (e << 52) | (mh & ((1ull << 52) - 1))));
+    uint64_t r = mh >> 10;
+    const uint32_t rem = uint32_t(mh & 0x3FFu);
+    r += (rem > 0x200u || (rem == 0x200u && (r & 1u))) ? 1u : 0u;
+    if (r >> 53) {
+        r >>= 1;
+        e += 1;
+    }
+    return __longlong_as_double(static_cast<long long>((uint64_t(uh >> 31) << 63) | (e << 52) | (r & ((1ull << 52) - 1))));
 }
 
 }  // namespace qs

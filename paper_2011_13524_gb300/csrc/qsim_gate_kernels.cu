@@ -19,6 +19,10 @@ namespace qs {
 namespace {
 
 constexpr int kThreads = 256;
+// elementwise in-place passes take this many amplitudes per thread and step, so that as many
+// loads are in flight before the first store (the stores alias the loaded buffer, so the
+// compiler keeps the order)
+constexpr int kConvUnroll = 4;
 
 int sm_count() {
     static int sms = 0;
@@ -156,28 +160,45 @@ struct DiagTableParams {
     int32_t tpos[kDiagTableBits];
 };
 
-template <typename P>
+// kIeeeOut (double-float only): the products are written as IEEE complex128, RN(hi + lo) per
+// component (the join of the layout-change pass), into the same 16 bytes
+template <typename P, bool kIeeeOut>
 __global__ void __launch_bounds__(kThreads) k_diag_table(typename P::C* __restrict__ psi,
                                                          const typename P::K* __restrict__ table,
                                                          const __grid_constant__ DiagTableParams<P> Pm) {
+    using C = typename P::C;
     extern __shared__ __align__(16) unsigned char dsm[];
     typename P::K* t = reinterpret_cast<typename P::K*>(dsm);
     for (int i = threadIdx.x; i < (1 << Pm.m); i += blockDim.x) t[i] = table[i];
     __syncthreads();
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t x = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < Pm.N; x += stride) {
-        uint32_t r = 0;
+    for (uint64_t x0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x0 < Pm.N; x0 += kConvUnroll * stride) {
+        C v[kConvUnroll];  // several loads in flight per thread
+#pragma unroll
+        for (int u = 0; u < kConvUnroll; u++)
+            if (x0 + u * stride < Pm.N) v[u] = __ldcg(psi + x0 + u * stride);
+#pragma unroll
+        for (int u = 0; u < kConvUnroll; u++) {
+            const uint64_t x = x0 + u * stride;
+            if (x >= Pm.N) continue;
+            uint32_t r = 0;
 #pragma unroll 4
-        for (int j = 0; j < Pm.m; j++) r |= uint32_t((x >> Pm.tpos[j]) & 1) << j;
-        typename P::Acc a = P::zero();
-        P::mac(a, t[r], psi[x]);
-        psi[x] = P::out(a);
+            for (int j = 0; j < Pm.m; j++) r |= uint32_t((x >> Pm.tpos[j]) & 1) << j;
+            typename P::Acc a = P::zero();
+            P::mac(a, t[r], v[u]);
+            if constexpr (kIeeeOut) {
+                const float4 o = P::out(a);
+                reinterpret_cast<double2*>(psi)[x] = make_double2(join_df_int(o.x, o.y), join_df_int(o.z, o.w));
+            } else {
+                psi[x] = P::out(a);
+            }
+        }
     }
 }
 
 template <typename P>
 void launch_diag_table_t(const std::vector<int>& u, const std::vector<cplx>& tab, void* psi, int n, cudaStream_t st,
-                         void* stage) {
+                         void* stage, bool ieee_out) {
     using K = typename P::K;
     const size_t bytes = tab.size() * sizeof(K);
     QS_REQUIRE(stage != nullptr && bytes <= kStageBytes, "no staging buffer for a diagonal table");
@@ -191,12 +212,20 @@ void launch_diag_table_t(const std::vector<int>& u, const std::vector<cplx>& tab
     for (size_t j = 0; j < u.size(); j++) Pm.tpos[j] = u[j];
     static bool attr = false;
     if (!attr) {
-        QS_TRY_CUDA(cudaFuncSetAttribute(k_diag_table<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_diag_table<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(sizeof(K) << kDiagTableBits)));
+        if constexpr (std::is_same<P, DFArith>::value)
+            QS_TRY_CUDA(cudaFuncSetAttribute(k_diag_table<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(sizeof(K) << kDiagTableBits)));
         attr = true;
     }
-    k_diag_table<P><<<grid_for(Pm.N), kThreads, bytes, st>>>(reinterpret_cast<typename P::C*>(psi),
-                                                             static_cast<const K*>(stage), Pm);
+    auto kern = k_diag_table<P, false>;
+    if constexpr (std::is_same<P, DFArith>::value) {
+        if (ieee_out) kern = k_diag_table<P, true>;
+    } else {
+        QS_REQUIRE(!ieee_out, "IEEE output is a double-float layout change");
+    }
+    kern<<<grid_for(Pm.N), kThreads, bytes, st>>>(reinterpret_cast<typename P::C*>(psi), static_cast<const K*>(stage), Pm);
     QS_TRY_CUDA(cudaGetLastError());
 }
 
@@ -314,9 +343,7 @@ __global__ void k_set_basis(typename P::C* __restrict__ psi, uint64_t N, uint64_
 
 // IEEE complex128 <-> double-float, in place (same 16 bytes per amplitude), with the
 // integer-pipe splits of qsim_arith.cuh
-// In-place layout changes, four amplitudes per thread and step so that four loads are in flight
-// before the first store (the stores alias the loaded buffer, so the compiler keeps the order).
-constexpr int kConvUnroll = 4;
+// In-place layout changes, four amplitudes per thread and step (kConvUnroll).
 __global__ void k_to_df(double2* __restrict__ psi, uint64_t N) {
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     for (uint64_t i0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < N; i0 += kConvUnroll * stride) {
@@ -391,7 +418,7 @@ void launch_dense_smem(const Op& op, const IndexPlan& ip, void* psi, const void*
 }
 
 template <typename P>
-void launch_with(const Op& op, void* psi, int n, cudaStream_t st, void* stage) {
+void launch_with(const Op& op, void* psi, int n, cudaStream_t st, void* stage, bool ieee_in) {
     using C = typename P::C;
     using K = typename P::K;
     std::vector<int> fixed;
@@ -445,7 +472,7 @@ void launch_with(const Op& op, void* psi, int n, cudaStream_t st, void* stage) {
                     QS_TRY_CUDA(cudaStreamSynchronize(st));  // hk is host memory that dies on return
                     dK = stage;
                 }
-                return launch_dense_oz4(psi, n, os.targets, os.controls, os.cvals, dK, st);
+                return launch_dense_oz4(psi, n, os.targets, os.controls, os.cvals, dK, st, ieee_in);
             }
             // double-float blocks of 5 targets: tensor cores, outputs in two halves
             if (std::is_same<P, DFArith>::value && m == 5 && tensor_c128_enabled()) {
@@ -459,7 +486,7 @@ void launch_with(const Op& op, void* psi, int n, cudaStream_t st, void* stage) {
                     QS_TRY_CUDA(cudaStreamSynchronize(st));  // hk is host memory that dies on return
                     dK = stage;
                 }
-                return launch_dense_oz5(psi, n, os.targets, os.controls, os.cvals, dK, st);
+                return launch_dense_oz5(psi, n, os.targets, os.controls, os.cvals, dK, st, ieee_in);
             }
             if (m == 1) return launch_dense_reg<P, 1>(op, ip, psi, st);
             if (m == 2) return launch_dense_reg<P, 2>(op, ip, psi, st);
@@ -556,18 +583,31 @@ void launch_with(const Op& op, void* psi, int n, cudaStream_t st, void* stage) {
 
 }  // namespace
 
-void launch_op_arith(const Op& op, void* psi, int n, Arith ar, cudaStream_t st, void* stage) {
+// the double-float launch of op reads every amplitude once in a kernel that can take the IEEE
+// layout itself: an uncontrolled dense block of 4 or 5 targets on the tensor cores
+bool takes_ieee_in(const Op& op) {
+    const size_t m = op.targets.size();
+    return op.kind == OpKind::Dense && op.controls.empty() && (m == 4 || m == 5) && tensor_c128_enabled();
+}
+
+void launch_op_arith(const Op& op, void* psi, int n, Arith ar, cudaStream_t st, void* stage, bool ieee_in) {
+    QS_REQUIRE(!ieee_in || ar == Arith::DF, "IEEE input is a double-float layout change");
+    if (ieee_in && !takes_ieee_in(op)) {
+        launch_to_df(psi, n, st);
+        ieee_in = false;
+    }
     switch (ar) {
-        case Arith::F32: launch_with<NativeArith<float>>(op, psi, n, st, stage); break;
-        case Arith::F64: launch_with<NativeArith<double>>(op, psi, n, st, stage); break;
-        case Arith::DF: launch_with<DFArith>(op, psi, n, st, stage); break;
+        case Arith::F32: launch_with<NativeArith<float>>(op, psi, n, st, stage, false); break;
+        case Arith::F64: launch_with<NativeArith<double>>(op, psi, n, st, stage, false); break;
+        case Arith::DF: launch_with<DFArith>(op, psi, n, st, stage, ieee_in); break;
     }
     QS_TRY_CUDA(cudaGetLastError());
 }
 
 // Diagonal ops (no controls) applied as one pass: the product of their diagonals over the union
 // of their targets (at most kDiagTableBits qubits).
-void launch_diag_run(const Op* ops, size_t count, void* psi, int n, Arith ar, cudaStream_t st, void* stage) {
+void launch_diag_run(const Op* ops, size_t count, void* psi, int n, Arith ar, cudaStream_t st, void* stage,
+                     bool ieee_out) {
     // uncontrolled diagonals (on their targets) and phases (on their control qubits' values)
     auto qubits = [](const Op& op) -> const std::vector<int>& {
         return op.kind == OpKind::Phase ? op.controls : op.targets;
@@ -599,9 +639,9 @@ void launch_diag_run(const Op* ops, size_t count, void* psi, int n, Arith ar, cu
         }
     }
     switch (ar) {
-        case Arith::F32: launch_diag_table_t<NativeArith<float>>(u, tab, psi, n, st, stage); break;
-        case Arith::F64: launch_diag_table_t<NativeArith<double>>(u, tab, psi, n, st, stage); break;
-        case Arith::DF: launch_diag_table_t<DFArith>(u, tab, psi, n, st, stage); break;
+        case Arith::F32: launch_diag_table_t<NativeArith<float>>(u, tab, psi, n, st, stage, ieee_out); break;
+        case Arith::F64: launch_diag_table_t<NativeArith<double>>(u, tab, psi, n, st, stage, ieee_out); break;
+        case Arith::DF: launch_diag_table_t<DFArith>(u, tab, psi, n, st, stage, ieee_out); break;
     }
 }
 

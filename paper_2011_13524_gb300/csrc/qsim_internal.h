@@ -126,10 +126,16 @@ inline Arith arith_of(const qs_state* s) {
 // kernels when op.dmat is not set.
 constexpr size_t kStageBytes = 2 * 128 * 128 * 4;  // >= 64x64 complex128 and the tensor-core form
 void launch_op(const Op& op, void* psi, int n, qs_dtype dt, cudaStream_t st, void* stage);
-void launch_op_arith(const Op& op, void* psi, int n, Arith ar, cudaStream_t st, void* stage);
-// consecutive uncontrolled diagonal ops on at most kDiagTableBits qubits together: one pass
+// ieee_in (double-float arithmetic only): psi still holds IEEE complex128 and the op leaves it in
+// the double-float layout, the layout change done by the op's own kernel where it reads every
+// amplitude once (takes_ieee_in), else by a conversion pass before it
+void launch_op_arith(const Op& op, void* psi, int n, Arith ar, cudaStream_t st, void* stage, bool ieee_in = false);
+bool takes_ieee_in(const Op& op);
+// consecutive uncontrolled diagonal ops on at most kDiagTableBits qubits together: one pass;
+// ieee_out (double-float only): the pass writes its results as IEEE complex128
 constexpr int kDiagTableBits = 12;
-void launch_diag_run(const Op* ops, size_t count, void* psi, int n, Arith ar, cudaStream_t st, void* stage);
+void launch_diag_run(const Op* ops, size_t count, void* psi, int n, Arith ar, cudaStream_t st, void* stage,
+                     bool ieee_out = false);
 // for each op: the number of ops launched together from it (>= 1), or 0 if an earlier op's
 // diagonal run covers it
 std::vector<int> diag_runs(const std::vector<Op>& ops);
@@ -295,13 +301,14 @@ Op sort_targets(const Op& op);
 // host image of the sliced operand of a 16 x 16 matrix (stacked bf16 slices, row scales)
 size_t oz4_matrix_bytes();
 void prepare_oz4_matrix(const std::vector<cplx>& K, unsigned char* host_out);
+// ieee_in: the state is read as IEEE complex128 (no controls: every amplitude is rewritten)
 void launch_dense_oz4(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
-                      const std::vector<int>& cvals, const void* dmat, cudaStream_t st);
+                      const std::vector<int>& cvals, const void* dmat, cudaStream_t st, bool ieee_in = false);
 // 5-target blocks: the same method with the outputs in two halves (two stacked half matrices)
 size_t oz5_matrix_bytes();
 void prepare_oz5_matrix(const std::vector<cplx>& K, unsigned char* host_out);
 void launch_dense_oz5(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
-                      const std::vector<int>& cvals, const void* dmat, cudaStream_t st);
+                      const std::vector<int>& cvals, const void* dmat, cudaStream_t st, bool ieee_in = false);
 // complex64 5- and 6-target blocks: three bf16 slices per operand, exact FP32 sums, one FP32
 // rounding per output
 bool tensor_c64x_enabled();

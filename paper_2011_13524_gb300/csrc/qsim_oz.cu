@@ -172,7 +172,16 @@ __device__ __forceinline__ void st_pair(float4* p, const float4& a, const float4
                  : "memory");
 }
 
-template <bool kPairs>
+// the 16 bytes of an IEEE complex128 amplitude, loaded as four floats, in the double-float layout
+// {re_hi, re_lo, im_hi, im_lo} (the split of the layout-change pass)
+__device__ __forceinline__ float4 df_of_ieee(const float4& w) {
+    float4 r;
+    split_double_int(__hiloint2double(__float_as_int(w.y), __float_as_int(w.x)), r.x, r.y);
+    split_double_int(__hiloint2double(__float_as_int(w.w), __float_as_int(w.z)), r.z, r.w);
+    return r;
+}
+
+template <bool kPairs, bool kIeeeIn>
 __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict__ psi, const unsigned char* __restrict__ dmat,
                                                              const __grid_constant__ OzParams P, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -227,6 +236,10 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
 #pragma unroll
             for (int i = 0; i < kOzAmpsPerThread; i++)
                 v[i] = x0 != ~0ull ? __ldcg(psi + x0 + off[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (kIeeeIn) {
+#pragma unroll
+            for (int i = 0; i < kOzAmpsPerThread; i++) v[i] = df_of_ieee(v[i]);
         }
     };
     // slices of this thread's amplitudes into abuf(j); returns the group scale nu
@@ -419,7 +432,7 @@ __device__ __forceinline__ uint64_t sdesc5(uint32_t saddr) {
     return d;
 }
 
-template <bool kPairs>
+template <bool kPairs, bool kIeeeIn>
 __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict__ psi,
                                                                const unsigned char* __restrict__ dmat,
                                                                const __grid_constant__ Oz5Params P, int* err) {
@@ -476,6 +489,10 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
 #pragma unroll
             for (int i = 0; i < kOz5Amps; i++)
                 v[i] = x0 != ~0ull ? __ldcg(psi + x0 + off[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (kIeeeIn) {
+#pragma unroll
+            for (int i = 0; i < kOz5Amps; i++) v[i] = df_of_ieee(v[i]);
         }
     };
     auto slice = [&](const float4 (&v)[kOz5Amps]) {
@@ -873,6 +890,21 @@ __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(f
 int g_oz_sms = 0;
 int* g_oz_err = nullptr;
 
+// SM count, the error flag and the 4-target kernels' shared-memory limits, once per process
+void oz_init() {
+    if (g_oz_sms) return;
+    int dev = 0, sms = 0;
+    QS_TRY_CUDA(cudaGetDevice(&dev));
+    QS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
+    QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
+    QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
+    QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
+    QS_TRY_CUDA(cudaMalloc(&g_oz_err, sizeof(int)));
+    QS_TRY_CUDA(cudaMemset(g_oz_err, 0, sizeof(int)));
+    g_oz_sms = sms;
+}
+
 // the real form of K~ (16 x 16 complex): row n = 2z + c_out, column k = 2w + c_in
 double real_form(const std::vector<cplx>& K, int n, int k) {
     const cplx e = K[size_t(n >> 1) * kOzD + size_t(k >> 1)];
@@ -927,18 +959,10 @@ void prepare_oz4_matrix(const std::vector<cplx>& K, unsigned char* host_out) {
 
 // y = K v on every group of the 4 targets (ascending) of a double-float state.
 void launch_dense_oz4(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
-                      const std::vector<int>& cvals, const void* dmat, cudaStream_t st) {
+                      const std::vector<int>& cvals, const void* dmat, cudaStream_t st, bool ieee_in) {
     QS_REQUIRE(targets.size() == size_t(kOzQ), "tensor-core double-float path takes 4 targets");
     QS_REQUIRE(std::is_sorted(targets.begin(), targets.end()), "targets must be ascending");
-    if (!g_oz_sms) {
-        int dev = 0;
-        QS_TRY_CUDA(cudaGetDevice(&dev));
-        QS_TRY_CUDA(cudaDeviceGetAttribute(&g_oz_sms, cudaDevAttrMultiProcessorCount, dev));
-        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
-        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
-        QS_TRY_CUDA(cudaMalloc(&g_oz_err, sizeof(int)));
-        QS_TRY_CUDA(cudaMemset(g_oz_err, 0, sizeof(int)));
-    }
+    oz_init();
     std::vector<int> fixed(targets);
     uint64_t setmask = 0;
     for (size_t j = 0; j < controls.size(); j++) {
@@ -958,12 +982,12 @@ void launch_dense_oz4(void* psi, int n, const std::vector<int>& targets, const s
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, 2 * uint64_t(g_oz_sms))));
     // lowest target qubit 0 (and a 32-byte-aligned state): each thread's amplitudes come in
     // adjacent 32-byte-aligned pairs
-    if (targets[0] == 0 && (reinterpret_cast<uintptr_t>(psi) & 31) == 0)
-        k_dense_oz4<true><<<grid, kOzThreads, kOzSmem, st>>>(reinterpret_cast<float4*>(psi),
-                                                             static_cast<const unsigned char*>(dmat), P, g_oz_err);
-    else
-        k_dense_oz4<false><<<grid, kOzThreads, kOzSmem, st>>>(reinterpret_cast<float4*>(psi),
-                                                              static_cast<const unsigned char*>(dmat), P, g_oz_err);
+    QS_REQUIRE(!ieee_in || controls.empty(), "an IEEE-input block rewrites every amplitude (no controls)");
+    const bool pairs = targets[0] == 0 && (reinterpret_cast<uintptr_t>(psi) & 31) == 0;
+    auto kern = pairs ? (ieee_in ? k_dense_oz4<true, true> : k_dense_oz4<true, false>)
+                      : (ieee_in ? k_dense_oz4<false, true> : k_dense_oz4<false, false>);
+    kern<<<grid, kOzThreads, kOzSmem, st>>>(reinterpret_cast<float4*>(psi), static_cast<const unsigned char*>(dmat), P,
+                                            g_oz_err);
     QS_TRY_CUDA(cudaGetLastError());
 }
 
@@ -1010,22 +1034,16 @@ void prepare_oz5_matrix(const std::vector<cplx>& K, unsigned char* host_out) {
 }
 
 void launch_dense_oz5(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
-                      const std::vector<int>& cvals, const void* dmat, cudaStream_t st) {
+                      const std::vector<int>& cvals, const void* dmat, cudaStream_t st, bool ieee_in) {
     QS_REQUIRE(targets.size() == size_t(kOz5Q), "5-target tensor-core path takes 5 targets");
     QS_REQUIRE(std::is_sorted(targets.begin(), targets.end()), "targets must be ascending");
     static bool attr = false;
-    if (!g_oz_sms) {
-        int dev = 0;
-        QS_TRY_CUDA(cudaGetDevice(&dev));
-        QS_TRY_CUDA(cudaDeviceGetAttribute(&g_oz_sms, cudaDevAttrMultiProcessorCount, dev));
-        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
-        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
-        QS_TRY_CUDA(cudaMalloc(&g_oz_err, sizeof(int)));
-        QS_TRY_CUDA(cudaMemset(g_oz_err, 0, sizeof(int)));
-    }
+    oz_init();
     if (!attr) {
-        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz5<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOz5Smem)));
-        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz5<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOz5Smem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz5<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOz5Smem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz5<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOz5Smem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz5<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOz5Smem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz5<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOz5Smem)));
         attr = true;
     }
     std::vector<int> fixed(targets);
@@ -1045,12 +1063,12 @@ void launch_dense_oz5(void* psi, int n, const std::vector<int>& targets, const s
     }
     const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, uint64_t(g_oz_sms))));
-    if (targets[0] == 0 && (reinterpret_cast<uintptr_t>(psi) & 31) == 0)
-        k_dense_oz5<true><<<grid, kOz5Threads, kOz5Smem, st>>>(reinterpret_cast<float4*>(psi),
-                                                               static_cast<const unsigned char*>(dmat), P, g_oz_err);
-    else
-        k_dense_oz5<false><<<grid, kOz5Threads, kOz5Smem, st>>>(reinterpret_cast<float4*>(psi),
-                                                                static_cast<const unsigned char*>(dmat), P, g_oz_err);
+    QS_REQUIRE(!ieee_in || controls.empty(), "an IEEE-input block rewrites every amplitude (no controls)");
+    const bool pairs = targets[0] == 0 && (reinterpret_cast<uintptr_t>(psi) & 31) == 0;
+    auto kern = pairs ? (ieee_in ? k_dense_oz5<true, true> : k_dense_oz5<true, false>)
+                      : (ieee_in ? k_dense_oz5<false, true> : k_dense_oz5<false, false>);
+    kern<<<grid, kOz5Threads, kOz5Smem, st>>>(reinterpret_cast<float4*>(psi), static_cast<const unsigned char*>(dmat), P,
+                                              g_oz_err);
     QS_TRY_CUDA(cudaGetLastError());
 }
 
@@ -1102,15 +1120,7 @@ void launch_bz_t(void* psi, int n, const std::vector<int>& targets, const std::v
                  const std::vector<int>& cvals, const void* dmat, cudaStream_t st) {
     using B = Bz<Q>;
     static bool attr = false;
-    if (!g_oz_sms) {
-        int dev = 0;
-        QS_TRY_CUDA(cudaGetDevice(&dev));
-        QS_TRY_CUDA(cudaDeviceGetAttribute(&g_oz_sms, cudaDevAttrMultiProcessorCount, dev));
-        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
-        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
-        QS_TRY_CUDA(cudaMalloc(&g_oz_err, sizeof(int)));
-        QS_TRY_CUDA(cudaMemset(g_oz_err, 0, sizeof(int)));
-    }
+    oz_init();
     if (!attr) {
         QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_bz<Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(B::Smem)));
         QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_bz<Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(B::Smem)));

@@ -284,3 +284,28 @@ def test_diagonal_runs_share_one_pass_in_block_costs():
         assert len(qubits) <= 12
         if len(r) > 1:
             assert costs[r[0]][2] == full
+
+
+def test_layout_passes_folded_into_first_and_last_blocks():
+    """A double-float complex128 run of a plan adds separate layout-change passes only where its
+    first block is not an uncontrolled 4- or 5-target tensor-core block (entry) and its last
+    launch is not a run of diagonal blocks (exit); complex64 and FP64 runs add none (host only)."""
+    old_m, old_t = qs.get_c128_math(), qs.get_tensor_cores()
+    try:
+        qs.set_c128_math(qs.QS_MATH_DF)
+        qs.set_tensor_cores(qs.QS_TENSOR_C128)
+        p4 = qs.FusedCircuit(W.u3cz_circuit(14, 6, 35), 4)    # dense_oz ... diag, phase
+        p5 = qs.FusedCircuit(W.u3cz_circuit(14, 6, 36), 5)    # dense_oz5 ... dense_oz5
+        p3 = qs.FusedCircuit(W.u3cz_circuit(14, 6, 35), 3)    # 3-target blocks ... phase
+        assert p4.block_cost(0, qs.QS_C128)[0] == "dense_oz"
+        assert p4.layout_passes(qs.QS_C128) == 0
+        assert p5.layout_passes(qs.QS_C128) == 1
+        assert p3.layout_passes(qs.QS_C128) == 2
+        assert p4.layout_passes(qs.QS_C64) == 0
+        qs.set_tensor_cores(0)  # CUDA-core first block: the entry change is a pass of its own
+        assert p4.layout_passes(qs.QS_C128) == 1
+        qs.set_c128_math(qs.QS_MATH_FP64)
+        assert p4.layout_passes(qs.QS_C128) == 0
+    finally:
+        qs.set_c128_math(old_m)
+        qs.set_tensor_cores(old_t)

@@ -270,3 +270,54 @@ def test_oz_paired_access_alignment(oz):
         st.load(psi0)
         st.run(W.Circuit(n, c64_gates), 0)
         assert maxabs(st.get_vector(), ref64) < 1e-5, offset
+
+
+def _diag_only_circuit(n, seed):
+    rng = W.SplitMix64(seed)
+    gates = []
+    for q in range(n):
+        gates.append(W.Gate("RZ", (q,), params=(2 * np.pi * rng.uniform(),)))
+    for q in range(0, n - 1, 2):
+        gates.append(W.Gate("CZ", (q, q + 1)))
+    return W.Circuit(n, gates)
+
+
+@pytest.mark.parametrize("case", ["u3cz_k4", "u3cz_k5", "cuda_core_first", "diag_only"])
+def test_oz_plan_folds_layout_changes(oz, case):
+    """A double-float plan run changes the layout in its first and last passes where they read
+    every amplitude once: an uncontrolled tensor-core block first (it splits the IEEE doubles as
+    it loads them), a diagonal run last (it writes RN(hi + lo)). Each combination (both folded;
+    the first only; the last only, after a CUDA-core first block; a plan of one diagonal run)
+    matches the oracle at the complex128 bound from a state whose amplitudes span 1e-12 .. 1,
+    with exact zeros."""
+    qs = oz
+    n = 14
+    if case == "u3cz_k4":
+        c, k, first, last = W.u3cz_circuit(n, 6, 35), 4, "dense_oz", ("diag", "phase")
+    elif case == "u3cz_k5":
+        c, k, first, last = W.u3cz_circuit(n, 6, 36), 5, "dense_oz5", ("dense_oz5",)
+    elif case == "cuda_core_first":
+        qs.set_tensor_cores(0)
+        c, k, first, last = W.u3cz_circuit(n, 6, 35), 4, "dense_smem", ("diag", "phase")
+    else:
+        c, k, first, last = _diag_only_circuit(12, 5), 4, "diag", ("diag", "phase")
+        n = 12
+    plan = qs.FusedCircuit(c, k)
+    kinds = [plan.block_cost(b, qs.QS_C128)[0] for b in range(plan.n_blocks)]
+    assert kinds[0] == first and kinds[-1] in last, kinds
+    psi0 = W.random_state(n, 40 + n) * 10.0 ** -np.linspace(0, 12, 1 << n)
+    psi0[::29] = 0.0
+    ref = psi0.copy()
+    for g in c.gates:
+        oracle.apply_gate(ref, n, g)
+    st = qs.State(n, qs.QS_C128)
+    st.load(psi0)
+    st.apply_plan(plan)
+    got = st.get_vector()
+    assert maxabs(got, ref) < 1e-12 * float(np.max(np.abs(ref))), case
+    # the state is IEEE complex128 again: a second run continues from it
+    st.apply_plan(plan)
+    for g in c.gates:
+        oracle.apply_gate(ref, n, g)
+    assert maxabs(st.get_vector(), ref) < 2e-12 * float(np.max(np.abs(ref))), case
+    st.close()
