@@ -138,15 +138,26 @@ struct DiagParams {
 template <typename P>
 __global__ void __launch_bounds__(kThreads) k_diag(typename P::C* __restrict__ psi,
                                                    const __grid_constant__ DiagParams<P> Pm) {
+    using C = typename P::C;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < Pm.ip.n_iter; i += stride) {
-        const uint64_t x = expand(i, Pm.ip);
-        int r = 0;
+    for (uint64_t i0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < Pm.ip.n_iter; i0 += kConvUnroll * stride) {
+        uint64_t x[kConvUnroll];
+        C v[kConvUnroll];
+#pragma unroll
+        for (int u = 0; u < kConvUnroll; u++) {
+            x[u] = i0 + u * stride < Pm.ip.n_iter ? expand(i0 + u * stride, Pm.ip) : ~0ull;
+            if (x[u] != ~0ull) v[u] = __ldcg(psi + x[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kConvUnroll; u++) {
+            if (x[u] == ~0ull) continue;
+            int r = 0;
 #pragma unroll 1
-        for (int j = 0; j < Pm.m; j++) r |= int((x >> Pm.tpos[j]) & 1) << j;
-        typename P::Acc a = P::zero();
-        P::mac(a, Pm.d[r], psi[x]);
-        psi[x] = P::out(a);
+            for (int j = 0; j < Pm.m; j++) r |= int((x[u] >> Pm.tpos[j]) & 1) << j;
+            typename P::Acc a = P::zero();
+            P::mac(a, Pm.d[r], v[u]);
+            psi[x[u]] = P::out(a);
+        }
     }
 }
 
@@ -241,15 +252,26 @@ struct PhaseParams {
 template <typename P>
 __global__ void __launch_bounds__(kThreads) k_phase(typename P::C* __restrict__ psi,
                                                     const __grid_constant__ PhaseParams<P> Pm) {
+    using C = typename P::C;
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < Pm.ip.n_iter; i += stride) {
-        const uint64_t x = expand(i, Pm.ip);
-        if (Pm.mode == 0) {
-            typename P::Acc a = P::zero();
-            P::mac(a, Pm.phase, psi[x]);
-            psi[x] = P::out(a);
-        } else {
-            psi[x] = P::ipow(psi[x], Pm.mode);
+    for (uint64_t i0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < Pm.ip.n_iter; i0 += kConvUnroll * stride) {
+        uint64_t x[kConvUnroll];
+        C v[kConvUnroll];
+#pragma unroll
+        for (int u = 0; u < kConvUnroll; u++) {
+            x[u] = i0 + u * stride < Pm.ip.n_iter ? expand(i0 + u * stride, Pm.ip) : ~0ull;
+            if (x[u] != ~0ull) v[u] = __ldcg(psi + x[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < kConvUnroll; u++) {
+            if (x[u] == ~0ull) continue;
+            if (Pm.mode == 0) {
+                typename P::Acc a = P::zero();
+                P::mac(a, Pm.phase, v[u]);
+                psi[x[u]] = P::out(a);
+            } else {
+                psi[x[u]] = P::ipow(v[u], Pm.mode);
+            }
         }
     }
 }
