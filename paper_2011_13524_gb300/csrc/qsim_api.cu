@@ -249,17 +249,9 @@ std::vector<int> diag_runs(const std::vector<Op>& ops) {
     size_t b = 0;
     while (b < ops.size()) {
         size_t e = b;
-        if (diag_mergeable(ops[b])) {
-            std::vector<int> u(diag_qubits(ops[b]));
-            while (e + 1 < ops.size() && diag_mergeable(ops[e + 1])) {
-                std::vector<int> w(u);
-                for (int q : diag_qubits(ops[e + 1]))
-                    if (std::find(w.begin(), w.end(), q) == w.end()) w.push_back(q);
-                if (w.size() > size_t(kDiagTableBits)) break;
-                u.swap(w);
-                e++;
-            }
-        }
+        DiagSplit sp;
+        if (diag_mergeable(ops[b]) && diag_split_add(sp, diag_qubits(ops[b])))
+            while (e + 1 < ops.size() && diag_mergeable(ops[e + 1]) && diag_split_add(sp, diag_qubits(ops[e + 1]))) e++;
         len[b] = int(e - b + 1);
         for (size_t i = b + 1; i <= e; i++) len[i] = 0;
         b = e + 1;

@@ -161,14 +161,16 @@ __global__ void __launch_bounds__(kThreads) k_diag(typename P::C* __restrict__ p
     }
 }
 
-// Several diagonal blocks (no controls) in one pass: psi_x *= t[r(x)] with the product of their
-// diagonals tabulated over the union of their qubits (at most kDiagTableBits), staged in shared
-// memory per CTA; r(x) gathers the union's bits of x.
+// Several diagonal blocks (no controls) in one pass: psi_x *= t[r(x)] t2[r2(x)] with the product
+// of their diagonals held as two tables over two sets of qubits (at most kDiagTableBits and
+// kDiagTable2Bits; the second may be empty), staged in shared memory per CTA; r(x) and r2(x)
+// gather those qubits' bits of x.
 template <typename P>
 struct DiagTableParams {
     uint64_t N;
-    int32_t m;
+    int32_t m, m2;
     int32_t tpos[kDiagTableBits];
+    int32_t tpos2[kDiagTable2Bits];
 };
 
 // kIeeeOut (double-float only): the products are written as IEEE complex128, RN(hi + lo) per
@@ -180,7 +182,9 @@ __global__ void __launch_bounds__(kThreads) k_diag_table(typename P::C* __restri
     using C = typename P::C;
     extern __shared__ __align__(16) unsigned char dsm[];
     typename P::K* t = reinterpret_cast<typename P::K*>(dsm);
-    for (int i = threadIdx.x; i < (1 << Pm.m); i += blockDim.x) t[i] = table[i];
+    const typename P::K* t2 = t + (1 << Pm.m);
+    const int entries = (1 << Pm.m) + (Pm.m2 > 0 ? 1 << Pm.m2 : 0);
+    for (int i = threadIdx.x; i < entries; i += blockDim.x) t[i] = table[i];
     __syncthreads();
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     for (uint64_t x0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x0 < Pm.N; x0 += kConvUnroll * stride) {
@@ -197,6 +201,14 @@ __global__ void __launch_bounds__(kThreads) k_diag_table(typename P::C* __restri
             for (int j = 0; j < Pm.m; j++) r |= uint32_t((x >> Pm.tpos[j]) & 1) << j;
             typename P::Acc a = P::zero();
             P::mac(a, t[r], v[u]);
+            if (Pm.m2 > 0) {
+                uint32_t r2 = 0;
+#pragma unroll 2
+                for (int j = 0; j < Pm.m2; j++) r2 |= uint32_t((x >> Pm.tpos2[j]) & 1) << j;
+                const C w = P::out(a);
+                a = P::zero();
+                P::mac(a, t2[r2], w);
+            }
             if constexpr (kIeeeOut) {
                 const float4 o = P::out(a);
                 reinterpret_cast<double2*>(psi)[x] = make_double2(join_df_int(o.x, o.y), join_df_int(o.z, o.w));
@@ -208,26 +220,32 @@ __global__ void __launch_bounds__(kThreads) k_diag_table(typename P::C* __restri
 }
 
 template <typename P>
-void launch_diag_table_t(const std::vector<int>& u, const std::vector<cplx>& tab, void* psi, int n, cudaStream_t st,
-                         void* stage, bool ieee_out) {
+void launch_diag_table_t(const std::vector<int>& u, const std::vector<cplx>& tab, const std::vector<int>& u2,
+                         const std::vector<cplx>& tab2, void* psi, int n, cudaStream_t st, void* stage,
+                         bool ieee_out) {
     using K = typename P::K;
-    const size_t bytes = tab.size() * sizeof(K);
-    QS_REQUIRE(stage != nullptr && bytes <= kStageBytes, "no staging buffer for a diagonal table");
-    std::vector<K> hk(tab.size());
+    const size_t entries = tab.size() + (u2.empty() ? 0 : tab2.size());
+    const size_t bytes = entries * sizeof(K);
+    constexpr size_t kMaxBytes = sizeof(K) * ((size_t(1) << kDiagTableBits) + (size_t(1) << kDiagTable2Bits));
+    QS_REQUIRE(stage != nullptr && bytes <= kStageBytes && bytes <= kMaxBytes, "no staging buffer for a diagonal table");
+    std::vector<K> hk(entries);
     for (size_t i = 0; i < tab.size(); i++) hk[i] = P::host_k(tab[i].real(), tab[i].imag());
+    for (size_t i = tab.size(); i < entries; i++) hk[i] = P::host_k(tab2[i - tab.size()].real(), tab2[i - tab.size()].imag());
     QS_TRY_CUDA(cudaMemcpyAsync(stage, hk.data(), bytes, cudaMemcpyHostToDevice, st));
     QS_TRY_CUDA(cudaStreamSynchronize(st));  // hk is host memory that dies on return
     DiagTableParams<P> Pm;
     Pm.N = 1ull << n;
     Pm.m = int(u.size());
+    Pm.m2 = int(u2.size());
     for (size_t j = 0; j < u.size(); j++) Pm.tpos[j] = u[j];
+    for (size_t j = 0; j < u2.size(); j++) Pm.tpos2[j] = u2[j];
     static bool attr = false;
     if (!attr) {
         QS_TRY_CUDA(cudaFuncSetAttribute(k_diag_table<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(sizeof(K) << kDiagTableBits)));
+                                         int(kMaxBytes)));
         if constexpr (std::is_same<P, DFArith>::value)
             QS_TRY_CUDA(cudaFuncSetAttribute(k_diag_table<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(sizeof(K) << kDiagTableBits)));
+                                             int(kMaxBytes)));
         attr = true;
     }
     auto kern = k_diag_table<P, false>;
@@ -626,44 +644,70 @@ void launch_op_arith(const Op& op, void* psi, int n, Arith ar, cudaStream_t st, 
     QS_TRY_CUDA(cudaGetLastError());
 }
 
-// Diagonal ops (no controls) applied as one pass: the product of their diagonals over the union
-// of their targets (at most kDiagTableBits qubits).
+bool diag_split_add(DiagSplit& sp, const std::vector<int>& qubits) {
+    auto joined = [&](const std::vector<int>& u) {
+        std::vector<int> w(u);
+        for (int q : qubits)
+            if (std::find(w.begin(), w.end(), q) == w.end()) w.push_back(q);
+        return w;
+    };
+    std::vector<int> w = joined(sp.u);
+    if (w.size() <= size_t(kDiagTableBits)) {
+        sp.u.swap(w);
+        sp.side.push_back(0);
+        return true;
+    }
+    w = joined(sp.u2);
+    if (w.size() <= size_t(kDiagTable2Bits)) {
+        sp.u2.swap(w);
+        sp.side.push_back(1);
+        return true;
+    }
+    return false;
+}
+
+// Diagonal ops (uncontrolled diagonals, on their targets, and phases, on their control qubits'
+// values) applied as one pass: the product of their diagonals as two tables over the two qubit
+// sets of diag_split_add.
 void launch_diag_run(const Op* ops, size_t count, void* psi, int n, Arith ar, cudaStream_t st, void* stage,
                      bool ieee_out) {
-    // uncontrolled diagonals (on their targets) and phases (on their control qubits' values)
     auto qubits = [](const Op& op) -> const std::vector<int>& {
         return op.kind == OpKind::Phase ? op.controls : op.targets;
     };
-    std::vector<int> u;
+    DiagSplit sp;
     for (size_t i = 0; i < count; i++) {
         QS_REQUIRE((ops[i].kind == OpKind::Diag && ops[i].controls.empty()) || ops[i].kind == OpKind::Phase,
                    "diagonal run of uncontrolled diagonals and phases");
-        for (int q : qubits(ops[i]))
-            if (std::find(u.begin(), u.end(), q) == u.end()) u.push_back(q);
+        QS_REQUIRE(diag_split_add(sp, qubits(ops[i])), "diagonal run on too many qubits");
     }
-    std::sort(u.begin(), u.end());
-    QS_REQUIRE(u.size() <= size_t(kDiagTableBits), "diagonal run on too many qubits");
-    std::vector<cplx> tab(size_t(1) << u.size(), cplx(1.0, 0.0));
+    std::sort(sp.u.begin(), sp.u.end());
+    std::sort(sp.u2.begin(), sp.u2.end());
+    std::vector<cplx> tab(size_t(1) << sp.u.size(), cplx(1.0, 0.0)), tab2(size_t(1) << sp.u2.size(), cplx(1.0, 0.0));
     for (size_t i = 0; i < count; i++) {
-        const std::vector<int>& qs_i = qubits(ops[i]);
-        std::vector<int> pos;  // bit of the union index for each qubit of op i
-        for (int q : qs_i) pos.push_back(int(std::find(u.begin(), u.end(), q) - u.begin()));
-        for (size_t r = 0; r < tab.size(); r++) {
+        const std::vector<int>& u = sp.side[i] ? sp.u2 : sp.u;
+        std::vector<cplx>& t = sp.side[i] ? tab2 : tab;
+        std::vector<int> pos;  // bit of the table index for each qubit of op i
+        for (int q : qubits(ops[i])) pos.push_back(int(std::find(u.begin(), u.end(), q) - u.begin()));
+        for (size_t r = 0; r < t.size(); r++) {
             size_t ri = 0;
             for (size_t j = 0; j < pos.size(); j++) ri |= ((r >> pos[j]) & 1) << j;
             if (ops[i].kind == OpKind::Phase) {
                 bool match = true;
                 for (size_t j = 0; j < pos.size(); j++) match = match && int((ri >> j) & 1) == ops[i].cvals[j];
-                if (match) tab[r] *= ops[i].phase;
+                if (match) t[r] *= ops[i].phase;
             } else {
-                tab[r] *= ops[i].data[ri];
+                t[r] *= ops[i].data[ri];
             }
         }
     }
     switch (ar) {
-        case Arith::F32: launch_diag_table_t<NativeArith<float>>(u, tab, psi, n, st, stage, ieee_out); break;
-        case Arith::F64: launch_diag_table_t<NativeArith<double>>(u, tab, psi, n, st, stage, ieee_out); break;
-        case Arith::DF: launch_diag_table_t<DFArith>(u, tab, psi, n, st, stage, ieee_out); break;
+        case Arith::F32:
+            launch_diag_table_t<NativeArith<float>>(sp.u, tab, sp.u2, tab2, psi, n, st, stage, ieee_out);
+            break;
+        case Arith::F64:
+            launch_diag_table_t<NativeArith<double>>(sp.u, tab, sp.u2, tab2, psi, n, st, stage, ieee_out);
+            break;
+        case Arith::DF: launch_diag_table_t<DFArith>(sp.u, tab, sp.u2, tab2, psi, n, st, stage, ieee_out); break;
     }
 }
 

@@ -131,9 +131,18 @@ void launch_op(const Op& op, void* psi, int n, qs_dtype dt, cudaStream_t st, voi
 // amplitude once (takes_ieee_in), else by a conversion pass before it
 void launch_op_arith(const Op& op, void* psi, int n, Arith ar, cudaStream_t st, void* stage, bool ieee_in = false);
 bool takes_ieee_in(const Op& op);
-// consecutive uncontrolled diagonal ops on at most kDiagTableBits qubits together: one pass;
-// ieee_out (double-float only): the pass writes its results as IEEE complex128
+// Consecutive uncontrolled diagonal ops (and phases) together in one pass, their product held
+// as two tables: each op in turn joins the first table if the union of its qubits stays within
+// kDiagTableBits, else the second if within kDiagTable2Bits; a run ends at an op that fits
+// neither (diag_split_add false, split unchanged). ieee_out (double-float only): the pass
+// writes its results as IEEE complex128.
 constexpr int kDiagTableBits = 12;
+constexpr int kDiagTable2Bits = 8;
+struct DiagSplit {
+    std::vector<int> u, u2;  // the two tables' qubits
+    std::vector<int> side;   // per op added: 0 first table, 1 second
+};
+bool diag_split_add(DiagSplit& sp, const std::vector<int>& qubits);
 void launch_diag_run(const Op* ops, size_t count, void* psi, int n, Arith ar, cudaStream_t st, void* stage,
                      bool ieee_out = false);
 // for each op: the number of ops launched together from it (>= 1), or 0 if an earlier op's

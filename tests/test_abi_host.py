@@ -253,7 +253,9 @@ def test_expectation_plan_packs_flip_groups_into_tiles():
 def test_diagonal_runs_share_one_pass_in_block_costs():
     """Consecutive uncontrolled diagonal and phase blocks of a plan run as one pass: the block
     costs (host only) report one launch and one full pass for the first block of each run, none
-    for the others, and never join more than 12 qubits in a run."""
+    for the others. A run's product is held as two tables: each block in turn joins the first
+    if the union of its qubits stays within 12, else the second if within 8; a run ends at the
+    first block that fits neither."""
     n = 16
     gates = []
     for layer in range(4):
@@ -277,11 +279,19 @@ def test_diagonal_runs_share_one_pass_in_block_costs():
         else:
             assert by == 0 and cur is not None
             cur.append(b)
-    for r in runs:
-        qubits = set()
+    def split_add(sp, q):
+        for i, lim in ((0, 12), (1, 8)):
+            if len(sp[i] | q) <= lim:
+                sp[i] |= q
+                return True
+        return False
+
+    for i, r in enumerate(runs):
+        sp = [set(), set()]
         for b in r:
-            qubits |= set(plan.block(b)[0])
-        assert len(qubits) <= 12
+            assert split_add(sp, set(plan.block(b)[0]))
+        if i + 1 < len(runs):  # the next run's first block fits neither table
+            assert not split_add(sp, set(plan.block(runs[i + 1][0])[0]))
         if len(r) > 1:
             assert costs[r[0]][2] == full
 

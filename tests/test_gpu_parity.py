@@ -443,9 +443,9 @@ def test_precision_n24_vs_oracle(qs):
 @pytest.mark.parametrize("dtype,math_mode", [(2, "df"), (2, "fp64"), (1, "fp64")])
 def test_consecutive_diagonal_blocks_one_pass(qs, dtype, math_mode):
     """A circuit of diagonal gates only (RZ, CZ, T, S, controlled phases) fused at width 4: the
-    plan's consecutive diagonal blocks (at most 12 qubits together) run as one pass with a
-    tabulated product; the state matches the oracle and the block costs count one launch per
-    pass."""
+    plan's consecutive diagonal blocks run as one pass with their product in two tables (on at
+    most 12 and at most 8 qubits; here a run uses both); the state matches the oracle and the
+    block costs count one launch per pass."""
     n = 14
     rng = W.SplitMix64(1414)
     gates = []
@@ -469,6 +469,17 @@ def test_consecutive_diagonal_blocks_one_pass(qs, dtype, math_mode):
         assert all(k in ("diag", "phase") for k, _, _ in costs)
         launches = sum(l for _, l, _ in costs)
         assert launches < plan.n_blocks  # several blocks share a pass
+        second = set()  # qubits of the second table in the first run (greedy split)
+        first = set()
+        for b in range(plan.n_blocks):
+            if b > 0 and costs[b][1]:
+                break
+            q = set(plan.block(b)[0])
+            if len(first | q) <= 12:
+                first |= q
+            else:
+                second |= q
+        assert len(first) == 12 and 0 < len(second) <= 8
         full = 2 * (16 if dtype == 2 else 8) * 2 ** n
         assert all(by <= full and (l == 0) == (by == 0) for _, l, by in costs)
         st = qs.State(n, dtype)
