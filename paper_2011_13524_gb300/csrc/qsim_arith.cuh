@@ -183,39 +183,48 @@ __device__ __forceinline__ double widen_float_int(float f) {
 }
 
 // RN(hi + lo) as a double for a double-float pair, on the integer pipes when both are normal and
-// lo's exponent is 24..55 below hi's (every pair with |lo| <= ulp(hi)/2 has it at least 24 below):
-// hi's significand is placed at bits 62..39 of a 64-bit word and lo's shifted in beside it, with
-// the bits shifted out folded into bit 0 (a sticky bit, enough to round correctly with 10 bits
-// below the result's last place); the sum or difference (a difference below 2^62 moves up one
-// bit) is then rounded to 53 bits, to nearest with ties to even. Otherwise (zero hi, subnormal,
-// non-finite, lo far smaller) the FP64 add.
+// lo's exponent is 24..55 below hi's (every pair with |lo| <= ulp(hi)/2 has it at least 24
+// below). In units of the last place of a double with hi's exponent, hi is its significand
+// times 2^29 and |lo| = L + F / 2^s: for a gap d <= 29 an integer (F = 0), for d = 29 + s a
+// 32-bit integer part and an s-bit fraction. The sum or difference is formed on the 53-bit
+// significand and rounded to nearest-even from F; a difference that drops below 2^52 moves up
+// one bit when exact (F = 0). Otherwise (zero hi, subnormal, non-finite, lo far smaller, a
+// rounded difference below 2^52) the FP64 add.
 __device__ __forceinline__ double join_df_int(float hi, float lo) {
     const uint32_t uh = __float_as_uint(hi), ul = __float_as_uint(lo);
     if ((ul << 1) == 0u) return widen_float_int(hi);
     const uint32_t eh = (uh >> 23) & 0xFFu, el = (ul >> 23) & 0xFFu;
     const uint32_t d = eh - el;
     if (eh == 0u || eh == 255u || el == 0u || d - 24u > 31u) return widen_float_int(hi) + widen_float_int(lo);
-    uint64_t mh = uint64_t((uh & 0x7FFFFFu) | 0x800000u) << 39;
-    const uint64_t lf = uint64_t((ul & 0x7FFFFFu) | 0x800000u) << 39;
-    const uint64_t ml = (lf >> d) | uint64_t((lf << (64u - d)) != 0u);
+    const uint32_t ml = (ul & 0x7FFFFFu) | 0x800000u;
+    uint32_t L, F = 0u, half = 0u;
+    if (d <= 29u) {
+        L = ml << (29u - d);
+    } else {
+        const uint32_t sh = d - 29u;  // 1 .. 26
+        L = ml >> sh;
+        F = ml & ((1u << sh) - 1u);
+        half = 1u << (sh - 1u);
+    }
+    uint64_t m = uint64_t((uh & 0x7FFFFFu) | 0x800000u) << 29;
     uint64_t e = uint64_t(eh) + 896u;  // biased double exponent of hi
     if ((uh ^ ul) >> 31) {
-        mh -= ml;
-        if (mh < (1ull << 62)) {
-            mh <<= 1;
-            e -= 1;
+        if (F == 0u) {
+            m -= L;
+            if (m < (1ull << 52)) {
+                m <<= 1;
+                e -= 1;
+            }
+        } else {
+            m -= uint64_t(L) + 1u;  // + (1 - F / 2^s), rounded below
+            if (m < (1ull << 52)) return widen_float_int(hi) + widen_float_int(lo);
+            m += (F < half || (F == half && (m & 1u))) ? 1u : 0u;
         }
     } else {
-        mh += ml;
+        m += L;
+        if (F != 0u) m += (F > half || (F == half && (m & 1u))) ? 1u : 0u;
     }
-    uint64_t r = mh >> 10;
-    const uint32_t rem = uint32_t(mh & 0x3FFu);
-    r += (rem > 0x200u || (rem == 0x200u && (r & 1u))) ? 1u : 0u;
-    if (r >> 53) {
-        r >>= 1;
-        e += 1;
-    }
-    return __longlong_as_double(static_cast<long long>((uint64_t(uh >> 31) << 63) | (e << 52) | (r & ((1ull << 52) - 1))));
+    return __longlong_as_double(static_cast<long long>((uint64_t(uh >> 31) << 63) | (e << 52) | (m & ((1ull << 52) - 1))));
 }
 
 }  // namespace qs

@@ -169,14 +169,24 @@ template <typename P>
 struct DiagTableParams {
     uint64_t N;
     int32_t m, m2;
+    int32_t second;  // 0: no second table; 1: general entries; 2: entries 1, i, -1, -i only
     int32_t tpos[kDiagTableBits];
     int32_t tpos2[kDiagTable2Bits];
 };
 
+// k of an entry i^k (1, i, -1 or -i exactly): a quarter turn applied by swaps and signs
+__device__ __forceinline__ int quarter_of(const float2& k) { return k.x > 0.5f ? 0 : k.y > 0.5f ? 1 : k.x < -0.5f ? 2 : 3; }
+__device__ __forceinline__ int quarter_of(const double2& k) { return k.x > 0.5 ? 0 : k.y > 0.5 ? 1 : k.x < -0.5 ? 2 : 3; }
+__device__ __forceinline__ int quarter_of(const float4& k) { return k.x > 0.5f ? 0 : k.z > 0.5f ? 1 : k.x < -0.5f ? 2 : 3; }
+
 // kIeeeOut (double-float only): the products are written as IEEE complex128, RN(hi + lo) per
 // component (the join of the layout-change pass), into the same 16 bytes
+// one wave of CTAs (three of 512 threads per SM) that each stage the tables once; two loads in
+// flight per thread
+constexpr int kDiagThreads = 512;
+constexpr int kDiagUnroll = 2;
 template <typename P, bool kIeeeOut>
-__global__ void __launch_bounds__(kThreads) k_diag_table(typename P::C* __restrict__ psi,
+__global__ void __launch_bounds__(kDiagThreads, 3) k_diag_table(typename P::C* __restrict__ psi,
                                                          const typename P::K* __restrict__ table,
                                                          const __grid_constant__ DiagTableParams<P> Pm) {
     using C = typename P::C;
@@ -187,27 +197,31 @@ __global__ void __launch_bounds__(kThreads) k_diag_table(typename P::C* __restri
     for (int i = threadIdx.x; i < entries; i += blockDim.x) t[i] = table[i];
     __syncthreads();
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t x0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x0 < Pm.N; x0 += kConvUnroll * stride) {
-        C v[kConvUnroll];  // several loads in flight per thread
+    for (uint64_t x0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x0 < Pm.N; x0 += kDiagUnroll * stride) {
+        C v[kDiagUnroll];
 #pragma unroll
-        for (int u = 0; u < kConvUnroll; u++)
+        for (int u = 0; u < kDiagUnroll; u++)
             if (x0 + u * stride < Pm.N) v[u] = __ldcg(psi + x0 + u * stride);
 #pragma unroll
-        for (int u = 0; u < kConvUnroll; u++) {
+        for (int u = 0; u < kDiagUnroll; u++) {
             const uint64_t x = x0 + u * stride;
             if (x >= Pm.N) continue;
             uint32_t r = 0;
 #pragma unroll 4
             for (int j = 0; j < Pm.m; j++) r |= uint32_t((x >> Pm.tpos[j]) & 1) << j;
-            typename P::Acc a = P::zero();
-            P::mac(a, t[r], v[u]);
-            if (Pm.m2 > 0) {
-                uint32_t r2 = 0;
+            uint32_t r2 = 0;
 #pragma unroll 2
-                for (int j = 0; j < Pm.m2; j++) r2 |= uint32_t((x >> Pm.tpos2[j]) & 1) << j;
-                const C w = P::out(a);
-                a = P::zero();
-                P::mac(a, t2[r2], w);
+            for (int j = 0; j < Pm.m2; j++) r2 |= uint32_t((x >> Pm.tpos2[j]) & 1) << j;
+            typename P::Acc a = P::zero();
+            if (Pm.second == 2) {  // exact quarter turn, then the first table's entry
+                P::mac(a, t[r], P::ipow(v[u], quarter_of(t2[r2])));
+            } else {
+                P::mac(a, t[r], v[u]);
+                if (Pm.second == 1) {
+                    const C w = P::out(a);
+                    a = P::zero();
+                    P::mac(a, t2[r2], w);
+                }
             }
             if constexpr (kIeeeOut) {
                 const float4 o = P::out(a);
@@ -237,15 +251,29 @@ void launch_diag_table_t(const std::vector<int>& u, const std::vector<cplx>& tab
     Pm.N = 1ull << n;
     Pm.m = int(u.size());
     Pm.m2 = int(u2.size());
+    Pm.second = 0;
+    if (!u2.empty()) {
+        auto quarter = [](const cplx& z) {
+            return (z.imag() == 0.0 && (z.real() == 1.0 || z.real() == -1.0)) ||
+                   (z.real() == 0.0 && (z.imag() == 1.0 || z.imag() == -1.0));
+        };
+        Pm.second = std::all_of(tab2.begin(), tab2.end(), quarter) ? 2 : 1;
+    }
     for (size_t j = 0; j < u.size(); j++) Pm.tpos[j] = u[j];
     for (size_t j = 0; j < u2.size(); j++) Pm.tpos2[j] = u2[j];
     static bool attr = false;
+    static int resident[2] = {1, 1};  // CTAs per SM at the largest table, without / with IEEE output
     if (!attr) {
         QS_TRY_CUDA(cudaFuncSetAttribute(k_diag_table<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(kMaxBytes)));
-        if constexpr (std::is_same<P, DFArith>::value)
+        QS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[0], k_diag_table<P, false>, kDiagThreads,
+                                                                  kMaxBytes));
+        if constexpr (std::is_same<P, DFArith>::value) {
             QS_TRY_CUDA(cudaFuncSetAttribute(k_diag_table<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(kMaxBytes)));
+            QS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[1], k_diag_table<P, true>,
+                                                                      kDiagThreads, kMaxBytes));
+        }
         attr = true;
     }
     auto kern = k_diag_table<P, false>;
@@ -254,7 +282,10 @@ void launch_diag_table_t(const std::vector<int>& u, const std::vector<cplx>& tab
     } else {
         QS_REQUIRE(!ieee_out, "IEEE output is a double-float layout change");
     }
-    kern<<<grid_for(Pm.N), kThreads, bytes, st>>>(reinterpret_cast<typename P::C*>(psi), static_cast<const K*>(stage), Pm);
+    const uint64_t want = (Pm.N + kDiagThreads - 1) / kDiagThreads;
+    const uint64_t wave = uint64_t(sm_count()) * uint64_t(std::max(1, resident[ieee_out ? 1 : 0]));
+    const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, wave)));
+    kern<<<grid, kDiagThreads, bytes, st>>>(reinterpret_cast<typename P::C*>(psi), static_cast<const K*>(stage), Pm);
     QS_TRY_CUDA(cudaGetLastError());
 }
 

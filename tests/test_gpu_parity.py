@@ -492,3 +492,39 @@ def test_consecutive_diagonal_blocks_one_pass(qs, dtype, math_mode):
         assert maxabs(st.get_vector(), ref) < TOL[dtype]
     finally:
         qs.set_c128_math(old)
+
+
+@pytest.mark.parametrize("dtype,math_mode", [(2, "df"), (2, "fp64"), (1, "fp64")])
+def test_diagonal_run_quarter_turn_table(qs, dtype, math_mode):
+    """A diagonal run whose second table holds only 1, i, -1, -i (two CZ and an S after three
+    general 4-qubit diagonals filling the first table): the quarter turns are applied exactly by
+    swaps and signs before the first table's entry; as the last pass of a double-float run it
+    also writes IEEE doubles. The state matches the oracle."""
+    n = 16
+    rng = W.SplitMix64(1616)
+    gates = []
+    for b in range(3):
+        d = np.exp(1j * 2 * np.pi * np.array([rng.uniform() for _ in range(16)]))
+        gates.append(W.Gate("DIAG", tuple(range(4 * b, 4 * b + 4)), matrix=d))
+    gates += [W.Gate("CZ", (12, 13)), W.Gate("CZ", (13, 14)), W.Gate("S", (14,))]
+    c = W.Circuit(n, gates)
+    psi0 = W.random_state(n, 161)
+    ref = psi0.copy()
+    for g in gates:
+        oracle.apply_gate(ref, n, g)
+    old = qs.get_c128_math()
+    try:
+        qs.set_c128_math(qs.QS_MATH_DF if math_mode == "df" else qs.QS_MATH_FP64)
+        plan = qs.FusedCircuit(c, 4)
+        costs = [plan.block_cost(b, dtype) for b in range(plan.n_blocks)]
+        assert [l for _, l, _ in costs] == [1] + [0] * (plan.n_blocks - 1), costs
+        assert set(plan.block(plan.n_blocks - 1)[0]) == {12, 13, 14}
+        if dtype == 2 and math_mode == "df":
+            assert plan.layout_passes(dtype) == 1  # entry only: the run writes IEEE doubles
+        st = qs.State(n, dtype)
+        st.load(psi0)
+        st.apply_plan(plan)
+        assert maxabs(st.get_vector(), ref) < TOL[dtype]
+        st.close()
+    finally:
+        qs.set_c128_math(old)
