@@ -187,9 +187,10 @@ __device__ __forceinline__ double widen_float_int(float f) {
 // below). In units of the last place of a double with hi's exponent, hi is its significand
 // times 2^29 and |lo| = L + F / 2^s: for a gap d <= 29 an integer (F = 0), for d = 29 + s a
 // 32-bit integer part and an s-bit fraction. The sum or difference is formed on the 53-bit
-// significand and rounded to nearest-even from F; a difference that drops below 2^52 moves up
-// one bit when exact (F = 0). Otherwise (zero hi, subnormal, non-finite, lo far smaller, a
-// rounded difference below 2^52) the FP64 add.
+// significand and rounded to nearest-even from F, with selects rather than branches on the
+// gap and the signs; a difference that drops below 2^52 moves up one bit when exact (F = 0).
+// Otherwise (zero hi, subnormal, non-finite, lo far smaller, a rounded difference below 2^52)
+// the FP64 add.
 __device__ __forceinline__ double join_df_int(float hi, float lo) {
     const uint32_t uh = __float_as_uint(hi), ul = __float_as_uint(lo);
     if ((ul << 1) == 0u) return widen_float_int(hi);
@@ -197,33 +198,25 @@ __device__ __forceinline__ double join_df_int(float hi, float lo) {
     const uint32_t d = eh - el;
     if (eh == 0u || eh == 255u || el == 0u || d - 24u > 31u) return widen_float_int(hi) + widen_float_int(lo);
     const uint32_t ml = (ul & 0x7FFFFFu) | 0x800000u;
-    uint32_t L, F = 0u, half = 0u;
-    if (d <= 29u) {
-        L = ml << (29u - d);
-    } else {
-        const uint32_t sh = d - 29u;  // 1 .. 26
-        L = ml >> sh;
-        F = ml & ((1u << sh) - 1u);
-        half = 1u << (sh - 1u);
-    }
+    const uint32_t sl = d < 29u ? 29u - d : 0u;  // d <= 29: lo's bits all land on the significand
+    const uint32_t sr = d > 29u ? d - 29u : 0u;  // d > 29: sr bits of lo below it
+    const uint32_t L = (ml << sl) >> sr;
+    const uint32_t F = ml & ((1u << sr) - 1u);
+    const uint32_t half = (1u << sr) >> 1;
+    const uint32_t frac = F != 0u ? 1u : 0u;
+    const bool sub = ((uh ^ ul) >> 31) != 0u;
     uint64_t m = uint64_t((uh & 0x7FFFFFu) | 0x800000u) << 29;
     uint64_t e = uint64_t(eh) + 896u;  // biased double exponent of hi
-    if ((uh ^ ul) >> 31) {
-        if (F == 0u) {
-            m -= L;
-            if (m < (1ull << 52)) {
-                m <<= 1;
-                e -= 1;
-            }
-        } else {
-            m -= uint64_t(L) + 1u;  // + (1 - F / 2^s), rounded below
-            if (m < (1ull << 52)) return widen_float_int(hi) + widen_float_int(lo);
-            m += (F < half || (F == half && (m & 1u))) ? 1u : 0u;
-        }
-    } else {
-        m += L;
-        if (F != 0u) m += (F > half || (F == half && (m & 1u))) ? 1u : 0u;
+    // sum: m + L, rounded up on F; difference: m - L - 1 + (1 - F / 2^sr) when F != 0
+    m = sub ? m - (uint64_t(L) + frac) : m + L;
+    const uint32_t odd = uint32_t(m) & 1u;
+    const uint32_t up = sub ? (frac && (F < half || (F == half && odd))) : (F > half || (frac && F == half && odd));
+    if (m < (1ull << 52)) {  // a difference that left hi's binade
+        if (frac) return widen_float_int(hi) + widen_float_int(lo);
+        m <<= 1;
+        e -= 1;
     }
+    m += up;
     return __longlong_as_double(static_cast<long long>((uint64_t(uh >> 31) << 63) | (e << 52) | (m & ((1ull << 52) - 1))));
 }
 

@@ -170,9 +170,30 @@ struct DiagTableParams {
     uint64_t N;
     int32_t m, m2;
     int32_t second;  // 0: no second table; 1: general entries; 2: entries 1, i, -1, -i only
-    int32_t tpos[kDiagTableBits];
-    int32_t tpos2[kDiagTable2Bits];
+    int32_t nrun, nrun2;
+    // runs of consecutive table qubits: shift (bits 0..7), width (8..15), table bit (16..23)
+    uint32_t run[kDiagTableBits];
+    uint32_t run2[kDiagTable2Bits];
 };
+
+// table index of x: its bits at the table's qubits, gathered run by run
+__device__ __forceinline__ uint32_t gather_runs(uint64_t x, const uint32_t* run, int nrun) {
+    uint32_t r = 0;
+    for (int k = 0; k < nrun; k++) {
+        const uint32_t c = run[k];
+        r |= (uint32_t(x >> (c & 0xFFu)) & ((1u << ((c >> 8) & 0xFFu)) - 1u)) << (c >> 16);
+    }
+    return r;
+}
+
+// i^k (re + i im) of a double-float amplitude by selects and sign flips (exact)
+__device__ __forceinline__ float4 quarter_turn(const float4& v, int k) {
+    const bool sw = (k & 1) != 0;
+    const uint32_t sre = (k == 1 || k == 2) ? 0x80000000u : 0u, sim = (k & 2) ? 0x80000000u : 0u;
+    const float ah = sw ? v.z : v.x, al = sw ? v.w : v.y, bh = sw ? v.x : v.z, bl = sw ? v.y : v.w;
+    return make_float4(__uint_as_float(__float_as_uint(ah) ^ sre), __uint_as_float(__float_as_uint(al) ^ sre),
+                       __uint_as_float(__float_as_uint(bh) ^ sim), __uint_as_float(__float_as_uint(bl) ^ sim));
+}
 
 // k of an entry i^k (1, i, -1 or -i exactly): a quarter turn applied by swaps and signs
 __device__ __forceinline__ int quarter_of(const float2& k) { return k.x > 0.5f ? 0 : k.y > 0.5f ? 1 : k.x < -0.5f ? 2 : 3; }
@@ -206,22 +227,26 @@ __global__ void __launch_bounds__(kDiagThreads, 3) k_diag_table(typename P::C* _
         for (int u = 0; u < kDiagUnroll; u++) {
             const uint64_t x = x0 + u * stride;
             if (x >= Pm.N) continue;
-            uint32_t r = 0;
-#pragma unroll 4
-            for (int j = 0; j < Pm.m; j++) r |= uint32_t((x >> Pm.tpos[j]) & 1) << j;
-            uint32_t r2 = 0;
-#pragma unroll 2
-            for (int j = 0; j < Pm.m2; j++) r2 |= uint32_t((x >> Pm.tpos2[j]) & 1) << j;
-            typename P::Acc a = P::zero();
+            const uint32_t r = gather_runs(x, Pm.run, Pm.nrun);
+            const uint32_t r2 = gather_runs(x, Pm.run2, Pm.nrun2);
+            C w = v[u];
             if (Pm.second == 2) {  // exact quarter turn, then the first table's entry
-                P::mac(a, t[r], P::ipow(v[u], quarter_of(t2[r2])));
+                if constexpr (std::is_same<P, DFArith>::value)
+                    w = quarter_turn(w, quarter_of(t2[r2]));
+                else
+                    w = P::ipow(w, quarter_of(t2[r2]));
+            }
+            typename P::Acc a;
+            if constexpr (std::is_same<P, DFArith>::value) {
+                a = P::first(t[r], w);
             } else {
-                P::mac(a, t[r], v[u]);
-                if (Pm.second == 1) {
-                    const C w = P::out(a);
-                    a = P::zero();
-                    P::mac(a, t2[r2], w);
-                }
+                a = P::zero();
+                P::mac(a, t[r], w);
+            }
+            if (Pm.second == 1) {
+                const C y = P::out(a);
+                a = P::zero();
+                P::mac(a, t2[r2], y);
             }
             if constexpr (kIeeeOut) {
                 const float4 o = P::out(a);
@@ -259,8 +284,18 @@ void launch_diag_table_t(const std::vector<int>& u, const std::vector<cplx>& tab
         };
         Pm.second = std::all_of(tab2.begin(), tab2.end(), quarter) ? 2 : 1;
     }
-    for (size_t j = 0; j < u.size(); j++) Pm.tpos[j] = u[j];
-    for (size_t j = 0; j < u2.size(); j++) Pm.tpos2[j] = u2[j];
+    auto runs = [](const std::vector<int>& q, uint32_t* run) {  // q ascending
+        int nr = 0;
+        for (size_t j = 0; j < q.size();) {
+            size_t k = j + 1;
+            while (k < q.size() && q[k] == q[k - 1] + 1) k++;
+            run[nr++] = uint32_t(q[j]) | (uint32_t(k - j) << 8) | (uint32_t(j) << 16);
+            j = k;
+        }
+        return nr;
+    };
+    Pm.nrun = runs(u, Pm.run);
+    Pm.nrun2 = runs(u2, Pm.run2);
     static bool attr = false;
     static int resident[2] = {1, 1};  // CTAs per SM at the largest table, without / with IEEE output
     if (!attr) {
