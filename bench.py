@@ -43,7 +43,7 @@ HBM_PEAK_FALLBACK = 6800.0
 # launch). Traffic grows with the state, so the n = 30 entries are those figures times 8 and 64.
 NCU_TRAFFIC = {("dense_df", 27): 4232672512, ("dense_df", 30): 4232672512 * 8,
                ("dense_oz", 24): 475004672, ("dense_oz", 30): 475004672 * 64,
-               ("dense_oz5", 24): 475586560, ("dense_oz5", 30): 475586560 * 64}
+               ("dense_oz5", 24): 472413952, ("dense_oz5", 30): 472413952 * 64}
 
 
 def parse():
