@@ -184,19 +184,22 @@ __device__ __forceinline__ double widen_float_int(float f) {
 
 // RN(hi + lo) as a double for a double-float pair, on the integer pipes when both are normal and
 // lo's exponent is 24..55 below hi's (every pair with |lo| <= ulp(hi)/2 has it at least 24
-// below). In units of the last place of a double with hi's exponent, hi is its significand
-// times 2^29 and |lo| = L + F / 2^s: for a gap d <= 29 an integer (F = 0), for d = 29 + s a
-// 32-bit integer part and an s-bit fraction. The sum or difference is formed on the 53-bit
-// significand and rounded to nearest-even from F, with selects rather than branches on the
-// gap and the signs; a difference that drops below 2^52 moves up one bit when exact (F = 0).
-// Otherwise (zero hi, subnormal, non-finite, lo far smaller, a rounded difference below 2^52)
-// the FP64 add.
+// below). In units of the last place of a double with hi's exponent, |lo| = L + F / 2^s: for a
+// gap d <= 29 an integer (F = 0), for d = 29 + s a 32-bit integer part and an s-bit fraction.
+// Rounded to nearest-even from F, the change of hi's significand is + L (+1) for equal signs and
+// - (L + [F != 0]) (+1) for opposite ones; it never leaves hi's binade except below a power of
+// two, so it is added to the bit pattern of hi as a double (a carry into the exponent is the
+// exact power of two). Selects, not branches, on the gap and the signs. Otherwise (zero hi,
+// subnormal, non-finite, lo far smaller, a power-of-two hi with lo of the other sign) the FP64
+// add.
 __device__ __forceinline__ double join_df_int(float hi, float lo) {
     const uint32_t uh = __float_as_uint(hi), ul = __float_as_uint(lo);
     if ((ul << 1) == 0u) return widen_float_int(hi);
     const uint32_t eh = (uh >> 23) & 0xFFu, el = (ul >> 23) & 0xFFu;
     const uint32_t d = eh - el;
-    if (eh == 0u || eh == 255u || el == 0u || d - 24u > 31u) return widen_float_int(hi) + widen_float_int(lo);
+    const bool sub = ((uh ^ ul) >> 31) != 0u;
+    if (eh == 0u || eh == 255u || el == 0u || d - 24u > 31u || (sub && (uh & 0x7FFFFFu) == 0u))
+        return widen_float_int(hi) + widen_float_int(lo);
     const uint32_t ml = (ul & 0x7FFFFFu) | 0x800000u;
     const uint32_t sl = d < 29u ? 29u - d : 0u;  // d <= 29: lo's bits all land on the significand
     const uint32_t sr = d > 29u ? d - 29u : 0u;  // d > 29: sr bits of lo below it
@@ -204,20 +207,13 @@ __device__ __forceinline__ double join_df_int(float hi, float lo) {
     const uint32_t F = ml & ((1u << sr) - 1u);
     const uint32_t half = (1u << sr) >> 1;
     const uint32_t frac = F != 0u ? 1u : 0u;
-    const bool sub = ((uh ^ ul) >> 31) != 0u;
-    uint64_t m = uint64_t((uh & 0x7FFFFFu) | 0x800000u) << 29;
-    uint64_t e = uint64_t(eh) + 896u;  // biased double exponent of hi
-    // sum: m + L, rounded up on F; difference: m - L - 1 + (1 - F / 2^sr) when F != 0
-    m = sub ? m - (uint64_t(L) + frac) : m + L;
-    const uint32_t odd = uint32_t(m) & 1u;
+    const uint32_t t = sub ? L + frac : L;  // the parity of the significand after the change
+    const uint32_t odd = t & 1u;
     const uint32_t up = sub ? (frac && (F < half || (F == half && odd))) : (F > half || (frac && F == half && odd));
-    if (m < (1ull << 52)) {  // a difference that left hi's binade
-        if (frac) return widen_float_int(hi) + widen_float_int(lo);
-        m <<= 1;
-        e -= 1;
-    }
-    m += up;
-    return __longlong_as_double(static_cast<long long>((uint64_t(uh >> 31) << 63) | (e << 52) | (m & ((1ull << 52) - 1))));
+    const long long dm = sub ? (long long)up - (long long)t : (long long)t + (long long)up;
+    const uint32_t w_hi = (uh & 0x80000000u) | ((eh + 896u) << 20) | ((uh & 0x7FFFFFu) >> 3);
+    const uint32_t w_lo = uh << 29;
+    return __longlong_as_double(__double_as_longlong(__hiloint2double(int(w_hi), int(w_lo))) + dm);
 }
 
 }  // namespace qs
