@@ -597,10 +597,15 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
     };
 
     // per tile j: loads of tile j + 1; fold half 0 of tile j - 1 (its half 1 MMAs may still
-    // run), then half 1; slice tile j into the (now free) buffer; start the MMAs of tile j
+    // run), then half 1; slice tile j into the (now free) buffer; start the MMAs of tile j.
+    // Every thread waits on the commit barriers itself (no block barrier after the wait). A wait
+    // that runs out in any lane marks the warp, and s_fail the block; after the next block
+    // barrier every thread has seen s_fail, so none waits or folds again and no MMAs are issued:
+    // the loop ends with the same barriers in every thread.
     float4 vcur[kOz5Amps], vnext[kOz5Amps];
     uint64_t x0_cur = 0, x0_prev = 0;
     float nv_prev = 1.f;
+    bool failed = false;
     if (my_tiles > 0) {
         x0_cur = group_x0(0);
         load(x0_cur, vcur);
@@ -612,32 +617,33 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
             load(x0_next, vnext);
         }
         if (j >= 1) {
-            bool failed = false;
 #pragma unroll
             for (int hv = 0; hv < 2; hv++) {
-                if (tid == 0 && !mbar_wait(smem_u32(&mbar[hv]), uint32_t((j - 1) & 1))) s_fail = 1;
-                __syncthreads();
-                if (s_fail) {
-                    failed = true;
-                    break;
+                if (!failed) {  // warp-uniform; the vote also reconverges the warp for tcgen05.ld
+                    const bool late = !mbar_wait(smem_u32(&mbar[hv]), uint32_t((j - 1) & 1));
+                    if (__any_sync(0xffffffffu, late)) {
+                        failed = true;
+                        s_fail = 1;
+                    }
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                epilogue(hv, x0_prev, nv_prev);
+                if (!failed) epilogue(hv, x0_prev, nv_prev);
             }
-            if (failed) break;
         }
         float nv_cur = 1.f;
         if (j < my_tiles) nv_cur = slice(vcur);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();  // slices of tile j written; accumulators of tile j - 1 read
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (j < my_tiles) issue();
+        if (s_fail) failed = true;
+        if (j < my_tiles && !failed) issue();
         x0_prev = x0_cur;
         nv_prev = nv_cur;
         x0_cur = x0_next;
 #pragma unroll
         for (int i = 0; i < kOz5Amps; i++) vcur[i] = vnext[i];
     }
+    __syncthreads();  // every thread's s_fail store is visible
     if (s_fail && tid == 0) {
         atomicExch(err, 1);
         // bounded: let the MMAs in flight finish before TMEM is freed
