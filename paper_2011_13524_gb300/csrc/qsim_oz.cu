@@ -346,6 +346,7 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
     float4 vcur[kOzAmpsPerThread], vnext[kOzAmpsPerThread];
     uint64_t x0_cur = 0, x0_prev = 0;
     float nv_prev = 1.f;
+    bool failed = false;  // a commit wait ran out (warp-uniform, block-uniform after a barrier)
     if (my_tiles > 0) {
         x0_cur = group_x0(0);
         load(x0_cur, vcur);
@@ -359,22 +360,28 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
         float nv_cur = 1.f;
         if (j < my_tiles) nv_cur = slice(j, vcur);  // abuf(j) was read by the MMAs of tile j - 2
         if (j >= 1) {
-            if (tid == 0 && !mbar_wait(smem_u32(&mbar), uint32_t((j - 1) & 1))) s_fail = 1;
-            __syncthreads();
-            if (s_fail) break;
+            if (!failed) {  // every thread waits itself; the vote reconverges the warp for tcgen05.ld
+                const bool late = !mbar_wait(smem_u32(&mbar), uint32_t((j - 1) & 1));
+                if (__any_sync(0xffffffffu, late)) {
+                    failed = true;
+                    s_fail = 1;
+                }
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            epilogue(x0_prev, nv_prev);
+            if (!failed) epilogue(x0_prev, nv_prev);
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();  // slices of tile j written; accumulators of tile j - 1 read
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (j < my_tiles) issue(j);
+        if (s_fail) failed = true;  // block-uniform from here
+        if (j < my_tiles && !failed) issue(j);
         x0_prev = x0_cur;
         nv_prev = nv_cur;
         x0_cur = x0_next;
 #pragma unroll
         for (int i = 0; i < kOzAmpsPerThread; i++) vcur[i] = vnext[i];
     }
+    __syncthreads();  // every thread's s_fail store is visible
     if (s_fail && tid == 0) {
         atomicExch(err, 1);
         mbar_wait(smem_u32(&mbar), 0);  // bounded: let the MMAs in flight finish before TMEM is freed
@@ -854,6 +861,7 @@ __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(f
     float2 vcur[B::Amps], vnext[B::Amps];
     uint64_t x0_cur = 0, x0_prev = 0;
     float nv_prev = 1.f;
+    bool failed = false;  // a commit wait ran out (warp-uniform, block-uniform after a barrier)
     if (my_tiles > 0) {
         x0_cur = group_x0(0);
         load(x0_cur, vcur);
@@ -865,24 +873,30 @@ __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(f
             load(x0_next, vnext);
         }
         if (j >= 1) {
-            if (tid == 0 && !mbar_wait(smem_u32(&mbar), uint32_t((j - 1) & 1))) s_fail = 1;
-            __syncthreads();
-            if (s_fail) break;
+            if (!failed) {  // every thread waits itself; the vote reconverges the warp for tcgen05.ld
+                const bool late = !mbar_wait(smem_u32(&mbar), uint32_t((j - 1) & 1));
+                if (__any_sync(0xffffffffu, late)) {
+                    failed = true;
+                    s_fail = 1;
+                }
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            epilogue(x0_prev, nv_prev);
+            if (!failed) epilogue(x0_prev, nv_prev);
         }
         float nv_cur = 1.f;
         if (j < my_tiles) nv_cur = slice(vcur);  // the buffer was read by the MMAs of tile j - 1 (done)
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();  // slices of tile j written; accumulators of tile j - 1 read
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (j < my_tiles) issue();
+        if (s_fail) failed = true;  // block-uniform from here
+        if (j < my_tiles && !failed) issue();
         x0_prev = x0_cur;
         nv_prev = nv_cur;
         x0_cur = x0_next;
 #pragma unroll
         for (int i = 0; i < B::Amps; i++) vcur[i] = vnext[i];
     }
+    __syncthreads();  // every thread's s_fail store is visible
     if (s_fail && tid == 0) {
         atomicExch(err, 1);
         mbar_wait(smem_u32(&mbar), 0);  // bounded: let the MMAs in flight finish before TMEM is freed
