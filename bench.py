@@ -38,12 +38,10 @@ METRIC = "state-vector GB/s & gates/s at n=30 c128 vs HBM peak; adjoint-grad ms;
 HBM_PEAK_FALLBACK = 6800.0
 # DRAM bytes (read + write) per launch from one ncu capture, keyed by kernel; filled in only
 # for a kernel unchanged since the capture (profiles/<kernel>_<workload>.md gives the command).
-# k_dense_reg<DFArith, 2>: captured at n = 27 (2 GiB state, 4.233e9 bytes per launch);
-# k_dense_oz4 and k_dense_oz5: captured at n = 24 (256 MiB state, 4.750e8 and 4.756e8 bytes per
-# launch). Traffic grows with the state, so the n = 30 entries are those figures times 8 and 64.
-NCU_TRAFFIC = {("dense_df", 27): 4232672512, ("dense_df", 30): 4232672512 * 8,
-               ("dense_oz", 24): 475004672, ("dense_oz", 30): 475004672 * 64,
-               ("dense_oz5", 24): 472413952, ("dense_oz5", 30): 472413952 * 64}
+# k_dense_reg<DFArith, 2>: captured at n = 27 (2 GiB state, 4.233e9 bytes per launch); traffic
+# grows with the state, so the n = 30 entry is that figure times 8. The tensor-core kernels
+# (k_dense_oz4, k_dense_oz5) changed after their last capture, so they report none.
+NCU_TRAFFIC = {("dense_df", 27): 4232672512, ("dense_df", 30): 4232672512 * 8}
 
 
 def parse():
