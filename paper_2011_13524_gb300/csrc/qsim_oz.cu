@@ -30,8 +30,11 @@
 // needed (for low targets the loads and stores are strided; the rest of each 32-byte sector is
 // touched by the same thread and served by L2). Per tile j: the loads of tile j + 1 are issued,
 // tile j is sliced into the second slice buffer while the MMAs of tile j - 1 run, tile j - 1's
-// accumulators are folded and stored, and the MMAs of tile j start. Every mbarrier wait is
-// bounded; on expiry the kernel records an error, waits (bounded) for its MMAs and frees TMEM.
+// accumulators are folded and stored, and the MMAs of tile j start. One thread issues the MMAs
+// and commits them to an mbarrier; every thread waits on that mbarrier itself before it reads
+// the accumulators (no block barrier after the wait). Every wait is bounded; on expiry the warp
+// (by a vote) and then the block stop folding and issuing, the kernel records an error, waits
+// (bounded) for its MMAs and frees TMEM.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
