@@ -206,3 +206,31 @@ def test_df_layout_round_trip_bit_exact(df):
     want = hi.astype(np.float64) + lo.astype(np.float64)
     assert np.array_equal(np.ascontiguousarray(got).view(np.float64).view(np.uint64), want.view(np.uint64))
     st.close()
+
+
+def test_df_layout_round_trip_near_powers_of_two(df):
+    """Doubles just below and above powers of two (hi = 2^k with lo of either sign, the join's
+    binade edge and its FP64 fallback), long runs of ones, and lo exponents 24..60 below hi's:
+    in place to double-float and back gives exactly RN(hi + lo) of numpy's float32 split."""
+    qs = df
+    n = 12
+    rng = np.random.default_rng(4242)
+    N = 1 << n
+    k = rng.integers(-60, 60, 2 * N)
+    eps = np.ldexp(1.0, -rng.integers(24, 61, 2 * N))
+    kind = rng.integers(0, 4, 2 * N)
+    base = np.ldexp(1.0, k)
+    vals = np.where(kind == 0, base * (1 - eps), np.where(kind == 1, base * (1 + eps),
+                    np.where(kind == 2, base * (1 - eps) * (1 - 2.0 ** -53), base * (1.5 + eps))))
+    vals *= rng.choice([-1.0, 1.0], 2 * N)
+    psi0 = vals[0::2] + 1j * vals[1::2]
+    st = qs.State(n, qs.QS_C128)
+    st.load(psi0)
+    st.run(W.Circuit(n, []), 0)
+    got = st.get_vector()
+    re = np.ascontiguousarray(psi0).view(np.float64)
+    hi = re.astype(np.float32)
+    lo = (re - hi.astype(np.float64)).astype(np.float32)
+    want = hi.astype(np.float64) + lo.astype(np.float64)
+    assert np.array_equal(np.ascontiguousarray(got).view(np.float64).view(np.uint64), want.view(np.uint64))
+    st.close()
