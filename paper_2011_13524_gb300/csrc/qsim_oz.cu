@@ -103,6 +103,21 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, 
         "l"(a), "l"(b), "r"(id), "r"(acc));
 }
 
+// The threads that hold groups 32 s .. 32 s + 31 of a tile (group = tid mod 128, so the warps
+// with warp mod 4 = s: a quarter of the block) meet at named barrier 1 + s; shared-memory writes
+// before it are visible to those threads after it.
+// (Constant barrier ids, so that the kernel reserves five hardware barriers, not all sixteen.)
+template <int kBlockThreads>
+__device__ __forceinline__ void group_set_sync(int warp) {
+    constexpr int n = kBlockThreads / 4;
+    switch (warp & 3) {  // warp-uniform
+        case 0: asm volatile("bar.sync 1, %0;" ::"n"(n) : "memory"); break;
+        case 1: asm volatile("bar.sync 2, %0;" ::"n"(n) : "memory"); break;
+        case 2: asm volatile("bar.sync 3, %0;" ::"n"(n) : "memory"); break;
+        default: asm volatile("bar.sync 4, %0;" ::"n"(n) : "memory"); break;
+    }
+}
+
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     for (long long spins = 0; spins < kOzSpinLimit; spins++) {
         uint32_t done;
@@ -251,7 +266,7 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
 #pragma unroll
         for (int i = 0; i < kOzAmpsPerThread; i++) m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].z)));
         nu_part[h * kOzTG + g] = m;
-        __syncthreads();
+        group_set_sync<kOzThreads>(warp);  // the other thread of each group is in warp +- 4
         m = fmaxf(nu_part[g], nu_part[kOzTG + g]);
         const float nv = pow2_ceil(m);
         const float inv = __uint_as_float((254u - (__float_as_uint(nv) >> 23)) << 23);
@@ -510,7 +525,7 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
 #pragma unroll
         for (int i = 0; i < kOz5Amps; i++) m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].z)));
         nu_part[q * kOzTG + g] = m;
-        __syncthreads();
+        group_set_sync<kOz5Threads>(warp);  // a group's four threads are in warps w, w + 4, w + 8, w + 12
         m = nu_part[g];
 #pragma unroll
         for (int t = 1; t < kOz5TPG; t++) m = fmaxf(m, nu_part[t * kOzTG + g]);
@@ -785,7 +800,7 @@ __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(f
 #pragma unroll
         for (int i = 0; i < B::Amps; i++) m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
         nu_part[h * kOzTG + g] = m;
-        __syncthreads();
+        group_set_sync<B::Threads>(warp);  // a group's threads are in the warps with the same warp mod 4
         m = nu_part[g];
 #pragma unroll
         for (int t = 1; t < B::Tpg; t++) m = fmaxf(m, nu_part[t * kOzTG + g]);
