@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
     float4 vcur[kOzAmpsPerThread], vnext[kOzAmpsPerThread];
     uint64_t x0_cur = 0, x0_prev = 0;
     float nv_prev = 1.f;
-    bool failed = false;  // a commit wait ran out (warp-uniform, block-uniform after a barrier)
+    bool failed = false;  // a commit wait ran out in this warp, or s_fail was seen (warp-uniform)
     if (my_tiles > 0) {
         x0_cur = group_x0(0);
         load(x0_cur, vcur);
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();  // slices of tile j written; accumulators of tile j - 1 read
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (s_fail) failed = true;  // block-uniform from here
+        if (s_fail) failed = true;  // read by a converged warp: stays warp-uniform
         if (j < my_tiles && !failed) issue(j);
         x0_prev = x0_cur;
         nv_prev = nv_cur;
@@ -624,9 +624,10 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
     // per tile j: loads of tile j + 1; fold half 0 of tile j - 1 (its half 1 MMAs may still
     // run), then half 1; slice tile j into the (now free) buffer; start the MMAs of tile j.
     // Every thread waits on the commit barriers itself (no block barrier after the wait). A wait
-    // that runs out in any lane marks the warp, and s_fail the block; after the next block
-    // barrier every thread has seen s_fail, so none waits or folds again and no MMAs are issued:
-    // the loop ends with the same barriers in every thread.
+    // that runs out in any lane marks the warp (a vote, so that `failed` stays warp-uniform for
+    // the warp-wide tcgen05.ld) and sets s_fail; a warp that reads s_fail after a block barrier
+    // stops waiting and folding, and thread 0 then issues no more MMAs. Every thread passes the
+    // same barriers, and every wait is bounded.
     float4 vcur[kOz5Amps], vnext[kOz5Amps];
     uint64_t x0_cur = 0, x0_prev = 0;
     float nv_prev = 1.f;
@@ -879,7 +880,7 @@ __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(f
     float2 vcur[B::Amps], vnext[B::Amps];
     uint64_t x0_cur = 0, x0_prev = 0;
     float nv_prev = 1.f;
-    bool failed = false;  // a commit wait ran out (warp-uniform, block-uniform after a barrier)
+    bool failed = false;  // a commit wait ran out in this warp, or s_fail was seen (warp-uniform)
     if (my_tiles > 0) {
         x0_cur = group_x0(0);
         load(x0_cur, vcur);
@@ -906,7 +907,7 @@ __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(f
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();  // slices of tile j written; accumulators of tile j - 1 read
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (s_fail) failed = true;  // block-uniform from here
+        if (s_fail) failed = true;  // read by a converged warp: stays warp-uniform
         if (j < my_tiles && !failed) issue();
         x0_prev = x0_cur;
         nv_prev = nv_cur;
