@@ -319,3 +319,35 @@ def test_layout_passes_folded_into_first_and_last_blocks():
     finally:
         qs.set_c128_math(old_m)
         qs.set_tensor_cores(old_t)
+
+
+def test_diagonal_run_table_limits():
+    """A diagonal run's two tables at their limits (host only): three 4-qubit diagonals fill the
+    first table (12 qubits), two more fill the second (8), and the next one, on 4 new qubits, fits
+    neither and starts a second run; a diagonal whose qubits all lie in one table joins the run
+    (one whose qubits straddle both tables would not)."""
+    n = 28
+    rng = W.SplitMix64(2828)
+
+    def diag(qubits):
+        d = np.exp(1j * 2 * np.pi * np.array([rng.uniform() for _ in range(1 << len(qubits))]))
+        return W.Gate("DIAG", tuple(qubits), matrix=d)
+
+    gates = [diag(range(4 * b, 4 * b + 4)) for b in range(5)]   # qubits 0..19
+    gates.append(diag((0, 5, 10, 11)))                           # inside the first table
+    gates.append(diag(range(20, 24)))                            # fits neither table
+    gates.append(diag(range(24, 28)))
+    plan = qs.FusedCircuit(W.Circuit(n, gates), 4)
+    blocks = [tuple(sorted(plan.block(b)[0])) for b in range(plan.n_blocks)]
+    launches = [plan.block_cost(b, qs.QS_C128)[1] for b in range(plan.n_blocks)]
+    assert len(blocks) == len(gates), blocks
+    first_run = [i for i, b in enumerate(blocks) if max(b) < 20]
+    assert len(first_run) == 6 and launches[first_run[0]] == 1
+    assert all(launches[i] == 0 for i in first_run[1:])
+    later = [i for i in range(len(blocks)) if i not in first_run]
+    assert sorted(launches[i] for i in later) == [0, 1], (blocks, launches)
+    # qubits in both tables: the block fits neither table alone and starts a new run
+    gates2 = gates[:5] + [diag((0, 5, 10, 15))]
+    plan2 = qs.FusedCircuit(W.Circuit(n, gates2), 4)
+    launches2 = [plan2.block_cost(b, qs.QS_C128)[1] for b in range(plan2.n_blocks)]
+    assert plan2.n_blocks == 6 and launches2 == [1, 0, 0, 0, 0, 1], launches2
