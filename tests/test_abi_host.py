@@ -312,6 +312,8 @@ def test_layout_passes_folded_into_first_and_last_blocks():
         assert p5.layout_passes(qs.QS_C128) == 1
         assert p3.layout_passes(qs.QS_C128) == 2
         assert p4.layout_passes(qs.QS_C64) == 0
+        # the benchmark circuit (n = 30, depth 20) at k = 5: both changes folded
+        assert qs.FusedCircuit(W.u3cz_circuit(30, 20, 20201127), 5).layout_passes(qs.QS_C128) == 0
         qs.set_tensor_cores(0)  # CUDA-core first block: the entry change is a pass of its own
         assert p4.layout_passes(qs.QS_C128) == 1
         qs.set_c128_math(qs.QS_MATH_FP64)
