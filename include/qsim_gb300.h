@@ -277,13 +277,13 @@ qs_status qs_expectation(const qs_state* s, const qs_pauli_obs* obs, double out[
  * *n_single (optional) = the reads of single groups that fit no tile. */
 qs_status qs_expectation_plan(int n, const qs_pauli_obs* obs, int* n_passes, uint64_t* tile_masks, int cap,
                               int* n_single);
-/* Allocation-free expectation, for callers that cannot allocate device memory: code that runs
- * while a stream is being captured into a CUDA graph (cudaMalloc is not allowed there), hosts
- * whose every device byte belongs to another allocator or a fixed budget, and loops that must not
- * touch the allocator at all. Same value as qs_expectation (within FP64 rounding of the block
- * count), computed from caller-owned memory: dev_psi holds 2^n amplitudes of type dt in the IEEE
- * layout (16-byte aligned), out (host) receives (re, im). The paper has no counterpart; it exists
- * for these callers only.
+/* Allocation-free expectation, for callers that cannot allocate device memory: a process whose
+ * device memory is all reserved by another allocator (a framework's caching pool) or held to a
+ * fixed budget, where a cudaMalloc would fail or break the budget, and loops that must not call
+ * the allocator at all because cudaMalloc and cudaFree can synchronise the whole device. Same
+ * value as qs_expectation (within FP64 rounding of the block count), computed from caller-owned
+ * memory: dev_psi holds 2^n amplitudes of type dt in the IEEE layout (16-byte aligned), out
+ * (host) receives (re, im). The paper has no counterpart; it exists for these callers only.
  * It calls no cudaMalloc, cudaFree or other allocating routine. Its per-block partial sums live
  * in one fixed 512 KiB array in device memory that every GPU loading the library keeps until the
  * process exits. The first call on a device looks up that array's address (once per device, with
@@ -291,7 +291,8 @@ qs_status qs_expectation_plan(int n, const qs_pauli_obs* obs, int* n_passes, uin
  * array and each block overwrites its own slots, so nothing needs clearing, but calls that overlap
  * on the GPU (other streams, other threads) race on it: serialise them. The launches share the
  * array's 32767 block partials (grids shrink to fit); an observable that needs more launches than
- * that is rejected with QS_ERR_INVALID_ARG before any launch. Runs on `stream`; synchronises. */
+ * that is rejected with QS_ERR_INVALID_ARG before any launch. Runs on `stream`, then copies the
+ * result to `out` and synchronises `stream` before returning. */
 qs_status qs_expectation_noalloc(const void* dev_psi, int n, qs_dtype dt, void* stream, const qs_pauli_obs* obs,
                                  double out[2]);
 /* out = <a|b> (Sec. 4.2.2 inner_product) as (re, im); same n and dtype; synchronises. */
