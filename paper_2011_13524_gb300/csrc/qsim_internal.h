@@ -326,6 +326,8 @@ void prepare_bz_matrix(int q, const std::vector<cplx>& K, unsigned char* host_ou
 void launch_dense_bz(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
                      const std::vector<int>& cvals, const void* dmat, cudaStream_t st);
 bool oz_error_pending();
+// try_wait attempts of the tensor-core kernels' pipeline waits before they give up (< 0: default)
+void oz_set_wait_spins(long long spins);
 
 // complex128 arithmetic mode (QS_MATH_FP64 / QS_MATH_DF)
 int c128_math();

@@ -36,8 +36,10 @@
 // (by a vote) and then the block stop folding and issuing, the kernel records an error, waits
 // (bounded) for its MMAs and frees TMEM.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "qsim_arith.cuh"
 
@@ -412,38 +414,59 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
 
 // ---------------------------------------------------------------- 5-target blocks
 // The same method for 32 x 32 complex blocks: A is the 64 x 64 real form, K = 64 (four K-steps),
-// 128 groups of 32 amplitudes per tile. The accumulators of all 64 output reals (7 x 64 TMEM
-// columns) would leave no room for a second set, so the outputs are split into two halves of
-// 32 reals (amplitudes 0..15 and 16..31), each with its own stacked matrix slices (192 x 64),
-// seven diagonals of 32 columns (TMEM columns 0..223 and 256..479) and its own commit barrier:
-// half 0 is folded while the MMAs of half 1 still run. One CTA per SM (512 threads: four per
-// group, each owning four amplitudes of either half; 146 KB of shared memory with one state
-// slice buffer of 96 KB; all 512 TMEM columns).
+// 128 groups of 32 amplitudes per tile. The outputs are split into two halves of 32 reals
+// (amplitudes 0..15 and 16..31), each with its own stacked matrix slices (192 x 64), seven
+// diagonals of 32 columns (TMEM columns 0..223 and 256..479) and its own commit barrier.
+//
+// Warp roles: sixteen worker warps (four threads per group, each owning four amplitudes of either
+// half) load, slice and fold; one more warp issues the MMAs. The state slices are double-buffered
+// so that a tile's MMAs run while the workers slice the next tile: slices 0..4 of a buffer sit in
+// shared memory (80 KB each, 2 x 80 + 48 KB of matrix slices = 210 KB) and slice 5 is the MMA's A
+// operand straight from TMEM (32 columns per buffer, in the two 32-column gaps after each half's
+// accumulators: all 512 columns). Hand-offs are mbarriers, no block barrier inside the loop:
+//   full[b]     the 16 worker warps have written the slices of the tile in buffer b
+//   accfree[h]  the 16 worker warps have read half h's accumulators (fold done)
+//   done[h]     commit of half h's MMAs (the tensor cores finished them)
+// Per tile j a worker issues the loads of tile j + 1, slices tile j into buffer j & 1 (free: the
+// MMAs of tile j - 2 finished before its fold), then waits for and folds half 0 and half 1 of tile
+// j - 1. The issuer waits for full[j & 1], then for each half for accfree of tile j - 1 and issues
+// that half's 28 MMAs: half 0 of tile j runs while the workers fold half 1 of tile j - 1 and slice
+// tile j + 1. Every wait is bounded; a wait that runs out sets a shared flag that makes every other
+// wait give up at once, the kernel records an error, and the issuer waits (bounded, with the full
+// limit) for the MMAs it issued before TMEM is freed.
 constexpr int kOz5Q = 5;
 constexpr int kOz5D = 1 << kOz5Q;                               // 32 amplitudes per group
 constexpr int kOz5R = 2 * kOz5D;                                // 64 reals per group
-constexpr int kOz5Threads = 512;
-constexpr int kOz5TPG = kOz5Threads / kOzTG;                    // 4 threads per group
+constexpr int kOz5Workers = 512;                                // 16 worker warps
+constexpr int kOz5WorkerWarps = kOz5Workers / 32;
+constexpr int kOz5Threads = kOz5Workers + 32;                   // + the MMA-issuing warp
+constexpr int kOz5TPG = kOz5Workers / kOzTG;                    // 4 threads per group
 constexpr int kOz5Amps = kOz5D / kOz5TPG;                       // 8 amplitudes per thread
 constexpr uint32_t kOz5Sbo = (kOz5R / 8) * 128;                 // 1024
 constexpr size_t kOz5Slice = size_t(kOzTG) * kOz5R * 2;         // 16 KB
-constexpr size_t kOz5ABuf = kOzNS * kOz5Slice;                  // 96 KB
+constexpr int kOz5SmemSlices = kOzNS - 1;                       // slices 0..4 in shared memory
+constexpr size_t kOz5ABuf = kOz5SmemSlices * kOz5Slice;         // 80 KB per buffer
 constexpr int kOz5HalfRows = kOzNS * kOz5D;                     // 192 rows per half stack
 constexpr size_t kOz5Half = size_t(kOz5HalfRows) * kOz5R * 2;   // 24 KB
 constexpr size_t kOz5Mat = 2 * kOz5Half;                        // 48 KB
 constexpr int kOz5TmemCols = 512;
 constexpr uint32_t kOz5HalfCol = 256;
-constexpr size_t kOff5A = 0;
-constexpr size_t kOff5Mat = kOff5A + kOz5ABuf;
+constexpr uint32_t kOz5A5Col = kOzND * kOz5D;                   // slice 5 of buffer b at b * 256 + 224
+constexpr size_t kOff5A = 0;                                    // 2 buffers
+constexpr size_t kOff5Mat = kOff5A + 2 * kOz5ABuf;
 constexpr size_t kOff5Mu = kOff5Mat + kOz5Mat;
 constexpr size_t kOff5NuPart = kOff5Mu + kOz5R * 4;
 constexpr size_t kOz5Smem = kOff5NuPart + size_t(kOz5TPG) * kOzTG * 4;
-static_assert(kOzND * kOz5D <= int(kOz5HalfCol), "a half's accumulators fit its TMEM columns");
+static_assert(kOzND * kOz5D <= int(kOz5A5Col) && kOz5A5Col + kOz5R / 2 <= kOz5HalfCol,
+              "a half's accumulators and one slice-5 buffer fit its 256 TMEM columns");
+static_assert(kOz5Smem <= 227 * 1024, "shared memory of one CTA");
+static_assert(kOz5Threads * 120 <= 65536, "120 registers per thread");
 
 struct Oz5Params {
     IndexPlan ip;            // 5 targets (and controls) inserted
     uint64_t offs[kOz5D];    // s(w), targets ascending
     uint64_t n_groups;
+    long long wait_spins;    // try_wait attempts of each pipeline wait before it gives up
 };
 
 __device__ __forceinline__ uint32_t kmaj5(uint32_t r, uint32_t k) {
@@ -457,27 +480,56 @@ __device__ __forceinline__ uint64_t sdesc5(uint32_t saddr) {
     return d;
 }
 
+// A operand from TMEM (lane m = row m of the tile, column c = K elements 2c (low) and 2c + 1)
+__device__ __forceinline__ void mma_bf16_tmem_a(uint32_t tmem, uint32_t a_tmem, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem),
+        "r"(a_tmem), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
+}
+
+// bounded wait for the phase of the given parity; gives up at once when *abort is set
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t mbar, uint32_t parity, long long spins,
+                                                   const volatile int* abort) {
+    for (long long i = 0; i <= spins; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (*abort) return false;
+    }
+    return false;
+}
+
 template <bool kPairs, bool kIeeeIn>
 __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict__ psi,
                                                                const unsigned char* __restrict__ dmat,
                                                                const __grid_constant__ Oz5Params P, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    // full[0..1], accfree[0..1], done[0..1], drain
+    __shared__ __align__(8) uint64_t bars[7];
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    // thread (g, q): group g of the tile (= TMEM lane); amplitudes 4q..4q+3 (half 0) and
-    // 16+4q..16+4q+3 (half 1), held as v[0..3] and v[4..7]
-    const int g = tid & (kOzTG - 1), q = tid >> 7;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float* mu = reinterpret_cast<const float*>(smem + kOff5Mu);
     float* nu_part = reinterpret_cast<float*>(smem + kOff5NuPart);
-    unsigned char* ab = smem + kOff5A;
+    const uint32_t full0 = smem_u32(&bars[0]), accfree0 = smem_u32(&bars[2]), done0 = smem_u32(&bars[4]);
+    const uint32_t drain = smem_u32(&bars[6]);
+    volatile int* fail = &s_fail;
 
     for (int i = tid; i < int((kOz5Mat + kOz5R * 4) / 16); i += kOz5Threads)
         reinterpret_cast<uint4*>(smem + kOff5Mat)[i] = reinterpret_cast<const uint4*>(dmat)[i];
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        for (int i = 0; i < 4; i++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full0 + 8u * i), "r"(kOz5WorkerWarps));
+        for (int i = 4; i < 7; i++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8u * i));
         s_fail = 0;
     }
     if (warp == 0) {
@@ -491,195 +543,242 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
     const uint32_t tmem = tmem_base;
     const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
     const uint64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-    uint64_t off[kOz5Amps];
-#pragma unroll
-    for (int i = 0; i < kOz5Amps; i++) off[i] = P.offs[(i >> 2) * (kOz5D / 2) + 4 * q + (i & 3)];
+    const long long spins = P.wait_spins;
 
-    auto group_x0 = [&](uint64_t j) {
-        const uint64_t gi = (blockIdx.x + j * gridDim.x) * kOzTG + uint64_t(g);
-        return gi < P.n_groups ? expand(gi, P.ip) : ~0ull;
-    };
-    auto load = [&](uint64_t x0, float4 (&v)[kOz5Amps]) {
-        if (kPairs) {
-#pragma unroll
-            for (int i = 0; i < kOz5Amps; i += 2) {
-                if (x0 != ~0ull) {
-                    ld_pair(psi + x0 + off[i], v[i], v[i + 1]);
-                } else {
-                    v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    v[i + 1] = v[i];
-                }
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < kOz5Amps; i++)
-                v[i] = x0 != ~0ull ? __ldcg(psi + x0 + off[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        if (kIeeeIn) {
-#pragma unroll
-            for (int i = 0; i < kOz5Amps; i++) v[i] = df_of_ieee(v[i]);
-        }
-    };
-    auto slice = [&](const float4 (&v)[kOz5Amps]) {
-        float m = 0.f;
-#pragma unroll
-        for (int i = 0; i < kOz5Amps; i++) m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].z)));
-        nu_part[q * kOzTG + g] = m;
-        group_set_sync<kOz5Threads>(warp);  // a group's four threads are in warps w, w + 4, w + 8, w + 12
-        m = nu_part[g];
-#pragma unroll
-        for (int t = 1; t < kOz5TPG; t++) m = fmaxf(m, nu_part[t * kOzTG + g]);
-        const float nv = pow2_ceil(m);
-        const float inv = __uint_as_float((254u - (__float_as_uint(nv) >> 23)) << 23);
-#pragma unroll
-        for (int c = 0; c < 2; c++) {  // 4 amplitudes = K columns 32c + 8q .. +7: one 16-byte chunk per slice
-            uint32_t pk[kOzNS][4];
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-                float ar[kOzNS], ai[kOzNS];
-                slice6(v[4 * c + i].x, v[4 * c + i].y, inv, ar);
-                slice6(v[4 * c + i].z, v[4 * c + i].w, inv, ai);
-#pragma unroll
-                for (int s2 = 0; s2 < kOzNS; s2++) pk[s2][i] = pack_bf16(ar[s2], ai[s2]);
-            }
-            const uint32_t o = kmaj5(uint32_t(g), uint32_t(32 * c + 8 * q));
-#pragma unroll
-            for (int s2 = 0; s2 < kOzNS; s2++)
-                *reinterpret_cast<uint4*>(ab + s2 * kOz5Slice + o) = make_uint4(pk[s2][0], pk[s2][1], pk[s2][2], pk[s2][3]);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        return nv;
-    };
-    auto issue = [&]() {  // MMAs of the tile in the slice buffer: half 0, commit, half 1, commit
-        if (tid != 0) return;
-        const uint32_t a0 = smem_u32(ab), m0 = smem_u32(smem + kOff5Mat);
-#pragma unroll
-        for (int hv = 0; hv < 2; hv++) {
-            auto prod = [&](int s2, int t0, int nt, int ks, uint32_t acc) {
-                mma_bf16(tmem + kOz5HalfCol * uint32_t(hv) + uint32_t((s2 + t0) * kOz5D),
-                         sdesc5(a0 + uint32_t(s2 * kOz5Slice) + uint32_t(ks * 256)),
-                         sdesc5(m0 + uint32_t(hv * kOz5Half) + uint32_t(t0 * kOz5D / 8) * kOz5Sbo + uint32_t(ks * 256)),
-                         idesc(uint32_t(nt * kOz5D)), acc);
-            };
-#pragma unroll
-            for (int ks = 0; ks < kOz5R / 16; ks++) {
-                if (ks == 0) {
-                    prod(1, 0, kOzNS, 0, 0u);
-                    prod(0, 0, 1, 0, 0u);
-                    prod(0, 1, kOzNS - 1, 0, 1u);
-                } else {
-                    prod(0, 0, kOzNS, ks, 1u);
-                    prod(1, 0, kOzNS, ks, 1u);
-                }
-#pragma unroll
-                for (int s2 = 2; s2 < kOzNS; s2++) prod(s2, 0, kOzND - s2 < kOzNS ? kOzND - s2 : kOzNS, ks, 1u);
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&mbar[hv])));
-        }
-    };
-    // half hv's accumulators -> double-float outputs of this thread's 4 amplitudes of that half
-    auto epilogue = [&](int hv, uint64_t x0, float nv) {
-        const uint32_t lane_base = tmem + (uint32_t((warp & 3) * 32) << 16) + kOz5HalfCol * uint32_t(hv) + uint32_t(8 * q);
-#pragma unroll
-        for (int c = 0; c < 2; c++) {  // 4 output reals = 2 amplitudes per step
-            uint32_t r[kOzND][4];
-#pragma unroll
-            for (int d = 0; d < kOzND; d++)
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                             : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3])
-                             : "r"(lane_base + uint32_t(d * kOz5D + 4 * c)));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            float o[2][4];
-#pragma unroll
-            for (int i = 0; i < 2; i++) {
-#pragma unroll
-                for (int cc = 0; cc < 2; cc++) {
-                    const int col = 2 * i + cc;
-                    float sm = __fadd_rn(__fadd_rn(__uint_as_float(r[6][col]), __uint_as_float(r[5][col])),
-                                         __uint_as_float(r[4][col]));
-                    float lo = 0.f, t;
-#pragma unroll
-                    for (int d = 3; d >= 0; d--) {
-                        fast_two_sum(__uint_as_float(r[d][col]), sm, sm, t);
-                        lo = __fadd_rn(lo, t);
-                    }
-                    const float sc = __fmul_rn(mu[kOz5D * hv + 8 * q + 4 * c + col], nv);
-                    fast_two_sum(__fmul_rn(sm, sc), __fmul_rn(lo, sc), o[i][2 * cc], o[i][2 * cc + 1]);
-                }
-            }
-            if (x0 != ~0ull) {
-                const float4 a = make_float4(o[0][0], o[0][1], o[0][2], o[0][3]);
-                const float4 b = make_float4(o[1][0], o[1][1], o[1][2], o[1][3]);
-                if (kPairs) {
-                    st_pair(psi + x0 + off[4 * hv + 2 * c], a, b);
-                } else {
-                    psi[x0 + off[4 * hv + 2 * c]] = a;
-                    psi[x0 + off[4 * hv + 2 * c + 1]] = b;
-                }
-            }
-        }
-    };
-
-    // per tile j: loads of tile j + 1; fold half 0 of tile j - 1 (its half 1 MMAs may still
-    // run), then half 1; slice tile j into the (now free) buffer; start the MMAs of tile j.
-    // Every thread waits on the commit barriers itself (no block barrier after the wait). A wait
-    // that runs out in any lane marks the warp (a vote, so that `failed` stays warp-uniform for
-    // the warp-wide tcgen05.ld) and sets s_fail; a warp that reads s_fail after a block barrier
-    // stops waiting and folding, and thread 0 then issues no more MMAs. Every thread passes the
-    // same barriers, and every wait is bounded.
-    float4 vcur[kOz5Amps], vnext[kOz5Amps];
-    uint64_t x0_cur = 0, x0_prev = 0;
-    float nv_prev = 1.f;
-    bool failed = false;
-    if (my_tiles > 0) {
-        x0_cur = group_x0(0);
-        load(x0_cur, vcur);
-    }
-    for (uint64_t j = 0; j <= my_tiles && my_tiles > 0; j++) {
-        uint64_t x0_next = 0;
-        if (j + 1 < my_tiles) {
-            x0_next = group_x0(j + 1);
-            load(x0_next, vnext);
-        }
-        if (j >= 1) {
-#pragma unroll
-            for (int hv = 0; hv < 2; hv++) {
-                if (!failed) {  // warp-uniform; the vote also reconverges the warp for tcgen05.ld
-                    const bool late = !mbar_wait(smem_u32(&mbar[hv]), uint32_t((j - 1) & 1));
-                    if (__any_sync(0xffffffffu, late)) {
-                        failed = true;
-                        s_fail = 1;
-                    }
+    if (warp == kOz5WorkerWarps) {
+        // ---------------------------------------------------------- MMA issuer (one thread)
+        if (lane == 0) {
+            const uint32_t m0 = smem_u32(smem + kOff5Mat);
+            for (uint64_t j = 0; j < my_tiles; j++) {
+                const uint32_t b = uint32_t(j & 1);
+                if (!mbar_wait_or_abort(full0 + 8u * b, uint32_t((j >> 1) & 1), spins, fail)) {
+                    *fail = 1;
+                    break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                if (!failed) epilogue(hv, x0_prev, nv_prev);
-            }
-        }
-        float nv_cur = 1.f;
-        if (j < my_tiles) nv_cur = slice(vcur);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();  // slices of tile j written; accumulators of tile j - 1 read
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (s_fail) failed = true;
-        if (j < my_tiles && !failed) issue();
-        x0_prev = x0_cur;
-        nv_prev = nv_cur;
-        x0_cur = x0_next;
+                const uint32_t a0 = smem_u32(smem + kOff5A + b * kOz5ABuf);
+                const uint32_t a5 = tmem + kOz5HalfCol * b + kOz5A5Col;
+                bool stop = false;
+#pragma unroll 1
+                for (int hv = 0; hv < 2; hv++) {
+                    if (j >= 1 && !mbar_wait_or_abort(accfree0 + 8u * hv, uint32_t((j - 1) & 1), spins, fail)) {
+                        *fail = 1;
+                        stop = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t dh = tmem + kOz5HalfCol * uint32_t(hv);
+                    const uint32_t mh = m0 + uint32_t(hv * kOz5Half);
+                    // state slice s times matrix slices t0 .. t0 + nt - 1 into diagonals s + t
+                    auto prod = [&](int s2, int t0, int nt, int ks, uint32_t acc) {
+                        const uint32_t d = dh + uint32_t((s2 + t0) * kOz5D);
+                        const uint64_t bd = sdesc5(mh + uint32_t(t0 * kOz5D / 8) * kOz5Sbo + uint32_t(ks * 256));
+                        const uint32_t id = idesc(uint32_t(nt * kOz5D));
+                        if (s2 < kOz5SmemSlices)
+                            mma_bf16(d, sdesc5(a0 + uint32_t(s2 * kOz5Slice) + uint32_t(ks * 256)), bd, id, acc);
+                        else
+                            mma_bf16_tmem_a(d, a5 + uint32_t(ks * 8), bd, id, acc);
+                    };
 #pragma unroll
-        for (int i = 0; i < kOz5Amps; i++) vcur[i] = vnext[i];
-    }
-    __syncthreads();  // every thread's s_fail store is visible
-    if (s_fail && tid == 0) {
-        atomicExch(err, 1);
-        // bounded: let the MMAs in flight finish before TMEM is freed
-        mbar_wait(smem_u32(&mbar[0]), 0);
-        mbar_wait(smem_u32(&mbar[0]), 1);
-        mbar_wait(smem_u32(&mbar[1]), 0);
-        mbar_wait(smem_u32(&mbar[1]), 1);
+                    for (int ks = 0; ks < kOz5R / 16; ks++) {
+                        if (ks == 0) {  // first writes: slice 1 starts diagonals 1..6, slice 0 diagonal 0
+                            prod(1, 0, kOzNS, 0, 0u);
+                            prod(0, 0, 1, 0, 0u);
+                            prod(0, 1, kOzNS - 1, 0, 1u);
+                        } else {
+                            prod(0, 0, kOzNS, ks, 1u);
+                            prod(1, 0, kOzNS, ks, 1u);
+                        }
+#pragma unroll
+                        for (int s2 = 2; s2 < kOzNS; s2++) prod(s2, 0, kOzND - s2 < kOzNS ? kOzND - s2 : kOzNS, ks, 1u);
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        done0 + 8u * uint32_t(hv)));
+                }
+                if (stop) break;
+            }
+            // every MMA issued above has finished before TMEM is freed (bounded, full limit)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(drain));
+            if (!mbar_wait(drain, 0)) *fail = 1;
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------- workers
+        // thread (g, q): group g of the tile (= TMEM lane); amplitudes 4q..4q+3 (half 0) and
+        // 16+4q..16+4q+3 (half 1), held as v[0..3] and v[4..7]
+        const int g = tid & (kOzTG - 1), q = tid >> 7;
+        // s(w) of this thread's amplitude i, read from the parameter bank at each use (not held in
+        // registers): amplitude (i / 4) * 16 + 4 q + i % 4
+        auto off = [&](int i) { return P.offs[(i >> 2) * (kOz5D / 2) + 4 * q + (i & 3)]; };
+        const uint32_t lane_off = uint32_t((warp & 3) * 32) << 16;
+
+        auto group_x0 = [&](uint64_t j) {
+            const uint64_t gi = (blockIdx.x + j * gridDim.x) * kOzTG + uint64_t(g);
+            return gi < P.n_groups ? expand(gi, P.ip) : ~0ull;
+        };
+        auto load = [&](uint64_t x0, float4 (&v)[kOz5Amps]) {
+            if (kPairs) {
+#pragma unroll
+                for (int i = 0; i < kOz5Amps; i += 2) {
+                    if (x0 != ~0ull) {
+                        ld_pair(psi + x0 + off(i), v[i], v[i + 1]);
+                    } else {
+                        v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        v[i + 1] = v[i];
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < kOz5Amps; i++)
+                    v[i] = x0 != ~0ull ? __ldcg(psi + x0 + off(i)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            if (kIeeeIn) {
+#pragma unroll
+                for (int i = 0; i < kOz5Amps; i++) v[i] = df_of_ieee(v[i]);
+            }
+        };
+        // slices 0..4 of this thread's amplitudes into shared-memory buffer b, slice 5 into TMEM
+        // (this warp's 32 lanes, columns 4q.. and 16 + 4q.. of buffer b's slice-5 block). Every
+        // worker takes part in the group-scale barrier; a warp that has given up (`store` false,
+        // warp-uniform) writes nothing, so no buffer that an unfinished MMA may read is touched.
+        auto slice = [&](uint32_t b, const float4 (&v)[kOz5Amps], bool store) {
+            float m = 0.f;
+#pragma unroll
+            for (int i = 0; i < kOz5Amps; i++) m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].z)));
+            nu_part[q * kOzTG + g] = m;
+            group_set_sync<kOz5Workers>(warp);  // a group's four threads are in warps w, w + 4, w + 8, w + 12
+            m = nu_part[g];
+#pragma unroll
+            for (int t = 1; t < kOz5TPG; t++) m = fmaxf(m, nu_part[t * kOzTG + g]);
+            const float nv = pow2_ceil(m);
+            if (!store) return nv;
+            const float inv = __uint_as_float((254u - (__float_as_uint(nv) >> 23)) << 23);
+            unsigned char* ab = smem + kOff5A + b * kOz5ABuf;
+            uint32_t t5[2][4];
+#pragma unroll
+            for (int c = 0; c < 2; c++) {  // 4 amplitudes = K columns 32c + 8q .. +7: one 16-byte chunk per slice
+                uint32_t pk[kOzNS][4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    float ar[kOzNS], ai[kOzNS];
+                    slice6(v[4 * c + i].x, v[4 * c + i].y, inv, ar);
+                    slice6(v[4 * c + i].z, v[4 * c + i].w, inv, ai);
+#pragma unroll
+                    for (int s2 = 0; s2 < kOzNS; s2++) pk[s2][i] = pack_bf16(ar[s2], ai[s2]);
+                }
+                const uint32_t o = kmaj5(uint32_t(g), uint32_t(32 * c + 8 * q));
+#pragma unroll
+                for (int s2 = 0; s2 < kOz5SmemSlices; s2++)
+                    *reinterpret_cast<uint4*>(ab + s2 * kOz5Slice + o) = make_uint4(pk[s2][0], pk[s2][1], pk[s2][2], pk[s2][3]);
+#pragma unroll
+                for (int i = 0; i < 4; i++) t5[c][i] = pk[kOzNS - 1][i];
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const uint32_t ta = tmem + lane_off + kOz5HalfCol * b + kOz5A5Col + uint32_t(4 * q);
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(ta), "r"(t5[0][0]),
+                         "r"(t5[0][1]), "r"(t5[0][2]), "r"(t5[0][3]));
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(ta + 16u), "r"(t5[1][0]),
+                         "r"(t5[1][1]), "r"(t5[1][2]), "r"(t5[1][3]));
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            return nv;
+        };
+        // half hv's accumulators -> double-float outputs of this thread's 4 amplitudes of that half
+        auto epilogue = [&](int hv, uint64_t x0, float nv) {
+            const uint32_t lane_base = tmem + lane_off + kOz5HalfCol * uint32_t(hv) + uint32_t(8 * q);
+#pragma unroll
+            for (int c = 0; c < 2; c++) {  // 4 output reals = 2 amplitudes per step
+                uint32_t r[kOzND][4];
+#pragma unroll
+                for (int d = 0; d < kOzND; d++)
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                                 : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3])
+                                 : "r"(lane_base + uint32_t(d * kOz5D + 4 * c)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float o[2][4];
+#pragma unroll
+                for (int i = 0; i < 2; i++) {
+#pragma unroll
+                    for (int cc = 0; cc < 2; cc++) {
+                        const int col = 2 * i + cc;
+                        // D_6 + D_5 + D_4 in FP32 (rounding far below 2^-48 of the output), then
+                        // D_3..D_0 added exactly with Fast2Sum, the errors collected in lo
+                        float sm = __fadd_rn(__fadd_rn(__uint_as_float(r[6][col]), __uint_as_float(r[5][col])),
+                                             __uint_as_float(r[4][col]));
+                        float lo = 0.f, t;
+#pragma unroll
+                        for (int d = 3; d >= 0; d--) {
+                            fast_two_sum(__uint_as_float(r[d][col]), sm, sm, t);
+                            lo = __fadd_rn(lo, t);
+                        }
+                        const float sc = __fmul_rn(mu[kOz5D * hv + 8 * q + 4 * c + col], nv);
+                        fast_two_sum(__fmul_rn(sm, sc), __fmul_rn(lo, sc), o[i][2 * cc], o[i][2 * cc + 1]);
+                    }
+                }
+                if (x0 != ~0ull) {
+                    const float4 a = make_float4(o[0][0], o[0][1], o[0][2], o[0][3]);
+                    const float4 bb = make_float4(o[1][0], o[1][1], o[1][2], o[1][3]);
+                    if (kPairs) {
+                        st_pair(psi + x0 + off(4 * hv + 2 * c), a, bb);
+                    } else {
+                        psi[x0 + off(4 * hv + 2 * c)] = a;
+                        psi[x0 + off(4 * hv + 2 * c + 1)] = bb;
+                    }
+                }
+            }
+        };
+
+        float4 vcur[kOz5Amps], vnext[kOz5Amps];
+        uint64_t x0_cur = 0, x0_prev = 0;
+        float nv_prev = 1.f;
+        bool failed = false;  // warp-uniform: a wait ran out in this warp, or the shared flag was seen
+        if (my_tiles > 0) {
+            x0_cur = group_x0(0);
+            load(x0_cur, vcur);
+        }
+        for (uint64_t j = 0; j <= my_tiles && my_tiles > 0; j++) {
+            uint64_t x0_next = 0;
+            if (j + 1 < my_tiles) {
+                x0_next = group_x0(j + 1);
+                load(x0_next, vnext);
+            }
+            float nv_cur = 1.f;
+            if (j < my_tiles) {
+                // buffer j & 1 was last read by the MMAs of tile j - 2, which finished before
+                // this warp folded half 1 of that tile (the commit tracks every earlier MMA)
+                if (__any_sync(0xffffffffu, *fail != 0)) failed = true;
+                nv_cur = slice(uint32_t(j & 1), vcur, !failed);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0 && !failed) mbar_arrive(full0 + 8u * uint32_t(j & 1));
+            }
+            if (j >= 1) {
+#pragma unroll
+                for (int hv = 0; hv < 2; hv++) {
+                    if (!failed) {  // the vote keeps `failed` warp-uniform for tcgen05.ld
+                        const bool late = !mbar_wait_or_abort(done0 + 8u * uint32_t(hv), uint32_t((j - 1) & 1), spins, fail);
+                        if (__any_sync(0xffffffffu, late)) {
+                            failed = true;
+                            *fail = 1;
+                        }
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    if (!failed) epilogue(hv, x0_prev, nv_prev);
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0 && !failed) mbar_arrive(accfree0 + 8u * uint32_t(hv));
+                }
+            }
+            x0_prev = x0_cur;
+            nv_prev = nv_cur;
+            x0_cur = x0_next;
+#pragma unroll
+            for (int i = 0; i < kOz5Amps; i++) vcur[i] = vnext[i];
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
+    __syncthreads();  // the issuer's drain wait is over; every s_fail store is visible
+    if (tid == 0 && s_fail) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kOz5TmemCols));
 }
 
@@ -926,22 +1025,35 @@ __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(f
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(B::TmemCols));
 }
 
-int g_oz_sms = 0;
-int* g_oz_err = nullptr;
+// Per device (the current one at launch): SM count, the device-side error flag, and whether the
+// shared-memory limits of each kernel family have been raised there (function attributes are per
+// device context).
+constexpr int kOzMaxDevices = 64;
+struct OzDevice {
+    int sms = 0;
+    int* err = nullptr;
+    bool attr4 = false, attr5 = false, attr_bz5 = false, attr_bz6 = false;
+};
+OzDevice g_oz_dev[kOzMaxDevices];
+std::mutex g_oz_mu;
+std::atomic<long long> g_oz_wait_spins{kOzSpinLimit};
 
-// SM count, the error flag and the 4-target kernels' shared-memory limits, once per process
-void oz_init() {
-    if (g_oz_sms) return;
-    int dev = 0, sms = 0;
+OzDevice& oz_init() {
+    int dev = 0;
     QS_TRY_CUDA(cudaGetDevice(&dev));
-    QS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
-    QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
-    QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
-    QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
-    QS_TRY_CUDA(cudaMalloc(&g_oz_err, sizeof(int)));
-    QS_TRY_CUDA(cudaMemset(g_oz_err, 0, sizeof(int)));
-    g_oz_sms = sms;
+    QS_REQUIRE(dev >= 0 && dev < kOzMaxDevices, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_oz_mu);
+    OzDevice& d = g_oz_dev[dev];
+    if (!d.sms) {
+        int sms = 0;
+        QS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (!d.err) {
+            QS_TRY_CUDA(cudaMalloc(&d.err, sizeof(int)));
+            QS_TRY_CUDA(cudaMemset(d.err, 0, sizeof(int)));
+        }
+        d.sms = sms;
+    }
+    return d;
 }
 
 // the real form of K~ (16 x 16 complex): row n = 2z + c_out, column k = 2w + c_in
@@ -1001,7 +1113,14 @@ void launch_dense_oz4(void* psi, int n, const std::vector<int>& targets, const s
                       const std::vector<int>& cvals, const void* dmat, cudaStream_t st, bool ieee_in) {
     QS_REQUIRE(targets.size() == size_t(kOzQ), "tensor-core double-float path takes 4 targets");
     QS_REQUIRE(std::is_sorted(targets.begin(), targets.end()), "targets must be ascending");
-    oz_init();
+    OzDevice& D = oz_init();
+    if (!D.attr4) {
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz4<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOzSmem)));
+        D.attr4 = true;
+    }
     std::vector<int> fixed(targets);
     uint64_t setmask = 0;
     for (size_t j = 0; j < controls.size(); j++) {
@@ -1018,7 +1137,7 @@ void launch_dense_oz4(void* psi, int n, const std::vector<int>& targets, const s
     }
     P.n_groups = P.ip.n_iter;
     const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
-    const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, 2 * uint64_t(g_oz_sms))));
+    const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, 2 * uint64_t(D.sms))));
     // lowest target qubit 0 (and a 32-byte-aligned state): each thread's amplitudes come in
     // adjacent 32-byte-aligned pairs
     QS_REQUIRE(!ieee_in || controls.empty(), "an IEEE-input block rewrites every amplitude (no controls)");
@@ -1026,7 +1145,7 @@ void launch_dense_oz4(void* psi, int n, const std::vector<int>& targets, const s
     auto kern = pairs ? (ieee_in ? k_dense_oz4<true, true> : k_dense_oz4<true, false>)
                       : (ieee_in ? k_dense_oz4<false, true> : k_dense_oz4<false, false>);
     kern<<<grid, kOzThreads, kOzSmem, st>>>(reinterpret_cast<float4*>(psi), static_cast<const unsigned char*>(dmat), P,
-                                            g_oz_err);
+                                            D.err);
     QS_TRY_CUDA(cudaGetLastError());
 }
 
@@ -1076,14 +1195,13 @@ void launch_dense_oz5(void* psi, int n, const std::vector<int>& targets, const s
                       const std::vector<int>& cvals, const void* dmat, cudaStream_t st, bool ieee_in) {
     QS_REQUIRE(targets.size() == size_t(kOz5Q), "5-target tensor-core path takes 5 targets");
     QS_REQUIRE(std::is_sorted(targets.begin(), targets.end()), "targets must be ascending");
-    static bool attr = false;
-    oz_init();
-    if (!attr) {
+    OzDevice& D = oz_init();
+    if (!D.attr5) {
         QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz5<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOz5Smem)));
         QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz5<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOz5Smem)));
         QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz5<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOz5Smem)));
         QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_oz5<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kOz5Smem)));
-        attr = true;
+        D.attr5 = true;
     }
     std::vector<int> fixed(targets);
     uint64_t setmask = 0;
@@ -1094,6 +1212,7 @@ void launch_dense_oz5(void* psi, int n, const std::vector<int>& targets, const s
     Oz5Params P;
     P.ip = make_index_plan(n, fixed, setmask);
     P.n_groups = P.ip.n_iter;
+    P.wait_spins = g_oz_wait_spins.load();
     for (int w = 0; w < kOz5D; w++) {
         uint64_t o = 0;
         for (int j = 0; j < kOz5Q; j++)
@@ -1101,13 +1220,13 @@ void launch_dense_oz5(void* psi, int n, const std::vector<int>& targets, const s
         P.offs[w] = o;
     }
     const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
-    const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, uint64_t(g_oz_sms))));
+    const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, uint64_t(D.sms))));
     QS_REQUIRE(!ieee_in || controls.empty(), "an IEEE-input block rewrites every amplitude (no controls)");
     const bool pairs = targets[0] == 0 && (reinterpret_cast<uintptr_t>(psi) & 31) == 0;
     auto kern = pairs ? (ieee_in ? k_dense_oz5<true, true> : k_dense_oz5<true, false>)
                       : (ieee_in ? k_dense_oz5<false, true> : k_dense_oz5<false, false>);
     kern<<<grid, kOz5Threads, kOz5Smem, st>>>(reinterpret_cast<float4*>(psi), static_cast<const unsigned char*>(dmat), P,
-                                              g_oz_err);
+                                              D.err);
     QS_TRY_CUDA(cudaGetLastError());
 }
 
@@ -1158,8 +1277,8 @@ template <int Q>
 void launch_bz_t(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
                  const std::vector<int>& cvals, const void* dmat, cudaStream_t st) {
     using B = Bz<Q>;
-    static bool attr = false;
-    oz_init();
+    OzDevice& D = oz_init();
+    bool& attr = Q == 5 ? D.attr_bz5 : D.attr_bz6;
     if (!attr) {
         QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_bz<Q, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(B::Smem)));
         QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_bz<Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(B::Smem)));
@@ -1182,13 +1301,13 @@ void launch_bz_t(void* psi, int n, const std::vector<int>& targets, const std::v
     }
     const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
     const unsigned grid =
-        unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, uint64_t(B::MinBlocks) * uint64_t(g_oz_sms))));
+        unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, uint64_t(B::MinBlocks) * uint64_t(D.sms))));
     if (targets[0] == 0 && (reinterpret_cast<uintptr_t>(psi) & 15) == 0)
         k_dense_bz<Q, true><<<grid, B::Threads, B::Smem, st>>>(reinterpret_cast<float2*>(psi),
-                                                               static_cast<const unsigned char*>(dmat), P, g_oz_err);
+                                                               static_cast<const unsigned char*>(dmat), P, D.err);
     else
         k_dense_bz<Q, false><<<grid, B::Threads, B::Smem, st>>>(reinterpret_cast<float2*>(psi),
-                                                                static_cast<const unsigned char*>(dmat), P, g_oz_err);
+                                                                static_cast<const unsigned char*>(dmat), P, D.err);
     QS_TRY_CUDA(cudaGetLastError());
 }
 
@@ -1202,13 +1321,25 @@ void launch_dense_bz(void* psi, int n, const std::vector<int>& targets, const st
         launch_bz_t<6>(psi, n, targets, controls, cvals, dmat, st);
 }
 
-// device-side error recorded by the kernel (a bounded wait ran out); cleared on read
+// device-side error recorded by a tensor-core kernel on the current device (a bounded wait ran
+// out); cleared on read
 bool oz_error_pending() {
-    if (!g_oz_err) return false;
+    int dev = 0;
+    QS_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kOzMaxDevices) return false;
+    int* flag = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_oz_mu);
+        flag = g_oz_dev[dev].err;
+    }
+    if (!flag) return false;
     int e = 0;
-    QS_TRY_CUDA(cudaMemcpy(&e, g_oz_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (e) QS_TRY_CUDA(cudaMemset(g_oz_err, 0, sizeof(int)));
+    QS_TRY_CUDA(cudaMemcpy(&e, flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) QS_TRY_CUDA(cudaMemset(flag, 0, sizeof(int)));
     return e != 0;
 }
+
+// try_wait attempts of the 5-target kernel's pipeline waits (spins < 0: the default limit)
+void oz_set_wait_spins(long long spins) { g_oz_wait_spins.store(spins < 0 ? kOzSpinLimit : spins); }
 
 }  // namespace qs
