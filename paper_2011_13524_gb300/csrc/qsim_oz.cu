@@ -141,26 +141,27 @@ __device__ __forceinline__ float grid_round(float x) {
     return __fsub_rn(__fadd_rn(x, c), c);
 }
 
-// the six slices of x = (h + l) * inv_nu, each exact in bf16 (see the header comment)
+// the six slices of x = (h + l) * inv_nu, each exact in bf16 (see the header comment). inv_nu is
+// a power of two and |x| <= 1, so h * inv_nu and l * inv_nu are exact: the scaling rides in the
+// FMAs that round to the first grid, form the first remainder and add the low word.
 __device__ __forceinline__ void slice6(float h, float l, float inv_nu, float (&a)[kOzNS]) {
-    h = __fmul_rn(h, inv_nu);
-    l = __fmul_rn(l, inv_nu);
-    a[0] = grid_round<0>(h);
-    float r = __fsub_rn(h, a[0]);
+    constexpr float c0 = 1.5f * float(1 << 15);
+    a[0] = __fsub_rn(__fmaf_rn(h, inv_nu, c0), c0);
+    float r = __fmaf_rn(h, inv_nu, -a[0]);  // exact
     a[1] = grid_round<1>(r);
     r = __fsub_rn(r, a[1]);
     a[2] = grid_round<2>(r);
-    r = __fadd_rn(__fsub_rn(r, a[2]), l);  // rounding error below 2^-49
+    r = __fmaf_rn(l, inv_nu, __fsub_rn(r, a[2]));  // rounding error below 2^-49
     a[3] = grid_round<3>(r);
     r = __fsub_rn(r, a[3]);
     a[4] = grid_round<4>(r);
     a[5] = grid_round<5>(__fsub_rn(r, a[4]));
 }
 
+// two values with at most 8 significant bits (exact in bf16) packed as bf16x2, lo in the low
+// half: the upper 16 bits of each FP32 pattern (the lower 16 are zero)
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    uint32_t r;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-    return r;
+    return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 
 // (a + b) exactly as (s, t) when a is a multiple of ulp(b) or |a| >= |b|
@@ -427,9 +428,9 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
 //   full[b]     the 16 worker warps have written the slices of the tile in buffer b
 //   accfree[h]  the 16 worker warps have read half h's accumulators (fold done)
 //   done[h]     commit of half h's MMAs (the tensor cores finished them)
-// Per tile j a worker issues the loads of tile j + 1, slices tile j into buffer j & 1 (free: the
-// MMAs of tile j - 2 finished before its fold), then waits for and folds half 0 and half 1 of tile
-// j - 1. The issuer waits for full[j & 1], then for each half for accfree of tile j - 1 and issues
+// Per tile j a worker slices tile j into buffer j & 1 (free: the MMAs of tile j - 2 finished
+// before its fold), issues the loads of tile j + 1, then waits for and folds half 0 and half 1 of
+// tile j - 1. The issuer waits for full[j & 1], then for each half for accfree of tile j - 1 and issues
 // that half's 28 MMAs: half 0 of tile j runs while the workers fold half 1 of tile j - 1 and slice
 // tile j + 1. Every wait is bounded; a wait that runs out sets a shared flag that makes every other
 // wait give up at once, the kernel records an error, and the issuer waits (bounded, with the full
@@ -440,6 +441,9 @@ constexpr int kOz5R = 2 * kOz5D;                                // 64 reals per 
 constexpr int kOz5Workers = 512;                                // 16 worker warps
 constexpr int kOz5WorkerWarps = kOz5Workers / 32;
 constexpr int kOz5Threads = kOz5Workers + 32;                   // + the MMA-issuing warp
+// 17 warps: the sub-partition that holds five of them limits every thread to 96 registers
+// (16384 / (5 x 32), in steps of 8); the workers issue the next tile's loads after slicing,
+// so that at most one tile of amplitudes is live in registers and nothing spills.
 constexpr int kOz5TPG = kOz5Workers / kOzTG;                    // 4 threads per group
 constexpr int kOz5Amps = kOz5D / kOz5TPG;                       // 8 amplitudes per thread
 constexpr uint32_t kOz5Sbo = (kOz5R / 8) * 128;                 // 1024
@@ -460,7 +464,6 @@ constexpr size_t kOz5Smem = kOff5NuPart + size_t(kOz5TPG) * kOzTG * 4;
 static_assert(kOzND * kOz5D <= int(kOz5A5Col) && kOz5A5Col + kOz5R / 2 <= kOz5HalfCol,
               "a half's accumulators and one slice-5 buffer fit its 256 TMEM columns");
 static_assert(kOz5Smem <= 227 * 1024, "shared memory of one CTA");
-static_assert(kOz5Threads * 120 <= 65536, "120 registers per thread");
 
 struct Oz5Params {
     IndexPlan ip;            // 5 targets (and controls) inserted
@@ -545,10 +548,14 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
     const uint64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     const long long spins = P.wait_spins;
 
-    if (warp == kOz5WorkerWarps) {
+    if (warp >= kOz5WorkerWarps) {
         // ---------------------------------------------------------- MMA issuer (one thread)
-        if (lane == 0) {
-            const uint32_t m0 = smem_u32(smem + kOff5Mat);
+        if (warp == kOz5WorkerWarps && lane == 0) {
+            // descriptors of the slice buffers and of half 0's matrix stack; each MMA adds a
+            // constant to them (the 14-bit address field, in 16-byte units, never carries: the
+            // shared memory used is below 256 KB)
+            const uint64_t abase0 = sdesc5(smem_u32(smem + kOff5A)), abase1 = sdesc5(smem_u32(smem + kOff5A + kOz5ABuf));
+            const uint64_t mbase = sdesc5(smem_u32(smem + kOff5Mat));
             for (uint64_t j = 0; j < my_tiles; j++) {
                 const uint32_t b = uint32_t(j & 1);
                 if (!mbar_wait_or_abort(full0 + 8u * b, uint32_t((j >> 1) & 1), spins, fail)) {
@@ -556,7 +563,7 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t a0 = smem_u32(smem + kOff5A + b * kOz5ABuf);
+                const uint64_t ad = b ? abase1 : abase0;
                 const uint32_t a5 = tmem + kOz5HalfCol * b + kOz5A5Col;
                 bool stop = false;
 #pragma unroll 1
@@ -568,14 +575,14 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t dh = tmem + kOz5HalfCol * uint32_t(hv);
-                    const uint32_t mh = m0 + uint32_t(hv * kOz5Half);
+                    const uint64_t bdh = mbase + uint64_t(hv * (kOz5Half >> 4));
                     // state slice s times matrix slices t0 .. t0 + nt - 1 into diagonals s + t
                     auto prod = [&](int s2, int t0, int nt, int ks, uint32_t acc) {
                         const uint32_t d = dh + uint32_t((s2 + t0) * kOz5D);
-                        const uint64_t bd = sdesc5(mh + uint32_t(t0 * kOz5D / 8) * kOz5Sbo + uint32_t(ks * 256));
+                        const uint64_t bd = bdh + uint64_t(((t0 * kOz5D / 8) * kOz5Sbo + ks * 256) >> 4);
                         const uint32_t id = idesc(uint32_t(nt * kOz5D));
                         if (s2 < kOz5SmemSlices)
-                            mma_bf16(d, sdesc5(a0 + uint32_t(s2 * kOz5Slice) + uint32_t(ks * 256)), bd, id, acc);
+                            mma_bf16(d, ad + uint64_t((s2 * kOz5Slice + ks * 256) >> 4), bd, id, acc);
                         else
                             mma_bf16_tmem_a(d, a5 + uint32_t(ks * 8), bd, id, acc);
                     };
@@ -612,25 +619,20 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
         auto off = [&](int i) { return P.offs[(i >> 2) * (kOz5D / 2) + 4 * q + (i & 3)]; };
         const uint32_t lane_off = uint32_t((warp & 3) * 32) << 16;
 
-        auto group_x0 = [&](uint64_t j) {
+        // this thread's group in tile j; a group past the end (the last tile's tail) reads the
+        // last group instead (valid memory, its outputs are never stored)
+        auto group_x0 = [&](uint64_t j, bool& valid) {
             const uint64_t gi = (blockIdx.x + j * gridDim.x) * kOzTG + uint64_t(g);
-            return gi < P.n_groups ? expand(gi, P.ip) : ~0ull;
+            valid = gi < P.n_groups;
+            return expand(valid ? gi : P.n_groups - 1, P.ip);
         };
         auto load = [&](uint64_t x0, float4 (&v)[kOz5Amps]) {
             if (kPairs) {
 #pragma unroll
-                for (int i = 0; i < kOz5Amps; i += 2) {
-                    if (x0 != ~0ull) {
-                        ld_pair(psi + x0 + off(i), v[i], v[i + 1]);
-                    } else {
-                        v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        v[i + 1] = v[i];
-                    }
-                }
+                for (int i = 0; i < kOz5Amps; i += 2) ld_pair(psi + x0 + off(i), v[i], v[i + 1]);
             } else {
 #pragma unroll
-                for (int i = 0; i < kOz5Amps; i++)
-                    v[i] = x0 != ~0ull ? __ldcg(psi + x0 + off(i)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int i = 0; i < kOz5Amps; i++) v[i] = __ldcg(psi + x0 + off(i));
             }
             if (kIeeeIn) {
 #pragma unroll
@@ -654,7 +656,7 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
             if (!store) return nv;
             const float inv = __uint_as_float((254u - (__float_as_uint(nv) >> 23)) << 23);
             unsigned char* ab = smem + kOff5A + b * kOz5ABuf;
-            uint32_t t5[2][4];
+            const uint32_t ta = tmem + lane_off + kOz5HalfCol * b + kOz5A5Col + uint32_t(4 * q);
 #pragma unroll
             for (int c = 0; c < 2; c++) {  // 4 amplitudes = K columns 32c + 8q .. +7: one 16-byte chunk per slice
                 uint32_t pk[kOzNS][4];
@@ -670,20 +672,15 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
 #pragma unroll
                 for (int s2 = 0; s2 < kOz5SmemSlices; s2++)
                     *reinterpret_cast<uint4*>(ab + s2 * kOz5Slice + o) = make_uint4(pk[s2][0], pk[s2][1], pk[s2][2], pk[s2][3]);
-#pragma unroll
-                for (int i = 0; i < 4; i++) t5[c][i] = pk[kOzNS - 1][i];
+                asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(ta + 16u * c),
+                             "r"(pk[kOzNS - 1][0]), "r"(pk[kOzNS - 1][1]), "r"(pk[kOzNS - 1][2]), "r"(pk[kOzNS - 1][3]));
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            const uint32_t ta = tmem + lane_off + kOz5HalfCol * b + kOz5A5Col + uint32_t(4 * q);
-            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(ta), "r"(t5[0][0]),
-                         "r"(t5[0][1]), "r"(t5[0][2]), "r"(t5[0][3]));
-            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(ta + 16u), "r"(t5[1][0]),
-                         "r"(t5[1][1]), "r"(t5[1][2]), "r"(t5[1][3]));
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             return nv;
         };
         // half hv's accumulators -> double-float outputs of this thread's 4 amplitudes of that half
-        auto epilogue = [&](int hv, uint64_t x0, float nv) {
+        auto epilogue = [&](int hv, uint64_t x0, bool valid, float nv) {
             const uint32_t lane_base = tmem + lane_off + kOz5HalfCol * uint32_t(hv) + uint32_t(8 * q);
 #pragma unroll
             for (int c = 0; c < 2; c++) {  // 4 output reals = 2 amplitudes per step
@@ -700,21 +697,24 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
 #pragma unroll
                     for (int cc = 0; cc < 2; cc++) {
                         const int col = 2 * i + cc;
-                        // D_6 + D_5 + D_4 in FP32 (rounding far below 2^-48 of the output), then
-                        // D_3..D_0 added exactly with Fast2Sum, the errors collected in lo
-                        float sm = __fadd_rn(__fadd_rn(__uint_as_float(r[6][col]), __uint_as_float(r[5][col])),
-                                             __uint_as_float(r[4][col]));
-                        float lo = 0.f, t;
-#pragma unroll
-                        for (int d = 3; d >= 0; d--) {
-                            fast_two_sum(__uint_as_float(r[d][col]), sm, sm, t);
-                            lo = __fadd_rn(lo, t);
-                        }
+                        // D_0 + D_1 + D_2 + D_3 from the largest: each partial sum is a multiple of
+                        // the unit of the next diagonal (2^-8(d+2)), which is at least the ulp of
+                        // that diagonal's value, so every Fast2Sum is exact; when a partial sum
+                        // cancels to below its next diagonal's range it is exact and its error
+                        // term is zero. The error terms and D_4 + D_5 + D_6 (FP32, rounding far below
+                        // 2^-48 of the output) make up lo.
+                        float sm, t1, t2, t3;
+                        fast_two_sum(__uint_as_float(r[0][col]), __uint_as_float(r[1][col]), sm, t1);
+                        fast_two_sum(sm, __uint_as_float(r[2][col]), sm, t2);
+                        fast_two_sum(sm, __uint_as_float(r[3][col]), sm, t3);
+                        const float low = __fadd_rn(__fadd_rn(__uint_as_float(r[6][col]), __uint_as_float(r[5][col])),
+                                                    __uint_as_float(r[4][col]));
+                        const float lo = __fadd_rn(__fadd_rn(__fadd_rn(t3, t2), t1), low);
                         const float sc = __fmul_rn(mu[kOz5D * hv + 8 * q + 4 * c + col], nv);
                         fast_two_sum(__fmul_rn(sm, sc), __fmul_rn(lo, sc), o[i][2 * cc], o[i][2 * cc + 1]);
                     }
                 }
-                if (x0 != ~0ull) {
+                if (valid) {
                     const float4 a = make_float4(o[0][0], o[0][1], o[0][2], o[0][3]);
                     const float4 bb = make_float4(o[1][0], o[1][1], o[1][2], o[1][3]);
                     if (kPairs) {
@@ -727,29 +727,29 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
             }
         };
 
-        float4 vcur[kOz5Amps], vnext[kOz5Amps];
+        // Per tile j: slice tile j (held in vc), issue the loads of tile j + 1 into vn (their
+        // latency is covered by the folds), fold both halves of tile j - 1.
+        float4 va[kOz5Amps], vb[kOz5Amps];
         uint64_t x0_cur = 0, x0_prev = 0;
+        bool ok_cur = false, ok_prev = false;
         float nv_prev = 1.f;
         bool failed = false;  // warp-uniform: a wait ran out in this warp, or the shared flag was seen
-        if (my_tiles > 0) {
-            x0_cur = group_x0(0);
-            load(x0_cur, vcur);
-        }
-        for (uint64_t j = 0; j <= my_tiles && my_tiles > 0; j++) {
-            uint64_t x0_next = 0;
-            if (j + 1 < my_tiles) {
-                x0_next = group_x0(j + 1);
-                load(x0_next, vnext);
-            }
+        auto step = [&](uint64_t j, const float4 (&vc)[kOz5Amps], float4 (&vn)[kOz5Amps]) {
             float nv_cur = 1.f;
+            uint64_t x0_next = 0;
+            bool ok_next = false;
             if (j < my_tiles) {
                 // buffer j & 1 was last read by the MMAs of tile j - 2, which finished before
                 // this warp folded half 1 of that tile (the commit tracks every earlier MMA)
                 if (__any_sync(0xffffffffu, *fail != 0)) failed = true;
-                nv_cur = slice(uint32_t(j & 1), vcur, !failed);
+                nv_cur = slice(uint32_t(j & 1), vc, !failed);
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0 && !failed) mbar_arrive(full0 + 8u * uint32_t(j & 1));
+            }
+            if (j + 1 < my_tiles) {
+                x0_next = group_x0(j + 1, ok_next);
+                load(x0_next, vn);
             }
             if (j >= 1) {
 #pragma unroll
@@ -762,17 +762,26 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
                         }
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    if (!failed) epilogue(hv, x0_prev, nv_prev);
+                    if (!failed) epilogue(hv, x0_prev, ok_prev, nv_prev);
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
                     if (lane == 0 && !failed) mbar_arrive(accfree0 + 8u * uint32_t(hv));
                 }
             }
             x0_prev = x0_cur;
+            ok_prev = ok_cur;
             nv_prev = nv_cur;
             x0_cur = x0_next;
+            ok_cur = ok_next;
+        };
+        if (my_tiles > 0) {
+            x0_cur = group_x0(0, ok_cur);
+            load(x0_cur, va);
+            for (uint64_t j = 0; j <= my_tiles; j++) {
+                step(j, va, vb);
 #pragma unroll
-            for (int i = 0; i < kOz5Amps; i++) vcur[i] = vnext[i];
+                for (int i = 0; i < kOz5Amps; i++) va[i] = vb[i];
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
