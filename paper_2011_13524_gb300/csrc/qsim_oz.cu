@@ -619,12 +619,16 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
         auto off = [&](int i) { return P.offs[(i >> 2) * (kOz5D / 2) + 4 * q + (i & 3)]; };
         const uint32_t lane_off = uint32_t((warp & 3) * 32) << 16;
 
-        // this thread's group in tile j; a group past the end (the last tile's tail) reads the
-        // last group instead (valid memory, its outputs are never stored)
+        // This thread's group in tile j: group index t 128 + g, whose bit string with the fixed
+        // bits inserted is the OR of the insertions of t 128 (the same for the whole CTA) and of g
+        // (per thread, once), as the two have disjoint bits. A tail (only when there are fewer
+        // than 128 groups, all in one tile) reads the last group instead: valid memory, its
+        // outputs are never stored.
+        const uint64_t gx = expand(uint64_t(g) < P.n_groups ? uint64_t(g) : P.n_groups - 1, P.ip);
         auto group_x0 = [&](uint64_t j, bool& valid) {
-            const uint64_t gi = (blockIdx.x + j * gridDim.x) * kOzTG + uint64_t(g);
-            valid = gi < P.n_groups;
-            return expand(valid ? gi : P.n_groups - 1, P.ip);
+            const uint64_t t = blockIdx.x + j * gridDim.x;
+            valid = t * kOzTG + uint64_t(g) < P.n_groups;
+            return expand(t * kOzTG, P.ip) | gx;
         };
         auto load = [&](uint64_t x0, float4 (&v)[kOz5Amps]) {
             if (kPairs) {
@@ -727,29 +731,33 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
             }
         };
 
-        // Per tile j: slice tile j (held in vc), issue the loads of tile j + 1 into vn (their
-        // latency is covered by the folds), fold both halves of tile j - 1.
-        float4 va[kOz5Amps], vb[kOz5Amps];
+        // Per tile j: slice tile j, then load tile j + 1 into the same registers (their latency is
+        // covered by the folds), fold both halves of tile j - 1.
+        float4 v[kOz5Amps];
         uint64_t x0_cur = 0, x0_prev = 0;
         bool ok_cur = false, ok_prev = false;
         float nv_prev = 1.f;
         bool failed = false;  // warp-uniform: a wait ran out in this warp, or the shared flag was seen
-        auto step = [&](uint64_t j, const float4 (&vc)[kOz5Amps], float4 (&vn)[kOz5Amps]) {
+        if (my_tiles > 0) {
+            x0_cur = group_x0(0, ok_cur);
+            load(x0_cur, v);
+        }
+        for (uint64_t j = 0; j <= my_tiles && my_tiles > 0; j++) {
             float nv_cur = 1.f;
-            uint64_t x0_next = 0;
-            bool ok_next = false;
             if (j < my_tiles) {
                 // buffer j & 1 was last read by the MMAs of tile j - 2, which finished before
                 // this warp folded half 1 of that tile (the commit tracks every earlier MMA)
                 if (__any_sync(0xffffffffu, *fail != 0)) failed = true;
-                nv_cur = slice(uint32_t(j & 1), vc, !failed);
+                nv_cur = slice(uint32_t(j & 1), v, !failed);
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0 && !failed) mbar_arrive(full0 + 8u * uint32_t(j & 1));
             }
+            uint64_t x0_next = 0;
+            bool ok_next = false;
             if (j + 1 < my_tiles) {
                 x0_next = group_x0(j + 1, ok_next);
-                load(x0_next, vn);
+                load(x0_next, v);
             }
             if (j >= 1) {
 #pragma unroll
@@ -773,15 +781,6 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
             nv_prev = nv_cur;
             x0_cur = x0_next;
             ok_cur = ok_next;
-        };
-        if (my_tiles > 0) {
-            x0_cur = group_x0(0, ok_cur);
-            load(x0_cur, va);
-            for (uint64_t j = 0; j <= my_tiles; j++) {
-                step(j, va, vb);
-#pragma unroll
-                for (int i = 0; i < kOz5Amps; i++) va[i] = vb[i];
-            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
