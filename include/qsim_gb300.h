@@ -49,9 +49,10 @@ typedef int qs_dtype;
 #define QS_C64 1  /* complex64 storage, FP32 gate arithmetic with FP64-built matrices, FP64-class accumulation */
 #define QS_C128 2 /* complex128 storage */
 
-/* Arithmetic used for complex128 gate updates (qs_set_c128_math). */
-#define QS_MATH_FP64 0 /* native FP64 multiply-adds */
-#define QS_MATH_DF 1   /* double-float (two FP32 words per double, ~2^-46 relative) on the FP32 pipes */
+/* Arithmetic used for complex128 gate updates (qs_set_c128_math, qs_state_set_arith). */
+#define QS_MATH_FP64 0 /* native FP64 multiply-adds (GB300 runs FP64 at 1/64 of the FP32 rate) */
+#define QS_MATH_DF 1   /* double-float (two FP32 words per double, ~2^-46 relative) on the FP32 pipes;
+                          the default */
 
 #define QS_MAX_QUBITS 34
 #define QS_MAX_TARGETS 6
@@ -140,14 +141,15 @@ typedef struct qs_fused_circuit qs_fused_circuit; /* opaque */
 const char* qs_last_error(void);
 /* Library version string. */
 const char* qs_version(void);
-/* Arithmetic for complex128 gate updates, process-wide: QS_MATH_FP64 or QS_MATH_DF. */
+/* Settings. Each call reads the settings it uses once, at entry: a state's own settings
+ * (qs_state_set_arith) where it has them, else the process-wide ones below. A call is therefore
+ * not affected by settings that another thread changes while it runs; a state whose settings
+ * are its own is not affected by the process-wide ones at all.
+ * Process-wide arithmetic for complex128 gate updates: QS_MATH_FP64 or QS_MATH_DF (default). */
 qs_status qs_set_c128_math(int mode);
 qs_status qs_get_c128_math(int* mode);
 /* Tensor-core paths for fused dense blocks (Sec. 5.4 blocks applied by Eq. update_mat),
  * process-wide, as a bit mask:
- * QS_TENSOR_C64: complex64 blocks of 5 or 6 targets (tcgen05.mma kind::tf32, each FP32 operand
- *   split into a TF32 head and remainder, three products: FP32-class accuracy per block, but the
- *   tensor cores' FP32 accumulator rounds toward zero, shrinking the norm by ~2e-6 per block).
  * QS_TENSOR_C128: complex128 blocks of 4 or 5 targets in double-float runs (QS_MATH_DF): the
  *   matrix and every 16- or 32-amplitude group are scaled by powers of two and cut into six
  *   8-bit bf16 slices (the splitting of Ozaki, Ogita, Oishi and Rump); the 26 slice products of
@@ -157,12 +159,8 @@ qs_status qs_get_c128_math(int* mode);
  * QS_TENSOR_C64X: complex64 blocks of 5 or 6 targets: the matrix and every 32- or 64-amplitude
  *   group cut into three 8-bit bf16 slices; the 6 products with s + t <= 2 summed exactly in
  *   FP32 by tcgen05.mma kind::f16, added in FP32 with one rounding to nearest: about 2^-24
- *   relative error per block and no drift, the accuracy of the FP32 CUDA-core kernels. Takes
- *   precedence over QS_TENSOR_C64.
- * Unknown bits -> QS_ERR_INVALID_ARG. Default: QS_TENSOR_C128 | QS_TENSOR_C64X (their blocks
- * meet the complex128 and complex64 bounds; the TF32 path stays opt-in because of its norm
- * drift). */
-#define QS_TENSOR_C64 1
+ *   relative error per block and no drift, the accuracy of the FP32 CUDA-core kernels.
+ * Unknown bits -> QS_ERR_INVALID_ARG. Process-wide default: QS_TENSOR_C128 | QS_TENSOR_C64X. */
 #define QS_TENSOR_C128 2
 #define QS_TENSOR_C64X 4
 qs_status qs_set_tensor_cores(int mask);
@@ -176,6 +174,11 @@ qs_status qs_create_state(int n, qs_dtype dt, void* stream, qs_state** out);
 /* Wraps caller-owned device memory of 2^n amplitudes of type dt (16-byte aligned). The
  * contents are left as they are. qs_destroy_state frees only the handle. */
 qs_status qs_wrap_state(void* dev_ptr, int n, qs_dtype dt, void* stream, qs_state** out);
+/* The state's own arithmetic settings: c128_math is QS_MATH_FP64 or QS_MATH_DF, tensor_mask a
+ * QS_TENSOR_* mask; -1 for either makes the state follow the process-wide setting (the default
+ * of a new state). Used by every later call that applies gates to this state. */
+qs_status qs_state_set_arith(qs_state* s, int c128_math, int tensor_mask);
+qs_status qs_state_get_arith(const qs_state* s, int* c128_math, int* tensor_mask);
 /* Frees the handle (and the memory, if the library allocated it). NULL is accepted. */
 qs_status qs_destroy_state(qs_state* s);
 /* Reports the qubit count, dtype and device pointer of a state (any output may be NULL). */
@@ -221,6 +224,11 @@ qs_status qs_apply_observable_rotation(qs_state* s, const qs_pauli_obs* H, doubl
 /* ---------------------------------------------------------------- fusion (Sec. 5.4) */
 /* Plans the fused circuit for width k (2..6) without applying it. */
 qs_status qs_plan_fusion(const qs_circuit* c, int k, qs_fused_circuit** out);
+/* The library keeps the partitions of the last 16 circuit structures it planned (the qubits of
+ * each gate, the width): a circuit run again with new angles or matrices is not partitioned
+ * again. This forgets them; the next run or plan of any circuit partitions it afresh. The
+ * autotuner's per-kernel timings of this GPU are kept. */
+qs_status qs_clear_plan_cache(void);
 /* Number of blocks of a plan and, for block b, its width and targets (ascending) and its
  * FP64 matrix (2^w x 2^w complex, row-major) copied to host memory; any output may be NULL. */
 qs_status qs_fused_info(const qs_fused_circuit* f, int* n_blocks, int* n_source_gates);
@@ -240,7 +248,6 @@ qs_status qs_destroy_fused(qs_fused_circuit* f);
 #define QS_KERNEL_PAULI 4      /* Pauli string (permutation with phases) */
 #define QS_KERNEL_SWAP 5       /* SWAP / controlled SWAP */
 #define QS_KERNEL_DENSE_DF 6   /* complex128 dense gate matrix in double-float arithmetic */
-#define QS_KERNEL_DENSE_TC 7   /* complex64 dense block of 5-6 targets on the tensor cores (3xTF32) */
 #define QS_KERNEL_DENSE_OZ 8   /* double-float complex128 block of 4 targets on the tensor cores (bf16 slices) */
 #define QS_KERNEL_PAULI_ROT 9  /* Pauli rotation exp(i phi P / 2), one pass over amplitude pairs */
 #define QS_KERNEL_DENSE_OZ5 10 /* double-float complex128 block of 5 targets on the tensor cores (bf16 slices) */

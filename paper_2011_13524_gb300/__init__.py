@@ -39,7 +39,7 @@ QS_MAX_CONTROLS = 8
 
 QS_GATE_DENSE, QS_GATE_DIAG, QS_GATE_PAULI, QS_GATE_NAMED = 0, 1, 2, 3
 KERNEL_NAMES = {0: "dense_reg", 1: "dense_smem", 2: "diag", 3: "phase", 4: "pauli", 5: "swap", 6: "dense_df",
-                7: "dense_tc", 8: "dense_oz", 9: "pauli_rot", 10: "dense_oz5", 11: "dense_bz"}
+                8: "dense_oz", 9: "pauli_rot", 10: "dense_oz5", 11: "dense_bz"}
 NAMED = {
     "X": 1, "Y": 2, "Z": 3, "H": 4, "S": 5, "Sdag": 6, "T": 7, "Tdag": 8, "sqrtX": 9,
     "sqrtXdag": 10, "sqrtY": 11, "sqrtYdag": 12, "RX": 13, "RY": 14, "RZ": 15, "U1": 16,
@@ -89,6 +89,8 @@ _SIGNATURES = {
     "qs_get_c128_math": ([ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "qs_set_tensor_cores": ([ctypes.c_int], ctypes.c_int),
     "qs_get_tensor_cores": ([ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "qs_state_set_arith": ([_VOIDP, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "qs_state_get_arith": ([_VOIDP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "qs_create_state": ([ctypes.c_int, ctypes.c_int, _VOIDP, ctypes.POINTER(_VOIDP)], ctypes.c_int),
     "qs_wrap_state": ([_VOIDP, ctypes.c_int, ctypes.c_int, _VOIDP, ctypes.POINTER(_VOIDP)], ctypes.c_int),
     "qs_destroy_state": ([_VOIDP], ctypes.c_int),
@@ -109,6 +111,7 @@ _SIGNATURES = {
     "qs_apply_fused": ([_VOIDP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _DP], ctypes.c_int),
     "qs_run_circuit": ([_VOIDP, ctypes.POINTER(QsCircuit), ctypes.c_int], ctypes.c_int),
     "qs_plan_fusion": ([ctypes.POINTER(QsCircuit), ctypes.c_int, ctypes.POINTER(_VOIDP)], ctypes.c_int),
+    "qs_clear_plan_cache": ([], ctypes.c_int),
     "qs_fused_info": ([_VOIDP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "qs_fused_block": ([_VOIDP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _DP],
                        ctypes.c_int),
@@ -169,14 +172,12 @@ def set_c128_math(mode: int) -> None:
     check(lib().qs_set_c128_math(int(mode)))
 
 
-QS_TENSOR_C64 = 1
 QS_TENSOR_C128 = 2
 QS_TENSOR_C64X = 4
 
 
-def set_tensor_cores(mask) -> None:
-    """Tensor-core paths as a bit mask of QS_TENSOR_C64 / QS_TENSOR_C128 / QS_TENSOR_C64X
-    (True = QS_TENSOR_C64)."""
+def set_tensor_cores(mask: int) -> None:
+    """Tensor-core paths as a bit mask of QS_TENSOR_C128 / QS_TENSOR_C64X (0: CUDA cores only)."""
     check(lib().qs_set_tensor_cores(int(mask)))
 
 
@@ -330,6 +331,16 @@ class State:
             if fresh:
                 check(lib().qs_set_basis(h, 0))
         self.handle = h
+
+    def set_arith(self, math: int = -1, tensor: int = -1) -> None:
+        """This state's own complex128 arithmetic (QS_MATH_*) and tensor-core mask (QS_TENSOR_*);
+        -1 follows the process-wide setting."""
+        check(lib().qs_state_set_arith(self.handle, int(math), int(tensor)))
+
+    def get_arith(self) -> Tuple[int, int]:
+        m, t = ctypes.c_int(0), ctypes.c_int(0)
+        check(lib().qs_state_get_arith(self.handle, ctypes.byref(m), ctypes.byref(t)))
+        return m.value, t.value
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
@@ -489,6 +500,11 @@ class FusedCircuit:
                 self.handle = None
         except Exception:
             pass
+
+
+def clear_plan_cache() -> None:
+    """Forget the cached fusion partitions (the next run of any circuit plans it afresh)."""
+    check(lib().qs_clear_plan_cache())
 
 
 def autotune_fusion(circuit, dtype: int = QS_C128):

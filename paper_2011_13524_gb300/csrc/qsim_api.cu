@@ -20,17 +20,37 @@ namespace qs {
 
 namespace {
 thread_local std::string g_err;
-std::atomic<int> g_c128_math{QS_MATH_FP64};
+// process-wide settings: the default of states without settings of their own and of calls that
+// take no state
+std::atomic<int> g_c128_math{QS_MATH_DF};
 std::atomic<int> g_tensor{QS_TENSOR_C128 | QS_TENSOR_C64X};  // QS_TENSOR_* bits
+// the settings of the call in progress on this thread (-1 outside a call), taken once at entry
+thread_local int t_math = -1, t_tensor = -1;
+
+// Snapshot of the settings for one call: the state's own where it has them, else the
+// process-wide ones as they are at entry; restored on exit (calls nest inside the library).
+struct SettingsScope {
+    int old_math, old_tensor;
+    explicit SettingsScope(const qs_state* s) : old_math(t_math), old_tensor(t_tensor) {
+        t_math = (s && s->math >= 0) ? s->math : (old_math >= 0 ? old_math : g_c128_math.load());
+        t_tensor = (s && s->tensor >= 0) ? s->tensor : (old_tensor >= 0 ? old_tensor : g_tensor.load());
+    }
+    ~SettingsScope() {
+        t_math = old_math;
+        t_tensor = old_tensor;
+    }
+    SettingsScope(const SettingsScope&) = delete;
+    SettingsScope& operator=(const SettingsScope&) = delete;
+};
+int cur_tensor() { return t_tensor >= 0 ? t_tensor : g_tensor.load(); }
 }  // namespace
 
-bool tensor_c64_enabled() { return (g_tensor.load() & QS_TENSOR_C64) != 0; }
-bool tensor_c128_enabled() { return (g_tensor.load() & QS_TENSOR_C128) != 0; }
-bool tensor_c64x_enabled() { return (g_tensor.load() & QS_TENSOR_C64X) != 0; }
+bool tensor_c128_enabled() { return (cur_tensor() & QS_TENSOR_C128) != 0; }
+bool tensor_c64x_enabled() { return (cur_tensor() & QS_TENSOR_C64X) != 0; }
 
 void set_error(const std::string& msg) { g_err = msg; }
 void clear_error() { g_err.clear(); }
-int c128_math() { return g_c128_math.load(); }
+int c128_math() { return t_math >= 0 ? t_math : g_c128_math.load(); }
 
 namespace {
 
@@ -148,7 +168,6 @@ void op_cost(const Op& op, int n, qs_dtype dt, int* kernel, int* launches, doubl
             const int m = int(op.targets.size());
             const bool reg = m <= 3 || (m == 4 && dt == QS_C64);
             k = reg ? QS_KERNEL_DENSE_REG : QS_KERNEL_DENSE_SMEM;
-            if (dt == QS_C64 && m >= 5 && tensor_c64_enabled()) k = QS_KERNEL_DENSE_TC;
             if (dt == QS_C64 && (m == 5 || m == 6) && tensor_c64x_enabled()) k = QS_KERNEL_DENSE_BZ;
             if (dt == QS_C128 && c128_math() == QS_MATH_DF && m <= 3) k = QS_KERNEL_DENSE_DF;
             if (dt == QS_C128 && c128_math() == QS_MATH_DF && (m == 4 || m == 5) && tensor_c128_enabled())
@@ -186,23 +205,19 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
     w.ptr.assign(ops.size(), nullptr);
     size_t total = 0;
     std::vector<size_t> offs(ops.size(), 0);
-    std::vector<char> tc(ops.size(), 0), oz(ops.size(), 0);
+    std::vector<char> oz(ops.size(), 0);
     for (size_t b = 0; b < ops.size(); b++) {
         if (ops[b].kind != OpKind::Dense || ops[b].targets.size() < 4) continue;
         if (ar == Arith::F32 && (ops[b].targets.size() == 5 || ops[b].targets.size() == 6) && tensor_c64x_enabled()) {
             ops[b] = sort_targets(ops[b]);
             oz[b] = char(10 + ops[b].targets.size());  // the complex64 form, 15 or 16
-        } else if (ar == Arith::F32 && ops[b].targets.size() >= 5 && tensor_c64_enabled()) {
-            ops[b] = pad_dense_to6(ops[b], s->n);
-            tc[b] = 1;
         }
         if (ar == Arith::DF && (ops[b].targets.size() == 4 || ops[b].targets.size() == 5) && tensor_c128_enabled()) {
             ops[b] = sort_targets(ops[b]);
             oz[b] = char(ops[b].targets.size());
         }
         offs[b] = total;
-        total += tc[b]         ? tc6_matrix_bytes()
-                 : oz[b] == 4 ? oz4_matrix_bytes()
+        total += oz[b] == 4 ? oz4_matrix_bytes()
                  : oz[b] == 5 ? oz5_matrix_bytes()
                  : oz[b] >= 15 ? bz_matrix_bytes(oz[b] - 10)
                               : ops[b].data.size() * kernel_entry_bytes(ar);
@@ -212,9 +227,7 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
     std::vector<unsigned char> host(total);
     for (size_t b = 0; b < ops.size(); b++) {
         if (ops[b].kind != OpKind::Dense || ops[b].targets.size() < 4) continue;
-        if (tc[b])
-            prepare_tc6_matrix(ops[b].data, reinterpret_cast<float*>(host.data() + offs[b]));
-        else if (oz[b] == 4)
+        if (oz[b] == 4)
             prepare_oz4_matrix(ops[b].data, host.data() + offs[b]);
         else if (oz[b] == 5)
             prepare_oz5_matrix(ops[b].data, host.data() + offs[b]);
@@ -230,7 +243,6 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
         if (ops[b].kind == OpKind::Dense && ops[b].targets.size() >= 4) {
             w.ptr[b] = static_cast<unsigned char*>(w.dbuf) + offs[b];
             ops[b].dmat = w.ptr[b];
-            ops[b].dmat_tc = tc[b] != 0;
             ops[b].dmat_oz = oz[b] != 0;
         }
     return w;
@@ -428,7 +440,7 @@ double predicted_seconds(const Op& op, int n, qs_dtype dt) {
     int dev = 0;
     cudaGetDevice(&dev);
     const int width = op.kind == OpKind::Dense || op.kind == OpKind::Diag ? int(op.targets.size()) : 0;
-    auto key = std::make_tuple(dev, int(dt), dt == QS_C128 ? c128_math() : g_tensor.load() & (QS_TENSOR_C64 | QS_TENSOR_C64X),
+    auto key = std::make_tuple(dev, int(dt), dt == QS_C128 ? c128_math() : cur_tensor() & QS_TENSOR_C64X,
                                kernel, width, touches_low(op));
     // (the kernel id already tells the tensor-core forms apart)
     double per_byte;
@@ -480,7 +492,10 @@ using namespace qs;
 
 #define API_BEGIN \
     try {         \
-        clear_error();
+        clear_error();\
+        SettingsScope settings_scope_(nullptr);
+// a call on a state: that state's settings (where it has its own) for the whole call
+#define STATE_SETTINGS(s) SettingsScope state_settings_scope_(s)
 #define API_END                                  \
     }                                            \
     catch (const Error& e) {                     \
@@ -512,7 +527,7 @@ qs_status qs_set_c128_math(int mode) {
 
 qs_status qs_set_tensor_cores(int mask) {
     API_BEGIN
-    QS_REQUIRE((mask & ~(QS_TENSOR_C64 | QS_TENSOR_C128 | QS_TENSOR_C64X)) == 0, "unknown tensor-core path bits");
+    QS_REQUIRE((mask & ~(QS_TENSOR_C128 | QS_TENSOR_C64X)) == 0, "unknown tensor-core path bits");
     g_tensor.store(mask);
     API_END
 }
@@ -528,6 +543,26 @@ qs_status qs_get_c128_math(int* mode) {
     API_BEGIN
     QS_REQUIRE(mode != nullptr, "null output");
     *mode = g_c128_math.load();
+    API_END
+}
+
+qs_status qs_state_set_arith(qs_state* s, int c128_math_mode, int tensor_mask) {
+    API_BEGIN
+    check_state(s);
+    QS_REQUIRE(c128_math_mode == -1 || c128_math_mode == QS_MATH_FP64 || c128_math_mode == QS_MATH_DF,
+               "unknown complex128 arithmetic mode");
+    QS_REQUIRE(tensor_mask == -1 || (tensor_mask & ~(QS_TENSOR_C128 | QS_TENSOR_C64X)) == 0,
+               "unknown tensor-core path bits");
+    s->math = c128_math_mode;
+    s->tensor = tensor_mask;
+    API_END
+}
+
+qs_status qs_state_get_arith(const qs_state* s, int* c128_math_mode, int* tensor_mask) {
+    API_BEGIN
+    check_state(s);
+    if (c128_math_mode) *c128_math_mode = s->math;
+    if (tensor_mask) *tensor_mask = s->tensor;
     API_END
 }
 
@@ -649,13 +684,13 @@ qs_status qs_synchronize(const qs_state* s) {
     check_state(s);
     QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
     QS_TRY_CUDA(cudaGetLastError());
-    if (tc_error_pending()) throw Error{QS_ERR_TIMEOUT, "tensor-core kernel: a bounded wait ran out"};
-    if (oz_error_pending()) throw Error{QS_ERR_TIMEOUT, "tensor-core double-float kernel: a bounded wait ran out"};
+    if (oz_error_pending()) throw Error{QS_ERR_TIMEOUT, "tensor-core kernel: a bounded wait ran out"};
     API_END
 }
 
 qs_status qs_apply_gate(qs_state* s, const qs_gate* g) {
     API_BEGIN
+    STATE_SETTINGS(s);
     check_state(s);
     QS_REQUIRE(g != nullptr, "null gate");
     Op op = op_of_gate(*g, s->n, nullptr);
@@ -665,6 +700,7 @@ qs_status qs_apply_gate(qs_state* s, const qs_gate* g) {
 
 qs_status qs_apply_fused(qs_state* s, int k, const int* targets, const double* mat) {
     API_BEGIN
+    STATE_SETTINGS(s);
     check_state(s);
     QS_REQUIRE(targets != nullptr && mat != nullptr, "null targets or matrix");
     QS_REQUIRE(k >= 1 && k <= QS_MAX_TARGETS, "fused width must be in 1..6");
@@ -682,6 +718,7 @@ qs_status qs_apply_fused(qs_state* s, int k, const int* targets, const double* m
 
 qs_status qs_run_circuit(qs_state* s, const qs_circuit* c, int fusion_k) {
     API_BEGIN
+    STATE_SETTINGS(s);
     check_state(s);
     QS_REQUIRE(c != nullptr, "null circuit");
     QS_REQUIRE(c->n == s->n, "circuit and state have different qubit counts");
@@ -706,6 +743,12 @@ qs_status qs_plan_fusion(const qs_circuit* c, int k, qs_fused_circuit** out) {
     std::unique_ptr<qs_fused_circuit> f(new qs_fused_circuit());
     f->plan = plan_fusion(c, k);
     *out = f.release();
+    API_END
+}
+
+qs_status qs_clear_plan_cache(void) {
+    API_BEGIN
+    clear_partition_cache();
     API_END
 }
 
@@ -775,6 +818,7 @@ qs_status qs_fused_block(const qs_fused_circuit* f, int b, int* width, int* targ
 
 qs_status qs_apply_fused_circuit(qs_state* s, const qs_fused_circuit* f) {
     API_BEGIN
+    STATE_SETTINGS(s);
     check_state(s);
     QS_REQUIRE(f != nullptr, "null plan");
     apply_plan(s, f->plan);
@@ -824,6 +868,7 @@ qs_status qs_fused_layout_passes(const qs_fused_circuit* f, qs_dtype dt, int* pa
 
 qs_status qs_apply_fused_circuit_timed(qs_state* s, const qs_fused_circuit* f, float* block_ms) {
     API_BEGIN
+    STATE_SETTINGS(s);
     check_state(s);
     QS_REQUIRE(f != nullptr && block_ms != nullptr, "null plan or output");
     apply_plan_impl(s, f->plan, block_ms);
@@ -915,6 +960,7 @@ qs_status qs_norm2(const qs_state* s, double* out) {
 
 qs_status qs_apply_pauli_rotation(qs_state* s, uint64_t x_mask, uint64_t z_mask, double angle) {
     API_BEGIN
+    STATE_SETTINGS(s);
     QS_REQUIRE(s != nullptr, "null state");
     const uint64_t all = s->n >= 64 ? ~0ull : ((1ull << s->n) - 1);
     QS_REQUIRE(((x_mask | z_mask) & ~all) == 0, "Pauli mask names a qubit outside the state");
@@ -930,6 +976,7 @@ qs_status qs_apply_pauli_rotation(qs_state* s, uint64_t x_mask, uint64_t z_mask,
 
 qs_status qs_apply_observable_rotation(qs_state* s, const qs_pauli_obs* H, double angle, int n_slices) {
     API_BEGIN
+    STATE_SETTINGS(s);
     QS_REQUIRE(s != nullptr && H != nullptr, "null state or observable");
     QS_REQUIRE(n_slices >= 1, "n_slices must be positive");
     QS_REQUIRE(H->n_terms >= 0 && (H->n_terms == 0 || (H->coef && H->x_mask && H->z_mask)), "null observable arrays");

@@ -37,16 +37,7 @@ namespace qs {
 
 namespace {
 
-int sm_count() {
-    static int s = 0;
-    if (!s) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
-        if (s <= 0) s = 1;
-    }
-    return s;
-}
+int sm_count() { return device_sms(); }
 
 // smem element of a tile: complex64 stays float2, complex128 becomes double-float float4
 template <typename C>
@@ -538,30 +529,33 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_transition_tiled(const C* _
     }
 }
 
+// CTAs per SM of the tiled kernels at their shared-memory size (attribute raised once per device)
 template <typename C>
 int trans_blocks_per_sm() {
-    static int b = 0;
-    if (!b) {
+    static PerDevice setup;
+    static int b[kMaxDevices];
+    setup.once([](int dev) {
         const size_t bytes = trans_smem_bytes(sizeof(typename TileElem<C>::T));
-        cudaFuncSetAttribute(k_transition_tiled<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_transition_tiled<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transition_tiled<C>, kTileThreads, bytes);
-        b = nb > 0 ? nb : 1;
-    }
-    return b;
+        QS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_transition_tiled<C>, kTileThreads, bytes));
+        b[dev] = nb > 0 ? nb : 1;
+    });
+    return b[current_device()];
 }
 
 template <typename C>
 int tile_blocks_per_sm() {
-    static int b = 0;
-    if (!b) {
+    static PerDevice setup;
+    static int b[kMaxDevices];
+    setup.once([](int dev) {
         const size_t bytes = tile_smem_bytes(sizeof(typename TileElem<C>::T));
-        cudaFuncSetAttribute(k_expect_tiled<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_expect_tiled<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_expect_tiled<C>, kTileThreads, bytes);
-        b = nb > 0 ? nb : 1;
-    }
-    return b;
+        QS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_expect_tiled<C>, kTileThreads, bytes));
+        b[dev] = nb > 0 ? nb : 1;
+    });
+    return b[current_device()];
 }
 
 template <typename C>

@@ -450,6 +450,11 @@ std::vector<OpenBlock> partition(const qs_circuit* c, const std::vector<uint64_t
 }
 }  // namespace
 
+void clear_partition_cache() {
+    std::lock_guard<std::mutex> lk(g_part_mu);
+    g_part_cache.clear();
+}
+
 FusionPlan plan_fusion(const qs_circuit* c, int k, const double* theta) {
     QS_REQUIRE(c != nullptr, "null circuit");
     QS_REQUIRE(c->n >= 1 && c->n <= QS_MAX_QUBITS, "qubit count out of range");

@@ -24,16 +24,7 @@ constexpr int kThreads = 256;
 // compiler keeps the order)
 constexpr int kConvUnroll = 4;
 
-int sm_count() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    return sms;
-}
+int sm_count() { return device_sms(); }
 
 unsigned grid_for(uint64_t work) {
     const uint64_t want = (work + kThreads - 1) / kThreads;
@@ -296,21 +287,22 @@ void launch_diag_table_t(const std::vector<int>& u, const std::vector<cplx>& tab
     };
     Pm.nrun = runs(u, Pm.run);
     Pm.nrun2 = runs(u2, Pm.run2);
-    static bool attr = false;
-    static int resident[2] = {1, 1};  // CTAs per SM at the largest table, without / with IEEE output
-    if (!attr) {
+    static PerDevice setup;
+    static int resident_of[kMaxDevices][2];  // CTAs per SM at the largest table, without / with IEEE output
+    setup.once([](int dev) {
+        int* r = resident_of[dev];
+        r[0] = r[1] = 1;
         QS_TRY_CUDA(cudaFuncSetAttribute(k_diag_table<P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(kMaxBytes)));
-        QS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[0], k_diag_table<P, false>, kDiagThreads,
-                                                                  kMaxBytes));
+        QS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r[0], k_diag_table<P, false>, kDiagThreads, kMaxBytes));
         if constexpr (std::is_same<P, DFArith>::value) {
             QS_TRY_CUDA(cudaFuncSetAttribute(k_diag_table<P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(kMaxBytes)));
-            QS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident[1], k_diag_table<P, true>,
-                                                                      kDiagThreads, kMaxBytes));
+            QS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r[1], k_diag_table<P, true>, kDiagThreads,
+                                                                      kMaxBytes));
         }
-        attr = true;
-    }
+    });
+    const int* resident = resident_of[current_device()];
     auto kern = k_diag_table<P, false>;
     if constexpr (std::is_same<P, DFArith>::value) {
         if (ieee_out) kern = k_diag_table<P, true>;
@@ -513,11 +505,10 @@ void launch_dense_smem(const Op& op, const IndexPlan& ip, void* psi, const void*
     Pm.ip = ip;
     fill_offs<M>(op, Pm.offs);
     const size_t smem = sizeof(K) * D * D + sizeof(C) * D * G + sizeof(uint64_t) * G;
-    static bool attr_set = false;
-    if (!attr_set) {
+    static PerDevice setup;
+    setup.once([smem](int) {
         QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_smem<P, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        attr_set = true;
-    }
+    });
     const uint64_t n_tiles = (ip.n_iter + G - 1) / G;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, uint64_t(sm_count()) * 4)));
     k_dense_smem<P, M><<<grid, kThreads, smem, st>>>(reinterpret_cast<C*>(psi), reinterpret_cast<const K*>(dK), Pm);
@@ -551,20 +542,6 @@ void launch_with(const Op& op, void* psi, int n, cudaStream_t st, void* stage, b
                     dK = stage;
                 }
                 return launch_dense_bz(psi, n, os.targets, os.controls, os.cvals, dK, st);
-            }
-            // complex64 blocks of 5-6 targets: tensor cores (a 5-target block is padded to 6)
-            if (sizeof(C) == 8 && m >= 5 && tensor_c64_enabled()) {
-                const Op o6 = m == 6 ? op : pad_dense_to6(op, n);
-                const float* dK = static_cast<const float*>(op.dmat_tc ? op.dmat : nullptr);
-                if (!dK) {
-                    QS_REQUIRE(stage != nullptr, "no staging buffer for a wide dense gate");
-                    std::vector<float> hk(tc6_matrix_bytes() / sizeof(float));
-                    prepare_tc6_matrix(o6.data, hk.data());
-                    QS_TRY_CUDA(cudaMemcpyAsync(stage, hk.data(), tc6_matrix_bytes(), cudaMemcpyHostToDevice, st));
-                    QS_TRY_CUDA(cudaStreamSynchronize(st));  // hk is host memory that dies on return
-                    dK = static_cast<const float*>(stage);
-                }
-                return launch_dense_tc6(psi, n, o6.targets, o6.controls, o6.cvals, dK, st);
             }
             // double-float blocks of 4 targets: tensor cores (targets ascending)
             if (std::is_same<P, DFArith>::value && m == 4 && tensor_c128_enabled()) {
@@ -813,26 +790,6 @@ void launch_from_df(void* psi, int n, cudaStream_t st) {
     QS_TRY_CUDA(cudaGetLastError());
 }
 
-Op pad_dense_to6(const Op& op, int n) {
-    if (op.kind != OpKind::Dense || op.targets.size() != 5) return op;
-    uint64_t used = 0;
-    for (int t : op.targets) used |= 1ull << t;
-    for (int c : op.controls) used |= 1ull << c;
-    int extra = -1;
-    for (int q = 0; q < n; q++)
-        if (!((used >> q) & 1)) { extra = q; break; }
-    QS_REQUIRE(extra >= 0, "no free qubit to pad a 5-target block");
-    Op r = op;
-    r.targets.push_back(extra);
-    r.data.assign(64 * 64, cplx(0.0, 0.0));
-    for (int z = 0; z < 64; z++)
-        for (int w = 0; w < 64; w++)
-            if ((z >> 5) == (w >> 5)) r.data[size_t(z) * 64 + w] = op.data[size_t(z & 31) * 32 + (w & 31)];
-    r.dmat = nullptr;
-    r.dmat_tc = false;
-    return r;
-}
-
 Op sort_targets(const Op& op) {
     const int m = int(op.targets.size());
     std::vector<int> perm(m);
@@ -852,7 +809,6 @@ Op sort_targets(const Op& op) {
             for (int w = 0; w < D; w++) r.data[size_t(z) * D + w] = op.data[size_t(old_index(z)) * D + old_index(w)];
     }
     r.dmat = nullptr;
-    r.dmat_tc = false;
     r.dmat_oz = false;
     return r;
 }

@@ -277,6 +277,26 @@ Op op_of_gate(const qs_gate& g, int n, const double* theta) {
     return op;
 }
 
+int current_device() {
+    int dev = 0;
+    QS_TRY_CUDA(cudaGetDevice(&dev));
+    QS_REQUIRE(dev >= 0 && dev < kMaxDevices, "device index out of range");
+    return dev;
+}
+
+int device_sms() {
+    static std::mutex mu;
+    static int sms[kMaxDevices] = {};
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lk(mu);
+    if (!sms[dev]) {
+        int s = 0;
+        QS_TRY_CUDA(cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev));
+        sms[dev] = s > 0 ? s : 1;
+    }
+    return sms[dev];
+}
+
 IndexPlan make_index_plan(int n, const std::vector<int>& fixed, uint64_t setmask) {
     IndexPlan p;
     std::vector<int> f = fixed;

@@ -7,6 +7,7 @@
 
 #include <complex>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -61,11 +62,38 @@ struct qs_state {
     qs::Scratch scratch;
     void* d_stage = nullptr;  // kStageBytes, allocated on first wide dense gate
     int df = 0;               // 1 while a complex128 buffer holds the double-float layout
+    int math = -1;            // QS_MATH_* of this state, -1: the process-wide setting
+    int tensor = -1;          // QS_TENSOR_* bits of this state, -1: the process-wide setting
 };
 
 namespace qs {
 
 inline size_t amp_bytes(qs_dtype dt) { return dt == QS_C64 ? 8 : 16; }
+
+// ------------------------------------------------------------------ per-device setup
+constexpr int kMaxDevices = 64;
+// index of the current device (QS_ERR_INVALID_ARG beyond kMaxDevices)
+int current_device();
+// SM count of the current device, looked up once per device; thread-safe
+int device_sms();
+// Runs a setup step once for each device, with that device current: function attributes such
+// as a raised shared-memory limit belong to the device context they were set in. Thread-safe.
+class PerDevice {
+  public:
+    template <typename F>
+    void once(F&& f) {
+        const int dev = current_device();
+        std::lock_guard<std::mutex> lk(mu_);
+        if (!((done_ >> dev) & 1ull)) {
+            f(dev);
+            done_ |= 1ull << dev;
+        }
+    }
+
+  private:
+    std::mutex mu_;
+    uint64_t done_ = 0;
+};
 
 // ------------------------------------------------------------------ launch plans
 // Enumeration of the x0 of Eq. (update_mat): iteration index i -> bit string with zero
@@ -102,7 +130,6 @@ struct Op {
     uint64_t xmask = 0, zmask = 0;  // Pauli, PauliRot
     double angle = 0.0;             // PauliRot: exp(i angle P / 2)
     const void* dmat = nullptr;     // Dense, optional: device copy of `data` in the state's element type
-    bool dmat_tc = false;           // dmat holds the tensor-core form (complex64, 6 targets)
     bool dmat_oz = false;           // dmat holds the sliced tensor-core form (double-float, 4 targets)
 };
 
@@ -291,17 +318,6 @@ void launch_adjoint_diag(void* psi, void* lam, int n, Arith ar, const void* tab,
 // out[s] = sum_j part[s * nb + j] for s < nslots (fixed order)
 void launch_slot_sums(const double* part, int nslots, unsigned nb, double* out, cudaStream_t st);
 
-// Tensor-core path for complex64 dense blocks of 5 or 6 targets (tcgen05, 3xTF32).
-bool tensor_c64_enabled();
-// 5-target dense op -> 6 targets (K (x) I on the lowest free qubit); other ops unchanged
-Op pad_dense_to6(const Op& op, int n);
-// host image of the tensor-core operand (Ah, Al: 2 x 128 x 128 floats) of a 64 x 64 matrix
-void prepare_tc6_matrix(const std::vector<cplx>& K, float* host_out);
-size_t tc6_matrix_bytes();
-void launch_dense_tc6(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
-                      const std::vector<int>& cvals, const float* dmat, cudaStream_t st);
-bool tc_error_pending();
-
 // Tensor-core path for double-float complex128 dense blocks of 4 targets (tcgen05, bf16
 // slices with exact FP32 accumulation).
 bool tensor_c128_enabled();
@@ -349,6 +365,8 @@ struct FusionPlan {
     std::vector<std::vector<double>> source_mats;
 };
 // theta (optional): parameter vector overriding the angles of parametric gates
+// forgets the cached partitions (planning starts afresh for every circuit)
+void clear_partition_cache();
 FusionPlan plan_fusion(const qs_circuit* c, int k, const double* theta = nullptr);
 void apply_plan(qs_state* s, const FusionPlan& p);
 

@@ -27,16 +27,7 @@ constexpr int kRedThreads = 256;
 constexpr int kMaxTermsPerLaunch = 48;
 static_assert(kHeavyChunkTerms <= kMaxTermsPerLaunch, "heavy chunks must fit one launch");
 
-int sms() {
-    static int s = 0;
-    if (!s) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
-        if (s <= 0) s = 1;
-    }
-    return s;
-}
+int sms() { return device_sms(); }
 
 unsigned red_grid(uint64_t work) {
     const uint64_t want = (work + kRedThreads * 4 - 1) / (kRedThreads * 4);

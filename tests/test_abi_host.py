@@ -2,10 +2,11 @@
 declares, validates arguments without a GPU, and its host-side fusion planner produces block
 matrices whose product equals the unfused circuit (checked with the oracle)."""
 import ctypes
+import math
 import os
 import re
-
-import math
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -14,7 +15,8 @@ import oracle
 import workloads as W
 import paper_2011_13524_gb300 as qs
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "qsim_gb300.h")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qsim_gb300.h")
 
 
 def declared_functions():
@@ -36,8 +38,23 @@ def test_version_and_error_message():
     rc = qs.lib().qs_set_c128_math(7)
     assert rc == qs.QS_ERR_INVALID_ARG
     assert b"mode" in qs.lib().qs_last_error()
+    old = qs.get_c128_math()
     qs.set_c128_math(qs.QS_MATH_FP64)
     assert qs.get_c128_math() == qs.QS_MATH_FP64
+    qs.set_c128_math(old)
+    rc = qs.lib().qs_set_tensor_cores(1)  # no such path
+    assert rc == qs.QS_ERR_INVALID_ARG
+
+
+def test_library_defaults():
+    """A fresh process: complex128 gates run in double-float arithmetic with the tensor-core
+    blocks of both dtypes on (the configuration the benchmark times), read through the ABI."""
+    code = ("import paper_2011_13524_gb300 as qs; "
+            "print(qs.get_c128_math(), qs.get_tensor_cores())")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, check=True)
+    math_mode, mask = map(int, out.stdout.split())
+    assert math_mode == qs.QS_MATH_DF
+    assert mask == qs.QS_TENSOR_C128 | qs.QS_TENSOR_C64X
 
 
 def test_invalid_arguments_without_gpu():

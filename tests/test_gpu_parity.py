@@ -3,7 +3,8 @@
 Tolerances (max-abs amplitude error): 1e-12 for complex128, 1e-5 for complex64, the bounds
 the workload states; fidelity 1 - |<ref|psi>|^2 is reported beside them. Sizes span several
 thread blocks and ragged tails (n = 1 .. 22); full-size (n = 30) runs are checked on sampled
-amplitudes that a closed form gives one by one.
+amplitudes that a closed form gives one by one. Every test runs under both complex128
+arithmetics (IEEE FP64, and double-float with tensor-core blocks, the library default).
 """
 import math
 
@@ -26,6 +27,17 @@ def qs():
     import paper_2011_13524_gb300 as qs
     qs.lib()
     return qs
+
+
+@pytest.fixture(scope="module", autouse=True, params=["fp64", "double-float"])
+def c128_arith(qs, request):
+    """Every test of this file runs with both complex128 arithmetics as the process-wide setting:
+    IEEE FP64 kernels and double-float with tensor-core blocks (the default); complex64 tests run
+    the same kernels twice. Tests that pick an arithmetic themselves restore this one."""
+    old = qs.get_c128_math()
+    qs.set_c128_math(qs.QS_MATH_FP64 if request.param == "fp64" else qs.QS_MATH_DF)
+    yield request.param
+    qs.set_c128_math(old)
 
 
 def maxabs(a, b):
