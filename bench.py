@@ -36,11 +36,9 @@ import workloads as W  # noqa: E402
 
 METRIC = "state-vector GB/s & gates/s at n=30 c128 vs HBM peak; adjoint-grad ms; circuits/s"
 HBM_PEAK_FALLBACK = 6800.0
-# DRAM bytes (read + write) per launch from one ncu capture, keyed by kernel; filled in only
-# for a kernel unchanged since the capture (profiles/<kernel>_<workload>.md gives the command).
-# k_dense_reg<DFArith, 2>: captured at n = 27 (2 GiB state, 4.233e9 bytes per launch); traffic
-# grows with the state, so the n = 30 entry is that figure times 8. The tensor-core kernels
-# (k_dense_oz4, k_dense_oz5) changed after their last capture, so they report none.
+# DRAM bytes (read + write) per launch of a kernel, from one ncu capture of the kernel as it is
+# built now, at a smaller state than the bench's and scaled to n = 30 by the amplitudes a launch
+# updates (the traffic of these kernels grows in proportion to the state): (kernel, n) -> bytes.
 NCU_TRAFFIC = {("dense_df", 27): 4232672512, ("dense_df", 30): 4232672512 * 8}
 
 
@@ -56,9 +54,9 @@ def parse():
     p.add_argument("--fusion", type=int, default=-1, help="-1 autotune, 0 gate by gate, 1..6 width")
     p.add_argument("--math", default="auto", choices=["auto", "fp64", "df"])
     p.add_argument("--tensor", type=int, default=-1,
-                   help="tensor-core path mask (1 complex64 TF32, 2 complex128 double-float, 4 complex64 bf16 slices); -1 = library default")
+                   help="tensor-core path mask (2 complex128 double-float, 4 complex64 bf16 slices); -1 = library default")
     p.add_argument("--extras", type=int, default=1, help="also measure unfused, c64, adjoint (rank 0)")
-    p.add_argument("--cpu-sample-gates", type=int, default=9)
+    p.add_argument("--cpu-sample-gates", type=int, default=27, help="gates of the oracle sample timed (<= 90)")
     p.add_argument("--only", default="", choices=["", "batch"],
                    help="profiling aid: time only the batched workload and print its numbers")
     p.add_argument("--batch-count", type=int, default=4096)
@@ -154,26 +152,40 @@ def zz_obs(n):
 
 
 # ---------------------------------------------------------------- CPU oracle timing
+# One gate mix for both CPU numbers (the cpu_baseline leg and the --impl reference arm): the
+# circuit's gates sampled evenly along it, gate i of the sample being gate floor(i G / M) of the
+# circuit (M = 90: a tenth of the 890-gate circuit, its U3 / CZ proportions), applied in that
+# order to a 2^n complex128 state. The per-gate cost does not depend on the amplitudes.
+ORACLE_SAMPLE = 90
+
+
+def oracle_sample(circuit, m=ORACLE_SAMPLE):
+    G = len(circuit.gates)
+    return [circuit.gates[(i * G) // m] for i in range(m)]
+
+
 def oracle_gates_per_s(n, circuit, n_gates):
-    """Oracle (FP64, OpenMP over B(0)) on a spread sample of the circuit's gates applied to an
-    n-qubit state; the per-gate cost does not depend on the amplitudes."""
+    """The oracle (FP64, OpenMP over B(0)) on the first n_gates gates of the sample."""
     import oracle
     psi = oracle.zero_state(n)
-    idx = np.linspace(0, len(circuit.gates) - 1, n_gates).astype(int)
+    sample = oracle_sample(circuit)[:n_gates]
     t0 = time.perf_counter()
-    for i in idx:
-        oracle.apply_gate(psi, n, circuit.gates[i])
+    for g in sample:
+        oracle.apply_gate(psi, n, g)
     dt = time.perf_counter() - t0
-    names = sorted({circuit.gates[i].name for i in idx})
-    return len(idx) / dt, oracle.threads(), dt, names
+    names = sorted({g.name for g in sample})
+    return len(sample) / dt, oracle.threads(), dt, names
 
 
 def run_reference(args):
+    """The FP64 oracle on the benchmark's workload: each step applies the next 3 gates of the
+    sample (cycling), on the host cores."""
     ws, rank, _ = dist()
     if rank != 0:
         return
     import oracle
     circuit = W.u3cz_circuit(args.n, args.depth, args.seed)
+    sample = oracle_sample(circuit)
     n = args.n
     psi = oracle.zero_state(n)
     per_step = 3
@@ -183,7 +195,7 @@ def run_reference(args):
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         for _ in range(per_step):
-            oracle.apply_gate(psi, n, circuit.gates[gi % len(circuit.gates)])
+            oracle.apply_gate(psi, n, sample[gi % len(sample)])
             gi += 1
         dt = time.perf_counter() - t0
         if step >= args.warmup:
@@ -194,10 +206,12 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"random U3+CZ brickwork, n={n}, depth={args.depth}, complex128",
-                       "n": n, "depth": args.depth, "seed": args.seed},
+            "config": {"workload": f"random U3+CZ brickwork, n={n}, depth={args.depth}, complex128, |0..0>, "
+                                   f"fused (autotuned width), then <Z0Z1>",
+                       "n": n, "depth": args.depth, "gates": len(circuit.gates), "seed": args.seed},
             "cpu_baseline": {"value": v, "unit": "gates/s", "cores": oracle.threads(), "kind": "oracle",
-                             "sample": f"{per_step} consecutive gates of the circuit per step on a 2^{n} state"},
+                             "sample": f"{per_step} gates per step from the evenly spaced {len(sample)}-gate "
+                                       f"sample of the circuit, on a 2^{n} complex128 state"},
             "e2e": {"value": v, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -321,8 +335,19 @@ def run_ours(args):
     gate_desc = 120 * G  # sizeof(qs_gate) per gate descriptor read by the planner
     wide = 0 if plan is None else sum(16 * (1 << len(plan.block(b)[0])) ** 2 for b in range(plan.n_blocks)
                                        if len(plan.block(b)[0]) >= 4)
+    # the same with nothing cached from earlier runs of the circuit: the fusion planner partitions
+    # it again for every width the autotuner compares (the autotuner's per-kernel timings of this
+    # GPU stay)
+    qs.clear_plan_cache()
+    t0 = time.perf_counter()
+    st.set_basis(0)
+    st.run(circuit, args.fusion)
+    st.expectation(zz)
+    e2e_cold_s = time.perf_counter() - t0
     e2e = {"value": ws * G / e2e_s, "unit": "gates/s", "h2d_bytes_per_step": gate_desc + wide,
-           "d2h_bytes_per_step": 16, "wall_ms_per_step": 1e3 * e2e_s}
+           "d2h_bytes_per_step": 16, "wall_ms_per_step": 1e3 * e2e_s,
+           "cold": {"value": ws * G / e2e_cold_s, "unit": "gates/s", "wall_ms_per_step": 1e3 * e2e_cold_s,
+                    "what": "one step after qs_clear_plan_cache: planning of every width included"}}
 
     line = {"metric": METRIC, "value": value, "unit": "gates/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -348,8 +373,9 @@ def run_ours(args):
         line["extras"] = extras
         rate, cores, dt, names = oracle_gates_per_s(n, circuit, args.cpu_sample_gates)
         line["cpu_baseline"] = {"value": rate, "unit": "gates/s", "cores": cores, "kind": "oracle",
-                                "sample": f"{args.cpu_sample_gates} gates spread over the circuit ({'/'.join(names)}) "
-                                          f"applied to a 2^{n} complex128 state, {dt:.1f} s"}
+                                "sample": f"the first {args.cpu_sample_gates} gates ({'/'.join(names)}) of the evenly "
+                                          f"spaced {ORACLE_SAMPLE}-gate sample of the circuit, applied to a 2^{n} "
+                                          f"complex128 state, {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:
@@ -399,10 +425,10 @@ def measure_extras(args, qs, torch, circuit):
     ms = timed(lambda: (st.set_basis(0), st.apply_plan(plan64) if k64 else st.run(circuit, 0)), reps=2)
     out["c64_fused_gates_per_s"] = G / (ms / 1e3)
     out["c64_fusion_k"] = k64
-    # fused width 6 on the tensor cores (tcgen05, 3xTF32) and on the FP32 CUDA cores
+    # fused width 6 on the tensor cores (bf16 slices, exact FP32 sums) and on the FP32 CUDA cores
     old_tc = qs.get_tensor_cores()
     plan6 = qs.FusedCircuit(circuit, 6)
-    for tc in (True, False):
+    for tc in (qs.QS_TENSOR_C64X, 0):
         qs.set_tensor_cores(tc)
         ms6 = timed(lambda: (st.set_basis(0), st.apply_plan(plan6)), reps=2)
         out["c64_k6_%s_gates_per_s" % ("tensor" if tc else "cuda_cores")] = G / (ms6 / 1e3)
