@@ -354,6 +354,30 @@ qs_status qs_batch_run(qs_batch* b, const double* theta, void* stream, int use_g
 qs_status qs_batch_info(const qs_batch* b, int* total_params, int* total_passes, size_t* workspace_bytes);
 qs_status qs_batch_destroy(qs_batch* b);
 
+/* ---------------------------------------------------------------- test hooks */
+/* Every device-side wait of the library is bounded: when one gives up, its kernel records an
+ * error, stops its work, waits (bounded) for its own asynchronous operations and exits; the next
+ * synchronising call (qs_synchronize, or the call itself where it synchronises) reports
+ * QS_ERR_TIMEOUT, the state's contents are then undefined, and the library stays usable. These
+ * process-wide hooks let a test make such a wait run out without faulting or hanging the GPU.
+ * qs_debug_set_wait_limit: polls of each pipeline wait of the tensor-core kernels and of each
+ *   grid-barrier wait of the batch kernel before it gives up; -1 restores the defaults (seconds).
+ *   The tensor-core kernels' final waits for their own MMAs always keep the default limit.
+ * qs_debug_set_fault: QS_DEBUG_NONE; QS_DEBUG_TC_LATE: the first accumulator wait of every later
+ *   tensor-core kernel launch reports a timeout without waiting; QS_DEBUG_BATCH_HOLD: CTA 0 of the
+ *   batch kernel does not arrive at its first grid barrier (with a small wait limit every wait
+ *   there runs out). A batch's captured graph is captured again when these settings change. */
+#define QS_DEBUG_NONE 0
+#define QS_DEBUG_TC_LATE 1
+#define QS_DEBUG_BATCH_HOLD 2
+qs_status qs_debug_set_wait_limit(long long polls);
+qs_status qs_debug_set_fault(int what);
+/* Every device and pinned-host allocation of the library is counted. qs_debug_fail_alloc makes
+ * the allocation after `after` more successful ones fail as if memory had run out (-1: none), so
+ * that the failing call returns QS_ERR_OOM; *held (optional) receives the number of allocations
+ * the library holds now, to check that a failed call freed everything it had allocated. */
+qs_status qs_debug_fail_alloc(long long after, long long* held);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,6 +38,7 @@ QS_MAX_TARGETS = 6
 QS_MAX_CONTROLS = 8
 
 QS_GATE_DENSE, QS_GATE_DIAG, QS_GATE_PAULI, QS_GATE_NAMED = 0, 1, 2, 3
+QS_DEBUG_NONE, QS_DEBUG_TC_LATE, QS_DEBUG_BATCH_HOLD = 0, 1, 2
 KERNEL_NAMES = {0: "dense_reg", 1: "dense_smem", 2: "diag", 3: "phase", 4: "pauli", 5: "swap", 6: "dense_df",
                 8: "dense_oz", 9: "pauli_rot", 10: "dense_oz5", 11: "dense_bz"}
 NAMED = {
@@ -112,6 +113,9 @@ _SIGNATURES = {
     "qs_run_circuit": ([_VOIDP, ctypes.POINTER(QsCircuit), ctypes.c_int], ctypes.c_int),
     "qs_plan_fusion": ([ctypes.POINTER(QsCircuit), ctypes.c_int, ctypes.POINTER(_VOIDP)], ctypes.c_int),
     "qs_clear_plan_cache": ([], ctypes.c_int),
+    "qs_debug_set_wait_limit": ([ctypes.c_longlong], ctypes.c_int),
+    "qs_debug_set_fault": ([ctypes.c_int], ctypes.c_int),
+    "qs_debug_fail_alloc": ([ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     "qs_fused_info": ([_VOIDP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "qs_fused_block": ([_VOIDP, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _DP],
                        ctypes.c_int),

@@ -56,16 +56,22 @@ namespace {
 
 void check_state(const qs_state* s) { QS_REQUIRE(s != nullptr && s->data != nullptr, "null state"); }
 
+// after a synchronisation: an error that a tensor-core kernel on this device recorded (a bounded
+// wait ran out; the state's contents are then undefined) is reported once
+void report_device_errors() {
+    if (oz_error_pending()) throw Error{QS_ERR_TIMEOUT, "tensor-core kernel: a bounded wait ran out"};
+}
+
 void* stage_of(qs_state* s) {
-    if (!s->d_stage) QS_TRY_CUDA(cudaMalloc(&s->d_stage, kStageBytes));
+    if (!s->d_stage) QS_TRY_CUDA(dev_malloc(&s->d_stage, kStageBytes));
     return s->d_stage;
 }
 
 void free_state_resources(qs_state* s) {
-    if (s->scratch.d_part) cudaFree(s->scratch.d_part);
-    if (s->scratch.h_out) cudaFreeHost(s->scratch.h_out);
-    if (s->d_stage) cudaFree(s->d_stage);
-    if (s->owns && s->data) cudaFree(s->data);
+    if (s->scratch.d_part) dev_free(s->scratch.d_part);
+    if (s->scratch.h_out) host_free_pinned(s->scratch.h_out);
+    if (s->d_stage) dev_free(s->d_stage);
+    if (s->owns && s->data) dev_free(s->data);
     s->scratch = Scratch{};
     s->d_stage = nullptr;
     s->data = nullptr;
@@ -236,7 +242,7 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
         else
             encode_entries(ar, ops[b].data, host.data() + offs[b]);
     }
-    QS_TRY_CUDA(cudaMallocAsync(&w.dbuf, total, s->stream));
+    QS_TRY_CUDA(dev_malloc_async(&w.dbuf, total, s->stream));
     QS_TRY_CUDA(cudaMemcpyAsync(w.dbuf, host.data(), total, cudaMemcpyHostToDevice, s->stream));
     cudaStreamSynchronize(s->stream);  // the host staging vector dies on return
     for (size_t b = 0; b < ops.size(); b++)
@@ -327,11 +333,11 @@ void apply_plan_impl(qs_state* s, const FusionPlan& p, float* block_ms) {
         }
     } catch (...) {
         for (auto& e : ev) cudaEventDestroy(e);
-        if (wm.dbuf) cudaFreeAsync(wm.dbuf, s->stream);
+        if (wm.dbuf) dev_free_async(wm.dbuf, s->stream);
         throw;
     }
     for (auto& e : ev) cudaEventDestroy(e);
-    if (wm.dbuf) QS_TRY_CUDA(cudaFreeAsync(wm.dbuf, s->stream));
+    if (wm.dbuf) QS_TRY_CUDA(dev_free_async(wm.dbuf, s->stream));
 }
 
 }  // namespace
@@ -376,7 +382,7 @@ double measure_cost(int dev, qs_dtype dt, const Op& probe_op, int np_) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (wm.dbuf) cudaFree(wm.dbuf);
+    if (wm.dbuf) dev_free(wm.dbuf);
     (void)dev;
     double bytes = 0;
     op_cost(op, np_, dt, nullptr, nullptr, &bytes);
@@ -546,6 +552,31 @@ qs_status qs_get_c128_math(int* mode) {
     API_END
 }
 
+qs_status qs_debug_set_wait_limit(long long polls) {
+    API_BEGIN
+    QS_REQUIRE(polls >= -1, "wait limit must be -1 (default) or a poll count");
+    oz_set_wait_spins(polls);
+    batch_set_wait_polls(polls);
+    API_END
+}
+
+qs_status qs_debug_set_fault(int what) {
+    API_BEGIN
+    QS_REQUIRE(what == QS_DEBUG_NONE || what == QS_DEBUG_TC_LATE || what == QS_DEBUG_BATCH_HOLD,
+               "unknown wait-test setting");
+    oz_set_force_late(what == QS_DEBUG_TC_LATE);
+    batch_set_hold_cta(what == QS_DEBUG_BATCH_HOLD);
+    API_END
+}
+
+qs_status qs_debug_fail_alloc(long long after, long long* held) {
+    API_BEGIN
+    QS_REQUIRE(after >= -1, "allocation count must be -1 (none) or at least 0");
+    set_alloc_failure(after);
+    if (held) *held = allocations_held();
+    API_END
+}
+
 qs_status qs_state_set_arith(qs_state* s, int c128_math_mode, int tensor_mask) {
     API_BEGIN
     check_state(s);
@@ -579,7 +610,7 @@ qs_status qs_create_state(int n, qs_dtype dt, void* stream, qs_state** out) {
     s->owns = true;
     QS_TRY_CUDA(cudaGetDevice(&s->device));
     const size_t bytes = (size_t(1) << n) * amp_bytes(dt);
-    cudaError_t e = cudaMalloc(&s->data, bytes);
+    cudaError_t e = dev_malloc(&s->data, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         s->data = nullptr;
@@ -665,6 +696,7 @@ qs_status qs_get_vector(const qs_state* s, void* host_out) {
     const size_t bytes = (size_t(1) << s->n) * amp_bytes(s->dt);
     QS_TRY_CUDA(cudaMemcpyAsync(host_out, s->data, bytes, cudaMemcpyDeviceToHost, s->stream));
     QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
+    report_device_errors();
     API_END
 }
 
@@ -684,7 +716,7 @@ qs_status qs_synchronize(const qs_state* s) {
     check_state(s);
     QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
     QS_TRY_CUDA(cudaGetLastError());
-    if (oz_error_pending()) throw Error{QS_ERR_TIMEOUT, "tensor-core kernel: a bounded wait ran out"};
+    report_device_errors();
     API_END
 }
 
@@ -889,6 +921,7 @@ qs_status qs_expectation(const qs_state* s, const qs_pauli_obs* obs, double out[
     check_state(s);
     QS_REQUIRE(out != nullptr, "null output");
     reduce_expectation(const_cast<qs_state*>(s), obs, out);
+    report_device_errors();
     API_END
 }
 
@@ -955,6 +988,7 @@ qs_status qs_norm2(const qs_state* s, double* out) {
     check_state(s);
     QS_REQUIRE(out != nullptr, "null output");
     reduce_norm2(const_cast<qs_state*>(s), out);
+    report_device_errors();
     API_END
 }
 
@@ -1211,13 +1245,13 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
     double* d_part = nullptr;
     void* d_tab = nullptr;
     const size_t eb = kernel_entry_bytes(ar);
-    if (nslots) QS_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_part), sizeof(double) * (size_t(nslots) * nb + nslots), st));
+    if (nslots) QS_TRY_CUDA(dev_malloc_async(reinterpret_cast<void**>(&d_part), sizeof(double) * (size_t(nslots) * nb + nslots), st));
     std::vector<int> slot_param(nslots, -1);
     try {
         if (!tabs.empty()) {
             std::vector<unsigned char> host(tabs.size() * eb);
             encode_entries(ar, tabs, host.data());
-            QS_TRY_CUDA(cudaMallocAsync(&d_tab, host.size(), st));
+            QS_TRY_CUDA(dev_malloc_async(&d_tab, host.size(), st));
             QS_TRY_CUDA(cudaMemcpyAsync(d_tab, host.data(), host.size(), cudaMemcpyHostToDevice, st));
             QS_TRY_CUDA(cudaStreamSynchronize(st));  // the host copy dies on return
         }
@@ -1274,13 +1308,14 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
             for (int sidx = 0; sidx < nslots; sidx++) grad[slot_param[sidx]] += -sums[sidx];
         }
     } catch (...) {
-        if (d_part) cudaFreeAsync(d_part, st);
-        if (d_tab) cudaFreeAsync(d_tab, st);
+        if (d_part) dev_free_async(d_part, st);
+        if (d_tab) dev_free_async(d_tab, st);
         throw;
     }
-    if (d_tab) QS_TRY_CUDA(cudaFreeAsync(d_tab, st));
-    if (d_part) QS_TRY_CUDA(cudaFreeAsync(d_part, st));
+    if (d_tab) QS_TRY_CUDA(dev_free_async(d_tab, st));
+    if (d_part) QS_TRY_CUDA(dev_free_async(d_part, st));
     QS_TRY_CUDA(cudaStreamSynchronize(st));
+    report_device_errors();
     API_END
 }
 

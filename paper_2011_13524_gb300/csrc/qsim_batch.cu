@@ -19,6 +19,7 @@
 //    at a rotation exp(i theta P/2) the gradient is -Im <lambda|P|psi>, then the gate is
 //    un-applied from psi and lambda.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -93,6 +94,10 @@ struct LevelEntry {
     int32_t kind;
 };
 constexpr long long kBarrierSpinLimit = 1ll << 25;  // x 256 ns sleeps: ~10 s
+// test hooks of the grid barrier (kernel arguments): polls before a wait gives up, and CTA 0
+// holding back its arrival at the first barrier
+std::atomic<long long> g_batch_polls{kBarrierSpinLimit};
+std::atomic<int> g_batch_hold{0};
 
 struct BatchDev {
     const BItem* items;
@@ -117,6 +122,8 @@ struct BatchDev {
     unsigned int* bar_count;
     unsigned int* bar_gen;
     int* err;
+    long long barrier_polls;      // polls of a grid-barrier wait before it gives up
+    int hold_cta;                 // test hook: CTA 0 does not arrive at the first grid barrier
     int32_t cls_begin[kClasses + 1];
 };
 
@@ -538,8 +545,9 @@ __device__ __forceinline__ double lambda_range(const BatchDev& B, const BItem& i
 }
 
 // grid-wide barrier with a bounded wait (all CTAs are co-resident: cooperative launch). On
-// timeout it sets the error flag and returns false; every caller then leaves the kernel.
-__device__ bool grid_barrier(unsigned int* count, unsigned int* gen, int* err) {
+// timeout it sets the error flag and returns false; every caller then leaves the kernel. A CTA
+// told to hold back (a test of the timeout) waits without arriving, so that every wait runs out.
+__device__ bool grid_barrier(unsigned int* count, unsigned int* gen, int* err, long long polls, bool hold) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -547,14 +555,14 @@ __device__ bool grid_barrier(unsigned int* count, unsigned int* gen, int* err) {
         const unsigned int g = *vgen;
         __threadfence();
         int ok = 1;
-        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+        if (!hold && atomicAdd(count, 1u) == gridDim.x - 1) {
             *count = 0;
             __threadfence();
             atomicAdd(gen, 1u);
         } else {
             long long spins = 0;
             while (*vgen == g) {
-                if (++spins > kBarrierSpinLimit || *(volatile int*)err) {
+                if (++spins > polls || *(volatile int*)err) {
                     atomicExch(err, 1);
                     ok = 0;
                     break;
@@ -578,6 +586,7 @@ __global__ void __launch_bounds__(kBT, 1) k_batch(const BatchDev B) {
     __shared__ int s_claim[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int parity = 0;
+    bool first_barrier = true;
 
     // ================= circuits wider than the window: level-synchronous over the grid
     for (int lv = 0; lv < B.nlevels; lv++) {
@@ -662,7 +671,9 @@ __global__ void __launch_bounds__(kBT, 1) k_batch(const BatchDev B) {
                 __syncthreads();
             }
         }
-        if (!grid_barrier(B.bar_count, B.bar_gen, B.err)) return;
+        if (!grid_barrier(B.bar_count, B.bar_gen, B.err, B.barrier_polls, B.hold_cta && blockIdx.x == 0 && first_barrier))
+            return;
+        first_barrier = false;
     }
 
     // ================= circuits within the window: whole circuit per warp group, in shared memory
@@ -792,6 +803,8 @@ struct qs_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t graph_stream = nullptr;
+    long long graph_polls = 0;   // wait-test settings the graph was captured with
+    int graph_hold = 0;
     int device = 0;
 };
 
@@ -927,17 +940,17 @@ void free_batch(qs_batch* b) {
                    b->d_lev_entries, b->d_lev_off, b->d_lev_units, b->d_bar, b->d_err, b->d_energy, b->d_grad,
                    b->d_counter};
     for (void* p : dev)
-        if (p) cudaFree(p);
-    if (b->h_theta) cudaFreeHost(b->h_theta);
-    if (b->h_energy) cudaFreeHost(b->h_energy);
-    if (b->h_grad) cudaFreeHost(b->h_grad);
-    if (b->h_err) cudaFreeHost(b->h_err);
+        if (p) dev_free(p);
+    if (b->h_theta) host_free_pinned(b->h_theta);
+    if (b->h_energy) host_free_pinned(b->h_energy);
+    if (b->h_grad) host_free_pinned(b->h_grad);
+    if (b->h_err) host_free_pinned(b->h_err);
 }
 
 template <typename T>
 void upload(void** d, const std::vector<T>& h) {
     const size_t bytes = std::max<size_t>(1, h.size()) * sizeof(T);
-    QS_TRY_CUDA(cudaMalloc(d, bytes));
+    QS_TRY_CUDA(dev_malloc(d, bytes));
     if (!h.empty()) QS_TRY_CUDA(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
 }
 
@@ -976,6 +989,8 @@ void enqueue(qs_batch* b, cudaStream_t st) {
     B.bar_count = b->d_bar;
     B.bar_gen = b->d_bar + 1;
     B.err = b->d_err;
+    B.barrier_polls = g_batch_polls.load();
+    B.hold_cta = g_batch_hold.load();
     for (int c = 0; c <= kClasses; c++) B.cls_begin[c] = b->cls_begin[c];
     // cooperative launch: every CTA is resident at once, so the grid barrier cannot wait on a
     // CTA that never runs
@@ -1224,25 +1239,25 @@ qs_status qs_batch_create(const qs_circuit* circuits, const qs_pauli_obs* observ
         upload(&b->d_gates, b->gates);
         upload(&b->d_gate_slot, b->gate_slot);
         upload(&b->d_terms, b->terms);
-        QS_TRY_CUDA(cudaMalloc(&b->d_theta, sizeof(double) * std::max(1, b->total_angles)));
-        QS_TRY_CUDA(cudaMalloc(&b->d_ws, sizeof(float2) * std::max<uint64_t>(1, b->ws_amps)));
+        QS_TRY_CUDA(dev_malloc(&b->d_theta, sizeof(double) * std::max(1, b->total_angles)));
+        QS_TRY_CUDA(dev_malloc(&b->d_ws, sizeof(float2) * std::max<uint64_t>(1, b->ws_amps)));
         upload(&b->d_ws_off, b->ws_off);
         upload(&b->d_part_e_off, b->part_e_off);
         upload(&b->d_part_g_off, b->part_g_off);
-        QS_TRY_CUDA(cudaMalloc(&b->d_part_e, sizeof(double) * std::max<int64_t>(1, b->part_e_total)));
-        QS_TRY_CUDA(cudaMalloc(&b->d_part_g, sizeof(double) * std::max<int64_t>(1, b->part_g_total)));
+        QS_TRY_CUDA(dev_malloc(&b->d_part_e, sizeof(double) * std::max<int64_t>(1, b->part_e_total)));
+        QS_TRY_CUDA(dev_malloc(&b->d_part_g, sizeof(double) * std::max<int64_t>(1, b->part_g_total)));
         upload(&b->d_lev_entries, b->lev_entries);
         upload(&b->d_lev_off, b->lev_off);
         upload(&b->d_lev_units, b->lev_units);
-        QS_TRY_CUDA(cudaMalloc(&b->d_bar, sizeof(unsigned int) * 2));
-        QS_TRY_CUDA(cudaMalloc(&b->d_err, sizeof(int)));
-        QS_TRY_CUDA(cudaMallocHost(&b->h_err, sizeof(int)));
-        QS_TRY_CUDA(cudaMalloc(&b->d_energy, sizeof(double) * count));
-        QS_TRY_CUDA(cudaMalloc(&b->d_grad, sizeof(double) * std::max(1, b->total_grads)));
-        QS_TRY_CUDA(cudaMalloc(&b->d_counter, sizeof(unsigned int) * (kClasses + b->lev_units.size())));
-        QS_TRY_CUDA(cudaMallocHost(&b->h_theta, sizeof(double) * std::max(1, b->total_angles)));
-        QS_TRY_CUDA(cudaMallocHost(&b->h_energy, sizeof(double) * count));
-        QS_TRY_CUDA(cudaMallocHost(&b->h_grad, sizeof(double) * std::max(1, b->total_grads)));
+        QS_TRY_CUDA(dev_malloc(&b->d_bar, sizeof(unsigned int) * 2));
+        QS_TRY_CUDA(dev_malloc(&b->d_err, sizeof(int)));
+        QS_TRY_CUDA(host_malloc_pinned(&b->h_err, sizeof(int)));
+        QS_TRY_CUDA(dev_malloc(&b->d_energy, sizeof(double) * count));
+        QS_TRY_CUDA(dev_malloc(&b->d_grad, sizeof(double) * std::max(1, b->total_grads)));
+        QS_TRY_CUDA(dev_malloc(&b->d_counter, sizeof(unsigned int) * (kClasses + b->lev_units.size())));
+        QS_TRY_CUDA(host_malloc_pinned(&b->h_theta, sizeof(double) * std::max(1, b->total_angles)));
+        QS_TRY_CUDA(host_malloc_pinned(&b->h_energy, sizeof(double) * count));
+        QS_TRY_CUDA(host_malloc_pinned(&b->h_grad, sizeof(double) * std::max(1, b->total_grads)));
         QS_TRY_CUDA(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem)));
     } catch (...) {
         free_batch(b.get());
@@ -1276,8 +1291,18 @@ qs_status qs_batch_run(qs_batch* b, const double* theta, void* stream, int use_g
     QS_REQUIRE(theta != nullptr || b->total_grads == 0, "parametric batch needs theta");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (use_graph) {
+        if (b->exec && (b->graph_polls != g_batch_polls.load() || b->graph_hold != g_batch_hold.load())) {
+            // the wait-test settings are kernel arguments: a graph captured under others is redone
+            QS_TRY_CUDA(cudaStreamSynchronize(b->graph_stream));
+            cudaGraphExecDestroy(b->exec);
+            cudaGraphDestroy(b->graph);
+            b->exec = nullptr;
+            b->graph = nullptr;
+        }
         if (!b->exec) {
-            QS_TRY_CUDA(cudaStreamCreateWithFlags(&b->graph_stream, cudaStreamNonBlocking));
+            b->graph_polls = g_batch_polls.load();
+            b->graph_hold = g_batch_hold.load();
+            if (!b->graph_stream) QS_TRY_CUDA(cudaStreamCreateWithFlags(&b->graph_stream, cudaStreamNonBlocking));
             QS_TRY_CUDA(cudaStreamBeginCapture(b->graph_stream, cudaStreamCaptureModeThreadLocal));
             try {
                 enqueue(b, b->graph_stream);
@@ -1300,6 +1325,15 @@ qs_status qs_batch_run(qs_batch* b, const double* theta, void* stream, int use_g
     if (b->total_grads) std::memcpy(grads, b->h_grad, sizeof(double) * b->total_grads);
     BATCH_END
 }
+
+}  // extern "C"
+
+namespace qs {
+void batch_set_wait_polls(long long polls) { g_batch_polls.store(polls < 0 ? kBarrierSpinLimit : polls); }
+void batch_set_hold_cta(bool on) { g_batch_hold.store(on ? 1 : 0); }
+}  // namespace qs
+
+extern "C" {
 
 qs_status qs_batch_destroy(qs_batch* b) {
     BATCH_BEGIN

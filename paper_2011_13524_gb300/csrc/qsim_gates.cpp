@@ -9,6 +9,7 @@
 // subspace where that entry sits (a phase on 2^(n-m) amplitudes), other diagonals scale
 // every amplitude, and everything else is a dense gate-matrix update.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "qsim_internal.h"
@@ -276,6 +277,55 @@ Op op_of_gate(const qs_gate& g, int n, const double* theta) {
     op.data = d.mat;
     return op;
 }
+
+namespace {
+std::atomic<long long> g_alloc_held{0};
+std::atomic<long long> g_alloc_fail_after{-1};
+// true when this allocation is the one the test hook makes fail
+bool injected_failure() {
+    long long k = g_alloc_fail_after.load();
+    while (k >= 0) {
+        if (g_alloc_fail_after.compare_exchange_weak(k, k - 1)) return k == 0;
+    }
+    return false;
+}
+}  // namespace
+
+cudaError_t dev_malloc_raw(void** p, size_t bytes) {
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) g_alloc_held++;
+    return e;
+}
+cudaError_t dev_malloc_async_raw(void** p, size_t bytes, cudaStream_t st) {
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e == cudaSuccess) g_alloc_held++;
+    return e;
+}
+cudaError_t host_malloc_pinned_raw(void** p, size_t bytes) {
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMallocHost(p, bytes);
+    if (e == cudaSuccess) g_alloc_held++;
+    return e;
+}
+cudaError_t dev_free(void* p) {
+    if (!p) return cudaSuccess;
+    g_alloc_held--;
+    return cudaFree(p);
+}
+cudaError_t dev_free_async(void* p, cudaStream_t st) {
+    if (!p) return cudaSuccess;
+    g_alloc_held--;
+    return cudaFreeAsync(p, st);
+}
+cudaError_t host_free_pinned(void* p) {
+    if (!p) return cudaSuccess;
+    g_alloc_held--;
+    return cudaFreeHost(p);
+}
+void set_alloc_failure(long long after) { g_alloc_fail_after.store(after < 0 ? -1 : after); }
+long long allocations_held() { return g_alloc_held.load(); }
 
 int current_device() {
     int dev = 0;

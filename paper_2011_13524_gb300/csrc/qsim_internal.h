@@ -70,6 +70,28 @@ namespace qs {
 
 inline size_t amp_bytes(qs_dtype dt) { return dt == QS_C64 ? 8 : 16; }
 
+// ------------------------------------------------------------------ allocations
+// Every device and pinned-host allocation of the library goes through these: they count the
+// allocations held, and a test hook can make one of them fail as if memory had run out
+// (cudaErrorMemoryAllocation, reported as QS_ERR_OOM), to check that no call leaks on that path.
+cudaError_t dev_malloc_raw(void** p, size_t bytes);
+cudaError_t dev_malloc_async_raw(void** p, size_t bytes, cudaStream_t st);
+cudaError_t host_malloc_pinned_raw(void** p, size_t bytes);
+cudaError_t dev_free(void* p);
+cudaError_t dev_free_async(void* p, cudaStream_t st);
+cudaError_t host_free_pinned(void* p);
+template <typename T>
+cudaError_t dev_malloc(T** p, size_t bytes) { return dev_malloc_raw(reinterpret_cast<void**>(p), bytes); }
+template <typename T>
+cudaError_t dev_malloc_async(T** p, size_t bytes, cudaStream_t st) {
+    return dev_malloc_async_raw(reinterpret_cast<void**>(p), bytes, st);
+}
+template <typename T>
+cudaError_t host_malloc_pinned(T** p, size_t bytes) { return host_malloc_pinned_raw(reinterpret_cast<void**>(p), bytes); }
+// test hook: the allocation after `after` more successful ones fails (-1: none); allocations held
+void set_alloc_failure(long long after);
+long long allocations_held();
+
 // ------------------------------------------------------------------ per-device setup
 constexpr int kMaxDevices = 64;
 // index of the current device (QS_ERR_INVALID_ARG beyond kMaxDevices)
@@ -342,8 +364,14 @@ void prepare_bz_matrix(int q, const std::vector<cplx>& K, unsigned char* host_ou
 void launch_dense_bz(void* psi, int n, const std::vector<int>& targets, const std::vector<int>& controls,
                      const std::vector<int>& cvals, const void* dmat, cudaStream_t st);
 bool oz_error_pending();
-// try_wait attempts of the tensor-core kernels' pipeline waits before they give up (< 0: default)
+// test hooks of the tensor-core kernels' bounded waits: try_wait attempts before a wait gives up
+// (< 0: default), and a first accumulator wait that reports a timeout at once
 void oz_set_wait_spins(long long spins);
+void oz_set_force_late(bool on);
+// test hooks of the batch kernel's grid barrier: polls before a wait gives up (< 0: default), and
+// CTA 0 not arriving at the first barrier
+void batch_set_wait_polls(long long polls);
+void batch_set_hold_cta(bool on);
 
 // complex128 arithmetic mode (QS_MATH_FP64 / QS_MATH_DF)
 int c128_math();

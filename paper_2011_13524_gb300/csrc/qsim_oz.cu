@@ -78,6 +78,8 @@ struct OzParams {
     IndexPlan ip;            // 4 targets (and controls) inserted
     uint64_t offs[kOzD];     // s(w), targets ascending
     uint64_t n_groups;
+    long long wait_spins;    // try_wait attempts of each accumulator wait before it gives up
+    int force_late;          // test hook: the first accumulator wait reports a timeout at once
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -120,8 +122,8 @@ __device__ __forceinline__ void group_set_sync(int warp) {
     }
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (long long spins = 0; spins < kOzSpinLimit; spins++) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit = kOzSpinLimit) {
+    for (long long spins = 0; spins <= limit; spins++) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -206,7 +208,7 @@ template <bool kPairs, bool kIeeeIn>
 __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict__ psi, const unsigned char* __restrict__ dmat,
                                                              const __grid_constant__ OzParams P, int* err) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar, drain_bar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -221,6 +223,7 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
         reinterpret_cast<uint4*>(smem + kOffMat)[i] = reinterpret_cast<const uint4*>(dmat)[i];
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&drain_bar)));
         s_fail = 0;
     }
     if (warp == 0) {
@@ -382,7 +385,7 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
         if (j < my_tiles) nv_cur = slice(j, vcur);  // abuf(j) was read by the MMAs of tile j - 2
         if (j >= 1) {
             if (!failed) {  // every thread waits itself; the vote reconverges the warp for tcgen05.ld
-                const bool late = !mbar_wait(smem_u32(&mbar), uint32_t((j - 1) & 1));
+                const bool late = (P.force_late && j == 1) || !mbar_wait(smem_u32(&mbar), uint32_t((j - 1) & 1), P.wait_spins);
                 if (__any_sync(0xffffffffu, late)) {
                     failed = true;
                     s_fail = 1;
@@ -405,8 +408,11 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
     __syncthreads();  // every thread's s_fail store is visible
     if (s_fail && tid == 0) {
         atomicExch(err, 1);
-        mbar_wait(smem_u32(&mbar), 0);  // bounded: let the MMAs in flight finish before TMEM is freed
-        mbar_wait(smem_u32(&mbar), 1);
+        // bounded: the MMAs this thread issued finish before TMEM is freed (a commit to a barrier
+        // of its own tracks every one of them)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&drain_bar)));
+        mbar_wait(smem_u32(&drain_bar), 0);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -470,6 +476,7 @@ struct Oz5Params {
     uint64_t offs[kOz5D];    // s(w), targets ascending
     uint64_t n_groups;
     long long wait_spins;    // try_wait attempts of each pipeline wait before it gives up
+    int force_late;          // test hook: a worker's first accumulator wait reports a timeout at once
 };
 
 __device__ __forceinline__ uint32_t kmaj5(uint32_t r, uint32_t k) {
@@ -763,7 +770,8 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
 #pragma unroll
                 for (int hv = 0; hv < 2; hv++) {
                     if (!failed) {  // the vote keeps `failed` warp-uniform for tcgen05.ld
-                        const bool late = !mbar_wait_or_abort(done0 + 8u * uint32_t(hv), uint32_t((j - 1) & 1), spins, fail);
+                        const bool late = (P.force_late && j == 1 && hv == 0) ||
+                                          !mbar_wait_or_abort(done0 + 8u * uint32_t(hv), uint32_t((j - 1) & 1), spins, fail);
                         if (__any_sync(0xffffffffu, late)) {
                             failed = true;
                             *fail = 1;
@@ -830,6 +838,8 @@ struct BzParams {
     IndexPlan ip;
     uint64_t offs[1 << Q];
     uint64_t n_groups;
+    long long wait_spins;    // try_wait attempts of each accumulator wait before it gives up
+    int force_late;          // test hook: the first accumulator wait reports a timeout at once
 };
 
 // the three slices of x * inv (|x * inv| <= 1): multiples of 2^-8, 2^-16, 2^-24
@@ -857,7 +867,7 @@ __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(f
                                                                                int* err) {
     using B = Bz<Q>;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar, drain_bar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -870,6 +880,7 @@ __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(f
         reinterpret_cast<uint4*>(smem + B::OffMat)[i] = reinterpret_cast<const uint4*>(dmat)[i];
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&drain_bar)));
         s_fail = 0;
     }
     if (warp == 0) {
@@ -1000,7 +1011,7 @@ __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(f
         }
         if (j >= 1) {
             if (!failed) {  // every thread waits itself; the vote reconverges the warp for tcgen05.ld
-                const bool late = !mbar_wait(smem_u32(&mbar), uint32_t((j - 1) & 1));
+                const bool late = (P.force_late && j == 1) || !mbar_wait(smem_u32(&mbar), uint32_t((j - 1) & 1), P.wait_spins);
                 if (__any_sync(0xffffffffu, late)) {
                     failed = true;
                     s_fail = 1;
@@ -1025,8 +1036,11 @@ __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(f
     __syncthreads();  // every thread's s_fail store is visible
     if (s_fail && tid == 0) {
         atomicExch(err, 1);
-        mbar_wait(smem_u32(&mbar), 0);  // bounded: let the MMAs in flight finish before TMEM is freed
-        mbar_wait(smem_u32(&mbar), 1);
+        // bounded: the MMAs this thread issued finish before TMEM is freed (a commit to a barrier
+        // of its own tracks every one of them)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&drain_bar)));
+        mbar_wait(smem_u32(&drain_bar), 0);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -1045,6 +1059,7 @@ struct OzDevice {
 OzDevice g_oz_dev[kOzMaxDevices];
 std::mutex g_oz_mu;
 std::atomic<long long> g_oz_wait_spins{kOzSpinLimit};
+std::atomic<int> g_oz_force_late{0};
 
 OzDevice& oz_init() {
     int dev = 0;
@@ -1056,7 +1071,7 @@ OzDevice& oz_init() {
         int sms = 0;
         QS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         if (!d.err) {
-            QS_TRY_CUDA(cudaMalloc(&d.err, sizeof(int)));
+            QS_TRY_CUDA(dev_malloc(&d.err, sizeof(int)));
             QS_TRY_CUDA(cudaMemset(d.err, 0, sizeof(int)));
         }
         d.sms = sms;
@@ -1143,6 +1158,8 @@ void launch_dense_oz4(void* psi, int n, const std::vector<int>& targets, const s
             if ((w >> j) & 1) o |= 1ull << targets[j];
         P.offs[w] = o;
     }
+    P.wait_spins = g_oz_wait_spins.load();
+    P.force_late = g_oz_force_late.load();
     P.n_groups = P.ip.n_iter;
     const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, 2 * uint64_t(D.sms))));
@@ -1221,6 +1238,7 @@ void launch_dense_oz5(void* psi, int n, const std::vector<int>& targets, const s
     P.ip = make_index_plan(n, fixed, setmask);
     P.n_groups = P.ip.n_iter;
     P.wait_spins = g_oz_wait_spins.load();
+    P.force_late = g_oz_force_late.load();
     for (int w = 0; w < kOz5D; w++) {
         uint64_t o = 0;
         for (int j = 0; j < kOz5Q; j++)
@@ -1300,6 +1318,8 @@ void launch_bz_t(void* psi, int n, const std::vector<int>& targets, const std::v
     }
     BzParams<Q> P;
     P.ip = make_index_plan(n, fixed, setmask);
+    P.wait_spins = g_oz_wait_spins.load();
+    P.force_late = g_oz_force_late.load();
     P.n_groups = P.ip.n_iter;
     for (int w = 0; w < B::D; w++) {
         uint64_t o = 0;
@@ -1347,7 +1367,9 @@ bool oz_error_pending() {
     return e != 0;
 }
 
-// try_wait attempts of the 5-target kernel's pipeline waits (spins < 0: the default limit)
+// test hooks: try_wait attempts of the tensor-core kernels' accumulator and pipeline waits (< 0:
+// the default limit), and whether their first accumulator wait reports a timeout at once
 void oz_set_wait_spins(long long spins) { g_oz_wait_spins.store(spins < 0 ? kOzSpinLimit : spins); }
+void oz_set_force_late(bool on) { g_oz_force_late.store(on ? 1 : 0); }
 
 }  // namespace qs

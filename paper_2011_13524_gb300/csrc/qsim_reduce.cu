@@ -337,15 +337,15 @@ void ensure_scratch(qs_state* s, size_t part_doubles) {
     if (sc.part_cap < part_doubles) {
         if (sc.d_part) {
             QS_TRY_CUDA(cudaStreamSynchronize(s->stream));
-            cudaFree(sc.d_part);
+            dev_free(sc.d_part);
             sc.d_part = nullptr;
             sc.part_cap = 0;
         }
-        QS_TRY_CUDA(cudaMalloc(&sc.d_part, part_doubles * sizeof(double)));
+        QS_TRY_CUDA(dev_malloc(&sc.d_part, part_doubles * sizeof(double)));
         sc.part_cap = part_doubles;
     }
     if (!sc.h_out) {
-        QS_TRY_CUDA(cudaMallocHost(&sc.h_out, 16 * sizeof(double)));
+        QS_TRY_CUDA(host_malloc_pinned(&sc.h_out, 16 * sizeof(double)));
         sc.out_cap = 16;
     }
 }
@@ -573,13 +573,13 @@ void sample_state(const qs_state* st, int count, const double* uniforms, uint64_
     double* d_resid = nullptr;
     uint64_t* d_out = nullptr;
     auto cleanup = [&]() {
-        if (d_mass) cudaFreeAsync(d_mass, s->stream);
-        if (d_chunk) cudaFreeAsync(d_chunk, s->stream);
-        if (d_resid) cudaFreeAsync(d_resid, s->stream);
-        if (d_out) cudaFreeAsync(d_out, s->stream);
+        if (d_mass) dev_free_async(d_mass, s->stream);
+        if (d_chunk) dev_free_async(d_chunk, s->stream);
+        if (d_resid) dev_free_async(d_resid, s->stream);
+        if (d_out) dev_free_async(d_out, s->stream);
     };
     try {
-        QS_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_mass), B * sizeof(double), s->stream));
+        QS_TRY_CUDA(dev_malloc_async(reinterpret_cast<void**>(&d_mass), B * sizeof(double), s->stream));
         with_type(arith_of(s), s->data, [&](auto p) {
             k_chunk_mass<<<unsigned(B), kRedThreads, 0, s->stream>>>(p, N, chunk_log, d_mass);
         });
@@ -604,9 +604,9 @@ void sample_state(const qs_state* st, int count, const double* uniforms, uint64_
             chunk[k] = c;
             resid[k] = target - cum[c];
         }
-        QS_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_chunk), count * sizeof(uint64_t), s->stream));
-        QS_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_resid), count * sizeof(double), s->stream));
-        QS_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_out), count * sizeof(uint64_t), s->stream));
+        QS_TRY_CUDA(dev_malloc_async(reinterpret_cast<void**>(&d_chunk), count * sizeof(uint64_t), s->stream));
+        QS_TRY_CUDA(dev_malloc_async(reinterpret_cast<void**>(&d_resid), count * sizeof(double), s->stream));
+        QS_TRY_CUDA(dev_malloc_async(reinterpret_cast<void**>(&d_out), count * sizeof(uint64_t), s->stream));
         QS_TRY_CUDA(cudaMemcpyAsync(d_chunk, chunk.data(), count * sizeof(uint64_t), cudaMemcpyHostToDevice, s->stream));
         QS_TRY_CUDA(cudaMemcpyAsync(d_resid, resid.data(), count * sizeof(double), cudaMemcpyHostToDevice, s->stream));
         const unsigned blocks = unsigned((uint64_t(count) * 32 + kRedThreads - 1) / kRedThreads);
@@ -635,7 +635,7 @@ void launch_apply_observable(const std::vector<PauliGroup>& groups, const void* 
         return;
     }
     ObsDevTerm* d_terms = nullptr;
-    QS_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d_terms), terms.size() * sizeof(ObsDevTerm), st));
+    QS_TRY_CUDA(dev_malloc_async(reinterpret_cast<void**>(&d_terms), terms.size() * sizeof(ObsDevTerm), st));
     QS_TRY_CUDA(cudaMemcpyAsync(d_terms, terms.data(), terms.size() * sizeof(ObsDevTerm), cudaMemcpyHostToDevice, st));
     const unsigned g = red_grid(N);
     if (ar == Arith::DF) {
@@ -659,7 +659,7 @@ void launch_apply_observable(const std::vector<PauliGroup>& groups, const void* 
         });
     }
     QS_TRY_CUDA(cudaGetLastError());
-    QS_TRY_CUDA(cudaFreeAsync(d_terms, st));
+    QS_TRY_CUDA(dev_free_async(d_terms, st));
 }
 
 }  // namespace qs
