@@ -461,6 +461,11 @@ def measure_extras(args, qs, torch, circuit):
     out["batch_ms"] = 1e3 * dt
     out["batch_params"] = b.total_params
     out["batch_workspace_gib"] = b.workspace_bytes / 2**30
+    peak, _ = measured_peaks()
+    out["batch_roofline"] = {"bound": "hbm", "achieved": b.traffic_bytes / dt / 1e9, "peak": peak, "unit": "GB/s",
+                             "frac": b.traffic_bytes / dt / 1e9 / peak, "bytes_per_run": b.traffic_bytes,
+                             "note": "psi/lambda passes of the circuits wider than 13 qubits; the narrower "
+                                     "ones run in shared memory (latency-bound, no HBM traffic)"}
     del b
     # precision: the same circuit as complex64 and complex128 (double-float) on the GPU, n = 30;
     # max-abs amplitude difference, 1 - fidelity and the transverse-field Ising energy (h = 1)
@@ -559,20 +564,62 @@ def measure_extras(args, qs, torch, circuit):
     return out
 
 
+def batch_shard(args, rank, ws):
+    """The 4096-pair batch workload, split across ranks by cost (every rank computes the same
+    split); this rank's (indices, items)."""
+    from paper_2011_13524_gb300 import shard
+    items = W.batch_workload(args.batch_count, args.seed)
+    parts = shard.split([shard.pair_cost(i.circuit) for i in items], ws)
+    idx = parts[rank]
+    return idx, [items[i] for i in idx], len(items)
+
+
 def run_batch_only(args):
+    """The batched workload alone: each rank evaluates its share of the pairs (split by cost, no
+    data exchanged), the results are gathered on rank 0, which prints one JSON line."""
     import torch
     import paper_2011_13524_gb300 as qs
-    items = W.batch_workload(args.batch_count, args.seed)
+    from paper_2011_13524_gb300 import shard
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        pg = tdist
+    idx, items, count = batch_shard(args, rank, ws)
     b = qs.Batch([i.circuit for i in items], [i.observable for i in items])
     theta = np.concatenate([i.circuit.parameters() for i in items])
     for _ in range(args.warmup):
         b.run(theta, use_graph=True)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        b.run(theta, use_graph=True)
+        e, g = b.run(theta, use_graph=True)
+    torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / args.steps
-    print(json.dumps({"batch_circuits": args.batch_count, "batch_ms": 1e3 * dt,
-                      "batch_circuits_per_s": args.batch_count / dt, "passes": b.total_passes}), flush=True)
+    dt = max_over_ranks(1e3 * dt, pg, "cuda") / 1e3
+    e_all, g_all = shard.gather(pg, count, idx, e, g)
+    traffic = b.traffic_bytes
+    if pg:
+        t = torch.tensor([traffic], device="cuda", dtype=torch.float64)
+        pg.all_reduce(t)
+        traffic = float(t.item())
+    peak, peak_kind = measured_peaks()
+    if rank == 0:
+        print(json.dumps({"batch_circuits": count, "ranks": ws, "batch_ms": 1e3 * dt,
+                          "batch_circuits_per_s": count / dt, "passes_rank0": b.total_passes,
+                          "energies_finite": bool(np.all(np.isfinite(e_all))),
+                          "roofline": {"bound": "hbm", "achieved": traffic / dt / 1e9 / ws, "peak": peak,
+                                       "unit": "GB/s per GPU", "frac": traffic / dt / 1e9 / ws / peak,
+                                       "peak_source": peak_kind,
+                                       "bytes_per_run": traffic,
+                                       "note": "psi/lambda traffic of the circuits wider than 13 qubits; "
+                                               "narrower ones run in shared memory"}}), flush=True)
+    if pg:
+        pg.destroy_process_group()
 
 
 def main():

@@ -350,6 +350,12 @@ qs_status qs_batch_create(const qs_circuit* circuits, const qs_pauli_obs* observ
  * gradients concatenated like theta. Synchronises. */
 qs_status qs_batch_run(qs_batch* b, const double* theta, void* stream, int use_graph, double* energies,
                        double* grads);
+/* Algorithmic device-memory traffic of one qs_batch_run, in bytes: the psi and lambda buffers of
+ * the circuits wider than 13 qubits that their passes read and write (the first forward pass
+ * writes psi, later ones read and write it; lambda = H psi reads psi and writes lambda; each
+ * reverse pass reads and writes both). Narrower circuits run in shared memory and move only
+ * their results. */
+qs_status qs_batch_traffic(const qs_batch* b, double* bytes);
 /* Total parameters, total passes of the compiled batch and device workspace bytes (any may be NULL). */
 qs_status qs_batch_info(const qs_batch* b, int* total_params, int* total_passes, size_t* workspace_bytes);
 qs_status qs_batch_destroy(qs_batch* b);

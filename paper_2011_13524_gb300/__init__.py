@@ -139,6 +139,7 @@ _SIGNATURES = {
     "qs_batch_info": ([_VOIDP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                        ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "qs_batch_destroy": ([_VOIDP], ctypes.c_int),
+    "qs_batch_traffic": ([_VOIDP, _DP], ctypes.c_int),
     "qs_norm2": ([_VOIDP, _DP], ctypes.c_int),
     "qs_adjoint_grad": ([ctypes.POINTER(QsCircuit), _DP, ctypes.POINTER(QsPauliObs), ctypes.c_int, _VOIDP,
                          _DP, _DP], ctypes.c_int),
@@ -543,6 +544,9 @@ class Batch:
         tp, npass, ws = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_size_t(0)
         check(lib().qs_batch_info(h, ctypes.byref(tp), ctypes.byref(npass), ctypes.byref(ws)))
         self.total_params, self.total_passes, self.workspace_bytes = tp.value, npass.value, ws.value
+        tr = ctypes.c_double(0)
+        check(lib().qs_batch_traffic(h, ctypes.byref(tr)))
+        self.traffic_bytes = tr.value
 
     def run(self, theta=None, use_graph: bool = True, stream=None):
         """(energies, list of per-circuit gradient arrays)."""

@@ -1278,6 +1278,24 @@ qs_status qs_batch_info(const qs_batch* b, int* total_params, int* total_passes,
     BATCH_END
 }
 
+qs_status qs_batch_traffic(const qs_batch* b, double* bytes) {
+    BATCH_BEGIN
+    QS_REQUIRE(b != nullptr && bytes != nullptr, "null batch or output");
+    // circuits wider than the window: the first forward pass writes psi (it starts from |0..0> in
+    // shared memory), every later one reads and writes it; lambda = H psi reads psi and writes
+    // lambda; every reverse pass reads and writes both. Narrower circuits stay in shared memory.
+    double total = 0.0;
+    for (const BItem& it : b->items) {
+        if (it.n <= kLocal) continue;
+        const double amp = 8.0 * std::ldexp(1.0, it.n);  // complex64
+        const int np_ = it.p1 - it.p0;
+        if (np_ > 0) total += amp + 2.0 * amp * (np_ - 1);
+        total += 2.0 * amp + 4.0 * amp * np_;
+    }
+    *bytes = total;
+    BATCH_END
+}
+
 qs_status qs_batch_run(qs_batch* b, const double* theta, void* stream, int use_graph, double* energies,
                        double* grads) {
     BATCH_BEGIN
