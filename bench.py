@@ -39,7 +39,9 @@ HBM_PEAK_FALLBACK = 6800.0
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of the kernel as it is
 # built now, at a smaller state than the bench's and scaled to n = 30 by the amplitudes a launch
 # updates (the traffic of these kernels grows in proportion to the state): (kernel, n) -> bytes.
-NCU_TRAFFIC = {("dense_df", 27): 4232672512, ("dense_df", 30): 4232672512 * 8}
+# k_dense_oz5 at n = 27: 2147592448 bytes read + 2085491712 written in one launch.
+NCU_TRAFFIC = {("dense_df", 27): 4232672512, ("dense_df", 30): 4232672512 * 8,
+               ("dense_oz5", 27): 4233084160, ("dense_oz5", 30): 4233084160 * 8}
 
 
 def parse():
@@ -152,16 +154,21 @@ def zz_obs(n):
 
 
 # ---------------------------------------------------------------- CPU oracle timing
-# One gate mix for both CPU numbers (the cpu_baseline leg and the --impl reference arm): the
-# circuit's gates sampled evenly along it, gate i of the sample being gate floor(i G / M) of the
-# circuit (M = 90: a tenth of the 890-gate circuit, its U3 / CZ proportions), applied in that
-# order to a 2^n complex128 state. The per-gate cost does not depend on the amplitudes.
+# One gate mix for both CPU numbers (the cpu_baseline leg and the --impl reference arm): triples
+# of two U3 gates and one CZ taken in circuit order (the circuit has 600 U3 and 290 CZ, about 2:1),
+# 30 triples (90 gates), applied to a 2^n complex128 state. The cpu_baseline leg times the first
+# 9 triples; each step of the reference arm applies the next triple. The per-gate cost does not
+# depend on the amplitudes.
 ORACLE_SAMPLE = 90
 
 
 def oracle_sample(circuit, m=ORACLE_SAMPLE):
-    G = len(circuit.gates)
-    return [circuit.gates[(i * G) // m] for i in range(m)]
+    u3 = [g for g in circuit.gates if g.name == "U3"]
+    cz = [g for g in circuit.gates if g.name == "CZ"]
+    out = []
+    for t in range(m // 3):
+        out += [u3[(2 * t) % len(u3)], u3[(2 * t + 1) % len(u3)], cz[t % len(cz)]]
+    return out
 
 
 def oracle_gates_per_s(n, circuit, n_gates):
@@ -178,8 +185,8 @@ def oracle_gates_per_s(n, circuit, n_gates):
 
 
 def run_reference(args):
-    """The FP64 oracle on the benchmark's workload: each step applies the next 3 gates of the
-    sample (cycling), on the host cores."""
+    """The FP64 oracle on the benchmark's workload: each step applies the next triple (two U3,
+    one CZ) of the sample, on the host cores."""
     ws, rank, _ = dist()
     if rank != 0:
         return
@@ -210,8 +217,8 @@ def run_reference(args):
                                    f"fused (autotuned width), then <Z0Z1>",
                        "n": n, "depth": args.depth, "gates": len(circuit.gates), "seed": args.seed},
             "cpu_baseline": {"value": v, "unit": "gates/s", "cores": oracle.threads(), "kind": "oracle",
-                             "sample": f"{per_step} gates per step from the evenly spaced {len(sample)}-gate "
-                                       f"sample of the circuit, on a 2^{n} complex128 state"},
+                             "sample": f"{per_step} gates per step (two U3, one CZ: the circuit's 2:1 mix) from the "
+                                       f"{len(sample)}-gate sample of the circuit, on a 2^{n} complex128 state"},
             "e2e": {"value": v, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -373,9 +380,9 @@ def run_ours(args):
         line["extras"] = extras
         rate, cores, dt, names = oracle_gates_per_s(n, circuit, args.cpu_sample_gates)
         line["cpu_baseline"] = {"value": rate, "unit": "gates/s", "cores": cores, "kind": "oracle",
-                                "sample": f"the first {args.cpu_sample_gates} gates ({'/'.join(names)}) of the evenly "
-                                          f"spaced {ORACLE_SAMPLE}-gate sample of the circuit, applied to a 2^{n} "
-                                          f"complex128 state, {dt:.1f} s"}
+                                "sample": f"the first {args.cpu_sample_gates} gates ({'/'.join(names)}; two U3 and one "
+                                          f"CZ per triple, the circuit's 2:1 mix) of the {ORACLE_SAMPLE}-gate sample "
+                                          f"of the circuit, applied to a 2^{n} complex128 state, {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:

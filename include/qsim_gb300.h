@@ -197,7 +197,9 @@ qs_status qs_copy_state(const qs_state* src, qs_state* dst);
 qs_status qs_synchronize(const qs_state* s);
 
 /* ---------------------------------------------------------------- gates (Sec. 4.3) */
-/* psi <- K psi for one gate (Eq. update_mat; controlled, diagonal, Pauli and named forms). */
+/* psi <- K psi for one gate (Eq. update_mat; controlled, diagonal, Pauli and named forms).
+ * complex128 dense gates of 3 or more targets use the double-float arithmetic (with its layout
+ * change in and out) when it is selected; other gates use IEEE FP64 arithmetic, one pass. */
 qs_status qs_apply_gate(qs_state* s, const qs_gate* g);
 /* psi <- K psi for a dense k-qubit matrix (k in 1..6), as produced by gate fusion
  * (Sec. 5.4 merge). Equivalent to qs_apply_gate with a QS_GATE_DENSE gate. */

@@ -134,6 +134,19 @@ struct DFScope {
     }
 };
 
+// One gate outside a circuit run. complex128 dense gates of three or more targets take the
+// double-float arithmetic (and the tensor-core blocks) when the state's settings select it: in
+// FP64 they are bound by GB300's FP64 rate, so the layout change in and out (two passes) costs
+// less than the FP64 update. Other gates keep IEEE FP64 arithmetic (one pass).
+void apply_single(qs_state* s, const Op& op) {
+    if (use_df(s) && op.kind == OpKind::Dense && op.targets.size() >= 3) {
+        DFScope df(s, true);
+        launch_op_arith(op, s->data, s->n, Arith::DF, s->stream, stage_of(s));
+        return;
+    }
+    launch_op(op, s->data, s->n, s->dt, s->stream, stage_of(s));
+}
+
 void run_gates(qs_state* s, const qs_circuit* c, const double* theta) {
     std::vector<Op> ops;
     ops.reserve(c->n_gates);
@@ -725,8 +738,7 @@ qs_status qs_apply_gate(qs_state* s, const qs_gate* g) {
     STATE_SETTINGS(s);
     check_state(s);
     QS_REQUIRE(g != nullptr, "null gate");
-    Op op = op_of_gate(*g, s->n, nullptr);
-    launch_op(op, s->data, s->n, s->dt, s->stream, stage_of(s));
+    apply_single(s, op_of_gate(*g, s->n, nullptr));
     API_END
 }
 
@@ -743,8 +755,7 @@ qs_status qs_apply_fused(qs_state* s, int k, const int* targets, const double* m
     for (int j = 0; j < k; j++) g.targets[j] = targets[j];
     g.mat = mat;
     g.param_index = -1;
-    Op op = op_of_gate(g, s->n, nullptr);
-    launch_op(op, s->data, s->n, s->dt, s->stream, stage_of(s));
+    apply_single(s, op_of_gate(g, s->n, nullptr));
     API_END
 }
 
