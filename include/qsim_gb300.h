@@ -296,7 +296,7 @@ qs_status qs_expectation_plan(int n, const qs_pauli_obs* obs, int* n_passes, uin
  * It calls no cudaMalloc, cudaFree or other allocating routine. Its per-block partial sums live
  * in one fixed 512 KiB array in device memory that every GPU loading the library keeps until the
  * process exits. The first call on a device looks up that array's address (once per device, with
- * the device current); make that first call before any stream capture. Every call shares the
+ * the device current). Every call shares the
  * array and each block overwrites its own slots, so nothing needs clearing, but calls that overlap
  * on the GPU (other streams, other threads) race on it: serialise them. The launches share the
  * array's 32767 block partials (grids shrink to fit); an observable that needs more launches than
