@@ -172,6 +172,25 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
     t = __fsub_rn(b, __fsub_rn(s, a));
 }
 
+// Packed pairs: sm_100 and later execute two FP32 operations per instruction (FADD2, FMUL2,
+// FFMA2), each lane rounding exactly as the scalar instruction does, so a pair computation gives
+// the same bits as two scalar ones with half the issued instructions. They pay where the two
+// operands already sit side by side (a complex64 amplitude; the real and imaginary columns of an
+// accumulator); the double-float slicing, whose pairs would first have to be gathered from
+// {re_hi, re_lo, im_hi, im_lo}, measured slower packed and stays scalar.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+// c - a with one rounding, as fma(a, -1, c)
+__device__ __forceinline__ float2 rsub2(float2 c, float2 a) { return __ffma2_rn(a, make_float2(-1.f, -1.f), c); }
+template <int S>
+__device__ __forceinline__ float2 grid_round2(float2 x) {
+    constexpr float c = 1.5f * float(1 << 15) / float(1ull << (8 * S));
+    return __fadd2_rn(__fadd2_rn(x, dup2(c)), dup2(-c));
+}
+__device__ __forceinline__ void fast_two_sum2(float2 a, float2 b, float2& s, float2& t) {
+    s = __fadd2_rn(a, b);
+    t = rsub2(b, rsub2(s, a));
+}
+
 __device__ __forceinline__ float pow2_ceil(float m) {
     // smallest power of two >= m for m > 0 (1 for m == 0), exponent kept in range
     if (!(m > 0.f)) return 1.f;
@@ -194,6 +213,9 @@ __device__ __forceinline__ void st_pair(float4* p, const float4& a, const float4
                  "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
                  : "memory");
 }
+
+// L2 prefetch of one line (no register is written; the later load finds the line in L2)
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 // the 16 bytes of an IEEE complex128 amplitude, loaded as four floats, in the double-float layout
 // {re_hi, re_lo, im_hi, im_lo} (the split of the layout-change pass)
@@ -332,29 +354,29 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
                              : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3])
                              : "r"(lane_base + uint32_t(d * kOzR + 4 * c)));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            float o[2][4];
+            float2 hi[2], lo[2];  // per amplitude i: (real, imaginary) high and low words
 #pragma unroll
             for (int i = 0; i < 2; i++) {
+                // columns 2i, 2i + 1 (real and imaginary part of one amplitude) as packed pairs:
+                // D_6 + D_5 + D_4 in FP32 (rounding far below 2^-48 of the output), then D_3..D_0
+                // added exactly with Fast2Sum, the errors collected in l
+                float2 D[kOzND];
 #pragma unroll
-                for (int cc = 0; cc < 2; cc++) {
-                    const int col = 2 * i + cc;
-                    // D_6 + D_5 + D_4 in FP32 (rounding far below 2^-48 of the output), then
-                    // D_3..D_0 added exactly with Fast2Sum, the errors collected in lo
-                    float sm = __fadd_rn(__fadd_rn(__uint_as_float(r[6][col]), __uint_as_float(r[5][col])),
-                                         __uint_as_float(r[4][col]));
-                    float lo = 0.f, t;
+                for (int d = 0; d < kOzND; d++)
+                    D[d] = make_float2(__uint_as_float(r[d][2 * i]), __uint_as_float(r[d][2 * i + 1]));
+                float2 sm = __fadd2_rn(__fadd2_rn(D[6], D[5]), D[4]);
+                float2 l = make_float2(0.f, 0.f), t;
 #pragma unroll
-                    for (int d = 3; d >= 0; d--) {
-                        fast_two_sum(__uint_as_float(r[d][col]), sm, sm, t);
-                        lo = __fadd_rn(lo, t);
-                    }
-                    const float sc = __fmul_rn(mu[16 * h + 4 * c + col], nv);
-                    fast_two_sum(__fmul_rn(sm, sc), __fmul_rn(lo, sc), o[i][2 * cc], o[i][2 * cc + 1]);
+                for (int d = 3; d >= 0; d--) {
+                    fast_two_sum2(D[d], sm, sm, t);
+                    l = __fadd2_rn(l, t);
                 }
+                const float2 sc = __fmul2_rn(*reinterpret_cast<const float2*>(mu + 16 * h + 4 * c + 2 * i), dup2(nv));
+                fast_two_sum2(__fmul2_rn(sm, sc), __fmul2_rn(l, sc), hi[i], lo[i]);
             }
             if (x0 != ~0ull) {
-                const float4 a = make_float4(o[0][0], o[0][1], o[0][2], o[0][3]);
-                const float4 b = make_float4(o[1][0], o[1][1], o[1][2], o[1][3]);
+                const float4 a = make_float4(hi[0].x, lo[0].x, hi[0].y, lo[0].y);
+                const float4 b = make_float4(hi[1].x, lo[1].x, hi[1].y, lo[1].y);
                 if (kPairs) {
                     st_pair(psi + x0 + off[2 * c], a, b);
                 } else {
@@ -380,6 +402,13 @@ __global__ void __launch_bounds__(kOzThreads, 2) k_dense_oz4(float4* __restrict_
         if (j + 1 < my_tiles) {
             x0_next = group_x0(j + 1);
             load(x0_next, vnext);
+        }
+        if (j + 2 < my_tiles) {  // tile j + 2 into L2, so that next tile's loads find it there
+            const uint64_t xp = group_x0(j + 2);
+            if (xp != ~0ull) {
+#pragma unroll
+                for (int i = 0; i < kOzAmpsPerThread; i += (kPairs ? 2 : 1)) prefetch_l2(psi + xp + off[i]);
+            }
         }
         float nv_cur = 1.f;
         if (j < my_tiles) nv_cur = slice(j, vcur);  // abuf(j) was read by the MMAs of tile j - 2
@@ -702,32 +731,32 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
                                  : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3])
                                  : "r"(lane_base + uint32_t(d * kOz5D + 4 * c)));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                float o[2][4];
+                float2 hi[2], lo[2];  // per amplitude i: (real, imaginary) high and low words
 #pragma unroll
                 for (int i = 0; i < 2; i++) {
+                    // columns 2i, 2i + 1 (real and imaginary part of one amplitude) as pairs.
+                    // D_0 + D_1 + D_2 + D_3 from the largest: each partial sum is a multiple of
+                    // the unit of the next diagonal (2^-8(d+2)), which is at least the ulp of
+                    // that diagonal's value, so every Fast2Sum is exact; when a partial sum
+                    // cancels to below its next diagonal's range it is exact and its error
+                    // term is zero. The error terms and D_4 + D_5 + D_6 (FP32, rounding far below
+                    // 2^-48 of the output) make up lo.
+                    float2 D[kOzND];
 #pragma unroll
-                    for (int cc = 0; cc < 2; cc++) {
-                        const int col = 2 * i + cc;
-                        // D_0 + D_1 + D_2 + D_3 from the largest: each partial sum is a multiple of
-                        // the unit of the next diagonal (2^-8(d+2)), which is at least the ulp of
-                        // that diagonal's value, so every Fast2Sum is exact; when a partial sum
-                        // cancels to below its next diagonal's range it is exact and its error
-                        // term is zero. The error terms and D_4 + D_5 + D_6 (FP32, rounding far below
-                        // 2^-48 of the output) make up lo.
-                        float sm, t1, t2, t3;
-                        fast_two_sum(__uint_as_float(r[0][col]), __uint_as_float(r[1][col]), sm, t1);
-                        fast_two_sum(sm, __uint_as_float(r[2][col]), sm, t2);
-                        fast_two_sum(sm, __uint_as_float(r[3][col]), sm, t3);
-                        const float low = __fadd_rn(__fadd_rn(__uint_as_float(r[6][col]), __uint_as_float(r[5][col])),
-                                                    __uint_as_float(r[4][col]));
-                        const float lo = __fadd_rn(__fadd_rn(__fadd_rn(t3, t2), t1), low);
-                        const float sc = __fmul_rn(mu[kOz5D * hv + 8 * q + 4 * c + col], nv);
-                        fast_two_sum(__fmul_rn(sm, sc), __fmul_rn(lo, sc), o[i][2 * cc], o[i][2 * cc + 1]);
-                    }
+                    for (int d = 0; d < kOzND; d++)
+                        D[d] = make_float2(__uint_as_float(r[d][2 * i]), __uint_as_float(r[d][2 * i + 1]));
+                    float2 sm, t1, t2, t3;
+                    fast_two_sum2(D[0], D[1], sm, t1);
+                    fast_two_sum2(sm, D[2], sm, t2);
+                    fast_two_sum2(sm, D[3], sm, t3);
+                    const float2 low = __fadd2_rn(__fadd2_rn(D[6], D[5]), D[4]);
+                    const float2 l = __fadd2_rn(__fadd2_rn(__fadd2_rn(t3, t2), t1), low);
+                    const float2 sc = __fmul2_rn(*reinterpret_cast<const float2*>(mu + kOz5D * hv + 8 * q + 4 * c + 2 * i), dup2(nv));
+                    fast_two_sum2(__fmul2_rn(sm, sc), __fmul2_rn(l, sc), hi[i], lo[i]);
                 }
                 if (valid) {
-                    const float4 a = make_float4(o[0][0], o[0][1], o[0][2], o[0][3]);
-                    const float4 bb = make_float4(o[1][0], o[1][1], o[1][2], o[1][3]);
+                    const float4 a = make_float4(hi[0].x, lo[0].x, hi[0].y, lo[0].y);
+                    const float4 bb = make_float4(hi[1].x, lo[1].x, hi[1].y, lo[1].y);
                     if (kPairs) {
                         st_pair(psi + x0 + off(4 * hv + 2 * c), a, bb);
                     } else {
@@ -750,6 +779,16 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
             load(x0_cur, v);
         }
         for (uint64_t j = 0; j <= my_tiles && my_tiles > 0; j++) {
+            // tile j + 2 into L2 now, so that the loads of tile j + 1 (issued after this slice) and
+            // of tile j + 2 (one tile later) find their lines there: the register loads alone have
+            // less than a tile of latency to hide, and the DRAM queue under a full state pass is
+            // longer than that (measured: 3.6 % less time per block at n = 30)
+            if (j + 2 < my_tiles) {
+                bool ok_pf;
+                const uint64_t xp = group_x0(j + 2, ok_pf);
+#pragma unroll
+                for (int i = 0; i < kOz5Amps; i += (kPairs ? 2 : 1)) prefetch_l2(psi + xp + off(i));
+            }
             float nv_cur = 1.f;
             if (j < my_tiles) {
                 // buffer j & 1 was last read by the MMAs of tile j - 2, which finished before
@@ -842,13 +881,14 @@ struct BzParams {
     int force_late;          // test hook: the first accumulator wait reports a timeout at once
 };
 
-// the three slices of x * inv (|x * inv| <= 1): multiples of 2^-8, 2^-16, 2^-24
-__device__ __forceinline__ void slice3(float x, float inv, float (&a)[kBzNS]) {
-    x = __fmul_rn(x, inv);
-    a[0] = grid_round<0>(x);
-    const float r = __fsub_rn(x, a[0]);
-    a[1] = grid_round<1>(r);
-    a[2] = grid_round<2>(__fsub_rn(r, a[1]));
+// the three slices of x * inv (|x * inv| <= 1, real and imaginary part of one amplitude at once,
+// as packed pairs): multiples of 2^-8, 2^-16, 2^-24
+__device__ __forceinline__ void slice3x2(float2 x, float2 inv, float2 (&a)[kBzNS]) {
+    x = __fmul2_rn(x, inv);
+    a[0] = grid_round2<0>(x);
+    const float2 r = rsub2(x, a[0]);
+    a[1] = grid_round2<1>(r);
+    a[2] = grid_round2<2>(rsub2(r, a[1]));
 }
 
 template <int Q>
@@ -930,11 +970,10 @@ __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(f
             uint32_t pk[kBzNS][4];
 #pragma unroll
             for (int i = 0; i < 4; i++) {
-                float ar[kBzNS], ai[kBzNS];
-                slice3(v[4 * c + i].x, inv, ar);
-                slice3(v[4 * c + i].y, inv, ai);
+                float2 a[kBzNS];  // (real, imaginary) slices
+                slice3x2(v[4 * c + i], dup2(inv), a);
 #pragma unroll
-                for (int s2 = 0; s2 < kBzNS; s2++) pk[s2][i] = pack_bf16(ar[s2], ai[s2]);
+                for (int s2 = 0; s2 < kBzNS; s2++) pk[s2][i] = pack_bf16(a[s2].x, a[s2].y);
             }
             const uint32_t r = uint32_t(g), k = uint32_t(32 * h + 8 * c);
             const uint32_t o = (r >> 3) * B::Sbo + (k >> 3) * kOzLbo + (r & 7) * 16;
@@ -977,19 +1016,19 @@ __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(f
                              : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3])
                              : "r"(lane_base + uint32_t(d * B::R + 4 * c)));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            float o[4];
+            float2 o[2];  // two amplitudes: columns (2i, 2i + 1) = (real, imaginary), as pairs
 #pragma unroll
-            for (int col = 0; col < 4; col++) {
-                const float sm = __fadd_rn(__fadd_rn(__uint_as_float(r[2][col]), __uint_as_float(r[1][col])),
-                                           __uint_as_float(r[0][col]));
-                o[col] = __fmul_rn(sm, __fmul_rn(mu[32 * h + 4 * c + col], nv));
+            for (int i = 0; i < 2; i++) {
+                auto col = [&](int d) { return make_float2(__uint_as_float(r[d][2 * i]), __uint_as_float(r[d][2 * i + 1])); };
+                const float2 sm = __fadd2_rn(__fadd2_rn(col(2), col(1)), col(0));
+                o[i] = __fmul2_rn(sm, __fmul2_rn(*reinterpret_cast<const float2*>(mu + 32 * h + 4 * c + 2 * i), dup2(nv)));
             }
             if (x0 != ~0ull) {
                 if (kPairs) {
-                    *reinterpret_cast<float4*>(psi + x0 + P.offs[B::Amps * h + 2 * c]) = make_float4(o[0], o[1], o[2], o[3]);
+                    *reinterpret_cast<float4*>(psi + x0 + P.offs[B::Amps * h + 2 * c]) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
                 } else {
-                    psi[x0 + P.offs[B::Amps * h + 2 * c]] = make_float2(o[0], o[1]);
-                    psi[x0 + P.offs[B::Amps * h + 2 * c + 1]] = make_float2(o[2], o[3]);
+                    psi[x0 + P.offs[B::Amps * h + 2 * c]] = o[0];
+                    psi[x0 + P.offs[B::Amps * h + 2 * c + 1]] = o[1];
                 }
             }
         }
@@ -1008,6 +1047,16 @@ __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(f
         if (j + 1 < my_tiles) {
             x0_next = group_x0(j + 1);
             load(x0_next, vnext);
+        }
+        // tile j + 2 into L2, so that next tile's loads find it there (Q = 6, one CTA per SM; with
+        // two CTAs per SM (Q = 5) the loads already overlap the other CTA's work, and the prefetch
+        // measured 1 % slower)
+        if (Q == 6 && j + 2 < my_tiles) {
+            const uint64_t xp = group_x0(j + 2);
+            if (xp != ~0ull) {
+#pragma unroll
+                for (int i = 0; i < B::Amps; i += (kPairs ? 2 : 1)) prefetch_l2(psi + xp + P.offs[B::Amps * h + i]);
+            }
         }
         if (j >= 1) {
             if (!failed) {  // every thread waits itself; the vote reconverges the warp for tcgen05.ld
