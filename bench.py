@@ -41,7 +41,7 @@ HBM_PEAK_FALLBACK = 6800.0
 # updates (the traffic of these kernels grows in proportion to the state): (kernel, n) -> bytes.
 # k_dense_oz5 at n = 27: 2147592448 bytes read + 2085491712 written in one launch.
 NCU_TRAFFIC = {("dense_df", 27): 4232672512, ("dense_df", 30): 4232672512 * 8,
-               ("dense_oz5", 27): 4233084160, ("dense_oz5", 30): 4233084160 * 8}
+               ("dense_oz5", 27): 4267769472, ("dense_oz5", 30): 4267769472 * 8}
 
 
 def parse():
