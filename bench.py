@@ -39,7 +39,8 @@ HBM_PEAK_FALLBACK = 6800.0
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of the kernel as it is
 # built now, at a smaller state than the bench's and scaled to n = 30 by the amplitudes a launch
 # updates (the traffic of these kernels grows in proportion to the state): (kernel, n) -> bytes.
-# k_dense_oz5 at n = 27: 2147592448 bytes read + 2085491712 written in one launch.
+# k_dense_oz5 at n = 27: the mean of two launches, (2163700736 + 2085665536) and
+# (2203815936 + 2082356736) bytes read + written.
 NCU_TRAFFIC = {("dense_df", 27): 4232672512, ("dense_df", 30): 4232672512 * 8,
                ("dense_oz5", 27): 4267769472, ("dense_oz5", 30): 4267769472 * 8}
 
@@ -497,7 +498,6 @@ def measure_extras(args, qs, torch, circuit):
         ms = timed(lambda: stt.expectation(tf), reps=3)
         out["tfim_expectation_n30_%s_ms" % label] = ms
         out["tfim_expectation_n30_%s_read_gbps" % label] = reads * S * 2.0 ** n / (ms / 1e3) / 1e9
-        out["tfim_expectation_n30_%s_group_gbps" % label] = groups * S * 2.0 ** n / (ms / 1e3) / 1e9
     out["tfim_expectation_n30_reads"] = reads
     out["tfim_expectation_n30_groups"] = groups
     del a, c

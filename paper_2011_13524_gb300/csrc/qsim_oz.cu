@@ -651,9 +651,11 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
         // thread (g, q): group g of the tile (= TMEM lane); amplitudes 4q..4q+3 (half 0) and
         // 16+4q..16+4q+3 (half 1), held as v[0..3] and v[4..7]
         const int g = tid & (kOzTG - 1), q = tid >> 7;
-        // s(w) of this thread's amplitude i, read from the parameter bank at each use (not held in
-        // registers): amplitude (i / 4) * 16 + 4 q + i % 4
-        auto off = [&](int i) { return P.offs[(i >> 2) * (kOz5D / 2) + 4 * q + (i & 3)]; };
+        // s(w) of this thread's amplitude i, w = (i / 4) * 16 + 4 q + i % 4: s is additive over
+        // the disjoint bits of w, so s(w) = s(4q) (once per thread) + s((i / 4) * 16 + i % 4), a
+        // parameter at a compile-time index (an operand of the add, no indexed constant load)
+        const uint64_t qoff = P.offs[4 * q];
+        auto off = [&](int i) { return qoff + P.offs[(i >> 2) * (kOz5D / 2) + (i & 3)]; };
         const uint32_t lane_off = uint32_t((warp & 3) * 32) << 16;
 
         // This thread's group in tile j: group index t 128 + g, whose bit string with the fixed
