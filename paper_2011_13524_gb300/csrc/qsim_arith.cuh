@@ -141,10 +141,11 @@ __device__ __forceinline__ float4 narrow<float4>(double re, double im) {
 
 // double -> (hi, lo) floats with hi = RN(x) and lo = RN(x - hi), as split_double, but on the
 // integer pipes (GB300 runs FP64 and its conversions at 1/64 of the FP32 rate): hi takes the top
-// 24 significant bits rounded to nearest-even, lo the exact remainder rescaled (an integer below
-// 2^29 converted with rounding to nearest, times powers of two: an exact scaling into FP32's
-// normal range, then one rounding to the final, possibly subnormal, value, which equals RN of the
-// remainder). Zero is split directly. Magnitudes below 2^-126 (under FP32's normal range) become
+// 24 significant bits rounded to nearest-even, lo the remainder, an integer below 2^29 converted
+// to float with rounding to nearest and then scaled by powers of two. When lo is a normal float
+// the scaling is exact and lo = RN(x - hi); when it is subnormal (possible for |x| below 2^-74)
+// the last scaling rounds a second time and lo may differ from RN(x - hi) by one subnormal ulp
+// (below 1.5e-45 in absolute value). Zero is split directly. Magnitudes below 2^-126 (under FP32's normal range) become
 // a signed zero: the absolute change is below 1.2e-38. At or above 2^125 (huge, non-finite) it
 // falls back to the FP64 instructions.
 __device__ __forceinline__ void split_double_int(double x, float& hi, float& lo) {
@@ -192,7 +193,7 @@ __device__ __forceinline__ double widen_float_int(float f) {
 // exact power of two). Selects, not branches, on the gap and the signs. Otherwise (zero hi,
 // subnormal, non-finite, lo far smaller, a power-of-two hi with lo of the other sign) the FP64
 // add.
-__device__ __forceinline__ double join_df_int(float hi, float lo) {
+__device__ __forceinline__ double join_df_general(float hi, float lo) {
     const uint32_t uh = __float_as_uint(hi), ul = __float_as_uint(lo);
     if ((ul << 1) == 0u) return widen_float_int(hi);
     const uint32_t eh = (uh >> 23) & 0xFFu, el = (ul >> 23) & 0xFFu;
@@ -214,6 +215,25 @@ __device__ __forceinline__ double join_df_int(float hi, float lo) {
     const uint32_t w_hi = (uh & 0x80000000u) | ((eh + 896u) << 20) | ((uh & 0x7FFFFFu) >> 3);
     const uint32_t w_lo = uh << 29;
     return __longlong_as_double(__double_as_longlong(__hiloint2double(int(w_hi), int(w_lo))) + dm);
+}
+
+// The same value with fewer instructions for the common case. With u the last place of a double
+// in hi's binade (2^(E - 52), E hi's exponent), y = lo / u with hi's sign taken out is exact in
+// FP32 (a power-of-two scaling; |y| <= 2^28 for |lo| <= ulp(hi)/2), the exact sum is
+// hi + y u = (S + y) u with S hi's significand shifted to 53 bits, an even integer, and its
+// rounding to the double grid of hi's binade is S + RN_int(y) (ties to even on the integer:
+// S is even). The sum stays in hi's binade (|y| <= 2^28 cannot reach the next power of two up),
+// except below a power-of-two hi with y < 0, where the grid below is finer: that case, and zero,
+// subnormal, non-finite or tiny (|hi| < 2^-74, where 2^(52 - E) leaves FP32's range) hi, take the
+// general join above.
+__device__ __forceinline__ double join_df_int(float hi, float lo) {
+    const uint32_t uh = __float_as_uint(hi);
+    const uint32_t eb = (uh >> 23) & 0xFFu, mant = uh & 0x7FFFFFu, sign = uh & 0x80000000u;
+    const float y = __fmul_rn(__uint_as_float(__float_as_uint(lo) ^ sign), __uint_as_float((306u - eb) << 23));
+    if (eb < 53u || eb == 255u || (mant == 0u && y < 0.f)) return join_df_general(hi, lo);
+    const uint32_t w_hi = sign | ((eb + 896u) << 20) | (mant >> 3);
+    const long long w = (static_cast<long long>(w_hi) << 32) | static_cast<long long>(mant << 29);
+    return __longlong_as_double(w + static_cast<long long>(__float2int_rn(y)));
 }
 
 }  // namespace qs

@@ -192,13 +192,18 @@ __device__ __forceinline__ int quarter_of(const double2& k) { return k.x > 0.5 ?
 __device__ __forceinline__ int quarter_of(const float4& k) { return k.x > 0.5f ? 0 : k.z > 0.5f ? 1 : k.x < -0.5f ? 2 : 3; }
 
 // kIeeeOut (double-float only): the products are written as IEEE complex128, RN(hi + lo) per
-// component (the join of the layout-change pass), into the same 16 bytes
-// one wave of CTAs (three of 512 threads per SM) that each stage the tables once; two loads in
-// flight per thread
+// component (the join of the layout-change pass), into the same 16 bytes.
+// Chunks of 2^11 amplitudes, four per thread (four loads in flight): the table indices are
+// gathers of the bits of x at the tables' qubits, and a gather is an OR over disjoint bit sets,
+// so r(x) = r(chunk base) | r(x mod 2^11): the low part is fixed per thread and computed once,
+// the high part once per chunk. One wave of CTAs (two of 512 threads per SM) that each stage
+// the tables once.
 constexpr int kDiagThreads = 512;
-constexpr int kDiagUnroll = 2;
+constexpr int kDiagPer = 4;
+constexpr int kDiagChunkBits = 11;  // kDiagThreads x kDiagPer amplitudes per chunk
+static_assert(kDiagThreads * kDiagPer == 1 << kDiagChunkBits, "chunk size");
 template <typename P, bool kIeeeOut>
-__global__ void __launch_bounds__(kDiagThreads, 3) k_diag_table(typename P::C* __restrict__ psi,
+__global__ void __launch_bounds__(kDiagThreads, 2) k_diag_table(typename P::C* __restrict__ psi,
                                                          const typename P::K* __restrict__ table,
                                                          const __grid_constant__ DiagTableParams<P> Pm) {
     using C = typename P::C;
@@ -208,18 +213,28 @@ __global__ void __launch_bounds__(kDiagThreads, 3) k_diag_table(typename P::C* _
     const int entries = (1 << Pm.m) + (Pm.m2 > 0 ? 1 << Pm.m2 : 0);
     for (int i = threadIdx.x; i < entries; i += blockDim.x) t[i] = table[i];
     __syncthreads();
-    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-    for (uint64_t x0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; x0 < Pm.N; x0 += kDiagUnroll * stride) {
-        C v[kDiagUnroll];
+    uint32_t rl[kDiagPer], rl2[kDiagPer];
 #pragma unroll
-        for (int u = 0; u < kDiagUnroll; u++)
-            if (x0 + u * stride < Pm.N) v[u] = __ldcg(psi + x0 + u * stride);
+    for (int u = 0; u < kDiagPer; u++) {
+        const uint64_t j = threadIdx.x + uint64_t(u) * kDiagThreads;
+        rl[u] = gather_runs(j, Pm.run, Pm.nrun);
+        rl2[u] = gather_runs(j, Pm.run2, Pm.nrun2);
+    }
+    const uint64_t n_chunks = (Pm.N + (1ull << kDiagChunkBits) - 1) >> kDiagChunkBits;
+    for (uint64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+        const uint64_t base = ch << kDiagChunkBits;
+        const uint32_t rh = gather_runs(base, Pm.run, Pm.nrun), rh2 = gather_runs(base, Pm.run2, Pm.nrun2);
+        C v[kDiagPer];
 #pragma unroll
-        for (int u = 0; u < kDiagUnroll; u++) {
-            const uint64_t x = x0 + u * stride;
+        for (int u = 0; u < kDiagPer; u++) {
+            const uint64_t x = base + threadIdx.x + uint64_t(u) * kDiagThreads;
+            if (x < Pm.N) v[u] = __ldcg(psi + x);
+        }
+#pragma unroll
+        for (int u = 0; u < kDiagPer; u++) {
+            const uint64_t x = base + threadIdx.x + uint64_t(u) * kDiagThreads;
             if (x >= Pm.N) continue;
-            const uint32_t r = gather_runs(x, Pm.run, Pm.nrun);
-            const uint32_t r2 = gather_runs(x, Pm.run2, Pm.nrun2);
+            const uint32_t r = rh | rl[u], r2 = rh2 | rl2[u];
             C w = v[u];
             if (Pm.second == 2) {  // exact quarter turn, then the first table's entry
                 if constexpr (std::is_same<P, DFArith>::value)
@@ -309,7 +324,7 @@ void launch_diag_table_t(const std::vector<int>& u, const std::vector<cplx>& tab
     } else {
         QS_REQUIRE(!ieee_out, "IEEE output is a double-float layout change");
     }
-    const uint64_t want = (Pm.N + kDiagThreads - 1) / kDiagThreads;
+    const uint64_t want = (Pm.N + (1ull << kDiagChunkBits) - 1) >> kDiagChunkBits;
     const uint64_t wave = uint64_t(sm_count()) * uint64_t(std::max(1, resident[ieee_out ? 1 : 0]));
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min(want, wave)));
     kern<<<grid, kDiagThreads, bytes, st>>>(reinterpret_cast<typename P::C*>(psi), static_cast<const K*>(stage), Pm);
