@@ -283,7 +283,9 @@ qs_status qs_autotune_fusion(const qs_circuit* c, qs_dtype dt, int* best_k, doub
 qs_status qs_expectation(const qs_state* s, const qs_pauli_obs* obs, double out[2]);
 /* Host only (no GPU needed): how qs_expectation reads an n-qubit state for obs. *n_passes = the
  * tiled reads; tile_masks (optional, cap entries) receives each read's tile qubits as a bit mask;
- * *n_single (optional) = the reads of single groups that fit no tile. */
+ * *n_single (optional) = the reads of single groups that fit no tile. A diagonal observable (every
+ * term a Z string) whose Z qubits number at most 12 takes one streaming read instead, reported as
+ * one pass whose mask is those qubits. */
 qs_status qs_expectation_plan(int n, const qs_pauli_obs* obs, int* n_passes, uint64_t* tile_masks, int cap,
                               int* n_single);
 /* Allocation-free expectation, for callers that cannot allocate device memory: a process whose

@@ -944,7 +944,7 @@ qs_status qs_expectation_plan(int n, const qs_pauli_obs* obs, int* n_passes, uin
     QS_REQUIRE(cap >= 0 && (cap == 0 || tile_masks != nullptr), "null tile mask array");
     const std::vector<PauliGroup> groups = group_observable(obs, n);
     const ExpectPlan plan = plan_expectation(groups, n);
-    *n_passes = int(plan.passes.size());
+    *n_passes = int(plan.passes.size()) + (plan.diag ? 1 : 0);
     for (size_t p = 0; p < plan.tmask.size() && p < size_t(cap); p++) tile_masks[p] = plan.tmask[p];
     if (n_single) *n_single = int(plan.heavy.size());
     API_END

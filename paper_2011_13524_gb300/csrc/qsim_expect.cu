@@ -380,6 +380,87 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_expect_tiled(const C* __res
     }
 }
 
+// ---------------------------------------------------------------- diagonal observables
+// E = sum_x c(r(x)) |psi_x|^2 in one streaming read. Each CTA forms the table c(r) for every
+// index r of the union of the Z qubits in FP64 (the sum over terms of alpha_t with the sign of
+// r's bits at term t's qubits) and keeps it as double-float in shared memory. Chunks of 2^11
+// amplitudes, four per thread: r(x) = r(chunk base) | r(x mod 2^11) (a gather is an OR over
+// disjoint bits), the low part fixed per thread. |psi_x|^2 is formed as a double-float (exact
+// hi x hi products), multiplied by the entry and added to a double-float accumulator per thread;
+// per-block FP64 sums.
+constexpr int kDiagObsThreads = 512;
+constexpr int kDiagObsPer = 4;
+constexpr int kDiagObsChunkBits = 11;
+static_assert(kDiagObsThreads * kDiagObsPer == 1 << kDiagObsChunkBits, "chunk size");
+
+__device__ __forceinline__ uint32_t gather_obs(uint64_t x, const uint32_t* run, int nrun) {
+    uint32_t r = 0;
+    for (int k = 0; k < nrun; k++) {
+        const uint32_t c = run[k];
+        r |= (uint32_t(x >> (c & 0xFFu)) & ((1u << ((c >> 8) & 0xFFu)) - 1u)) << (c >> 16);
+    }
+    return r;
+}
+
+// |v|^2 as a double-float (h, l) for each storage type
+__device__ __forceinline__ void norm2_df(double2 v, float& h, float& l) {
+    float rh, rl, ih, il;
+    split_tile(v.x, rh, rl);
+    split_tile(v.y, ih, il);
+    df_dot2<true>(rh, rl, rh, rl, ih, il, ih, il, h, l);
+}
+__device__ __forceinline__ void norm2_df(float4 v, float& h, float& l) {
+    df_dot2<true>(v.x, v.y, v.x, v.y, v.z, v.w, v.z, v.w, h, l);
+}
+__device__ __forceinline__ void norm2_df(float2 v, float& h, float& l) {
+    df_dot2<false>(v.x, 0.f, v.x, 0.f, v.y, 0.f, v.y, 0.f, h, l);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kDiagObsThreads, 2) k_expect_diag(const C* __restrict__ psi,
+                                                                    const __grid_constant__ DiagObsParams P,
+                                                                    double* __restrict__ part) {
+    __shared__ float2 ctab[1 << kDiagObsBits];
+    __shared__ double sh[kDiagObsThreads / 32];
+    for (int r = threadIdx.x; r < (1 << P.m); r += kDiagObsThreads) {
+        double c = 0.0;
+        for (int t = 0; t < P.nterms; t++) c += (__popc(uint32_t(r) & P.z[t]) & 1) ? -P.alpha[t] : P.alpha[t];
+        float h, l;
+        split_double_int(c, h, l);
+        ctab[r] = make_float2(h, l);
+    }
+    __syncthreads();
+    uint32_t rl[kDiagObsPer];
+#pragma unroll
+    for (int u = 0; u < kDiagObsPer; u++) rl[u] = gather_obs(threadIdx.x + uint64_t(u) * kDiagObsThreads, P.run, P.nrun);
+    float ah = 0.f, al = 0.f;
+    const uint64_t n_chunks = (P.N + (1ull << kDiagObsChunkBits) - 1) >> kDiagObsChunkBits;
+    for (uint64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+        const uint64_t base = ch << kDiagObsChunkBits;
+        const uint32_t rh = gather_obs(base, P.run, P.nrun);
+        C v[kDiagObsPer];
+#pragma unroll
+        for (int u = 0; u < kDiagObsPer; u++) {
+            const uint64_t x = base + threadIdx.x + uint64_t(u) * kDiagObsThreads;
+            if (x < P.N) v[u] = __ldcs(psi + x);
+        }
+#pragma unroll
+        for (int u = 0; u < kDiagObsPer; u++) {
+            const uint64_t x = base + threadIdx.x + uint64_t(u) * kDiagObsThreads;
+            if (x >= P.N) continue;
+            float h, l;
+            norm2_df(v[u], h, l);
+            const float2 c = ctab[rh | rl[u]];
+            acc_prod(ah, al, c.x, c.y, h, l);
+        }
+    }
+    const double tot = block_sum<kDiagObsThreads>(widen_float_int(ah) + widen_float_int(al), sh);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = tot;
+        part[2 * blockIdx.x + 1] = 0.0;
+    }
+}
+
 // ---------------------------------------------------------------- transition amplitude
 // <bra| sum_t alpha_t P_t |ket> with P_t |x> = i^{nY} (-1)^{popc(x & z)} |x ^ f>: per flip group,
 // sum_y conj(bra_y) ket_{y^f} alpha (-i)^{nY} (-1)^{popc(y & z)} over every y (no pairing), on
@@ -786,8 +867,45 @@ void build_trans_group(const Chunk& ch, const int* tpos, int b, uint64_t T, Tile
 
 }  // namespace
 
+// a diagonal observable whose Z qubits number at most kDiagObsBits (and whose table costs at
+// most 2^17 term evaluations per CTA): the streaming pass's parameters, else false
+bool plan_diag_obs(const std::vector<PauliGroup>& groups, int n, DiagObsParams& P) {
+    if (groups.size() != 1 || groups[0].xmask != 0) return false;
+    const PauliGroup& G = groups[0];
+    uint64_t u = 0;
+    for (uint64_t z : G.zmask) u |= z;
+    const int m = __builtin_popcountll(u);
+    const int nt = int(G.coef.size());
+    if (m > kDiagObsBits || nt > kDiagObsMaxTerms || (uint64_t(nt) << m) > (1ull << 17)) return false;
+    int pos[64], np_ = 0;
+    for (int q = 0; q < n; q++)
+        if ((u >> q) & 1) pos[np_++] = q;
+    P.N = 1ull << n;
+    P.m = m;
+    P.nterms = nt;
+    P.nrun = 0;
+    for (int j = 0; j < np_;) {  // runs of consecutive qubits
+        int k = j + 1;
+        while (k < np_ && pos[k] == pos[k - 1] + 1) k++;
+        P.run[P.nrun++] = uint32_t(pos[j]) | (uint32_t(k - j) << 8) | (uint32_t(j) << 16);
+        j = k;
+    }
+    for (int t = 0; t < nt; t++) {
+        P.z[t] = compress_bits(G.zmask[t], pos, np_);
+        P.alpha[t] = G.coef[t];
+    }
+    return true;
+}
+
 ExpectPlan plan_expectation(const std::vector<PauliGroup>& groups, int n) {
     ExpectPlan plan;
+    if (plan_diag_obs(groups, n, plan.dp)) {
+        plan.diag = true;
+        uint64_t u = 0;
+        for (uint64_t z : groups[0].zmask) u |= z;
+        plan.tmask.push_back(u);
+        return plan;
+    }
     pack_tiles(groups, n, kTileBits, plan, build_group);
     // groups that use only the plain sum of Re A first, so that the kernel takes them in pairs
     for (TileParams& P : plan.passes)
@@ -799,6 +917,36 @@ ExpectPlan plan_transition(const std::vector<PauliGroup>& groups, int n) {
     ExpectPlan plan;
     pack_tiles(groups, n, kTransBits, plan, build_trans_group);
     return plan;
+}
+
+unsigned expect_diag_grid(int n, Arith ar) {
+    static PerDevice setup;
+    static int resident_of[kMaxDevices][3];
+    setup.once([](int dev) {
+        int* r = resident_of[dev];
+        QS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r[0], k_expect_diag<float2>, kDiagObsThreads, 0));
+        QS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r[1], k_expect_diag<double2>, kDiagObsThreads, 0));
+        QS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r[2], k_expect_diag<float4>, kDiagObsThreads, 0));
+    });
+    const int res = std::max(1, resident_of[current_device()][ar == Arith::F32 ? 0 : ar == Arith::F64 ? 1 : 2]);
+    const uint64_t chunks = ((1ull << n) + (1ull << kDiagObsChunkBits) - 1) >> kDiagObsChunkBits;
+    return unsigned(std::max<uint64_t>(1, std::min<uint64_t>(chunks, uint64_t(res) * uint64_t(sm_count()))));
+}
+
+void launch_expect_diag(const DiagObsParams& P, const void* psi, Arith ar, double* part, unsigned grid,
+                        cudaStream_t st) {
+    switch (ar) {
+        case Arith::F32:
+            k_expect_diag<float2><<<grid, kDiagObsThreads, 0, st>>>(static_cast<const float2*>(psi), P, part);
+            break;
+        case Arith::F64:
+            k_expect_diag<double2><<<grid, kDiagObsThreads, 0, st>>>(static_cast<const double2*>(psi), P, part);
+            break;
+        default:
+            k_expect_diag<float4><<<grid, kDiagObsThreads, 0, st>>>(static_cast<const float4*>(psi), P, part);
+            break;
+    }
+    QS_TRY_CUDA(cudaGetLastError());
 }
 
 unsigned expect_pass_grid(const TileParams& P, Arith ar) {

@@ -285,11 +285,29 @@ struct HeavyChunk {
     const PauliGroup* g;
     size_t t0, t1;
 };
+// Diagonal observables (every term a Z string) whose Z qubits number at most kDiagObsBits: one
+// streaming read, E = sum_x c(r(x)) |psi_x|^2 with c(r) = sum_t alpha_t (-1)^{popc(r & z_t)},
+// r(x) the bits of x at the union of the terms' Z qubits (Sec. 4.5 with every flip mask zero).
+constexpr int kDiagObsBits = 12;
+constexpr int kDiagObsMaxTerms = 128;
+struct DiagObsParams {
+    uint64_t N = 0;
+    int32_t m = 0, nterms = 0, nrun = 0;
+    uint32_t run[kDiagObsBits] = {};  // runs of consecutive union qubits: shift | width << 8 | index bit << 16
+    uint32_t z[kDiagObsMaxTerms] = {};  // term t's Z qubits as bits of the table index
+    double alpha[kDiagObsMaxTerms] = {};
+};
 struct ExpectPlan {
     std::vector<TileParams> passes;
     std::vector<uint64_t> tmask;     // qubits of each pass's tile
     std::vector<HeavyChunk> heavy;   // terms [t0, t1) of groups that fit no tile
+    bool diag = false;               // a diagonal observable read in one streaming pass (dp)
+    DiagObsParams dp;
 };
+unsigned expect_diag_grid(int n, Arith ar);
+// part[2 j], part[2 j + 1] = block j's partial (real, 0) for j < grid
+void launch_expect_diag(const DiagObsParams& P, const void* psi, Arith ar, double* part, unsigned grid,
+                        cudaStream_t st);
 ExpectPlan plan_expectation(const std::vector<PauliGroup>& groups, int n);
 unsigned expect_pass_grid(const TileParams& P, Arith ar);
 // Transition amplitude <bra|O|ket>: tiles of 2^11 slots of both states (qubits 0..2 plus 8

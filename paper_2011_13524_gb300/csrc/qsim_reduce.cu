@@ -416,11 +416,12 @@ void reduce_inner(const qs_state* a, const qs_state* b, double out[2]) {
 // Launches of one expectation: the tile passes, then one launch per heavy chunk. With a cap on
 // the block partials the grids shrink proportionally (the kernels loop over their work).
 struct ExpectLaunches {
-    std::vector<unsigned> pass_grid, heavy_grid;
+    std::vector<unsigned> pass_grid, heavy_grid;  // a diagonal observable: its one streaming pass in pass_grid
     size_t slots = 0;
 };
 ExpectLaunches expectation_launches(const ExpectPlan& plan, int n, Arith ar, size_t cap) {
     ExpectLaunches L;
+    if (plan.diag) L.pass_grid.push_back(expect_diag_grid(n, ar));
     for (const TileParams& P : plan.passes) L.pass_grid.push_back(expect_pass_grid(P, ar));
     for (const HeavyChunk& h : plan.heavy) L.heavy_grid.push_back(red_grid((1ull << n) >> (h.g->xmask ? 1 : 0)));
     size_t tot = 0;
@@ -441,6 +442,10 @@ ExpectLaunches expectation_launches(const ExpectPlan& plan, int n, Arith ar, siz
 void launch_expectation(const ExpectPlan& plan, const ExpectLaunches& L, const void* psi, int n, Arith ar,
                         cudaStream_t st, double* part) {
     size_t slots = 0;
+    if (plan.diag) {
+        launch_expect_diag(plan.dp, psi, ar, part, L.pass_grid[0], st);
+        return;
+    }
     for (size_t p = 0; p < plan.passes.size(); p++) {
         launch_expect_pass(plan.passes[p], psi, ar, part + 2 * slots, L.pass_grid[p], st);
         slots += L.pass_grid[p];
