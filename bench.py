@@ -39,10 +39,10 @@ HBM_PEAK_FALLBACK = 6800.0
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of the kernel as it is
 # built now, at a smaller state than the bench's and scaled to n = 30 by the amplitudes a launch
 # updates (the traffic of these kernels grows in proportion to the state): (kernel, n) -> bytes.
-# k_dense_oz5 at n = 27: the mean of two launches, (2163700736 + 2085665536) and
-# (2203815936 + 2082356736) bytes read + written.
+# k_dense_oz5 at n = 27: the mean of two launches, (2163699712 + 2085241088) and
+# (2203977728 + 2082443776) bytes read + written.
 NCU_TRAFFIC = {("dense_df", 27): 4232672512, ("dense_df", 30): 4232672512 * 8,
-               ("dense_oz5", 27): 4267769472, ("dense_oz5", 30): 4267769472 * 8}
+               ("dense_oz5", 27): 4267681152, ("dense_oz5", 30): 4267681152 * 8}
 
 
 def parse():
