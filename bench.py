@@ -423,6 +423,8 @@ def measure_extras(args, qs, torch, circuit):
         ms = timed(lambda: (st.set_basis(0), st.apply_plan(pl)))
         out[label + "_gates_per_s"] = G / (ms / 1e3)
         out[label + "_fusion_k"] = kk
+        # rows per thread of the shared-memory dense kernel the autotuner timed and kept, per width
+        out[label + "_tile_rows"] = {m: qs.dense_tile_rows(qs.QS_C128, m)[0] for m in (4, 5, 6)}
     qs.set_tensor_cores(old_tc)
     qs.set_c128_math(old_math)
     del st
@@ -438,6 +440,9 @@ def measure_extras(args, qs, torch, circuit):
     plan6 = qs.FusedCircuit(circuit, 6)
     for tc in (qs.QS_TENSOR_C64X, 0):
         qs.set_tensor_cores(tc)
+        if not tc:  # the CUDA-core tile shapes timed by the autotuner
+            qs.autotune_fusion(circuit, qs.QS_C64)
+            out["c64_cuda_cores_tile_rows"] = {m: qs.dense_tile_rows(qs.QS_C64, m)[0] for m in (5, 6)}
         ms6 = timed(lambda: (st.set_basis(0), st.apply_plan(plan6)), reps=2)
         out["c64_k6_%s_gates_per_s" % ("tensor" if tc else "cuda_cores")] = G / (ms6 / 1e3)
     qs.set_tensor_cores(old_tc)

@@ -272,6 +272,15 @@ qs_status qs_apply_fused_circuit_timed(qs_state* s, const qs_fused_circuit* f, f
  * min(n, 24) qubits and scaled by 2^n), and returns the fastest width in *best_k. pred_ms
  * (optional, 7 entries): index 0 = gate by gate, 1..6 = fused widths. */
 qs_status qs_autotune_fusion(const qs_circuit* c, qs_dtype dt, int* best_k, double* pred_ms);
+/* Tile shape of the shared-memory dense kernel (QS_KERNEL_DENSE_SMEM: 4..6 targets on the CUDA
+ * cores): output rows per thread, 4, 8 or 16 (the tile holds 256 rows / 2^m groups per row of
+ * threads). The autotuner times the three shapes on this GPU the first time it costs that kernel
+ * for an arithmetic (complex64; complex128 FP64 or double-float, the current setting) and width
+ * m, and every later launch uses the fastest; until then 8. *rows = the shape in use for dt and
+ * m on the current device; *tuned (optional) = 1 when it was timed or set. The shapes give the
+ * same bits (every output is the same sum in the same order). m outside 4..6 ->
+ * QS_ERR_INVALID_ARG. */
+qs_status qs_dense_tile_rows(qs_dtype dt, int m, int* rows, int* tuned);
 
 /* ---------------------------------------------------------------- observables (Sec. 4.5) */
 /* out[0] = sum_k coef[k] <psi|P_k|psi>, out[1] = 0 (the terms are Hermitian and the coefficients
@@ -365,6 +374,10 @@ qs_status qs_batch_info(const qs_batch* b, int* total_params, int* total_passes,
 qs_status qs_batch_destroy(qs_batch* b);
 
 /* ---------------------------------------------------------------- test hooks */
+/* Sets the shared-memory dense kernel's rows per thread (4, 8 or 16; 0 = back to untuned) for dt
+ * (and, for complex128, the current arithmetic setting) and m in 4..6 on the current device, as
+ * if the autotuner had chosen it. Other values -> QS_ERR_INVALID_ARG. */
+qs_status qs_debug_set_tile_rows(qs_dtype dt, int m, int rows);
 /* Every device-side wait of the library is bounded: when one gives up, its kernel records an
  * error, stops its work, waits (bounded) for its own asynchronous operations and exits; the next
  * synchronising call (qs_synchronize, or the call itself where it synchronises) reports

@@ -114,6 +114,9 @@ _SIGNATURES = {
     "qs_plan_fusion": ([ctypes.POINTER(QsCircuit), ctypes.c_int, ctypes.POINTER(_VOIDP)], ctypes.c_int),
     "qs_clear_plan_cache": ([], ctypes.c_int),
     "qs_debug_set_wait_limit": ([ctypes.c_longlong], ctypes.c_int),
+    "qs_debug_set_tile_rows": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "qs_dense_tile_rows": ([ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+                           ctypes.c_int),
     "qs_debug_set_fault": ([ctypes.c_int], ctypes.c_int),
     "qs_debug_fail_alloc": ([ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     "qs_fused_info": ([_VOIDP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -510,6 +513,14 @@ class FusedCircuit:
 def clear_plan_cache() -> None:
     """Forget the cached fusion partitions (the next run of any circuit plans it afresh)."""
     check(lib().qs_clear_plan_cache())
+
+
+def dense_tile_rows(dtype: int, m: int):
+    """(rows per thread of the shared-memory dense kernel for dtype and m targets under the current
+    arithmetic setting, whether the autotuner timed it or a test set it)."""
+    r, t = ctypes.c_int(0), ctypes.c_int(0)
+    check(lib().qs_dense_tile_rows(int(dtype), int(m), ctypes.byref(r), ctypes.byref(t)))
+    return r.value, bool(t.value)
 
 
 def autotune_fusion(circuit, dtype: int = QS_C128):

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <exception>
+#include <thread>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -383,16 +385,38 @@ double measure_cost(int dev, qs_dtype dt, const Op& probe_op, int np_) {
     cudaEvent_t e0, e1;
     QS_TRY_CUDA(cudaEventCreate(&e0));
     QS_TRY_CUDA(cudaEventCreate(&e1));
-    float best = 1e30f;
-    for (int r = 0; r < 4; r++) {
-        QS_TRY_CUDA(cudaEventRecord(e0, s->stream));
-        launch_op_arith(op, s->data, s->n, ar, s->stream, stage_of(s));
-        QS_TRY_CUDA(cudaEventRecord(e1, s->stream));
-        QS_TRY_CUDA(cudaEventSynchronize(e1));
-        float ms = 0;
-        QS_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (r > 0) best = std::min(best, ms);
+    auto time_op = [&]() {  // best of three launches after one warm-up
+        float best = 1e30f;
+        for (int r = 0; r < 4; r++) {
+            QS_TRY_CUDA(cudaEventRecord(e0, s->stream));
+            launch_op_arith(op, s->data, s->n, ar, s->stream, stage_of(s));
+            QS_TRY_CUDA(cudaEventRecord(e1, s->stream));
+            QS_TRY_CUDA(cudaEventSynchronize(e1));
+            float ms = 0;
+            QS_TRY_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (r > 0) best = std::min(best, ms);
+        }
+        return best;
+    };
+    // the shared-memory dense kernel's tile shape (rows per thread) for this arithmetic and
+    // width, timed once per device before its cost is measured
+    int kernel = 0;
+    op_cost(op, np_, dt, &kernel, nullptr, nullptr);
+    const int m = int(op.targets.size());
+    if (kernel == QS_KERNEL_DENSE_SMEM && !dense_tile_rows_tuned(ar, m)) {
+        float best_ms = 1e30f;
+        int best_rows = 8;
+        for (int rows : {4, 8, 16}) {
+            set_dense_tile_rows(ar, m, rows);
+            const float t = time_op();
+            if (t < best_ms) {
+                best_ms = t;
+                best_rows = rows;
+            }
+        }
+        set_dense_tile_rows(ar, m, best_rows);
     }
+    const float best = time_op();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (wm.dbuf) dev_free(wm.dbuf);
@@ -490,11 +514,29 @@ double predict_unfused(const qs_circuit* c, qs_dtype dt) {
 }
 
 int autotune(const qs_circuit* c, qs_dtype dt, double* pred_ms) {
+    // the plans of every width are made on host threads at once (planning is CPU work, independent
+    // per width); the predictions, which may time kernels on the GPU, follow one by one
+    std::vector<FusionPlan> plans(QS_MAX_TARGETS + 1);
+    std::vector<std::exception_ptr> errs(QS_MAX_TARGETS + 1);
+    {
+        std::vector<std::thread> pool;
+        for (int k = 1; k <= QS_MAX_TARGETS; k++)
+            pool.emplace_back([&, k]() {
+                try {
+                    plans[k] = plan_fusion(c, k);
+                } catch (...) {
+                    errs[k] = std::current_exception();
+                }
+            });
+        for (auto& th : pool) th.join();
+    }
+    for (auto& e : errs)
+        if (e) std::rethrow_exception(e);
     double best = predict_unfused(c, dt);
     if (pred_ms) pred_ms[0] = 1e3 * best;
     int best_k = 0;
     for (int k = 1; k <= QS_MAX_TARGETS; k++) {
-        const double t = predict_plan(plan_fusion(c, k), dt);
+        const double t = predict_plan(plans[k], dt);
         if (pred_ms) pred_ms[k] = 1e3 * t;
         if (t < best) {
             best = t;
@@ -915,6 +957,25 @@ qs_status qs_apply_fused_circuit_timed(qs_state* s, const qs_fused_circuit* f, f
     check_state(s);
     QS_REQUIRE(f != nullptr && block_ms != nullptr, "null plan or output");
     apply_plan_impl(s, f->plan, block_ms);
+    API_END
+}
+
+qs_status qs_dense_tile_rows(qs_dtype dt, int m, int* rows, int* tuned) {
+    API_BEGIN
+    QS_REQUIRE(dt == QS_C64 || dt == QS_C128, "dtype must be QS_C64 or QS_C128");
+    QS_REQUIRE(m >= 4 && m <= 6, "tile rows exist for 4..6 targets");
+    QS_REQUIRE(rows != nullptr, "null output");
+    const Arith ar = dt == QS_C64 ? Arith::F32 : (c128_math() == QS_MATH_DF ? Arith::DF : Arith::F64);
+    *rows = dense_tile_rows(ar, m);
+    if (tuned) *tuned = dense_tile_rows_tuned(ar, m) ? 1 : 0;
+    API_END
+}
+
+qs_status qs_debug_set_tile_rows(qs_dtype dt, int m, int rows) {
+    API_BEGIN
+    QS_REQUIRE(dt == QS_C64 || dt == QS_C128, "dtype must be QS_C64 or QS_C128");
+    const Arith ar = dt == QS_C64 ? Arith::F32 : (c128_math() == QS_MATH_DF ? Arith::DF : Arith::F64);
+    set_dense_tile_rows(ar, m, rows);
     API_END
 }
 

@@ -435,14 +435,36 @@ std::vector<OpenBlock> partition(const qs_circuit* c, const std::vector<uint64_t
                 return it->second;
             }
     }
-    std::vector<OpenBlock> a = partition_greedy(c, masks, k);
-    std::vector<OpenBlock> b = partition_frontier(c, masks, tags, k);
-    std::vector<OpenBlock> best = b.size() < a.size() ? std::move(b) : std::move(a);
-    // wider lookahead: depth 2 always, depth 3 within a budget of visited gates (about 0.1 s)
-    for (int depth = 2; depth <= 3; depth++) {
-        std::vector<OpenBlock> d = partition_frontier(c, masks, tags, k, depth, depth == 2 ? -1 : 15000000);
-        if (!d.empty() && d.size() < best.size()) best = std::move(d);
+    // four partitions, independent of each other, on host threads: greedy, frontier growth, and
+    // frontier growth with a wider lookahead (depth 2 always, depth 3 within a budget of visited
+    // gates, about 0.1 s); the one with the fewest blocks is kept (ties: the earlier one)
+    std::vector<OpenBlock> cand[4];
+    std::exception_ptr err[4];
+    auto run = [&](int i) {
+        try {
+            if (i == 0)
+                cand[0] = partition_greedy(c, masks, k);
+            else if (i == 1)
+                cand[1] = partition_frontier(c, masks, tags, k);
+            else
+                cand[i] = partition_frontier(c, masks, tags, k, i, i == 2 ? -1 : 15000000);
+        } catch (...) {
+            err[i] = std::current_exception();
+        }
+    };
+    if (c->n_gates >= 64 && std::thread::hardware_concurrency() > 1) {
+        std::vector<std::thread> pool;
+        for (int i = 1; i < 4; i++) pool.emplace_back(run, i);
+        run(0);
+        for (auto& th : pool) th.join();
+    } else {
+        for (int i = 0; i < 4; i++) run(i);
     }
+    for (auto& e : err)
+        if (e) std::rethrow_exception(e);
+    std::vector<OpenBlock> best = cand[1].size() < cand[0].size() ? std::move(cand[1]) : std::move(cand[0]);
+    for (int i = 2; i < 4; i++)
+        if (!cand[i].empty() && cand[i].size() < best.size()) best = std::move(cand[i]);
     std::lock_guard<std::mutex> lk(g_part_mu);
     g_part_cache.emplace_front(std::move(key), best);
     if (g_part_cache.size() > kPartCacheSize) g_part_cache.pop_back();

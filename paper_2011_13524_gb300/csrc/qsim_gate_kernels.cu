@@ -63,21 +63,24 @@ __global__ void __launch_bounds__(kThreads) k_dense_reg(typename P::C* __restric
 
 // ------------------------------------------------------------------ dense, shared-memory tile
 // For 4..6 targets: a CTA stages G groups of 2^M amplitudes in shared memory (coalesced
-// loads: consecutive threads read consecutive x0), then thread (rc, g) forms 8 output rows
-// of group g from the staged vector and the gate matrix held in shared memory.
+// loads: consecutive threads read consecutive x0), then thread (rc, g) forms R output rows
+// of group g from the staged vector and the gate matrix held in shared memory. The tile shape
+// (R rows per thread, so G = 256 R / 2^M groups per tile) is a template parameter, 4, 8 or 16;
+// the autotuner times the three on this GPU per arithmetic and width and keeps the fastest
+// (dense_tile_rows). Every output is the same sum in the same order whatever R is.
 struct DenseSmemParams {
     IndexPlan ip;
     uint64_t offs[64];
 };
 
-template <typename P, int M>
+template <typename P, int M, int R>
 __global__ void __launch_bounds__(kThreads) k_dense_smem(typename P::C* __restrict__ psi,
                                                          const typename P::K* __restrict__ Kg,
                                                          const __grid_constant__ DenseSmemParams Pm) {
     using C = typename P::C;
     using K = typename P::K;
     constexpr int D = 1 << M;
-    constexpr int RC = D / 8;          // row chunks of 8
+    constexpr int RC = D / R;          // row chunks of R
     constexpr int G = kThreads / RC;   // groups per tile
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K* Ks = reinterpret_cast<K*>(smem_raw);
@@ -102,17 +105,17 @@ __global__ void __launch_bounds__(kThreads) k_dense_smem(typename P::C* __restri
         __syncthreads();
         const uint64_t x0 = xs[g];
         if (x0 != ~0ull) {
-            typename P::Acc acc[8];
+            typename P::Acc acc[R];
 #pragma unroll
-            for (int r = 0; r < 8; r++) acc[r] = P::zero();
+            for (int r = 0; r < R; r++) acc[r] = P::zero();
 #pragma unroll 2
             for (int w = 0; w < D; w++) {
                 const C v = tile[w * G + g];
 #pragma unroll
-                for (int r = 0; r < 8; r++) P::mac(acc[r], Ks[(rc * 8 + r) * D + w], v);
+                for (int r = 0; r < R; r++) P::mac(acc[r], Ks[(rc * R + r) * D + w], v);
             }
 #pragma unroll
-            for (int r = 0; r < 8; r++) psi[x0 + Pm.offs[rc * 8 + r]] = P::out(acc[r]);
+            for (int r = 0; r < R; r++) psi[x0 + Pm.offs[rc * R + r]] = P::out(acc[r]);
         }
     }
 }
@@ -510,23 +513,35 @@ void launch_dense_reg(const Op& op, const IndexPlan& ip, void* psi, cudaStream_t
     k_dense_reg<P, M><<<grid_for(ip.n_iter), kThreads, 0, st>>>(reinterpret_cast<typename P::C*>(psi), Pm);
 }
 
-template <typename P, int M>
-void launch_dense_smem(const Op& op, const IndexPlan& ip, void* psi, const void* dK, cudaStream_t st) {
+template <typename P, int M, int R>
+void launch_dense_smem_r(const DenseSmemParams& Pm, void* psi, const void* dK, cudaStream_t st) {
     using C = typename P::C;
     using K = typename P::K;
     constexpr int D = 1 << M;
-    constexpr int G = kThreads / (D / 8);
-    DenseSmemParams Pm;
-    Pm.ip = ip;
-    fill_offs<M>(op, Pm.offs);
+    constexpr int G = kThreads / (D / R);
     const size_t smem = sizeof(K) * D * D + sizeof(C) * D * G + sizeof(uint64_t) * G;
     static PerDevice setup;
     setup.once([smem](int) {
-        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_smem<P, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_smem<P, M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     });
-    const uint64_t n_tiles = (ip.n_iter + G - 1) / G;
+    const uint64_t n_tiles = (Pm.ip.n_iter + G - 1) / G;
     const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, uint64_t(sm_count()) * 4)));
-    k_dense_smem<P, M><<<grid, kThreads, smem, st>>>(reinterpret_cast<C*>(psi), reinterpret_cast<const K*>(dK), Pm);
+    k_dense_smem<P, M, R><<<grid, kThreads, smem, st>>>(reinterpret_cast<C*>(psi), reinterpret_cast<const K*>(dK), Pm);
+}
+
+template <typename P, int M>
+void launch_dense_smem(const Op& op, const IndexPlan& ip, void* psi, const void* dK, cudaStream_t st) {
+    DenseSmemParams Pm;
+    Pm.ip = ip;
+    fill_offs<M>(op, Pm.offs);
+    const Arith ar = std::is_same<P, DFArith>::value ? Arith::DF
+                     : sizeof(typename P::C) == 8  ? Arith::F32
+                                                    : Arith::F64;
+    switch (dense_tile_rows(ar, M)) {
+        case 4: return launch_dense_smem_r<P, M, 4>(Pm, psi, dK, st);
+        case 16: return launch_dense_smem_r<P, M, 16>(Pm, psi, dK, st);
+        default: return launch_dense_smem_r<P, M, 8>(Pm, psi, dK, st);
+    }
 }
 
 template <typename P>

@@ -334,6 +334,24 @@ int current_device() {
     return dev;
 }
 
+namespace {
+// 0: not set (the default, 8 rows, applies)
+std::atomic<int> g_tile_rows[kMaxDevices][3][3];
+}
+int dense_tile_rows(Arith ar, int m) {
+    if (m < 4 || m > 6) return 8;
+    const int r = g_tile_rows[current_device()][int(ar)][m - 4].load();
+    return r ? r : 8;
+}
+void set_dense_tile_rows(Arith ar, int m, int rows) {
+    QS_REQUIRE(m >= 4 && m <= 6, "tile rows are set for 4..6 targets");
+    QS_REQUIRE(rows == 0 || rows == 4 || rows == 8 || rows == 16, "tile rows must be 4, 8 or 16 (0: default)");
+    g_tile_rows[current_device()][int(ar)][m - 4].store(rows);
+}
+bool dense_tile_rows_tuned(Arith ar, int m) {
+    return m >= 4 && m <= 6 && g_tile_rows[current_device()][int(ar)][m - 4].load() != 0;
+}
+
 int device_sms() {
     static std::mutex mu;
     static int sms[kMaxDevices] = {};

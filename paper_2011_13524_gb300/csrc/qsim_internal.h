@@ -179,6 +179,12 @@ void launch_op(const Op& op, void* psi, int n, qs_dtype dt, cudaStream_t st, voi
 // the double-float layout, the layout change done by the op's own kernel where it reads every
 // amplitude once (takes_ieee_in), else by a conversion pass before it
 void launch_op_arith(const Op& op, void* psi, int n, Arith ar, cudaStream_t st, void* stage, bool ieee_in = false);
+// Tile shape of the shared-memory dense kernel (4..6 targets on the CUDA cores): output rows per
+// thread, 4, 8 or 16, per device, arithmetic and width; 8 until the autotuner has timed them
+// (tune_dense_tile_rows) or a test has set one.
+int dense_tile_rows(Arith ar, int m);
+void set_dense_tile_rows(Arith ar, int m, int rows);
+bool dense_tile_rows_tuned(Arith ar, int m);
 bool takes_ieee_in(const Op& op);
 // Consecutive uncontrolled diagonal ops (and phases) together in one pass, their product held
 // as two tables: each op in turn joins the first table if the union of its qubits stays within
