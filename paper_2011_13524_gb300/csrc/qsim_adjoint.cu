@@ -97,16 +97,17 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rot(typename P::C* __restri
     if (threadIdx.x == 0) part[blockIdx.x] = v;
 }
 
-// Two consecutive reverse steps for rotations on distinct qubits a (later in the circuit) and b:
-// each group of four amplitudes (bits a, b) gets the gradient partial of a, the un-apply of
-// R_a, then the gradient partial of b and the un-apply of R_b, all in registers. Partials of a
-// go to part[0 .. grid), those of b to part[grid .. 2 grid).
-template <typename P>
-struct AdjRot2Params {
-    IndexPlan ip;            // bits a and b inserted
-    uint64_t bit[2];         // 1 << a, 1 << b
-    typename P::K U[2][4];   // R_a^+, R_b^+
-    int32_t axis[2];
+// NR consecutive reverse steps (2 to 4) for rotations on distinct qubits q_0 (the latest in the
+// circuit), q_1, ...: each group of 2^NR amplitudes (bits q_0..q_{NR-1}) gets, rotation by
+// rotation in that order, the gradient partial of rotation r and the un-apply of R_r, all in
+// registers. (The rotations commute, so each gradient is the same whichever others are already
+// un-applied.) Partials of rotation r go to part[r grid .. (r + 1) grid).
+template <typename P, int NR>
+struct AdjRotNParams {
+    IndexPlan ip;            // the NR bits inserted
+    uint64_t bit[NR];        // 1 << q_r
+    typename P::K U[NR][4];  // R_r^+
+    int32_t axis[NR];
 };
 
 template <typename P>
@@ -133,36 +134,106 @@ __device__ __forceinline__ void rot_step(typename P::C& a, typename P::C& b, typ
     lb = P::out(s1);
 }
 
-template <typename P>
-__global__ void __launch_bounds__(kAdjThreads) k_adj_rot2(typename P::C* __restrict__ psi, typename P::C* __restrict__ lam,
-                                                           const __grid_constant__ AdjRot2Params<P> A, double* part) {
+// The double-float update of a pair by R^+ for X or Y axes, whose entries are real multiples of
+// 1 and i (X: [[c, -i s], [-i s, c]]; Y: [[c, -s], [s, c]]): every output component is a sum of
+// two real products, formed as one double-float dot product (the general 2 x 2 complex form
+// costs twice the products, half of them by zero). Z axes keep the general form.
+__device__ __forceinline__ void df_dot_re(float ah, float al, float bh, float bl, float ch, float cl, float dh,
+                                          float dl, float& h, float& l) {
+    float s, c;
+    DFArith::dprod0(s, c, ah, al, bh, bl);
+    DFArith::dprod(s, c, ch, cl, dh, dl);
+    DFArith::two_sum(s, c, h, l);
+}
+__device__ __forceinline__ void df_rot_pair(float4& a, float4& b, int axis, float ch, float cl, float sh, float sl) {
+    float4 ra, rb;
+    if (axis == 1) {  // a' = c a - i s b, b' = -i s a + c b
+        df_dot_re(ch, cl, a.x, a.y, sh, sl, b.z, b.w, ra.x, ra.y);
+        df_dot_re(ch, cl, a.z, a.w, -sh, -sl, b.x, b.y, ra.z, ra.w);
+        df_dot_re(sh, sl, a.z, a.w, ch, cl, b.x, b.y, rb.x, rb.y);
+        df_dot_re(-sh, -sl, a.x, a.y, ch, cl, b.z, b.w, rb.z, rb.w);
+    } else {  // a' = c a - s b, b' = s a + c b
+        df_dot_re(ch, cl, a.x, a.y, -sh, -sl, b.x, b.y, ra.x, ra.y);
+        df_dot_re(ch, cl, a.z, a.w, -sh, -sl, b.z, b.w, ra.z, ra.w);
+        df_dot_re(sh, sl, a.x, a.y, ch, cl, b.x, b.y, rb.x, rb.y);
+        df_dot_re(sh, sl, a.z, a.w, ch, cl, b.z, b.w, rb.z, rb.w);
+    }
+    a = ra;
+    b = rb;
+}
+template <>
+__device__ __forceinline__ void rot_step<DFArith>(float4& a, float4& b, float4& la, float4& lb, int axis,
+                                                  const float4* U, GradAcc<DFArith>& g) {
+    if (axis == 3) {  // general form
+        g.add(la, a);
+        g.add(lb, DFArith::ipow(b, 2));
+        DFArith::Acc r0 = DFArith::first(U[0], a), r1 = DFArith::first(U[2], a), s0 = DFArith::first(U[0], la),
+                     s1 = DFArith::first(U[2], la);
+        DFArith::mac(r0, U[1], b);
+        DFArith::mac(r1, U[3], b);
+        DFArith::mac(s0, U[1], lb);
+        DFArith::mac(s1, U[3], lb);
+        a = DFArith::out(r0);
+        b = DFArith::out(r1);
+        la = DFArith::out(s0);
+        lb = DFArith::out(s1);
+        return;
+    }
+    if (axis == 1) {
+        g.add(la, b);
+        g.add(lb, a);
+    } else {
+        g.add(la, DFArith::ipow(b, 3));
+        g.add(lb, DFArith::ipow(a, 1));
+    }
+    // c = Re U[0]; s = -Im U[1] (X) or -Re U[1] (Y)
+    const float ch = U[0].x, cl = U[0].y;
+    const float sh = axis == 1 ? -U[1].z : -U[1].x, sl = axis == 1 ? -U[1].w : -U[1].y;
+    df_rot_pair(a, b, axis, ch, cl, sh, sl);
+    df_rot_pair(la, lb, axis, ch, cl, sh, sl);
+}
+
+template <typename P, int NR>
+__global__ void __launch_bounds__(kAdjThreads) k_adj_rotn(typename P::C* __restrict__ psi, typename P::C* __restrict__ lam,
+                                                           const __grid_constant__ AdjRotNParams<P, NR> A, double* part) {
     using C = typename P::C;
-    GradAcc<P> ga, gb;
+    constexpr int E = 1 << NR;
+    GradAcc<P> g[NR];
     const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < A.ip.n_iter; i += stride) {
         const uint64_t i0 = expand(i, A.ip);
-        const uint64_t ix[4] = {i0, i0 | A.bit[0], i0 | A.bit[1], i0 | A.bit[0] | A.bit[1]};
-        C v[4], l[4];
+        uint64_t ix[E];
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
+        for (int e = 0; e < E; e++) {
+            uint64_t x = i0;
+#pragma unroll
+            for (int r = 0; r < NR; r++)
+                if ((e >> r) & 1) x |= A.bit[r];
+            ix[e] = x;
+        }
+        C v[E], l[E];
+#pragma unroll
+        for (int e = 0; e < E; e++) {
             v[e] = psi[ix[e]];
             l[e] = lam[ix[e]];
         }
-        rot_step<P>(v[0], v[1], l[0], l[1], A.axis[0], A.U[0], ga);  // pairs along a
-        rot_step<P>(v[2], v[3], l[2], l[3], A.axis[0], A.U[0], ga);
-        rot_step<P>(v[0], v[2], l[0], l[2], A.axis[1], A.U[1], gb);  // pairs along b
-        rot_step<P>(v[1], v[3], l[1], l[3], A.axis[1], A.U[1], gb);
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
+        for (int r = 0; r < NR; r++)
+#pragma unroll
+            for (int e = 0; e < E; e++)
+                if (!((e >> r) & 1)) rot_step<P>(v[e], v[e | (1 << r)], l[e], l[e | (1 << r)], A.axis[r], A.U[r], g[r]);
+#pragma unroll
+        for (int e = 0; e < E; e++) {
             psi[ix[e]] = v[e];
             lam[ix[e]] = l[e];
         }
     }
     __shared__ double sh[kAdjThreads / 32];
-    const double va = block_sum<kAdjThreads>(ga.imag(), sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = va;
-    const double vb = block_sum<kAdjThreads>(gb.imag(), sh);
-    if (threadIdx.x == 0) part[gridDim.x + blockIdx.x] = vb;
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+        const double val = block_sum<kAdjThreads>(g[r].imag(), sh);
+        if (threadIdx.x == 0) part[size_t(r) * gridDim.x + blockIdx.x] = val;
+    }
 }
 
 // out[s] = sum of part[s * nb .. s * nb + nb) in a fixed order, one block per slot
@@ -274,6 +345,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_diag(typename P::C* __restr
                 const AdjDiagFactor& F = A.f[k];
                 if ((x & F.cond_mask) != F.cond_val) continue;
                 sign ^= parity64(x & F.zmask);
+                if (F.pair_shift) sign ^= parity64(x & (x >> F.pair_shift) & F.pair_mask);
                 if (F.sign_only) {
                     sign ^= 1;
                 } else if (F.tab_off >= 0) {
@@ -331,20 +403,30 @@ void rot_dagger(int axis, double theta, cplx (&U)[4]) {
     else { U[0] = cplx(c, -s); U[1] = 0.0; U[2] = 0.0; U[3] = cplx(c, s); }
 }
 
-template <typename P>
-void launch_rot2(void* psi, void* lam, int n, const int (&qubit)[2], const int (&axis)[2], const double (&theta)[2],
-                 double* part, unsigned grid, cudaStream_t st) {
-    AdjRot2Params<P> A;
-    A.ip = make_index_plan(n, {qubit[0], qubit[1]}, 0);
-    for (int r = 0; r < 2; r++) {
+template <typename P, int NR>
+void launch_rotn(void* psi, void* lam, int n, const int* qubit, const int* axis, const double* theta, double* part,
+                 unsigned grid, cudaStream_t st) {
+    AdjRotNParams<P, NR> A;
+    A.ip = make_index_plan(n, std::vector<int>(qubit, qubit + NR), 0);
+    for (int r = 0; r < NR; r++) {
         A.bit[r] = 1ull << qubit[r];
         A.axis[r] = axis[r];
         cplx U[4];
         rot_dagger(axis[r], theta[r], U);
         for (int e = 0; e < 4; e++) A.U[r][e] = P::host_k(U[e].real(), U[e].imag());
     }
-    k_adj_rot2<P><<<grid, kAdjThreads, 0, st>>>(reinterpret_cast<typename P::C*>(psi),
-                                                reinterpret_cast<typename P::C*>(lam), A, part);
+    k_adj_rotn<P, NR><<<grid, kAdjThreads, 0, st>>>(reinterpret_cast<typename P::C*>(psi),
+                                                    reinterpret_cast<typename P::C*>(lam), A, part);
+}
+
+template <typename P>
+void launch_rotn_any(int nr, void* psi, void* lam, int n, const int* qubit, const int* axis, const double* theta,
+                     double* part, unsigned grid, cudaStream_t st) {
+    switch (nr) {
+        case 2: return launch_rotn<P, 2>(psi, lam, n, qubit, axis, theta, part, grid, st);
+        case 3: return launch_rotn<P, 3>(psi, lam, n, qubit, axis, theta, part, grid, st);
+        default: return launch_rotn<P, 4>(psi, lam, n, qubit, axis, theta, part, grid, st);
+    }
 }
 
 template <typename P>
@@ -385,12 +467,16 @@ void launch_adjoint_rotation(void* psi, void* lam, int n, Arith ar, int qubit, i
     QS_TRY_CUDA(cudaGetLastError());
 }
 
-void launch_adjoint_rotation2(void* psi, void* lam, int n, Arith ar, const int (&qubit)[2], const int (&axis)[2],
-                              const double (&theta)[2], double* part, unsigned grid, cudaStream_t st) {
+int adjoint_max_rotations(Arith ar) { return ar == Arith::DF ? 2 : 4; }
+
+void launch_adjoint_rotations(void* psi, void* lam, int n, Arith ar, int nr, const int* qubit, const int* axis,
+                              const double* theta, double* part, unsigned grid, cudaStream_t st) {
+    QS_REQUIRE(nr >= 2 && nr <= adjoint_max_rotations(ar), "2..4 rotations per pass");
+    QS_REQUIRE(n >= nr, "fewer qubits than rotations");
     switch (ar) {
-        case Arith::F32: launch_rot2<NativeArith<float>>(psi, lam, n, qubit, axis, theta, part, grid, st); break;
-        case Arith::F64: launch_rot2<NativeArith<double>>(psi, lam, n, qubit, axis, theta, part, grid, st); break;
-        case Arith::DF: launch_rot2<DFArith>(psi, lam, n, qubit, axis, theta, part, grid, st); break;
+        case Arith::F32: launch_rotn_any<NativeArith<float>>(nr, psi, lam, n, qubit, axis, theta, part, grid, st); break;
+        case Arith::F64: launch_rotn_any<NativeArith<double>>(nr, psi, lam, n, qubit, axis, theta, part, grid, st); break;
+        case Arith::DF: launch_rotn_any<DFArith>(nr, psi, lam, n, qubit, axis, theta, part, grid, st); break;
     }
     QS_TRY_CUDA(cudaGetLastError());
 }

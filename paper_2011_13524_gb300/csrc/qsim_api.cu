@@ -246,8 +246,10 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
     }
     if (!total) return w;
     std::vector<unsigned char> host(total);
-    for (size_t b = 0; b < ops.size(); b++) {
-        if (ops[b].kind != OpKind::Dense || ops[b].targets.size() < 4) continue;
+    std::vector<size_t> wide;
+    for (size_t b = 0; b < ops.size(); b++)
+        if (ops[b].kind == OpKind::Dense && ops[b].targets.size() >= 4) wide.push_back(b);
+    auto prepare = [&](size_t b) {
         if (oz[b] == 4)
             prepare_oz4_matrix(ops[b].data, host.data() + offs[b]);
         else if (oz[b] == 5)
@@ -256,6 +258,27 @@ WideMats upload_wide(qs_state* s, Arith ar, std::vector<Op>& ops) {
             prepare_bz_matrix(oz[b] - 10, ops[b].data, host.data() + offs[b]);
         else
             encode_entries(ar, ops[b].data, host.data() + offs[b]);
+    };
+    // the blocks' device forms (sliced for the tensor cores, or encoded entries) are independent:
+    // several host threads for long plans
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const unsigned nth = wide.size() < 8 ? 1u : std::min<unsigned>(std::min(hw, 8u), unsigned(wide.size() / 4));
+    if (nth <= 1) {
+        for (size_t b : wide) prepare(b);
+    } else {
+        std::vector<std::thread> pool;
+        std::vector<std::exception_ptr> errs(nth);
+        for (unsigned t = 0; t < nth; t++)
+            pool.emplace_back([&, t]() {
+                try {
+                    for (size_t i = t; i < wide.size(); i += nth) prepare(wide[i]);
+                } catch (...) {
+                    errs[t] = std::current_exception();
+                }
+            });
+        for (auto& th : pool) th.join();
+        for (auto& e : errs)
+            if (e) std::rethrow_exception(e);
     }
     QS_TRY_CUDA(dev_malloc_async(&w.dbuf, total, s->stream));
     QS_TRY_CUDA(cudaMemcpyAsync(w.dbuf, host.data(), total, cudaMemcpyHostToDevice, s->stream));
@@ -1172,11 +1195,11 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
         return g.param_index >= 0 && g.mc == 0 && (g.named == QS_NAMED_RX || g.named == QS_NAMED_RY);
     };
     struct Step {
-        int kind = 0;               // 0 rotation, 1 diagonal run, 2 other gate, 3 two rotations
-        int gate = -1;              // kinds 0, 2 and 3
-        int gate2 = -1;             // kind 3: the second rotation (slot slot0 + 1)
+        int kind = 0;               // 0 rotation, 1 diagonal run, 2 other gate, 3 rotations sharing a pass
+        int gate = -1;              // kinds 0, 2
+        std::vector<int> rots;      // kind 3: the rotations, latest first (slots slot0, slot0 + 1, ...)
         int slot0 = 0;              // first gradient slot
-        AdjDiagParams A;            // kind 1
+        std::shared_ptr<AdjDiagParams> diag;  // kind 1 (a few KB: held once, not copied with the step)
         size_t tab_byte = 0;        // kind 1: offset of its tables in the upload
         std::vector<int> params;    // kind 1: parameter index of each gradient term
     };
@@ -1186,27 +1209,35 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
     {
         std::vector<int> run;       // gate indices, reverse order
         int run_f = 0, run_g = 0, run_t = 0;  // its factor, gradient and table-entry bounds
+        uint64_t run_sq = 0;        // qubits of its uncontrolled single-qubit diagonals (tables of 6)
+        auto single_entries = [](uint64_t q) {
+            const int k = __builtin_popcountll(q);
+            return (k / 6) * 64 + (k % 6 ? 1 << (k % 6) : 0);
+        };
         auto flush = [&]() {
             run_f = run_g = run_t = 0;
+            run_sq = 0;
             if (run.empty()) return;
             Step stp;
             stp.kind = 1;
             stp.slot0 = nslots;
-            stp.A.n_amp = 1ull << c->n;
+            stp.diag = std::make_shared<AdjDiagParams>();
+            AdjDiagParams& A = *stp.diag;
+            A.n_amp = 1ull << c->n;
             stp.tab_byte = tabs.size();
             // single-qubit uncontrolled diagonals multiply into per-qubit pairs, then into tables
             // over up to 4 qubits; every other diagonal keeps a factor of its own
             std::map<int, std::pair<cplx, cplx>> one;
             int ntab = 0;
             auto add_factor = [&](const AdjDiagFactor& f, const std::vector<cplx>& t) {
-                QS_REQUIRE(stp.A.nf < kAdjDiagMaxF, "diagonal run too long");
+                QS_REQUIRE(A.nf < kAdjDiagMaxF, "diagonal run too long");
                 AdjDiagFactor g = f;
                 if (!t.empty()) {
                     g.tab_off = ntab;
                     for (const cplx& v : t) tabs.push_back(v);
                     ntab += int(t.size());
                 }
-                stp.A.f[stp.A.nf++] = g;
+                A.f[A.nf++] = g;
             };
             for (int gi : run) {
                 const qs_gate& g = c->gates[gi];
@@ -1216,7 +1247,7 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
                     for (int j = 0; j < g.m; j++)
                         if (g.kind == QS_GATE_NAMED && g.named == QS_NAMED_RZ) zm |= 1ull << g.targets[j];
                         else if (g.pauli[j] == 3) zm |= 1ull << g.targets[j];
-                    stp.A.gz[stp.A.ng++] = zm;
+                    A.gz[A.ng++] = zm;
                     stp.params.push_back(g.param_index);
                 }
                 uint64_t cm = 0, cv = 0;
@@ -1247,10 +1278,41 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
                     add_factor(f, op.data);
                 }
             }
+            // CZ gates (a -1 on the subspace where both of two qubits are 1, no other condition)
+            // with the same qubit distance d share one factor: the parity of x & (x >> d) over
+            // their lower qubits
+            {
+                std::map<int, uint64_t> pairs;
+                std::vector<AdjDiagFactor> keep;
+                for (int k = 0; k < A.nf; k++) {
+                    const AdjDiagFactor& g = A.f[k];
+                    if (g.sign_only && g.zmask == 0 && g.tab_off < 0 && __builtin_popcountll(g.cond_mask) == 2 &&
+                        g.cond_val == g.cond_mask) {
+                        const int a = __builtin_ctzll(g.cond_mask), b = 63 - __builtin_clzll(g.cond_mask);
+                        uint64_t& m = pairs[b - a];
+                        if (!((m >> a) & 1)) {
+                            m |= 1ull << a;
+                            continue;
+                        }
+                        m &= ~(1ull << a);  // the same CZ twice cancels
+                        continue;
+                    }
+                    keep.push_back(g);
+                }
+                A.nf = 0;
+                for (const AdjDiagFactor& g : keep) A.f[A.nf++] = g;
+                for (const auto& pm : pairs) {
+                    if (!pm.second) continue;
+                    AdjDiagFactor g;
+                    g.pair_shift = pm.first;
+                    g.pair_mask = pm.second;
+                    A.f[A.nf++] = g;
+                }
+            }
             std::vector<std::pair<int, std::pair<cplx, cplx>>> ones(one.begin(), one.end());
-            for (size_t i0 = 0; i0 < ones.size(); i0 += 4) {
+            for (size_t i0 = 0; i0 < ones.size(); i0 += 6) {
                 AdjDiagFactor f;
-                f.nq = int(std::min<size_t>(4, ones.size() - i0));
+                f.nq = int(std::min<size_t>(6, ones.size() - i0));
                 std::vector<cplx> t(size_t(1) << f.nq, cplx(1.0, 0.0));
                 for (int j = 0; j < f.nq; j++) {
                     f.q[j] = ones[i0 + j].first;
@@ -1259,9 +1321,9 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
                 }
                 add_factor(f, t);
             }
-            stp.A.ntab = ntab;
+            A.ntab = ntab;
             QS_REQUIRE(ntab <= kAdjDiagMaxTab, "diagonal run tables too large");
-            nslots += stp.A.ng;
+            nslots += A.ng;
             steps.push_back(std::move(stp));
             run.clear();
         };
@@ -1272,15 +1334,19 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
                               (op.kind == OpKind::Pauli && op.xmask == 0);
             const bool diag_param = g.param_index < 0 || (op.kind != OpKind::Dense && g.mc == 0);
             if (diag && diag_param) {
-                // bound the run by the kernel's factor, gradient and table limits (worst case)
-                const int tab_need = op.kind == OpKind::Diag ? (1 << op.targets.size()) : 1;
+                // bound the run by the kernel's factor, gradient and table limits (worst case);
+                // uncontrolled single-qubit diagonals share tables of up to 6 qubits
+                const bool single = op.kind == OpKind::Diag && op.targets.size() == 1 && op.controls.empty();
+                const int tab_need = single ? 0 : op.kind == OpKind::Diag ? (1 << op.targets.size()) : 1;
+                const uint64_t sq = single ? run_sq | (1ull << op.targets[0]) : run_sq;
                 if (run_f + 1 > kAdjDiagMaxF || run_g + (g.param_index >= 0) > kAdjDiagMaxG ||
-                    run_t + tab_need > kAdjDiagMaxTab)
+                    run_t + tab_need + single_entries(sq) > kAdjDiagMaxTab)
                     flush();
                 run.push_back(i);
                 run_f += 1;
                 run_g += g.param_index >= 0;
                 run_t += tab_need;
+                if (single) run_sq |= 1ull << op.targets[0];
                 continue;
             }
             flush();
@@ -1296,20 +1362,32 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
         }
         flush();
     }
-    // two consecutive rotation steps on distinct qubits share one pass (their slots are adjacent)
+    // up to adjoint_max_rotations consecutive rotation steps on distinct qubits share one pass
+    // (their slots are adjacent)
     {
+        const int maxr = std::min(adjoint_max_rotations(ar), c->n);
         std::vector<Step> merged;
-        for (size_t i = 0; i < steps.size(); i++) {
-            if (i + 1 < steps.size() && steps[i].kind == 0 && steps[i + 1].kind == 0 &&
-                c->gates[steps[i].gate].targets[0] != c->gates[steps[i + 1].gate].targets[0] && c->n >= 2) {
-                Step m = steps[i];
-                m.kind = 3;
-                m.gate2 = steps[i + 1].gate;
-                merged.push_back(m);
-                i++;
+        for (size_t i = 0; i < steps.size();) {
+            if (steps[i].kind != 0 || maxr < 2) {
+                merged.push_back(steps[i++]);
                 continue;
             }
-            merged.push_back(steps[i]);
+            size_t j = i;
+            uint64_t used = 0;
+            while (j < steps.size() && int(j - i) < maxr && steps[j].kind == 0 &&
+                   !((used >> c->gates[steps[j].gate].targets[0]) & 1)) {
+                used |= 1ull << c->gates[steps[j].gate].targets[0];
+                j++;
+            }
+            if (j - i >= 2) {
+                Step m = steps[i];
+                m.kind = 3;
+                for (size_t t = i; t < j; t++) m.rots.push_back(steps[t].gate);
+                merged.push_back(m);
+            } else {
+                merged.push_back(steps[i]);
+            }
+            i = j > i + 1 ? j : i + 1;
         }
         steps.swap(merged);
     }
@@ -1330,20 +1408,24 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
         for (const Step& stp : steps) {
             if (stp.kind == 1) {
                 launch_adjoint_diag(psi->data, lam->data, c->n, ar,
-                                    static_cast<const unsigned char*>(d_tab) + stp.tab_byte * eb, stp.A,
+                                    static_cast<const unsigned char*>(d_tab) + stp.tab_byte * eb, *stp.diag,
                                     d_part ? d_part + size_t(stp.slot0) * nb : nullptr, nb, st);
                 for (size_t g = 0; g < stp.params.size(); g++) slot_param[stp.slot0 + g] = stp.params[g];
                 continue;
             }
             const qs_gate& g = c->gates[stp.gate];
             if (stp.kind == 3) {
-                const qs_gate& g2 = c->gates[stp.gate2];
-                const int q[2] = {g.targets[0], g2.targets[0]};
-                const int ax[2] = {g.named == QS_NAMED_RX ? 1 : 2, g2.named == QS_NAMED_RX ? 1 : 2};
-                const double th[2] = {theta ? theta[g.param_index] : g.params[0], theta ? theta[g2.param_index] : g2.params[0]};
-                launch_adjoint_rotation2(psi->data, lam->data, c->n, ar, q, ax, th, d_part + size_t(stp.slot0) * nb, nb, st);
-                slot_param[stp.slot0] = g.param_index;
-                slot_param[stp.slot0 + 1] = g2.param_index;
+                const int nr = int(stp.rots.size());
+                int q[4], ax[4];
+                double th[4];
+                for (int r = 0; r < nr; r++) {
+                    const qs_gate& gr = c->gates[stp.rots[r]];
+                    q[r] = gr.targets[0];
+                    ax[r] = gr.named == QS_NAMED_RX ? 1 : 2;
+                    th[r] = theta ? theta[gr.param_index] : gr.params[0];
+                    slot_param[stp.slot0 + r] = gr.param_index;
+                }
+                launch_adjoint_rotations(psi->data, lam->data, c->n, ar, nr, q, ax, th, d_part + size_t(stp.slot0) * nb, nb, st);
                 continue;
             }
             if (stp.kind == 0) {

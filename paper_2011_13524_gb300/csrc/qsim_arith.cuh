@@ -141,13 +141,13 @@ __device__ __forceinline__ float4 narrow<float4>(double re, double im) {
 
 // double -> (hi, lo) floats with hi = RN(x) and lo = RN(x - hi), as split_double, but on the
 // integer pipes (GB300 runs FP64 and its conversions at 1/64 of the FP32 rate): hi takes the top
-// 24 significant bits rounded to nearest-even, lo the remainder, an integer below 2^29 converted
-// to float with rounding to nearest and then scaled by powers of two. When lo is a normal float
-// the scaling is exact and lo = RN(x - hi); when it is subnormal (possible for |x| below 2^-74)
-// the last scaling rounds a second time and lo may differ from RN(x - hi) by one subnormal ulp
-// (below 1.5e-45 in absolute value). Zero is split directly. Magnitudes below 2^-126 (under FP32's normal range) become
-// a signed zero: the absolute change is below 1.2e-38. At or above 2^125 (huge, non-finite) it
-// falls back to the FP64 instructions.
+// 24 significant bits rounded to nearest-even, lo the remainder, an integer number of the
+// double's last places below 2^29, converted to float with rounding to nearest and scaled by
+// powers of two (exact, as lo is then a normal float): lo = RN(x - hi). Below 2^-74 (a double
+// exponent field under 949) a nonzero remainder can be subnormal in FP32, where a second
+// rounding could creep in; those magnitudes take the FP64 split. Zero is split directly.
+// Magnitudes below 2^-126 (under FP32's normal range) become a signed zero: the absolute change
+// is below 1.2e-38. At or above 2^125 (huge, non-finite) it falls back to the FP64 instructions.
 __device__ __forceinline__ void split_double_int(double x, float& hi, float& lo) {
     const uint64_t b = uint64_t(__double_as_longlong(x));
     const uint32_t e = uint32_t(b >> 52) & 0x7FFu;
@@ -157,7 +157,7 @@ __device__ __forceinline__ void split_double_int(double x, float& hi, float& lo)
         lo = 0.f;
         return;
     }
-    if (e > 1148u) {
+    if (e > 1148u || e < 949u) {
         split_double(x, hi, lo);
         return;
     }
@@ -167,10 +167,8 @@ __device__ __forceinline__ void split_double_int(double x, float& hi, float& lo)
     const uint32_t up = (rem > (1u << 28) || (rem == (1u << 28) && (hm & 1u))) ? 1u : 0u;
     hi = __uint_as_float(sign | (((e - 1023u + 127u) << 23) + hm + up));
     const int32_t li = int32_t(rem) - int32_t(up << 29);
-    const uint32_t off = e < 960u ? 64u : 0u;                         // keep the first scale normal
-    const float scale = __uint_as_float((e + off - 1075u + 127u) << 23);  // 2^(e + off - 1075)
-    const float unscale = __uint_as_float((127u - off) << 23);            // 2^-off
-    const float l = __fmul_rn(__fmul_rn(__int2float_rn(li), scale), unscale);
+    const float scale = __uint_as_float((e - 1075u + 127u) << 23);  // 2^(e - 1075), normal for e >= 949
+    const float l = __fmul_rn(__int2float_rn(li), scale);
     lo = sign ? -l : l;
 }
 // float -> double exactly, on the integer pipes for zero and normal floats

@@ -83,12 +83,15 @@ __device__ __forceinline__ void split_tile(double x, float& hi, float& lo) {
     lo = __fmul_rn(__fsub_rn(__uint_as_float(se | ((bl >> 6) & 0x7FFFFFu)), __uint_as_float(se)), 1.1920928955078125e-07f);
 }
 
+// A complex128 tile element is held as {re_hi, im_hi, re_lo, im_lo}: the high words of the real
+// and imaginary parts side by side, and the low words, so that both parts are processed as
+// packed FP32 pairs.
 __device__ __forceinline__ float2 to_tile(float2 v) { return v; }
-__device__ __forceinline__ float4 to_tile(float4 v) { return v; }
+__device__ __forceinline__ float4 to_tile(float4 v) { return make_float4(v.x, v.z, v.y, v.w); }
 __device__ __forceinline__ float4 to_tile(double2 v) {
     float4 r;
-    split_tile(v.x, r.x, r.y);
-    split_tile(v.y, r.z, r.w);
+    split_tile(v.x, r.x, r.z);
+    split_tile(v.y, r.y, r.w);
     return r;
 }
 
@@ -96,7 +99,7 @@ struct DFc {
     float rh, rl, ih, il;
 };
 __device__ __forceinline__ DFc dfc(float2 e) { return DFc{e.x, 0.f, e.y, 0.f}; }
-__device__ __forceinline__ DFc dfc(float4 e) { return DFc{e.x, e.y, e.z, e.w}; }
+__device__ __forceinline__ DFc dfc(float4 e) { return DFc{e.x, e.z, e.y, e.w}; }
 
 __device__ __forceinline__ void two_sum_f(float a, float b, float& h, float& l) {
     h = __fadd_rn(a, b);
@@ -223,15 +226,70 @@ __device__ __forceinline__ void slot_sums(const TileGroup& G, const TileSlot* S,
     }
 }
 
+// The plain sum over the thread's 8 pair representatives of Re A = a.re b.re + a.im b.im
+// (A = conj(b) a, b = psi_{y^f}), as (h, l), with the products of the real and imaginary parts
+// as packed pairs. A grid above three times the thread's sum of |hi x hi| products is chosen
+// first (as grid_transform does); each hi product P is then cut into H = RN(P + c) - c, exact on
+// the grid, whose sum is exact, and the rest a b - H, formed by one FMA with -H (exactly -H as
+// c - RN(P + c)) plus the hi x lo cross products, summed in FP32 (it is below the grid's unit).
+template <typename E, bool kLo>
+__device__ __forceinline__ void re_sum_packed(const E* tile, uint32_t tb, uint32_t f, const uint32_t* im, float& h,
+                                              float& l) {
+    uint32_t o[8];
+    o[0] = tb;
+#pragma unroll
+    for (int k = 1; k < 8; k++) o[k] = o[k ^ (1 << top_bit(k))] | im[top_bit(k)];
+    float S = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const E a = tile[o[k]], b = tile[o[k] ^ f];
+        const float2 P = __fmul2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+        S = __fadd_rn(__fadd_rn(S, fabsf(P.x)), fabsf(P.y));
+    }
+    uint32_t e = (__float_as_uint(S) >> 23) & 0xFFu;
+    e = e > 250u ? 250u : e;
+    const float c = __uint_as_float(((e + 2u) << 23) | 0x400000u);  // 1.5 * 2^(e - 125) > 3 S
+    const float2 C2 = make_float2(c, c), NC2 = make_float2(-c, -c), M1 = make_float2(-1.f, -1.f);
+    float2 HS = make_float2(0.f, 0.f), LS = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const E a = tile[o[k]], b = tile[o[k] ^ f];
+        const float2 ah = make_float2(a.x, a.y), bh = make_float2(b.x, b.y);
+        const float2 P = __fmul2_rn(ah, bh);
+        const float2 T = __fadd2_rn(P, C2);
+        const float2 H = __fadd2_rn(T, NC2);
+        const float2 NH = __ffma2_rn(T, M1, C2);  // c - T = -H exactly
+        float2 L = __ffma2_rn(ah, bh, NH);        // a b - H (one rounding, far below the grid's unit)
+        if constexpr (kLo) {
+            const float4& a4 = reinterpret_cast<const float4&>(a);
+            const float4& b4 = reinterpret_cast<const float4&>(b);
+            L = __ffma2_rn(ah, make_float2(b4.z, b4.w), L);
+            L = __ffma2_rn(make_float2(a4.z, a4.w), bh, L);
+        }
+        HS = __fadd2_rn(HS, H);
+        LS = __fadd2_rn(LS, L);
+    }
+    h = __fadd_rn(HS.x, HS.y);  // both on the grid: exact
+    l = __fadd_rn(LS.x, LS.y);
+}
+
 template <typename E, bool kLo, int kKind>
 __device__ __forceinline__ void group_kind(const TileGroup& G, const TileSlot* S, const E* tile, const float2* gam,
                                            uint32_t tid, uint32_t tb, float& ah, float& al) {
     uint32_t im[4];
 #pragma unroll
     for (int i = 0; i < 4; i++) im[i] = G.imask[i];
+    const bool full = G.wht != 0;
+    if constexpr (kKind == kTileRe) {
+        if (!full) {  // only the plain sum of Re A: packed pairs
+            float qh[1], ql[1];
+            re_sum_packed<E, kLo>(tile, tb, G.f, im, qh[0], ql[0]);
+            slot_sums<0, 1>(G, S, gam, tid, qh, ql, ah, al);
+            return;
+        }
+    }
     float qh[16], ql[16];
     group_values<E, kLo, kKind>(tile, tb, G.f, im, qh, ql);
-    const bool full = G.wht != 0;
     if (kKind == kTileDiag) {
         grid_transform<16>(qh, ql, full);
     } else {
@@ -273,11 +331,9 @@ __device__ __forceinline__ void tile_group_pair_re(const TileGroup& G1, const Ti
         im1[i] = G1.imask[i];
         im2[i] = G2.imask[i];
     }
-    float qh1[8], ql1[8], qh2[8], ql2[8];
-    group_values<E, kLo, kTileRe>(tile, tb1, G1.f, im1, qh1, ql1);
-    group_values<E, kLo, kTileRe>(tile, tb2, G2.f, im2, qh2, ql2);
-    grid_transform<8>(qh1, ql1, false);
-    grid_transform<8>(qh2, ql2, false);
+    float qh1[1], ql1[1], qh2[1], ql2[1];
+    re_sum_packed<E, kLo>(tile, tb1, G1.f, im1, qh1[0], ql1[0]);
+    re_sum_packed<E, kLo>(tile, tb2, G2.f, im2, qh2[0], ql2[0]);
     slot_sums<0, 1>(G1, S, gam, tid, qh1, ql1, ah, al);
     slot_sums<0, 1>(G2, S, gam, tid, qh2, ql2, ah, al);
 }

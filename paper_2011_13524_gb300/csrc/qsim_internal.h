@@ -335,10 +335,12 @@ void launch_apply_observable(const std::vector<PauliGroup>& groups, const void* 
 unsigned adj_grid(int n);
 void launch_adjoint_rotation(void* psi, void* lam, int n, Arith ar, int qubit, int axis, double theta, double* part,
                              unsigned grid, cudaStream_t st);
-// Two consecutive rotation steps on distinct qubits (qubit[0] first), one pass: partials of the
-// first into part[0 .. grid), of the second into part[grid .. 2 grid).
-void launch_adjoint_rotation2(void* psi, void* lam, int n, Arith ar, const int (&qubit)[2], const int (&axis)[2],
-                              const double (&theta)[2], double* part, unsigned grid, cudaStream_t st);
+// nr consecutive rotation steps (2..adjoint_max_rotations(ar)) on distinct qubits (qubit[0]
+// first, the latest in the circuit), one pass: partials of rotation r into
+// part[r grid .. (r + 1) grid).
+int adjoint_max_rotations(Arith ar);
+void launch_adjoint_rotations(void* psi, void* lam, int n, Arith ar, int nr, const int* qubit, const int* axis,
+                              const double* theta, double* part, unsigned grid, cudaStream_t st);
 // Reverse step for a run of diagonal gates on psi and lam (both multiplied by the run's inverse),
 // with the gradient partials of the run's diagonal rotations exp(i theta P / 2) (P a Z string
 // gz[g]) computed before: part[g * grid + block] = block's sum of (-1)^popc(x & gz[g]) Im(conj(lam_x) psi_x).
@@ -348,6 +350,8 @@ constexpr int kAdjDiagMaxTab = 1024;
 struct AdjDiagFactor {
     uint64_t cond_mask = 0, cond_val = 0;  // applies where (x & cond_mask) == cond_val
     uint64_t zmask = 0;                    // sign (-1)^popc(x & zmask)
+    uint64_t pair_mask = 0;                // sign (-1)^popc(x & (x >> pair_shift) & pair_mask): a set of
+    int32_t pair_shift = 0;                //   CZ gates on qubit pairs (a, a + pair_shift), bit a set
     int32_t sign_only = 0;                 // the factor is -1 (no table)
     int32_t tab_off = -1;                  // table of 2^nq entries (or none)
     int32_t nq = 0;

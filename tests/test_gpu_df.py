@@ -208,6 +208,31 @@ def test_df_layout_round_trip_bit_exact(df):
     st.close()
 
 
+def test_df_layout_round_trip_small_magnitudes_bit_exact(df):
+    """Magnitudes from 2^-126 to 2^-70, where the low word of the split can be subnormal in FP32:
+    in place to double-float and back still gives exactly RN(hi + lo) of numpy's float32 split
+    (one rounding of lo, also when it is subnormal)."""
+    qs = df
+    n = 12
+    rng = np.random.default_rng(2718)
+    N = 1 << n
+    mags = np.ldexp(1.0, rng.integers(-126, -70, 2 * N)) * rng.uniform(1.0, 2.0, 2 * N)
+    vals = rng.choice([-1.0, 1.0], 2 * N) * mags
+    vals[::29] = np.ldexp(1.0, rng.integers(-126, -70, len(vals[::29])))  # powers of two
+    vals[3::31] *= (1 + 2.0 ** -40)  # remainders far below hi
+    psi0 = vals[0::2] + 1j * vals[1::2]
+    st = qs.State(n, qs.QS_C128)
+    st.load(psi0)
+    st.run(W.Circuit(n, []), 0)
+    got = st.get_vector()
+    re = np.ascontiguousarray(psi0).view(np.float64)
+    hi = re.astype(np.float32)
+    lo = (re - hi.astype(np.float64)).astype(np.float32)
+    want = hi.astype(np.float64) + lo.astype(np.float64)
+    assert np.array_equal(np.ascontiguousarray(got).view(np.float64).view(np.uint64), want.view(np.uint64))
+    st.close()
+
+
 def test_df_layout_round_trip_near_powers_of_two(df):
     """Doubles just below and above powers of two (hi = 2^k with lo of either sign, the join's
     binade edge and its FP64 fallback), long runs of ones, and lo exponents 24..60 below hi's:

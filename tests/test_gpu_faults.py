@@ -10,6 +10,7 @@
   no more allocations than before it, and the call succeeds once k passes its allocations.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -125,6 +126,7 @@ def sweep_allocation_failures(qs, op, cleanup, limit=60):
     """Runs op with the k-th allocation failing, k = 0, 1, ...: every failing run reports
     QS_ERR_OOM and leaves the library holding what it held before; returns the first k at which
     op succeeds (its allocation count)."""
+    gc.collect()  # objects left by earlier tests release their allocations now, not mid-sweep
     base = held(qs)
     for k in range(limit):
         objs = []
@@ -138,6 +140,7 @@ def sweep_allocation_failures(qs, op, cleanup, limit=60):
         finally:
             qs.check(qs.lib().qs_debug_fail_alloc(-1, None))
             cleanup(objs)
+            gc.collect()
         assert held(qs) == base, (k, held(qs), base)
         if ok:
             return k
