@@ -419,14 +419,14 @@ void launch_rotn(void* psi, void* lam, int n, const int* qubit, const int* axis,
                                                     reinterpret_cast<typename P::C*>(lam), A, part);
 }
 
+// Two rotations per pass: three or four (8 or 16 amplitudes of psi and lambda per thread) were
+// measured slower in every arithmetic at n = 20 (the registers cut the resident warps), so only
+// NR = 2 is instantiated.
 template <typename P>
 void launch_rotn_any(int nr, void* psi, void* lam, int n, const int* qubit, const int* axis, const double* theta,
                      double* part, unsigned grid, cudaStream_t st) {
-    switch (nr) {
-        case 2: return launch_rotn<P, 2>(psi, lam, n, qubit, axis, theta, part, grid, st);
-        case 3: return launch_rotn<P, 3>(psi, lam, n, qubit, axis, theta, part, grid, st);
-        default: return launch_rotn<P, 4>(psi, lam, n, qubit, axis, theta, part, grid, st);
-    }
+    QS_REQUIRE(nr == 2, "two rotations per pass");
+    launch_rotn<P, 2>(psi, lam, n, qubit, axis, theta, part, grid, st);
 }
 
 template <typename P>
@@ -467,11 +467,11 @@ void launch_adjoint_rotation(void* psi, void* lam, int n, Arith ar, int qubit, i
     QS_TRY_CUDA(cudaGetLastError());
 }
 
-int adjoint_max_rotations(Arith ar) { return ar == Arith::DF ? 2 : 4; }
+int adjoint_max_rotations(Arith) { return 2; }
 
 void launch_adjoint_rotations(void* psi, void* lam, int n, Arith ar, int nr, const int* qubit, const int* axis,
                               const double* theta, double* part, unsigned grid, cudaStream_t st) {
-    QS_REQUIRE(nr >= 2 && nr <= adjoint_max_rotations(ar), "2..4 rotations per pass");
+    QS_REQUIRE(nr >= 2 && nr <= adjoint_max_rotations(ar), "rotations per pass out of range");
     QS_REQUIRE(n >= nr, "fewer qubits than rotations");
     switch (ar) {
         case Arith::F32: launch_rotn_any<NativeArith<float>>(nr, psi, lam, n, qubit, axis, theta, part, grid, st); break;

@@ -335,8 +335,8 @@ void launch_apply_observable(const std::vector<PauliGroup>& groups, const void* 
 unsigned adj_grid(int n);
 void launch_adjoint_rotation(void* psi, void* lam, int n, Arith ar, int qubit, int axis, double theta, double* part,
                              unsigned grid, cudaStream_t st);
-// nr consecutive rotation steps (2..adjoint_max_rotations(ar)) on distinct qubits (qubit[0]
-// first, the latest in the circuit), one pass: partials of rotation r into
+// nr consecutive rotation steps (2..adjoint_max_rotations(ar), which is 2) on distinct qubits
+// (qubit[0] first, the latest in the circuit), one pass: partials of rotation r into
 // part[r grid .. (r + 1) grid).
 int adjoint_max_rotations(Arith ar);
 void launch_adjoint_rotations(void* psi, void* lam, int n, Arith ar, int nr, const int* qubit, const int* axis,
