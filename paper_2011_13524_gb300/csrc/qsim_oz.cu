@@ -166,11 +166,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 
-// (a + b) exactly as (s, t) when a is a multiple of ulp(b) or |a| >= |b|
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& t) {
-    s = __fadd_rn(a, b);
-    t = __fsub_rn(b, __fsub_rn(s, a));
-}
 
 // Packed pairs: sm_100 and later execute two FP32 operations per instruction (FADD2, FMUL2,
 // FFMA2), each lane rounding exactly as the scalar instruction does, so a pair computation gives
@@ -187,6 +182,7 @@ __device__ __forceinline__ float2 grid_round2(float2 x) {
     constexpr float c = 1.5f * float(1 << 15) / float(1ull << (8 * S));
     return __fadd2_rn(__fadd2_rn(x, dup2(c)), dup2(-c));
 }
+// (a + b) exactly as (s, t) when a is a multiple of ulp(b) or |a| >= |b|, both lanes
 __device__ __forceinline__ void fast_two_sum2(float2 a, float2 b, float2& s, float2& t) {
     s = __fadd2_rn(a, b);
     t = rsub2(b, rsub2(s, a));
@@ -1099,6 +1095,317 @@ __global__ void __launch_bounds__(Bz<Q>::Threads, Bz<Q>::MinBlocks) k_dense_bz(f
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(B::TmemCols));
 }
 
+// ---------------------------------------------------------------- complex64, 6 targets, pipelined
+// 64 x 64 complex blocks (R = 128 reals, K = 128: eight K-steps) with the 5-target kernel's
+// pipeline. The outputs are split into two halves of 64 reals (amplitudes 0..31 and 32..63), each
+// with its stacked matrix slices [B_0h; B_1h; B_2h] (192 x 128 bf16), three diagonals in its own
+// 192 TMEM columns and its own commit barrier; the MMAs of a half are, per K-step, slice 0 times
+// all three matrix slices (N = 192, diagonals 0..2), slice 1 times two (N = 128, diagonals 1, 2)
+// and slice 2 times one (N = 64, diagonal 2). Sixteen worker warps (four threads per group, each
+// owning eight amplitudes of either half) load, slice and sum; one more warp issues the MMAs. The
+// state slices are double-buffered: buffer 0 holds its three slices in shared memory, buffer 1
+// its slice 0 in shared memory and slices 1 and 2 as the MMA's A operand in TMEM, in the 64-column
+// gaps after each half's accumulators (2 x (192 + 64) = all 512 columns; shared memory
+// 3 x 32 + 32 + 96 KB of matrix slices; the row scales are read from global memory). Hand-offs,
+// bounded waits and the recovery on a timeout are those of the 5-target kernel.
+constexpr int kBz6D = 64;                                      // amplitudes per group
+constexpr int kBz6R = 2 * kBz6D;                               // 128 reals
+constexpr int kBz6Workers = 512;
+constexpr int kBz6WorkerWarps = kBz6Workers / 32;
+constexpr int kBz6Threads = kBz6Workers + 32;
+constexpr int kBz6TPG = kBz6Workers / kOzTG;                   // 4 threads per group
+constexpr int kBz6Amps = kBz6D / kBz6TPG;                      // 16 amplitudes per thread
+constexpr uint32_t kBz6Sbo = (kBz6R / 8) * 128;                // 2048
+constexpr size_t kBz6Slice = size_t(kOzTG) * kBz6R * 2;        // 32 KB
+constexpr int kBz6HalfRows = kBzNS * (kBz6R / 2);              // 192 rows per half stack
+constexpr size_t kBz6Half = size_t(kBz6HalfRows) * kBz6R * 2;  // 48 KB
+constexpr size_t kBz6Mat = 2 * kBz6Half;                       // 96 KB
+constexpr int kBz6TmemCols = 512;
+constexpr uint32_t kBz6HalfCol = 256;
+constexpr uint32_t kBz6ACol = kBzND * (kBz6R / 2);             // 192: the A slice of buffer 1 in half h's gap
+constexpr size_t kOff6A0 = 0;                                  // buffer 0: slices 0..2
+constexpr size_t kOff6A1 = kBzNS * kBz6Slice;                  // buffer 1: slice 0
+constexpr size_t kOff6Mat = kOff6A1 + kBz6Slice;
+constexpr size_t kOff6NuPart = kOff6Mat + kBz6Mat;
+constexpr size_t kBz6Smem = kOff6NuPart + size_t(kBz6TPG) * kOzTG * 4;
+static_assert(kBz6ACol + kBz6R / 2 <= kBz6HalfCol, "a half's accumulators and one A slice fit its 256 TMEM columns");
+// with the 1 KB of static shared memory (the barriers, padded to the dynamic array's alignment)
+static_assert(kBz6Smem + 1024 <= 227 * 1024, "shared memory of one CTA");
+
+struct Bz6Params {
+    IndexPlan ip;
+    uint64_t offs[kBz6D];    // s(w), targets ascending
+    uint64_t n_groups;
+    long long wait_spins;    // try_wait attempts of each pipeline wait before it gives up
+    int force_late;          // test hook: a worker's first accumulator wait reports a timeout at once
+};
+
+__device__ __forceinline__ uint64_t sdesc6(uint32_t saddr) {
+    uint64_t d = uint64_t((saddr >> 4) & 0x3FFF);
+    d |= uint64_t((kOzLbo >> 4) & 0x3FFF) << 16;
+    d |= uint64_t((kBz6Sbo >> 4) & 0x3FFF) << 32;
+    d |= uint64_t(1) << 46;
+    return d;
+}
+
+template <bool kPairs>
+__global__ void __launch_bounds__(kBz6Threads, 1) k_dense_bz6(float2* __restrict__ psi,
+                                                              const unsigned char* __restrict__ dmat,
+                                                              const __grid_constant__ Bz6Params P, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[7];  // full[0..1], accfree[0..1], done[0..1], drain
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // the row scales stay in global memory (512 bytes, read through L1): shared memory is full
+    const float* __restrict__ mu = reinterpret_cast<const float*>(dmat + kBz6Mat);
+    float* nu_part = reinterpret_cast<float*>(smem + kOff6NuPart);
+    const uint32_t full0 = smem_u32(&bars[0]), accfree0 = smem_u32(&bars[2]), done0 = smem_u32(&bars[4]);
+    const uint32_t drain = smem_u32(&bars[6]);
+    volatile int* fail = &s_fail;
+
+    for (int i = tid; i < int(kBz6Mat / 16); i += kBz6Threads)
+        reinterpret_cast<uint4*>(smem + kOff6Mat)[i] = reinterpret_cast<const uint4*>(dmat)[i];
+    if (tid == 0) {
+        for (int i = 0; i < 4; i++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full0 + 8u * i), "r"(kBz6WorkerWarps));
+        for (int i = 4; i < 7; i++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8u * i));
+        s_fail = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(kBz6TmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
+    const uint64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const long long spins = P.wait_spins;
+
+    if (warp >= kBz6WorkerWarps) {
+        // ---------------------------------------------------------- MMA issuer (one thread)
+        if (warp == kBz6WorkerWarps && lane == 0) {
+            const uint64_t a0 = sdesc6(smem_u32(smem + kOff6A0)), a1 = sdesc6(smem_u32(smem + kOff6A1));
+            const uint64_t mbase = sdesc6(smem_u32(smem + kOff6Mat));
+            for (uint64_t j = 0; j < my_tiles; j++) {
+                const uint32_t b = uint32_t(j & 1);
+                if (!mbar_wait_or_abort(full0 + 8u * b, uint32_t((j >> 1) & 1), spins, fail)) {
+                    *fail = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                bool stop = false;
+#pragma unroll 1
+                for (int hv = 0; hv < 2; hv++) {
+                    if (j >= 1 && !mbar_wait_or_abort(accfree0 + 8u * hv, uint32_t((j - 1) & 1), spins, fail)) {
+                        *fail = 1;
+                        stop = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t dh = tmem + kBz6HalfCol * uint32_t(hv);
+                    const uint64_t bdh = mbase + uint64_t(hv * (kBz6Half >> 4));
+                    // state slice s2 of buffer b times matrix slices 0 .. nt - 1 into diagonals s2..
+                    auto prod = [&](int s2, int nt, int ks, uint32_t acc) {
+                        const uint32_t d = dh + uint32_t(s2 * (kBz6R / 2));
+                        const uint64_t bd = bdh + uint64_t((ks * 256) >> 4);
+                        const uint32_t id = idesc(uint32_t(nt * (kBz6R / 2)));
+                        if (b == 0)
+                            mma_bf16(d, a0 + uint64_t((s2 * kBz6Slice + ks * 256) >> 4), bd, id, acc);
+                        else if (s2 == 0)
+                            mma_bf16(d, a1 + uint64_t((ks * 256) >> 4), bd, id, acc);
+                        else
+                            mma_bf16_tmem_a(d, tmem + kBz6HalfCol * uint32_t(s2 - 1) + kBz6ACol + uint32_t(ks * 8), bd,
+                                            id, acc);
+                    };
+#pragma unroll
+                    for (int ks = 0; ks < kBz6R / 16; ks++) {
+                        prod(0, 3, ks, ks > 0 ? 1u : 0u);  // starts diagonals 0..2 at the first K-step
+                        prod(1, 2, ks, 1u);
+                        prod(2, 1, ks, 1u);
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        done0 + 8u * uint32_t(hv)));
+                }
+                if (stop) break;
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(drain));
+            if (!mbar_wait(drain, 0)) *fail = 1;
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------- workers
+        // thread (g, q): group g of the tile (= TMEM lane); amplitudes 8q..8q+7 (half 0) and
+        // 32+8q..32+8q+7 (half 1), held as v[0..7] and v[8..15]
+        const int g = tid & (kOzTG - 1), q = tid >> 7;
+        // s(w) of amplitude i, w = (i / 8) * 32 + 8 q + i % 8: s(8q) once per thread plus a
+        // parameter at a compile-time index
+        const uint64_t qoff = P.offs[8 * q];
+        auto off = [&](int i) { return qoff + P.offs[(i >> 3) * 32 + (i & 7)]; };
+        const uint32_t lane_off = uint32_t((warp & 3) * 32) << 16;
+        const uint64_t gx = expand(uint64_t(g) < P.n_groups ? uint64_t(g) : P.n_groups - 1, P.ip);
+        auto group_x0 = [&](uint64_t j, bool& valid) {
+            const uint64_t t = blockIdx.x + j * gridDim.x;
+            valid = t * kOzTG + uint64_t(g) < P.n_groups;
+            return expand(t * kOzTG, P.ip) | gx;
+        };
+        auto load = [&](uint64_t x0, float2 (&v)[kBz6Amps]) {
+            if (kPairs) {  // lowest target qubit 0: amplitudes 2k, 2k + 1 adjacent, one 128-bit load
+#pragma unroll
+                for (int i = 0; i < kBz6Amps; i += 2) {
+                    const float4 w4 = __ldcg(reinterpret_cast<const float4*>(psi + x0 + off(i)));
+                    v[i] = make_float2(w4.x, w4.y);
+                    v[i + 1] = make_float2(w4.z, w4.w);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < kBz6Amps; i++) v[i] = __ldcg(psi + x0 + off(i));
+            }
+        };
+        // slices of this thread's amplitudes into buffer b (a warp that has given up, `store`
+        // false and warp-uniform, writes nothing)
+        auto slice = [&](uint32_t b, const float2 (&v)[kBz6Amps], bool store) {
+            float m = 0.f;
+#pragma unroll
+            for (int i = 0; i < kBz6Amps; i++) m = fmaxf(m, fmaxf(fabsf(v[i].x), fabsf(v[i].y)));
+            nu_part[q * kOzTG + g] = m;
+            group_set_sync<kBz6Workers>(warp);
+            m = nu_part[g];
+#pragma unroll
+            for (int t = 1; t < kBz6TPG; t++) m = fmaxf(m, nu_part[t * kOzTG + g]);
+            const float nv = pow2_ceil(m);
+            if (!store) return nv;
+            const float inv = __uint_as_float((254u - (__float_as_uint(nv) >> 23)) << 23);
+#pragma unroll
+            for (int c = 0; c < 4; c++) {  // 4 amplitudes = K columns kb .. kb + 7
+                uint32_t pk[kBzNS][4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    float2 a[kBzNS];
+                    slice3x2(v[4 * c + i], dup2(inv), a);
+#pragma unroll
+                    for (int s2 = 0; s2 < kBzNS; s2++) pk[s2][i] = pack_bf16(a[s2].x, a[s2].y);
+                }
+                const uint32_t kb = uint32_t((c >> 1) * (kBz6R / 2) + 16 * q + 8 * (c & 1));
+                const uint32_t r = uint32_t(g);
+                const uint32_t o = (r >> 3) * kBz6Sbo + (kb >> 3) * kOzLbo + (r & 7) * 16;
+                if (b == 0) {
+#pragma unroll
+                    for (int s2 = 0; s2 < kBzNS; s2++)
+                        *reinterpret_cast<uint4*>(smem + kOff6A0 + s2 * kBz6Slice + o) =
+                            make_uint4(pk[s2][0], pk[s2][1], pk[s2][2], pk[s2][3]);
+                } else {
+                    *reinterpret_cast<uint4*>(smem + kOff6A1 + o) = make_uint4(pk[0][0], pk[0][1], pk[0][2], pk[0][3]);
+#pragma unroll
+                    for (int s2 = 1; s2 < kBzNS; s2++)
+                        asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(
+                                         tmem + lane_off + kBz6HalfCol * uint32_t(s2 - 1) + kBz6ACol + kb / 2),
+                                     "r"(pk[s2][0]), "r"(pk[s2][1]), "r"(pk[s2][2]), "r"(pk[s2][3]));
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (b != 0) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            return nv;
+        };
+        // half hv's accumulators -> outputs of this thread's 8 amplitudes of that half
+        auto epilogue = [&](int hv, uint64_t x0, bool valid, float nv) {
+            const uint32_t lane_base = tmem + lane_off + kBz6HalfCol * uint32_t(hv) + uint32_t(16 * q);
+#pragma unroll
+            for (int c = 0; c < 4; c++) {  // 4 output reals = 2 amplitudes per step
+                uint32_t r[kBzND][4];
+#pragma unroll
+                for (int d = 0; d < kBzND; d++)
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                                 : "=r"(r[d][0]), "=r"(r[d][1]), "=r"(r[d][2]), "=r"(r[d][3])
+                                 : "r"(lane_base + uint32_t(d * (kBz6R / 2) + 4 * c)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float2 o[2];
+#pragma unroll
+                for (int i = 0; i < 2; i++) {
+                    auto col = [&](int d) { return make_float2(__uint_as_float(r[d][2 * i]), __uint_as_float(r[d][2 * i + 1])); };
+                    const float2 sm = __fadd2_rn(__fadd2_rn(col(2), col(1)), col(0));
+                    o[i] = __fmul2_rn(sm, __fmul2_rn(__ldg(reinterpret_cast<const float2*>(mu + (kBz6R / 2) * hv + 16 * q + 4 * c + 2 * i)),
+                                                     dup2(nv)));
+                }
+                if (valid) {
+                    const int i0 = 8 * hv + 2 * c;  // this thread's amplitude index of the pair
+                    if (kPairs) {
+                        __stcg(reinterpret_cast<float4*>(psi + x0 + off(i0)), make_float4(o[0].x, o[0].y, o[1].x, o[1].y));
+                    } else {
+                        psi[x0 + off(i0)] = o[0];
+                        psi[x0 + off(i0 + 1)] = o[1];
+                    }
+                }
+            }
+        };
+
+        float2 v[kBz6Amps];
+        uint64_t x0_cur = 0, x0_prev = 0;
+        bool ok_cur = false, ok_prev = false;
+        float nv_prev = 1.f;
+        bool failed = false;
+        if (my_tiles > 0) {
+            x0_cur = group_x0(0, ok_cur);
+            load(x0_cur, v);
+        }
+        for (uint64_t j = 0; j <= my_tiles && my_tiles > 0; j++) {
+            if (j + 2 < my_tiles) {  // tile j + 2 into L2 (see the 5-target kernel)
+                bool ok_pf;
+                const uint64_t xp = group_x0(j + 2, ok_pf);
+#pragma unroll
+                for (int i = 0; i < kBz6Amps; i += (kPairs ? 2 : 1)) prefetch_l2(psi + xp + off(i));
+            }
+            float nv_cur = 1.f;
+            if (j < my_tiles) {
+                // buffer j & 1 was last read by the MMAs of tile j - 2, which finished before
+                // this warp summed half 1 of that tile
+                if (__any_sync(0xffffffffu, *fail != 0)) failed = true;
+                nv_cur = slice(uint32_t(j & 1), v, !failed);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0 && !failed) mbar_arrive(full0 + 8u * uint32_t(j & 1));
+            }
+            uint64_t x0_next = 0;
+            bool ok_next = false;
+            if (j + 1 < my_tiles) {
+                x0_next = group_x0(j + 1, ok_next);
+                load(x0_next, v);
+            }
+            if (j >= 1) {
+#pragma unroll
+                for (int hv = 0; hv < 2; hv++) {
+                    if (!failed) {
+                        const bool late = (P.force_late && j == 1 && hv == 0) ||
+                                          !mbar_wait_or_abort(done0 + 8u * uint32_t(hv), uint32_t((j - 1) & 1), spins, fail);
+                        if (__any_sync(0xffffffffu, late)) {
+                            failed = true;
+                            *fail = 1;
+                        }
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    if (!failed) epilogue(hv, x0_prev, ok_prev, nv_prev);
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0 && !failed) mbar_arrive(accfree0 + 8u * uint32_t(hv));
+                }
+            }
+            x0_prev = x0_cur;
+            ok_prev = ok_cur;
+            nv_prev = nv_cur;
+            x0_cur = x0_next;
+            ok_cur = ok_next;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid == 0 && s_fail) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBz6TmemCols));
+}
+
 // Per device (the current one at launch): SM count, the device-side error flag, and whether the
 // shared-memory limits of each kernel family have been raised there (function attributes are per
 // device context).
@@ -1308,10 +1615,11 @@ void launch_dense_oz5(void* psi, int n, const std::vector<int>& targets, const s
     QS_TRY_CUDA(cudaGetLastError());
 }
 
-size_t bz_matrix_bytes(int q) { return q == 5 ? Bz<5>::Mat + Bz<5>::R * 4 : Bz<6>::Mat + Bz<6>::R * 4; }
+size_t bz_matrix_bytes(int q) { return q == 5 ? Bz<5>::Mat + Bz<5>::R * 4 : kBz6Mat + kBz6R * 4; }
 
 // [B_0; B_1; B_2] (3 R x R bf16, K-major core-matrix layout) of the row-scaled real form of a
-// 2^q x 2^q matrix, then the R row scales.
+// 2^q x 2^q matrix (for q = 6 stacked per output half: [B_00; B_10; B_20; B_01; B_11; B_21]), then
+// the R row scales.
 void prepare_bz_matrix(int q, const std::vector<cplx>& K, unsigned char* host_out) {
     QS_REQUIRE(q == 5 || q == 6, "complex64 tensor-core path takes 5 or 6 targets");
     const int D = 1 << q, R = 2 * D;
@@ -1341,7 +1649,8 @@ void prepare_bz_matrix(int q, const std::vector<cplx>& K, unsigned char* host_ou
             for (int t = 0; t < kBzNS; t++) {
                 const double a = (r + magic[t]) - magic[t];
                 r -= a;
-                const int row = t * R + n;
+                // q = 5: [B_0; B_1; B_2]; q = 6: per output half h, [B_0h; B_1h; B_2h]
+                const int row = q == 5 ? t * R + n : (n / (R / 2)) * (kBzNS * (R / 2)) + t * (R / 2) + n % (R / 2);
                 const size_t off = size_t(row >> 3) * sbo + size_t(k >> 3) * kOzLbo + size_t(row & 7) * 16 +
                                    size_t(k & 7) * 2;
                 const uint16_t bits = bf16_bits_exact(a);
@@ -1395,10 +1704,40 @@ void launch_dense_bz(void* psi, int n, const std::vector<int>& targets, const st
                      const std::vector<int>& cvals, const void* dmat, cudaStream_t st) {
     QS_REQUIRE(targets.size() == 5 || targets.size() == 6, "complex64 tensor-core path takes 5 or 6 targets");
     QS_REQUIRE(std::is_sorted(targets.begin(), targets.end()), "targets must be ascending");
-    if (targets.size() == 5)
+    if (targets.size() == 5) {
         launch_bz_t<5>(psi, n, targets, controls, cvals, dmat, st);
-    else
-        launch_bz_t<6>(psi, n, targets, controls, cvals, dmat, st);
+        return;
+    }
+    OzDevice& D = oz_init();
+    if (!D.attr_bz6) {
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_bz6<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBz6Smem)));
+        QS_TRY_CUDA(cudaFuncSetAttribute(k_dense_bz6<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBz6Smem)));
+        D.attr_bz6 = true;
+    }
+    std::vector<int> fixed(targets);
+    uint64_t setmask = 0;
+    for (size_t i = 0; i < controls.size(); i++) {
+        fixed.push_back(controls[i]);
+        if (cvals[i]) setmask |= 1ull << controls[i];
+    }
+    Bz6Params P;
+    P.ip = make_index_plan(n, fixed, setmask);
+    P.n_groups = P.ip.n_iter;
+    P.wait_spins = g_oz_wait_spins.load();
+    P.force_late = g_oz_force_late.load();
+    for (int w = 0; w < kBz6D; w++) {
+        uint64_t o = 0;
+        for (int j = 0; j < 6; j++)
+            if ((w >> j) & 1) o |= 1ull << targets[j];
+        P.offs[w] = o;
+    }
+    const uint64_t n_tiles = (P.n_groups + kOzTG - 1) / kOzTG;
+    const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(n_tiles, uint64_t(D.sms))));
+    const bool pairs = targets[0] == 0 && (reinterpret_cast<uintptr_t>(psi) & 15) == 0;
+    auto kern = pairs ? k_dense_bz6<true> : k_dense_bz6<false>;
+    kern<<<grid, kBz6Threads, kBz6Smem, st>>>(reinterpret_cast<float2*>(psi), static_cast<const unsigned char*>(dmat), P,
+                                              D.err);
+    QS_TRY_CUDA(cudaGetLastError());
 }
 
 // device-side error recorded by a tensor-core kernel on the current device (a bounded wait ran
