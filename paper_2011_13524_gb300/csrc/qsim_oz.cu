@@ -844,10 +844,10 @@ __global__ void __launch_bounds__(kOz5Threads, 1) k_dense_oz5(float4* __restrict
 // and the epilogue adds them in FP32 from the smallest (one rounding to nearest, no bias) and
 // scales by mu_n nu. Error about 2^-24 of max|v| max|K~| per output, the accuracy of the FP32
 // CUDA-core kernels. Tile: 128 groups; each thread owns 16 amplitudes of a group; one slice
-// buffer. Q = 5: R = 64 reals, 256 threads, two CTAs per SM (75 KB, 256 TMEM columns each) so
-// that one CTA's MMAs overlap the other's slicing and folding. Q = 6: R = 128, 512 threads, one
-// CTA per SM (194 KB, 384 of 512 TMEM columns); the first slice's products (N = 384) take two
-// MMAs, as N is at most 256.
+// buffer. The template serves Q = 5: R = 64 reals, 256 threads, two CTAs per SM (75 KB, 256 TMEM
+// columns each) so that one CTA's MMAs overlap the other's slicing and folding. (Written for
+// Q = 6 too — R = 128, 512 threads, one CTA per SM, the first slice's N = 384 products in two
+// MMAs — but 6-target blocks run in the pipelined k_dense_bz6 below.)
 constexpr int kBzNS = 3;   // slices per operand
 constexpr int kBzND = 3;   // diagonals s + t <= 2
 template <int Q>
