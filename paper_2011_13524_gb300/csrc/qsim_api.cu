@@ -1330,9 +1330,18 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
         for (int i = c->n_gates - 1; i >= 0; i--) {
             const qs_gate& g = c->gates[i];
             const Op op = op_of_gate(g, c->n, theta);
+            // a parametric rotation joins a diagonal run when its generator is a Z string, whatever
+            // its matrix at this angle: RX(0) is the identity, but its derivative (i/2) X is not
+            // diagonal and needs the rotation step
+            bool gen_diag = true;
+            if (g.param_index >= 0) {
+                if (g.named == QS_NAMED_RX || g.named == QS_NAMED_RY) gen_diag = false;
+                if (g.named == QS_NAMED_PAULIROT)
+                    for (int j = 0; j < g.m; j++) gen_diag = gen_diag && (g.pauli[j] == 0 || g.pauli[j] == 3);
+            }
             const bool diag = op.kind == OpKind::Diag || op.kind == OpKind::Phase ||
                               (op.kind == OpKind::Pauli && op.xmask == 0);
-            const bool diag_param = g.param_index < 0 || (op.kind != OpKind::Dense && g.mc == 0);
+            const bool diag_param = g.param_index < 0 || (gen_diag && op.kind != OpKind::Dense && g.mc == 0);
             if (diag && diag_param) {
                 // bound the run by the kernel's factor, gradient and table limits (worst case);
                 // uncontrolled single-qubit diagonals share tables of up to 6 qubits

@@ -368,6 +368,65 @@ def test_adjoint_diagonal_runs(qs):
         qs.set_c128_math(old)
 
 
+def test_adjoint_cz_parities_and_wide_diagonal_runs(qs):
+    """A diagonal run whose CZ gates are grouped by qubit distance (distances 1, 3 and 5, one CZ
+    repeated so that it cancels) and whose uncontrolled single-qubit diagonals (RZ, T, S on every
+    qubit) fill more than one table of 6 qubits, between RY layers: gradients against parameter
+    shift and the energy against the oracle, in double-float, FP64 and complex64."""
+    n = 9
+    gates = [W.Gate("H", (q,)) for q in range(n)]
+    gates += [W.Gate("RY", (q,), params=(0.3 + 0.07 * q,), param_index=q) for q in range(n)]
+    gates += [W.Gate("CZ", (0, 1)), W.Gate("CZ", (2, 3)), W.Gate("CZ", (0, 1)), W.Gate("CZ", (1, 4)),
+              W.Gate("CZ", (0, 5)), W.Gate("CZ", (3, 8)), W.Gate("CZ", (4, 5)), W.Gate("CZ", (6, 7))]
+    gates += [W.Gate("RZ", (q,), params=(0.9 - 0.11 * q,), param_index=n + q) for q in range(n)]
+    gates += [W.Gate("T", (q,)) for q in range(0, n, 2)] + [W.Gate("S", (q,)) for q in range(1, n, 2)]
+    gates += [W.Gate("CZ", (q, q + 3)) for q in range(n - 3)]
+    gates += [W.Gate("RY", (q,), params=(-0.4 + 0.05 * q,), param_index=2 * n + q) for q in range(n)]
+    c = W.Circuit(n, gates, n_params=3 * n)
+    obs = W.random_pauli_observable(n, 10, 777)
+    ps = oracle.grad_parameter_shift(c, obs, list(range(c.n_params)))
+    e_ref = oracle.energy(c, obs)
+    old = qs.get_c128_math()
+    try:
+        for dtype, math_mode, tol in ((2, qs.QS_MATH_DF, 1e-11), (2, qs.QS_MATH_FP64, 1e-11), (1, qs.QS_MATH_FP64, 1e-4)):
+            qs.set_c128_math(math_mode)
+            e, g = qs.adjoint_grad(c, obs, dtype=dtype)
+            assert abs(e - e_ref) < tol, (dtype, math_mode)
+            assert np.max(np.abs(g - ps)) < tol, (dtype, math_mode, np.max(np.abs(g - ps)))
+    finally:
+        qs.set_c128_math(old)
+
+
+def test_adjoint_zero_angles(qs):
+    """Every parametric rotation at angle 0, where its matrix is the identity but its derivative
+    is not: RX, RY and an XY Pauli rotation keep their rotation steps, RZ and a ZZ Pauli rotation
+    their diagonal run, and single rotations, pairs sharing a pass and a CZ between them all give
+    the parameter-shift gradient, in double-float, FP64 and complex64."""
+    n = 6
+    gates = [W.Gate("H", (q,)) for q in range(n)]
+    gates += [W.Gate("RY", (q,), params=(0.3 + 0.1 * q,)) for q in range(n)]
+    gates += [W.Gate("RX", (0,), params=(0.0,), param_index=0), W.Gate("RY", (1,), params=(0.0,), param_index=1),
+              W.Gate("RZ", (2,), params=(0.0,), param_index=2),
+              W.Gate("PAULIROT", (3, 4), pauli=(1, 2), params=(0.0,), param_index=3),
+              W.Gate("PAULIROT", (4, 5), pauli=(3, 3), params=(0.0,), param_index=4),
+              W.Gate("CZ", (0, 5)), W.Gate("RX", (5,), params=(0.0,), param_index=5)]
+    gates += [W.Gate("RX" if q % 2 else "RY", (q,), params=(0.0,), param_index=6 + q) for q in range(n)]
+    c = W.Circuit(n, gates, n_params=6 + n)
+    obs = W.random_pauli_observable(n, 40, 70)
+    ps = oracle.grad_parameter_shift(c, obs, range(c.n_params))
+    assert np.min(np.abs(ps)) > 0.01  # no gradient of this case vanishes
+    e_ref = oracle.energy(c, obs)
+    old = qs.get_c128_math()
+    try:
+        for dtype, math_mode, tol in ((2, qs.QS_MATH_DF, 1e-11), (2, qs.QS_MATH_FP64, 1e-11), (1, qs.QS_MATH_FP64, 1e-4)):
+            qs.set_c128_math(math_mode)
+            e, g = qs.adjoint_grad(c, obs, dtype=dtype)
+            assert abs(e - e_ref) < tol, (dtype, math_mode)
+            assert np.max(np.abs(g - ps)) < tol, (dtype, math_mode, g, ps)
+    finally:
+        qs.set_c128_math(old)
+
+
 def test_adjoint_hea_n12_vs_parameter_shift(qs):
     """The hardware-efficient ansatz of the differentiation configuration at n = 12 (RY and RZ
     layers, CZ ladders): the RZ layer and the ladder form one diagonal run per layer."""
