@@ -174,6 +174,11 @@ def test_oz5_controlled_and_scaled(oz):
     ref = psi0.copy()
     oracle.apply_gate(ref, n, g)
     assert maxabs(run_one(qs, n, g, psi0), ref) < 1e-12
+    # unsorted targets including qubits 0, 1 and 2 (the paired 32-byte accesses), control value 0
+    g = W.Gate("DENSE", (9, 2, 0, 6, 1), controls=(4,), control_values=(0,), matrix=W.random_unitary(32, rng))
+    ref = psi0.copy()
+    oracle.apply_gate(ref, n, g)
+    assert maxabs(run_one(qs, n, g, psi0), ref) < 1e-12
     psi1 = psi0.copy()
     psi1[: 1 << 9] *= 1e-6
     psi1[1 << 11: 1 << 12] = 0.0
