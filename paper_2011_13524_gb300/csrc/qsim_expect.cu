@@ -239,38 +239,50 @@ __device__ __forceinline__ void re_sum_packed(const E* tile, uint32_t tb, uint32
     o[0] = tb;
 #pragma unroll
     for (int k = 1; k < 8; k++) o[k] = o[k ^ (1 << top_bit(k))] | im[top_bit(k)];
-    float S = 0.f;
+    // hi x hi products (kept for the cut below) and the sum of their magnitudes as a tree: the
+    // eight pairs are independent until the sums, which take three levels instead of a chain
+    float2 P[8];
+    float t[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) {
         const E a = tile[o[k]], b = tile[o[k] ^ f];
-        const float2 P = __fmul2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
-        S = __fadd_rn(__fadd_rn(S, fabsf(P.x)), fabsf(P.y));
+        P[k] = __fmul2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+        t[k] = __fadd_rn(fabsf(P[k].x), fabsf(P[k].y));
     }
-    uint32_t e = (__float_as_uint(S) >> 23) & 0xFFu;
+#pragma unroll
+    for (int s = 1; s < 8; s <<= 1)
+#pragma unroll
+        for (int k = 0; k < 8; k += 2 * s) t[k] = __fadd_rn(t[k], t[k + s]);
+    uint32_t e = (__float_as_uint(t[0]) >> 23) & 0xFFu;
     e = e > 250u ? 250u : e;
     const float c = __uint_as_float(((e + 2u) << 23) | 0x400000u);  // 1.5 * 2^(e - 125) > 3 S
     const float2 C2 = make_float2(c, c), NC2 = make_float2(-c, -c), M1 = make_float2(-1.f, -1.f);
-    float2 HS = make_float2(0.f, 0.f), LS = make_float2(0.f, 0.f);
+    float2 H[8], L[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) {
         const E a = tile[o[k]], b = tile[o[k] ^ f];
         const float2 ah = make_float2(a.x, a.y), bh = make_float2(b.x, b.y);
-        const float2 P = __fmul2_rn(ah, bh);
-        const float2 T = __fadd2_rn(P, C2);
-        const float2 H = __fadd2_rn(T, NC2);
+        const float2 T = __fadd2_rn(P[k], C2);
+        H[k] = __fadd2_rn(T, NC2);
         const float2 NH = __ffma2_rn(T, M1, C2);  // c - T = -H exactly
-        float2 L = __ffma2_rn(ah, bh, NH);        // a b - H (one rounding, far below the grid's unit)
+        L[k] = __ffma2_rn(ah, bh, NH);            // a b - H (one rounding, far below the grid's unit)
         if constexpr (kLo) {
             const float4& a4 = reinterpret_cast<const float4&>(a);
             const float4& b4 = reinterpret_cast<const float4&>(b);
-            L = __ffma2_rn(ah, make_float2(b4.z, b4.w), L);
-            L = __ffma2_rn(make_float2(a4.z, a4.w), bh, L);
+            L[k] = __ffma2_rn(ah, make_float2(b4.z, b4.w), L[k]);
+            L[k] = __ffma2_rn(make_float2(a4.z, a4.w), bh, L[k]);
         }
-        HS = __fadd2_rn(HS, H);
-        LS = __fadd2_rn(LS, L);
     }
-    h = __fadd_rn(HS.x, HS.y);  // both on the grid: exact
-    l = __fadd_rn(LS.x, LS.y);
+    // the H sum is exact in any order (multiples of the grid's unit, far below 2^24 of it)
+#pragma unroll
+    for (int s = 1; s < 8; s <<= 1)
+#pragma unroll
+        for (int k = 0; k < 8; k += 2 * s) {
+            H[k] = __fadd2_rn(H[k], H[k + s]);
+            L[k] = __fadd2_rn(L[k], L[k + s]);
+        }
+    h = __fadd_rn(H[0].x, H[0].y);  // both on the grid: exact
+    l = __fadd_rn(L[0].x, L[0].y);
 }
 
 template <typename E, bool kLo, int kKind>
@@ -322,9 +334,8 @@ __device__ __forceinline__ uint32_t thread_slot(uint32_t tid, uint32_t ex) {
 // independent arithmetic interleaves
 template <typename E, bool kLo>
 __device__ __forceinline__ void tile_group_pair_re(const TileGroup& G1, const TileGroup& G2, const TileSlot* S,
-                                                   const E* tile, const float2* gam, uint32_t tid, float& ah,
-                                                   float& al) {
-    const uint32_t tb1 = thread_slot(tid, G1.excl), tb2 = thread_slot(tid, G2.excl);
+                                                   const E* tile, const float2* gam, uint32_t tid, uint32_t tb1,
+                                                   uint32_t tb2, float& ah, float& al) {
     uint32_t im1[4], im2[4];
 #pragma unroll
     for (int i = 0; i < 4; i++) {
@@ -341,8 +352,7 @@ __device__ __forceinline__ void tile_group_pair_re(const TileGroup& G1, const Ti
 // one group's contribution from the tile in shared memory
 template <typename E, bool kLo>
 __device__ __forceinline__ void tile_group(const TileGroup& G, const TileSlot* __restrict__ S, const E* tile,
-                                           const float2* gam, uint32_t tid, float& ah, float& al) {
-    const uint32_t tb = thread_slot(tid, G.excl);
+                                           const float2* gam, uint32_t tid, uint32_t tb, float& ah, float& al) {
     switch (G.kind) {
         case kTileDiag: group_kind<E, kLo, kTileDiag>(G, S, tile, gam, tid, tb, ah, al); break;
         case kTileRe: group_kind<E, kLo, kTileRe>(G, S, tile, gam, tid, tb, ah, al); break;
@@ -360,7 +370,7 @@ __device__ __forceinline__ uint64_t deposit64(uint64_t x, uint64_t mask) {
 
 constexpr size_t tile_smem_bytes(size_t elem) {
     return elem * kTileAmps + sizeof(float2) * kTileMaxSlots + sizeof(TileSlot) * kTileMaxSlots +
-           sizeof(TileTerm) * kTileMaxTerms;
+           sizeof(TileTerm) * kTileMaxTerms + sizeof(uint16_t) * kTileMaxGroups * kTileThreads;
 }
 
 template <typename C>
@@ -373,9 +383,12 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_expect_tiled(const C* __res
     float2* gam = reinterpret_cast<float2*>(tsm + sizeof(E) * kTileAmps);
     TileSlot* slots = reinterpret_cast<TileSlot*>(gam + kTileMaxSlots);
     TileTerm* terms = reinterpret_cast<TileTerm*>(slots + kTileMaxSlots);
+    // tile slot of each group's item 0 for each thread, formed once (the same for every tile)
+    uint16_t* tbt = reinterpret_cast<uint16_t*>(terms + kTileMaxTerms);
     const uint32_t tid = threadIdx.x;
     for (int i = tid; i < P.nslots; i += kTileThreads) slots[i] = P.s[i];
     for (int i = tid; i < P.nterms; i += kTileThreads) terms[i] = P.t[i];
+    for (int g = 0; g < P.ngroups; g++) tbt[g * kTileThreads + tid] = uint16_t(thread_slot(tid, P.g[g].excl));
     const int namps = 1 << P.b;
     uint64_t dthr = 0;
     for (int i = 0; i < 8 && i < P.b; i++)
@@ -418,10 +431,11 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_expect_tiled(const C* __res
         for (int g = 0; g < P.ngroups;) {
             const TileGroup& G = P.g[g];
             if (g + 1 < P.ngroups && G.kind == kTileRe && !G.wht && P.g[g + 1].kind == kTileRe && !P.g[g + 1].wht) {
-                tile_group_pair_re<E, TileElem<C>::kLo>(G, P.g[g + 1], slots, tile, gam, tid, ah, al);
+                tile_group_pair_re<E, TileElem<C>::kLo>(G, P.g[g + 1], slots, tile, gam, tid, tbt[g * kTileThreads + tid],
+                                                        tbt[(g + 1) * kTileThreads + tid], ah, al);
                 g += 2;
             } else {
-                tile_group<E, TileElem<C>::kLo>(G, slots, tile, gam, tid, ah, al);
+                tile_group<E, TileElem<C>::kLo>(G, slots, tile, gam, tid, tbt[g * kTileThreads + tid], ah, al);
                 g += 1;
             }
         }
