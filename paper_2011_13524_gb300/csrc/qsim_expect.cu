@@ -226,27 +226,27 @@ __device__ __forceinline__ void slot_sums(const TileGroup& G, const TileSlot* S,
     }
 }
 
-// The plain sum over the thread's 8 pair representatives of Re A = a.re b.re + a.im b.im
-// (A = conj(b) a, b = psi_{y^f}), as (h, l), with the products of the real and imaginary parts
-// as packed pairs. A grid above three times the thread's sum of |hi x hi| products is chosen
-// first (as grid_transform does); each hi product P is then cut into H = RN(P + c) - c, exact on
-// the grid, whose sum is exact, and the rest a b - H, formed by one FMA with -H (exactly -H as
-// c - RN(P + c)) plus the hi x lo cross products, summed in FP32 (it is below the grid's unit).
-template <typename E, bool kLo>
-__device__ __forceinline__ void re_sum_packed(const E* tile, uint32_t tb, uint32_t f, const uint32_t* im, float& h,
-                                              float& l) {
-    uint32_t o[8];
-    o[0] = tb;
-#pragma unroll
-    for (int k = 1; k < 8; k++) o[k] = o[k ^ (1 << top_bit(k))] | im[top_bit(k)];
+// The plain sum over the thread's 8 items of b.re c.re + b.im c.im (kIm false) or
+// b.re c.im - b.im c.re (kIm true), b = tb_[o[k]] and c = tc_[o[k] ^ f], as (h, l), with the two
+// products of each item as a packed pair. A grid above three times the thread's sum of |hi x hi|
+// products is chosen first (as grid_transform does); each hi product P is then cut into
+// H = RN(P + c) - c, exact on the grid, whose sum is exact, and the rest b c - H, formed by one FMA
+// with -H (exactly -H as c - RN(P + c)) plus the hi x lo cross products, summed in FP32 (it is
+// below the grid's unit). The expectation's pair sums Re A (A = conj(psi_{y^f}) psi_y) and the
+// transition amplitude's Re and Im of conj(bra_y) ket_{y^f} are such sums.
+template <typename E, bool kLo, bool kIm>
+__device__ __forceinline__ void cross_sum_packed(const E* tb_, const E* tc_, const uint32_t (&o)[8], uint32_t f,
+                                                 float& h, float& l) {
+    // operand pairs: (b.re, b.im) times (c.re, c.im), or (c.im, c.re) for the imaginary part
+    auto cs = [](const E& c) { return kIm ? make_float2(c.y, c.x) : make_float2(c.x, c.y); };
     // hi x hi products (kept for the cut below) and the sum of their magnitudes as a tree: the
-    // eight pairs are independent until the sums, which take three levels instead of a chain
+    // eight items are independent until the sums, which take three levels instead of a chain
     float2 P[8];
     float t[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) {
-        const E a = tile[o[k]], b = tile[o[k] ^ f];
-        P[k] = __fmul2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y));
+        const E b = tb_[o[k]], c = tc_[o[k] ^ f];
+        P[k] = __fmul2_rn(make_float2(b.x, b.y), cs(c));
         t[k] = __fadd_rn(fabsf(P[k].x), fabsf(P[k].y));
     }
 #pragma unroll
@@ -260,17 +260,17 @@ __device__ __forceinline__ void re_sum_packed(const E* tile, uint32_t tb, uint32
     float2 H[8], L[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) {
-        const E a = tile[o[k]], b = tile[o[k] ^ f];
-        const float2 ah = make_float2(a.x, a.y), bh = make_float2(b.x, b.y);
+        const E b = tb_[o[k]], cc = tc_[o[k] ^ f];
+        const float2 bh = make_float2(b.x, b.y), ch = cs(cc);
         const float2 T = __fadd2_rn(P[k], C2);
         H[k] = __fadd2_rn(T, NC2);
         const float2 NH = __ffma2_rn(T, M1, C2);  // c - T = -H exactly
-        L[k] = __ffma2_rn(ah, bh, NH);            // a b - H (one rounding, far below the grid's unit)
+        L[k] = __ffma2_rn(bh, ch, NH);            // b c - H (one rounding, far below the grid's unit)
         if constexpr (kLo) {
-            const float4& a4 = reinterpret_cast<const float4&>(a);
             const float4& b4 = reinterpret_cast<const float4&>(b);
-            L[k] = __ffma2_rn(ah, make_float2(b4.z, b4.w), L[k]);
-            L[k] = __ffma2_rn(make_float2(a4.z, a4.w), bh, L[k]);
+            const float4& c4 = reinterpret_cast<const float4&>(cc);
+            L[k] = __ffma2_rn(bh, kIm ? make_float2(c4.w, c4.z) : make_float2(c4.z, c4.w), L[k]);
+            L[k] = __ffma2_rn(make_float2(b4.z, b4.w), ch, L[k]);
         }
     }
     // the H sum is exact in any order (multiples of the grid's unit, far below 2^24 of it)
@@ -281,8 +281,18 @@ __device__ __forceinline__ void re_sum_packed(const E* tile, uint32_t tb, uint32
             H[k] = __fadd2_rn(H[k], H[k + s]);
             L[k] = __fadd2_rn(L[k], L[k + s]);
         }
-    h = __fadd_rn(H[0].x, H[0].y);  // both on the grid: exact
-    l = __fadd_rn(L[0].x, L[0].y);
+    h = kIm ? __fsub_rn(H[0].x, H[0].y) : __fadd_rn(H[0].x, H[0].y);  // both on the grid: exact
+    l = kIm ? __fsub_rn(L[0].x, L[0].y) : __fadd_rn(L[0].x, L[0].y);
+}
+
+template <typename E, bool kLo>
+__device__ __forceinline__ void re_sum_packed(const E* tile, uint32_t tb, uint32_t f, const uint32_t* im, float& h,
+                                              float& l) {
+    uint32_t o[8];
+    o[0] = tb;
+#pragma unroll
+    for (int k = 1; k < 8; k++) o[k] = o[k ^ (1 << top_bit(k))] | im[top_bit(k)];
+    cross_sum_packed<E, kLo, false>(tile, tile, o, f, h, l);
 }
 
 template <typename E, bool kLo, int kKind>
@@ -580,14 +590,20 @@ __device__ __forceinline__ void trans_slot_sums(const TileGroup& G, const TileSl
 
 template <typename E, bool kLo>
 __device__ __forceinline__ void trans_group(const TileGroup& G, const TileSlot* S, const E* tbra, const E* tket,
-                                            const float2* gam, uint32_t tid, float& rh, float& rl, float& ih,
-                                            float& il) {
-    const uint32_t tb = thread_slot3(tid, G.excl);
+                                            const float2* gam, uint32_t tid, uint32_t tb, float& rh, float& rl,
+                                            float& ih, float& il) {
     const uint32_t f = G.f;
     uint32_t o[8];
     o[0] = tb;
 #pragma unroll
     for (int k = 1; k < 8; k++) o[k] = o[k ^ (1 << top_bit(k))] | G.imask[top_bit(k)];
+    if (!G.wht) {  // every slot uses the plain sums: packed pairs
+        float qr[1], qrl[1], qi[1], qil[1];
+        cross_sum_packed<E, kLo, false>(tbra, tket, o, f, qr[0], qrl[0]);
+        cross_sum_packed<E, kLo, true>(tbra, tket, o, f, qi[0], qil[0]);
+        trans_slot_sums<0, 1>(G, S, gam, tid, qr, qrl, qi, qil, rh, rl, ih, il);
+        return;
+    }
     float qr[8], qrl[8], qi[8], qil[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) {
@@ -596,18 +612,14 @@ __device__ __forceinline__ void trans_group(const TileGroup& G, const TileSlot* 
         df_dot2<kLo>(b.rh, b.rl, c.rh, c.rl, b.ih, b.il, c.ih, c.il, qr[k], qrl[k]);
         df_dot2<kLo>(b.rh, b.rl, c.ih, c.il, -b.ih, -b.il, c.rh, c.rl, qi[k], qil[k]);
     }
-    const bool full = G.wht != 0;
-    grid_transform<8>(qr, qrl, full);
-    grid_transform<8>(qi, qil, full);
-    if (full)
-        trans_slot_sums<0, 8>(G, S, gam, tid, qr, qrl, qi, qil, rh, rl, ih, il);
-    else
-        trans_slot_sums<0, 1>(G, S, gam, tid, qr, qrl, qi, qil, rh, rl, ih, il);
+    grid_transform<8>(qr, qrl, true);
+    grid_transform<8>(qi, qil, true);
+    trans_slot_sums<0, 8>(G, S, gam, tid, qr, qrl, qi, qil, rh, rl, ih, il);
 }
 
 constexpr size_t trans_smem_bytes(size_t elem) {
     return 2 * elem * (size_t(1) << kTransBits) + sizeof(float2) * kTileMaxSlots + sizeof(TileSlot) * kTileMaxSlots +
-           sizeof(TileTerm) * kTileMaxTerms;
+           sizeof(TileTerm) * kTileMaxTerms + sizeof(uint16_t) * kTileMaxGroups * kTileThreads;
 }
 
 template <typename C>
@@ -623,9 +635,12 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_transition_tiled(const C* _
     float2* gam = reinterpret_cast<float2*>(tket + kA);
     TileSlot* slots = reinterpret_cast<TileSlot*>(gam + kTileMaxSlots);
     TileTerm* terms = reinterpret_cast<TileTerm*>(slots + kTileMaxSlots);
+    // tile slot of each group's item 0 for each thread, formed once (the same for every tile)
+    uint16_t* tbt = reinterpret_cast<uint16_t*>(terms + kTileMaxTerms);
     const uint32_t tid = threadIdx.x;
     for (int i = tid; i < P.nslots; i += kTileThreads) slots[i] = P.s[i];
     for (int i = tid; i < P.nterms; i += kTileThreads) terms[i] = P.t[i];
+    for (int g = 0; g < P.ngroups; g++) tbt[g * kTileThreads + tid] = uint16_t(thread_slot3(tid, P.g[g].excl));
     const int namps = 1 << P.b;
     for (int j = namps + int(tid); j < kA; j += kTileThreads) {
         tbra[j] = E{};
@@ -676,7 +691,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_transition_tiled(const C* _
         __syncthreads();
         float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
         for (int g = 0; g < P.ngroups; g++)
-            trans_group<E, TileElem<C>::kLo>(P.g[g], slots, tbra, tket, gam, tid, rh, rl, ih, il);
+            trans_group<E, TileElem<C>::kLo>(P.g[g], slots, tbra, tket, gam, tid, tbt[g * kTileThreads + tid], rh, rl,
+                                             ih, il);
         accr += widen_float_int(rh) + widen_float_int(rl);
         acci += widen_float_int(ih) + widen_float_int(il);
         rbase = ((rbase | ~P.rest_mask) + step) & P.rest_mask;
