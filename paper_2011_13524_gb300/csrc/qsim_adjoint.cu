@@ -292,6 +292,45 @@ __device__ __forceinline__ RedSum<NativeArith<double>> im_conj_prod(double2 l, d
     return w;
 }
 
+// The Walsh-Hadamard transform of one value per lane: lane l ends with the sum over lanes s of
+// (-1)^{popc(s & l)} v_s (five butterfly stages across the warp, (a + b, a - b) per lane pair).
+template <typename P>
+__device__ __forceinline__ RedSum<P> lane_wht(RedSum<P> v, int lane) {
+#pragma unroll
+    for (int m = 1; m < 32; m <<= 1) {
+        RedSum<P> o;
+        o.s = __shfl_xor_sync(0xffffffffu, v.s, m);
+        o.c = __shfl_xor_sync(0xffffffffu, v.c, m);
+        const bool hi = (lane & m) != 0;  // this lane takes o - v, its partner v + o
+        RedSum<P> r = hi ? o : v;
+        r.add(hi ? v : o, hi);
+        v = r;
+    }
+    return v;
+}
+template <>
+__device__ __forceinline__ RedSum<NativeArith<double>> lane_wht(RedSum<NativeArith<double>> v, int lane) {
+#pragma unroll
+    for (int m = 1; m < 32; m <<= 1) {
+        const double o = __shfl_xor_sync(0xffffffffu, v.v, m);
+        v.v = (lane & m) ? o - v.v : v.v + o;
+    }
+    return v;
+}
+template <typename P>
+__device__ __forceinline__ RedSum<P> lane_fetch(const RedSum<P>& v, int src) {
+    RedSum<P> o;
+    o.s = __shfl_sync(0xffffffffu, v.s, src);
+    o.c = __shfl_sync(0xffffffffu, v.c, src);
+    return o;
+}
+template <>
+__device__ __forceinline__ RedSum<NativeArith<double>> lane_fetch(const RedSum<NativeArith<double>>& v, int src) {
+    RedSum<NativeArith<double>> o;
+    o.v = __shfl_sync(0xffffffffu, v.v, src);
+    return o;
+}
+
 __device__ __forceinline__ float4 kmul(float4 a, float4 b) { return DFArith::out(DFArith::first(a, b)); }
 __device__ __forceinline__ float2 kmul(float2 a, float2 b) { return cmul(a, b); }
 __device__ __forceinline__ double2 kmul(double2 a, double2 b) { return cmul(a, b); }
@@ -306,10 +345,11 @@ __device__ __forceinline__ double2 kone<double2>() { return make_double2(1.0, 0.
 
 constexpr int kDiagKA = 4;  // amplitudes per thread between two gradient flushes
 
-// Thread t of T = grid x 256 threads takes the amplitudes x = j T + t. Between flushes it keeps
-// one running sum of Im(conj(lam_x) psi_x) per j (kDiagKA of them); at a flush the warp's sums go
-// through shared memory and lane g adds every one of them with the sign (-1)^popc(x & gz[g]) of
-// its own gradient term, so the per-amplitude cost does not grow with the number of gradients.
+// Thread t of T = grid x 256 threads takes the amplitudes x = j T + t, kDiagKA values of j at a
+// time, each giving w_x = Im(conj(lam_x) psi_x). Per j the warp transforms its 32 values
+// (Walsh-Hadamard across the lanes), and lane g takes the coefficient at its gradient term's Z
+// bits among the lane bits, with the sign of the rest of the term's Z bits: every term of the
+// run from one transform, so the per-amplitude cost does not grow with the number of gradients.
 template <typename P>
 __global__ void __launch_bounds__(kAdjThreads) k_adj_diag(typename P::C* __restrict__ psi, typename P::C* __restrict__ lam,
                                                            const typename P::K* __restrict__ tab,
@@ -319,8 +359,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_diag(typename P::C* __restr
     using R = RedSum<P>;
     extern __shared__ __align__(16) unsigned char adj_smem[];
     K* stab = reinterpret_cast<K*>(adj_smem);
-    R* red = reinterpret_cast<R*>(adj_smem + ((size_t(A.ntab) * sizeof(K) + 15) & ~size_t(15)));  // [warp][lane][j]
-    R* wred = red + (kAdjThreads / 32) * 32 * kDiagKA;                                             // [warp][g]
+    R* wred = reinterpret_cast<R*>(adj_smem + ((size_t(A.ntab) * sizeof(K) + 15) & ~size_t(15)));  // [warp][g]
     for (int i = threadIdx.x; i < A.ntab; i += kAdjThreads) stab[i] = tab[i];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -329,7 +368,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_diag(typename P::C* __restr
     const uint64_t J = (A.n_amp + T - 1) / T;
     const uint64_t gz = lane < A.ng ? A.gz[lane] : 0;
     R gsum;  // lane g: this warp's sum for gradient term g
-    R* myred = red + (size_t(warp) * 32) * kDiagKA;
+    const uint64_t t0 = t - uint64_t(lane);  // the warp's first thread
     for (uint64_t j0 = 0; j0 < J; j0 += kDiagKA) {
         R acc[kDiagKA];
 #pragma unroll
@@ -364,19 +403,16 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_diag(typename P::C* __restr
             lam[x] = l;
         }
         if (A.ng) {
+            // gradient term g over the warp's 32 amplitudes of item j, x = (j0 + j) T + t0 + s:
+            // the lane bits s, the warp's bits of t0 and the item's bits of (j0 + j) T are
+            // disjoint (T is a power of two), so the sign (-1)^{popc(x & z_g)} factors into
+            // (-1)^{popc(s & z_g)}, whose sum over s is the warp's Walsh-Hadamard coefficient at
+            // z_g mod 32, times the sign of the rest
 #pragma unroll
-            for (int j = 0; j < kDiagKA; j++) myred[lane * kDiagKA + j] = acc[j];
-            __syncwarp();
-            if (lane < A.ng) {
-                const uint64_t t0 = t - uint64_t(lane);
-                for (int src = 0; src < 32; src++)
-#pragma unroll
-                    for (int j = 0; j < kDiagKA; j++) {
-                        const uint64_t x = (j0 + j) * T + t0 + uint64_t(src);
-                        gsum.add(myred[src * kDiagKA + j], parity64(x & gz) != 0);
-                    }
+            for (int j = 0; j < kDiagKA; j++) {
+                const R w = lane_fetch(lane_wht(acc[j], lane), int(gz & 31u));
+                if (lane < A.ng && j0 + j < J) gsum.add(w, parity64(((j0 + j) * T + t0) & gz) != 0);
             }
-            __syncwarp();
         }
     }
     if (A.ng) {
@@ -392,7 +428,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_diag(typename P::C* __restr
 
 size_t adj_diag_smem(int ntab, Arith ar) {
     const size_t rs = ar == Arith::F64 ? sizeof(double) : 2 * sizeof(float);
-    return ((size_t(ntab) * kernel_entry_bytes(ar) + 15) & ~size_t(15)) + rs * (kAdjThreads / 32) * 32 * (kDiagKA + 1);
+    return ((size_t(ntab) * kernel_entry_bytes(ar) + 15) & ~size_t(15)) + rs * (kAdjThreads / 32) * 32;
 }
 
 // R_P(theta)^+ = cos(theta/2) I - i sin(theta/2) P as a row-major 2x2 matrix
