@@ -54,6 +54,61 @@ struct GradAcc<DFArith> {
     __device__ double imag() const { return double(s) + double(c); }
 };
 
+// the imaginary part of an FP32-pair gradient accumulator as its unevaluated pair (s, c)
+__device__ __forceinline__ void acc_pair(const GradAcc<DFArith>& g, float& s, float& c) {
+    s = g.s;
+    c = g.c;
+}
+__device__ __forceinline__ void acc_pair(const GradAcc<NativeArith<float>>& g, float& s, float& c) {
+    s = g.im.hi;
+    c = g.im.lo;
+}
+
+// Block sums of NR gradient partials, to part[r * gridDim.x + blockIdx.x]. FP32-pair
+// accumulators are summed across each warp as FP32 pairs (TwoSum), and only the eight warp sums in
+// FP64: GB300's FP64 rate made the warp stages of a double sum several microseconds per launch.
+// One barrier for all NR sums. The order is fixed, so results are reproducible.
+template <typename P, int NR>
+__device__ __forceinline__ void grad_block_sums(const GradAcc<P> (&g)[NR], double* part) {
+    __shared__ double sh[NR][kAdjThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double wv[NR];
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+        if constexpr (std::is_same<P, NativeArith<double>>::value) {
+            double v = g[r].imag();
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            wv[r] = v;
+        } else {
+            float s, c;
+            acc_pair(g[r], s, c);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float os = __shfl_down_sync(0xffffffffu, s, o), oc = __shfl_down_sync(0xffffffffu, c, o);
+                float h, e;
+                DFArith::two_sum(s, os, h, e);
+                s = h;
+                c = __fadd_rn(c, __fadd_rn(oc, e));
+            }
+            wv[r] = double(s) + double(c);
+        }
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int r = 0; r < NR; r++) sh[r][wid] = wv[r];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+            double v = lane < kAdjThreads / 32 ? sh[r][lane] : 0.0;
+#pragma unroll
+            for (int o = kAdjThreads / 64; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) part[size_t(r) * gridDim.x + blockIdx.x] = v;
+        }
+    }
+}
+
 template <typename P>
 struct AdjRotParams {
     IndexPlan ip;            // pivot bit = the rotation's qubit
@@ -92,9 +147,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rot(typename P::C* __restri
         lam[i0] = P::out(s0);
         lam[i1] = P::out(s1);
     }
-    __shared__ double sh[kAdjThreads / 32];
-    const double v = block_sum<kAdjThreads>(g.imag(), sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = v;
+    const GradAcc<P> ga[1] = {g};
+    grad_block_sums<P, 1>(ga, part);
 }
 
 // NR consecutive reverse steps (2 to 4) for rotations on distinct qubits q_0 (the latest in the
@@ -193,8 +247,9 @@ __device__ __forceinline__ void rot_step<DFArith>(float4& a, float4& b, float4& 
     df_rot_pair(la, lb, axis, ch, cl, sh, sl);
 }
 
+// Four CTAs per SM (64 registers; a few bytes spill): 8.37 -> 8.05 ms for the n = 20 HEA gradient.
 template <typename P, int NR>
-__global__ void __launch_bounds__(kAdjThreads) k_adj_rotn(typename P::C* __restrict__ psi, typename P::C* __restrict__ lam,
+__global__ void __launch_bounds__(kAdjThreads, 4) k_adj_rotn(typename P::C* __restrict__ psi, typename P::C* __restrict__ lam,
                                                            const __grid_constant__ AdjRotNParams<P, NR> A, double* part) {
     using C = typename P::C;
     constexpr int E = 1 << NR;
@@ -228,12 +283,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_rotn(typename P::C* __restr
             lam[ix[e]] = l[e];
         }
     }
-    __shared__ double sh[kAdjThreads / 32];
-#pragma unroll
-    for (int r = 0; r < NR; r++) {
-        const double val = block_sum<kAdjThreads>(g[r].imag(), sh);
-        if (threadIdx.x == 0) part[size_t(r) * gridDim.x + blockIdx.x] = val;
-    }
+    grad_block_sums<P, NR>(g, part);
 }
 
 // out[s] = sum of part[s * nb .. s * nb + nb) in a fixed order, one block per slot
