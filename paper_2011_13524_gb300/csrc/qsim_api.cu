@@ -1170,21 +1170,6 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
         launch_set_basis_arith(psi->data, c->n, Arith::DF, 0, st);
     }
     const Arith ar = arith_of(psi);
-    // forward: psi = U_G ... U_1 |0>, fused (the partition of a circuit structure is cached, so
-    // repeated calls with new angles only rebuild the block matrices)
-    // (tensor-core widths: 5 for double-float, 6 for complex64; the CUDA-core kernels' own)
-    const int kf = ar == Arith::DF && tensor_c128_enabled()     ? 5
-                   : ar == Arith::F32 && tensor_c64x_enabled() ? 6
-                   : ar == Arith::F32                           ? 4
-                                                                : 2;
-    apply_plan(psi, plan_fusion(c, kf, theta));
-    // lambda = H psi ; E = Re <psi|lambda>
-    launch_apply_observable(groups, psi->data, lam->data, c->n, ar, st);
-    double e2[2];
-    reduce_inner(psi, lam, e2);
-    *energy = e2[0];
-    for (int p = 0; p < c->n_params; p++) grad[p] = 0.0;
-
     // The reverse sweep as steps: single-qubit X/Y rotations use the fused reverse step
     // (gradient partials + un-apply in one pass); maximal runs of diagonal gates (CZ, phases,
     // RZ and Z-string rotations, diagonal gates) take one pass for the whole run; other gates
@@ -1206,200 +1191,233 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
     std::vector<Step> steps;
     std::vector<cplx> tabs;         // every run's tables, in order
     int nslots = 0;
-    {
-        std::vector<int> run;       // gate indices, reverse order
-        int run_f = 0, run_g = 0, run_t = 0;  // its factor, gradient and table-entry bounds
-        uint64_t run_sq = 0;        // qubits of its uncontrolled single-qubit diagonals (tables of 6)
-        auto single_entries = [](uint64_t q) {
-            const int k = __builtin_popcountll(q);
-            return (k / 6) * 64 + (k % 6 ? 1 << (k % 6) : 0);
-        };
-        auto flush = [&]() {
-            run_f = run_g = run_t = 0;
-            run_sq = 0;
-            if (run.empty()) return;
-            Step stp;
-            stp.kind = 1;
-            stp.slot0 = nslots;
-            stp.diag = std::make_shared<AdjDiagParams>();
-            AdjDiagParams& A = *stp.diag;
-            A.n_amp = 1ull << c->n;
-            stp.tab_byte = tabs.size();
-            // single-qubit uncontrolled diagonals multiply into per-qubit pairs, then into tables
-            // over up to 4 qubits; every other diagonal keeps a factor of its own
-            std::map<int, std::pair<cplx, cplx>> one;
-            int ntab = 0;
-            auto add_factor = [&](const AdjDiagFactor& f, const std::vector<cplx>& t) {
-                QS_REQUIRE(A.nf < kAdjDiagMaxF, "diagonal run too long");
-                AdjDiagFactor g = f;
-                if (!t.empty()) {
-                    g.tab_off = ntab;
-                    for (const cplx& v : t) tabs.push_back(v);
-                    ntab += int(t.size());
-                }
-                A.f[A.nf++] = g;
-            };
-            for (int gi : run) {
-                const qs_gate& g = c->gates[gi];
-                Op op = dagger(op_of_gate(g, c->n, theta));
-                if (g.param_index >= 0) {
-                    uint64_t zm = 0;
-                    for (int j = 0; j < g.m; j++)
-                        if (g.kind == QS_GATE_NAMED && g.named == QS_NAMED_RZ) zm |= 1ull << g.targets[j];
-                        else if (g.pauli[j] == 3) zm |= 1ull << g.targets[j];
-                    A.gz[A.ng++] = zm;
-                    stp.params.push_back(g.param_index);
-                }
-                uint64_t cm = 0, cv = 0;
-                for (size_t j = 0; j < op.controls.size(); j++) {
-                    cm |= 1ull << op.controls[j];
-                    if (op.cvals[j]) cv |= 1ull << op.controls[j];
-                }
-                AdjDiagFactor f;
-                f.cond_mask = cm;
-                f.cond_val = cv;
-                if (op.kind == OpKind::Pauli) {
-                    f.zmask = op.zmask;
-                    add_factor(f, {});
-                } else if (op.kind == OpKind::Phase) {
-                    if (op.phase == cplx(-1.0, 0.0)) {
-                        f.sign_only = 1;
-                        add_factor(f, {});
-                    } else if (op.phase != cplx(1.0, 0.0)) {
-                        add_factor(f, {op.phase});
-                    }
-                } else if (op.targets.size() == 1 && cm == 0) {
-                    auto it = one.find(op.targets[0]);
-                    if (it == one.end()) one[op.targets[0]] = {op.data[0], op.data[1]};
-                    else it->second = {it->second.first * op.data[0], it->second.second * op.data[1]};
-                } else {
-                    f.nq = int(op.targets.size());
-                    for (int j = 0; j < f.nq; j++) f.q[j] = op.targets[j];
-                    add_factor(f, op.data);
-                }
-            }
-            // CZ gates (a -1 on the subspace where both of two qubits are 1, no other condition)
-            // with the same qubit distance d share one factor: the parity of x & (x >> d) over
-            // their lower qubits
+    // The steps depend only on the circuit and the angles: a host thread builds them while this
+    // one plans and launches the forward pass and the energy (joined before the sweep, and on
+    // every way out of this scope).
+    std::exception_ptr step_err;
+    std::thread step_builder([&]() {
+        try {
             {
-                std::map<int, uint64_t> pairs;
-                std::vector<AdjDiagFactor> keep;
-                for (int k = 0; k < A.nf; k++) {
-                    const AdjDiagFactor& g = A.f[k];
-                    if (g.sign_only && g.zmask == 0 && g.tab_off < 0 && __builtin_popcountll(g.cond_mask) == 2 &&
-                        g.cond_val == g.cond_mask) {
-                        const int a = __builtin_ctzll(g.cond_mask), b = 63 - __builtin_clzll(g.cond_mask);
-                        uint64_t& m = pairs[b - a];
-                        if (!((m >> a) & 1)) {
-                            m |= 1ull << a;
-                            continue;
+                std::vector<int> run;       // gate indices, reverse order
+                int run_f = 0, run_g = 0, run_t = 0;  // its factor, gradient and table-entry bounds
+                uint64_t run_sq = 0;        // qubits of its uncontrolled single-qubit diagonals (tables of 6)
+                auto single_entries = [](uint64_t q) {
+                    const int k = __builtin_popcountll(q);
+                    return (k / 6) * 64 + (k % 6 ? 1 << (k % 6) : 0);
+                };
+                auto flush = [&]() {
+                    run_f = run_g = run_t = 0;
+                    run_sq = 0;
+                    if (run.empty()) return;
+                    Step stp;
+                    stp.kind = 1;
+                    stp.slot0 = nslots;
+                    stp.diag = std::make_shared<AdjDiagParams>();
+                    AdjDiagParams& A = *stp.diag;
+                    A.n_amp = 1ull << c->n;
+                    stp.tab_byte = tabs.size();
+                    // single-qubit uncontrolled diagonals multiply into per-qubit pairs, then into tables
+                    // over up to 4 qubits; every other diagonal keeps a factor of its own
+                    std::map<int, std::pair<cplx, cplx>> one;
+                    int ntab = 0;
+                    auto add_factor = [&](const AdjDiagFactor& f, const std::vector<cplx>& t) {
+                        QS_REQUIRE(A.nf < kAdjDiagMaxF, "diagonal run too long");
+                        AdjDiagFactor g = f;
+                        if (!t.empty()) {
+                            g.tab_off = ntab;
+                            for (const cplx& v : t) tabs.push_back(v);
+                            ntab += int(t.size());
                         }
-                        m &= ~(1ull << a);  // the same CZ twice cancels
+                        A.f[A.nf++] = g;
+                    };
+                    for (int gi : run) {
+                        const qs_gate& g = c->gates[gi];
+                        Op op = dagger(op_of_gate(g, c->n, theta));
+                        if (g.param_index >= 0) {
+                            uint64_t zm = 0;
+                            for (int j = 0; j < g.m; j++)
+                                if (g.kind == QS_GATE_NAMED && g.named == QS_NAMED_RZ) zm |= 1ull << g.targets[j];
+                                else if (g.pauli[j] == 3) zm |= 1ull << g.targets[j];
+                            A.gz[A.ng++] = zm;
+                            stp.params.push_back(g.param_index);
+                        }
+                        uint64_t cm = 0, cv = 0;
+                        for (size_t j = 0; j < op.controls.size(); j++) {
+                            cm |= 1ull << op.controls[j];
+                            if (op.cvals[j]) cv |= 1ull << op.controls[j];
+                        }
+                        AdjDiagFactor f;
+                        f.cond_mask = cm;
+                        f.cond_val = cv;
+                        if (op.kind == OpKind::Pauli) {
+                            f.zmask = op.zmask;
+                            add_factor(f, {});
+                        } else if (op.kind == OpKind::Phase) {
+                            if (op.phase == cplx(-1.0, 0.0)) {
+                                f.sign_only = 1;
+                                add_factor(f, {});
+                            } else if (op.phase != cplx(1.0, 0.0)) {
+                                add_factor(f, {op.phase});
+                            }
+                        } else if (op.targets.size() == 1 && cm == 0) {
+                            auto it = one.find(op.targets[0]);
+                            if (it == one.end()) one[op.targets[0]] = {op.data[0], op.data[1]};
+                            else it->second = {it->second.first * op.data[0], it->second.second * op.data[1]};
+                        } else {
+                            f.nq = int(op.targets.size());
+                            for (int j = 0; j < f.nq; j++) f.q[j] = op.targets[j];
+                            add_factor(f, op.data);
+                        }
+                    }
+                    // CZ gates (a -1 on the subspace where both of two qubits are 1, no other condition)
+                    // with the same qubit distance d share one factor: the parity of x & (x >> d) over
+                    // their lower qubits
+                    {
+                        std::map<int, uint64_t> pairs;
+                        std::vector<AdjDiagFactor> keep;
+                        for (int k = 0; k < A.nf; k++) {
+                            const AdjDiagFactor& g = A.f[k];
+                            if (g.sign_only && g.zmask == 0 && g.tab_off < 0 && __builtin_popcountll(g.cond_mask) == 2 &&
+                                g.cond_val == g.cond_mask) {
+                                const int a = __builtin_ctzll(g.cond_mask), b = 63 - __builtin_clzll(g.cond_mask);
+                                uint64_t& m = pairs[b - a];
+                                if (!((m >> a) & 1)) {
+                                    m |= 1ull << a;
+                                    continue;
+                                }
+                                m &= ~(1ull << a);  // the same CZ twice cancels
+                                continue;
+                            }
+                            keep.push_back(g);
+                        }
+                        A.nf = 0;
+                        for (const AdjDiagFactor& g : keep) A.f[A.nf++] = g;
+                        for (const auto& pm : pairs) {
+                            if (!pm.second) continue;
+                            AdjDiagFactor g;
+                            g.pair_shift = pm.first;
+                            g.pair_mask = pm.second;
+                            A.f[A.nf++] = g;
+                        }
+                    }
+                    std::vector<std::pair<int, std::pair<cplx, cplx>>> ones(one.begin(), one.end());
+                    for (size_t i0 = 0; i0 < ones.size(); i0 += 6) {
+                        AdjDiagFactor f;
+                        f.nq = int(std::min<size_t>(6, ones.size() - i0));
+                        std::vector<cplx> t(size_t(1) << f.nq, cplx(1.0, 0.0));
+                        for (int j = 0; j < f.nq; j++) {
+                            f.q[j] = ones[i0 + j].first;
+                            for (size_t li = 0; li < t.size(); li++)
+                                t[li] *= ((li >> j) & 1) ? ones[i0 + j].second.second : ones[i0 + j].second.first;
+                        }
+                        add_factor(f, t);
+                    }
+                    A.ntab = ntab;
+                    QS_REQUIRE(ntab <= kAdjDiagMaxTab, "diagonal run tables too large");
+                    nslots += A.ng;
+                    steps.push_back(std::move(stp));
+                    run.clear();
+                };
+                for (int i = c->n_gates - 1; i >= 0; i--) {
+                    const qs_gate& g = c->gates[i];
+                    const Op op = op_of_gate(g, c->n, theta);
+                    // a parametric rotation joins a diagonal run when its generator is a Z string, whatever
+                    // its matrix at this angle: RX(0) is the identity, but its derivative (i/2) X is not
+                    // diagonal and needs the rotation step
+                    bool gen_diag = true;
+                    if (g.param_index >= 0) {
+                        if (g.named == QS_NAMED_RX || g.named == QS_NAMED_RY) gen_diag = false;
+                        if (g.named == QS_NAMED_PAULIROT)
+                            for (int j = 0; j < g.m; j++) gen_diag = gen_diag && (g.pauli[j] == 0 || g.pauli[j] == 3);
+                    }
+                    const bool diag = op.kind == OpKind::Diag || op.kind == OpKind::Phase ||
+                                      (op.kind == OpKind::Pauli && op.xmask == 0);
+                    const bool diag_param = g.param_index < 0 || (gen_diag && op.kind != OpKind::Dense && g.mc == 0);
+                    if (diag && diag_param) {
+                        // bound the run by the kernel's factor, gradient and table limits (worst case);
+                        // uncontrolled single-qubit diagonals share tables of up to 6 qubits
+                        const bool single = op.kind == OpKind::Diag && op.targets.size() == 1 && op.controls.empty();
+                        const int tab_need = single ? 0 : op.kind == OpKind::Diag ? (1 << op.targets.size()) : 1;
+                        const uint64_t sq = single ? run_sq | (1ull << op.targets[0]) : run_sq;
+                        if (run_f + 1 > kAdjDiagMaxF || run_g + (g.param_index >= 0) > kAdjDiagMaxG ||
+                            run_t + tab_need + single_entries(sq) > kAdjDiagMaxTab)
+                            flush();
+                        run.push_back(i);
+                        run_f += 1;
+                        run_g += g.param_index >= 0;
+                        run_t += tab_need;
+                        if (single) run_sq |= 1ull << op.targets[0];
                         continue;
                     }
-                    keep.push_back(g);
-                }
-                A.nf = 0;
-                for (const AdjDiagFactor& g : keep) A.f[A.nf++] = g;
-                for (const auto& pm : pairs) {
-                    if (!pm.second) continue;
-                    AdjDiagFactor g;
-                    g.pair_shift = pm.first;
-                    g.pair_mask = pm.second;
-                    A.f[A.nf++] = g;
-                }
-            }
-            std::vector<std::pair<int, std::pair<cplx, cplx>>> ones(one.begin(), one.end());
-            for (size_t i0 = 0; i0 < ones.size(); i0 += 6) {
-                AdjDiagFactor f;
-                f.nq = int(std::min<size_t>(6, ones.size() - i0));
-                std::vector<cplx> t(size_t(1) << f.nq, cplx(1.0, 0.0));
-                for (int j = 0; j < f.nq; j++) {
-                    f.q[j] = ones[i0 + j].first;
-                    for (size_t li = 0; li < t.size(); li++)
-                        t[li] *= ((li >> j) & 1) ? ones[i0 + j].second.second : ones[i0 + j].second.first;
-                }
-                add_factor(f, t);
-            }
-            A.ntab = ntab;
-            QS_REQUIRE(ntab <= kAdjDiagMaxTab, "diagonal run tables too large");
-            nslots += A.ng;
-            steps.push_back(std::move(stp));
-            run.clear();
-        };
-        for (int i = c->n_gates - 1; i >= 0; i--) {
-            const qs_gate& g = c->gates[i];
-            const Op op = op_of_gate(g, c->n, theta);
-            // a parametric rotation joins a diagonal run when its generator is a Z string, whatever
-            // its matrix at this angle: RX(0) is the identity, but its derivative (i/2) X is not
-            // diagonal and needs the rotation step
-            bool gen_diag = true;
-            if (g.param_index >= 0) {
-                if (g.named == QS_NAMED_RX || g.named == QS_NAMED_RY) gen_diag = false;
-                if (g.named == QS_NAMED_PAULIROT)
-                    for (int j = 0; j < g.m; j++) gen_diag = gen_diag && (g.pauli[j] == 0 || g.pauli[j] == 3);
-            }
-            const bool diag = op.kind == OpKind::Diag || op.kind == OpKind::Phase ||
-                              (op.kind == OpKind::Pauli && op.xmask == 0);
-            const bool diag_param = g.param_index < 0 || (gen_diag && op.kind != OpKind::Dense && g.mc == 0);
-            if (diag && diag_param) {
-                // bound the run by the kernel's factor, gradient and table limits (worst case);
-                // uncontrolled single-qubit diagonals share tables of up to 6 qubits
-                const bool single = op.kind == OpKind::Diag && op.targets.size() == 1 && op.controls.empty();
-                const int tab_need = single ? 0 : op.kind == OpKind::Diag ? (1 << op.targets.size()) : 1;
-                const uint64_t sq = single ? run_sq | (1ull << op.targets[0]) : run_sq;
-                if (run_f + 1 > kAdjDiagMaxF || run_g + (g.param_index >= 0) > kAdjDiagMaxG ||
-                    run_t + tab_need + single_entries(sq) > kAdjDiagMaxTab)
                     flush();
-                run.push_back(i);
-                run_f += 1;
-                run_g += g.param_index >= 0;
-                run_t += tab_need;
-                if (single) run_sq |= 1ull << op.targets[0];
-                continue;
+                    Step stp;
+                    stp.gate = i;
+                    if (fused_rot(g)) {
+                        stp.kind = 0;
+                        stp.slot0 = nslots++;
+                    } else {
+                        stp.kind = 2;
+                    }
+                    steps.push_back(stp);
+                }
+                flush();
             }
-            flush();
-            Step stp;
-            stp.gate = i;
-            if (fused_rot(g)) {
-                stp.kind = 0;
-                stp.slot0 = nslots++;
-            } else {
-                stp.kind = 2;
+            // up to adjoint_max_rotations consecutive rotation steps on distinct qubits share one pass
+            // (their slots are adjacent)
+            {
+                const int maxr = std::min(adjoint_max_rotations(ar), c->n);
+                std::vector<Step> merged;
+                for (size_t i = 0; i < steps.size();) {
+                    if (steps[i].kind != 0 || maxr < 2) {
+                        merged.push_back(steps[i++]);
+                        continue;
+                    }
+                    size_t j = i;
+                    uint64_t used = 0;
+                    while (j < steps.size() && int(j - i) < maxr && steps[j].kind == 0 &&
+                           !((used >> c->gates[steps[j].gate].targets[0]) & 1)) {
+                        used |= 1ull << c->gates[steps[j].gate].targets[0];
+                        j++;
+                    }
+                    if (j - i >= 2) {
+                        Step m = steps[i];
+                        m.kind = 3;
+                        for (size_t t = i; t < j; t++) m.rots.push_back(steps[t].gate);
+                        merged.push_back(m);
+                    } else {
+                        merged.push_back(steps[i]);
+                    }
+                    i = j > i + 1 ? j : i + 1;
+                }
+                steps.swap(merged);
             }
-            steps.push_back(stp);
+        } catch (...) {
+            step_err = std::current_exception();
         }
-        flush();
-    }
-    // up to adjoint_max_rotations consecutive rotation steps on distinct qubits share one pass
-    // (their slots are adjacent)
-    {
-        const int maxr = std::min(adjoint_max_rotations(ar), c->n);
-        std::vector<Step> merged;
-        for (size_t i = 0; i < steps.size();) {
-            if (steps[i].kind != 0 || maxr < 2) {
-                merged.push_back(steps[i++]);
-                continue;
-            }
-            size_t j = i;
-            uint64_t used = 0;
-            while (j < steps.size() && int(j - i) < maxr && steps[j].kind == 0 &&
-                   !((used >> c->gates[steps[j].gate].targets[0]) & 1)) {
-                used |= 1ull << c->gates[steps[j].gate].targets[0];
-                j++;
-            }
-            if (j - i >= 2) {
-                Step m = steps[i];
-                m.kind = 3;
-                for (size_t t = i; t < j; t++) m.rots.push_back(steps[t].gate);
-                merged.push_back(m);
-            } else {
-                merged.push_back(steps[i]);
-            }
-            i = j > i + 1 ? j : i + 1;
+    });
+    struct Joiner {
+        std::thread& t;
+        ~Joiner() {
+            if (t.joinable()) t.join();
         }
-        steps.swap(merged);
-    }
+    } joiner{step_builder};
+
+    // forward: psi = U_G ... U_1 |0>, fused (the partition of a circuit structure is cached, so
+    // repeated calls with new angles only rebuild the block matrices)
+    // (tensor-core widths: 5 for double-float, 6 for complex64; the CUDA-core kernels' own)
+    const int kf = ar == Arith::DF && tensor_c128_enabled()     ? 5
+                   : ar == Arith::F32 && tensor_c64x_enabled() ? 6
+                   : ar == Arith::F32                           ? 4
+                                                                : 2;
+    apply_plan(psi, plan_fusion(c, kf, theta));
+    // lambda = H psi ; E = Re <psi|lambda>
+    launch_apply_observable(groups, psi->data, lam->data, c->n, ar, st);
+    double e2[2];
+    reduce_inner(psi, lam, e2);
+    *energy = e2[0];
+    for (int p = 0; p < c->n_params; p++) grad[p] = 0.0;
+    step_builder.join();
+    if (step_err) std::rethrow_exception(step_err);
     const unsigned nb = adj_grid(c->n);
     double* d_part = nullptr;
     void* d_tab = nullptr;
