@@ -65,46 +65,60 @@ __device__ __forceinline__ void acc_pair(const GradAcc<NativeArith<float>>& g, f
 }
 
 // Block sums of NR gradient partials, to part[r * gridDim.x + blockIdx.x]. FP32-pair
-// accumulators are summed across each warp as FP32 pairs (TwoSum), and only the eight warp sums in
-// FP64: GB300's FP64 rate made the warp stages of a double sum several microseconds per launch.
-// One barrier for all NR sums. The order is fixed, so results are reproducible.
+// accumulators are summed as FP32 pairs (TwoSum) across each warp and then across the eight warp
+// sums, and converted to FP64 once per block: on GB300 FP64 warp stages (or a conversion in every
+// lane) cost microseconds per launch. FP64 accumulators keep FP64 sums. One barrier for all NR
+// sums; the order is fixed, so results are reproducible.
+__device__ __forceinline__ void pair_sum_down(float& s, float& c, int o) {
+    const float os = __shfl_down_sync(0xffffffffu, s, o), oc = __shfl_down_sync(0xffffffffu, c, o);
+    float h, e;
+    DFArith::two_sum(s, os, h, e);
+    s = h;
+    c = __fadd_rn(c, __fadd_rn(oc, e));
+}
 template <typename P, int NR>
 __device__ __forceinline__ void grad_block_sums(const GradAcc<P> (&g)[NR], double* part) {
-    __shared__ double sh[NR][kAdjThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double wv[NR];
+    constexpr int W = kAdjThreads / 32;
+    if constexpr (std::is_same<P, NativeArith<double>>::value) {
+        __shared__ double sh[NR][W];
 #pragma unroll
-    for (int r = 0; r < NR; r++) {
-        if constexpr (std::is_same<P, NativeArith<double>>::value) {
+        for (int r = 0; r < NR; r++) {
             double v = g[r].imag();
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            wv[r] = v;
-        } else {
+            if (lane == 0) sh[r][wid] = v;
+        }
+        __syncthreads();
+        if (wid == 0) {
+#pragma unroll
+            for (int r = 0; r < NR; r++) {
+                double v = lane < W ? sh[r][lane] : 0.0;
+#pragma unroll
+                for (int o = W / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                if (lane == 0) part[size_t(r) * gridDim.x + blockIdx.x] = v;
+            }
+        }
+    } else {
+        __shared__ float2 sh[NR][W];
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
             float s, c;
             acc_pair(g[r], s, c);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float os = __shfl_down_sync(0xffffffffu, s, o), oc = __shfl_down_sync(0xffffffffu, c, o);
-                float h, e;
-                DFArith::two_sum(s, os, h, e);
-                s = h;
-                c = __fadd_rn(c, __fadd_rn(oc, e));
-            }
-            wv[r] = double(s) + double(c);
+            for (int o = 16; o > 0; o >>= 1) pair_sum_down(s, c, o);
+            if (lane == 0) sh[r][wid] = make_float2(s, c);
         }
-    }
-    if (lane == 0)
+        __syncthreads();
+        if (wid == 0) {
 #pragma unroll
-        for (int r = 0; r < NR; r++) sh[r][wid] = wv[r];
-    __syncthreads();
-    if (wid == 0) {
+            for (int r = 0; r < NR; r++) {
+                const float2 v = lane < W ? sh[r][lane] : make_float2(0.f, 0.f);
+                float s = v.x, c = v.y;
 #pragma unroll
-        for (int r = 0; r < NR; r++) {
-            double v = lane < kAdjThreads / 32 ? sh[r][lane] : 0.0;
-#pragma unroll
-            for (int o = kAdjThreads / 64; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) part[size_t(r) * gridDim.x + blockIdx.x] = v;
+                for (int o = W / 2; o > 0; o >>= 1) pair_sum_down(s, c, o);
+                if (lane == 0) part[size_t(r) * gridDim.x + blockIdx.x] = double(s) + double(c);
+            }
         }
     }
 }
@@ -438,9 +452,12 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_diag(typename P::C* __restr
                 if (F.sign_only) {
                     sign ^= 1;
                 } else if (F.tab_off >= 0) {
-                    int li = 0;
-                    for (int b = 0; b < F.nq; b++) li |= int((x >> F.q[b]) & 1) << b;
-                    f = kmul(f, stab[F.tab_off + li]);
+                    uint32_t li = 0;
+                    for (int b = 0; b < F.nrun; b++) {
+                        const uint32_t c = F.run[b];
+                        li |= (uint32_t(x >> (c & 0xFFu)) & ((1u << ((c >> 8) & 0xFFu)) - 1u)) << (c >> 16);
+                    }
+                    f = kmul(f, stab[F.tab_off + int(li)]);
                 }
             }
             p = P::out(P::first(f, p));

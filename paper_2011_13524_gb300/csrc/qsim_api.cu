@@ -1223,6 +1223,13 @@ qs_status qs_adjoint_grad(const qs_circuit* c, const double* theta, const qs_pau
                     auto add_factor = [&](const AdjDiagFactor& f, const std::vector<cplx>& t) {
                         QS_REQUIRE(A.nf < kAdjDiagMaxF, "diagonal run too long");
                         AdjDiagFactor g = f;
+                        g.nrun = 0;
+                        for (int j = 0; j < g.nq;) {
+                            int k = j + 1;
+                            while (k < g.nq && g.q[k] == g.q[k - 1] + 1) k++;
+                            g.run[g.nrun++] = uint32_t(g.q[j]) | (uint32_t(k - j) << 8) | (uint32_t(j) << 16);
+                            j = k;
+                        }
                         if (!t.empty()) {
                             g.tab_off = ntab;
                             for (const cplx& v : t) tabs.push_back(v);

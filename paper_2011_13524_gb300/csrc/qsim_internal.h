@@ -356,6 +356,10 @@ struct AdjDiagFactor {
     int32_t tab_off = -1;                  // table of 2^nq entries (or none)
     int32_t nq = 0;
     int32_t q[6] = {0, 0, 0, 0, 0, 0};     // table index bit j = bit q[j] of x
+    // the same gather as runs of consecutive q (consecutive j): x bits from (run & 0xFF), width
+    // (run >> 8) & 0xFF, to table index bits from run >> 16
+    int32_t nrun = 0;
+    uint32_t run[6] = {0, 0, 0, 0, 0, 0};
 };
 struct AdjDiagParams {
     uint64_t n_amp = 0;
