@@ -3,8 +3,9 @@
 // the state instead of one pass per gate; merging multiplies the arithmetic by
 // 2^(|M1 u M2| - |M1|) and halves the memory traffic.
 //
-// Two partitions of the gate list into blocks of at most k qubits are formed and the one with
-// fewer blocks is kept (ties: the first).
+// Partitions of the gate list into blocks of at most k qubits are formed by two methods (the
+// second with three lookahead depths) and the one with the fewest blocks is kept (ties: the
+// first).
 //
 // 1. Open-block greedy (the light strategy with a width budget k): every qubit belongs to at
 //    most one open block. A gate whose qubits (targets and controls) meet a set S of open
