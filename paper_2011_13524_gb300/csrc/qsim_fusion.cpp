@@ -28,6 +28,7 @@
 #include <list>
 #include <mutex>
 #include <thread>
+#include <unordered_map>
 
 #include "qsim_internal.h"
 
@@ -314,13 +315,14 @@ struct Frontier {
         }
         return added;
     }
-    // Distinct qubit sets q | m of the ready gates that widen q without exceeding k qubits.
-    std::vector<uint64_t> widening(uint64_t q, int k) {
+    // Distinct qubit sets q | m of the ready gates that widen q without exceeding k qubits; with
+    // id >= 0 the gates of trial id count as members too.
+    std::vector<uint64_t> widening(uint64_t q, int k, int id = -1) {
         std::vector<uint64_t> cand;
         Scan sc;
         for (int g : rem) {
             visits++;
-            if (member(g, false)) continue;
+            if (in[g] == blk || (id >= 0 && trial[g] == id)) continue;
             const uint64_t m = masks[g];
             if ((m & ~q) && __builtin_popcountll(q | m) <= k && sc.ready(m, tags[g]) &&
                 std::find(cand.begin(), cand.end(), q | m) == cand.end())
@@ -332,26 +334,49 @@ struct Frontier {
     }
 };
 
-// The most gates that `levels` more widenings of q can add, the trial gates of the last
-// close_over (tid) counted in the block meanwhile.
-int lookahead(Frontier& f, const std::vector<int>& rem, uint64_t q, int k, int levels) {
-    const int t1 = f.tid;
-    std::vector<int> added;
-    for (int g : rem)
-        if (f.trial[g] == t1 && f.in[g] != f.blk) {
-            f.in[g] = f.blk;
-            added.push_back(g);
-        }
-    int more = 0;
-    for (uint64_t u2 : f.widening(q, k)) {
-        f.tid++;
-        int got = f.close_over(u2, true);
-        if (levels > 1 && __builtin_popcountll(u2) < k) got += lookahead(f, rem, u2, k, levels - 1);
-        more = std::max(more, got);
+// Lookahead over widenings, for a fixed block membership B. The gates a qubit set X can hold,
+// closure(X), grow with X, and one ordered scan finds them (a gate joins when it lies in X and no
+// earlier non-member on its qubits blocks it). So the gates a chain of widenings q -> u -> u2 ...
+// adds in total are |closure(last) \ B|, and the search needs, per distinct X, only that count
+// and X's widenings (given B and closure(X)); both are memoized until B changes.
+struct Lookahead {
+    Frontier& f;
+    int k;
+    std::unordered_map<uint64_t, int> cnt;
+    std::unordered_map<uint64_t, std::vector<uint64_t>> wid;
+    void reset() {
+        cnt.clear();
+        wid.clear();
     }
-    for (int g : added) f.in[g] = -1;
-    return more;
-}
+    int count(uint64_t X) {
+        auto it = cnt.find(X);
+        if (it != cnt.end()) return it->second;
+        f.tid++;
+        const int v = f.close_over(X, true);
+        cnt.emplace(X, v);
+        return v;
+    }
+    std::vector<uint64_t> widenings(uint64_t X) {
+        auto it = wid.find(X);
+        if (it != wid.end()) return it->second;
+        f.tid++;
+        f.close_over(X, true);
+        std::vector<uint64_t> w = f.widening(X, k, f.tid);
+        wid.emplace(X, w);
+        return w;
+    }
+    // the most gates that `levels` more widenings of X add beyond closure(X)
+    int more(uint64_t X, int levels) {
+        const int cx = count(X);
+        int best = 0;
+        for (uint64_t u2 : widenings(X)) {
+            int got = count(u2) - cx;
+            if (levels > 1 && __builtin_popcountll(u2) < k) got += more(u2, levels - 1);
+            best = std::max(best, got);
+        }
+        return best;
+    }
+};
 
 // depth: 1 picks each widening by the gates it absorbs; d > 1 by the best total after d - 1
 // more widenings (each trial runs on top of the previous one's membership).
@@ -365,6 +390,7 @@ std::vector<OpenBlock> partition_frontier(const qs_circuit* c, const std::vector
     std::vector<int> in(c->n_gates, -1), trial(c->n_gates, -1);
     const uint64_t all = c->n >= 64 ? ~0ull : ((1ull << c->n) - 1);
     Frontier f{masks, tags, rem, all, in, trial};
+    Lookahead la{f, k, {}, {}};
     while (!rem.empty()) {
         if (max_visits >= 0 && f.visits > max_visits) return {};
         uint64_t q = masks[rem[0]];
@@ -373,12 +399,12 @@ std::vector<OpenBlock> partition_frontier(const qs_circuit* c, const std::vector
         while (__builtin_popcountll(q) < k) {
             const std::vector<uint64_t> cand = f.widening(q, k);
             if (cand.empty()) break;
+            la.reset();  // the block's membership changed
             int best = -1;
             uint64_t best_q = 0;
             for (uint64_t u : cand) {
-                f.tid++;
-                int got = f.close_over(u, true);
-                if (depth > 1 && __builtin_popcountll(u) < k) got += lookahead(f, rem, u, k, depth - 1);
+                int got = la.count(u);
+                if (depth > 1 && __builtin_popcountll(u) < k) got += la.more(u, depth - 1);
                 // more gates first, then the narrower set
                 if (got > best || (got == best && __builtin_popcountll(u) < __builtin_popcountll(best_q))) {
                     best = got;
