@@ -114,6 +114,24 @@ def test_fusion_reduces_block_count():
     assert counts[4] <= 80 and counts[6] <= 42, counts
 
 
+def test_fusion_benchmark_plans():
+    """The plans of the benchmark workloads (host only): the depth-20 U3+CZ circuit at n = 30 in
+    at most 74 / 53 / 36 blocks at k = 4 / 5 / 6, and 50 launches at k = 5 (its trailing diagonal
+    blocks share one pass); the 20-layer ansatz at n = 20 in at most 35 blocks at k = 5. Planning
+    twice from an empty partition cache gives the same plan."""
+    c = W.u3cz_circuit(30, 20, 20201127)
+    bound = {4: 74, 5: 53, 6: 36}
+    for k, b in bound.items():
+        assert qs.FusedCircuit(c, k).n_blocks <= b, k
+    plan = qs.FusedCircuit(c, 5)
+    assert sum(plan.block_cost(i, qs.QS_C128)[1] for i in range(plan.n_blocks)) <= 50
+    first = [tuple(plan.block(i)[0]) for i in range(plan.n_blocks)]
+    qs.clear_plan_cache()
+    again = qs.FusedCircuit(c, 5)
+    assert [tuple(again.block(i)[0]) for i in range(again.n_blocks)] == first
+    assert qs.FusedCircuit(W.hea_circuit(20, 20, 20201127), 5).n_blocks <= 35
+
+
 def commuting_mix_circuit(n, seed):
     """Gates that commute in several bases: diagonal layers (CZ, RZ, S, T, U1, controlled phases,
     DIAG), X-basis layers (RX, CNOT targets, sqrtX, X-string PAULIROT), Y rotations, PAULI and
